@@ -1,0 +1,2 @@
+"""CPU FP64 oracle (test infrastructure only; see dme_oracle's header)."""
+from .dme_oracle import *  # noqa: F401,F403
