@@ -1,0 +1,295 @@
+"""Benchmark: Strang steps/s of the large dense DRE (n = 4096) on one GB300.
+
+Workload (the metric's configuration): A = 5-point Dirichlet Laplacian on a
+64 x 64 grid (n = 4096), B = N(0,1) n x 8, R = I_8, C = U(0,1) 8 x n
+(Q = C^T C), P0 = 0, T = 1, h = T/256, Strang F12F3:
+T12(h/2) T3(h) T12(h/2) per step.  One step = one pass of the whole hot path
+(two congruences E^T P E + W and one Riccati update).  All data are seeded
+synthetic inputs; the P, E, W, X working set (4 x 134 MB) exceeds the 129 MB
+L2, so no flush is needed between timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|split|both]
+    python bench.py --impl reference      # the CPU FP64 oracle on the same workload
+
+With N > 1 (torchrun) every rank runs an independent replica (the path has no
+exchange step); value = steps of all ranks / max over ranks of the time.
+Prints ONE JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import dme_workloads as W  # noqa: E402
+
+METRIC = "Strang steps/s at n=4096 (FP64 vs split-prec @1e-7); mixed-n solves/s, p99 ms"
+WORKLOAD = ("large dense DRE: 5-point Laplacian 64x64 (n=4096), B 4096x8 N(0,1), R=I_8, C 8x4096 U(0,1), "
+            "P0=0, T=1, h=1/256, Strang F12F3")
+NOMINAL_FP64_TFLOPS = 1.25    # GB300 FP64 (non-tensor and tensor), the profiling recipe's nominal figure
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return rank, ws, local, dist
+
+
+# ------------------------------------------------------------------ oracle (CPU)
+def oracle_steps(pr, nsteps, E=None, Wm=None):
+    """Time nsteps oracle Strang F12F3 steps of the workload; returns (seconds, E, W)."""
+    import oracle as O
+    h = pr.T / 256
+    plan = O.Plan(pr.A, pr.Q, pr.B, pr.R)
+    if E is None:
+        E, Wm = O.van_loan(pr.A, pr.Q, 0.5 * h)
+    plan._ew[float(0.5 * h)] = (E, Wm)
+    P = np.array(pr.P0)
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        P = plan.step(P, "strang", ["F12", "F3"], h)
+    return time.perf_counter() - t0, E, Wm
+
+
+def run_reference(args):
+    rank, ws, _, dist = dist_init()
+    if rank != 0:
+        return 0
+    pr = W.dre_heat_large()
+    t0 = time.perf_counter()
+    _, E, Wm = oracle_steps(pr, 0)
+    plan_s = time.perf_counter() - t0
+    oracle_steps(pr, args.warmup, E, Wm)
+    secs, _, _ = oracle_steps(pr, args.steps, E, Wm)
+    v = args.steps / secs
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "impl": "CPU FP64 oracle (numpy/OpenBLAS)"},
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{args.steps} oracle Strang F12F3 steps at n=4096 after {args.warmup} "
+                                       f"warm-up steps; oracle plan (2n x 2n Pade expm) {plan_s:.1f} s untimed"},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import torch
+    rank, ws, local, dist = dist_init()
+    import paper_1805_08990_gb300 as dme
+    from paper_1805_08990_gb300 import build
+    build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    peaks, peaks_src = load_peaks()
+    pr = W.dre_heat_large()
+    n = pr.n
+    K, Wu = args.steps, args.warmup
+    h = pr.T / 256
+    stream = torch.cuda.Stream(device=dev)
+
+    def to_dev(x):
+        return torch.as_tensor(x, dtype=torch.float64, device=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    results = {}
+    precs = ["fp64", "split"] if args.prec == "both" else [args.prec]
+    for prec in precs:
+        kprec = "fp64" if prec == "fp64" else "split_bf16"
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            plan = dme.Plan(to_dev(pr.A), C=to_dev(pr.C), h=h, flows=["F12", "F3"], comp="strang",
+                            B=to_dev(pr.B), R=to_dev(pr.R), prec=kprec, stream=stream)
+        plan_s = time.perf_counter() - t0
+        P = torch.zeros(n, n, dtype=torch.float64, device=dev)
+        steps = K if prec == "fp64" else args.split_steps
+        warm = Wu
+        plan.step(P, warm)
+        torch.cuda.synchronize(dev)
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            e0.record(stream)
+            plan.step(P, steps)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+        barrier()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        kps = plan.kernels_per_step
+        # dominant kernel: the congruence E^T P E (+ W), timed alone with events on the plan's stream
+        R = 3 if prec == "fp64" else 20
+        Pc = P.clone()
+        plan.apply_async("F12", 0.5 * h, Pc)
+        plan.sync()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(R):
+            plan.apply_async("F12", 0.5 * h, Pc)
+        c1.record(stream)
+        plan.sync()
+        cong_ms = c0.elapsed_time(c1) / R
+        # end to end through the C ABI with host buffers: H2D of P0, K steps, D2H of P(T)
+        P0h = torch.zeros(n, n, dtype=torch.float64).pin_memory()
+        Ph = torch.empty(n, n, dtype=torch.float64).pin_memory()
+        plan.solve(P0h, steps * h, steps, Ph)        # E, W for this h already cached
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        plan.solve(P0h, steps * h, steps, Ph)
+        e2e_s = time.perf_counter() - t0
+        results[prec] = {"ms": ms, "steps": steps, "kps": kps, "cong_ms": cong_ms, "plan_s": plan_s,
+                         "e2e_s": e2e_s, "clocks": clk.summary(), "P": P, "bytes": plan.nbytes}
+        plan.close()
+
+    head = "split" if "split" in results else "fp64"
+    r = results[head]
+    value = ws * r["steps"] / (r["ms"] / 1e3)
+    cong_flops = 3.0 * n ** 3          # P E (2n^3) + upper triangle of E^T X (n^3)
+    if head == "fp64":
+        achieved = cong_flops / (r["cong_ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": None,
+                "kernel": "gemm64_batch_kernel (congruence, 2 launches)",
+                "peak_source": "nominal GB300 FP64 rate (profiling recipe table)"}
+    else:
+        roof = r.get("roof")
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": r["steps"], "warmup": Wu,
+        "ms_per_step": r["ms"] / r["steps"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if head == "fp64" else "bf16-slices/f32-exact/f64",
+        "data": "synthetic (seeded generators; no datasets or weights)",
+        "config": {"workload": WORKLOAD, "prec": head, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": "working set P,E,W,X = 536 MB > L2 (no flush)", "plan_s": r["plan_s"],
+                   "device_bytes": r["bytes"]},
+        "roofline": roof,
+        "e2e": {"value": r["steps"] / r["e2e_s"], "unit": "steps/s", "h2d_bytes_per_step": 8 * n * n / r["steps"],
+                "d2h_bytes_per_step": 8 * n * n / r["steps"],
+                "what": f"dme_solve with pinned host P0 and P_out, {r['steps']} steps per call"},
+        "gpu_launches": r["kps"] * r["steps"],
+        "clocks": r["clocks"],
+    }
+    for prec, rr in results.items():
+        line[f"{prec}_steps_per_s"] = ws * rr["steps"] / (rr["ms"] / 1e3)
+        line[f"{prec}_plan_s"] = rr["plan_s"]
+    line["peaks_source"] = peaks_src
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        secs, _, _ = oracle_steps(pr, args.cpu_steps)
+        line["cpu_baseline"] = {"value": args.cpu_steps / secs, "unit": "steps/s", "cores": os.cpu_count(),
+                                "kind": "oracle",
+                                "sample": f"{args.cpu_steps} oracle Strang F12F3 steps at n=4096 (numpy/OpenBLAS, "
+                                          "FP64); the oracle's own 2n x 2n expm for E, W is untimed"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "split", "both"])
+    ap.add_argument("--split-steps", type=int, default=64)
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,166 @@
+/*
+ * dme.h -- C ABI of libdme.so: dense splitting schemes for differential
+ * Lyapunov and Riccati equations on one GB300 (sm_103a).
+ *
+ * Problem class (Mena, Pfurtscheller & Stillfjord, arXiv:1805.08990, §1):
+ *     dP/dt = A^T P + P A + Q + G(P),   P(0) = P0,
+ *     G = 0 (DLE, Eq. lyap), G(P) = -P B R^{-1} B^T P (DRE, Eq. ricc),
+ *     plus S P S^T in the generalised forms (Eq. lyapGen, §2.4).
+ *
+ * Sub-flows (§2): T1(t)P = e^{tA^T} P e^{tA}; T2(t)P = P + tQ;
+ * T12(t)P = E^T P E + W with E = e^{tA}, W = int_0^t e^{sA^T} Q e^{sA} ds
+ * (Eq. full); T3(t)P = (I + t P B R^{-1} B^T)^{-1} P (Eq. nonlinear), applied
+ * through an m x m solve; T4(t)P ~ P + t S(P + t/2 S P S^T)S^T (midpoint, §2.3)
+ * or P + t S P S^T (explicit Euler, enough for Lie).  Compositions (§2, §3):
+ * Lie applies the listed flows in order, each over h; Strang "Fa Fb Fc" applies
+ * Ta(h/2) Tb(h/2) Tc(h) Tb(h/2) Ta(h/2).
+ *
+ * Conventions for every entry point:
+ *  - Matrices are float64, row-major, dense, leading dimension = column count.
+ *  - Pointers may be host or device memory (detected per pointer); the caller
+ *    owns them and keeps them valid for the duration of the call.  The plan
+ *    copies A, Q/C, B, R, S into plan-owned device buffers.
+ *  - Functions return a dme_status and never throw across the ABI; the text
+ *    of the last error of the calling thread is returned by dme_last_error().
+ *  - Work is enqueued on the plan's CUDA stream; every entry point that
+ *    reports a device status synchronises that stream before returning.
+ */
+#ifndef DME_H
+#define DME_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DME_OK = 0,
+    DME_EINVAL = 1,     /* bad argument (sizes, flags, null where required)      */
+    DME_ENOMEM = 2,     /* device allocation failed or HBM budget exceeded       */
+    DME_ENOTSPD = 3,    /* R, or I_m + t Bt^T P Bt, failed its Cholesky           */
+    DME_ECUDA = 4,      /* a CUDA runtime/driver call failed                      */
+    DME_ETIMEOUT = 5,   /* dme_poll waited longer than its timeout                */
+    DME_EBUSY = 6,      /* server has no free slot and the queue is full          */
+    DME_ENOTREADY = 7   /* request not finished (dme_poll with timeout 0)         */
+} dme_status;
+
+typedef enum { DME_DLE = 0, DME_DRE = 1, DME_GDLE = 2, DME_GDRE = 3 } dme_eq;
+/* sub-flows T1, T2, T12, T3, T4 of §2 */
+typedef enum { DME_F1 = 1, DME_F2 = 2, DME_F12 = 3, DME_F3 = 4, DME_F4 = 5 } dme_flow;
+typedef enum { DME_LIE = 1, DME_STRANG = 2 } dme_comp;
+/* DME_FP64: every product in float64 on the FP64 pipe.
+ * DME_SPLIT_BF16: congruences as error-free bf16 slice products on tcgen05
+ *   tensor cores accumulated exactly in fp32 (Ozaki splitting), combined in
+ *   fp64; the m x m solves, expm denominator solve and squaring stay fp64. */
+typedef enum { DME_FP64 = 0, DME_SPLIT_BF16 = 1 } dme_prec;
+/* T4 rule; AUTO = midpoint for Strang, explicit Euler for Lie (§2.3). */
+typedef enum { DME_T4_AUTO = 0, DME_T4_MIDPOINT = 1, DME_T4_EULER = 2 } dme_t4_rule;
+
+typedef struct {
+    int n;              /* state dimension, 1 <= n <= 16384                          */
+    int m;              /* columns of B (DRE/GDRE), 0 otherwise, m <= 32             */
+    int p;              /* rows of C when q_is_factor = 1 (Q = C^T C)                 */
+    int eq;             /* dme_eq                                                     */
+    int comp;           /* dme_comp                                                   */
+    int nflows;         /* 1..4                                                       */
+    int flows[4];       /* dme_flow list in application order (e.g. F12,F3)          */
+    int prec;           /* dme_prec                                                   */
+    double h;           /* step size                                                  */
+    int q_is_factor;    /* 1: QorC is C (p x n); 0: QorC is Q (n x n, symmetric)      */
+    int t4_rule;        /* dme_t4_rule                                                */
+    int slices;         /* DME_SPLIT_BF16: bf16 slices per operand, 0 = default (4)   */
+} dme_plan_desc;
+
+typedef struct dme_plan_s* dme_plan_t;
+typedef struct dme_server_s* dme_server_t;
+
+/* Build a plan: copy the problem data to the device, form Q = C^T C (if
+ * q_is_factor), Bt = B L_R^{-T} with R = L_R L_R^T (so B R^{-1} B^T = Bt Bt^T),
+ * and, for every step length t the scheme uses in T1/T12, E_t = e^{tA} and
+ * W_t (Eq. full) by [13/13] Pade scaling and squaring of the Van Loan matrix
+ * t[[-A^T, Q],[0, A]] (its 1-norm sets the squarings; the exponential is
+ * built from its n x n blocks, see dme_expm).
+ *   A: n x n.  QorC: n x n or p x n.  B: n x m (NULL unless DRE/GDRE).
+ *   R: m x m SPD (NULL unless DRE/GDRE).  S: n x n (NULL unless GDLE/GDRE).
+ *   cuda_stream: a cudaStream_t, or NULL for a plan-owned stream.
+ * Errors: DME_EINVAL (inconsistent desc), DME_ENOTSPD (R), DME_ENOMEM,
+ * DME_ECUDA.  On error *out is NULL. */
+dme_status dme_plan(const dme_plan_desc* desc, const double* A, const double* QorC,
+                    const double* B, const double* R, const double* S,
+                    void* cuda_stream, dme_plan_t* out);
+
+/* Export E_t = e^{tA} and W_t = int_0^t e^{sA^T} Q e^{sA} ds (Eq. full),
+ * computing and caching them if t is new.  E_out / W_out: n x n, host or
+ * device, either may be NULL. */
+dme_status dme_expm(dme_plan_t plan, double t, double* E_out, double* W_out);
+
+/* Apply one sub-flow T_flow(t) in place to the symmetric n x n state P
+ * (device memory).  The result is exactly symmetric. */
+dme_status dme_apply(dme_plan_t plan, int flow, double t, double* P);
+
+/* dme_apply without the final synchronisation: the sub-flow is only
+ * enqueued on the plan's stream.  Device-side failures (DME_ENOTSPD) are
+ * reported by the next dme_sync (or any synchronising call) on the plan. */
+dme_status dme_apply_async(dme_plan_t plan, int flow, double t, double* P);
+
+/* Wait for the plan's stream and report any device-side status raised since
+ * the last synchronising call. */
+dme_status dme_sync(dme_plan_t plan);
+
+/* Advance P (device, n x n, symmetric) by nsteps steps of the plan's
+ * composition with the plan's h, in place.  Steps are replayed from a CUDA
+ * graph captured on first use for this P. */
+dme_status dme_step(dme_plan_t plan, double* P, int nsteps);
+
+/* P_out = P_N, N = nsteps steps of size h = T/nsteps from P0 (§2).  If
+ * T/nsteps differs from desc.h the missing E_t, W_t are built first.
+ * P0, P_out: n x n, host or device; P_out may equal P0. */
+dme_status dme_solve(dme_plan_t plan, const double* P0, double T, int nsteps, double* P_out);
+
+/* Bytes of device memory the plan holds. */
+size_t dme_plan_bytes(dme_plan_t plan);
+
+/* Kernel nodes in the CUDA graph of one step (captured by the last
+ * dme_step / dme_solve), or -1 if no step has been captured yet. */
+int dme_plan_kernels_per_step(dme_plan_t plan);
+
+dme_status dme_plan_destroy(dme_plan_t plan);
+
+/* ---- serving: continuous batching of independent DRE/DLE solves ----------
+ * A server owns one stream and a worker thread.  Requests are admitted into
+ * slots while their device footprint (P, E, W and work buffers) fits in
+ * hbm_budget_bytes and a slot is free; every resident request advances one
+ * composition step per scheduler round through grouped kernels covering all
+ * resident requests, so newly admitted requests overlap with running ones. */
+dme_status dme_server_create(size_t hbm_budget_bytes, int max_slots, dme_server_t* out);
+
+/* Queue one solve of nsteps steps over [0, T] (h = T/nsteps; desc->h is
+ * ignored).  All pointers are host memory and are copied before return.
+ * *ticket identifies the request for dme_poll.  DME_EBUSY if the queue is full;
+ * DME_ENOMEM if the request alone exceeds the budget. */
+dme_status dme_submit(dme_server_t srv, const dme_plan_desc* desc, const double* A,
+                      const double* QorC, const double* B, const double* R,
+                      const double* S, const double* P0, double T, int nsteps,
+                      uint64_t* ticket);
+
+/* Wait up to timeout_us (0: do not wait, < 0: forever) for a request; on
+ * completion copy P(T) into P_out (host, n x n, may be NULL) and release the
+ * ticket.  DME_ENOTREADY (timeout 0) / DME_ETIMEOUT if still running; the
+ * request's own error status (e.g. DME_ENOTSPD) once it has failed. */
+dme_status dme_poll(dme_server_t srv, uint64_t ticket, double* P_out, int64_t timeout_us);
+
+/* Server statistics as a JSON object (completed, failed, resident, queued,
+ * p50/p99 latency in ms, solves/s); the string stays valid until the next call. */
+const char* dme_server_stats(dme_server_t srv);
+
+dme_status dme_server_destroy(dme_server_t srv);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* dme_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DME_H */

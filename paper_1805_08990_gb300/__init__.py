@@ -1,0 +1,79 @@
+"""GB300-native dense splitting schemes for differential Lyapunov and Riccati
+equations (Mena, Pfurtscheller & Stillfjord, arXiv:1805.08990).
+
+The compute path is libdme.so (CUDA for sm_103a, C ABI in include/dme.h);
+this package only marshals arguments to it.  Importing the package does not
+load the library; the first call does, and fails loudly if it is not built.
+"""
+from .binding import (  # noqa: F401
+    DME_DLE, DME_DRE, DME_GDLE, DME_GDRE, DME_F1, DME_F2, DME_F12, DME_F3, DME_F4,
+    DME_LIE, DME_STRANG, DME_FP64, DME_SPLIT_BF16, DME_T4_AUTO, DME_T4_MIDPOINT, DME_T4_EULER,
+    DME_OK, DME_EINVAL, DME_ENOMEM, DME_ENOTSPD, DME_ECUDA, DME_ETIMEOUT, DME_EBUSY, DME_ENOTREADY,
+    DmeError, LibraryNotBuilt, dme_plan_desc, make_desc, lib, header_functions,
+    dme_plan, dme_expm, dme_apply, dme_apply_async, dme_sync, dme_plan_kernels_per_step, dme_step, dme_solve, dme_plan_bytes, dme_plan_destroy,
+    dme_server_create, dme_submit, dme_poll, dme_server_stats, dme_server_destroy, dme_last_error,
+)
+
+EQ_IDS = {"dle": DME_DLE, "dre": DME_DRE, "gdle": DME_GDLE, "gdre": DME_GDRE}
+
+
+class Plan:
+    """Owning wrapper of a dme_plan_t.
+
+    ``Plan(A, C, h, scheme=["F12", "F3"], comp="strang", B=B, R=R)`` with
+    Q = C^T C (``q_is_factor``) or ``Q=...`` for a dense Q."""
+
+    def __init__(self, A, C=None, h=1e-3, flows=("F12",), comp="strang", B=None, R=None, S=None,
+                 Q=None, prec="fp64", t4_rule=DME_T4_AUTO, slices=0, stream=None):
+        n = int(A.shape[0])
+        m = 0 if B is None else int(B.shape[1])
+        eq = ("g" if S is not None else "") + ("dre" if B is not None else "dle")
+        if Q is None and C is None:
+            raise ValueError("give C (Q = C^T C) or Q")
+        self.n, self.m = n, m
+        self.desc = make_desc(n, m=m, p=0 if C is None else int(C.shape[0]), eq=EQ_IDS[eq], comp=comp,
+                              flows=flows, prec=prec, h=h, q_is_factor=Q is None, t4_rule=t4_rule, slices=slices)
+        self.handle = dme_plan(self.desc, A, C if Q is None else Q, B, R, S, stream)
+
+    def expm(self, t, E_out=None, W_out=None):
+        dme_expm(self.handle, t, E_out, W_out)
+
+    def apply(self, flow, t, P):
+        dme_apply(self.handle, flow, t, P)
+
+    def apply_async(self, flow, t, P):
+        dme_apply_async(self.handle, flow, t, P)
+
+    def sync(self):
+        dme_sync(self.handle)
+
+    @property
+    def kernels_per_step(self):
+        return dme_plan_kernels_per_step(self.handle)
+
+    def step(self, P, nsteps=1):
+        dme_step(self.handle, P, nsteps)
+
+    def solve(self, P0, T, nsteps, P_out):
+        dme_solve(self.handle, P0, T, nsteps, P_out)
+
+    @property
+    def nbytes(self):
+        return dme_plan_bytes(self.handle)
+
+    def close(self):
+        if self.handle:
+            dme_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,245 @@
+"""ctypes binding of libdme.so (include/dme.h).  Argument marshalling only:
+every step of the splitting schemes runs in the library's CUDA kernels.
+
+Matrices are passed as torch tensors (CUDA or CPU) or numpy arrays; they must
+be float64 and C-contiguous (they are made so, which copies if needed).  The
+library itself decides host vs device per pointer.  There is no fallback:
+if libdme.so is missing, every call raises ``LibraryNotBuilt``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "lib", "libdme.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "dme.h")
+
+DME_OK, DME_EINVAL, DME_ENOMEM, DME_ENOTSPD, DME_ECUDA, DME_ETIMEOUT, DME_EBUSY, DME_ENOTREADY = range(8)
+STATUS_NAMES = ["DME_OK", "DME_EINVAL", "DME_ENOMEM", "DME_ENOTSPD", "DME_ECUDA", "DME_ETIMEOUT",
+                "DME_EBUSY", "DME_ENOTREADY"]
+DME_DLE, DME_DRE, DME_GDLE, DME_GDRE = range(4)
+DME_F1, DME_F2, DME_F12, DME_F3, DME_F4 = 1, 2, 3, 4, 5
+DME_LIE, DME_STRANG = 1, 2
+DME_FP64, DME_SPLIT_BF16 = 0, 1
+DME_T4_AUTO, DME_T4_MIDPOINT, DME_T4_EULER = 0, 1, 2
+
+FLOW_IDS = {"F1": DME_F1, "F2": DME_F2, "F12": DME_F12, "F3": DME_F3, "F4": DME_F4}
+COMP_IDS = {"lie": DME_LIE, "strang": DME_STRANG}
+PREC_IDS = {"fp64": DME_FP64, "split_bf16": DME_SPLIT_BF16}
+
+
+class LibraryNotBuilt(RuntimeError):
+    pass
+
+
+class DmeError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{where}: {name}: {msg}")
+
+
+class dme_plan_desc(C.Structure):
+    _fields_ = [("n", C.c_int), ("m", C.c_int), ("p", C.c_int), ("eq", C.c_int), ("comp", C.c_int),
+                ("nflows", C.c_int), ("flows", C.c_int * 4), ("prec", C.c_int), ("h", C.c_double),
+                ("q_is_factor", C.c_int), ("t4_rule", C.c_int), ("slices", C.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_SIGS = {
+    "dme_plan": (C.c_int, [C.POINTER(dme_plan_desc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                           C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "dme_expm": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
+    "dme_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p]),
+    "dme_apply_async": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p]),
+    "dme_sync": (C.c_int, [C.c_void_p]),
+    "dme_plan_kernels_per_step": (C.c_int, [C.c_void_p]),
+    "dme_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "dme_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_void_p]),
+    "dme_plan_bytes": (C.c_size_t, [C.c_void_p]),
+    "dme_plan_destroy": (C.c_int, [C.c_void_p]),
+    "dme_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]),
+    "dme_submit": (C.c_int, [C.c_void_p, C.POINTER(dme_plan_desc), C.c_void_p, C.c_void_p, C.c_void_p,
+                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_uint64)]),
+    "dme_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int64]),
+    "dme_server_stats": (C.c_char_p, [C.c_void_p]),
+    "dme_server_destroy": (C.c_int, [C.c_void_p]),
+    "dme_last_error": (C.c_char_p, []),
+}
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/dme.h declares."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(dme_[a-z_]+)\s*\(", txt)))
+
+
+def lib():
+    """Load libdme.so (once).  Raises LibraryNotBuilt if it is absent."""
+    global _lib
+    if _lib is None:
+        with _lock:
+            if _lib is None:
+                if not os.path.exists(LIB_PATH):
+                    raise LibraryNotBuilt(f"{LIB_PATH} is missing: run paper_1805_08990_gb300.build.build()")
+                L = C.CDLL(LIB_PATH)
+                for name, (res, args) in _SIGS.items():
+                    f = getattr(L, name)
+                    f.restype = res
+                    f.argtypes = args
+                _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return (lib().dme_last_error() or b"").decode()
+
+
+def _check(status: int, where: str):
+    if status != DME_OK:
+        raise DmeError(status, where, last_error())
+
+
+def _ptr(x, keep: list):
+    """Raw pointer of a float64 C-contiguous matrix (torch tensor or numpy array)."""
+    if x is None:
+        return None
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if x.dtype != torch.float64 or not x.is_contiguous():
+                x = x.to(torch.float64).contiguous()
+            keep.append(x)
+            return x.data_ptr()
+    except ImportError:
+        pass
+    import numpy as np
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    keep.append(a)
+    return a.ctypes.data
+
+
+def make_desc(n, *, m=0, p=0, eq=DME_DLE, comp="strang", flows=("F12",), prec="fp64", h=1e-3,
+              q_is_factor=False, t4_rule=DME_T4_AUTO, slices=0) -> dme_plan_desc:
+    d = dme_plan_desc()
+    d.n, d.m, d.p, d.eq = n, m, p, eq
+    d.comp = COMP_IDS[comp] if isinstance(comp, str) else comp
+    fl = [FLOW_IDS[f] if isinstance(f, str) else f for f in flows]
+    d.nflows = len(fl)
+    for i, f in enumerate(fl):
+        d.flows[i] = f
+    d.prec = PREC_IDS[prec] if isinstance(prec, str) else prec
+    d.h = float(h)
+    d.q_is_factor = int(bool(q_is_factor))
+    d.t4_rule = t4_rule
+    d.slices = slices
+    return d
+
+
+# ------------------------------------------------------------------ C-ABI mirrors
+def dme_plan(desc: dme_plan_desc, A, QorC, B=None, R=None, S=None, stream=None) -> int:
+    keep: list = []
+    out = C.c_void_p()
+    st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib().dme_plan(C.byref(desc), _ptr(A, keep), _ptr(QorC, keep), _ptr(B, keep), _ptr(R, keep),
+                          _ptr(S, keep), st, C.byref(out)), "dme_plan")
+    return out.value
+
+
+def dme_expm(plan: int, t: float, E_out=None, W_out=None):
+    _check(lib().dme_expm(plan, float(t), _out_ptr(E_out), _out_ptr(W_out)), "dme_expm")
+
+
+def dme_apply(plan: int, flow, t: float, P):
+    f = FLOW_IDS[flow] if isinstance(flow, str) else flow
+    _check(lib().dme_apply(plan, f, float(t), _out_ptr(P)), "dme_apply")
+
+
+def dme_apply_async(plan: int, flow, t: float, P):
+    f = FLOW_IDS[flow] if isinstance(flow, str) else flow
+    _check(lib().dme_apply_async(plan, f, float(t), _out_ptr(P)), "dme_apply_async")
+
+
+def dme_sync(plan: int):
+    _check(lib().dme_sync(plan), "dme_sync")
+
+
+def dme_plan_kernels_per_step(plan: int) -> int:
+    return int(lib().dme_plan_kernels_per_step(plan))
+
+
+def dme_step(plan: int, P, nsteps: int):
+    _check(lib().dme_step(plan, _out_ptr(P), int(nsteps)), "dme_step")
+
+
+def dme_solve(plan: int, P0, T: float, nsteps: int, P_out):
+    keep: list = []
+    _check(lib().dme_solve(plan, _ptr(P0, keep), float(T), int(nsteps), _out_ptr(P_out)), "dme_solve")
+
+
+def dme_plan_bytes(plan: int) -> int:
+    return int(lib().dme_plan_bytes(plan))
+
+
+def dme_plan_destroy(plan: int):
+    if plan:
+        _check(lib().dme_plan_destroy(plan), "dme_plan_destroy")
+
+
+def dme_server_create(hbm_budget_bytes: int, max_slots: int) -> int:
+    out = C.c_void_p()
+    _check(lib().dme_server_create(int(hbm_budget_bytes), int(max_slots), C.byref(out)), "dme_server_create")
+    return out.value
+
+
+def dme_submit(srv: int, desc: dme_plan_desc, A, QorC, B, R, S, P0, T: float, nsteps: int) -> int:
+    keep: list = []
+    tk = C.c_uint64()
+    _check(lib().dme_submit(srv, C.byref(desc), _ptr(A, keep), _ptr(QorC, keep), _ptr(B, keep), _ptr(R, keep),
+                            _ptr(S, keep), _ptr(P0, keep), float(T), int(nsteps), C.byref(tk)), "dme_submit")
+    return tk.value
+
+
+def dme_poll(srv: int, ticket: int, P_out=None, timeout_us: int = -1) -> int:
+    """Returns DME_OK when done (P_out filled); DME_ENOTREADY / DME_ETIMEOUT otherwise."""
+    s = lib().dme_poll(srv, C.c_uint64(ticket), _out_ptr(P_out), C.c_int64(timeout_us))
+    if s in (DME_OK, DME_ENOTREADY, DME_ETIMEOUT):
+        return s
+    raise DmeError(s, "dme_poll", last_error())
+
+
+def dme_server_stats(srv: int) -> str:
+    return (lib().dme_server_stats(srv) or b"{}").decode()
+
+
+def dme_server_destroy(srv: int):
+    if srv:
+        _check(lib().dme_server_destroy(srv), "dme_server_destroy")
+
+
+def dme_last_error() -> str:
+    return last_error()
+
+
+def _out_ptr(x):
+    """Pointer of an output buffer, which must already be float64 and contiguous."""
+    if x is None:
+        return None
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if x.dtype != torch.float64 or not x.is_contiguous():
+                raise ValueError("output tensors must be float64 and contiguous")
+            return x.data_ptr()
+    except ImportError:
+        pass
+    import numpy as np
+    if not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous):
+        raise ValueError("output arrays must be float64 and C-contiguous")
+    return x.ctypes.data

@@ -1,0 +1,95 @@
+// Internal declarations shared by the libdme translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "dme.h"
+
+namespace dme {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+const char* get_error();
+
+#define DME_CUDA_TRY(expr)                                                          \
+    do {                                                                            \
+        cudaError_t _e = (expr);                                                    \
+        if (_e != cudaSuccess) {                                                    \
+            ::dme::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));   \
+            return DME_ECUDA;                                                       \
+        }                                                                           \
+    } while (0)
+
+#define DME_TRY(expr)                                   \
+    do {                                                \
+        dme_status _s = (expr);                         \
+        if (_s != DME_OK) return _s;                    \
+    } while (0)
+
+// Device status word bits written by kernels (read back after a sync).
+enum : int { DEV_OK = 0, DEV_NOTSPD = 1, DEV_SINGULAR = 2, DEV_NONFINITE = 4, DEV_TIMEOUT = 8 };
+
+// ---------------------------------------------------------------- FP64 GEMM
+// One GEMM problem for the grouped FP64 kernel:
+//   C = alpha * op(A) op(B) + b1*D1 + b2*D2 + b3*D3
+// op(X) = X or X^T.  If tri != 0 the output is symmetric (M == N): only tiles
+// on or above the diagonal are computed, and each value (i, j), i <= j, is
+// written to both C[i][j] and C[j][i].  D1..D3 are then read on i <= j only.
+struct GemmProb {
+    const double* A;
+    const double* B;
+    double* C;
+    const double* D1;
+    const double* D2;
+    const double* D3;
+    int M, N, K;
+    int lda, ldb, ldc, ldd;
+    double alpha, b1, b2, b3;
+    int transA, transB, tri;
+    int tiles_n;       // filled by the launcher
+    int tile_start;    // filled by the launcher
+    int ntiles;        // filled by the launcher
+};
+
+constexpr int G64_BM = 64, G64_BN = 64, G64_BK = 16;
+
+// Enqueue a grouped FP64 GEMM over `probs` (host array); `dev_scratch` must
+// hold at least nprobs GemmProb and stay untouched until the kernel finished
+// (the launcher copies the descriptors there with cudaMemcpyAsync).
+dme_status gemm64_grouped(std::vector<GemmProb>& probs, GemmProb* dev_desc, cudaStream_t st);
+
+// ---------------------------------------------------------------- small kernels
+void launch_axpy_sym(double* P, const double* Q, double a, int n, int ld, cudaStream_t st);
+void launch_transpose(const double* X, double* Y, int rows, int cols, int ldx, int ldy, cudaStream_t st);
+void launch_scale_add_identity(double* X, double a, double c, int n, int ld, cudaStream_t st);  // X = a X + c I
+void launch_lincomb(double* Y, int n, int ld, const double* X1, double c1, const double* X2, double c2,
+                    const double* X3, double c3, double cI, cudaStream_t st);  // Y = c1X1+c2X2+c3X3+cI I
+void launch_symmetrize(double* X, int n, int ld, cudaStream_t st);   // X = (X + X^T)/2
+void launch_block_norm1(const double* A, const double* Q, int n, double* colsum_out, cudaStream_t st);
+void launch_max_reduce(const double* x, int len, double* out, cudaStream_t st);
+
+// Dense LU with partial pivoting, in place, unblocked right-looking
+// (one pivot kernel and one trailing-update kernel per column).
+void launch_lu(double* A, int n, int ld, int* piv, int* status, cudaStream_t st);
+// Solve (from an LU in place in LU with pivots piv) op(A0) X = B for n x nrhs B, in place.
+// trans = 0: A0 X = B.  trans = 1: A0^T X = B.
+void launch_lu_solve(const double* LU, int n, int ld, const int* piv, double* B, int nrhs, int ldb,
+                     int trans, cudaStream_t st);
+
+// Cholesky of a small SPD matrix (m <= 32) in place (lower), one warp.
+void launch_small_cholesky(double* R, int m, int* status, cudaStream_t st);
+// Bt = B L^{-T} (rows of B solved against lower L), n x m.
+void launch_apply_linv_rows(const double* B, const double* L, double* Bt, int n, int m, cudaStream_t st);
+
+// ---------------------------------------------------------------- Riccati (T3)
+// P <- P - t Z (I + t Bt^T Z)^{-1} Z^T + q * Qadd, Z = P Bt  (Woodbury form
+// of (I + t P Bt Bt^T)^{-1} P).  Work buffers sized by riccati_work_bytes.
+size_t riccati_work_doubles(int n, int m);
+void launch_riccati(double* P, const double* Bt, int n, int m, double t, const double* Qadd,
+                    double q, double* work, int* status, cudaStream_t st);
+
+}  // namespace dme

@@ -1,0 +1,497 @@
+// FP64 kernels of libdme: grouped GEMM with a symmetric-triangle mode and a
+// fused additive epilogue, the elementwise helpers of the plan step, dense LU
+// with partial pivoting and its triangular sweeps, and the small m x m
+// Cholesky used for R.
+//
+// GB300 executes FP64 on a narrow pipe (about 1.25 TFLOP/s for the whole
+// chip), so these kernels are ALU-bound: the GEMM keeps a 4 x 4 register
+// tile per thread fed from shared memory and spends its effort on coalesced
+// tile loads, not on latency hiding.
+#include "dme_internal.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace dme {
+
+// ============================================================== grouped GEMM
+constexpr int kMaxBatch = 8;
+struct GemmBatch {
+    GemmProb p[kMaxBatch];
+    int nprobs;
+};
+
+__device__ __forceinline__ void tile_coords(const GemmProb& pb, int lt, int& ti, int& tj) {
+    if (pb.tri) {
+        int T = pb.tiles_n, r = 0, rem = lt;
+        while (rem >= T - r) {
+            rem -= T - r;
+            ++r;
+        }
+        ti = r;
+        tj = r + rem;
+    } else {
+        ti = lt / pb.tiles_n;
+        tj = lt % pb.tiles_n;
+    }
+}
+
+__device__ __forceinline__ void gemm64_tile(const GemmProb& pb, int lt) {
+    __shared__ double As[G64_BK][G64_BM + 1];
+    __shared__ double Bs[G64_BK][G64_BN + 1];
+    int ti, tj;
+    tile_coords(pb, lt, ti, tj);
+    const int row0 = ti * G64_BM, col0 = tj * G64_BN;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+    for (int k0 = 0; k0 < pb.K; k0 += G64_BK) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int e = tid + 256 * q;
+            int r, k;
+            double v = 0.0;
+            if (!pb.transA) {
+                r = e >> 4;
+                k = e & 15;
+                int gr = row0 + r, gk = k0 + k;
+                if (gr < pb.M && gk < pb.K) v = pb.A[(size_t)gr * pb.lda + gk];
+            } else {
+                r = e & 63;
+                k = e >> 6;
+                int gr = row0 + r, gk = k0 + k;
+                if (gr < pb.M && gk < pb.K) v = pb.A[(size_t)gk * pb.lda + gr];
+            }
+            As[k][r] = v;
+            int c;
+            double w = 0.0;
+            if (!pb.transB) {
+                c = e & 63;
+                k = e >> 6;
+                int gc = col0 + c, gk = k0 + k;
+                if (gc < pb.N && gk < pb.K) w = pb.B[(size_t)gk * pb.ldb + gc];
+            } else {
+                c = e >> 4;
+                k = e & 15;
+                int gc = col0 + c, gk = k0 + k;
+                if (gc < pb.N && gk < pb.K) w = pb.B[(size_t)gc * pb.ldb + gk];
+            }
+            Bs[k][c] = w;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < G64_BK; ++k) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = row0 + ty + 16 * i;
+        if (r >= pb.M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = col0 + tx + 16 * j;
+            if (c >= pb.N) continue;
+            if (pb.tri && r > c) continue;
+            const size_t off = (size_t)r * pb.ldd + c;
+            double v = pb.alpha * acc[i][j];
+            if (pb.D1) v += pb.b1 * pb.D1[off];
+            if (pb.D2) v += pb.b2 * pb.D2[off];
+            if (pb.D3) v += pb.b3 * pb.D3[off];
+            pb.C[(size_t)r * pb.ldc + c] = v;
+            if (pb.tri && r != c) pb.C[(size_t)c * pb.ldc + r] = v;
+        }
+    }
+}
+
+__device__ __forceinline__ int find_prob(const GemmProb* probs, int nprobs, int t) {
+    int lo = 0, hi = nprobs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (probs[mid].tile_start <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) gemm64_batch_kernel(const __grid_constant__ GemmBatch batch) {
+    const int t = blockIdx.x;
+    const int ip = find_prob(batch.p, batch.nprobs, t);
+    gemm64_tile(batch.p[ip], t - batch.p[ip].tile_start);
+}
+
+__global__ void __launch_bounds__(256) gemm64_desc_kernel(const GemmProb* __restrict__ probs, int nprobs) {
+    const int t = blockIdx.x;
+    const int ip = find_prob(probs, nprobs, t);
+    GemmProb pb = probs[ip];
+    gemm64_tile(pb, t - pb.tile_start);
+}
+
+static int prepare_tiles(std::vector<GemmProb>& probs) {
+    int total = 0;
+    for (auto& p : probs) {
+        int tm = (p.M + G64_BM - 1) / G64_BM, tn = (p.N + G64_BN - 1) / G64_BN;
+        p.tiles_n = tn;
+        p.ntiles = (p.M <= 0 || p.N <= 0) ? 0 : (p.tri ? tn * (tn + 1) / 2 : tm * tn);
+        p.tile_start = total;
+        total += p.ntiles;
+    }
+    return total;
+}
+
+dme_status gemm64_grouped(std::vector<GemmProb>& probs, GemmProb* dev_desc, cudaStream_t st) {
+    for (auto& p : probs) {
+        if (p.tri && p.M != p.N) {
+            set_error("gemm64: triangle mode needs M == N");
+            return DME_EINVAL;
+        }
+    }
+    // drop empty problems, keep order
+    std::vector<GemmProb> live;
+    for (auto& p : probs)
+        if (p.M > 0 && p.N > 0) live.push_back(p);
+    if (live.empty()) return DME_OK;
+    const int total = prepare_tiles(live);
+    if (total == 0) return DME_OK;
+    if ((int)live.size() <= kMaxBatch) {
+        GemmBatch b;
+        b.nprobs = (int)live.size();
+        for (int i = 0; i < b.nprobs; ++i) b.p[i] = live[i];
+        gemm64_batch_kernel<<<total, 256, 0, st>>>(b);
+    } else {
+        if (!dev_desc) {
+            set_error("gemm64: more than 8 problems need a device descriptor buffer");
+            return DME_EINVAL;
+        }
+        DME_CUDA_TRY(cudaMemcpyAsync(dev_desc, live.data(), live.size() * sizeof(GemmProb),
+                                     cudaMemcpyHostToDevice, st));
+        gemm64_desc_kernel<<<total, 256, 0, st>>>(dev_desc, (int)live.size());
+    }
+    DME_CUDA_TRY(cudaGetLastError());
+    return DME_OK;
+}
+
+// ============================================================== elementwise
+__global__ void axpy_kernel(double* P, const double* Q, double a, int n, int ld) {
+    size_t total = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        size_t i = e / n, j = e % n;
+        P[i * ld + j] += a * Q[i * ld + j];
+    }
+}
+
+static int grid_for(size_t total, int block = 256) {
+    size_t g = (total + block - 1) / block;
+    return (int)std::min<size_t>(std::max<size_t>(g, 1), 152 * 16);
+}
+
+void launch_axpy_sym(double* P, const double* Q, double a, int n, int ld, cudaStream_t st) {
+    axpy_kernel<<<grid_for((size_t)n * n), 256, 0, st>>>(P, Q, a, n, ld);
+}
+
+__global__ void transpose_kernel(const double* X, double* Y, int rows, int cols, int ldx, int ldy) {
+    __shared__ double tile[32][33];
+    int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        int r = by + k, c = bx + threadIdx.x;
+        if (r < rows && c < cols) tile[k][threadIdx.x] = X[(size_t)r * ldx + c];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        int r = bx + k, c = by + threadIdx.x;   // Y is cols x rows
+        if (r < cols && c < rows) Y[(size_t)r * ldy + c] = tile[threadIdx.x][k];
+    }
+}
+
+void launch_transpose(const double* X, double* Y, int rows, int cols, int ldx, int ldy, cudaStream_t st) {
+    dim3 g((cols + 31) / 32, (rows + 31) / 32), b(32, 8);
+    transpose_kernel<<<g, b, 0, st>>>(X, Y, rows, cols, ldx, ldy);
+}
+
+__global__ void scale_add_identity_kernel(double* X, double a, double c, int n, int ld) {
+    size_t total = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        size_t i = e / n, j = e % n;
+        double v = a * X[i * ld + j];
+        if (i == j) v += c;
+        X[i * ld + j] = v;
+    }
+}
+
+void launch_scale_add_identity(double* X, double a, double c, int n, int ld, cudaStream_t st) {
+    scale_add_identity_kernel<<<grid_for((size_t)n * n), 256, 0, st>>>(X, a, c, n, ld);
+}
+
+__global__ void lincomb_kernel(double* Y, int n, int ld, const double* X1, double c1, const double* X2,
+                               double c2, const double* X3, double c3, double cI) {
+    size_t total = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        size_t i = e / n, j = e % n, off = i * ld + j;
+        double v = 0.0;
+        if (X1) v += c1 * X1[off];
+        if (X2) v += c2 * X2[off];
+        if (X3) v += c3 * X3[off];
+        if (i == j) v += cI;
+        Y[off] = v;
+    }
+}
+
+void launch_lincomb(double* Y, int n, int ld, const double* X1, double c1, const double* X2, double c2,
+                    const double* X3, double c3, double cI, cudaStream_t st) {
+    lincomb_kernel<<<grid_for((size_t)n * n), 256, 0, st>>>(Y, n, ld, X1, c1, X2, c2, X3, c3, cI);
+}
+
+__global__ void symmetrize_kernel(double* X, int n, int ld) {
+    // one thread per pair (i < j): both entries get the same average
+    size_t total = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        size_t i = e / n, j = e % n;
+        if (i < j) {
+            double v = 0.5 * (X[i * ld + j] + X[j * ld + i]);
+            X[i * ld + j] = v;
+            X[j * ld + i] = v;
+        }
+    }
+}
+
+void launch_symmetrize(double* X, int n, int ld, cudaStream_t st) {
+    symmetrize_kernel<<<grid_for((size_t)n * n), 256, 0, st>>>(X, n, ld);
+}
+
+// Column abs-sums of the Van Loan matrix [[-A^T, Q], [0, A]] (2n columns).
+__global__ void block_norm1_kernel(const double* A, const double* Q, int n, double* colsum) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double s1 = 0.0, s2 = 0.0;
+    for (int i = 0; i < n; ++i) {
+        s1 += fabs(A[(size_t)j * n + i]);                                  // column j of -A^T = row j of A
+        s2 += fabs(Q[(size_t)i * n + j]) + fabs(A[(size_t)i * n + j]);    // column n+j
+    }
+    colsum[j] = s1;
+    colsum[n + j] = s2;
+}
+
+void launch_block_norm1(const double* A, const double* Q, int n, double* colsum_out, cudaStream_t st) {
+    block_norm1_kernel<<<(n + 127) / 128, 128, 0, st>>>(A, Q, n, colsum_out);
+}
+
+__global__ void max_reduce_kernel(const double* x, int len, double* out) {
+    __shared__ double red[1024];
+    double m = 0.0;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) m = fmax(m, x[i]);
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+void launch_max_reduce(const double* x, int len, double* out, cudaStream_t st) {
+    max_reduce_kernel<<<1, 1024, 0, st>>>(x, len, out);
+}
+
+// ============================================================== LU (partial pivoting)
+// Step k: pick the pivot row p = argmax_{i >= k} |A[i][k]| (smallest i on ties),
+// swap rows k and p over all columns, replace A[i][k] (i > k) by the multipliers.
+__global__ void __launch_bounds__(1024) lu_pivot_kernel(double* A, int n, int ld, int k, int* piv, int* status) {
+    __shared__ double sv[1024];
+    __shared__ int si[1024];
+    double best = -1.0;
+    int bi = n;
+    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+        double v = fabs(A[(size_t)i * ld + k]);
+        if (v > best) {
+            best = v;
+            bi = i;
+        }
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            double o = sv[threadIdx.x + s];
+            int oi = si[threadIdx.x + s];
+            if (o > sv[threadIdx.x] || (o == sv[threadIdx.x] && oi < si[threadIdx.x])) {
+                sv[threadIdx.x] = o;
+                si[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    const int p = si[0];
+    const double pv = sv[0];
+    if (threadIdx.x == 0) {
+        // a zero or NaN column keeps row k (piv stays a valid row index) and flags the status
+        piv[k] = (pv > 0.0 && p < n) ? p : k;
+        if (!(pv > 0.0)) atomicOr(status, DEV_SINGULAR);
+    }
+    if (!(pv > 0.0)) return;
+    if (p != k) {
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            double a = A[(size_t)k * ld + j];
+            A[(size_t)k * ld + j] = A[(size_t)p * ld + j];
+            A[(size_t)p * ld + j] = a;
+        }
+    }
+    __syncthreads();
+    const double d = A[(size_t)k * ld + k];
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[(size_t)i * ld + k] /= d;
+}
+
+// Trailing update A[i][j] -= A[i][k] * A[k][j] for i, j > k.
+__global__ void lu_update_kernel(double* A, int n, int ld, int k) {
+    const int j = k + 1 + blockIdx.x * 32 + threadIdx.x;
+    const int i0 = k + 1 + blockIdx.y * 32;
+    if (j >= n) return;
+    const double akj = A[(size_t)k * ld + j];
+    for (int di = threadIdx.y; di < 32; di += 8) {
+        int i = i0 + di;
+        if (i < n) A[(size_t)i * ld + j] -= A[(size_t)i * ld + k] * akj;
+    }
+}
+
+void launch_lu(double* A, int n, int ld, int* piv, int* status, cudaStream_t st) {
+    for (int k = 0; k < n; ++k) {
+        lu_pivot_kernel<<<1, 1024, 0, st>>>(A, n, ld, k, piv, status);
+        int rest = n - k - 1;
+        if (rest > 0) {
+            dim3 g((rest + 31) / 32, (rest + 31) / 32), b(32, 8);
+            lu_update_kernel<<<g, b, 0, st>>>(A, n, ld, k);
+        }
+    }
+}
+
+// B[i][:] -= c_i * B[k][:] for i in [r0, r1); c_i = LU[i][k] (colmode) or LU[k][i].
+__global__ void tri_update_kernel(const double* LU, int ld, int k, double* B, int ldb, int nrhs, int r0, int r1,
+                                  int rowcoef) {
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    const int i0 = r0 + blockIdx.y * 32;
+    if (j >= nrhs) return;
+    const double bk = B[(size_t)k * ldb + j];
+    for (int di = threadIdx.y; di < 32; di += 8) {
+        int i = i0 + di;
+        if (i < r1) {
+            double c = rowcoef ? LU[(size_t)k * ld + i] : LU[(size_t)i * ld + k];
+            B[(size_t)i * ldb + j] -= c * bk;
+        }
+    }
+}
+
+__global__ void row_div_kernel(double* B, int ldb, int k, int nrhs, const double* LU, int ld) {
+    const double d = LU[(size_t)k * ld + k];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nrhs; j += gridDim.x * blockDim.x)
+        B[(size_t)k * ldb + j] /= d;
+}
+
+// Row interchanges, applied in order k = 0..n-1 (forward) or n-1..0 (reverse).
+__global__ void apply_swaps_kernel(double* B, int ldb, int nrhs, const int* piv, int n, int reverse) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nrhs) return;
+    for (int s = 0; s < n; ++s) {
+        int k = reverse ? n - 1 - s : s;
+        int p = piv[k];
+        if (p != k) {
+            double a = B[(size_t)k * ldb + j];
+            B[(size_t)k * ldb + j] = B[(size_t)p * ldb + j];
+            B[(size_t)p * ldb + j] = a;
+        }
+    }
+}
+
+static void tri_update(const double* LU, int ld, int k, double* B, int ldb, int nrhs, int r0, int r1, int rowcoef,
+                       cudaStream_t st) {
+    if (r1 <= r0) return;
+    dim3 g((nrhs + 31) / 32, (r1 - r0 + 31) / 32), b(32, 8);
+    tri_update_kernel<<<g, b, 0, st>>>(LU, ld, k, B, ldb, nrhs, r0, r1, rowcoef);
+}
+
+// P A0 = L U.  trans = 0: A0 X = B -> swaps, L y = b (unit lower), U x = y.
+// trans = 1: A0^T X = B -> U^T y = b, L^T z = y, x = P^T z (swaps reversed).
+void launch_lu_solve(const double* LU, int n, int ld, const int* piv, double* B, int nrhs, int ldb, int trans,
+                     cudaStream_t st) {
+    const int sg = (nrhs + 255) / 256;
+    const int rg = std::min((nrhs + 255) / 256, 64);
+    if (!trans) {
+        apply_swaps_kernel<<<sg, 256, 0, st>>>(B, ldb, nrhs, piv, n, 0);
+        for (int k = 0; k < n; ++k) tri_update(LU, ld, k, B, ldb, nrhs, k + 1, n, 0, st);
+        for (int k = n - 1; k >= 0; --k) {
+            row_div_kernel<<<rg, 256, 0, st>>>(B, ldb, k, nrhs, LU, ld);
+            tri_update(LU, ld, k, B, ldb, nrhs, 0, k, 0, st);
+        }
+    } else {
+        for (int k = 0; k < n; ++k) {
+            row_div_kernel<<<rg, 256, 0, st>>>(B, ldb, k, nrhs, LU, ld);
+            tri_update(LU, ld, k, B, ldb, nrhs, k + 1, n, 1, st);   // (U^T)[i][k] = U[k][i]
+        }
+        for (int k = n - 1; k >= 0; --k) tri_update(LU, ld, k, B, ldb, nrhs, 0, k, 1, st);  // (L^T)[i][k] = L[k][i]
+        apply_swaps_kernel<<<sg, 256, 0, st>>>(B, ldb, nrhs, piv, n, 1);
+    }
+}
+
+// ============================================================== small Cholesky
+// R = L L^T in place (lower triangle; the strict upper part is zeroed).  One warp.
+__global__ void small_cholesky_kernel(double* R, int m, int* status) {
+    const int lane = threadIdx.x;
+    for (int j = 0; j < m; ++j) {
+        double d = R[j * m + j];
+        for (int k = 0; k < j; ++k) d -= R[j * m + k] * R[j * m + k];
+        if (!(d > 0.0)) {
+            if (lane == 0) atomicOr(status, DEV_NOTSPD);
+            return;
+        }
+        d = sqrt(d);
+        __syncwarp();
+        for (int i = j + 1 + lane; i < m; i += 32) {
+            double s = R[i * m + j];
+            for (int k = 0; k < j; ++k) s -= R[i * m + k] * R[j * m + k];
+            R[i * m + j] = s / d;
+        }
+        __syncwarp();
+        if (lane == 0) R[j * m + j] = d;
+        __syncwarp();
+    }
+    for (int e = lane; e < m * m; e += 32) {
+        int i = e / m, j = e % m;
+        if (j > i) R[e] = 0.0;
+    }
+}
+
+void launch_small_cholesky(double* R, int m, int* status, cudaStream_t st) {
+    small_cholesky_kernel<<<1, 32, 0, st>>>(R, m, status);
+}
+
+// Bt[i][:] = (L^{-1} B[i][:]^T)^T by forward substitution.
+__global__ void apply_linv_rows_kernel(const double* B, const double* L, double* Bt, int n, int m) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double y[32];
+    for (int r = 0; r < m; ++r) {
+        double s = B[(size_t)i * m + r];
+        for (int c = 0; c < r; ++c) s -= L[r * m + c] * y[c];
+        y[r] = s / L[r * m + r];
+        Bt[(size_t)i * m + r] = y[r];
+    }
+}
+
+void launch_apply_linv_rows(const double* B, const double* L, double* Bt, int n, int m, cudaStream_t st) {
+    apply_linv_rows_kernel<<<(n + 127) / 128, 128, 0, st>>>(B, L, Bt, n, m);
+}
+
+}  // namespace dme

@@ -1,0 +1,704 @@
+// Plan, exponential, stepping and the C ABI of libdme.
+//
+// A plan holds the problem on the device and, per step length t used by T1 or
+// T12, the pair (E_t, W_t) of Eq. full:  E_t = e^{tA},
+// W_t = int_0^t e^{sA^T} Q e^{sA} ds.  Both come from the Van Loan block
+// exponential e^{t M}, M = [[-A^T, Q], [0, A]] (F22 = E_t, F22^T F12 = W_t),
+// evaluated with Higham's [13/13] Pade approximant and scaling and squaring.
+// Everything is done on n x n blocks, never on the 2n x 2n matrix:
+//  * every polynomial in the block upper-triangular X = M/2^s is block upper
+//    triangular, and its (1,1) block is determined by its (2,2) block
+//    (X11 = -X22^T, so an even power has (1,1) = (2,2)^T and an odd one
+//    (1,1) = -(2,2)^T); a product therefore costs three n x n GEMMs;
+//  * the Pade denominator q = V - U has q11 = p22^T, so q R = p splits into
+//    R22 = q22^{-1} p22 and R12 = p22^{-T} (p12 - q12 R22): two n x n LU
+//    solves in FP64;
+//  * squaring the block matrix is the semigroup law of T12 (Eq. full):
+//    E_{2t} = E_t^2, W_{2t} = W_t + E_t^T W_t E_t.
+#include "dme_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace dme {
+
+static thread_local std::string g_err;
+void set_error(const std::string& m) { g_err = m; }
+const char* get_error() { return g_err.c_str(); }
+
+// theta_13 (Higham 2005): largest ||X||_1 for which the [13/13] approximant
+// meets unit-roundoff backward error in double precision.
+static const double kTheta13 = 5.371920351148152;
+
+// c_0 = 1, c_{j+1} = c_j (m - j) / ((2m - j)(j + 1)), m = 13: the numerator
+// coefficients of the [m/m] Pade approximant of e^x.
+static void pade13(double c[14]) {
+    c[0] = 1.0;
+    for (int j = 0; j < 13; ++j) c[j + 1] = c[j] * (13.0 - j) / ((26.0 - j) * (j + 1.0));
+}
+
+}  // namespace dme
+
+using namespace dme;
+
+struct EWEntry {
+    double tau;
+    double* E;
+    double* W;
+    int s;
+};
+
+enum OpKind { OP_CONG = 0, OP_AXPY = 1, OP_RICC = 2, OP_SFLOW = 3 };
+
+struct Op {
+    int kind;
+    double tau;
+    int ew;        // OP_CONG: index of (E, W)
+    double wcoef;  // OP_CONG: coefficient of W (1 for T12, 0 for T1)
+    double qcoef;  // fused T2: + qcoef Q
+    int rule;      // OP_SFLOW: DME_T4_MIDPOINT / DME_T4_EULER
+};
+
+struct dme_plan_s {
+    dme_plan_desc d;
+    int n = 0, m = 0;
+    cudaStream_t st = nullptr;
+    bool own_st = false;
+    double* A = nullptr;
+    double* Q = nullptr;
+    double* Bt = nullptr;
+    double* S = nullptr;
+    double* X = nullptr;       // n x n congruence intermediate
+    double* Xs = nullptr;      // n x n S-flow intermediates
+    double* Y1 = nullptr;
+    double* state = nullptr;   // n x n, dme_solve working state
+    double* rwork = nullptr;   // Riccati work
+    double* small = nullptr;   // 2n colsums + scalars
+    int* status = nullptr;
+    double normM = 0.0;
+    std::vector<EWEntry> ew;
+    std::vector<Op> ops;
+    double ops_h = -1.0;
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    cudaGraphExec_t gexec = nullptr;
+    double* gP = nullptr;
+    int graph_kernels = -1;
+};
+
+namespace {
+
+dme_status palloc(dme_plan_t p, void** out, size_t bytes) {
+    *out = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(out, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+        return DME_ENOMEM;
+    }
+    p->allocs.push_back(*out);
+    p->bytes += bytes;
+    return DME_OK;
+}
+
+template <typename T>
+dme_status palloc_t(dme_plan_t p, T** out, size_t count) {
+    return palloc(p, reinterpret_cast<void**>(out), count * sizeof(T));
+}
+
+// Temporary device buffers released at scope exit (plan-time only).
+struct TmpPool {
+    std::vector<void*> v;
+    ~TmpPool() {
+        for (void* q : v) cudaFree(q);
+    }
+    dme_status get(double** out, size_t count) {
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(out), std::max<size_t>(count, 2) * sizeof(double));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error(std::string("cudaMalloc (temporary): ") + cudaGetErrorString(e));
+            return DME_ENOMEM;
+        }
+        v.push_back(*out);
+        return DME_OK;
+    }
+};
+
+GemmProb gp(int M, int N, int K, const double* A, int lda, int tA, const double* B, int ldb, int tB, double* C,
+            int ldc, double alpha, int tri = 0, const double* D1 = nullptr, double b1 = 0.0,
+            const double* D2 = nullptr, double b2 = 0.0, const double* D3 = nullptr, double b3 = 0.0) {
+    GemmProb g;
+    std::memset(&g, 0, sizeof(g));
+    g.A = A;
+    g.B = B;
+    g.C = C;
+    g.D1 = D1;
+    g.D2 = D2;
+    g.D3 = D3;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.lda = lda;
+    g.ldb = ldb;
+    g.ldc = ldc;
+    g.ldd = ldc;
+    g.alpha = alpha;
+    g.b1 = b1;
+    g.b2 = b2;
+    g.b3 = b3;
+    g.transA = tA;
+    g.transB = tB;
+    g.tri = tri;
+    return g;
+}
+
+dme_status gemm1(const GemmProb& g, cudaStream_t st) {
+    std::vector<GemmProb> v{g};
+    return gemm64_grouped(v, nullptr, st);
+}
+
+// out = G^T P G + addends, symmetric, with G = E (so out = E^T P E); X is n x n work.
+dme_status cong64(int n, const double* P, const double* E, double* X, double* out, const double* D1, double b1,
+                  const double* D2, double b2, const double* D3, double b3, cudaStream_t st) {
+    DME_TRY(gemm1(gp(n, n, n, P, n, 0, E, n, 0, X, n, 1.0), st));                       // X = P E
+    DME_TRY(gemm1(gp(n, n, n, E, n, 1, X, n, 0, out, n, 1.0, 1, D1, b1, D2, b2, D3, b3), st));  // E^T X
+    return DME_OK;
+}
+
+dme_status check_status(dme_plan_t p, const char* where) {
+    DME_CUDA_TRY(cudaStreamSynchronize(p->st));
+    int hs = 0;
+    DME_CUDA_TRY(cudaMemcpy(&hs, p->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (hs) {
+        DME_CUDA_TRY(cudaMemset(p->status, 0, sizeof(int)));
+        if (hs & DEV_NOTSPD) {
+            set_error(std::string(where) + ": I_m + t Bt^T P Bt (or R) is not positive definite");
+            return DME_ENOTSPD;
+        }
+        if (hs & DEV_SINGULAR) {
+            set_error(std::string(where) + ": singular Pade denominator");
+            return DME_ECUDA;
+        }
+        set_error(std::string(where) + ": device status " + std::to_string(hs));
+        return DME_ECUDA;
+    }
+    return DME_OK;
+}
+
+// (O22, O12) = (L, L11 = ls L22^T) * (R):  O22 = L22 R22, O12 = ls L22^T R12 + L12 R22.
+dme_status bprod(int n, const double* L22, const double* L12, double ls, const double* R22, const double* R12,
+                 double* O22, double* O12, cudaStream_t st) {
+    DME_TRY(gemm1(gp(n, n, n, L22, n, 0, R22, n, 0, O22, n, 1.0), st));
+    DME_TRY(gemm1(gp(n, n, n, L22, n, 1, R12, n, 0, O12, n, ls), st));
+    DME_TRY(gemm1(gp(n, n, n, L12, n, 0, R22, n, 0, O12, n, 1.0, 0, O12, 1.0), st));
+    return DME_OK;
+}
+
+dme_status compute_ew(dme_plan_t p, double tau, int* idx) {
+    for (size_t i = 0; i < p->ew.size(); ++i)
+        if (p->ew[i].tau == tau) {
+            *idx = (int)i;
+            return DME_OK;
+        }
+    const int n = p->n;
+    const size_t nn = (size_t)n * n;
+    cudaStream_t st = p->st;
+    double c[14];
+    pade13(c);
+    const double nrm = std::fabs(tau) * p->normM;
+    int s = 0;
+    if (nrm > kTheta13) s = (int)std::ceil(std::log2(nrm / kTheta13));
+    const double sc = std::ldexp(tau, -s);
+
+    TmpPool tp;
+    double *X22, *X12, *A22, *A12, *B22, *B12, *C22, *C12, *Y22, *Y12, *T22, *T12, *U22, *U12, *V22, *V12;
+    double *LUq, *LUp, *R22, *R12;
+    DME_TRY(tp.get(&X22, nn));
+    DME_TRY(tp.get(&X12, nn));
+    DME_TRY(tp.get(&A22, nn));
+    DME_TRY(tp.get(&A12, nn));
+    DME_TRY(tp.get(&B22, nn));
+    DME_TRY(tp.get(&B12, nn));
+    DME_TRY(tp.get(&C22, nn));
+    DME_TRY(tp.get(&C12, nn));
+    DME_TRY(tp.get(&Y22, nn));
+    DME_TRY(tp.get(&Y12, nn));
+    DME_TRY(tp.get(&T22, nn));
+    DME_TRY(tp.get(&T12, nn));
+    DME_TRY(tp.get(&U22, nn));
+    DME_TRY(tp.get(&U12, nn));
+    DME_TRY(tp.get(&V22, nn));
+    DME_TRY(tp.get(&V12, nn));
+    int* piv = nullptr;
+    DME_CUDA_TRY(cudaMalloc(&piv, sizeof(int) * std::max(n, 1)));
+    std::unique_ptr<int, void (*)(int*)> piv_guard(piv, [](int* q) { cudaFree(q); });
+
+    // X = sc M:  X22 = sc A, X12 = sc Q, X11 = -X22^T (implicit)
+    launch_lincomb(X22, n, n, p->A, sc, nullptr, 0, nullptr, 0, 0.0, st);
+    launch_lincomb(X12, n, n, p->Q, sc, nullptr, 0, nullptr, 0, 0.0, st);
+    // X2 = X X (odd * odd -> even), X4 = X2 X2, X6 = X4 X2
+    DME_TRY(bprod(n, X22, X12, -1.0, X22, X12, A22, A12, st));
+    DME_TRY(bprod(n, A22, A12, 1.0, A22, A12, B22, B12, st));
+    DME_TRY(bprod(n, B22, B12, 1.0, A22, A12, C22, C12, st));
+    // odd part: U = X (X6 (c13 X6 + c11 X4 + c9 X2) + c7 X6 + c5 X4 + c3 X2 + c1 I)
+    launch_lincomb(Y22, n, n, C22, c[13], B22, c[11], A22, c[9], 0.0, st);
+    launch_lincomb(Y12, n, n, C12, c[13], B12, c[11], A12, c[9], 0.0, st);
+    DME_TRY(bprod(n, C22, C12, 1.0, Y22, Y12, T22, T12, st));
+    launch_lincomb(U22, n, n, C22, c[7], B22, c[5], A22, c[3], c[1], st);
+    launch_lincomb(U12, n, n, C12, c[7], B12, c[5], A12, c[3], 0.0, st);
+    launch_lincomb(T22, n, n, T22, 1.0, U22, 1.0, nullptr, 0, 0.0, st);
+    launch_lincomb(T12, n, n, T12, 1.0, U12, 1.0, nullptr, 0, 0.0, st);
+    DME_TRY(bprod(n, X22, X12, -1.0, T22, T12, U22, U12, st));
+    // even part: V = X6 (c12 X6 + c10 X4 + c8 X2) + c6 X6 + c4 X4 + c2 X2 + c0 I
+    launch_lincomb(Y22, n, n, C22, c[12], B22, c[10], A22, c[8], 0.0, st);
+    launch_lincomb(Y12, n, n, C12, c[12], B12, c[10], A12, c[8], 0.0, st);
+    DME_TRY(bprod(n, C22, C12, 1.0, Y22, Y12, V22, V12, st));
+    launch_lincomb(T22, n, n, C22, c[6], B22, c[4], A22, c[2], c[0], st);
+    launch_lincomb(T12, n, n, C12, c[6], B12, c[4], A12, c[2], 0.0, st);
+    launch_lincomb(V22, n, n, V22, 1.0, T22, 1.0, nullptr, 0, 0.0, st);
+    launch_lincomb(V12, n, n, V12, 1.0, T12, 1.0, nullptr, 0, 0.0, st);
+    // p = V + U, q = V - U (reuse X, A, B buffers)
+    double* p22 = X22;
+    double* p12 = X12;
+    double* q22 = A22;
+    double* q12 = A12;
+    launch_lincomb(p22, n, n, V22, 1.0, U22, 1.0, nullptr, 0, 0.0, st);
+    launch_lincomb(p12, n, n, V12, 1.0, U12, 1.0, nullptr, 0, 0.0, st);
+    launch_lincomb(q22, n, n, V22, 1.0, U22, -1.0, nullptr, 0, 0.0, st);
+    launch_lincomb(q12, n, n, V12, 1.0, U12, -1.0, nullptr, 0, 0.0, st);
+    // R22 = q22^{-1} p22
+    LUq = B22;
+    R22 = B12;
+    launch_lincomb(LUq, n, n, q22, 1.0, nullptr, 0, nullptr, 0, 0.0, st);
+    launch_lincomb(R22, n, n, p22, 1.0, nullptr, 0, nullptr, 0, 0.0, st);
+    launch_lu(LUq, n, n, piv, p->status, st);
+    launch_lu_solve(LUq, n, n, piv, R22, n, n, 0, st);
+    // R12 = p22^{-T} (p12 - q12 R22)
+    R12 = C12;
+    DME_TRY(gemm1(gp(n, n, n, q12, n, 0, R22, n, 0, R12, n, -1.0, 0, p12, 1.0), st));
+    LUp = C22;
+    launch_lincomb(LUp, n, n, p22, 1.0, nullptr, 0, nullptr, 0, 0.0, st);
+    launch_lu(LUp, n, n, piv, p->status, st);
+    launch_lu_solve(LUp, n, n, piv, R12, n, n, 1, st);
+    // E = R22, W = R22^T R12 (symmetrised), then s doublings
+    double* E = Y22;
+    double* Wm = Y12;
+    double* tmp = T22;
+    double* E2 = T12;
+    launch_lincomb(E, n, n, R22, 1.0, nullptr, 0, nullptr, 0, 0.0, st);
+    DME_TRY(gemm1(gp(n, n, n, R22, n, 1, R12, n, 0, Wm, n, 1.0), st));
+    launch_symmetrize(Wm, n, n, st);
+    for (int i = 0; i < s; ++i) {
+        DME_TRY(gemm1(gp(n, n, n, Wm, n, 0, E, n, 0, tmp, n, 1.0), st));             // tmp = W E
+        DME_TRY(gemm1(gp(n, n, n, E, n, 1, tmp, n, 0, Wm, n, 1.0, 1, Wm, 1.0), st));   // W = E^T tmp + W
+        DME_TRY(gemm1(gp(n, n, n, E, n, 0, E, n, 0, E2, n, 1.0), st));               // E2 = E E
+        std::swap(E, E2);
+    }
+    EWEntry ent;
+    ent.tau = tau;
+    ent.s = s;
+    DME_TRY(palloc_t(p, &ent.E, nn));
+    DME_TRY(palloc_t(p, &ent.W, nn));
+    DME_CUDA_TRY(cudaMemcpyAsync(ent.E, E, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    DME_CUDA_TRY(cudaMemcpyAsync(ent.W, Wm, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    DME_CUDA_TRY(cudaGetLastError());
+    DME_TRY(check_status(p, "dme_expm"));
+    p->ew.push_back(ent);
+    *idx = (int)p->ew.size() - 1;
+    return DME_OK;
+}
+
+// One composition step as (flow, t) pairs, in application order (§2):
+// Lie: each flow over h; Strang: outer flows over h/2 around the last over h.
+std::vector<std::pair<int, double>> step_sequence(const dme_plan_desc& d, double h) {
+    std::vector<std::pair<int, double>> seq;
+    const int k = d.nflows;
+    if (k == 1) {
+        seq.push_back({d.flows[0], h});
+    } else if (d.comp == DME_LIE) {
+        for (int i = 0; i < k; ++i) seq.push_back({d.flows[i], h});
+    } else {
+        for (int i = 0; i < k - 1; ++i) seq.push_back({d.flows[i], 0.5 * h});
+        seq.push_back({d.flows[k - 1], h});
+        for (int i = k - 2; i >= 0; --i) seq.push_back({d.flows[i], 0.5 * h});
+    }
+    return seq;
+}
+
+int t4_rule_of(const dme_plan_desc& d) {
+    if (d.t4_rule == DME_T4_MIDPOINT || d.t4_rule == DME_T4_EULER) return d.t4_rule;
+    return d.comp == DME_STRANG ? DME_T4_MIDPOINT : DME_T4_EULER;
+}
+
+// Compile one step into ops.  T2 (P + tQ) is fused into the epilogue of the
+// op before it in the same step when there is one, else it is a standalone axpy.
+dme_status build_ops(dme_plan_t p, double h) {
+    if (p->ops_h == h) return DME_OK;
+    std::vector<Op> ops;
+    for (auto& ft : step_sequence(p->d, h)) {
+        Op o;
+        std::memset(&o, 0, sizeof(o));
+        o.tau = ft.second;
+        switch (ft.first) {
+            case DME_F1:
+            case DME_F12: {
+                int idx;
+                DME_TRY(compute_ew(p, ft.second, &idx));
+                o.kind = OP_CONG;
+                o.ew = idx;
+                o.wcoef = (ft.first == DME_F12) ? 1.0 : 0.0;
+                ops.push_back(o);
+                break;
+            }
+            case DME_F2:
+                if (!ops.empty()) {
+                    ops.back().qcoef += ft.second;
+                } else {
+                    o.kind = OP_AXPY;
+                    o.qcoef = ft.second;
+                    ops.push_back(o);
+                }
+                break;
+            case DME_F3:
+                o.kind = OP_RICC;
+                ops.push_back(o);
+                break;
+            case DME_F4:
+                o.kind = OP_SFLOW;
+                o.rule = t4_rule_of(p->d);
+                ops.push_back(o);
+                break;
+            default:
+                set_error("unknown flow");
+                return DME_EINVAL;
+        }
+    }
+    p->ops = ops;
+    p->ops_h = h;
+    if (p->gexec) {
+        cudaGraphExecDestroy(p->gexec);
+        p->gexec = nullptr;
+        p->gP = nullptr;
+    }
+    return DME_OK;
+}
+
+dme_status run_sflow(dme_plan_t p, double* P, double tau, int rule, double qcoef) {
+    const int n = p->n;
+    cudaStream_t st = p->st;
+    const double* Qd = qcoef != 0.0 ? p->Q : nullptr;
+    // X1 = P S^T ; Xs = S X1  (= S P S^T, symmetric)
+    DME_TRY(gemm1(gp(n, n, n, P, n, 0, p->S, n, 1, p->X, n, 1.0), st));
+    if (rule == DME_T4_EULER) {
+        // P <- P + t S P S^T (+ q Q)
+        DME_TRY(gemm1(gp(n, n, n, p->S, n, 0, p->X, n, 0, P, n, tau, 1, P, 1.0, Qd, qcoef), st));
+        return DME_OK;
+    }
+    DME_TRY(gemm1(gp(n, n, n, p->S, n, 0, p->X, n, 0, p->Xs, n, 1.0, 1), st));
+    // Y1 = Xs S^T ; P <- P + t Xs + t^2/2 S Y1 (+ q Q)
+    DME_TRY(gemm1(gp(n, n, n, p->Xs, n, 0, p->S, n, 1, p->Y1, n, 1.0), st));
+    DME_TRY(gemm1(gp(n, n, n, p->S, n, 0, p->Y1, n, 0, P, n, 0.5 * tau * tau, 1, P, 1.0, p->Xs, tau, Qd, qcoef),
+                  st));
+    return DME_OK;
+}
+
+dme_status run_op(dme_plan_t p, const Op& o, double* P) {
+    const int n = p->n;
+    cudaStream_t st = p->st;
+    switch (o.kind) {
+        case OP_CONG: {
+            const EWEntry& e = p->ew[o.ew];
+            return cong64(n, P, e.E, p->X, P, o.wcoef != 0.0 ? e.W : nullptr, o.wcoef,
+                          o.qcoef != 0.0 ? p->Q : nullptr, o.qcoef, nullptr, 0.0, st);
+        }
+        case OP_AXPY:
+            launch_axpy_sym(P, p->Q, o.qcoef, n, n, st);
+            return DME_OK;
+        case OP_RICC:
+            launch_riccati(P, p->Bt, n, p->m, o.tau, o.qcoef != 0.0 ? p->Q : nullptr, o.qcoef, p->rwork, p->status,
+                           st);
+            return DME_OK;
+        case OP_SFLOW:
+            return run_sflow(p, P, o.tau, o.rule, o.qcoef);
+    }
+    set_error("bad op");
+    return DME_EINVAL;
+}
+
+dme_status run_step(dme_plan_t p, double* P) {
+    for (const Op& o : p->ops) DME_TRY(run_op(p, o, P));
+    DME_CUDA_TRY(cudaGetLastError());
+    return DME_OK;
+}
+
+dme_status validate(const dme_plan_desc* d, const double* A, const double* QorC, const double* B, const double* R,
+                    const double* S) {
+    if (!d || !A || !QorC) return set_error("desc, A and QorC are required"), DME_EINVAL;
+    if (d->n < 1 || d->n > 16384) return set_error("n must be in [1, 16384]"), DME_EINVAL;
+    if (d->eq < DME_DLE || d->eq > DME_GDRE) return set_error("bad eq"), DME_EINVAL;
+    if (d->comp != DME_LIE && d->comp != DME_STRANG) return set_error("bad comp"), DME_EINVAL;
+    if (d->nflows < 1 || d->nflows > 4) return set_error("nflows must be 1..4"), DME_EINVAL;
+    if (d->prec != DME_FP64 && d->prec != DME_SPLIT_BF16) return set_error("bad prec"), DME_EINVAL;
+    if (!(d->h > 0.0) || !std::isfinite(d->h)) return set_error("h must be positive and finite"), DME_EINVAL;
+    if (d->q_is_factor && (d->p < 1 || d->p > 16384)) return set_error("p must be >= 1 with q_is_factor"), DME_EINVAL;
+    const bool ric = (d->eq == DME_DRE || d->eq == DME_GDRE);
+    const bool gen = (d->eq == DME_GDLE || d->eq == DME_GDRE);
+    for (int i = 0; i < d->nflows; ++i) {
+        int f = d->flows[i];
+        if (f < DME_F1 || f > DME_F4) return set_error("bad flow id"), DME_EINVAL;
+        if (f == DME_F3 && !ric) return set_error("F3 needs eq = DRE or GDRE"), DME_EINVAL;
+        if (f == DME_F4 && !gen) return set_error("F4 needs eq = GDLE or GDRE"), DME_EINVAL;
+    }
+    if (ric && (d->m < 1 || d->m > 32 || !B || !R)) return set_error("DRE needs B, R and 1 <= m <= 32"), DME_EINVAL;
+    if (gen && !S) return set_error("generalised equations need S"), DME_EINVAL;
+    return DME_OK;
+}
+
+void free_plan(dme_plan_t p) {
+    if (!p) return;
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->st) cudaStreamSynchronize(p->st);
+    for (void* q : p->allocs) cudaFree(q);
+    if (p->own_st && p->st) cudaStreamDestroy(p->st);
+    delete p;
+}
+
+dme_status plan_create(const dme_plan_desc* d, const double* A, const double* QorC, const double* B,
+                       const double* R, const double* S, void* stream, dme_plan_t* out) {
+    DME_TRY(validate(d, A, QorC, B, R, S));
+    if (d->prec == DME_SPLIT_BF16) {
+        set_error("DME_SPLIT_BF16 is not available in this build");
+        return DME_EINVAL;
+    }
+    dme_plan_t p = new (std::nothrow) dme_plan_s();
+    if (!p) return set_error("host allocation failed"), DME_ENOMEM;
+    std::unique_ptr<dme_plan_s, void (*)(dme_plan_t)> guard(p, free_plan);
+    p->d = *d;
+    const int n = d->n;
+    const bool ric = (d->eq == DME_DRE || d->eq == DME_GDRE);
+    const bool gen = (d->eq == DME_GDLE || d->eq == DME_GDRE);
+    p->n = n;
+    p->m = ric ? d->m : 0;
+    if (stream) {
+        p->st = reinterpret_cast<cudaStream_t>(stream);
+    } else {
+        DME_CUDA_TRY(cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking));
+        p->own_st = true;
+    }
+    const size_t nn = (size_t)n * n;
+    cudaStream_t st = p->st;
+    DME_TRY(palloc_t(p, &p->status, 4));
+    DME_CUDA_TRY(cudaMemsetAsync(p->status, 0, 4 * sizeof(int), st));
+    DME_TRY(palloc_t(p, &p->A, nn));
+    DME_TRY(palloc_t(p, &p->Q, nn));
+    DME_TRY(palloc_t(p, &p->X, nn));
+    DME_TRY(palloc_t(p, &p->small, 2 * (size_t)n + 16));
+    DME_CUDA_TRY(cudaMemcpyAsync(p->A, A, nn * sizeof(double), cudaMemcpyDefault, st));
+    if (d->q_is_factor) {
+        double* C = nullptr;
+        DME_CUDA_TRY(cudaMalloc(&C, (size_t)d->p * n * sizeof(double)));
+        std::unique_ptr<double, void (*)(double*)> cg(C, [](double* q) { cudaFree(q); });
+        DME_CUDA_TRY(cudaMemcpyAsync(C, QorC, (size_t)d->p * n * sizeof(double), cudaMemcpyDefault, st));
+        DME_TRY(gemm1(gp(n, n, d->p, C, n, 1, C, n, 0, p->Q, n, 1.0), st));   // Q = C^T C
+        DME_CUDA_TRY(cudaStreamSynchronize(st));
+    } else {
+        DME_CUDA_TRY(cudaMemcpyAsync(p->Q, QorC, nn * sizeof(double), cudaMemcpyDefault, st));
+    }
+    if (ric) {
+        const int m = d->m;
+        double *Bd = nullptr, *Rd = nullptr;
+        DME_CUDA_TRY(cudaMalloc(&Bd, (size_t)n * m * sizeof(double)));
+        std::unique_ptr<double, void (*)(double*)> bg(Bd, [](double* q) { cudaFree(q); });
+        DME_CUDA_TRY(cudaMalloc(&Rd, (size_t)m * m * sizeof(double)));
+        std::unique_ptr<double, void (*)(double*)> rg(Rd, [](double* q) { cudaFree(q); });
+        DME_CUDA_TRY(cudaMemcpyAsync(Bd, B, (size_t)n * m * sizeof(double), cudaMemcpyDefault, st));
+        DME_CUDA_TRY(cudaMemcpyAsync(Rd, R, (size_t)m * m * sizeof(double), cudaMemcpyDefault, st));
+        DME_TRY(palloc_t(p, &p->Bt, (size_t)n * m));
+        launch_small_cholesky(Rd, m, p->status, st);
+        launch_apply_linv_rows(Bd, Rd, p->Bt, n, m, st);
+        DME_TRY(check_status(p, "dme_plan (Cholesky of R)"));
+        DME_TRY(palloc_t(p, &p->rwork, riccati_work_doubles(n, m)));
+    }
+    if (gen) {
+        DME_TRY(palloc_t(p, &p->S, nn));
+        DME_TRY(palloc_t(p, &p->Xs, nn));
+        DME_TRY(palloc_t(p, &p->Y1, nn));
+        DME_CUDA_TRY(cudaMemcpyAsync(p->S, S, nn * sizeof(double), cudaMemcpyDefault, st));
+    }
+    // ||[[-A^T, Q], [0, A]]||_1 for the scaling of every t
+    launch_block_norm1(p->A, p->Q, n, p->small, st);
+    launch_max_reduce(p->small, 2 * n, p->small + 2 * n, st);
+    DME_CUDA_TRY(cudaMemcpyAsync(&p->normM, p->small + 2 * n, sizeof(double), cudaMemcpyDeviceToHost, st));
+    DME_CUDA_TRY(cudaStreamSynchronize(st));
+    DME_TRY(build_ops(p, d->h));
+    DME_TRY(check_status(p, "dme_plan"));
+    *out = guard.release();
+    return DME_OK;
+}
+
+dme_status step_graph(dme_plan_t p, double* P, int nsteps) {
+    if (!p->gexec || p->gP != P) {
+        if (p->gexec) {
+            cudaGraphExecDestroy(p->gexec);
+            p->gexec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        DME_CUDA_TRY(cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal));
+        dme_status s = run_step(p, P);
+        cudaError_t e = cudaStreamEndCapture(p->st, &g);
+        if (s != DME_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e != cudaSuccess) return set_error(std::string("graph capture: ") + cudaGetErrorString(e)), DME_ECUDA;
+        size_t nn = 0;
+        int kernels = 0;
+        if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+                for (size_t i = 0; i < nn; ++i) {
+                    cudaGraphNodeType ty;
+                    if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
+                }
+        }
+        p->graph_kernels = kernels;
+        e = cudaGraphInstantiate(&p->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return set_error(std::string("graph instantiate: ") + cudaGetErrorString(e)), DME_ECUDA;
+        p->gP = P;
+    }
+    for (int k = 0; k < nsteps; ++k) DME_CUDA_TRY(cudaGraphLaunch(p->gexec, p->st));
+    return DME_OK;
+}
+
+template <typename F>
+dme_status guarded(F&& f) {
+    try {
+        return f();
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return DME_ENOMEM;
+    } catch (...) {
+        set_error("internal error");
+        return DME_EINVAL;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+dme_status dme_plan(const dme_plan_desc* desc, const double* A, const double* QorC, const double* B,
+                    const double* R, const double* S, void* cuda_stream, dme_plan_t* out) {
+    if (!out) return set_error("out is NULL"), DME_EINVAL;
+    *out = nullptr;
+    set_error("");
+    return guarded([&] { return plan_create(desc, A, QorC, B, R, S, cuda_stream, out); });
+}
+
+dme_status dme_expm(dme_plan_t plan, double t, double* E_out, double* W_out) {
+    if (!plan) return set_error("plan is NULL"), DME_EINVAL;
+    if (!std::isfinite(t)) return set_error("t must be finite"), DME_EINVAL;
+    return guarded([&]() -> dme_status {
+        int idx;
+        DME_TRY(compute_ew(plan, t, &idx));
+        const size_t bytes = (size_t)plan->n * plan->n * sizeof(double);
+        if (E_out) DME_CUDA_TRY(cudaMemcpyAsync(E_out, plan->ew[idx].E, bytes, cudaMemcpyDefault, plan->st));
+        if (W_out) DME_CUDA_TRY(cudaMemcpyAsync(W_out, plan->ew[idx].W, bytes, cudaMemcpyDefault, plan->st));
+        DME_CUDA_TRY(cudaStreamSynchronize(plan->st));
+        return DME_OK;
+    });
+}
+
+static dme_status apply_impl(dme_plan_t plan, int flow, double t, double* P, bool sync) {
+    if (!plan || !P) return set_error("plan and P are required"), DME_EINVAL;
+    if (!std::isfinite(t)) return set_error("t must be finite"), DME_EINVAL;
+    return guarded([&]() -> dme_status {
+        Op o;
+        std::memset(&o, 0, sizeof(o));
+        o.tau = t;
+        switch (flow) {
+            case DME_F1:
+            case DME_F12: {
+                int idx;
+                DME_TRY(compute_ew(plan, t, &idx));
+                o.kind = OP_CONG;
+                o.ew = idx;
+                o.wcoef = flow == DME_F12 ? 1.0 : 0.0;
+                break;
+            }
+            case DME_F2:
+                o.kind = OP_AXPY;
+                o.qcoef = t;
+                break;
+            case DME_F3:
+                if (!plan->Bt) return set_error("F3 needs a DRE/GDRE plan"), DME_EINVAL;
+                o.kind = OP_RICC;
+                break;
+            case DME_F4:
+                if (!plan->S) return set_error("F4 needs a GDLE/GDRE plan"), DME_EINVAL;
+                o.kind = OP_SFLOW;
+                o.rule = t4_rule_of(plan->d);
+                break;
+            default:
+                return set_error("bad flow id"), DME_EINVAL;
+        }
+        DME_TRY(run_op(plan, o, P));
+        DME_CUDA_TRY(cudaGetLastError());
+        return sync ? check_status(plan, "dme_apply") : DME_OK;
+    });
+}
+
+dme_status dme_apply(dme_plan_t plan, int flow, double t, double* P) { return apply_impl(plan, flow, t, P, true); }
+
+dme_status dme_apply_async(dme_plan_t plan, int flow, double t, double* P) {
+    return apply_impl(plan, flow, t, P, false);
+}
+
+dme_status dme_sync(dme_plan_t plan) {
+    if (!plan) return set_error("plan is NULL"), DME_EINVAL;
+    return guarded([&] { return check_status(plan, "dme_sync"); });
+}
+
+int dme_plan_kernels_per_step(dme_plan_t plan) { return plan ? plan->graph_kernels : -1; }
+
+dme_status dme_step(dme_plan_t plan, double* P, int nsteps) {
+    if (!plan || !P) return set_error("plan and P are required"), DME_EINVAL;
+    if (nsteps < 0) return set_error("nsteps must be >= 0"), DME_EINVAL;
+    return guarded([&]() -> dme_status {
+        DME_TRY(build_ops(plan, plan->d.h));
+        DME_TRY(step_graph(plan, P, nsteps));
+        return check_status(plan, "dme_step");
+    });
+}
+
+dme_status dme_solve(dme_plan_t plan, const double* P0, double T, int nsteps, double* P_out) {
+    if (!plan || !P0 || !P_out) return set_error("plan, P0 and P_out are required"), DME_EINVAL;
+    if (nsteps < 1 || !(T > 0.0) || !std::isfinite(T)) return set_error("need nsteps >= 1 and T > 0"), DME_EINVAL;
+    return guarded([&]() -> dme_status {
+        const size_t bytes = (size_t)plan->n * plan->n * sizeof(double);
+        if (!plan->state) DME_TRY(palloc_t(plan, &plan->state, (size_t)plan->n * plan->n));
+        DME_TRY(build_ops(plan, T / nsteps));
+        DME_CUDA_TRY(cudaMemcpyAsync(plan->state, P0, bytes, cudaMemcpyDefault, plan->st));
+        DME_TRY(step_graph(plan, plan->state, nsteps));
+        DME_CUDA_TRY(cudaMemcpyAsync(P_out, plan->state, bytes, cudaMemcpyDefault, plan->st));
+        return check_status(plan, "dme_solve");
+    });
+}
+
+size_t dme_plan_bytes(dme_plan_t plan) { return plan ? plan->bytes : 0; }
+
+dme_status dme_plan_destroy(dme_plan_t plan) {
+    free_plan(plan);
+    return DME_OK;
+}
+
+const char* dme_last_error(void) { return get_error(); }
+
+}  // extern "C"

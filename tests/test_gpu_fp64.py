@@ -1,0 +1,230 @@
+"""FP64 CUDA path against the CPU oracle, element by element, through the C ABI.
+Sizes span several 64-wide tiles and ragged tails; bar: relative Frobenius
+error <= 1e-11 (and exact symmetry of every GPU state)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import dme_workloads as W
+import oracle as O
+import paper_1805_08990_gb300 as dme
+from gpu_util import FP64_TOL, dev, host, plan_for, rel, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _gpu():
+    require_gpu()
+
+
+# ---------------------------------------------------------------- plan: E_t, W_t
+@pytest.mark.parametrize("n,kind,tau", [(1, "random", 0.3), (37, "random", 0.05), (100, "convdiff", 1e-3),
+                                        (130, "random", 2.0), (256, "laplace", 5e-4)])
+def test_expm_van_loan_matches_oracle(n, kind, tau):
+    rng = np.random.default_rng(n)
+    if kind == "convdiff":
+        A = W.convection_diffusion_2d(int(math.isqrt(n)))
+    elif kind == "laplace":
+        A = W.laplacian_2d(int(math.isqrt(n)))
+    else:
+        M = rng.standard_normal((n, n)) / math.sqrt(n)
+        A = M - (np.abs(M).sum(axis=0).max() * 0.5) * np.eye(n)
+    C = rng.uniform(0, 1, (3, n))
+    Q = C.T @ C
+    E_ref, W_ref = O.van_loan(A, Q, tau)
+    plan = dme.Plan(dev(A), C=dev(C), h=tau, flows=["F12"])
+    E = torch.empty(n, n, dtype=torch.float64, device="cuda")
+    Wd = torch.empty_like(E)
+    plan.expm(tau, E, Wd)
+    assert rel(host(E), E_ref) < FP64_TOL
+    assert rel(host(Wd), W_ref) < FP64_TOL
+    assert torch.equal(Wd, Wd.T)
+    # host output pointers work too
+    Eh = np.empty((n, n))
+    plan.expm(tau, Eh, None)
+    assert rel(Eh, E_ref) < FP64_TOL
+
+
+# ---------------------------------------------------------------- single sub-flows
+def _problem(n, m=3, with_S=True, seed=0):
+    rng = np.random.default_rng(seed)
+    M = rng.standard_normal((n, n)) / math.sqrt(n)
+    A = M - (np.abs(M).sum(axis=0).max() * 0.5 + 0.5) * np.eye(n)
+    C = rng.uniform(0, 1, (2, n))
+    B = rng.standard_normal((n, m))
+    G = rng.standard_normal((m, m))
+    R = G @ G.T + m * np.eye(m)
+    S = 0.3 * rng.standard_normal((n, n)) / math.sqrt(n) if with_S else None
+    return W.Problem("t", A, C, np.zeros((n, n)), 1.0, B=B, R=R, S=S)
+
+
+@pytest.mark.parametrize("n", [1, 37, 64, 130])
+@pytest.mark.parametrize("flow", ["F1", "F2", "F12", "F3", "F4"])
+def test_single_subflow_matches_oracle(n, flow):
+    pr = _problem(n, m=3)
+    tau = 0.07
+    plan = plan_for(pr, ["F12", "F3", "F4"], "strang", tau)
+    P0 = W.random_psd(n, 5 + n)
+    P = dev(P0)
+    plan.apply(flow, tau, P)
+    op = O.Plan(pr.A, pr.Q, pr.B, pr.R, pr.S)
+    ref = op.apply(flow, tau, P0, "midpoint")
+    assert rel(host(P), ref) < FP64_TOL, flow
+    assert torch.equal(P, P.T)
+
+
+@pytest.mark.parametrize("m", [1, 2, 8, 11])
+def test_riccati_flow_m_sizes(m):
+    n = 97
+    pr = _problem(n, m=m, with_S=False, seed=m)
+    plan = plan_for(pr, ["F12", "F3"], "strang", 0.1)
+    P0 = W.random_psd(n, m, scale=3.0)
+    P = dev(P0)
+    plan.apply("F3", 0.4, P)
+    ref = O.flow_T3(P0, pr.B @ np.linalg.solve(pr.R, pr.B.T), 0.4)
+    assert rel(host(P), ref) < FP64_TOL
+
+
+def test_t4_euler_rule_for_lie():
+    pr = _problem(50)
+    plan = plan_for(pr, ["F12", "F4"], "lie", 0.1)
+    P0 = W.random_psd(50, 1)
+    P = dev(P0)
+    plan.apply("F4", 0.1, P)
+    assert rel(host(P), O.flow_T4(P0, pr.S, 0.1, "euler")) < FP64_TOL
+
+
+# ---------------------------------------------------------------- compositions
+def _oracle_solve(pr, flows, comp, N, T=None, t4_rule=None):
+    T = pr.T if T is None else T
+    uses_B = "F3" in flows
+    return O.solve(pr.A, pr.Q, pr.P0, T, N, comp, flows, B=pr.B if uses_B else None,
+                   R=pr.R if uses_B else None, S=pr.S if "F4" in flows else None, t4_rule=t4_rule)
+
+
+@pytest.mark.parametrize("scheme,comp", [("F1F2", "strang"), ("F12", "strang"), ("F1F2", "lie")])
+def test_dle_heat_n256_full_config(scheme, comp):
+    """Plain DLE, n = 256 Laplacian, Q = all-ones, T = 0.1, h = T/100."""
+    pr = W.dle_heat(16)
+    N = 100
+    flows = W.SCHEMES[scheme]
+    plan = plan_for(pr, flows, comp, pr.T / N)
+    out = np.empty((pr.n, pr.n))
+    plan.solve(pr.P0, pr.T, N, out)
+    ref = _oracle_solve(pr, flows, comp, N)
+    assert rel(out, ref) < FP64_TOL
+    assert np.array_equal(out, out.T)
+
+
+@pytest.mark.parametrize("scheme", ["F12F3", "F1F2F3", "F1F3F2"])
+@pytest.mark.parametrize("comp", ["lie", "strang"])
+def test_dre_convdiff_small_schemes(scheme, comp):
+    pr = W.dre_convdiff(nx=10, m=2, p=3)        # n = 100: two 64-tiles, ragged
+    N = 16
+    flows = W.SCHEMES[scheme]
+    plan = plan_for(pr, flows, comp, pr.T / N)
+    P = dev(pr.P0)
+    plan.step(P, N)
+    assert rel(host(P), _oracle_solve(pr, flows, comp, N)) < FP64_TOL
+
+
+@pytest.mark.parametrize("scheme,comp", [("F12F3F4", "strang"), ("F12F4F3", "lie"), ("F12F4", "strang"),
+                                         ("F1F2F4", "strang"), ("F1F4F2", "strang"), ("F1F4F2", "lie")])
+def test_generalised_schemes_padded(scheme, comp):
+    pr = W.gdre_convdiff_padded(nx=8, n_pad=72, m=2, p=3)
+    N = 8
+    flows = W.SCHEMES[scheme]
+    plan = plan_for(pr, flows, comp, pr.T / N)
+    P = dev(pr.P0)
+    plan.step(P, N)
+    got = host(P)
+    assert rel(got, _oracle_solve(pr, flows, comp, N)) < FP64_TOL
+    na = pr.meta["n_active"]
+    assert np.all(got[na:, :] == 0) and np.all(got[:, na:] == 0)
+
+
+def test_dre_convdiff_n1024_full_size():
+    """DRE config at full size (n = 1024), FP64, Strang F12F3, h = T/16."""
+    pr = W.dre_convdiff()
+    N = 16
+    plan = plan_for(pr, ["F12", "F3"], "strang", pr.T / N)
+    P = dev(pr.P0)
+    plan.step(P, N)
+    ref = _oracle_solve(pr, ["F12", "F3"], "strang", N)
+    assert rel(host(P), ref) < FP64_TOL
+
+
+def test_scalar_dre_against_tanh_closed_form():
+    a, b, q = -1.0, 1.0, 2.0
+    A, C, B, R = np.array([[a]]), np.array([[math.sqrt(q)]]), np.array([[b]]), np.array([[1.0]])
+    beta = math.sqrt(a * a + q * b * b)
+    exact = q * math.tanh(beta) / (beta - a * math.tanh(beta))
+    errs = []
+    for N in (32, 64):
+        plan = dme.Plan(dev(A), C=dev(C), h=1.0 / N, flows=["F12", "F3"], comp="strang", B=dev(B), R=dev(R))
+        out = np.zeros((1, 1))
+        plan.solve(np.zeros((1, 1)), 1.0, N, out)
+        errs.append(abs(out[0, 0] - exact) / exact)
+    assert errs[1] < 1e-4 and 1.9 < math.log2(errs[0] / errs[1]) < 2.1
+
+
+def test_step_replay_equals_repeated_single_steps():
+    pr = W.dre_convdiff(nx=8, m=2, p=3)
+    plan = plan_for(pr, ["F12", "F3"], "strang", 0.05)
+    P1 = dev(W.random_psd(pr.n, 3))
+    P2 = P1.clone()
+    plan.step(P1, 3)
+    for _ in range(3):
+        plan.step(P2, 1)
+    assert torch.equal(P1, P2)
+
+
+def test_solve_host_and_device_buffers_agree():
+    pr = W.dre_convdiff(nx=8, m=2, p=3)
+    plan = plan_for(pr, ["F12", "F3"], "strang", 0.1)
+    Ph = np.empty((pr.n, pr.n))
+    plan.solve(pr.P0, 1.0, 10, Ph)
+    Pd = torch.empty(pr.n, pr.n, dtype=torch.float64, device="cuda")
+    plan.solve(dev(pr.P0), 1.0, 10, Pd)
+    assert np.array_equal(Ph, host(Pd))
+    # a different h than the plan's rebuilds E, W for the new step lengths
+    plan.solve(pr.P0, 1.0, 20, Ph)
+    assert rel(Ph, _oracle_solve(pr, ["F12", "F3"], "strang", 20)) < FP64_TOL
+
+
+# ---------------------------------------------------------------- errors
+def test_non_spd_R_is_reported():
+    pr = _problem(20, m=2, with_S=False)
+    with pytest.raises(dme.DmeError) as ei:
+        dme.Plan(dev(pr.A), C=dev(pr.C), h=0.1, flows=["F12", "F3"], B=dev(pr.B), R=dev(-np.eye(2)))
+    assert ei.value.status == dme.DME_ENOTSPD
+
+
+def test_invalid_descriptors_are_rejected():
+    A = dev(np.eye(4))
+    C = dev(np.ones((1, 4)))
+    with pytest.raises(dme.DmeError) as ei:
+        dme.Plan(A, C=C, h=-1.0)
+    assert ei.value.status == dme.DME_EINVAL
+    d = dme.make_desc(0, eq=dme.DME_DLE, flows=("F12",), h=0.1, q_is_factor=True, p=1)
+    with pytest.raises(dme.DmeError):
+        dme.dme_plan(d, A, C)
+    d = dme.make_desc(4, eq=dme.DME_DLE, flows=("F12", "F3"), h=0.1, q_is_factor=True, p=1)
+    with pytest.raises(dme.DmeError):                      # F3 in a DLE
+        dme.dme_plan(d, A, C)
+
+
+def test_riccati_not_spd_on_device_is_reported():
+    """M = I + t Bt^T P Bt fails its Cholesky when P is strongly indefinite."""
+    pr = _problem(16, m=2, with_S=False)
+    plan = plan_for(pr, ["F12", "F3"], "strang", 0.1)
+    P = dev(-50.0 * np.eye(16))
+    with pytest.raises(dme.DmeError) as ei:
+        plan.apply("F3", 1.0, P)
+    assert ei.value.status == dme.DME_ENOTSPD
+    # the plan stays usable afterwards
+    P = dev(W.random_psd(16, 1))
+    plan.apply("F3", 0.1, P)
