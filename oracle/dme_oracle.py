@@ -39,8 +39,10 @@ scaling and squaring method for the matrix exponential revisited", SIAM J.
 Matrix Anal. Appl. 26(4), 2005, Alg. 2.3 restricted to m = 13).
 
 Readings where the paper is silent: the paper approximates the integral by an
-unnamed quadrature (§3, Alg. 2); here it is exact to rounding.  After every
-sub-flow the state is symmetrised, P <- (P + P^T)/2.
+unnamed quadrature (§3, Alg. 2); here it is exact to rounding.  The block
+exponential is evaluated at a step t with ||t A||_1 <= 1 and doubled to tau
+with the semigroup law of Eq. full (see van_loan).  After every sub-flow the
+state is symmetrised, P <- (P + P^T)/2.
 
 Every function below is pinned by ``tests/test_oracle_*.py`` against closed
 forms, library routines (scipy) or brute force; none is "parity unpinned".
@@ -108,16 +110,28 @@ def expm(M: np.ndarray) -> np.ndarray:
 
 def van_loan(A: np.ndarray, Q: np.ndarray, tau: float):
     """E = e^{tau A} and W = int_0^tau e^{s A^T} Q e^{s A} ds (the integral of
-    Eq. full) from one 2n x 2n exponential of tau [[-A^T, Q], [0, A]]:
-    E = F22, W = F22^T F12."""
+    Eq. full) from the 2n x 2n exponential of t [[-A^T, Q], [0, A]]:
+    E_t = F22, W_t = F22^T F12.
+
+    The block exponential is taken at t = tau / 2^j with ||t A||_1 <= 1 and
+    brought to tau by the semigroup law of Eq. full, E_{2t} = E_t^2,
+    W_{2t} = W_t + E_t^T W_t E_t.  At large tau ||A|| the (1,1) block
+    e^{-tau A^T} of a stable A grows like e^{tau ||A||}, and W = F22^T F12 then
+    loses every digit to cancellation; at ||t A||_1 <= 1 no block grows."""
     n = A.shape[0]
+    nA = norm1(A) * abs(tau)
+    j = 0 if nA <= 1.0 else int(math.ceil(math.log2(nA)))
+    t = tau / (2.0 ** j)
     M = np.zeros((2 * n, 2 * n))
     M[:n, :n] = -A.T
     M[:n, n:] = Q
     M[n:, n:] = A
-    F = expm(tau * M)
+    F = expm(t * M)
     E = F[n:, n:].copy()
     W = E.T @ F[:n, n:]
+    for _ in range(j):
+        W = W + E.T @ W @ E
+        E = E @ E
     return E, W
 
 

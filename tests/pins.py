@@ -77,6 +77,34 @@ def van_loan_diag_error(orc, seed=1, n=7, tau=0.37) -> float:
     return max(np.linalg.norm(E - Ee) / np.linalg.norm(Ee), np.linalg.norm(Wm - We) / np.linalg.norm(We))
 
 
+def van_loan_stiff_diag_error(orc, seed=13, n=9, tau=0.5) -> float:
+    """Stiff diagonal A (tau a_i down to -400): the closed form of
+    van_loan_diag_error, where e^{-tau A^T} would reach e^{400}."""
+    rng = np.random.default_rng(seed)
+    a = -rng.uniform(1.0, 800.0, n)
+    G = rng.uniform(0.0, 1.0, (3, n))
+    Q = G.T @ G
+    E, Wm = orc.van_loan(np.diag(a), Q, tau)
+    L = a[:, None] + a[None, :]
+    We = Q * np.expm1(L * tau) / L
+    Ee = np.diag(np.exp(a * tau))
+    return max(np.linalg.norm(E - Ee) / np.linalg.norm(Ee), np.linalg.norm(Wm - We) / np.linalg.norm(We))
+
+
+def van_loan_lyapunov_error(orc, nx=10, tau=1.0 / 16, seed=14) -> float:
+    """Differentiating the integrand of Eq. full: A^T W + W A = E^T Q E - Q.
+    W from scipy.linalg.solve_continuous_lyapunov (Bartels-Stewart) on a stiff
+    non-normal convection-diffusion A (tau ||A||_1 ~ 60)."""
+    A = W.convection_diffusion_2d(nx)
+    rng = np.random.default_rng(seed)
+    C = rng.uniform(0, 1, (3, A.shape[0]))
+    Q = C.T @ C
+    E, Wm = orc.van_loan(A, Q, tau)
+    Wl = sla.solve_continuous_lyapunov(A.T, E.T @ Q @ E - Q)
+    Ee = sla.expm(tau * A)
+    return max(np.linalg.norm(Wm - Wl) / np.linalg.norm(Wl), np.linalg.norm(E - Ee) / np.linalg.norm(Ee))
+
+
 def van_loan_quadrature_error(orc, seed=2, n=6, tau=0.5) -> float:
     """Non-normal A: W against 40-point Gauss-Legendre quadrature of
     int_0^tau e^{sA^T} Q e^{sA} ds, each e^{sA} from scipy.linalg.expm."""

@@ -92,6 +92,23 @@ def _expm_one_squaring_short(M):
     return R
 
 
+def _vl_literal_block(A, Q, tau):
+    """The unscaled literal block exponential: unstable at large tau ||A||."""
+    n = A.shape[0]
+    M = np.zeros((2 * n, 2 * n))
+    M[:n, :n] = -A.T
+    M[:n, n:] = Q
+    M[n:, n:] = A
+    F = core.expm(tau * M)
+    E = F[n:, n:].copy()
+    return E, E.T @ F[:n, n:]
+
+
+def _vl_doubling_sign(A, Q, tau):
+    E, Wm = core.van_loan(A, Q, tau / 2)
+    return E @ E, Wm - E.T @ Wm @ E
+
+
 def _pade_shifted():
     c = core.pade13_coefficients()
     return c[1:] + [c[13] / 27.0]
@@ -112,6 +129,8 @@ def _strang_wrong_order(comp, flows, h):
 @pytest.mark.parametrize("name,mut,pin,bound", [
     ("W drops E^T", dict(van_loan=_vl_missing_E), lambda m: pins.van_loan_diag_error(m), 1e-6),
     ("sign of A^T block", dict(van_loan=_vl_sign), lambda m: pins.van_loan_quadrature_error(m), 1e-6),
+    ("unscaled block exponential", dict(van_loan=_vl_literal_block), lambda m: pins.van_loan_lyapunov_error(m), 1e-6),
+    ("doubling sign", dict(van_loan=_vl_doubling_sign), lambda m: pins.van_loan_lyapunov_error(m), 1e-6),
     ("T12 transposed congruence", dict(flow_T12=lambda P, E, Wm: core.symmetrize(E @ P @ E.T + Wm)),
      lambda m: pins.t12_vs_ode_error(m), 1e-6),
     ("T3 sign", dict(flow_T3=lambda P, BRB, t: core.symmetrize(

@@ -41,6 +41,14 @@ def test_van_loan_diagonal_closed_form():
     assert pins.van_loan_diag_error(O) < 1e-14
 
 
+def test_van_loan_stiff_diagonal_closed_form():
+    assert pins.van_loan_stiff_diag_error(O) < 1e-13
+
+
+def test_van_loan_stiff_nonnormal_lyapunov_identity():
+    assert pins.van_loan_lyapunov_error(O) < 1e-11
+
+
 def test_van_loan_against_quadrature_nonnormal():
     assert pins.van_loan_quadrature_error(O) < 1e-13
 
