@@ -192,10 +192,12 @@ def run_ours(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         with ClockSampler(local) as clk:
+            torch.cuda.nvtx.range_push("timed")
             e0.record(stream)
             plan.step(P, steps)
             e1.record(stream)
             torch.cuda.synchronize(dev)
+            torch.cuda.nvtx.range_pop()
         barrier()
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1)

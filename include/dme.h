@@ -157,6 +157,17 @@ const char* dme_server_stats(dme_server_t srv);
 
 dme_status dme_server_destroy(dme_server_t srv);
 
+/* C = A B^T on the split-precision tensor-core path used by DME_SPLIT_BF16:
+ * every row of A (M x K) and of B (N x K) is scaled by a power of two and cut
+ * into four bf16 slices (6 + 7 + 7 + 7 bits); the ten slice products of
+ * levels 0..3 are accumulated in fp32 on tcgen05 tensor cores, exactly for
+ * level 0 (K <= 4096 keeps every partial sum below 2^24 units), and combined
+ * in fp64.  Relative error per entry ~ 2^-28 of the row scales.  All
+ * matrices are float64 row-major device memory; C is M x N.  Synchronises
+ * `cuda_stream`.  DME_EINVAL unless 1 <= K <= 4096. */
+dme_status dme_gemm_split(int M, int N, int K, const double* A, const double* B, double* C,
+                          void* cuda_stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* dme_last_error(void);
 

@@ -70,6 +70,7 @@ _SIGS = {
     "dme_server_stats": (C.c_char_p, [C.c_void_p]),
     "dme_server_destroy": (C.c_int, [C.c_void_p]),
     "dme_last_error": (C.c_char_p, []),
+    "dme_gemm_split": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -221,6 +222,16 @@ def dme_server_stats(srv: int) -> str:
 def dme_server_destroy(srv: int):
     if srv:
         _check(lib().dme_server_destroy(srv), "dme_server_destroy")
+
+
+def dme_gemm_split(A, B, C_out, stream=None):
+    """C_out = A @ B.T on the split-precision tensor-core path (device tensors)."""
+    M, K = A.shape
+    N = B.shape[0]
+    keep: list = []
+    st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib().dme_gemm_split(int(M), int(N), int(K), _ptr(A, keep), _ptr(B, keep), _out_ptr(C_out), st),
+           "dme_gemm_split")
 
 
 def dme_last_error() -> str:

@@ -1,0 +1,363 @@
+// Split-precision congruence G P G^T on tcgen05 tensor cores.
+//
+// Error-free slicing (after Ozaki, Ogita, Oishi & Rump, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix
+// multiplication", Numer. Algorithms 59, 2012): each row r of an operand is
+// scaled by sigma_r = 2^E_r >= max |x_r.| and cut into four bf16 slices
+//     x / sigma = d0 2^-6 + d1 2^-13 + d2 2^-20 + d3 2^-27 (+ |res| <= 2^-28),
+// with integers |d_t| <= 64.  A slice product d_s d_t 2^-(12+7(s+t)) is exact in
+// bf16 x bf16, and a level l = s + t sums K <= 4096 such products: at most
+// 2^24 units of 2^-(12+7l), so the fp32 tensor-core accumulation of level 0 is
+// exact whatever its rounding mode, and levels 1-3 only round far below the
+// slice residual.  Levels 0..3 (10 slice pairs) each get their own TMEM
+// accumulator; the epilogue adds them as a two-float (hi = level 0 exact,
+// lo = levels 1-3) and scales by sigma_A,i sigma_B,j.
+//
+// Kernel shape: one CTA per 128 x 128 output tile, 6 warps:
+//   warp 0  TMA producer (one thread): 3-stage ring, each stage holds the 4
+//           slices of a 128 x 32 A tile and of a 128 x 32 B tile (64 KB),
+//   warp 1  TMEM allocator + MMA issuer (one thread): 20 tcgen05.mma per stage,
+//   warps 2-5 epilogue: tcgen05.ld of the 4 accumulators (512 TMEM columns).
+// Both operands are K-major (row-major with K contiguous):
+//   C[i][j] = sum_k A[i][k] B[j][k].
+#include "dme_internal.h"
+#include "split_internal.h"
+#include "tc_ptx.cuh"
+
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+namespace dme {
+
+using namespace tc;
+
+constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 32, OZ_STAGES = 3;
+constexpr int OZ_SLICE_BYTES = OZ_BM * OZ_BK * 2;              // 8 KB per slice tile
+constexpr int OZ_OPER_BYTES = OZ_SLICES * OZ_SLICE_BYTES;     // 32 KB per operand per stage
+constexpr int OZ_STAGE_BYTES = 2 * OZ_OPER_BYTES;             // 64 KB
+constexpr int OZ_SMEM_BYTES = OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256;
+constexpr uint64_t OZ_TIMEOUT_NS = 2000000000ull;             // 2 s per wait
+constexpr uint32_t OZ_IDESC = idesc_bf16_f32(OZ_BM, OZ_BN);
+
+// ============================================================== slicing
+__device__ __forceinline__ long long round_shift(unsigned long long mag, int shift) {
+    if (shift >= 64) return 0;
+    if (shift <= 0) return (long long)(mag << (-shift));
+    return (long long)((mag + (1ull << (shift - 1))) >> shift);
+}
+
+// round(x * 2^(34 - E)) for a double x
+__device__ __forceinline__ long long fixed34_d(double x, int E) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    if (ex == 0 || ex == 0x7FF) return 0;
+    const unsigned long long M = (b & ((1ull << 52) - 1)) | (1ull << 52);
+    const long long v = round_shift(M, 1075 + E - 34 - ex);
+    return (b >> 63) ? -v : v;
+}
+
+// round(f * 2^(34 - E)) for a float f
+__device__ __forceinline__ long long fixed34_f(float f, int E) {
+    const unsigned int b = __float_as_uint(f);
+    const int ef = (int)((b >> 23) & 0xFF);
+    if (ef == 0 || ef == 0xFF) return 0;
+    const unsigned long long M = (b & 0x7FFFFFu) | 0x800000u;
+    const long long v = round_shift(M, 116 + E - ef);
+    return (b >> 31) ? -v : v;
+}
+
+// One warp per row: pass 1 finds the row's max exponent, pass 2 writes the
+// four slices (zero beyond `cols`, up to Kp) and the row scale 2^E.
+template <bool PAIR>
+__global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restrict__ X, const float2* __restrict__ Xp,
+                                                         int rows, int cols, int ldx, __nv_bfloat16* __restrict__ out,
+                                                         int Kp, float* __restrict__ scale) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * 8 + warp;
+    if (row >= rows) return;
+    // pass 1: largest magnitude (as exponent)
+    int emax = -100000;
+    for (int k = lane; k < cols; k += 32) {
+        int e;
+        if (PAIR) {
+            const float2 v = Xp[(size_t)row * ldx + k];
+            const unsigned int b = __float_as_uint(v.x) & 0x7FFFFFFFu;
+            const int ef = (int)(b >> 23);
+            e = (b == 0 || ef == 0) ? -100000 : ef - 127;
+        } else {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(X[(size_t)row * ldx + k]);
+            const int ed = (int)((b >> 52) & 0x7FF);
+            e = (ed == 0) ? -100000 : ed - 1023;
+        }
+        emax = max(emax, e);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+    const bool zero_row = emax < -1000 || emax > 126;
+    const int E = emax + 1;                       // |x| < 2^E for every entry of the row
+    if (lane == 0) scale[row] = zero_row ? 0.0f : ldexpf(1.0f, E);
+    const size_t plane = (size_t)rows * Kp;
+    for (int k = lane; k < Kp; k += 32) {
+        long long V = 0;
+        if (!zero_row && k < cols) {
+            if (PAIR) {
+                const float2 v = Xp[(size_t)row * ldx + k];
+                V = fixed34_f(v.x, E) + fixed34_f(v.y, E);
+            } else {
+                V = fixed34_d(X[(size_t)row * ldx + k], E);
+            }
+        }
+        const long long d0 = (V + (1ll << 27)) >> 28;
+        long long r = V - (d0 << 28);
+        const long long d1 = (r + (1ll << 20)) >> 21;
+        r -= d1 << 21;
+        const long long d2 = (r + (1ll << 13)) >> 14;
+        r -= d2 << 14;
+        const long long d3 = (r + (1ll << 6)) >> 7;
+        const size_t o = (size_t)row * Kp + k;
+        out[o] = __float2bfloat16_rn(ldexpf((float)d0, -6));
+        out[plane + o] = __float2bfloat16_rn(ldexpf((float)d1, -13));
+        out[2 * plane + o] = __float2bfloat16_rn(ldexpf((float)d2, -20));
+        out[3 * plane + o] = __float2bfloat16_rn(ldexpf((float)d3, -27));
+    }
+}
+
+void launch_slice_rows_f64(const double* X, int rows, int cols, int ldx, __nv_bfloat16* out, int Kp, float* scale,
+                           cudaStream_t st) {
+    slice_rows_kernel<false><<<(rows + 7) / 8, 256, 0, st>>>(X, nullptr, rows, cols, ldx, out, Kp, scale);
+}
+
+void launch_slice_rows_pair(const float2* Xp, int rows, int cols, int ldx, __nv_bfloat16* out, int Kp, float* scale,
+                            cudaStream_t st) {
+    slice_rows_kernel<true><<<(rows + 7) / 8, 256, 0, st>>>(nullptr, Xp, rows, cols, ldx, out, Kp, scale);
+}
+
+// ============================================================== tcgen05 GEMM
+__device__ __forceinline__ void oz_tile_coords(const OzParams& p, int& tm, int& tn) {
+    const int t = blockIdx.x;
+    if (p.tri) {
+        int T = p.tiles_n, r = 0, rem = t;
+        while (rem >= T - r) {
+            rem -= T - r;
+            ++r;
+        }
+        tm = r;
+        tn = r + rem;
+    } else {
+        tm = t / p.tiles_n;
+        tn = t % p.tiles_n;
+    }
+}
+
+__global__ void __launch_bounds__(192, 1) ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                             const __grid_constant__ CUtensorMap tmB,
+                                                             const OzParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OZ_STAGES * OZ_STAGE_BYTES);
+    // bars[0..S): full, bars[S..2S): empty, bars[2S]: accumulators ready
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * OZ_STAGES + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int tm, tn;
+    oz_tile_coords(p, tm, tn);
+    const int m0 = tm * OZ_BM, n0 = tn * OZ_BN;
+    const int nk = p.Kp / OZ_BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < OZ_STAGES; ++s) {
+            mbar_init(smem_u32(&bars[s]), 1);
+            mbar_init(smem_u32(&bars[OZ_STAGES + s]), 1);
+        }
+        mbar_init(smem_u32(&bars[2 * OZ_STAGES]), 1);
+        fence_mbar_init();
+    }
+    if (warp == 0 && lane == 0) {
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmB);
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(tmem_slot), 512);
+        tmem_relinquish();
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued[OZ_STAGES] = {0, 0, 0};
+            bool ok = true;
+            for (int kb = 0; kb < nk && ok; ++kb) {
+                const int s = kb % OZ_STAGES;
+                const uint32_t ph = (kb / OZ_STAGES) & 1;
+                if (kb >= OZ_STAGES && !mbar_wait(smem_u32(&bars[OZ_STAGES + s]), ph ^ 1, OZ_TIMEOUT_NS)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t full = smem_u32(&bars[s]);
+                uint8_t* st = smem + s * OZ_STAGE_BYTES;
+                mbar_arrive_expect_tx(full, OZ_STAGE_BYTES);
+                tma_load_3d(smem_u32(st), &tmA, full, kb * OZ_BK, m0, 0);
+                tma_load_3d(smem_u32(st + OZ_OPER_BYTES), &tmB, full, kb * OZ_BK, n0, 0);
+                issued[s]++;
+            }
+            if (!ok) atomicOr(p.status, DEV_TIMEOUT);
+            // every load this thread issued has landed before the CTA may exit
+            for (int s = 0; s < OZ_STAGES; ++s)
+                if (issued[s] > 0 && !mbar_wait(smem_u32(&bars[s]), (issued[s] - 1) & 1, OZ_TIMEOUT_NS))
+                    atomicOr(p.status, DEV_TIMEOUT);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            bool ok = true;
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % OZ_STAGES;
+                const uint32_t ph = (kb / OZ_STAGES) & 1;
+                if (!mbar_wait(smem_u32(&bars[s]), ph, OZ_TIMEOUT_NS)) {
+                    ok = false;
+                    break;
+                }
+                fence_after_sync();
+                const uint32_t a0 = smem_u32(smem + s * OZ_STAGE_BYTES);
+                const uint32_t b0 = a0 + OZ_OPER_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+#pragma unroll
+                    for (int sa = 0; sa < OZ_SLICES; ++sa) {
+#pragma unroll
+                        for (int sb = 0; sb + sa < OZ_SLICES; ++sb) {
+                            const uint64_t ad = desc_kmajor_sw64(a0 + sa * OZ_SLICE_BYTES + kk * 32);
+                            const uint64_t bd = desc_kmajor_sw64(b0 + sb * OZ_SLICE_BYTES + kk * 32);
+                            const uint32_t acc = (kb > 0 || kk > 0 || sa > 0) ? 1u : 0u;
+                            mma_bf16(tmem + (uint32_t)((sa + sb) * OZ_BN), ad, bd, OZ_IDESC, acc);
+                        }
+                    }
+                }
+                mma_commit(smem_u32(&bars[OZ_STAGES + s]));
+            }
+            if (!ok) atomicOr(p.status, DEV_TIMEOUT);
+            mma_commit(smem_u32(&bars[2 * OZ_STAGES]));
+        }
+    } else {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 = tile rows
+        const int q = warp & 3;
+        const int i = m0 + 32 * q + lane;
+        const bool ready = mbar_wait(smem_u32(&bars[2 * OZ_STAGES]), 0, OZ_TIMEOUT_NS);
+        fence_after_sync();
+        if (!ready) {
+            if (lane == 0) atomicOr(p.status, DEV_TIMEOUT);
+        } else {
+            const float sA = (i < p.M) ? p.sa[i] : 0.0f;
+#pragma unroll 1
+            for (int c = 0; c < OZ_BN / 32; ++c) {
+                uint32_t r0[32], r1[32], r2[32], r3[32];
+                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(c * 32);
+                tmem_ld_32x32b_x32(ta, r0);
+                tmem_ld_32x32b_x32(ta + OZ_BN, r1);
+                tmem_ld_32x32b_x32(ta + 2 * OZ_BN, r2);
+                tmem_ld_32x32b_x32(ta + 3 * OZ_BN, r3);
+                tmem_ld_wait();
+                if (i >= p.M) continue;
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) {
+                    const int j = n0 + c * 32 + jj;
+                    if (j >= p.N) break;
+                    const float s = sA * p.sb[j];
+                    const float hi = __uint_as_float(r0[jj]);
+                    const float lo = (__uint_as_float(r1[jj]) + __uint_as_float(r2[jj])) + __uint_as_float(r3[jj]);
+                    // TwoSum: (sh, sl) = hi + lo exactly
+                    const float sh = hi + lo;
+                    const float bb = sh - hi;
+                    const float sl = (hi - (sh - bb)) + (lo - bb);
+                    if (p.mode == OZ_OUT_PAIR) {
+                        p.Cp[(size_t)i * p.ldc + j] = make_float2(sh * s, sl * s);
+                    } else {
+                        if (p.tri && i > j) continue;
+                        const size_t off = (size_t)i * p.ldc + j;
+                        double v = p.alpha * ((double)(sh * s) + (double)(sl * s));
+                        if (p.D1) v += p.b1 * p.D1[off];
+                        if (p.D2) v += p.b2 * p.D2[off];
+                        if (p.D3) v += p.b3 * p.D3[off];
+                        p.Cd[off] = v;
+                        if (p.tri && i != j) p.Cd[(size_t)j * p.ldc + i] = v;
+                    }
+                }
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (warp == 1) tmem_dealloc(tmem, 512);
+}
+
+// ============================================================== host side
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::once_flag g_encode_once;
+
+static dme_status get_encoder() {
+    std::call_once(g_encode_once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!g_encode) {
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return DME_ECUDA;
+    }
+    return DME_OK;
+}
+
+dme_status make_slice_tmap(const SliceBuf& sb, CUtensorMap* out) {
+    DME_TRY(get_encoder());
+    cuuint64_t dims[3] = {(cuuint64_t)sb.Kp, (cuuint64_t)sb.rows, (cuuint64_t)OZ_SLICES};
+    cuuint64_t strides[2] = {(cuuint64_t)sb.Kp * 2, (cuuint64_t)sb.rows * sb.Kp * 2};
+    cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)OZ_BM, (cuuint32_t)OZ_SLICES};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = g_encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)sb.data, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+        return DME_ECUDA;
+    }
+    return DME_OK;
+}
+
+int slice_kpad(int k) { return (k + OZ_BK - 1) / OZ_BK * OZ_BK; }
+
+size_t slice_buf_bytes(int rows, int k) { return (size_t)OZ_SLICES * rows * slice_kpad(k) * 2; }
+
+static bool g_attr_set = false;
+
+dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzParams p, cudaStream_t st) {
+    if (p.M <= 0 || p.N <= 0) return DME_OK;
+    if (p.Kp % OZ_BK != 0 || p.Kp > OZ_MAX_K) {
+        set_error("ozaki gemm: K must be a multiple of 32 and at most 4096");
+        return DME_EINVAL;
+    }
+    if (p.tri && p.M != p.N) {
+        set_error("ozaki gemm: triangle mode needs M == N");
+        return DME_EINVAL;
+    }
+    if (!g_attr_set) {
+        DME_CUDA_TRY(cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          OZ_SMEM_BYTES));
+        g_attr_set = true;
+    }
+    const int tmt = (p.M + OZ_BM - 1) / OZ_BM, tnt = (p.N + OZ_BN - 1) / OZ_BN;
+    p.tiles_n = tnt;
+    const int grid = p.tri ? tnt * (tnt + 1) / 2 : tmt * tnt;
+    ozaki_gemm_kernel<<<grid, 192, OZ_SMEM_BYTES, st>>>(tA, tB, p);
+    DME_CUDA_TRY(cudaGetLastError());
+    return DME_OK;
+}
+
+}  // namespace dme

@@ -16,6 +16,7 @@
 //  * squaring the block matrix is the semigroup law of T12 (Eq. full):
 //    E_{2t} = E_t^2, W_{2t} = W_t + E_t^T W_t E_t.
 #include "dme_internal.h"
+#include "split_internal.h"
 
 #include <algorithm>
 #include <cmath>
@@ -51,6 +52,7 @@ struct EWEntry {
     double* E;
     double* W;
     int s;
+    SliceBuf Gsl;   // split path: slices of E^T (rows of E^T = columns of E)
 };
 
 enum OpKind { OP_CONG = 0, OP_AXPY = 1, OP_RICC = 2, OP_SFLOW = 3 };
@@ -89,6 +91,9 @@ struct dme_plan_s {
     cudaGraphExec_t gexec = nullptr;
     double* gP = nullptr;
     int graph_kernels = -1;
+    bool split = false;
+    SliceBuf psl, usl, Ssl;    // split path: slices of P, of U = G P, and of S
+    float2* U = nullptr;       // split path: G P as normalised (hi, lo) pairs
 };
 
 namespace {
@@ -200,6 +205,57 @@ dme_status bprod(int n, const double* L22, const double* L12, double ls, const d
     return DME_OK;
 }
 
+dme_status alloc_slices(dme_plan_t p, SliceBuf* sb, int rows, int k) {
+    sb->rows = rows;
+    sb->k = k;
+    sb->Kp = slice_kpad(k);
+    DME_TRY(palloc(p, reinterpret_cast<void**>(&sb->data), slice_buf_bytes(rows, k)));
+    DME_TRY(palloc_t(p, &sb->scale, (size_t)rows));
+    return make_slice_tmap(*sb, &sb->tmap);
+}
+
+// out = alpha G P G^T + b1 D1 + b2 D2 + b3 D3 on the split-precision path (P
+// symmetric, G given by its row slices).  U = G P (P^T = P), then G U^T.
+dme_status split_cong(dme_plan_t p, const double* P, const SliceBuf& G, double* out, double alpha, const double* D1,
+                      double b1, const double* D2, double b2, const double* D3, double b3) {
+    const int n = p->n;
+    cudaStream_t st = p->st;
+    launch_slice_rows_f64(P, n, n, n, p->psl.data, p->psl.Kp, p->psl.scale, st);
+    OzParams a;
+    std::memset(&a, 0, sizeof(a));
+    a.M = n;
+    a.N = n;
+    a.Kp = G.Kp;
+    a.sa = G.scale;
+    a.sb = p->psl.scale;
+    a.mode = OZ_OUT_PAIR;
+    a.ldc = n;
+    a.Cp = p->U;
+    a.status = p->status;
+    DME_TRY(launch_ozaki_gemm(G.tmap, p->psl.tmap, a, st));
+    launch_slice_rows_pair(p->U, n, n, n, p->usl.data, p->usl.Kp, p->usl.scale, st);
+    OzParams b;
+    std::memset(&b, 0, sizeof(b));
+    b.M = n;
+    b.N = n;
+    b.Kp = G.Kp;
+    b.sa = G.scale;
+    b.sb = p->usl.scale;
+    b.mode = OZ_OUT_F64;
+    b.tri = 1;
+    b.ldc = n;
+    b.Cd = out;
+    b.alpha = alpha;
+    b.D1 = D1;
+    b.b1 = b1;
+    b.D2 = D2;
+    b.b2 = b2;
+    b.D3 = D3;
+    b.b3 = b3;
+    b.status = p->status;
+    return launch_ozaki_gemm(G.tmap, p->usl.tmap, b, st);
+}
+
 dme_status compute_ew(dme_plan_t p, double tau, int* idx) {
     for (size_t i = 0; i < p->ew.size(); ++i)
         if (p->ew[i].tau == tau) {
@@ -307,6 +363,11 @@ dme_status compute_ew(dme_plan_t p, double tau, int* idx) {
     DME_TRY(palloc_t(p, &ent.W, nn));
     DME_CUDA_TRY(cudaMemcpyAsync(ent.E, E, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
     DME_CUDA_TRY(cudaMemcpyAsync(ent.W, Wm, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (p->split) {
+        launch_transpose(ent.E, tmp, n, n, n, n, st);          // tmp = E^T
+        DME_TRY(alloc_slices(p, &ent.Gsl, n, n));
+        launch_slice_rows_f64(tmp, n, n, n, ent.Gsl.data, ent.Gsl.Kp, ent.Gsl.scale, st);
+    }
     DME_CUDA_TRY(cudaGetLastError());
     DME_TRY(check_status(p, "dme_expm"));
     p->ew.push_back(ent);
@@ -408,9 +469,22 @@ dme_status run_sflow(dme_plan_t p, double* P, double tau, int rule, double qcoef
     return DME_OK;
 }
 
+dme_status run_sflow_split(dme_plan_t p, double* P, double tau, int rule, double qcoef) {
+    const double* Qd = qcoef != 0.0 ? p->Q : nullptr;
+    if (rule == DME_T4_EULER) return split_cong(p, P, p->Ssl, P, tau, P, 1.0, Qd, qcoef, nullptr, 0.0);
+    DME_TRY(split_cong(p, P, p->Ssl, p->Xs, 1.0, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0));   // Xs = S P S^T
+    return split_cong(p, p->Xs, p->Ssl, P, 0.5 * tau * tau, P, 1.0, p->Xs, tau, Qd, qcoef);     // + t^2/2 S Xs S^T
+}
+
 dme_status run_op(dme_plan_t p, const Op& o, double* P) {
     const int n = p->n;
     cudaStream_t st = p->st;
+    if (p->split && o.kind == OP_CONG) {
+        const EWEntry& e = p->ew[o.ew];
+        return split_cong(p, P, e.Gsl, P, 1.0, o.wcoef != 0.0 ? e.W : nullptr, o.wcoef,
+                          o.qcoef != 0.0 ? p->Q : nullptr, o.qcoef, nullptr, 0.0);
+    }
+    if (p->split && o.kind == OP_SFLOW) return run_sflow_split(p, P, o.tau, o.rule, o.qcoef);
     switch (o.kind) {
         case OP_CONG: {
             const EWEntry& e = p->ew[o.ew];
@@ -472,8 +546,12 @@ void free_plan(dme_plan_t p) {
 dme_status plan_create(const dme_plan_desc* d, const double* A, const double* QorC, const double* B,
                        const double* R, const double* S, void* stream, dme_plan_t* out) {
     DME_TRY(validate(d, A, QorC, B, R, S));
-    if (d->prec == DME_SPLIT_BF16) {
-        set_error("DME_SPLIT_BF16 is not available in this build");
+    if (d->prec == DME_SPLIT_BF16 && d->n > OZ_MAX_K) {
+        set_error("DME_SPLIT_BF16 supports n <= 4096 (exact slice accumulation over K <= 4096)");
+        return DME_EINVAL;
+    }
+    if (d->prec == DME_SPLIT_BF16 && d->slices != 0 && d->slices != OZ_SLICES) {
+        set_error("DME_SPLIT_BF16 uses 4 slices per operand");
         return DME_EINVAL;
     }
     dme_plan_t p = new (std::nothrow) dme_plan_s();
@@ -485,6 +563,7 @@ dme_status plan_create(const dme_plan_desc* d, const double* A, const double* Qo
     const bool gen = (d->eq == DME_GDLE || d->eq == DME_GDRE);
     p->n = n;
     p->m = ric ? d->m : 0;
+    p->split = (d->prec == DME_SPLIT_BF16);
     if (stream) {
         p->st = reinterpret_cast<cudaStream_t>(stream);
     } else {
@@ -530,6 +609,15 @@ dme_status plan_create(const dme_plan_desc* d, const double* A, const double* Qo
         DME_TRY(palloc_t(p, &p->Xs, nn));
         DME_TRY(palloc_t(p, &p->Y1, nn));
         DME_CUDA_TRY(cudaMemcpyAsync(p->S, S, nn * sizeof(double), cudaMemcpyDefault, st));
+    }
+    if (p->split) {
+        DME_TRY(alloc_slices(p, &p->psl, n, n));
+        DME_TRY(alloc_slices(p, &p->usl, n, n));
+        DME_TRY(palloc_t(p, &p->U, nn));
+        if (gen) {
+            DME_TRY(alloc_slices(p, &p->Ssl, n, n));
+            launch_slice_rows_f64(p->S, n, n, n, p->Ssl.data, p->Ssl.Kp, p->Ssl.scale, st);
+        }
     }
     // ||[[-A^T, Q], [0, A]]||_1 for the scaling of every t
     launch_block_norm1(p->A, p->Q, n, p->small, st);
@@ -700,5 +788,77 @@ dme_status dme_plan_destroy(dme_plan_t plan) {
 }
 
 const char* dme_last_error(void) { return get_error(); }
+
+dme_status dme_gemm_split(int M, int N, int K, const double* A, const double* B, double* C, void* cuda_stream) {
+    if (M < 0 || N < 0 || K < 1 || K > OZ_MAX_K || !A || !B || !C)
+        return set_error("dme_gemm_split: need 1 <= K <= 4096 and non-null A, B, C"), DME_EINVAL;
+    if (M == 0 || N == 0) return DME_OK;
+    return guarded([&]() -> dme_status {
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+        const int Kp = slice_kpad(K);
+        std::vector<void*> tmp;
+        auto cleanup = [&] {
+            cudaStreamSynchronize(st);
+            for (void* q : tmp) cudaFree(q);
+        };
+        auto get = [&](size_t bytes, void** out) -> dme_status {
+            if (cudaMalloc(out, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("dme_gemm_split: cudaMalloc failed");
+                return DME_ENOMEM;
+            }
+            tmp.push_back(*out);
+            return DME_OK;
+        };
+        SliceBuf sa, sb;
+        sa.rows = M;
+        sa.k = K;
+        sa.Kp = Kp;
+        sb.rows = N;
+        sb.k = K;
+        sb.Kp = Kp;
+        int* status = nullptr;
+        dme_status s = DME_OK;
+        if ((s = get(slice_buf_bytes(M, K), reinterpret_cast<void**>(&sa.data))) != DME_OK ||
+            (s = get(slice_buf_bytes(N, K), reinterpret_cast<void**>(&sb.data))) != DME_OK ||
+            (s = get(sizeof(float) * M, reinterpret_cast<void**>(&sa.scale))) != DME_OK ||
+            (s = get(sizeof(float) * N, reinterpret_cast<void**>(&sb.scale))) != DME_OK ||
+            (s = get(sizeof(int), reinterpret_cast<void**>(&status))) != DME_OK ||
+            (s = make_slice_tmap(sa, &sa.tmap)) != DME_OK || (s = make_slice_tmap(sb, &sb.tmap)) != DME_OK) {
+            cleanup();
+            return s;
+        }
+        cudaMemsetAsync(status, 0, sizeof(int), st);
+        launch_slice_rows_f64(A, M, K, K, sa.data, Kp, sa.scale, st);
+        launch_slice_rows_f64(B, N, K, K, sb.data, Kp, sb.scale, st);
+        OzParams o;
+        std::memset(&o, 0, sizeof(o));
+        o.M = M;
+        o.N = N;
+        o.Kp = Kp;
+        o.sa = sa.scale;
+        o.sb = sb.scale;
+        o.mode = OZ_OUT_F64;
+        o.ldc = N;
+        o.Cd = C;
+        o.alpha = 1.0;
+        o.status = status;
+        s = launch_ozaki_gemm(sa.tmap, sb.tmap, o, st);
+        int hs = 0;
+        if (s == DME_OK) {
+            cudaError_t e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) {
+                set_error(std::string("dme_gemm_split: ") + cudaGetErrorString(e));
+                s = DME_ECUDA;
+            } else if (hs) {
+                set_error("dme_gemm_split: device status " + std::to_string(hs));
+                s = DME_ECUDA;
+            }
+        }
+        cleanup();
+        return s;
+    });
+}
 
 }  // extern "C"

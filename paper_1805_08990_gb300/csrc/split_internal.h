@@ -1,0 +1,52 @@
+// Declarations of the split-precision (bf16 slice) path shared by libdme units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "dme_internal.h"
+
+namespace dme {
+
+constexpr int OZ_SLICES = 4;        // bf16 slices per operand row
+constexpr int OZ_MAX_K = 4096;      // exact level-0 accumulation needs K * 64 * 64 <= 2^24
+enum { OZ_OUT_PAIR = 0, OZ_OUT_F64 = 1 };
+
+// Slices of a rows x k operand: planes [OZ_SLICES][rows][Kp] bf16 (Kp = k
+// rounded up to 32, zero padded) and one power-of-two scale per row.
+struct SliceBuf {
+    __nv_bfloat16* data = nullptr;
+    float* scale = nullptr;
+    int rows = 0, k = 0, Kp = 0;
+    CUtensorMap tmap;
+};
+
+struct OzParams {
+    int M, N, Kp;
+    const float* sa;      // row scales of A (M)
+    const float* sb;      // row scales of B (N)
+    int mode;             // OZ_OUT_PAIR or OZ_OUT_F64
+    int tri;              // OZ_OUT_F64 only: upper tiles, mirrored (M == N)
+    int ldc;
+    float2* Cp;           // OZ_OUT_PAIR output (normalised hi, lo)
+    double* Cd;           // OZ_OUT_F64 output
+    double alpha;         // OZ_OUT_F64: v = alpha acc + b1 D1 + b2 D2 + b3 D3
+    const double* D1;
+    const double* D2;
+    const double* D3;
+    double b1, b2, b3;
+    int tiles_n;          // set by the launcher
+    int* status;
+};
+
+int slice_kpad(int k);
+size_t slice_buf_bytes(int rows, int k);
+dme_status make_slice_tmap(const SliceBuf& sb, CUtensorMap* out);
+void launch_slice_rows_f64(const double* X, int rows, int cols, int ldx, __nv_bfloat16* out, int Kp, float* scale,
+                           cudaStream_t st);
+void launch_slice_rows_pair(const float2* Xp, int rows, int cols, int ldx, __nv_bfloat16* out, int Kp,
+                            float* scale, cudaStream_t st);
+dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzParams p, cudaStream_t st);
+
+}  // namespace dme
