@@ -51,9 +51,10 @@ typedef enum { DME_DLE = 0, DME_DRE = 1, DME_GDLE = 2, DME_GDRE = 3 } dme_eq;
 typedef enum { DME_F1 = 1, DME_F2 = 2, DME_F12 = 3, DME_F3 = 4, DME_F4 = 5 } dme_flow;
 typedef enum { DME_LIE = 1, DME_STRANG = 2 } dme_comp;
 /* DME_FP64: every product in float64 on the FP64 pipe.
- * DME_SPLIT_BF16: congruences as error-free bf16 slice products on tcgen05
- *   tensor cores accumulated exactly in fp32 (Ozaki splitting), combined in
- *   fp64; the m x m solves, expm denominator solve and squaring stay fp64. */
+ * DME_SPLIT_BF16: congruences (T1, T12, T4) as error-free bf16 slice products
+ *   on tcgen05 tensor cores accumulated exactly in fp32 (Ozaki splitting),
+ *   combined in fp64; n <= 4096.  The Riccati update with its m x m solve, the
+ *   expm (Pade chain, denominator solve, squaring) stay fp64. */
 typedef enum { DME_FP64 = 0, DME_SPLIT_BF16 = 1 } dme_prec;
 /* T4 rule; AUTO = midpoint for Strang, explicit Euler for Lie (§2.3). */
 typedef enum { DME_T4_AUTO = 0, DME_T4_MIDPOINT = 1, DME_T4_EULER = 2 } dme_t4_rule;
@@ -126,6 +127,20 @@ size_t dme_plan_bytes(dme_plan_t plan);
  * dme_step / dme_solve), or -1 if no step has been captured yet. */
 int dme_plan_kernels_per_step(dme_plan_t plan);
 
+/* Kernel kinds for dme_plan_timing. */
+enum { DME_KIND_SPLIT_GEMM = 0, DME_KIND_SLICE = 1, DME_KIND_FP64_GEMM = 2, DME_KIND_RICCATI = 3 };
+
+/* Profiling mode (off by default): while enabled, the launches the plan
+ * makes outside CUDA-graph replay (dme_apply, dme_apply_async, capture-free
+ * work) are bracketed by CUDA events on the plan's stream, per kernel kind.
+ * For DME_KIND_FP64_GEMM and DME_KIND_RICCATI one bracket covers the
+ * launches of one congruence or one Riccati update. */
+dme_status dme_plan_profile(dme_plan_t plan, int enable);
+
+/* Synchronise the plan's stream, then return the milliseconds and bracket
+ * count accumulated for `kind` since the last call, and reset them. */
+dme_status dme_plan_timing(dme_plan_t plan, int kind, double* ms, int* launches);
+
 dme_status dme_plan_destroy(dme_plan_t plan);
 
 /* ---- serving: continuous batching of independent DRE/DLE solves ----------
@@ -159,10 +174,11 @@ dme_status dme_server_destroy(dme_server_t srv);
 
 /* C = A B^T on the split-precision tensor-core path used by DME_SPLIT_BF16:
  * every row of A (M x K) and of B (N x K) is scaled by a power of two and cut
- * into four bf16 slices (6 + 7 + 7 + 7 bits); the ten slice products of
- * levels 0..3 are accumulated in fp32 on tcgen05 tensor cores, exactly for
- * level 0 (K <= 4096 keeps every partial sum below 2^24 units), and combined
- * in fp64.  Relative error per entry ~ 2^-28 of the row scales.  All
+ * into bf16 slices of 6 + 7 + 7 + ... bits (five for A, four for B); the 14
+ * slice products of levels 0..4 are accumulated in fp32 on tcgen05 tensor
+ * cores, exactly for level 0 (K <= 4096 keeps every partial sum below 2^24
+ * units), and combined in fp64.  Entry errors are ~2^-28 of the B row scale
+ * times the A row scale (times sqrt(K) for random signs).  All
  * matrices are float64 row-major device memory; C is M x N.  Synchronises
  * `cuda_stream`.  DME_EINVAL unless 1 <= K <= 4096. */
 dme_status dme_gemm_split(int M, int N, int K, const double* A, const double* B, double* C,

@@ -8,6 +8,7 @@ load the library; the first call does, and fails loudly if it is not built.
 from .binding import (  # noqa: F401
     DME_DLE, DME_DRE, DME_GDLE, DME_GDRE, DME_F1, DME_F2, DME_F12, DME_F3, DME_F4,
     DME_LIE, DME_STRANG, DME_FP64, DME_SPLIT_BF16, DME_T4_AUTO, DME_T4_MIDPOINT, DME_T4_EULER,
+    DME_KIND_SPLIT_GEMM, DME_KIND_SLICE, DME_KIND_FP64_GEMM, DME_KIND_RICCATI, dme_plan_profile, dme_plan_timing,
     DME_OK, DME_EINVAL, DME_ENOMEM, DME_ENOTSPD, DME_ECUDA, DME_ETIMEOUT, DME_EBUSY, DME_ENOTREADY,
     DmeError, LibraryNotBuilt, dme_plan_desc, make_desc, lib, header_functions,
     dme_plan, dme_expm, dme_apply, dme_apply_async, dme_sync, dme_plan_kernels_per_step, dme_step, dme_solve, dme_plan_bytes, dme_plan_destroy,
@@ -47,6 +48,12 @@ class Plan:
 
     def sync(self):
         dme_sync(self.handle)
+
+    def profile(self, enable=True):
+        dme_plan_profile(self.handle, enable)
+
+    def timing(self, kind):
+        return dme_plan_timing(self.handle, kind)
 
     @property
     def kernels_per_step(self):

@@ -25,6 +25,7 @@ DME_F1, DME_F2, DME_F12, DME_F3, DME_F4 = 1, 2, 3, 4, 5
 DME_LIE, DME_STRANG = 1, 2
 DME_FP64, DME_SPLIT_BF16 = 0, 1
 DME_T4_AUTO, DME_T4_MIDPOINT, DME_T4_EULER = 0, 1, 2
+DME_KIND_SPLIT_GEMM, DME_KIND_SLICE, DME_KIND_FP64_GEMM, DME_KIND_RICCATI = 0, 1, 2, 3
 
 FLOW_IDS = {"F1": DME_F1, "F2": DME_F2, "F12": DME_F12, "F3": DME_F3, "F4": DME_F4}
 COMP_IDS = {"lie": DME_LIE, "strang": DME_STRANG}
@@ -59,6 +60,8 @@ _SIGS = {
     "dme_apply_async": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p]),
     "dme_sync": (C.c_int, [C.c_void_p]),
     "dme_plan_kernels_per_step": (C.c_int, [C.c_void_p]),
+    "dme_plan_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "dme_plan_timing": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "dme_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "dme_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_void_p]),
     "dme_plan_bytes": (C.c_size_t, [C.c_void_p]),
@@ -173,6 +176,18 @@ def dme_sync(plan: int):
 
 def dme_plan_kernels_per_step(plan: int) -> int:
     return int(lib().dme_plan_kernels_per_step(plan))
+
+
+def dme_plan_profile(plan: int, enable: bool):
+    _check(lib().dme_plan_profile(plan, int(bool(enable))), "dme_plan_profile")
+
+
+def dme_plan_timing(plan: int, kind: int):
+    """(milliseconds, launches) accumulated for one kernel kind since the last call."""
+    ms = C.c_double()
+    cnt = C.c_int()
+    _check(lib().dme_plan_timing(plan, int(kind), C.byref(ms), C.byref(cnt)), "dme_plan_timing")
+    return ms.value, cnt.value
 
 
 def dme_step(plan: int, P, nsteps: int):

@@ -3,20 +3,27 @@
 // Error-free slicing (after Ozaki, Ogita, Oishi & Rump, "Error-free
 // transformations of matrix multiplication by using fast routines of matrix
 // multiplication", Numer. Algorithms 59, 2012): each row r of an operand is
-// scaled by sigma_r = 2^E_r >= max |x_r.| and cut into four bf16 slices
-//     x / sigma = d0 2^-6 + d1 2^-13 + d2 2^-20 + d3 2^-27 (+ |res| <= 2^-28),
-// with integers |d_t| <= 64.  A slice product d_s d_t 2^-(12+7(s+t)) is exact in
-// bf16 x bf16, and a level l = s + t sums K <= 4096 such products: at most
-// 2^24 units of 2^-(12+7l), so the fp32 tensor-core accumulation of level 0 is
-// exact whatever its rounding mode, and levels 1-3 only round far below the
-// slice residual.  Levels 0..3 (10 slice pairs) each get their own TMEM
-// accumulator; the epilogue adds them as a two-float (hi = level 0 exact,
-// lo = levels 1-3) and scales by sigma_A,i sigma_B,j.
+// scaled by sigma_r = 2^E_r > max |x_r.| and cut into bf16 slices
+//     x / sigma = d0 2^-6 + d1 2^-13 + d2 2^-20 + d3 2^-27 + d4 2^-34 + res,
+// with integers |d_t| <= 64.  The fixed operand (G = E^T or S, the A side)
+// keeps five slices (|res| <= 2^-35): its slicing error is the same at every
+// step and would otherwise add up coherently over the horizon.  The per-step
+// operand (P or U, the B side) keeps four (|res| <= 2^-28); its errors are
+// fresh each step and averaged by the congruence.
+// A slice product d_s d_t 2^-(12+7(s+t)) is exact in bf16 x bf16, and a level
+// l = s + t sums K <= 4096 such products: at most 2^24 units of
+// 2^-(12+7l), so the fp32 tensor-core accumulation of level 0 is exact
+// whatever its rounding mode, and the other levels round far below the
+// slice residuals.  The 14 pairs with s + t <= 4 are accumulated in four TMEM
+// accumulators (levels 0, 1, 2 and 3+4); the epilogue adds them as a
+// two-float (hi = level 0, exact; lo = levels 1-4) and scales by
+// sigma_A,i sigma_B,j.
 //
 // Kernel shape: one CTA per 128 x 128 output tile, 6 warps:
-//   warp 0  TMA producer (one thread): 3-stage ring, each stage holds the 4
-//           slices of a 128 x 32 A tile and of a 128 x 32 B tile (64 KB),
-//   warp 1  TMEM allocator + MMA issuer (one thread): 20 tcgen05.mma per stage,
+//   warp 0  TMA producer (one thread): 3-stage ring, each stage holds the 5
+//           slices of a 128 x 32 A tile and the 4 slices of a 128 x 32 B tile
+//           (72 KB, 64-byte swizzled rows),
+//   warp 1  TMEM allocator + MMA issuer (one thread): 28 tcgen05.mma per stage,
 //   warps 2-5 epilogue: tcgen05.ld of the 4 accumulators (512 TMEM columns).
 // Both operands are K-major (row-major with K contiguous):
 //   C[i][j] = sum_k A[i][k] B[j][k].
@@ -34,10 +41,13 @@ namespace dme {
 using namespace tc;
 
 constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 32, OZ_STAGES = 3;
-constexpr int OZ_SLICE_BYTES = OZ_BM * OZ_BK * 2;              // 8 KB per slice tile
-constexpr int OZ_OPER_BYTES = OZ_SLICES * OZ_SLICE_BYTES;     // 32 KB per operand per stage
-constexpr int OZ_STAGE_BYTES = 2 * OZ_OPER_BYTES;             // 64 KB
+constexpr int OZ_SLICE_BYTES = OZ_BM * OZ_BK * 2;                 // 8 KB per slice tile
+constexpr int OZ_A_BYTES = OZ_SLICES_A * OZ_SLICE_BYTES;         // 40 KB per stage
+constexpr int OZ_B_BYTES = OZ_SLICES_B * OZ_SLICE_BYTES;         // 32 KB per stage
+constexpr int OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;          // 72 KB
 constexpr int OZ_SMEM_BYTES = OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256;
+constexpr int OZ_MAX_LEVEL = 4;                                   // pairs with s + t <= 4
+constexpr int OZ_NACC = 4;                                        // accumulators: levels 0, 1, 2, 3+4
 constexpr uint64_t OZ_TIMEOUT_NS = 2000000000ull;             // 2 s per wait
 constexpr uint32_t OZ_IDESC = idesc_bf16_f32(OZ_BM, OZ_BN);
 
@@ -48,29 +58,32 @@ __device__ __forceinline__ long long round_shift(unsigned long long mag, int shi
     return (long long)((mag + (1ull << (shift - 1))) >> shift);
 }
 
-// round(x * 2^(34 - E)) for a double x
-__device__ __forceinline__ long long fixed34_d(double x, int E) {
+// round(x * 2^(41 - E)) for a double x (|x| < 2^E, so |result| <= 2^41)
+__device__ __forceinline__ long long fixed41_d(double x, int E) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int ex = (int)((b >> 52) & 0x7FF);
     if (ex == 0 || ex == 0x7FF) return 0;
     const unsigned long long M = (b & ((1ull << 52) - 1)) | (1ull << 52);
-    const long long v = round_shift(M, 1075 + E - 34 - ex);
+    const long long v = round_shift(M, 1075 + E - 41 - ex);
     return (b >> 63) ? -v : v;
 }
 
-// round(f * 2^(34 - E)) for a float f
-__device__ __forceinline__ long long fixed34_f(float f, int E) {
+// round(f * 2^(41 - E)) for a float f
+__device__ __forceinline__ long long fixed41_f(float f, int E) {
     const unsigned int b = __float_as_uint(f);
     const int ef = (int)((b >> 23) & 0xFF);
     if (ef == 0 || ef == 0xFF) return 0;
     const unsigned long long M = (b & 0x7FFFFFu) | 0x800000u;
-    const long long v = round_shift(M, 116 + E - ef);
+    const long long v = round_shift(M, 109 + E - ef);
     return (b >> 31) ? -v : v;
 }
 
 // One warp per row: pass 1 finds the row's max exponent, pass 2 writes the
-// four slices (zero beyond `cols`, up to Kp) and the row scale 2^E.
-template <bool PAIR>
+// NS slices (zero beyond `cols`, up to Kp) and the row scale 2^E.  The value
+// is first rounded to a 41-bit fixed-point integer V = round(x 2^(41-E)); the
+// slices are the base-2^7 digits of V with round-to-nearest:
+// d_t = round(r_t / 2^(35-7t)), r_{t+1} = r_t - d_t 2^(35-7t).
+template <bool PAIR, int NS>
 __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restrict__ X, const float2* __restrict__ Xp,
                                                          int rows, int cols, int ldx, __nv_bfloat16* __restrict__ out,
                                                          int Kp, float* __restrict__ scale) {
@@ -95,7 +108,9 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restric
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
-    const bool zero_row = emax < -1000 || emax > 126;
+    // rows whose largest entry is below 2^-100 or above 2^126 are stored as zero
+    // (fp32 scales and products must stay normal)
+    const bool zero_row = emax < -100 || emax > 126;
     const int E = emax + 1;                       // |x| < 2^E for every entry of the row
     if (lane == 0) scale[row] = zero_row ? 0.0f : ldexpf(1.0f, E);
     const size_t plane = (size_t)rows * Kp;
@@ -104,34 +119,36 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restric
         if (!zero_row && k < cols) {
             if (PAIR) {
                 const float2 v = Xp[(size_t)row * ldx + k];
-                V = fixed34_f(v.x, E) + fixed34_f(v.y, E);
+                V = fixed41_f(v.x, E) + fixed41_f(v.y, E);
             } else {
-                V = fixed34_d(X[(size_t)row * ldx + k], E);
+                V = fixed41_d(X[(size_t)row * ldx + k], E);
             }
         }
-        const long long d0 = (V + (1ll << 27)) >> 28;
-        long long r = V - (d0 << 28);
-        const long long d1 = (r + (1ll << 20)) >> 21;
-        r -= d1 << 21;
-        const long long d2 = (r + (1ll << 13)) >> 14;
-        r -= d2 << 14;
-        const long long d3 = (r + (1ll << 6)) >> 7;
         const size_t o = (size_t)row * Kp + k;
-        out[o] = __float2bfloat16_rn(ldexpf((float)d0, -6));
-        out[plane + o] = __float2bfloat16_rn(ldexpf((float)d1, -13));
-        out[2 * plane + o] = __float2bfloat16_rn(ldexpf((float)d2, -20));
-        out[3 * plane + o] = __float2bfloat16_rn(ldexpf((float)d3, -27));
+#pragma unroll
+        for (int t = 0; t < NS; ++t) {
+            const int sh = 35 - 7 * t;
+            const long long d = (V + (1ll << (sh - 1))) >> sh;
+            V -= d << sh;
+            out[t * plane + o] = __float2bfloat16_rn(ldexpf((float)d, -6 - 7 * t));
+        }
     }
 }
 
-void launch_slice_rows_f64(const double* X, int rows, int cols, int ldx, __nv_bfloat16* out, int Kp, float* scale,
-                           cudaStream_t st) {
-    slice_rows_kernel<false><<<(rows + 7) / 8, 256, 0, st>>>(X, nullptr, rows, cols, ldx, out, Kp, scale);
+void launch_slice_rows_f64(const double* X, int rows, int cols, int ldx, const SliceBuf& sb, cudaStream_t st) {
+    const int g = (rows + 7) / 8;
+    if (sb.ns == 5)
+        slice_rows_kernel<false, 5><<<g, 256, 0, st>>>(X, nullptr, rows, cols, ldx, sb.data, sb.Kp, sb.scale);
+    else
+        slice_rows_kernel<false, 4><<<g, 256, 0, st>>>(X, nullptr, rows, cols, ldx, sb.data, sb.Kp, sb.scale);
 }
 
-void launch_slice_rows_pair(const float2* Xp, int rows, int cols, int ldx, __nv_bfloat16* out, int Kp, float* scale,
-                            cudaStream_t st) {
-    slice_rows_kernel<true><<<(rows + 7) / 8, 256, 0, st>>>(nullptr, Xp, rows, cols, ldx, out, Kp, scale);
+void launch_slice_rows_pair(const float2* Xp, int rows, int cols, int ldx, const SliceBuf& sb, cudaStream_t st) {
+    const int g = (rows + 7) / 8;
+    if (sb.ns == 5)
+        slice_rows_kernel<true, 5><<<g, 256, 0, st>>>(nullptr, Xp, rows, cols, ldx, sb.data, sb.Kp, sb.scale);
+    else
+        slice_rows_kernel<true, 4><<<g, 256, 0, st>>>(nullptr, Xp, rows, cols, ldx, sb.data, sb.Kp, sb.scale);
 }
 
 // ============================================================== tcgen05 GEMM
@@ -202,7 +219,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_gemm_kernel(const __grid_constan
                 uint8_t* st = smem + s * OZ_STAGE_BYTES;
                 mbar_arrive_expect_tx(full, OZ_STAGE_BYTES);
                 tma_load_3d(smem_u32(st), &tmA, full, kb * OZ_BK, m0, 0);
-                tma_load_3d(smem_u32(st + OZ_OPER_BYTES), &tmB, full, kb * OZ_BK, n0, 0);
+                tma_load_3d(smem_u32(st + OZ_A_BYTES), &tmB, full, kb * OZ_BK, n0, 0);
                 issued[s]++;
             }
             if (!ok) atomicOr(p.status, DEV_TIMEOUT);
@@ -223,17 +240,21 @@ __global__ void __launch_bounds__(192, 1) ozaki_gemm_kernel(const __grid_constan
                 }
                 fence_after_sync();
                 const uint32_t a0 = smem_u32(smem + s * OZ_STAGE_BYTES);
-                const uint32_t b0 = a0 + OZ_OPER_BYTES;
+                const uint32_t b0 = a0 + OZ_A_BYTES;
 #pragma unroll
                 for (int kk = 0; kk < OZ_BK / 16; ++kk) {
 #pragma unroll
-                    for (int sa = 0; sa < OZ_SLICES; ++sa) {
+                    for (int sa = 0; sa < OZ_SLICES_A; ++sa) {
 #pragma unroll
-                        for (int sb = 0; sb + sa < OZ_SLICES; ++sb) {
+                        for (int sb = 0; sb < OZ_SLICES_B; ++sb) {
+                            if (sa + sb > OZ_MAX_LEVEL) continue;
+                            const int lvl = (sa + sb < OZ_NACC - 1) ? sa + sb : OZ_NACC - 1;
                             const uint64_t ad = desc_kmajor_sw64(a0 + sa * OZ_SLICE_BYTES + kk * 32);
                             const uint64_t bd = desc_kmajor_sw64(b0 + sb * OZ_SLICE_BYTES + kk * 32);
-                            const uint32_t acc = (kb > 0 || kk > 0 || sa > 0) ? 1u : 0u;
-                            mma_bf16(tmem + (uint32_t)((sa + sb) * OZ_BN), ad, bd, OZ_IDESC, acc);
+                            // the pairs (0, t) come first for every accumulator t: at the very
+                            // first k step they overwrite it, everything else accumulates
+                            const uint32_t acc = (kb == 0 && kk == 0 && sa == 0) ? 0u : 1u;
+                            mma_bf16(tmem + (uint32_t)(lvl * OZ_BN), ad, bd, OZ_IDESC, acc);
                         }
                     }
                 }
@@ -317,9 +338,9 @@ static dme_status get_encoder() {
 
 dme_status make_slice_tmap(const SliceBuf& sb, CUtensorMap* out) {
     DME_TRY(get_encoder());
-    cuuint64_t dims[3] = {(cuuint64_t)sb.Kp, (cuuint64_t)sb.rows, (cuuint64_t)OZ_SLICES};
+    cuuint64_t dims[3] = {(cuuint64_t)sb.Kp, (cuuint64_t)sb.rows, (cuuint64_t)sb.ns};
     cuuint64_t strides[2] = {(cuuint64_t)sb.Kp * 2, (cuuint64_t)sb.rows * sb.Kp * 2};
-    cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)OZ_BM, (cuuint32_t)OZ_SLICES};
+    cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)OZ_BM, (cuuint32_t)sb.ns};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = g_encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)sb.data, dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
@@ -333,7 +354,7 @@ dme_status make_slice_tmap(const SliceBuf& sb, CUtensorMap* out) {
 
 int slice_kpad(int k) { return (k + OZ_BK - 1) / OZ_BK * OZ_BK; }
 
-size_t slice_buf_bytes(int rows, int k) { return (size_t)OZ_SLICES * rows * slice_kpad(k) * 2; }
+size_t slice_buf_bytes(int rows, int k, int ns) { return (size_t)ns * rows * slice_kpad(k) * 2; }
 
 static bool g_attr_set = false;
 

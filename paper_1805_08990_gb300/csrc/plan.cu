@@ -94,6 +94,14 @@ struct dme_plan_s {
     bool split = false;
     SliceBuf psl, usl, Ssl;    // split path: slices of P, of U = G P, and of S
     float2* U = nullptr;       // split path: G P as normalised (hi, lo) pairs
+    // profiling: CUDA-event pairs around launches made outside graph capture
+    bool prof = false;
+    std::vector<cudaEvent_t> evpool;
+    struct EvRec {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<EvRec> evrec;
 };
 
 namespace {
@@ -205,11 +213,43 @@ dme_status bprod(int n, const double* L22, const double* L12, double ls, const d
     return DME_OK;
 }
 
-dme_status alloc_slices(dme_plan_t p, SliceBuf* sb, int rows, int k) {
+cudaEvent_t ev_get(dme_plan_t p) {
+    if (!p->evpool.empty()) {
+        cudaEvent_t e = p->evpool.back();
+        p->evpool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Bracket the launches of one kernel kind with events (profiling mode only).
+struct ProfScope {
+    dme_plan_t p;
+    int kind;
+    cudaEvent_t a = nullptr;
+    ProfScope(dme_plan_t p_, int kind_) : p(p_), kind(kind_) {
+        if (!p->prof) return;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(p->st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+        a = ev_get(p);
+        cudaEventRecord(a, p->st);
+    }
+    ~ProfScope() {
+        if (!a) return;
+        cudaEvent_t b = ev_get(p);
+        cudaEventRecord(b, p->st);
+        p->evrec.push_back({kind, a, b});
+    }
+};
+
+dme_status alloc_slices(dme_plan_t p, SliceBuf* sb, int rows, int k, int ns) {
     sb->rows = rows;
     sb->k = k;
     sb->Kp = slice_kpad(k);
-    DME_TRY(palloc(p, reinterpret_cast<void**>(&sb->data), slice_buf_bytes(rows, k)));
+    sb->ns = ns;
+    DME_TRY(palloc(p, reinterpret_cast<void**>(&sb->data), slice_buf_bytes(rows, k, ns)));
     DME_TRY(palloc_t(p, &sb->scale, (size_t)rows));
     return make_slice_tmap(*sb, &sb->tmap);
 }
@@ -220,7 +260,10 @@ dme_status split_cong(dme_plan_t p, const double* P, const SliceBuf& G, double* 
                       double b1, const double* D2, double b2, const double* D3, double b3) {
     const int n = p->n;
     cudaStream_t st = p->st;
-    launch_slice_rows_f64(P, n, n, n, p->psl.data, p->psl.Kp, p->psl.scale, st);
+    {
+        ProfScope ps(p, DME_KIND_SLICE);
+        launch_slice_rows_f64(P, n, n, n, p->psl, st);
+    }
     OzParams a;
     std::memset(&a, 0, sizeof(a));
     a.M = n;
@@ -232,8 +275,14 @@ dme_status split_cong(dme_plan_t p, const double* P, const SliceBuf& G, double* 
     a.ldc = n;
     a.Cp = p->U;
     a.status = p->status;
-    DME_TRY(launch_ozaki_gemm(G.tmap, p->psl.tmap, a, st));
-    launch_slice_rows_pair(p->U, n, n, n, p->usl.data, p->usl.Kp, p->usl.scale, st);
+    {
+        ProfScope ps(p, DME_KIND_SPLIT_GEMM);
+        DME_TRY(launch_ozaki_gemm(G.tmap, p->psl.tmap, a, st));
+    }
+    {
+        ProfScope ps(p, DME_KIND_SLICE);
+        launch_slice_rows_pair(p->U, n, n, n, p->usl, st);
+    }
     OzParams b;
     std::memset(&b, 0, sizeof(b));
     b.M = n;
@@ -253,6 +302,7 @@ dme_status split_cong(dme_plan_t p, const double* P, const SliceBuf& G, double* 
     b.D3 = D3;
     b.b3 = b3;
     b.status = p->status;
+    ProfScope ps(p, DME_KIND_SPLIT_GEMM);
     return launch_ozaki_gemm(G.tmap, p->usl.tmap, b, st);
 }
 
@@ -365,8 +415,8 @@ dme_status compute_ew(dme_plan_t p, double tau, int* idx) {
     DME_CUDA_TRY(cudaMemcpyAsync(ent.W, Wm, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
     if (p->split) {
         launch_transpose(ent.E, tmp, n, n, n, n, st);          // tmp = E^T
-        DME_TRY(alloc_slices(p, &ent.Gsl, n, n));
-        launch_slice_rows_f64(tmp, n, n, n, ent.Gsl.data, ent.Gsl.Kp, ent.Gsl.scale, st);
+        DME_TRY(alloc_slices(p, &ent.Gsl, n, n, OZ_SLICES_A));
+        launch_slice_rows_f64(tmp, n, n, n, ent.Gsl, st);
     }
     DME_CUDA_TRY(cudaGetLastError());
     DME_TRY(check_status(p, "dme_expm"));
@@ -488,16 +538,19 @@ dme_status run_op(dme_plan_t p, const Op& o, double* P) {
     switch (o.kind) {
         case OP_CONG: {
             const EWEntry& e = p->ew[o.ew];
+            ProfScope ps(p, DME_KIND_FP64_GEMM);
             return cong64(n, P, e.E, p->X, P, o.wcoef != 0.0 ? e.W : nullptr, o.wcoef,
                           o.qcoef != 0.0 ? p->Q : nullptr, o.qcoef, nullptr, 0.0, st);
         }
         case OP_AXPY:
             launch_axpy_sym(P, p->Q, o.qcoef, n, n, st);
             return DME_OK;
-        case OP_RICC:
+        case OP_RICC: {
+            ProfScope ps(p, DME_KIND_RICCATI);
             launch_riccati(P, p->Bt, n, p->m, o.tau, o.qcoef != 0.0 ? p->Q : nullptr, o.qcoef, p->rwork, p->status,
                            st);
             return DME_OK;
+        }
         case OP_SFLOW:
             return run_sflow(p, P, o.tau, o.rule, o.qcoef);
     }
@@ -538,6 +591,11 @@ void free_plan(dme_plan_t p) {
     if (!p) return;
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->st) cudaStreamSynchronize(p->st);
+    for (auto& r : p->evrec) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : p->evpool) cudaEventDestroy(e);
     for (void* q : p->allocs) cudaFree(q);
     if (p->own_st && p->st) cudaStreamDestroy(p->st);
     delete p;
@@ -550,8 +608,8 @@ dme_status plan_create(const dme_plan_desc* d, const double* A, const double* Qo
         set_error("DME_SPLIT_BF16 supports n <= 4096 (exact slice accumulation over K <= 4096)");
         return DME_EINVAL;
     }
-    if (d->prec == DME_SPLIT_BF16 && d->slices != 0 && d->slices != OZ_SLICES) {
-        set_error("DME_SPLIT_BF16 uses 4 slices per operand");
+    if (d->prec == DME_SPLIT_BF16 && d->slices != 0 && d->slices != OZ_SLICES_B) {
+        set_error("DME_SPLIT_BF16 uses 5 slices for E^T and S and 4 for P (slices = 0 or 4)");
         return DME_EINVAL;
     }
     dme_plan_t p = new (std::nothrow) dme_plan_s();
@@ -611,12 +669,12 @@ dme_status plan_create(const dme_plan_desc* d, const double* A, const double* Qo
         DME_CUDA_TRY(cudaMemcpyAsync(p->S, S, nn * sizeof(double), cudaMemcpyDefault, st));
     }
     if (p->split) {
-        DME_TRY(alloc_slices(p, &p->psl, n, n));
-        DME_TRY(alloc_slices(p, &p->usl, n, n));
+        DME_TRY(alloc_slices(p, &p->psl, n, n, OZ_SLICES_B));
+        DME_TRY(alloc_slices(p, &p->usl, n, n, OZ_SLICES_B));
         DME_TRY(palloc_t(p, &p->U, nn));
         if (gen) {
-            DME_TRY(alloc_slices(p, &p->Ssl, n, n));
-            launch_slice_rows_f64(p->S, n, n, n, p->Ssl.data, p->Ssl.Kp, p->Ssl.scale, st);
+            DME_TRY(alloc_slices(p, &p->Ssl, n, n, OZ_SLICES_A));
+            launch_slice_rows_f64(p->S, n, n, n, p->Ssl, st);
         }
     }
     // ||[[-A^T, Q], [0, A]]||_1 for the scaling of every t
@@ -756,6 +814,35 @@ dme_status dme_sync(dme_plan_t plan) {
 
 int dme_plan_kernels_per_step(dme_plan_t plan) { return plan ? plan->graph_kernels : -1; }
 
+dme_status dme_plan_profile(dme_plan_t plan, int enable) {
+    if (!plan) return set_error("plan is NULL"), DME_EINVAL;
+    plan->prof = enable != 0;
+    return DME_OK;
+}
+
+dme_status dme_plan_timing(dme_plan_t plan, int kind, double* ms, int* launches) {
+    if (!plan || !ms || !launches) return set_error("plan, ms and launches are required"), DME_EINVAL;
+    DME_CUDA_TRY(cudaStreamSynchronize(plan->st));
+    double tot = 0.0;
+    int cnt = 0;
+    std::vector<dme_plan_s::EvRec> keep;
+    for (auto& r : plan->evrec) {
+        if (r.kind != kind) {
+            keep.push_back(r);
+            continue;
+        }
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) tot += t;
+        ++cnt;
+        plan->evpool.push_back(r.a);
+        plan->evpool.push_back(r.b);
+    }
+    plan->evrec.swap(keep);
+    *ms = tot;
+    *launches = cnt;
+    return DME_OK;
+}
+
 dme_status dme_step(dme_plan_t plan, double* P, int nsteps) {
     if (!plan || !P) return set_error("plan and P are required"), DME_EINVAL;
     if (nsteps < 0) return set_error("nsteps must be >= 0"), DME_EINVAL;
@@ -814,13 +901,15 @@ dme_status dme_gemm_split(int M, int N, int K, const double* A, const double* B,
         sa.rows = M;
         sa.k = K;
         sa.Kp = Kp;
+        sa.ns = OZ_SLICES_A;
         sb.rows = N;
         sb.k = K;
         sb.Kp = Kp;
+        sb.ns = OZ_SLICES_B;
         int* status = nullptr;
         dme_status s = DME_OK;
-        if ((s = get(slice_buf_bytes(M, K), reinterpret_cast<void**>(&sa.data))) != DME_OK ||
-            (s = get(slice_buf_bytes(N, K), reinterpret_cast<void**>(&sb.data))) != DME_OK ||
+        if ((s = get(slice_buf_bytes(M, K, sa.ns), reinterpret_cast<void**>(&sa.data))) != DME_OK ||
+            (s = get(slice_buf_bytes(N, K, sb.ns), reinterpret_cast<void**>(&sb.data))) != DME_OK ||
             (s = get(sizeof(float) * M, reinterpret_cast<void**>(&sa.scale))) != DME_OK ||
             (s = get(sizeof(float) * N, reinterpret_cast<void**>(&sb.scale))) != DME_OK ||
             (s = get(sizeof(int), reinterpret_cast<void**>(&status))) != DME_OK ||
@@ -829,8 +918,8 @@ dme_status dme_gemm_split(int M, int N, int K, const double* A, const double* B,
             return s;
         }
         cudaMemsetAsync(status, 0, sizeof(int), st);
-        launch_slice_rows_f64(A, M, K, K, sa.data, Kp, sa.scale, st);
-        launch_slice_rows_f64(B, N, K, K, sb.data, Kp, sb.scale, st);
+        launch_slice_rows_f64(A, M, K, K, sa, st);
+        launch_slice_rows_f64(B, N, K, K, sb, st);
         OzParams o;
         std::memset(&o, 0, sizeof(o));
         o.M = M;

@@ -9,16 +9,17 @@
 
 namespace dme {
 
-constexpr int OZ_SLICES = 4;        // bf16 slices per operand row
+constexpr int OZ_SLICES_A = 5;      // bf16 slices per row of the fixed operand (E^T, S, A of dme_gemm_split)
+constexpr int OZ_SLICES_B = 4;      // bf16 slices per row of the per-step operand (P, U, B)
 constexpr int OZ_MAX_K = 4096;      // exact level-0 accumulation needs K * 64 * 64 <= 2^24
 enum { OZ_OUT_PAIR = 0, OZ_OUT_F64 = 1 };
 
-// Slices of a rows x k operand: planes [OZ_SLICES][rows][Kp] bf16 (Kp = k
-// rounded up to 32, zero padded) and one power-of-two scale per row.
+// Slices of a rows x k operand: planes [ns][rows][Kp] bf16 (Kp = k rounded
+// up to 32, zero padded) and one power-of-two scale per row.
 struct SliceBuf {
     __nv_bfloat16* data = nullptr;
     float* scale = nullptr;
-    int rows = 0, k = 0, Kp = 0;
+    int rows = 0, k = 0, Kp = 0, ns = 0;
     CUtensorMap tmap;
 };
 
@@ -41,12 +42,11 @@ struct OzParams {
 };
 
 int slice_kpad(int k);
-size_t slice_buf_bytes(int rows, int k);
+size_t slice_buf_bytes(int rows, int k, int ns);
 dme_status make_slice_tmap(const SliceBuf& sb, CUtensorMap* out);
-void launch_slice_rows_f64(const double* X, int rows, int cols, int ldx, __nv_bfloat16* out, int Kp, float* scale,
-                           cudaStream_t st);
-void launch_slice_rows_pair(const float2* Xp, int rows, int cols, int ldx, __nv_bfloat16* out, int Kp,
-                            float* scale, cudaStream_t st);
+// Slice the rows of X (rows x cols, leading dimension ldx) into sb (sb.ns = 4 or 5).
+void launch_slice_rows_f64(const double* X, int rows, int cols, int ldx, const SliceBuf& sb, cudaStream_t st);
+void launch_slice_rows_pair(const float2* Xp, int rows, int cols, int ldx, const SliceBuf& sb, cudaStream_t st);
 dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzParams p, cudaStream_t st);
 
 }  // namespace dme
