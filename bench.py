@@ -111,6 +111,22 @@ def dist_init():
     return rank, ws, local, dist
 
 
+def replica_max_ms(ms_local: float, dist, device=None) -> float:
+    """Timed-region length of the slowest rank (every rank runs an independent
+    replica; there is no data-path collective, only this timing reduction)."""
+    if dist is None:
+        return float(ms_local)
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(steps_per_rank: int, ms_max: float, world_size: int) -> float:
+    """Whole-job steps/s: the steps of all replicas over the slowest rank's time."""
+    return world_size * steps_per_rank / (ms_max / 1e3)
+
+
 # ------------------------------------------------------------------ oracle (CPU)
 def oracle_steps(pr, nsteps, E=None, Wm=None):
     """Time nsteps oracle Strang F12F3 steps of the workload; returns (seconds, E, W)."""
@@ -200,11 +216,7 @@ def run_ours(args):
             torch.cuda.nvtx.range_pop()
         barrier()
         torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = replica_max_ms(e0.elapsed_time(e1), dist, dev)
         kps = plan.kernels_per_step
         # dominant kernel: the congruence E^T P E (+ W) applied alone; the library brackets each of
         # its launches with CUDA events on the plan's stream (profiling mode), read back per kind
@@ -243,7 +255,7 @@ def run_ours(args):
 
     head = "split" if "split" in results else "fp64"
     r = results[head]
-    value = ws * r["steps"] / (r["ms"] / 1e3)
+    value = replica_value(r["steps"], r["ms"], ws)
     cong_flops = 3.0 * n ** 3          # P E (2n^3) + upper triangle of E^T X (n^3)
     if head == "fp64":
         achieved = cong_flops / (r["cong_ms"] / 1e3) / 1e12
@@ -279,7 +291,7 @@ def run_ours(args):
         "clocks": r["clocks"],
     }
     for prec, rr in results.items():
-        line[f"{prec}_steps_per_s"] = ws * rr["steps"] / (rr["ms"] / 1e3)
+        line[f"{prec}_steps_per_s"] = replica_value(rr["steps"], rr["ms"], ws)
         line[f"{prec}_plan_s"] = rr["plan_s"]
     line["peaks_source"] = peaks_src
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -295,6 +307,30 @@ def run_ours(args):
     return 0
 
 
+def run_gemm_only(args):
+    """The split-precision tensor-core product alone: C = A B^T, A, B seeded
+    N(0,1) of size N x N (inputs and their slices exceed L2 at N = 4096)."""
+    import torch
+    import paper_1805_08990_gb300 as dme
+    from paper_1805_08990_gb300 import build
+    build.build()
+    N = args.gemm_only
+    g = torch.Generator(device="cpu").manual_seed(0)
+    A = torch.randn(N, N, generator=g, dtype=torch.float64).cuda()
+    B = torch.randn(N, N, generator=g, dtype=torch.float64).cuda()
+    C = torch.empty(N, N, dtype=torch.float64, device="cuda")
+    dme.dme_gemm_split(A, B, C)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.reps):
+        dme.dme_gemm_split(A, B, C)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.reps
+    err = (torch.linalg.norm(C - A @ B.T) / torch.linalg.norm(A @ B.T)).item()
+    print(json.dumps({"gemm_only": N, "ms_per_call_with_slicing_and_alloc": dt * 1e3, "rel_err_vs_fp64": err}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -305,11 +341,15 @@ def main():
     ap.add_argument("--split-steps", type=int, default=64)
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--gemm-only", type=int, default=0, help="profile target: split GEMM of this size alone")
+    ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.gemm_only:
+        return run_gemm_only(args)
     return run_ours(args)
 
 

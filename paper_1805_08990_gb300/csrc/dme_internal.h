@@ -87,9 +87,25 @@ void launch_apply_linv_rows(const double* B, const double* L, double* Bt, int n,
 
 // ---------------------------------------------------------------- Riccati (T3)
 // P <- P - t Z (I + t Bt^T Z)^{-1} Z^T + q * Qadd, Z = P Bt  (Woodbury form
-// of (I + t P Bt Bt^T)^{-1} P).  Work buffers sized by riccati_work_bytes.
+// of (I + t P Bt Bt^T)^{-1} P).  Work buffers sized by riccati_work_doubles.
 size_t riccati_work_doubles(int n, int m);
 void launch_riccati(double* P, const double* Bt, int n, int m, double t, const double* Qadd,
                     double q, double* work, int* status, cudaStream_t st);
+struct RicItem {
+    double* P;
+    const double* Bt;
+    int n, m;
+    double t;
+    const double* Qadd;
+    double q;
+    double* work;
+    int* status;
+};
+RicItem make_ric_item(double* P, const double* Bt, int n, int m, double t, const double* Qadd, double q,
+                      double* work, int* status);
+// Grouped launch over independent problems; more than 8 need `dev_desc`
+// (riccati_desc_bytes() per problem, untouched until the kernels finish).
+dme_status launch_riccati_grouped(const std::vector<RicItem>& items, void* dev_desc, cudaStream_t st);
+size_t riccati_desc_bytes();
 
 }  // namespace dme

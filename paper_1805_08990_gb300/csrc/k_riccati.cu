@@ -7,185 +7,256 @@
 // counterpart of the r x r solve of §2.2).  With M = L L^T and Y = Z L^{-T}:
 //     T3(t) P = P - t Y Y^T.
 // Four kernels: (1) Z = P Bt with per-block partial Gram sums Bt^T Z,
-// (2) M, its Cholesky and L^{-1} (one warp, FP64, deterministic reduction
-// order), (3) Y = Z L^{-T}, (4) the rank-m update P <- P - t Y Y^T (+ q Q).
+// (2) M from the partials (deterministic reduction order), its Cholesky and
+// L^{-1} (FP64), (3) Y = Z L^{-T}, (4) the rank-m update P <- P - t Y Y^T (+ q Q).
+// Each kernel takes a batch of independent problems (grouped launch): the
+// blocks of every problem are laid end to end and each block finds its
+// problem by a binary search over the per-problem block offsets, so a
+// problem is computed identically alone or in a batch.
 // Everything is FP64.  (1) and (4) stream P once each with coalesced,
 // 16-byte vector loads; the row dot-products of (1) are warp reductions.
 #include "dme_internal.h"
 
 #include <algorithm>
+#include <cstring>
+#include <vector>
 
 namespace dme {
 
-constexpr int RZ_ROWS = 32;     // rows of P per block in kernel (1)
+constexpr int RZ_ROWS = 8;      // rows of P per block in kernel (1): one per warp
 constexpr int RZ_MB = 8;        // columns of Bt per pass
+constexpr int RU_TILE = 64;     // update tile
 
-static int rz_blocks(int n) { return (n + RZ_ROWS - 1) / RZ_ROWS; }
+__host__ __device__ __forceinline__ int rz_blocks(int n) { return (n + RZ_ROWS - 1) / RZ_ROWS; }
 
 size_t riccati_work_doubles(int n, int m) {
     // Z (n m) | Y (n m) | Gpart (blocks m m) | Linv (m m)
     return (size_t)2 * n * m + (size_t)rz_blocks(n) * m * m + (size_t)m * m + 8;
 }
 
-// (1) Z[r][c] = sum_k P[r][k] Bt[k][c] for the block's 32 rows, columns
-// c0 .. c0+MB-1; Bt chunks are staged in shared memory.
-__global__ void __launch_bounds__(256) riccati_z_kernel(const double* __restrict__ P, const double* __restrict__ Bt,
-                                                        double* __restrict__ Z, int n, int m, int c0) {
-    constexpr int KC = 256;
-    __shared__ double sB[KC][RZ_MB];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rbase = blockIdx.x * RZ_ROWS + warp * 4;
-    const int mb = min(RZ_MB, m - c0);
-    double acc[4][RZ_MB];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < RZ_MB; ++c) acc[r][c] = 0.0;
+// One problem of a (possibly grouped) Riccati update; the block-prefix fields
+// map a global block index of each kernel to (problem, local block).
+struct RicDesc {
+    double* P;
+    const double* Bt;
+    double* Z;
+    double* Y;
+    double* Gpart;
+    double* Linv;
+    const double* Qadd;
+    double t, q;
+    int n, m;
+    int* status;
+    int sz, sy, su;     // first block of this problem in the z, y and update grids
+};
 
-    for (int k0 = 0; k0 < n; k0 += KC) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < KC * RZ_MB; e += blockDim.x) {
-            int k = e / RZ_MB, c = e % RZ_MB;
-            sB[k][c] = (k0 + k < n && c < mb) ? Bt[(size_t)(k0 + k) * m + c0 + c] : 0.0;
-        }
-        __syncthreads();
-        const int kend = min(KC, n - k0);
+constexpr int kRicLocal = 8;
+struct RicBatch {
+    RicDesc local[kRicLocal];
+    const RicDesc* dev;     // used instead of `local` when nd > kRicLocal
+    int nd;
+};
+
+__device__ __forceinline__ const RicDesc* ric_descs(const RicBatch& b) { return b.dev ? b.dev : b.local; }
+
+// largest i with start(i) <= blk
+template <int FIELD>
+__device__ __forceinline__ int ric_find(const RicDesc* d, int nd, int blk) {
+    int lo = 0, hi = nd - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int st = FIELD == 0 ? d[mid].sz : (FIELD == 1 ? d[mid].sy : d[mid].su);
+        if (st <= blk) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// (1) Z[r][c] = sum_k P[r][k] Bt[k][c] for the block's 8 rows (one per warp),
+// in passes of 8 columns; Bt chunks staged in shared memory; then the block's
+// partial Gram sums Gpart[b][i][c] = sum_{r in block} Bt[r][i] Z[r][c] in a
+// fixed order (deterministic, no atomics).
+__global__ void __launch_bounds__(256) riccati_z_kernel(const __grid_constant__ RicBatch batch) {
+    constexpr int KC = 512;
+    __shared__ double sB[KC][RZ_MB];
+    __shared__ double sZ[RZ_ROWS][RZ_MB];
+    const RicDesc* ds = ric_descs(batch);
+    const int ip = ric_find<0>(ds, batch.nd, blockIdx.x);
+    const RicDesc& d = ds[ip];
+    const int lb = blockIdx.x - d.sz;
+    const int n = d.n, m = d.m;
+    const double* __restrict__ P = d.P;
+    const double* __restrict__ Bt = d.Bt;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = lb * RZ_ROWS + warp;
+    const bool vec = (n % 2) == 0;
+    for (int c0 = 0; c0 < m; c0 += RZ_MB) {
+        const int mb = min(RZ_MB, m - c0);
+        double acc[RZ_MB];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int row = rbase + r;
+        for (int c = 0; c < RZ_MB; ++c) acc[c] = 0.0;
+        for (int k0 = 0; k0 < n; k0 += KC) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < KC * RZ_MB; e += blockDim.x) {
+                int k = e / RZ_MB, c = e % RZ_MB;
+                sB[k][c] = (k0 + k < n && c < mb) ? Bt[(size_t)(k0 + k) * m + c0 + c] : 0.0;
+            }
+            __syncthreads();
             if (row >= n) continue;
+            const int kend = min(KC, n - k0);
             const double* prow = P + (size_t)row * n + k0;
             // 2 consecutive doubles per lane per iteration: a warp covers 64 columns
             for (int k = 2 * lane; k < kend; k += 64) {
-                double p0, p1;
-                if (k + 1 < kend && (((size_t)(prow + k)) & 15) == 0) {
+                double p0, p1 = 0.0;
+                if (vec && k + 1 < kend) {
                     double2 v = *reinterpret_cast<const double2*>(prow + k);
                     p0 = v.x;
                     p1 = v.y;
                 } else {
                     p0 = prow[k];
-                    p1 = (k + 1 < kend) ? prow[k + 1] : 0.0;
+                    if (k + 1 < kend) p1 = prow[k + 1];
                 }
+                // k is even and KC is even, so k + 1 < KC; past the row end p1 = 0 and sB is zero-filled
 #pragma unroll
-                for (int c = 0; c < RZ_MB; ++c) {
-                    acc[r][c] = fma(p0, sB[k][c], acc[r][c]);
-                    if (k + 1 < kend) acc[r][c] = fma(p1, sB[k + 1][c], acc[r][c]);
-                }
+                for (int c = 0; c < RZ_MB; ++c) acc[c] = fma(p1, sB[k + 1][c], fma(p0, sB[k][c], acc[c]));
             }
         }
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
 #pragma unroll
         for (int c = 0; c < RZ_MB; ++c) {
-            double v = acc[r][c];
+            double v = acc[c];
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            acc[r][c] = v;
+            acc[c] = v;
         }
-        const int row = rbase + r;
+        __syncthreads();
+        if (lane == 0) {
+#pragma unroll
+            for (int c = 0; c < RZ_MB; ++c) sZ[warp][c] = (row < n) ? acc[c] : 0.0;
+        }
         if (row < n && lane < mb) {
             double v = 0.0;
 #pragma unroll
             for (int c = 0; c < RZ_MB; ++c)
-                if (c == lane) v = acc[r][c];
-            Z[(size_t)row * m + c0 + lane] = v;
+                if (c == lane) v = acc[c];
+            d.Z[(size_t)row * m + c0 + lane] = v;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < m * mb; e += blockDim.x) {
+            const int i = e / mb, jj = e % mb;
+            double sacc = 0.0;
+            for (int r = 0; r < RZ_ROWS; ++r) {
+                const int rr = lb * RZ_ROWS + r;
+                if (rr < n) sacc = fma(Bt[(size_t)rr * m + i], sZ[r][jj], sacc);
+            }
+            d.Gpart[(size_t)lb * m * m + (size_t)i * m + c0 + jj] = sacc;
         }
     }
 }
 
-// (1b) Gpart[b][i][j] = sum over the block's rows r of Bt[r][i] Z[r][j], fixed order.
-__global__ void riccati_gram_part_kernel(const double* __restrict__ Bt, const double* __restrict__ Z,
-                                         double* __restrict__ Gpart, int n, int m) {
-    const int b = blockIdx.x;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        int i = e / m, j = e % m;
-        double s = 0.0;
-        for (int r = b * RZ_ROWS; r < min(n, (b + 1) * RZ_ROWS); ++r) s = fma(Bt[(size_t)r * m + i], Z[(size_t)r * m + j], s);
-        Gpart[(size_t)b * m * m + e] = s;
-    }
-}
-
-// (2) M = I + t sym(sum_b Gpart[b]); M = L L^T; Linv = L^{-1}.  One warp.
-__global__ void riccati_small_kernel(const double* __restrict__ Gpart, int nblocks, int m, double t,
-                                     double* __restrict__ Linv, int* status) {
-    __shared__ double M[32][33];
+// (2) M = I + t sym(sum_b Gpart[b]); M = L L^T; Linv = L^{-1}.  One block per
+// problem.  The sum over blocks is a fixed two-level order (strided partial
+// sums, then a tree), so the result does not depend on scheduling.
+__global__ void __launch_bounds__(1024) riccati_small_kernel(const __grid_constant__ RicBatch batch) {
+    __shared__ double red[1024];
     __shared__ double L[32][33];
-    const int lane = threadIdx.x;
-    for (int e = lane; e < m * m; e += 32) {
-        int i = e / m, j = e % m;
-        double s = 0.0;
-        for (int b = 0; b < nblocks; ++b) s += Gpart[(size_t)b * m * m + e];
-        M[i][j] = s;
+    const RicDesc& d = ric_descs(batch)[blockIdx.x];
+    const int m = d.m;
+    const int nblocks = rz_blocks(d.n);
+    const double t = d.t;
+    const int E = m * m;
+    const int G = max(1, 1024 / E);
+    const int tid = threadIdx.x;
+    const int e = tid % E, g = tid / E;
+    double sacc = 0.0;
+    if (g < G)
+        for (int b = g; b < nblocks; b += G) sacc += d.Gpart[(size_t)b * E + e];
+    red[tid] = (g < G) ? sacc : 0.0;
+    __syncthreads();
+    // tree over groups: group g adds group g + half (fixed order)
+    for (int half = 1; half < G; half <<= 1) {
+        if (g < G && (g % (2 * half)) == 0 && g + half < G) red[tid] += red[tid + half * E];
+        __syncthreads();
+    }
+    if (tid < E) L[tid / m][tid % m] = red[tid];
+    __syncthreads();
+    if (tid >= 32) return;
+    const int lane = tid;
+    // symmetrise and add the identity: M = I + t (G + G^T)/2
+    double Mv[32];
+    for (int e2 = lane; e2 < E; e2 += 32) {
+        const int i = e2 / m, j = e2 % m;
+        Mv[e2 / 32] = (i == j ? 1.0 : 0.0) + t * 0.5 * (L[i][j] + L[j][i]);
     }
     __syncwarp();
-    for (int e = lane; e < m * m; e += 32) {
-        int i = e / m, j = e % m;
-        L[i][j] = (i == j ? 1.0 : 0.0) + t * 0.5 * (M[i][j] + M[j][i]);
-    }
+    for (int e2 = lane; e2 < E; e2 += 32) L[e2 / m][e2 % m] = Mv[e2 / 32];
     __syncwarp();
     // Cholesky in place (lower)
     for (int j = 0; j < m; ++j) {
-        double d = L[j][j];
-        for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
-        if (!(d > 0.0)) {
-            if (lane == 0) atomicOr(status, DEV_NOTSPD);
+        double dj = L[j][j];
+        for (int k = 0; k < j; ++k) dj -= L[j][k] * L[j][k];
+        if (!(dj > 0.0)) {
+            if (lane == 0) atomicOr(d.status, DEV_NOTSPD);
             return;
         }
-        d = sqrt(d);
+        dj = sqrt(dj);
         __syncwarp();
         for (int i = j + 1 + lane; i < m; i += 32) {
-            double s = L[i][j];
-            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
-            L[i][j] = s / d;
+            double s2 = L[i][j];
+            for (int k = 0; k < j; ++k) s2 -= L[i][k] * L[j][k];
+            L[i][j] = s2 / dj;
         }
         __syncwarp();
-        if (lane == 0) L[j][j] = d;
+        if (lane == 0) L[j][j] = dj;
         __syncwarp();
     }
     // Linv column by column (forward substitution on e_c); lane c owns column c
     for (int c = lane; c < m; c += 32) {
         double x[32];
         for (int r = 0; r < m; ++r) {
-            double s = (r == c) ? 1.0 : 0.0;
-            for (int k = 0; k < r; ++k) s -= L[r][k] * x[k];
-            x[r] = (r < c) ? 0.0 : s / L[r][r];
+            double s2 = (r == c) ? 1.0 : 0.0;
+            for (int k = 0; k < r; ++k) s2 -= L[r][k] * x[k];
+            x[r] = (r < c) ? 0.0 : s2 / L[r][r];
         }
-        for (int r = 0; r < m; ++r) Linv[r * m + c] = x[r];
+        for (int r = 0; r < m; ++r) d.Linv[r * m + c] = x[r];
     }
 }
 
 // (3) Y[i][r] = sum_{c <= r} Linv[r][c] Z[i][c]   (Y = Z L^{-T}).
-__global__ void riccati_y_kernel(const double* __restrict__ Z, const double* __restrict__ Linv,
-                                 double* __restrict__ Y, int n, int m, const int* status) {
-    if (*status & DEV_NOTSPD) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+__global__ void riccati_y_kernel(const __grid_constant__ RicBatch batch) {
+    const RicDesc* ds = ric_descs(batch);
+    const RicDesc& d = ds[ric_find<1>(ds, batch.nd, blockIdx.x)];
+    if (*d.status & DEV_NOTSPD) return;
+    const int i = (blockIdx.x - d.sy) * blockDim.x + threadIdx.x;
+    const int m = d.m;
+    if (i >= d.n) return;
     for (int r = 0; r < m; ++r) {
         double s = 0.0;
-        for (int c = 0; c <= r; ++c) s = fma(Linv[r * m + c], Z[(size_t)i * m + c], s);
-        Y[(size_t)i * m + r] = s;
+        for (int c = 0; c <= r; ++c) s = fma(d.Linv[r * m + c], d.Z[(size_t)i * m + c], s);
+        d.Y[(size_t)i * m + r] = s;
     }
 }
 
 // (4) P[i][j] <- P[i][j] - t sum_r Y[i][r] Y[j][r] (+ q Q[i][j]).  The sum is
 // taken in the same order for (i, j) and (j, i), so a symmetric P stays
 // exactly symmetric.  64 x 64 tiles, 256 threads, Y rows staged in shared memory.
-__global__ void __launch_bounds__(256) riccati_update_kernel(double* __restrict__ P, const double* __restrict__ Y,
-                                                             int n, int m, double t, const double* __restrict__ Qadd,
-                                                             double q, const int* status) {
-    if (*status & DEV_NOTSPD) return;
-    __shared__ double Yi[64][33];
-    __shared__ double Yj[64][33];
-    const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
-    for (int e = threadIdx.x; e < 64 * m; e += blockDim.x) {
+__global__ void __launch_bounds__(256) riccati_update_kernel(const __grid_constant__ RicBatch batch) {
+    const RicDesc* ds = ric_descs(batch);
+    const RicDesc& d = ds[ric_find<2>(ds, batch.nd, blockIdx.x)];
+    if (*d.status & DEV_NOTSPD) return;
+    __shared__ double Yi[RU_TILE][33];
+    __shared__ double Yj[RU_TILE][33];
+    const int n = d.n, m = d.m;
+    const int tn = (n + RU_TILE - 1) / RU_TILE;
+    const int lt = blockIdx.x - d.su;
+    const int i0 = (lt / tn) * RU_TILE, j0 = (lt % tn) * RU_TILE;
+    for (int e = threadIdx.x; e < RU_TILE * m; e += blockDim.x) {
         int r = e / m, c = e % m;
-        Yi[r][c] = (i0 + r < n) ? Y[(size_t)(i0 + r) * m + c] : 0.0;
-        Yj[r][c] = (j0 + r < n) ? Y[(size_t)(j0 + r) * m + c] : 0.0;
+        Yi[r][c] = (i0 + r < n) ? d.Y[(size_t)(i0 + r) * m + c] : 0.0;
+        Yj[r][c] = (j0 + r < n) ? d.Y[(size_t)(j0 + r) * m + c] : 0.0;
     }
     __syncthreads();
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
-    for (int di = ty; di < 64; di += 8) {
+    for (int di = ty; di < RU_TILE; di += 8) {
         const int i = i0 + di;
         if (i >= n) break;
 #pragma unroll
@@ -195,26 +266,84 @@ __global__ void __launch_bounds__(256) riccati_update_kernel(double* __restrict_
             double s = 0.0;
             for (int c = 0; c < m; ++c) s = fma(Yi[di][c], Yj[dj][c], s);
             const size_t off = (size_t)i * n + j;
-            double v = P[off] - t * s;
-            if (Qadd) v += q * Qadd[off];
-            P[off] = v;
+            double v = d.P[off] - d.t * s;
+            if (d.Qadd) v += d.q * d.Qadd[off];
+            d.P[off] = v;
         }
     }
 }
 
+RicItem make_ric_item(double* P, const double* Bt, int n, int m, double t, const double* Qadd, double q,
+                      double* work, int* status) {
+    RicItem it;
+    it.P = P;
+    it.Bt = Bt;
+    it.n = n;
+    it.m = m;
+    it.t = t;
+    it.Qadd = Qadd;
+    it.q = q;
+    it.work = work;
+    it.status = status;
+    return it;
+}
+
+dme_status launch_riccati_grouped(const std::vector<RicItem>& items, void* dev_desc, cudaStream_t st) {
+    if (items.empty()) return DME_OK;
+    std::vector<RicDesc> ds(items.size());
+    int sz = 0, sy = 0, su = 0;
+    for (size_t k = 0; k < items.size(); ++k) {
+        const RicItem& it = items[k];
+        RicDesc& d = ds[k];
+        const int n = it.n, m = it.m;
+        d.P = it.P;
+        d.Bt = it.Bt;
+        d.Z = it.work;
+        d.Y = d.Z + (size_t)n * m;
+        d.Gpart = d.Y + (size_t)n * m;
+        d.Linv = d.Gpart + (size_t)rz_blocks(n) * m * m;
+        d.Qadd = it.Qadd;
+        d.t = it.t;
+        d.q = it.q;
+        d.n = n;
+        d.m = m;
+        d.status = it.status;
+        d.sz = sz;
+        d.sy = sy;
+        d.su = su;
+        sz += rz_blocks(n);
+        sy += (n + 127) / 128;
+        const int tn = (n + RU_TILE - 1) / RU_TILE;
+        su += tn * tn;
+    }
+    RicBatch b;
+    std::memset(&b, 0, sizeof(b));
+    b.nd = (int)ds.size();
+    if (ds.size() <= (size_t)kRicLocal) {
+        for (size_t k = 0; k < ds.size(); ++k) b.local[k] = ds[k];
+        b.dev = nullptr;
+    } else {
+        if (!dev_desc) {
+            set_error("grouped Riccati: more than 8 problems need a device descriptor buffer");
+            return DME_EINVAL;
+        }
+        DME_CUDA_TRY(cudaMemcpyAsync(dev_desc, ds.data(), ds.size() * sizeof(RicDesc), cudaMemcpyHostToDevice, st));
+        b.dev = reinterpret_cast<const RicDesc*>(dev_desc);
+    }
+    riccati_z_kernel<<<sz, 256, 0, st>>>(b);
+    riccati_small_kernel<<<b.nd, 1024, 0, st>>>(b);
+    riccati_y_kernel<<<sy, 128, 0, st>>>(b);
+    riccati_update_kernel<<<su, 256, 0, st>>>(b);
+    DME_CUDA_TRY(cudaGetLastError());
+    return DME_OK;
+}
+
+size_t riccati_desc_bytes() { return sizeof(RicDesc); }
+
 void launch_riccati(double* P, const double* Bt, int n, int m, double t, const double* Qadd, double q,
                     double* work, int* status, cudaStream_t st) {
-    double* Z = work;
-    double* Y = Z + (size_t)n * m;
-    double* Gpart = Y + (size_t)n * m;
-    const int nb = rz_blocks(n);
-    double* Linv = Gpart + (size_t)nb * m * m;
-    for (int c0 = 0; c0 < m; c0 += RZ_MB) riccati_z_kernel<<<nb, 256, 0, st>>>(P, Bt, Z, n, m, c0);
-    riccati_gram_part_kernel<<<nb, 64, 0, st>>>(Bt, Z, Gpart, n, m);
-    riccati_small_kernel<<<1, 32, 0, st>>>(Gpart, nb, m, t, Linv, status);
-    riccati_y_kernel<<<(n + 127) / 128, 128, 0, st>>>(Z, Linv, Y, n, m, status);
-    dim3 g((n + 63) / 64, (n + 63) / 64);
-    riccati_update_kernel<<<g, 256, 0, st>>>(P, Y, n, m, t, Qadd, q, status);
+    std::vector<RicItem> v{make_ric_item(P, Bt, n, m, t, Qadd, q, work, status)};
+    launch_riccati_grouped(v, nullptr, st);
 }
 
 }  // namespace dme

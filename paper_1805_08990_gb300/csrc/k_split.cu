@@ -78,11 +78,42 @@ __device__ __forceinline__ long long fixed41_f(float f, int E) {
     return (b >> 31) ? -v : v;
 }
 
+// Load entries k .. k+3 of a row (zeros past `cols`); vector loads when the
+// row start is 16-byte aligned and the four entries are in range.
+template <bool PAIR>
+__device__ __forceinline__ void load4(const double* X, const float2* Xp, size_t base, int k, int cols, bool vec,
+                                      double (&d)[4], float2 (&f)[4]) {
+    if (vec && k + 3 < cols) {
+        if (PAIR) {
+            const float4 a = *reinterpret_cast<const float4*>(Xp + base + k);
+            const float4 b = *reinterpret_cast<const float4*>(Xp + base + k + 2);
+            f[0] = make_float2(a.x, a.y);
+            f[1] = make_float2(a.z, a.w);
+            f[2] = make_float2(b.x, b.y);
+            f[3] = make_float2(b.z, b.w);
+        } else {
+            const double2 a = *reinterpret_cast<const double2*>(X + base + k);
+            const double2 b = *reinterpret_cast<const double2*>(X + base + k + 2);
+            d[0] = a.x;
+            d[1] = a.y;
+            d[2] = b.x;
+            d[3] = b.y;
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (PAIR) f[u] = (k + u < cols) ? Xp[base + k + u] : make_float2(0.f, 0.f);
+            else d[u] = (k + u < cols) ? X[base + k + u] : 0.0;
+        }
+    }
+}
+
 // One warp per row: pass 1 finds the row's max exponent, pass 2 writes the
 // NS slices (zero beyond `cols`, up to Kp) and the row scale 2^E.  The value
 // is first rounded to a 41-bit fixed-point integer V = round(x 2^(41-E)); the
 // slices are the base-2^7 digits of V with round-to-nearest:
 // d_t = round(r_t / 2^(35-7t)), r_{t+1} = r_t - d_t 2^(35-7t).
+// Each lane handles 4 consecutive entries (32-byte loads, 8-byte stores per plane).
 template <bool PAIR, int NS>
 __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restrict__ X, const float2* __restrict__ Xp,
                                                          int rows, int cols, int ldx, __nv_bfloat16* __restrict__ out,
@@ -90,21 +121,28 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restric
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = blockIdx.x * 8 + warp;
     if (row >= rows) return;
+    const size_t base = (size_t)row * ldx;
+    const bool vec = (ldx % 2) == 0;
+    double d[4];
+    float2 f[4];
     // pass 1: largest magnitude (as exponent)
     int emax = -100000;
-    for (int k = lane; k < cols; k += 32) {
-        int e;
-        if (PAIR) {
-            const float2 v = Xp[(size_t)row * ldx + k];
-            const unsigned int b = __float_as_uint(v.x) & 0x7FFFFFFFu;
-            const int ef = (int)(b >> 23);
-            e = (b == 0 || ef == 0) ? -100000 : ef - 127;
-        } else {
-            const unsigned long long b = (unsigned long long)__double_as_longlong(X[(size_t)row * ldx + k]);
-            const int ed = (int)((b >> 52) & 0x7FF);
-            e = (ed == 0) ? -100000 : ed - 1023;
+    for (int k = 4 * lane; k < cols; k += 128) {
+        load4<PAIR>(X, Xp, base, k, cols, vec, d, f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int e;
+            if (PAIR) {
+                const unsigned int b = __float_as_uint(f[u].x) & 0x7FFFFFFFu;
+                const int ef = (int)(b >> 23);
+                e = (b == 0 || ef == 0) ? -100000 : ef - 127;
+            } else {
+                const unsigned long long b = (unsigned long long)__double_as_longlong(d[u]);
+                const int ed = (int)((b >> 52) & 0x7FF);
+                e = (ed == 0) ? -100000 : ed - 1023;
+            }
+            emax = max(emax, e);
         }
-        emax = max(emax, e);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
@@ -114,23 +152,26 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restric
     const int E = emax + 1;                       // |x| < 2^E for every entry of the row
     if (lane == 0) scale[row] = zero_row ? 0.0f : ldexpf(1.0f, E);
     const size_t plane = (size_t)rows * Kp;
-    for (int k = lane; k < Kp; k += 32) {
-        long long V = 0;
+    for (int k = 4 * lane; k < Kp; k += 128) {
+        long long V[4] = {0, 0, 0, 0};
         if (!zero_row && k < cols) {
-            if (PAIR) {
-                const float2 v = Xp[(size_t)row * ldx + k];
-                V = fixed41_f(v.x, E) + fixed41_f(v.y, E);
-            } else {
-                V = fixed41_d(X[(size_t)row * ldx + k], E);
-            }
+            load4<PAIR>(X, Xp, base, k, cols, vec, d, f);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                V[u] = PAIR ? fixed41_f(f[u].x, E) + fixed41_f(f[u].y, E) : fixed41_d(d[u], E);
         }
         const size_t o = (size_t)row * Kp + k;
 #pragma unroll
         for (int t = 0; t < NS; ++t) {
             const int sh = 35 - 7 * t;
-            const long long d = (V + (1ll << (sh - 1))) >> sh;
-            V -= d << sh;
-            out[t * plane + o] = __float2bfloat16_rn(ldexpf((float)d, -6 - 7 * t));
+            __nv_bfloat16 q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long dd = (V[u] + (1ll << (sh - 1))) >> sh;
+                V[u] -= dd << sh;
+                q[u] = __float2bfloat16_rn(ldexpf((float)dd, -6 - 7 * t));
+            }
+            *reinterpret_cast<uint2*>(out + t * plane + o) = *reinterpret_cast<const uint2*>(q);
         }
     }
 }
@@ -152,6 +193,12 @@ void launch_slice_rows_pair(const float2* Xp, int rows, int cols, int ldx, const
 }
 
 // ============================================================== tcgen05 GEMM
+// Tile order.  Rectangular grids run in groups of OZ_GROUP tile rows, column
+// by column inside a group, so the CTAs resident at one time touch about
+// OZ_GROUP row tiles of A and 152/OZ_GROUP column tiles of B, which stay in L2.
+// Triangle grids enumerate (tm <= tn) row by row.
+constexpr int OZ_GROUP = 8;
+
 __device__ __forceinline__ void oz_tile_coords(const OzParams& p, int& tm, int& tn) {
     const int t = blockIdx.x;
     if (p.tri) {
@@ -163,9 +210,28 @@ __device__ __forceinline__ void oz_tile_coords(const OzParams& p, int& tm, int& 
         tm = r;
         tn = r + rem;
     } else {
-        tm = t / p.tiles_n;
-        tn = t % p.tiles_n;
+        const int tiles_m = (p.M + 127) / 128;
+        const int per_group = OZ_GROUP * p.tiles_n;
+        const int g = t / per_group;
+        const int first = g * OZ_GROUP;
+        const int rows = min(OZ_GROUP, tiles_m - first);
+        const int r = t - g * per_group;
+        tm = first + r % rows;
+        tn = r / rows;
     }
+}
+
+// Exact float -> double conversion of a normal or zero float by bit moves
+// (subnormal floats are flushed to zero; the epilogue never produces them
+// for in-range data).
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned int b = __float_as_uint(f);
+    const unsigned int e = (b >> 23) & 0xFFu;
+    if (e == 0) return 0.0;
+    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+    const unsigned long long ed = (unsigned long long)(e - 127 + 1023) << 52;
+    const unsigned long long m = (unsigned long long)(b & 0x7FFFFFu) << 29;
+    return __longlong_as_double((long long)(sign | ed | m));
 }
 
 __global__ void __launch_bounds__(192, 1) ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
@@ -299,7 +365,8 @@ __global__ void __launch_bounds__(192, 1) ozaki_gemm_kernel(const __grid_constan
                     } else {
                         if (p.tri && i > j) continue;
                         const size_t off = (size_t)i * p.ldc + j;
-                        double v = p.alpha * ((double)(sh * s) + (double)(sl * s));
+                        double v = f2d_bits(sh * s) + f2d_bits(sl * s);
+                        if (p.alpha != 1.0) v *= p.alpha;
                         if (p.D1) v += p.b1 * p.D1[off];
                         if (p.D2) v += p.b2 * p.D2[off];
                         if (p.D3) v += p.b3 * p.D3[off];

@@ -15,8 +15,7 @@
 //    solves in FP64;
 //  * squaring the block matrix is the semigroup law of T12 (Eq. full):
 //    E_{2t} = E_t^2, W_{2t} = W_t + E_t^T W_t E_t.
-#include "dme_internal.h"
-#include "split_internal.h"
+#include "plan_internal.h"
 
 #include <algorithm>
 #include <cmath>
@@ -47,69 +46,12 @@ static void pade13(double c[14]) {
 
 using namespace dme;
 
-struct EWEntry {
-    double tau;
-    double* E;
-    double* W;
-    int s;
-    SliceBuf Gsl;   // split path: slices of E^T (rows of E^T = columns of E)
-};
-
-enum OpKind { OP_CONG = 0, OP_AXPY = 1, OP_RICC = 2, OP_SFLOW = 3 };
-
-struct Op {
-    int kind;
-    double tau;
-    int ew;        // OP_CONG: index of (E, W)
-    double wcoef;  // OP_CONG: coefficient of W (1 for T12, 0 for T1)
-    double qcoef;  // fused T2: + qcoef Q
-    int rule;      // OP_SFLOW: DME_T4_MIDPOINT / DME_T4_EULER
-};
-
-struct dme_plan_s {
-    dme_plan_desc d;
-    int n = 0, m = 0;
-    cudaStream_t st = nullptr;
-    bool own_st = false;
-    double* A = nullptr;
-    double* Q = nullptr;
-    double* Bt = nullptr;
-    double* S = nullptr;
-    double* X = nullptr;       // n x n congruence intermediate
-    double* Xs = nullptr;      // n x n S-flow intermediates
-    double* Y1 = nullptr;
-    double* state = nullptr;   // n x n, dme_solve working state
-    double* rwork = nullptr;   // Riccati work
-    double* small = nullptr;   // 2n colsums + scalars
-    int* status = nullptr;
-    double normM = 0.0;
-    std::vector<EWEntry> ew;
-    std::vector<Op> ops;
-    double ops_h = -1.0;
-    std::vector<void*> allocs;
-    size_t bytes = 0;
-    cudaGraphExec_t gexec = nullptr;
-    double* gP = nullptr;
-    int graph_kernels = -1;
-    bool split = false;
-    SliceBuf psl, usl, Ssl;    // split path: slices of P, of U = G P, and of S
-    float2* U = nullptr;       // split path: G P as normalised (hi, lo) pairs
-    // profiling: CUDA-event pairs around launches made outside graph capture
-    bool prof = false;
-    std::vector<cudaEvent_t> evpool;
-    struct EvRec {
-        int kind;
-        cudaEvent_t a, b;
-    };
-    std::vector<EvRec> evrec;
-};
-
 namespace {
 
 dme_status palloc(dme_plan_t p, void** out, size_t bytes) {
     *out = nullptr;
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(out, bytes);
+    cudaError_t e = cudaMallocAsync(out, bytes, p->st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
@@ -125,14 +67,16 @@ dme_status palloc_t(dme_plan_t p, T** out, size_t count) {
     return palloc(p, reinterpret_cast<void**>(out), count * sizeof(T));
 }
 
-// Temporary device buffers released at scope exit (plan-time only).
+// Temporary device buffers released at scope exit (plan-time only), stream ordered.
 struct TmpPool {
+    cudaStream_t st;
     std::vector<void*> v;
+    explicit TmpPool(cudaStream_t s) : st(s) {}
     ~TmpPool() {
-        for (void* q : v) cudaFree(q);
+        for (void* q : v) cudaFreeAsync(q, st);
     }
     dme_status get(double** out, size_t count) {
-        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(out), std::max<size_t>(count, 2) * sizeof(double));
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(out), std::max<size_t>(count, 2) * sizeof(double), st);
         if (e != cudaSuccess) {
             cudaGetLastError();
             set_error(std::string("cudaMalloc (temporary): ") + cudaGetErrorString(e));
@@ -322,7 +266,7 @@ dme_status compute_ew(dme_plan_t p, double tau, int* idx) {
     if (nrm > kTheta13) s = (int)std::ceil(std::log2(nrm / kTheta13));
     const double sc = std::ldexp(tau, -s);
 
-    TmpPool tp;
+    TmpPool tp(st);
     double *X22, *X12, *A22, *A12, *B22, *B12, *C22, *C12, *Y22, *Y12, *T22, *T12, *U22, *U12, *V22, *V12;
     double *LUq, *LUp, *R22, *R12;
     DME_TRY(tp.get(&X22, nn));
@@ -341,9 +285,9 @@ dme_status compute_ew(dme_plan_t p, double tau, int* idx) {
     DME_TRY(tp.get(&U12, nn));
     DME_TRY(tp.get(&V22, nn));
     DME_TRY(tp.get(&V12, nn));
-    int* piv = nullptr;
-    DME_CUDA_TRY(cudaMalloc(&piv, sizeof(int) * std::max(n, 1)));
-    std::unique_ptr<int, void (*)(int*)> piv_guard(piv, [](int* q) { cudaFree(q); });
+    double* pivd = nullptr;
+    DME_TRY(tp.get(&pivd, (size_t)std::max(n, 1)));
+    int* piv = reinterpret_cast<int*>(pivd);
 
     // X = sc M:  X22 = sc A, X12 = sc Q, X11 = -X22^T (implicit)
     launch_lincomb(X22, n, n, p->A, sc, nullptr, 0, nullptr, 0, 0.0, st);
@@ -447,9 +391,11 @@ int t4_rule_of(const dme_plan_desc& d) {
     return d.comp == DME_STRANG ? DME_T4_MIDPOINT : DME_T4_EULER;
 }
 
+}  // namespace
+
 // Compile one step into ops.  T2 (P + tQ) is fused into the epilogue of the
 // op before it in the same step when there is one, else it is a standalone axpy.
-dme_status build_ops(dme_plan_t p, double h) {
+dme_status dme::build_ops(dme_plan_t p, double h) {
     if (p->ops_h == h) return DME_OK;
     std::vector<Op> ops;
     for (auto& ft : step_sequence(p->d, h)) {
@@ -500,6 +446,8 @@ dme_status build_ops(dme_plan_t p, double h) {
     return DME_OK;
 }
 
+namespace {
+
 dme_status run_sflow(dme_plan_t p, double* P, double tau, int rule, double qcoef) {
     const int n = p->n;
     cudaStream_t st = p->st;
@@ -526,7 +474,9 @@ dme_status run_sflow_split(dme_plan_t p, double* P, double tau, int rule, double
     return split_cong(p, p->Xs, p->Ssl, P, 0.5 * tau * tau, P, 1.0, p->Xs, tau, Qd, qcoef);     // + t^2/2 S Xs S^T
 }
 
-dme_status run_op(dme_plan_t p, const Op& o, double* P) {
+}  // namespace
+
+dme_status dme::run_op(dme_plan_t p, const Op& o, double* P) {
     const int n = p->n;
     cudaStream_t st = p->st;
     if (p->split && o.kind == OP_CONG) {
@@ -558,6 +508,8 @@ dme_status run_op(dme_plan_t p, const Op& o, double* P) {
     return DME_EINVAL;
 }
 
+namespace {
+
 dme_status run_step(dme_plan_t p, double* P) {
     for (const Op& o : p->ops) DME_TRY(run_op(p, o, P));
     DME_CUDA_TRY(cudaGetLastError());
@@ -587,7 +539,9 @@ dme_status validate(const dme_plan_desc* d, const double* A, const double* QorC,
     return DME_OK;
 }
 
-void free_plan(dme_plan_t p) {
+}  // namespace
+
+void dme::free_plan(dme_plan_t p) {
     if (!p) return;
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->st) cudaStreamSynchronize(p->st);
@@ -596,13 +550,28 @@ void free_plan(dme_plan_t p) {
         cudaEventDestroy(r.b);
     }
     for (cudaEvent_t e : p->evpool) cudaEventDestroy(e);
-    for (void* q : p->allocs) cudaFree(q);
+    for (void* q : p->allocs) cudaFreeAsync(q, p->st);
+    if (p->st) cudaStreamSynchronize(p->st);
     if (p->own_st && p->st) cudaStreamDestroy(p->st);
     delete p;
 }
 
-dme_status plan_create(const dme_plan_desc* d, const double* A, const double* QorC, const double* B,
-                       const double* R, const double* S, void* stream, dme_plan_t* out) {
+size_t dme::plan_estimate_bytes(const dme_plan_desc& d) {
+    const size_t nn = (size_t)d.n * d.n * sizeof(double);
+    int taus = 0;
+    for (int i = 0; i < d.nflows; ++i) taus += (d.flows[i] == DME_F1 || d.flows[i] == DME_F12) ? 1 : 0;
+    taus = std::max(taus, 1);
+    const size_t persistent = (3 + 2 * (size_t)taus + 3) * nn;           // A, Q, X, (E, W) per t, S-flow work
+    const size_t transient = 17 * nn;                                   // Pade chain blocks and LU copies
+    return persistent + transient + (size_t)d.n * 64 * sizeof(double) + (1u << 20);
+}
+
+namespace {
+
+}  // namespace
+
+dme_status dme::plan_create(const dme_plan_desc* d, const double* A, const double* QorC, const double* B,
+                            const double* R, const double* S, void* stream, dme_plan_t* out) {
     DME_TRY(validate(d, A, QorC, B, R, S));
     if (d->prec == DME_SPLIT_BF16 && d->n > OZ_MAX_K) {
         set_error("DME_SPLIT_BF16 supports n <= 4096 (exact slice accumulation over K <= 4096)");
@@ -638,9 +607,9 @@ dme_status plan_create(const dme_plan_desc* d, const double* A, const double* Qo
     DME_TRY(palloc_t(p, &p->small, 2 * (size_t)n + 16));
     DME_CUDA_TRY(cudaMemcpyAsync(p->A, A, nn * sizeof(double), cudaMemcpyDefault, st));
     if (d->q_is_factor) {
+        TmpPool tp(st);
         double* C = nullptr;
-        DME_CUDA_TRY(cudaMalloc(&C, (size_t)d->p * n * sizeof(double)));
-        std::unique_ptr<double, void (*)(double*)> cg(C, [](double* q) { cudaFree(q); });
+        DME_TRY(tp.get(&C, (size_t)d->p * n));
         DME_CUDA_TRY(cudaMemcpyAsync(C, QorC, (size_t)d->p * n * sizeof(double), cudaMemcpyDefault, st));
         DME_TRY(gemm1(gp(n, n, d->p, C, n, 1, C, n, 0, p->Q, n, 1.0), st));   // Q = C^T C
         DME_CUDA_TRY(cudaStreamSynchronize(st));
@@ -649,11 +618,10 @@ dme_status plan_create(const dme_plan_desc* d, const double* A, const double* Qo
     }
     if (ric) {
         const int m = d->m;
+        TmpPool tp(st);
         double *Bd = nullptr, *Rd = nullptr;
-        DME_CUDA_TRY(cudaMalloc(&Bd, (size_t)n * m * sizeof(double)));
-        std::unique_ptr<double, void (*)(double*)> bg(Bd, [](double* q) { cudaFree(q); });
-        DME_CUDA_TRY(cudaMalloc(&Rd, (size_t)m * m * sizeof(double)));
-        std::unique_ptr<double, void (*)(double*)> rg(Rd, [](double* q) { cudaFree(q); });
+        DME_TRY(tp.get(&Bd, (size_t)n * m));
+        DME_TRY(tp.get(&Rd, (size_t)m * m));
         DME_CUDA_TRY(cudaMemcpyAsync(Bd, B, (size_t)n * m * sizeof(double), cudaMemcpyDefault, st));
         DME_CUDA_TRY(cudaMemcpyAsync(Rd, R, (size_t)m * m * sizeof(double), cudaMemcpyDefault, st));
         DME_TRY(palloc_t(p, &p->Bt, (size_t)n * m));
@@ -687,6 +655,8 @@ dme_status plan_create(const dme_plan_desc* d, const double* A, const double* Qo
     *out = guard.release();
     return DME_OK;
 }
+
+namespace {
 
 dme_status step_graph(dme_plan_t p, double* P, int nsteps) {
     if (!p->gexec || p->gP != P) {

@@ -1,0 +1,84 @@
+// Plan internals shared by plan.cu and server.cu (not part of the C ABI).
+#pragma once
+
+#include <vector>
+
+#include "dme_internal.h"
+#include "split_internal.h"
+
+using dme::SliceBuf;
+using dme::GemmProb;
+
+struct EWEntry {
+    double tau;
+    double* E;
+    double* W;
+    int s;
+    SliceBuf Gsl;   // split path: slices of E^T (rows of E^T = columns of E)
+};
+
+enum OpKind { OP_CONG = 0, OP_AXPY = 1, OP_RICC = 2, OP_SFLOW = 3 };
+
+struct Op {
+    int kind;
+    double tau;
+    int ew;        // OP_CONG: index of (E, W)
+    double wcoef;  // OP_CONG: coefficient of W (1 for T12, 0 for T1)
+    double qcoef;  // fused T2: + qcoef Q
+    int rule;      // OP_SFLOW: DME_T4_MIDPOINT / DME_T4_EULER
+};
+
+struct dme_plan_s {
+    dme_plan_desc d;
+    int n = 0, m = 0;
+    cudaStream_t st = nullptr;
+    bool own_st = false;
+    double* A = nullptr;
+    double* Q = nullptr;
+    double* Bt = nullptr;
+    double* S = nullptr;
+    double* X = nullptr;       // n x n congruence intermediate
+    double* Xs = nullptr;      // n x n S-flow intermediates
+    double* Y1 = nullptr;
+    double* state = nullptr;   // n x n, dme_solve working state
+    double* rwork = nullptr;   // Riccati work
+    double* small = nullptr;   // 2n colsums + scalars
+    int* status = nullptr;
+    double normM = 0.0;
+    std::vector<EWEntry> ew;
+    std::vector<Op> ops;
+    double ops_h = -1.0;
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    cudaGraphExec_t gexec = nullptr;
+    double* gP = nullptr;
+    int graph_kernels = -1;
+    bool split = false;
+    SliceBuf psl, usl, Ssl;    // split path: slices of P, of U = G P, and of S
+    float2* U = nullptr;       // split path: G P as normalised (hi, lo) pairs
+    // profiling: CUDA-event pairs around launches made outside graph capture
+    bool prof = false;
+    std::vector<cudaEvent_t> evpool;
+    struct EvRec {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<EvRec> evrec;
+};
+
+
+namespace dme {
+
+// Build a plan (validated descriptor; pointers host or device).
+dme_status plan_create(const dme_plan_desc* d, const double* A, const double* QorC, const double* B,
+                       const double* R, const double* S, void* stream, dme_plan_t* out);
+// Free a plan and everything it owns (synchronises its stream).
+void free_plan(dme_plan_t p);
+// Compile one step of size h into p->ops (computes missing E_t, W_t).
+dme_status build_ops(dme_plan_t p, double h);
+// Enqueue one op on the plan's stream.
+dme_status run_op(dme_plan_t p, const Op& o, double* P);
+// Bytes reserved while a plan of this descriptor is built (persistent + transient).
+size_t plan_estimate_bytes(const dme_plan_desc& d);
+
+}  // namespace dme

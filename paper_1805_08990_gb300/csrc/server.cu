@@ -1,29 +1,441 @@
-// Serving entry points (placeholder until the grouped scheduler lands).
-#include "dme_internal.h"
+// Serving: continuous batching of independent DLE/DRE solves on one GPU.
+//
+// Two host threads share a request table under one mutex:
+//  * the admission thread takes queued requests while a slot is free and the
+//    request's device footprint fits in the HBM budget, and builds its plan
+//    (problem data, Q, Bt, E_t, W_t) on the plan's own stream, so planning
+//    overlaps with stepping on the GPU;
+//  * the stepper thread owns the resident requests and runs scheduler rounds:
+//    each round advances every resident request by one composition step.  The
+//    ops of all residents are executed stage by stage with grouped kernels:
+//    one grouped FP64 GEMM launch per congruence phase (P E, then E^T X with
+//    the W/tQ epilogue) and one grouped launch per Riccati kernel, covering all
+//    residents at that stage.  Requests admitted between rounds join the next
+//    round; finished ones leave after it.
+// Grouped kernels compute each problem's tiles exactly as they would alone
+// (no cross-request reduction), so a result is bit-identical alone or in a mix.
+// Latency is measured from dme_submit to the end of the round that finished it.
+#include "plan_internal.h"
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
 
 using namespace dme;
 
+namespace {
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+enum ReqState { Q_QUEUED = 0, Q_PLANNING = 1, Q_RESIDENT = 2, Q_DONE = 3 };
+
+struct Req {
+    uint64_t id = 0;
+    dme_plan_desc desc;
+    std::vector<double> A, QC, B, R, S, P0;
+    double T = 0;
+    int nsteps = 0;
+    int state = Q_QUEUED;
+    dme_plan_t plan = nullptr;
+    double* P = nullptr;
+    int slot = -1;
+    int done_steps = 0;
+    size_t reserved = 0;
+    std::vector<double> out;
+    dme_status status = DME_OK;
+    std::string err;
+    double t_submit = 0, t_done = 0;
+};
+
+}  // namespace
+
+struct dme_server_s {
+    size_t budget = 0;
+    int max_slots = 0;
+    size_t queue_cap = 0;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Req*> queue;
+    std::vector<Req*> ready;      // planned, waiting for the next round
+    std::unordered_map<uint64_t, std::unique_ptr<Req>> reqs;
+    std::vector<int> free_slots;
+    size_t reserved = 0;
+    uint64_t next_id = 1;
+    bool stop = false;
+    std::thread admit_thr, step_thr;
+    cudaStream_t st = nullptr;
+    int* dstat = nullptr;         // per-slot device status words
+    void* gdesc = nullptr;        // grouped GEMM descriptors
+    void* rdesc = nullptr;        // grouped Riccati descriptors
+    std::vector<double> lat_ms;
+    int completed = 0, failed = 0, rounds = 0;
+    double t_first = -1, t_last = 0;
+    std::string stats;
+};
+
+namespace {
+
+void finish(dme_server_t s, Req* r, dme_status st, const std::string& err) {
+    // called with s->mu held
+    r->status = st;
+    r->err = err;
+    r->state = Q_DONE;
+    r->t_done = now_s();
+    if (st == DME_OK) {
+        s->completed++;
+        s->lat_ms.push_back(1e3 * (r->t_done - r->t_submit));
+    } else {
+        s->failed++;
+    }
+    s->t_last = r->t_done;
+    s->cv.notify_all();
+}
+
+void release(dme_server_t s, Req* r) {
+    if (r->P && r->plan) cudaFreeAsync(r->P, r->plan->st);
+    r->P = nullptr;
+    if (r->plan) free_plan(r->plan);
+    r->plan = nullptr;
+    std::lock_guard<std::mutex> g(s->mu);
+    s->reserved -= r->reserved;
+    r->reserved = 0;
+    if (r->slot >= 0) s->free_slots.push_back(r->slot);
+    r->slot = -1;
+    s->cv.notify_all();
+}
+
+void admit_loop(dme_server_t s) {
+    for (;;) {
+        Req* r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv.wait(lk, [&] {
+                if (s->stop) return true;
+                if (s->queue.empty() || s->free_slots.empty()) return false;
+                return s->reserved + plan_estimate_bytes(s->queue.front()->desc) <= s->budget;
+            });
+            if (s->stop) return;
+            r = s->queue.front();
+            s->queue.pop_front();
+            r->state = Q_PLANNING;
+            r->slot = s->free_slots.back();
+            s->free_slots.pop_back();
+            r->reserved = plan_estimate_bytes(r->desc);
+            s->reserved += r->reserved;
+        }
+        set_error("");
+        dme_plan_t p = nullptr;
+        const double* Bp = r->B.empty() ? nullptr : r->B.data();
+        const double* Rp = r->R.empty() ? nullptr : r->R.data();
+        const double* Sp = r->S.empty() ? nullptr : r->S.data();
+        dme_status st = plan_create(&r->desc, r->A.data(), r->QC.data(), Bp, Rp, Sp, nullptr, &p);
+        const size_t nn = (size_t)r->desc.n * r->desc.n;
+        if (st == DME_OK) {
+            r->plan = p;
+            cudaError_t e = cudaMallocAsync(&r->P, nn * sizeof(double), p->st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(r->P, r->P0.data(), nn * sizeof(double), cudaMemcpyHostToDevice, p->st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                st = DME_ENOMEM;
+                set_error(std::string("serving: ") + cudaGetErrorString(e));
+            }
+        }
+        std::string err = get_error();
+        if (st != DME_OK) {
+            release(s, r);
+            std::lock_guard<std::mutex> g(s->mu);
+            finish(s, r, st, err);
+            continue;
+        }
+        // free the input copies; keep the measured footprint
+        std::vector<double>().swap(r->A);
+        std::vector<double>().swap(r->QC);
+        std::vector<double>().swap(r->P0);
+        std::lock_guard<std::mutex> g(s->mu);
+        const size_t actual = p->bytes + nn * sizeof(double);
+        s->reserved = s->reserved - r->reserved + actual;
+        r->reserved = actual;
+        r->state = Q_RESIDENT;
+        s->ready.push_back(r);
+        s->cv.notify_all();
+    }
+}
+
+// One scheduler round over the resident requests: stage by stage, grouped launches.
+dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
+    size_t stages = 0;
+    for (Req* r : res) stages = std::max(stages, r->plan->ops.size());
+    for (size_t k = 0; k < stages; ++k) {
+        std::vector<GemmProb> g1, g2;
+        std::vector<RicItem> ric;
+        for (Req* r : res) {
+            if (k >= r->plan->ops.size()) continue;
+            const Op& o = r->plan->ops[k];
+            dme_plan_t p = r->plan;
+            const int n = p->n;
+            if (o.kind == OP_CONG) {
+                const EWEntry& e = p->ew[o.ew];
+                GemmProb a;
+                std::memset(&a, 0, sizeof(a));
+                a.A = r->P;
+                a.B = e.E;
+                a.C = p->X;
+                a.M = a.N = a.K = n;
+                a.lda = a.ldb = a.ldc = a.ldd = n;
+                a.alpha = 1.0;
+                g1.push_back(a);
+                GemmProb b;
+                std::memset(&b, 0, sizeof(b));
+                b.A = e.E;
+                b.transA = 1;
+                b.B = p->X;
+                b.C = r->P;
+                b.M = b.N = b.K = n;
+                b.lda = b.ldb = b.ldc = b.ldd = n;
+                b.alpha = 1.0;
+                b.tri = 1;
+                if (o.wcoef != 0.0) {
+                    b.D1 = e.W;
+                    b.b1 = o.wcoef;
+                }
+                if (o.qcoef != 0.0) {
+                    b.D2 = p->Q;
+                    b.b2 = o.qcoef;
+                }
+                g2.push_back(b);
+            } else if (o.kind == OP_RICC) {
+                ric.push_back(make_ric_item(r->P, p->Bt, n, p->m, o.tau, o.qcoef != 0.0 ? p->Q : nullptr, o.qcoef,
+                                            p->rwork, s->dstat + r->slot));
+            } else if (o.kind == OP_AXPY) {
+                launch_axpy_sym(r->P, p->Q, o.qcoef, n, n, s->st);
+            } else {
+                set_error("serving: unsupported op");
+                return DME_EINVAL;
+            }
+        }
+        if (!g1.empty()) {
+            DME_TRY(gemm64_grouped(g1, reinterpret_cast<GemmProb*>(s->gdesc), s->st));
+            DME_TRY(gemm64_grouped(g2, reinterpret_cast<GemmProb*>(s->gdesc) + s->max_slots, s->st));
+        }
+        if (!ric.empty()) DME_TRY(launch_riccati_grouped(ric, s->rdesc, s->st));
+        // descriptors are uploaded per launch from host memory: wait before the next stage reuses them
+        DME_CUDA_TRY(cudaStreamSynchronize(s->st));
+    }
+    return DME_OK;
+}
+
+void step_loop(dme_server_t s) {
+    std::vector<Req*> res;
+    std::vector<int> hstat(s->max_slots);
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv.wait(lk, [&] { return s->stop || !s->ready.empty() || !res.empty(); });
+            if (s->stop) return;
+            for (Req* r : s->ready) res.push_back(r);
+            s->ready.clear();
+        }
+        dme_status st = run_round(s, res);
+        std::string err = get_error();
+        if (st == DME_OK) {
+            cudaError_t e = cudaMemcpyAsync(hstat.data(), s->dstat, sizeof(int) * s->max_slots,
+                                            cudaMemcpyDeviceToHost, s->st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+            if (e != cudaSuccess) {
+                st = DME_ECUDA;
+                err = std::string("serving: ") + cudaGetErrorString(e);
+            }
+        }
+        s->rounds++;
+        std::vector<Req*> keep;
+        for (Req* r : res) {
+            dme_status rs = st;
+            std::string rerr = err;
+            if (rs == DME_OK && hstat[r->slot]) {
+                rs = (hstat[r->slot] & DEV_NOTSPD) ? DME_ENOTSPD : DME_ECUDA;
+                rerr = "serving: I_m + t Bt^T P Bt is not positive definite";
+                cudaMemsetAsync(s->dstat + r->slot, 0, sizeof(int), s->st);
+            }
+            if (rs == DME_OK) r->done_steps++;
+            if (rs != DME_OK || r->done_steps >= r->nsteps) {
+                if (rs == DME_OK) {
+                    r->out.resize((size_t)r->desc.n * r->desc.n);
+                    cudaError_t e = cudaMemcpyAsync(r->out.data(), r->P, r->out.size() * sizeof(double),
+                                                    cudaMemcpyDeviceToHost, s->st);
+                    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+                    if (e != cudaSuccess) {
+                        rs = DME_ECUDA;
+                        rerr = std::string("serving: ") + cudaGetErrorString(e);
+                    }
+                }
+                release(s, r);
+                std::lock_guard<std::mutex> g(s->mu);
+                finish(s, r, rs, rerr);
+            } else {
+                keep.push_back(r);
+            }
+        }
+        res.swap(keep);
+    }
+}
+
+}  // namespace
+
 extern "C" {
 
-dme_status dme_server_create(size_t, int, dme_server_t* out) {
-    if (out) *out = nullptr;
-    set_error("serving is not available in this build");
-    return DME_EINVAL;
+dme_status dme_server_create(size_t hbm_budget_bytes, int max_slots, dme_server_t* out) {
+    if (!out) return set_error("out is NULL"), DME_EINVAL;
+    *out = nullptr;
+    if (max_slots < 1 || max_slots > 4096 || hbm_budget_bytes == 0)
+        return set_error("need 1 <= max_slots <= 4096 and a non-zero budget"), DME_EINVAL;
+    dme_server_t s = new (std::nothrow) dme_server_s();
+    if (!s) return set_error("host allocation failed"), DME_ENOMEM;
+    s->budget = hbm_budget_bytes;
+    s->max_slots = max_slots;
+    s->queue_cap = (size_t)max_slots * 64;
+    for (int i = max_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
+    cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&s->dstat, sizeof(int) * max_slots);
+    if (e == cudaSuccess) e = cudaMemset(s->dstat, 0, sizeof(int) * max_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&s->gdesc, sizeof(GemmProb) * 2 * max_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&s->rdesc, riccati_desc_bytes() * max_slots);
+    if (e != cudaSuccess) {
+        set_error(std::string("dme_server_create: ") + cudaGetErrorString(e));
+        cudaGetLastError();
+        if (s->st) cudaStreamDestroy(s->st);
+        cudaFree(s->dstat);
+        cudaFree(s->gdesc);
+        cudaFree(s->rdesc);
+        delete s;
+        return DME_ECUDA;
+    }
+    s->admit_thr = std::thread(admit_loop, s);
+    s->step_thr = std::thread(step_loop, s);
+    *out = s;
+    return DME_OK;
 }
 
-dme_status dme_submit(dme_server_t, const dme_plan_desc*, const double*, const double*, const double*,
-                      const double*, const double*, const double*, double, int, uint64_t*) {
-    set_error("serving is not available in this build");
-    return DME_EINVAL;
+dme_status dme_submit(dme_server_t s, const dme_plan_desc* desc, const double* A, const double* QorC,
+                      const double* B, const double* R, const double* S, const double* P0, double T, int nsteps,
+                      uint64_t* ticket) {
+    if (!s || !desc || !A || !QorC || !P0 || !ticket) return set_error("missing argument"), DME_EINVAL;
+    if (!(T > 0.0) || nsteps < 1) return set_error("need T > 0 and nsteps >= 1"), DME_EINVAL;
+    if (desc->prec != DME_FP64) return set_error("serving runs the FP64 path"), DME_EINVAL;
+    for (int i = 0; i < desc->nflows; ++i)
+        if (desc->flows[i] == DME_F4) return set_error("serving supports DLE/DRE schemes (no F4)"), DME_EINVAL;
+    try {
+        auto r = std::make_unique<Req>();
+        r->desc = *desc;
+        r->desc.h = T / nsteps;
+        const int n = desc->n;
+        if (n < 1 || n > 16384) return set_error("n must be in [1, 16384]"), DME_EINVAL;
+        const size_t nn = (size_t)n * n;
+        const int rows_c = desc->q_is_factor ? desc->p : n;
+        if (desc->q_is_factor && (desc->p < 1 || desc->p > 16384)) return set_error("bad p"), DME_EINVAL;
+        r->A.assign(A, A + nn);
+        r->QC.assign(QorC, QorC + (size_t)rows_c * n);
+        r->P0.assign(P0, P0 + nn);
+        const bool ric = desc->eq == DME_DRE || desc->eq == DME_GDRE;
+        if (ric) {
+            if (!B || !R || desc->m < 1 || desc->m > 32) return set_error("DRE needs B, R, 1 <= m <= 32"), DME_EINVAL;
+            r->B.assign(B, B + (size_t)n * desc->m);
+            r->R.assign(R, R + (size_t)desc->m * desc->m);
+        }
+        if (S) r->S.assign(S, S + nn);
+        r->T = T;
+        r->nsteps = nsteps;
+        std::lock_guard<std::mutex> g(s->mu);
+        if (plan_estimate_bytes(r->desc) > s->budget)
+            return set_error("request footprint exceeds the server's HBM budget"), DME_ENOMEM;
+        if (s->queue.size() >= s->queue_cap) return set_error("queue full"), DME_EBUSY;
+        r->id = s->next_id++;
+        r->t_submit = now_s();
+        if (s->t_first < 0) s->t_first = r->t_submit;
+        *ticket = r->id;
+        s->queue.push_back(r.get());
+        s->reqs[r->id] = std::move(r);
+        s->cv.notify_all();
+        return DME_OK;
+    } catch (const std::bad_alloc&) {
+        return set_error("host allocation failed"), DME_ENOMEM;
+    }
 }
 
-dme_status dme_poll(dme_server_t, uint64_t, double*, int64_t) {
-    set_error("serving is not available in this build");
-    return DME_EINVAL;
+dme_status dme_poll(dme_server_t s, uint64_t ticket, double* P_out, int64_t timeout_us) {
+    if (!s) return set_error("server is NULL"), DME_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return set_error("unknown ticket"), DME_EINVAL;
+    Req* r = it->second.get();
+    auto done = [&] { return r->state == Q_DONE; };
+    if (!done()) {
+        if (timeout_us == 0) return set_error("not finished"), DME_ENOTREADY;
+        if (timeout_us < 0) {
+            s->cv.wait(lk, done);
+        } else if (!s->cv.wait_for(lk, std::chrono::microseconds(timeout_us), done)) {
+            return set_error("timed out"), DME_ETIMEOUT;
+        }
+    }
+    dme_status st = r->status;
+    if (st == DME_OK && P_out) std::memcpy(P_out, r->out.data(), r->out.size() * sizeof(double));
+    if (st != DME_OK) set_error(r->err);
+    s->reqs.erase(it);
+    return st;
 }
 
-const char* dme_server_stats(dme_server_t) { return "{}"; }
+const char* dme_server_stats(dme_server_t s) {
+    if (!s) return "{}";
+    std::lock_guard<std::mutex> g(s->mu);
+    std::vector<double> l = s->lat_ms;
+    std::sort(l.begin(), l.end());
+    auto pct = [&](double q) { return l.empty() ? 0.0 : l[std::min(l.size() - 1, (size_t)(q * (l.size() - 1) + 0.5))]; };
+    int resident = 0, queued = (int)s->queue.size();
+    for (auto& kv : s->reqs)
+        if (kv.second->state == Q_RESIDENT || kv.second->state == Q_PLANNING) ++resident;
+    const double span = (s->t_first >= 0 && s->t_last > s->t_first) ? s->t_last - s->t_first : 0.0;
+    char buf[512];
+    snprintf(buf, sizeof(buf),
+             "{\"completed\": %d, \"failed\": %d, \"resident\": %d, \"queued\": %d, \"rounds\": %d, "
+             "\"p50_ms\": %.3f, \"p99_ms\": %.3f, \"solves_per_s\": %.4f, \"reserved_bytes\": %zu}",
+             s->completed, s->failed, resident, queued, s->rounds, pct(0.5), pct(0.99),
+             span > 0 ? s->completed / span : 0.0, s->reserved);
+    s->stats = buf;
+    return s->stats.c_str();
+}
 
-dme_status dme_server_destroy(dme_server_t) { return DME_OK; }
+dme_status dme_server_destroy(dme_server_t s) {
+    if (!s) return DME_OK;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        s->stop = true;
+        s->cv.notify_all();
+    }
+    if (s->admit_thr.joinable()) s->admit_thr.join();
+    if (s->step_thr.joinable()) s->step_thr.join();
+    cudaStreamSynchronize(s->st);
+    for (auto& kv : s->reqs) {
+        Req* r = kv.second.get();
+        if (r->P && r->plan) cudaFreeAsync(r->P, r->plan->st);
+        if (r->plan) free_plan(r->plan);
+    }
+    cudaFree(s->dstat);
+    cudaFree(s->gdesc);
+    cudaFree(s->rdesc);
+    cudaStreamDestroy(s->st);
+    delete s;
+    return DME_OK;
+}
 
 }  // extern "C"
