@@ -184,6 +184,25 @@ dme_status dme_server_destroy(dme_server_t srv);
 dme_status dme_gemm_split(int M, int N, int K, const double* A, const double* B, double* C,
                           void* cuda_stream);
 
+/* dme_gemm_split without any device allocation, for callers that cannot
+ * call cudaMalloc: code whose device memory is owned by a host application's
+ * own allocator, or loops that must not pay cudaMalloc's implicit device
+ * synchronisation.  The paper has no counterpart; it is a library service.
+ * Same arguments, arithmetic and results as dme_gemm_split (A, B, C float64
+ * row-major device memory, C = A B^T, 1 <= K <= 4096).  Its scratch is an
+ * 8 MiB array in the library's device memory, held by every device that
+ * loads the library until the process exits:
+ *   (5 M + 4 N) * roundup(K, 32) * 2 bytes of slices plus the row scales must
+ *   fit in it (e.g. M = N = K = 640), otherwise DME_EINVAL with the sizes.
+ * The first call on a device looks up that array's device address (with the
+ * device current) and caches it; make that first call before any stream
+ * capture.  Every call shares the one array and finds the previous call's
+ * contents there: calls on the same device that overlap on the GPU (two
+ * streams, or two host threads) race and must be serialised by the caller.
+ * Synchronises `cuda_stream`. */
+dme_status dme_gemm_split_noalloc(int M, int N, int K, const double* A, const double* B, double* C,
+                                  void* cuda_stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* dme_last_error(void);
 

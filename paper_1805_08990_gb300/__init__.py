@@ -13,7 +13,7 @@ from .binding import (  # noqa: F401
     DmeError, LibraryNotBuilt, dme_plan_desc, make_desc, lib, header_functions,
     dme_plan, dme_expm, dme_apply, dme_apply_async, dme_sync, dme_plan_kernels_per_step, dme_step, dme_solve, dme_plan_bytes, dme_plan_destroy,
     dme_server_create, dme_submit, dme_poll, dme_server_stats, dme_server_destroy, dme_last_error,
-    dme_gemm_split,
+    dme_gemm_split, dme_gemm_split_noalloc,
 )
 
 EQ_IDS = {"dle": DME_DLE, "dre": DME_DRE, "gdle": DME_GDLE, "gdre": DME_GDRE}

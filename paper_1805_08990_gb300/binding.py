@@ -74,6 +74,8 @@ _SIGS = {
     "dme_server_destroy": (C.c_int, [C.c_void_p]),
     "dme_last_error": (C.c_char_p, []),
     "dme_gemm_split": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dme_gemm_split_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p]),
 }
 
 
@@ -247,6 +249,17 @@ def dme_gemm_split(A, B, C_out, stream=None):
     st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     _check(lib().dme_gemm_split(int(M), int(N), int(K), _ptr(A, keep), _ptr(B, keep), _out_ptr(C_out), st),
            "dme_gemm_split")
+
+
+def dme_gemm_split_noalloc(A, B, C_out, stream=None):
+    """C_out = A @ B.T like dme_gemm_split, with the library's fixed 8 MiB
+    device scratch instead of any allocation (see include/dme.h)."""
+    M, K = A.shape
+    N = B.shape[0]
+    keep: list = []
+    st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib().dme_gemm_split_noalloc(int(M), int(N), int(K), _ptr(A, keep), _ptr(B, keep), _out_ptr(C_out), st),
+           "dme_gemm_split_noalloc")
 
 
 def dme_last_error() -> str:

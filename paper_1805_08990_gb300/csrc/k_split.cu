@@ -34,7 +34,9 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <cstring>
 #include <mutex>
+#include <string>
 
 namespace dme {
 
@@ -449,3 +451,113 @@ dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzPar
 }
 
 }  // namespace dme
+
+// ============================================================== allocation-free split GEMM
+// dme_gemm_split_noalloc keeps its scratch (the bf16 slices of A and B, their
+// row scales and a status word) in this file-scope device array instead of
+// allocating it.  Every device that loads the library holds the array until
+// the process exits; every call shares it.
+namespace dme {
+
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;    // 8 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[256];
+
+// Device address of the scratch array on the current device.  The first call
+// on a device looks it up (with that device current) and caches it.
+static dme_status noalloc_scratch_address(void** out) {
+    int dev = 0;
+    DME_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return set_error("device ordinal out of range"), DME_EINVAL;
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            set_error(std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+            return DME_ECUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return DME_OK;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace dme
+
+extern "C" dme_status dme_gemm_split_noalloc(int M, int N, int K, const double* A, const double* B, double* C,
+                                             void* cuda_stream) {
+    using namespace dme;
+    if (M < 0 || N < 0 || K < 1 || K > OZ_MAX_K || !A || !B || !C)
+        return set_error("dme_gemm_split_noalloc: need 1 <= K <= 4096 and non-null A, B, C"), DME_EINVAL;
+    if (M == 0 || N == 0) return DME_OK;
+    try {
+        const int Kp = slice_kpad(K);
+        // scratch layout: status | scales of A | scales of B | slices of A | slices of B
+        const size_t off_sa = 256;
+        const size_t off_sb = off_sa + align256(sizeof(float) * (size_t)M);
+        const size_t off_a = off_sb + align256(sizeof(float) * (size_t)N);
+        const size_t off_b = off_a + align256(slice_buf_bytes(M, K, OZ_SLICES_A));
+        const size_t need = off_b + align256(slice_buf_bytes(N, K, OZ_SLICES_B));
+        if (need > kNoAllocScratchBytes) {
+            set_error("dme_gemm_split_noalloc: M=" + std::to_string(M) + " N=" + std::to_string(N) +
+                      " K=" + std::to_string(K) + " needs " + std::to_string(need) +
+                      " bytes of scratch, more than its 8 MiB ((5 M + 4 N) * roundup(K, 32) * 2 bytes of slices"
+                      " plus row scales)");
+            return DME_EINVAL;
+        }
+        unsigned char* base = nullptr;
+        DME_TRY(noalloc_scratch_address(reinterpret_cast<void**>(&base)));
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+        int* status = reinterpret_cast<int*>(base);
+        SliceBuf sa, sb;
+        sa.rows = M;
+        sa.k = K;
+        sa.Kp = Kp;
+        sa.ns = OZ_SLICES_A;
+        sa.scale = reinterpret_cast<float*>(base + off_sa);
+        sa.data = reinterpret_cast<__nv_bfloat16*>(base + off_a);
+        sb.rows = N;
+        sb.k = K;
+        sb.Kp = Kp;
+        sb.ns = OZ_SLICES_B;
+        sb.scale = reinterpret_cast<float*>(base + off_sb);
+        sb.data = reinterpret_cast<__nv_bfloat16*>(base + off_b);
+        DME_TRY(make_slice_tmap(sa, &sa.tmap));
+        DME_TRY(make_slice_tmap(sb, &sb.tmap));
+        // the array keeps the previous call's contents: the status word must start at zero
+        // (slices, padding and scales are rewritten in full below)
+        DME_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+        launch_slice_rows_f64(A, M, K, K, sa, st);
+        launch_slice_rows_f64(B, N, K, K, sb, st);
+        OzParams o;
+        std::memset(&o, 0, sizeof(o));
+        o.M = M;
+        o.N = N;
+        o.Kp = Kp;
+        o.sa = sa.scale;
+        o.sb = sb.scale;
+        o.mode = OZ_OUT_F64;
+        o.ldc = N;
+        o.Cd = C;
+        o.alpha = 1.0;
+        o.status = status;
+        DME_TRY(launch_ozaki_gemm(sa.tmap, sb.tmap, o, st));
+        int hs = 0;
+        DME_CUDA_TRY(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+        DME_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hs) {
+            set_error("dme_gemm_split_noalloc: device status " + std::to_string(hs));
+            return DME_ECUDA;
+        }
+        return DME_OK;
+    } catch (...) {
+        set_error("dme_gemm_split_noalloc: internal error");
+        return DME_EINVAL;
+    }
+}
