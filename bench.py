@@ -127,6 +127,38 @@ def replica_value(steps_per_rank: int, ms_max: float, world_size: int) -> float:
     return world_size * steps_per_rank / (ms_max / 1e3)
 
 
+def serving_run(count: int, seed: int, rate: float | None):
+    """Submit `count` requests of the serving stream (n log-uniform 32..1024,
+    Laplacian or stable random A, m, p ~ U{1..8}, T ~ U[0.1, 10], 50-500 Strang
+    F12F3 steps) to a server, at Poisson arrival times (rate req/s) or all at
+    once (rate None); wait for all.  Returns the server's statistics."""
+    import paper_1805_08990_gb300 as dme
+    specs = W.serving_requests(count, seed=seed, rate=rate or 1.0)
+    probs = [W.materialize(sp) for sp in specs]
+    srv = dme.dme_server_create(64 << 30, 32)
+    try:
+        t0 = time.perf_counter()
+        tickets = []
+        for sp, pr in zip(specs, probs):
+            if rate is not None:
+                delay = sp["arrival"] - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+            d = dme.make_desc(pr.n, m=pr.B.shape[1], p=pr.C.shape[0], eq=dme.DME_DRE, comp="strang",
+                              flows=("F12", "F3"), h=pr.T / sp["steps"], q_is_factor=True)
+            tickets.append((dme.dme_submit(srv, d, pr.A, pr.C, pr.B, pr.R, None, pr.P0, pr.T, sp["steps"]), pr.n))
+        for tk, n in tickets:
+            out = np.empty((n, n))
+            assert dme.dme_poll(srv, tk, out, -1) == dme.DME_OK
+        wall = time.perf_counter() - t0
+        st = json.loads(dme.dme_server_stats(srv))
+        st["wall_s"] = wall
+        st["steps_total"] = int(sum(sp["steps"] for sp in specs))
+        return st
+    finally:
+        dme.dme_server_destroy(srv)
+
+
 # ------------------------------------------------------------------ oracle (CPU)
 def oracle_steps(pr, nsteps, E=None, Wm=None):
     """Time nsteps oracle Strang F12F3 steps of the workload; returns (seconds, E, W)."""
@@ -294,6 +326,17 @@ def run_ours(args):
         line[f"{prec}_steps_per_s"] = replica_value(rr["steps"], rr["ms"], ws)
         line[f"{prec}_plan_s"] = rr["plan_s"]
     line["peaks_source"] = peaks_src
+    if args.serving_requests > 0:
+        burst = serving_run(args.serving_requests, seed=1, rate=None)
+        sat = burst["completed"] / burst["wall_s"]
+        live = serving_run(args.serving_requests, seed=2, rate=0.9 * sat)
+        line["serving"] = {
+            "requests": args.serving_requests, "prec": "fp64", "scheme": "strang F12F3",
+            "workload": "n log-uniform 32..1024 (Laplacian or stable random A), m,p ~ U{1..8}, T ~ U[0.1,10], "
+                        "50-500 steps, R = I_m, P0 = 0",
+            "saturation_solves_per_s": sat, "poisson_rate": 0.9 * sat,
+            "solves_per_s": live["completed"] / live["wall_s"], "p50_ms": live["p50_ms"], "p99_ms": live["p99_ms"],
+            "burst_p50_ms": burst["p50_ms"], "burst_p99_ms": burst["p99_ms"], "max_slots": 32}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         secs, _, _ = oracle_steps(pr, args.cpu_steps)
         line["cpu_baseline"] = {"value": args.cpu_steps / secs, "unit": "steps/s", "cores": os.cpu_count(),
@@ -343,6 +386,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--gemm-only", type=int, default=0, help="profile target: split GEMM of this size alone")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--serving-requests", type=int, default=32, help="serving sample size (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

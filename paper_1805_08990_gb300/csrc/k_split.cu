@@ -166,14 +166,20 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restric
 #pragma unroll
         for (int t = 0; t < NS; ++t) {
             const int sh = 35 - 7 * t;
-            __nv_bfloat16 q[4];
+            const float unit = __int_as_float((127 - 6 - 7 * t) << 23);     // 2^(-6-7t), exact
+            float q[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const long long dd = (V[u] + (1ll << (sh - 1))) >> sh;
                 V[u] -= dd << sh;
-                q[u] = __float2bfloat16_rn(ldexpf((float)dd, -6 - 7 * t));
+                q[u] = (float)(int)dd * unit;          // |dd| <= 64: exact in int and float
             }
-            *reinterpret_cast<uint2*>(out + t * plane + o) = *reinterpret_cast<const uint2*>(q);
+            const __nv_bfloat162 p01 = __floats2bfloat162_rn(q[0], q[1]);
+            const __nv_bfloat162 p23 = __floats2bfloat162_rn(q[2], q[3]);
+            uint2 w;
+            w.x = *reinterpret_cast<const unsigned int*>(&p01);
+            w.y = *reinterpret_cast<const unsigned int*>(&p23);
+            *reinterpret_cast<uint2*>(out + t * plane + o) = w;
         }
     }
 }

@@ -1,0 +1,39 @@
+"""Parity at the bench's full size: the large dense DRE (n = 4096 Laplacian,
+B 4096 x 8, R = I_8, C 8 x 4096, h = 1/256, Strang F12F3), two steps from a
+seeded PSD state, FP64 and split precision against the oracle (whose own 2n x 2n
+exponential supplies E and W).  The oracle's share takes about a minute."""
+import numpy as np
+import pytest
+import torch
+
+import dme_workloads as W
+import oracle as O
+from gpu_util import FP64_TOL, SPLIT_TOL, dev, host, plan_for, rel, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 2
+
+
+@pytest.fixture(scope="module")
+def case():
+    require_gpu()
+    pr = W.dre_heat_large()
+    h = pr.T / 256
+    P0 = W.random_psd(pr.n, 17, rank=64, scale=2.0)
+    plan = O.Plan(pr.A, pr.Q, pr.B, pr.R)
+    P = P0
+    for _ in range(STEPS):
+        P = plan.step(P, "strang", ["F12", "F3"], h)
+    return pr, h, P0, P
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", FP64_TOL), ("split_bf16", SPLIT_TOL)])
+def test_large_dre_two_steps(case, prec, tol):
+    pr, h, P0, ref = case
+    plan = plan_for(pr, ["F12", "F3"], "strang", h, prec=prec)
+    P = dev(P0)
+    plan.step(P, STEPS)
+    got = host(P)
+    assert rel(got, ref) < tol
+    assert np.array_equal(got, got.T)
