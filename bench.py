@@ -127,7 +127,7 @@ def replica_value(steps_per_rank: int, ms_max: float, world_size: int) -> float:
     return world_size * steps_per_rank / (ms_max / 1e3)
 
 
-def serving_run(count: int, seed: int, rate: float | None):
+def serving_run(count: int, seed: int, rate: float | None, prec: str = "fp64"):
     """Submit `count` requests of the serving stream (n log-uniform 32..1024,
     Laplacian or stable random A, m, p ~ U{1..8}, T ~ U[0.1, 10], 50-500 Strang
     F12F3 steps) to a server, at Poisson arrival times (rate req/s) or all at
@@ -145,7 +145,7 @@ def serving_run(count: int, seed: int, rate: float | None):
                 if delay > 0:
                     time.sleep(delay)
             d = dme.make_desc(pr.n, m=pr.B.shape[1], p=pr.C.shape[0], eq=dme.DME_DRE, comp="strang",
-                              flows=("F12", "F3"), h=pr.T / sp["steps"], q_is_factor=True)
+                              flows=("F12", "F3"), h=pr.T / sp["steps"], q_is_factor=True, prec=prec)
             tickets.append((dme.dme_submit(srv, d, pr.A, pr.C, pr.B, pr.R, None, pr.P0, pr.T, sp["steps"]), pr.n))
         for tk, n in tickets:
             out = np.empty((n, n))
@@ -279,12 +279,24 @@ def run_ours(args):
         t0 = time.perf_counter()
         plan.solve(P0h, steps * h, steps, Ph)
         e2e_s = time.perf_counter() - t0
+        # accuracy probe: the state after exactly 6 steps from P0 = 0 (FP64: warm-up 3 + timed 3)
+        if prec == "fp64" and warm + steps == 6:
+            P6 = P.clone()
+        else:
+            P6 = torch.zeros(n, n, dtype=torch.float64, device=dev)
+            plan.step(P6, 6)
+        results[prec + "_P6"] = P6
         results[prec] = {"ms": ms, "steps": steps, "kps": kps, "cong_ms": cong_ms, "plan_s": plan_s,
                          "e2e_s": e2e_s, "clocks": clk.summary(), "P": P, "bytes": plan.nbytes,
                          "kernel_ms": k_ms, "kernel_launches": k_launch, "slice_ms": s_ms, "slice_launches": s_launch,
                          "R": R}
         plan.close()
 
+    err6 = None
+    if "fp64_P6" in results and "split_P6" in results:
+        a, b = results["split_P6"], results["fp64_P6"]
+        err6 = (torch.linalg.norm(a - b) / torch.linalg.norm(b)).item()
+    results = {k: v for k, v in results.items() if not k.endswith("_P6")}
     head = "split" if "split" in results else "fp64"
     r = results[head]
     value = replica_value(r["steps"], r["ms"], ws)
@@ -326,17 +338,21 @@ def run_ours(args):
         line[f"{prec}_steps_per_s"] = replica_value(rr["steps"], rr["ms"], ws)
         line[f"{prec}_plan_s"] = rr["plan_s"]
     line["peaks_source"] = peaks_src
+    if err6 is not None:
+        line["split_rel_err_vs_fp64_gpu_after_6_steps"] = err6
     if args.serving_requests > 0:
-        burst = serving_run(args.serving_requests, seed=1, rate=None)
-        sat = burst["completed"] / burst["wall_s"]
-        live = serving_run(args.serving_requests, seed=2, rate=0.9 * sat)
-        line["serving"] = {
-            "requests": args.serving_requests, "prec": "fp64", "scheme": "strang F12F3",
-            "workload": "n log-uniform 32..1024 (Laplacian or stable random A), m,p ~ U{1..8}, T ~ U[0.1,10], "
-                        "50-500 steps, R = I_m, P0 = 0",
-            "saturation_solves_per_s": sat, "poisson_rate": 0.9 * sat,
-            "solves_per_s": live["completed"] / live["wall_s"], "p50_ms": live["p50_ms"], "p99_ms": live["p99_ms"],
-            "burst_p50_ms": burst["p50_ms"], "burst_p99_ms": burst["p99_ms"], "max_slots": 32}
+        line["serving"] = {"requests": args.serving_requests, "scheme": "strang F12F3", "max_slots": 32,
+                           "workload": "n log-uniform 32..1024 (Laplacian or stable random A), m,p ~ U{1..8}, "
+                                       "T ~ U[0.1,10], 50-500 steps, R = I_m, P0 = 0; burst: all submitted at t=0; "
+                                       "live: Poisson arrivals at 0.9x the burst throughput"}
+        for prec, kprec in (("fp64", "fp64"), ("split", "split_bf16")):
+            burst = serving_run(args.serving_requests, seed=1, rate=None, prec=kprec)
+            sat = burst["completed"] / burst["wall_s"]
+            live = serving_run(args.serving_requests, seed=2, rate=0.9 * sat, prec=kprec)
+            line["serving"][prec] = {
+                "saturation_solves_per_s": sat, "poisson_rate": 0.9 * sat,
+                "solves_per_s": live["completed"] / live["wall_s"], "p50_ms": live["p50_ms"],
+                "p99_ms": live["p99_ms"], "burst_p50_ms": burst["p50_ms"], "burst_p99_ms": burst["p99_ms"]}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         secs, _, _ = oracle_steps(pr, args.cpu_steps)
         line["cpu_baseline"] = {"value": args.cpu_steps / secs, "unit": "steps/s", "cores": os.cpu_count(),

@@ -78,7 +78,9 @@ __device__ __forceinline__ int ric_find(const RicDesc* d, int nd, int blk) {
 // fixed order (deterministic, no atomics).
 __global__ void __launch_bounds__(256) riccati_z_kernel(const __grid_constant__ RicBatch batch) {
     constexpr int KC = 512;
-    __shared__ double sB[KC][RZ_MB];
+    // Bt chunk stored column-major in pairs: sB2[c][k/2] = (Bt[k][c], Bt[k+1][c]), so the lanes of a
+    // warp (consecutive k pairs) read consecutive 16-byte words of one column
+    __shared__ double2 sB2[RZ_MB][KC / 2];
     __shared__ double sZ[RZ_ROWS][RZ_MB];
     const RicDesc* ds = ric_descs(batch);
     const int ip = ric_find<0>(ds, batch.nd, blockIdx.x);
@@ -97,9 +99,12 @@ __global__ void __launch_bounds__(256) riccati_z_kernel(const __grid_constant__ 
         for (int c = 0; c < RZ_MB; ++c) acc[c] = 0.0;
         for (int k0 = 0; k0 < n; k0 += KC) {
             __syncthreads();
-            for (int e = threadIdx.x; e < KC * RZ_MB; e += blockDim.x) {
-                int k = e / RZ_MB, c = e % RZ_MB;
-                sB[k][c] = (k0 + k < n && c < mb) ? Bt[(size_t)(k0 + k) * m + c0 + c] : 0.0;
+            for (int e = threadIdx.x; e < (KC / 2) * RZ_MB; e += blockDim.x) {
+                const int c = e / (KC / 2), kp = e % (KC / 2), k = 2 * kp;
+                double2 v;
+                v.x = (k0 + k < n && c < mb) ? Bt[(size_t)(k0 + k) * m + c0 + c] : 0.0;
+                v.y = (k0 + k + 1 < n && c < mb) ? Bt[(size_t)(k0 + k + 1) * m + c0 + c] : 0.0;
+                sB2[c][kp] = v;
             }
             __syncthreads();
             if (row >= n) continue;
@@ -116,9 +121,12 @@ __global__ void __launch_bounds__(256) riccati_z_kernel(const __grid_constant__ 
                     p0 = prow[k];
                     if (k + 1 < kend) p1 = prow[k + 1];
                 }
-                // k is even and KC is even, so k + 1 < KC; past the row end p1 = 0 and sB is zero-filled
+                // k is even; past the row end p1 = 0 and the staged Bt is zero-filled
 #pragma unroll
-                for (int c = 0; c < RZ_MB; ++c) acc[c] = fma(p1, sB[k + 1][c], fma(p0, sB[k][c], acc[c]));
+                for (int c = 0; c < RZ_MB; ++c) {
+                    const double2 b = sB2[c][k >> 1];
+                    acc[c] = fma(p1, b.y, fma(p0, b.x, acc[c]));
+                }
             }
         }
 #pragma unroll
@@ -236,19 +244,33 @@ __global__ void riccati_y_kernel(const __grid_constant__ RicBatch batch) {
     }
 }
 
-// (4) P[i][j] <- P[i][j] - t sum_r Y[i][r] Y[j][r] (+ q Q[i][j]).  The sum is
-// taken in the same order for (i, j) and (j, i), so a symmetric P stays
-// exactly symmetric.  64 x 64 tiles, 256 threads, Y rows staged in shared memory.
+// (4) P[i][j] <- P[i][j] - t sum_r Y[i][r] Y[j][r] (+ q Q[i][j]).  The result is
+// symmetric (the sum is taken in the same order for (i, j) and (j, i)), so only
+// the 64 x 64 tiles on or above the diagonal are computed: each reads its
+// upper block of P, writes it, and for an off-diagonal tile also writes the
+// transposed block below the diagonal from a shared-memory copy (coalesced).
+// Half of the FP64 work and of the traffic on P of a full update.
+constexpr int RU_LD = RU_TILE + 1;
+constexpr size_t RU_SMEM = sizeof(double) * (2 * RU_TILE * 33 + RU_TILE * RU_LD);
+
 __global__ void __launch_bounds__(256) riccati_update_kernel(const __grid_constant__ RicBatch batch) {
     const RicDesc* ds = ric_descs(batch);
     const RicDesc& d = ds[ric_find<2>(ds, batch.nd, blockIdx.x)];
     if (*d.status & DEV_NOTSPD) return;
-    __shared__ double Yi[RU_TILE][33];
-    __shared__ double Yj[RU_TILE][33];
+    extern __shared__ double ru_smem[];
+    double(*Yi)[33] = reinterpret_cast<double(*)[33]>(ru_smem);
+    double(*Yj)[33] = reinterpret_cast<double(*)[33]>(ru_smem + RU_TILE * 33);
+    double* Vt = ru_smem + 2 * RU_TILE * 33;           // [RU_TILE][RU_LD]
     const int n = d.n, m = d.m;
-    const int tn = (n + RU_TILE - 1) / RU_TILE;
-    const int lt = blockIdx.x - d.su;
-    const int i0 = (lt / tn) * RU_TILE, j0 = (lt % tn) * RU_TILE;
+    const int T = (n + RU_TILE - 1) / RU_TILE;
+    // upper-triangle tile (ti <= tj), row by row
+    int rem = blockIdx.x - d.su, ti = 0;
+    while (rem >= T - ti) {
+        rem -= T - ti;
+        ++ti;
+    }
+    const int tj = ti + rem;
+    const int i0 = ti * RU_TILE, j0 = tj * RU_TILE;
     for (int e = threadIdx.x; e < RU_TILE * m; e += blockDim.x) {
         int r = e / m, c = e % m;
         Yi[r][c] = (i0 + r < n) ? d.Y[(size_t)(i0 + r) * m + c] : 0.0;
@@ -269,6 +291,20 @@ __global__ void __launch_bounds__(256) riccati_update_kernel(const __grid_consta
             double v = d.P[off] - d.t * s;
             if (d.Qadd) v += d.q * d.Qadd[off];
             d.P[off] = v;
+            Vt[di * RU_LD + dj] = v;
+        }
+    }
+    if (ti == tj) return;
+    __syncthreads();
+    // mirror: P[j][i] = V[i][j] for the block below the diagonal
+    for (int dj = ty; dj < RU_TILE; dj += 8) {
+        const int j = j0 + dj;
+        if (j >= n) break;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int di = tx + 32 * h, i = i0 + di;
+            if (i >= n) continue;
+            d.P[(size_t)j * n + i] = Vt[di * RU_LD + dj];
         }
     }
 }
@@ -314,7 +350,7 @@ dme_status launch_riccati_grouped(const std::vector<RicItem>& items, void* dev_d
         sz += rz_blocks(n);
         sy += (n + 127) / 128;
         const int tn = (n + RU_TILE - 1) / RU_TILE;
-        su += tn * tn;
+        su += tn * (tn + 1) / 2;
     }
     RicBatch b;
     std::memset(&b, 0, sizeof(b));
@@ -333,7 +369,13 @@ dme_status launch_riccati_grouped(const std::vector<RicItem>& items, void* dev_d
     riccati_z_kernel<<<sz, 256, 0, st>>>(b);
     riccati_small_kernel<<<b.nd, 1024, 0, st>>>(b);
     riccati_y_kernel<<<sy, 128, 0, st>>>(b);
-    riccati_update_kernel<<<su, 256, 0, st>>>(b);
+    static bool attr_set = false;
+    if (!attr_set) {
+        DME_CUDA_TRY(cudaFuncSetAttribute(riccati_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)RU_SMEM));
+        attr_set = true;
+    }
+    riccati_update_kernel<<<su, 256, RU_SMEM, st>>>(b);
     DME_CUDA_TRY(cudaGetLastError());
     return DME_OK;
 }

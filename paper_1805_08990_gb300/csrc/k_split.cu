@@ -37,6 +37,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 namespace dme {
 
@@ -207,8 +208,7 @@ void launch_slice_rows_pair(const float2* Xp, int rows, int cols, int ldx, const
 // Triangle grids enumerate (tm <= tn) row by row.
 constexpr int OZ_GROUP = 8;
 
-__device__ __forceinline__ void oz_tile_coords(const OzParams& p, int& tm, int& tn) {
-    const int t = blockIdx.x;
+__device__ __forceinline__ void oz_tile_coords(const OzParams& p, int t, int& tm, int& tn) {
     if (p.tri) {
         int T = p.tiles_n, r = 0, rem = t;
         while (rem >= T - r) {
@@ -242,9 +242,10 @@ __device__ __forceinline__ double f2d_bits(float f) {
     return __longlong_as_double((long long)(sign | ed | m));
 }
 
-__global__ void __launch_bounds__(192, 1) ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                             const __grid_constant__ CUtensorMap tmB,
-                                                             const OzParams p) {
+// One 128 x 128 output tile (index t of problem p) by one CTA; tmA / tmB are
+// the addresses of the tensor maps (kernel parameters or global memory).
+__device__ __forceinline__ void oz_gemm_tile(const CUtensorMap* tmA, const CUtensorMap* tmB, const OzParams& p,
+                                             int t) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OZ_STAGES * OZ_STAGE_BYTES);
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_gemm_kernel(const __grid_constan
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int tm, tn;
-    oz_tile_coords(p, tm, tn);
+    oz_tile_coords(p, t, tm, tn);
     const int m0 = tm * OZ_BM, n0 = tn * OZ_BN;
     const int nk = p.Kp / OZ_BK;
 
@@ -266,8 +267,8 @@ __global__ void __launch_bounds__(192, 1) ozaki_gemm_kernel(const __grid_constan
         fence_mbar_init();
     }
     if (warp == 0 && lane == 0) {
-        tma_prefetch_desc(&tmA);
-        tma_prefetch_desc(&tmB);
+        tma_prefetch_desc(tmA);
+        tma_prefetch_desc(tmB);
     }
     if (warp == 1) {
         tmem_alloc(smem_u32(tmem_slot), 512);
@@ -292,9 +293,20 @@ __global__ void __launch_bounds__(192, 1) ozaki_gemm_kernel(const __grid_constan
                 const uint32_t full = smem_u32(&bars[s]);
                 uint8_t* st = smem + s * OZ_STAGE_BYTES;
                 mbar_arrive_expect_tx(full, OZ_STAGE_BYTES);
-                tma_load_3d(smem_u32(st), &tmA, full, kb * OZ_BK, m0, 0);
-                tma_load_3d(smem_u32(st + OZ_A_BYTES), &tmB, full, kb * OZ_BK, n0, 0);
+                tma_load_3d(smem_u32(st), tmA, full, kb * OZ_BK, m0, 0);
+                tma_load_3d(smem_u32(st + OZ_A_BYTES), tmB, full, kb * OZ_BK, n0, 0);
                 issued[s]++;
+                // spread over the K loop: pull the epilogue's addend rows (full 128-column
+                // segments only, all in bounds) into L2, one row per k block
+                if (p.mode == OZ_OUT_F64 && kb < OZ_BM && m0 + kb < p.M && n0 + OZ_BN <= p.N &&
+                    (p.ldc % 2) == 0) {
+                    const size_t off = (size_t)(m0 + kb) * p.ldc + n0;
+                    // the bulk prefetch needs a 16-byte aligned start (addends may be caller memory)
+                    if (p.D1 && ((reinterpret_cast<uintptr_t>(p.D1 + off) & 15) == 0))
+                        prefetch_l2_bulk(p.D1 + off, OZ_BN * sizeof(double));
+                    if (p.D2 && ((reinterpret_cast<uintptr_t>(p.D2 + off) & 15) == 0))
+                        prefetch_l2_bulk(p.D2 + off, OZ_BN * sizeof(double));
+                }
             }
             if (!ok) atomicOr(p.status, DEV_TIMEOUT);
             // every load this thread issued has landed before the CTA may exit
@@ -341,11 +353,24 @@ __global__ void __launch_bounds__(192, 1) ozaki_gemm_kernel(const __grid_constan
         // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 = tile rows
         const int q = warp & 3;
         const int i = m0 + 32 * q + lane;
-        const bool ready = mbar_wait(smem_u32(&bars[2 * OZ_STAGES]), 0, OZ_TIMEOUT_NS);
+        const bool ready_here = mbar_wait(smem_u32(&bars[2 * OZ_STAGES]), 0, OZ_TIMEOUT_NS);
+        // one decision for all 128 epilogue threads (they share named barrier 1 below)
+        uint32_t all_ready;
+        asm volatile(
+            "{\n"
+            " .reg .pred p, r;\n"
+            " setp.ne.u32 p, %1, 0;\n"
+            " bar.red.and.pred r, 1, 128, p;\n"
+            " selp.u32 %0, 1, 0, r;\n"
+            "}\n"
+            : "=r"(all_ready)
+            : "r"((uint32_t)ready_here)
+            : "memory");
+        const bool ready = all_ready != 0;
         fence_after_sync();
         if (!ready) {
             if (lane == 0) atomicOr(p.status, DEV_TIMEOUT);
-        } else {
+        } else if (p.mode == OZ_OUT_PAIR) {
             const float sA = (i < p.M) ? p.sa[i] : 0.0f;
 #pragma unroll 1
             for (int c = 0; c < OZ_BN / 32; ++c) {
@@ -368,18 +393,90 @@ __global__ void __launch_bounds__(192, 1) ozaki_gemm_kernel(const __grid_constan
                     const float sh = hi + lo;
                     const float bb = sh - hi;
                     const float sl = (hi - (sh - bb)) + (lo - bb);
-                    if (p.mode == OZ_OUT_PAIR) {
-                        p.Cp[(size_t)i * p.ldc + j] = make_float2(sh * s, sl * s);
-                    } else {
-                        if (p.tri && i > j) continue;
-                        const size_t off = (size_t)i * p.ldc + j;
-                        double v = f2d_bits(sh * s) + f2d_bits(sl * s);
-                        if (p.alpha != 1.0) v *= p.alpha;
-                        if (p.D1) v += p.b1 * p.D1[off];
-                        if (p.D2) v += p.b2 * p.D2[off];
+                    p.Cp[(size_t)i * p.ldc + j] = make_float2(sh * s, sl * s);
+                }
+            }
+        } else {
+            // FP64 output, staged through shared memory (the operand stages are idle now: every
+            // MMA has completed, so every TMA load they consumed has landed):
+            // (1) each thread converts its row of the tile into T[row][col];
+            // (2) the four warps write row segments of C coalesced, adding the addends;
+            // (3) for a symmetric output they write the mirror from T's columns, coalesced.
+            constexpr int TLD = OZ_BN + 1;
+            double* T = reinterpret_cast<double*>(smem);
+            const int il = 32 * q + lane;
+            const float sA = (i < p.M) ? p.sa[i] : 0.0f;
+#pragma unroll 1
+            for (int c = 0; c < OZ_BN / 32; ++c) {
+                uint32_t r0[32], r1[32], r2[32], r3[32];
+                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(c * 32);
+                tmem_ld_32x32b_x32(ta, r0);
+                tmem_ld_32x32b_x32(ta + OZ_BN, r1);
+                tmem_ld_32x32b_x32(ta + 2 * OZ_BN, r2);
+                tmem_ld_32x32b_x32(ta + 3 * OZ_BN, r3);
+                tmem_ld_wait();
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) {
+                    const int j = n0 + c * 32 + jj;
+                    const float s = (j < p.N) ? sA * p.sb[j] : 0.0f;
+                    const float hi = __uint_as_float(r0[jj]);
+                    const float lo = (__uint_as_float(r1[jj]) + __uint_as_float(r2[jj])) + __uint_as_float(r3[jj]);
+                    const float sh = hi + lo;
+                    const float bb = sh - hi;
+                    const float sl = (hi - (sh - bb)) + (lo - bb);
+                    T[il * TLD + c * 32 + jj] = f2d_bits(sh * s) + f2d_bits(sl * s);
+                }
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            const double alpha = p.alpha;
+            // rows q, q+4, ..., in batches of 8 rows x 4 column groups: 32 independent
+            // addend loads in flight per thread
+            for (int rb = 0; rb < OZ_BM / 4; rb += 8) {
+                double a1[8][OZ_BN / 32], a2[8][OZ_BN / 32];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int gi = m0 + q + 4 * (rb + u);
+#pragma unroll
+                    for (int h = 0; h < OZ_BN / 32; ++h) {
+                        const int gj = n0 + lane + 32 * h;
+                        const bool in = gi < p.M && gj < p.N;
+                        const size_t off = (size_t)gi * p.ldc + gj;
+                        a1[u][h] = (in && p.D1) ? p.D1[off] : 0.0;
+                        a2[u][h] = (in && p.D2) ? p.D2[off] : 0.0;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int r = q + 4 * (rb + u);
+                    const int gi = m0 + r;
+                    if (gi >= p.M) continue;
+#pragma unroll
+                    for (int h = 0; h < OZ_BN / 32; ++h) {
+                        const int cc = lane + 32 * h;
+                        const int gj = n0 + cc;
+                        if (gj >= p.N || (p.tri && gi > gj)) continue;
+                        const size_t off = (size_t)gi * p.ldc + gj;
+                        double v = T[r * TLD + cc];
+                        if (alpha != 1.0) v *= alpha;
+                        if (p.D1) v += p.b1 * a1[u][h];
+                        if (p.D2) v += p.b2 * a2[u][h];
                         if (p.D3) v += p.b3 * p.D3[off];
                         p.Cd[off] = v;
-                        if (p.tri && i != j) p.Cd[(size_t)j * p.ldc + i] = v;
+                        T[r * TLD + cc] = v;
+                    }
+                }
+            }
+            if (p.tri) {
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                for (int cc = q; cc < OZ_BN; cc += 4) {
+                    const int gj = n0 + cc;
+                    if (gj >= p.N) continue;
+#pragma unroll
+                    for (int h = 0; h < OZ_BM / 32; ++h) {
+                        const int r = lane + 32 * h;
+                        const int gi = m0 + r;
+                        if (gi >= p.M || gi >= gj) continue;
+                        p.Cd[(size_t)gj * p.ldc + gi] = T[r * TLD + cc];
                     }
                 }
             }
@@ -389,6 +486,27 @@ __global__ void __launch_bounds__(192, 1) ozaki_gemm_kernel(const __grid_constan
     __syncthreads();
     fence_after_sync();
     if (warp == 1) tmem_dealloc(tmem, 512);
+}
+
+__global__ void __launch_bounds__(192, 1) ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                             const __grid_constant__ CUtensorMap tmB,
+                                                             const OzParams p) {
+    oz_gemm_tile(&tmA, &tmB, p, blockIdx.x);
+}
+
+// Grouped form: the tiles of every problem laid end to end; a CTA finds its
+// problem by binary search over the start offsets and reads that problem's
+// tensor maps from global memory.  A tile is computed exactly as in the
+// single-problem kernel.
+__global__ void __launch_bounds__(192, 1) ozaki_gemm_grouped_kernel(const OzGroupDesc* __restrict__ d, int nd) {
+    const int b = blockIdx.x;
+    int lo = 0, hi = nd - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d[mid].start <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    oz_gemm_tile(&d[lo].tmA, &d[lo].tmB, d[lo].p, b - d[lo].start);
 }
 
 // ============================================================== host side
@@ -452,6 +570,37 @@ dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzPar
     p.tiles_n = tnt;
     const int grid = p.tri ? tnt * (tnt + 1) / 2 : tmt * tnt;
     ozaki_gemm_kernel<<<grid, 192, OZ_SMEM_BYTES, st>>>(tA, tB, p);
+    DME_CUDA_TRY(cudaGetLastError());
+    return DME_OK;
+}
+
+static bool g_attr_grouped_set = false;
+
+dme_status launch_ozaki_grouped(std::vector<OzGroupDesc>& items, OzGroupDesc* dev_desc, cudaStream_t st) {
+    int total = 0;
+    std::vector<OzGroupDesc> live;
+    for (auto& it : items) {
+        OzParams& p = it.p;
+        if (p.M <= 0 || p.N <= 0) continue;
+        if (p.Kp % OZ_BK != 0 || p.Kp > OZ_MAX_K || (p.tri && p.M != p.N)) {
+            set_error("ozaki grouped gemm: bad problem shape");
+            return DME_EINVAL;
+        }
+        const int tmt = (p.M + OZ_BM - 1) / OZ_BM, tnt = (p.N + OZ_BN - 1) / OZ_BN;
+        p.tiles_n = tnt;
+        it.start = total;
+        total += p.tri ? tnt * (tnt + 1) / 2 : tmt * tnt;
+        live.push_back(it);
+    }
+    if (total == 0) return DME_OK;
+    if (!g_attr_grouped_set) {
+        DME_CUDA_TRY(cudaFuncSetAttribute(ozaki_gemm_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          OZ_SMEM_BYTES));
+        g_attr_grouped_set = true;
+    }
+    DME_CUDA_TRY(cudaMemcpyAsync(dev_desc, live.data(), live.size() * sizeof(OzGroupDesc), cudaMemcpyHostToDevice,
+                                 st));
+    ozaki_gemm_grouped_kernel<<<total, 192, OZ_SMEM_BYTES, st>>>(dev_desc, (int)live.size());
     DME_CUDA_TRY(cudaGetLastError());
     return DME_OK;
 }

@@ -563,7 +563,12 @@ size_t dme::plan_estimate_bytes(const dme_plan_desc& d) {
     taus = std::max(taus, 1);
     const size_t persistent = (3 + 2 * (size_t)taus + 3) * nn;           // A, Q, X, (E, W) per t, S-flow work
     const size_t transient = 17 * nn;                                   // Pade chain blocks and LU copies
-    return persistent + transient + (size_t)d.n * 64 * sizeof(double) + (1u << 20);
+    size_t split = 0;
+    if (d.prec == DME_SPLIT_BF16) {
+        const size_t sl = (size_t)d.n * slice_kpad(d.n) * 2;           // one bf16 slice plane
+        split = (5 * (size_t)taus + 5 + 8) * sl + nn;                   // E^T / S slices, P and U slices, U pairs
+    }
+    return persistent + transient + split + (size_t)d.n * 64 * sizeof(double) + (1u << 20);
 }
 
 namespace {

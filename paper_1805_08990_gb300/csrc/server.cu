@@ -8,9 +8,10 @@
 //  * the stepper thread owns the resident requests and runs scheduler rounds:
 //    each round advances every resident request by one composition step.  The
 //    ops of all residents are executed stage by stage with grouped kernels:
-//    one grouped FP64 GEMM launch per congruence phase (P E, then E^T X with
-//    the W/tQ epilogue) and one grouped launch per Riccati kernel, covering all
-//    residents at that stage.  Requests admitted between rounds join the next
+//    one grouped GEMM launch per congruence phase (FP64: P E, then E^T X with
+//    the W/tQ epilogue; split precision: the tcgen05 slice GEMMs G P and G U^T
+//    with the slicing of P and U in between) and one grouped launch per
+//    Riccati kernel, covering all residents at that stage.  Requests admitted between rounds join the next
 //    round; finished ones leave after it.
 // Grouped kernels compute each problem's tiles exactly as they would alone
 // (no cross-request reduction), so a result is bit-identical alone or in a mix.
@@ -78,6 +79,7 @@ struct dme_server_s {
     int* dstat = nullptr;         // per-slot device status words
     void* gdesc = nullptr;        // grouped GEMM descriptors
     void* rdesc = nullptr;        // grouped Riccati descriptors
+    OzGroupDesc* odesc = nullptr; // grouped split-GEMM descriptors (2 x max_slots)
     std::vector<double> lat_ms;
     int completed = 0, failed = 0, rounds = 0;
     double t_first = -1, t_last = 0;
@@ -180,12 +182,15 @@ dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
     for (size_t k = 0; k < stages; ++k) {
         std::vector<GemmProb> g1, g2;
         std::vector<RicItem> ric;
+        std::vector<Req*> sc;                          // split-precision congruences at this stage
         for (Req* r : res) {
             if (k >= r->plan->ops.size()) continue;
             const Op& o = r->plan->ops[k];
             dme_plan_t p = r->plan;
             const int n = p->n;
-            if (o.kind == OP_CONG) {
+            if (o.kind == OP_CONG && p->split) {
+                sc.push_back(r);
+            } else if (o.kind == OP_CONG) {
                 const EWEntry& e = p->ew[o.ew];
                 GemmProb a;
                 std::memset(&a, 0, sizeof(a));
@@ -229,6 +234,57 @@ dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
             DME_TRY(gemm64_grouped(g1, reinterpret_cast<GemmProb*>(s->gdesc), s->st));
             DME_TRY(gemm64_grouped(g2, reinterpret_cast<GemmProb*>(s->gdesc) + s->max_slots, s->st));
         }
+        if (!sc.empty()) {
+            // the split congruence G P G^T of every request: slice P, grouped U = G P,
+            // slice U, grouped G U^T (upper tiles, FP64 + W / tQ, mirrored)
+            std::vector<OzGroupDesc> o1, o2;
+            for (Req* r : sc) {
+                dme_plan_t p = r->plan;
+                const Op& o = p->ops[k];
+                const EWEntry& e = p->ew[o.ew];
+                const int n = p->n;
+                launch_slice_rows_f64(r->P, n, n, n, p->psl, s->st);
+                OzGroupDesc a;
+                std::memset(&a, 0, sizeof(a));
+                a.tmA = e.Gsl.tmap;
+                a.tmB = p->psl.tmap;
+                a.p.M = a.p.N = n;
+                a.p.Kp = e.Gsl.Kp;
+                a.p.sa = e.Gsl.scale;
+                a.p.sb = p->psl.scale;
+                a.p.mode = OZ_OUT_PAIR;
+                a.p.ldc = n;
+                a.p.Cp = p->U;
+                a.p.status = s->dstat + r->slot;
+                o1.push_back(a);
+                OzGroupDesc b;
+                std::memset(&b, 0, sizeof(b));
+                b.tmA = e.Gsl.tmap;
+                b.tmB = p->usl.tmap;
+                b.p.M = b.p.N = n;
+                b.p.Kp = e.Gsl.Kp;
+                b.p.sa = e.Gsl.scale;
+                b.p.sb = p->usl.scale;
+                b.p.mode = OZ_OUT_F64;
+                b.p.tri = 1;
+                b.p.ldc = n;
+                b.p.Cd = r->P;
+                b.p.alpha = 1.0;
+                if (o.wcoef != 0.0) {
+                    b.p.D1 = e.W;
+                    b.p.b1 = o.wcoef;
+                }
+                if (o.qcoef != 0.0) {
+                    b.p.D2 = p->Q;
+                    b.p.b2 = o.qcoef;
+                }
+                b.p.status = s->dstat + r->slot;
+                o2.push_back(b);
+            }
+            DME_TRY(launch_ozaki_grouped(o1, s->odesc, s->st));
+            for (Req* r : sc) launch_slice_rows_pair(r->plan->U, r->plan->n, r->plan->n, r->plan->n, r->plan->usl, s->st);
+            DME_TRY(launch_ozaki_grouped(o2, s->odesc + s->max_slots, s->st));
+        }
         if (!ric.empty()) DME_TRY(launch_riccati_grouped(ric, s->rdesc, s->st));
         // descriptors are uploaded per launch from host memory: wait before the next stage reuses them
         DME_CUDA_TRY(cudaStreamSynchronize(s->st));
@@ -265,7 +321,8 @@ void step_loop(dme_server_t s) {
             std::string rerr = err;
             if (rs == DME_OK && hstat[r->slot]) {
                 rs = (hstat[r->slot] & DEV_NOTSPD) ? DME_ENOTSPD : DME_ECUDA;
-                rerr = "serving: I_m + t Bt^T P Bt is not positive definite";
+                rerr = (rs == DME_ENOTSPD) ? "serving: I_m + t Bt^T P Bt is not positive definite"
+                                           : "serving: device status " + std::to_string(hstat[r->slot]);
                 cudaMemsetAsync(s->dstat + r->slot, 0, sizeof(int), s->st);
             }
             if (rs == DME_OK) r->done_steps++;
@@ -311,6 +368,7 @@ dme_status dme_server_create(size_t hbm_budget_bytes, int max_slots, dme_server_
     if (e == cudaSuccess) e = cudaMemset(s->dstat, 0, sizeof(int) * max_slots);
     if (e == cudaSuccess) e = cudaMalloc(&s->gdesc, sizeof(GemmProb) * 2 * max_slots);
     if (e == cudaSuccess) e = cudaMalloc(&s->rdesc, riccati_desc_bytes() * max_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&s->odesc, sizeof(OzGroupDesc) * 2 * max_slots);
     if (e != cudaSuccess) {
         set_error(std::string("dme_server_create: ") + cudaGetErrorString(e));
         cudaGetLastError();
@@ -318,6 +376,7 @@ dme_status dme_server_create(size_t hbm_budget_bytes, int max_slots, dme_server_
         cudaFree(s->dstat);
         cudaFree(s->gdesc);
         cudaFree(s->rdesc);
+        cudaFree(s->odesc);
         delete s;
         return DME_ECUDA;
     }
@@ -332,7 +391,8 @@ dme_status dme_submit(dme_server_t s, const dme_plan_desc* desc, const double* A
                       uint64_t* ticket) {
     if (!s || !desc || !A || !QorC || !P0 || !ticket) return set_error("missing argument"), DME_EINVAL;
     if (!(T > 0.0) || nsteps < 1) return set_error("need T > 0 and nsteps >= 1"), DME_EINVAL;
-    if (desc->prec != DME_FP64) return set_error("serving runs the FP64 path"), DME_EINVAL;
+    if (desc->prec != DME_FP64 && desc->prec != DME_SPLIT_BF16) return set_error("bad prec"), DME_EINVAL;
+    if (desc->prec == DME_SPLIT_BF16 && desc->n > 4096) return set_error("split serving needs n <= 4096"), DME_EINVAL;
     for (int i = 0; i < desc->nflows; ++i)
         if (desc->flows[i] == DME_F4) return set_error("serving supports DLE/DRE schemes (no F4)"), DME_EINVAL;
     try {
@@ -433,6 +493,7 @@ dme_status dme_server_destroy(dme_server_t s) {
     cudaFree(s->dstat);
     cudaFree(s->gdesc);
     cudaFree(s->rdesc);
+    cudaFree(s->odesc);
     cudaStreamDestroy(s->st);
     delete s;
     return DME_OK;

@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "dme_internal.h"
 
 namespace dme {
@@ -41,6 +43,14 @@ struct OzParams {
     int* status;
 };
 
+// One problem of a grouped split GEMM (tensor maps live in global memory).
+struct OzGroupDesc {
+    CUtensorMap tmA;
+    CUtensorMap tmB;
+    OzParams p;
+    int start;            // first tile index (set by the launcher)
+};
+
 int slice_kpad(int k);
 size_t slice_buf_bytes(int rows, int k, int ns);
 dme_status make_slice_tmap(const SliceBuf& sb, CUtensorMap* out);
@@ -48,5 +58,7 @@ dme_status make_slice_tmap(const SliceBuf& sb, CUtensorMap* out);
 void launch_slice_rows_f64(const double* X, int rows, int cols, int ldx, const SliceBuf& sb, cudaStream_t st);
 void launch_slice_rows_pair(const float2* Xp, int rows, int cols, int ldx, const SliceBuf& sb, cudaStream_t st);
 dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzParams p, cudaStream_t st);
+// Grouped launch over independent problems; dev_desc holds items.size() descriptors.
+dme_status launch_ozaki_grouped(std::vector<OzGroupDesc>& items, OzGroupDesc* dev_desc, cudaStream_t st);
 
 }  // namespace dme

@@ -13,7 +13,7 @@ import torch
 import dme_workloads as W
 import oracle as O
 import paper_1805_08990_gb300 as dme
-from gpu_util import FP64_TOL, dev, rel, require_gpu
+from gpu_util import FP64_TOL, SPLIT_TOL, dev, rel, require_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -23,16 +23,16 @@ def _gpu():
     require_gpu()
 
 
-def _desc(pr, nsteps, flows=("F12", "F3")):
+def _desc(pr, nsteps, flows=("F12", "F3"), prec="fp64"):
     ric = "F3" in flows
     return dme.make_desc(pr.n, m=pr.B.shape[1] if ric else 0, p=pr.C.shape[0],
                          eq=dme.DME_DRE if ric else dme.DME_DLE, comp="strang", flows=flows,
-                         h=pr.T / nsteps, q_is_factor=True)
+                         h=pr.T / nsteps, q_is_factor=True, prec=prec)
 
 
-def _submit(srv, pr, nsteps, flows=("F12", "F3")):
+def _submit(srv, pr, nsteps, flows=("F12", "F3"), prec="fp64"):
     ric = "F3" in flows
-    return dme.dme_submit(srv, _desc(pr, nsteps, flows), pr.A, pr.C, pr.B if ric else None,
+    return dme.dme_submit(srv, _desc(pr, nsteps, flows, prec), pr.A, pr.C, pr.B if ric else None,
                           pr.R if ric else None, None, pr.P0, pr.T, nsteps)
 
 
@@ -135,10 +135,30 @@ def test_failed_request_is_reported_and_server_keeps_serving(server):
     assert st["failed"] >= 1
 
 
+def test_split_precision_requests_in_a_mix(server):
+    """Split-precision requests (grouped tcgen05 GEMMs) beside FP64 ones: each
+    matches the oracle at its bar, and the split ones equal the single-plan
+    split path bit for bit."""
+    reqs = _requests()
+    precs = ["split_bf16" if i % 2 == 0 else "fp64" for i in range(len(reqs))]
+    tickets = [_submit(server, pr, N, prec=pc) for (pr, N), pc in zip(reqs, precs)]
+    for (pr, N), pc, tk in zip(reqs, precs, tickets):
+        s, got = _poll(server, tk, pr.n)
+        assert s == dme.DME_OK
+        ref = O.solve(pr.A, pr.Q, pr.P0, pr.T, N, "strang", ["F12", "F3"], B=pr.B, R=pr.R)
+        assert rel(got, ref) < (SPLIT_TOL if pc == "split_bf16" else FP64_TOL)
+        if pc == "split_bf16":
+            plan = dme.Plan(dev(pr.A), C=dev(pr.C), h=pr.T / N, flows=["F12", "F3"], B=dev(pr.B), R=dev(pr.R),
+                            prec="split_bf16")
+            single = np.empty((pr.n, pr.n))
+            plan.solve(pr.P0, pr.T, N, single)
+            assert np.array_equal(got, single)
+
+
 def test_submit_rejections(server):
     pr = W.dre_convdiff(nx=5)
     d = _desc(pr, 4)
-    d.prec = dme.DME_SPLIT_BF16
+    d.prec = 7
     with pytest.raises(dme.DmeError):
         dme.dme_submit(server, d, pr.A, pr.C, pr.B, pr.R, None, pr.P0, pr.T, 4)
     with pytest.raises(dme.DmeError):
