@@ -19,12 +19,13 @@
 // two-float (hi = level 0, exact; lo = levels 1-4) and scales by
 // sigma_A,i sigma_B,j.
 //
-// Kernel shape: one CTA per 128 x 128 output tile, 6 warps:
+// Kernel shape: one CTA per 128 x 128 output tile, 10 warps:
 //   warp 0  TMA producer (one thread): 3-stage ring, each stage holds the 5
 //           slices of a 128 x 32 A tile and the 4 slices of a 128 x 32 B tile
 //           (72 KB, 64-byte swizzled rows),
 //   warp 1  TMEM allocator + MMA issuer (one thread): 28 tcgen05.mma per stage,
-//   warps 2-5 epilogue: tcgen05.ld of the 4 accumulators (512 TMEM columns).
+//   warps 2-9 epilogue: tcgen05.ld of the 4 accumulators (512 TMEM columns),
+//           two warps per TMEM lane quadrant, each on half of the tile's columns.
 // Both operands are K-major (row-major with K contiguous):
 //   C[i][j] = sum_k A[i][k] B[j][k].
 #include "dme_internal.h"
@@ -52,6 +53,9 @@ constexpr int OZ_SMEM_BYTES = OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256;
 constexpr int OZ_MAX_LEVEL = 4;                                   // pairs with s + t <= 4
 constexpr int OZ_NACC = 4;                                        // accumulators: levels 0, 1, 2, 3+4
 constexpr uint64_t OZ_TIMEOUT_NS = 2000000000ull;             // 2 s per wait
+constexpr int OZ_EPI_WARPS = 8;                                  // two per TMEM lane quadrant
+constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;               // producer + MMA warps + epilogue
+constexpr int OZ_EPI_COLS = OZ_BN / (OZ_EPI_WARPS / 4);          // columns per epilogue warp
 constexpr uint32_t OZ_IDESC = idesc_bf16_f32(OZ_BM, OZ_BN);
 
 // ============================================================== slicing
@@ -350,17 +354,20 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap* tmA, const CUten
             mma_commit(smem_u32(&bars[2 * OZ_STAGES]));
         }
     } else {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 = tile rows
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 = tile rows, columns
+        // [cq, cq + OZ_EPI_COLS) with cq = OZ_EPI_COLS * ((w - 2) / 4)
         const int q = warp & 3;
+        const int ew = warp - 2;                                   // 0 .. OZ_EPI_WARPS-1
+        const int cq = OZ_EPI_COLS * (ew / 4);
         const int i = m0 + 32 * q + lane;
         const bool ready_here = mbar_wait(smem_u32(&bars[2 * OZ_STAGES]), 0, OZ_TIMEOUT_NS);
-        // one decision for all 128 epilogue threads (they share named barrier 1 below)
+        // one decision for all epilogue threads (they share named barrier 1 below)
         uint32_t all_ready;
         asm volatile(
             "{\n"
             " .reg .pred p, r;\n"
             " setp.ne.u32 p, %1, 0;\n"
-            " bar.red.and.pred r, 1, 128, p;\n"
+            " bar.red.and.pred r, 1, 256, p;\n"
             " selp.u32 %0, 1, 0, r;\n"
             "}\n"
             : "=r"(all_ready)
@@ -373,7 +380,7 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap* tmA, const CUten
         } else if (p.mode == OZ_OUT_PAIR) {
             const float sA = (i < p.M) ? p.sa[i] : 0.0f;
 #pragma unroll 1
-            for (int c = 0; c < OZ_BN / 32; ++c) {
+            for (int c = cq / 32; c < (cq + OZ_EPI_COLS) / 32; ++c) {
                 uint32_t r0[32], r1[32], r2[32], r3[32];
                 const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(c * 32);
                 tmem_ld_32x32b_x32(ta, r0);
@@ -407,7 +414,7 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap* tmA, const CUten
             const int il = 32 * q + lane;
             const float sA = (i < p.M) ? p.sa[i] : 0.0f;
 #pragma unroll 1
-            for (int c = 0; c < OZ_BN / 32; ++c) {
+            for (int c = cq / 32; c < (cq + OZ_EPI_COLS) / 32; ++c) {
                 uint32_t r0[32], r1[32], r2[32], r3[32];
                 const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(c * 32);
                 tmem_ld_32x32b_x32(ta, r0);
@@ -427,15 +434,15 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap* tmA, const CUten
                     T[il * TLD + c * 32 + jj] = f2d_bits(sh * s) + f2d_bits(sl * s);
                 }
             }
-            asm volatile("bar.sync 1, 128;" ::: "memory");
+            asm volatile("bar.sync 1, 256;" ::: "memory");
             const double alpha = p.alpha;
-            // rows q, q+4, ..., in batches of 8 rows x 4 column groups: 32 independent
-            // addend loads in flight per thread
-            for (int rb = 0; rb < OZ_BM / 4; rb += 8) {
-                double a1[8][OZ_BN / 32], a2[8][OZ_BN / 32];
+            // rows ew, ew+8, ..., in batches of 4 rows x 4 column groups (the whole tile width):
+            // 16 independent addend loads in flight per thread
+            for (int rb = 0; rb < OZ_BM / OZ_EPI_WARPS; rb += 4) {
+                double a1[4][OZ_BN / 32], a2[4][OZ_BN / 32];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int gi = m0 + q + 4 * (rb + u);
+                for (int u = 0; u < 4; ++u) {
+                    const int gi = m0 + ew + OZ_EPI_WARPS * (rb + u);
 #pragma unroll
                     for (int h = 0; h < OZ_BN / 32; ++h) {
                         const int gj = n0 + lane + 32 * h;
@@ -446,8 +453,8 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap* tmA, const CUten
                     }
                 }
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int r = q + 4 * (rb + u);
+                for (int u = 0; u < 4; ++u) {
+                    const int r = ew + OZ_EPI_WARPS * (rb + u);
                     const int gi = m0 + r;
                     if (gi >= p.M) continue;
 #pragma unroll
@@ -467,8 +474,8 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap* tmA, const CUten
                 }
             }
             if (p.tri) {
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-                for (int cc = q; cc < OZ_BN; cc += 4) {
+                asm volatile("bar.sync 1, 256;" ::: "memory");
+                for (int cc = ew; cc < OZ_BN; cc += OZ_EPI_WARPS) {
                     const int gj = n0 + cc;
                     if (gj >= p.N) continue;
 #pragma unroll
@@ -488,7 +495,7 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap* tmA, const CUten
     if (warp == 1) tmem_dealloc(tmem, 512);
 }
 
-__global__ void __launch_bounds__(192, 1) ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                              const __grid_constant__ CUtensorMap tmB,
                                                              const OzParams p) {
     oz_gemm_tile(&tmA, &tmB, p, blockIdx.x);
@@ -498,7 +505,7 @@ __global__ void __launch_bounds__(192, 1) ozaki_gemm_kernel(const __grid_constan
 // problem by binary search over the start offsets and reads that problem's
 // tensor maps from global memory.  A tile is computed exactly as in the
 // single-problem kernel.
-__global__ void __launch_bounds__(192, 1) ozaki_gemm_grouped_kernel(const OzGroupDesc* __restrict__ d, int nd) {
+__global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_gemm_grouped_kernel(const OzGroupDesc* __restrict__ d, int nd) {
     const int b = blockIdx.x;
     int lo = 0, hi = nd - 1;
     while (lo < hi) {
@@ -569,7 +576,7 @@ dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzPar
     const int tmt = (p.M + OZ_BM - 1) / OZ_BM, tnt = (p.N + OZ_BN - 1) / OZ_BN;
     p.tiles_n = tnt;
     const int grid = p.tri ? tnt * (tnt + 1) / 2 : tmt * tnt;
-    ozaki_gemm_kernel<<<grid, 192, OZ_SMEM_BYTES, st>>>(tA, tB, p);
+    ozaki_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM_BYTES, st>>>(tA, tB, p);
     DME_CUDA_TRY(cudaGetLastError());
     return DME_OK;
 }
@@ -600,7 +607,7 @@ dme_status launch_ozaki_grouped(std::vector<OzGroupDesc>& items, OzGroupDesc* de
     }
     DME_CUDA_TRY(cudaMemcpyAsync(dev_desc, live.data(), live.size() * sizeof(OzGroupDesc), cudaMemcpyHostToDevice,
                                  st));
-    ozaki_gemm_grouped_kernel<<<total, 192, OZ_SMEM_BYTES, st>>>(dev_desc, (int)live.size());
+    ozaki_gemm_grouped_kernel<<<total, OZ_THREADS, OZ_SMEM_BYTES, st>>>(dev_desc, (int)live.size());
     DME_CUDA_TRY(cudaGetLastError());
     return DME_OK;
 }
