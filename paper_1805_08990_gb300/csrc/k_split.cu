@@ -249,7 +249,7 @@ __device__ __forceinline__ double f2d_bits(float f) {
 // One 128 x 128 output tile (index t of problem p) by one CTA; tmA / tmB are
 // the addresses of the tensor maps (kernel parameters or global memory).
 __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap* tmA, const CUtensorMap* tmB, const OzParams& p,
-                                             int t) {
+                                             int t, int part, int nparts, int widx) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OZ_STAGES * OZ_STAGE_BYTES);
@@ -260,7 +260,9 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap* tmA, const CUten
     int tm, tn;
     oz_tile_coords(p, t, tm, tn);
     const int m0 = tm * OZ_BM, n0 = tn * OZ_BN;
-    const int nk = p.Kp / OZ_BK;
+    const int nk_all = p.Kp / OZ_BK;
+    const int kb0 = part * nk_all / nparts;                 // this CTA's K blocks [kb0, kb0 + nk)
+    const int nk = (part + 1) * nk_all / nparts - kb0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < OZ_STAGES; ++s) {
@@ -287,10 +289,11 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap* tmA, const CUten
         if (lane == 0) {
             int issued[OZ_STAGES] = {0, 0, 0};
             bool ok = true;
-            for (int kb = 0; kb < nk && ok; ++kb) {
-                const int s = kb % OZ_STAGES;
-                const uint32_t ph = (kb / OZ_STAGES) & 1;
-                if (kb >= OZ_STAGES && !mbar_wait(smem_u32(&bars[OZ_STAGES + s]), ph ^ 1, OZ_TIMEOUT_NS)) {
+            for (int it = 0; it < nk && ok; ++it) {
+                const int kb = kb0 + it;
+                const int s = it % OZ_STAGES;
+                const uint32_t ph = (it / OZ_STAGES) & 1;
+                if (it >= OZ_STAGES && !mbar_wait(smem_u32(&bars[OZ_STAGES + s]), ph ^ 1, OZ_TIMEOUT_NS)) {
                     ok = false;
                     break;
                 }
@@ -302,9 +305,10 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap* tmA, const CUten
                 issued[s]++;
                 // spread over the K loop: pull the epilogue's addend rows (full 128-column
                 // segments only, all in bounds) into L2, one row per k block
-                if (p.mode == OZ_OUT_F64 && kb < OZ_BM && m0 + kb < p.M && n0 + OZ_BN <= p.N &&
+                const int pr = it * nparts + part;
+                if (p.mode == OZ_OUT_F64 && pr < OZ_BM && m0 + pr < p.M && n0 + OZ_BN <= p.N &&
                     (p.ldc % 2) == 0) {
-                    const size_t off = (size_t)(m0 + kb) * p.ldc + n0;
+                    const size_t off = (size_t)(m0 + pr) * p.ldc + n0;
                     // the bulk prefetch needs a 16-byte aligned start (addends may be caller memory)
                     if (p.D1 && ((reinterpret_cast<uintptr_t>(p.D1 + off) & 15) == 0))
                         prefetch_l2_bulk(p.D1 + off, OZ_BN * sizeof(double));
@@ -321,9 +325,9 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap* tmA, const CUten
     } else if (warp == 1) {
         if (lane == 0) {
             bool ok = true;
-            for (int kb = 0; kb < nk; ++kb) {
-                const int s = kb % OZ_STAGES;
-                const uint32_t ph = (kb / OZ_STAGES) & 1;
+            for (int it = 0; it < nk; ++it) {
+                const int s = it % OZ_STAGES;
+                const uint32_t ph = (it / OZ_STAGES) & 1;
                 if (!mbar_wait(smem_u32(&bars[s]), ph, OZ_TIMEOUT_NS)) {
                     ok = false;
                     break;
@@ -343,7 +347,7 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap* tmA, const CUten
                             const uint64_t bd = desc_kmajor_sw64(b0 + sb * OZ_SLICE_BYTES + kk * 32);
                             // the pairs (0, t) come first for every accumulator t: at the very
                             // first k step they overwrite it, everything else accumulates
-                            const uint32_t acc = (kb == 0 && kk == 0 && sa == 0) ? 0u : 1u;
+                            const uint32_t acc = (it == 0 && kk == 0 && sa == 0) ? 0u : 1u;
                             mma_bf16(tmem + (uint32_t)(lvl * OZ_BN), ad, bd, OZ_IDESC, acc);
                         }
                     }
@@ -377,44 +381,11 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap* tmA, const CUten
         fence_after_sync();
         if (!ready) {
             if (lane == 0) atomicOr(p.status, DEV_TIMEOUT);
-        } else if (p.mode == OZ_OUT_PAIR) {
-            const float sA = (i < p.M) ? p.sa[i] : 0.0f;
-#pragma unroll 1
-            for (int c = cq / 32; c < (cq + OZ_EPI_COLS) / 32; ++c) {
-                uint32_t r0[32], r1[32], r2[32], r3[32];
-                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(c * 32);
-                tmem_ld_32x32b_x32(ta, r0);
-                tmem_ld_32x32b_x32(ta + OZ_BN, r1);
-                tmem_ld_32x32b_x32(ta + 2 * OZ_BN, r2);
-                tmem_ld_32x32b_x32(ta + 3 * OZ_BN, r3);
-                tmem_ld_wait();
-                if (i >= p.M) continue;
-#pragma unroll
-                for (int jj = 0; jj < 32; ++jj) {
-                    const int j = n0 + c * 32 + jj;
-                    if (j >= p.N) break;
-                    const float s = sA * p.sb[j];
-                    const float hi = __uint_as_float(r0[jj]);
-                    const float lo = (__uint_as_float(r1[jj]) + __uint_as_float(r2[jj])) + __uint_as_float(r3[jj]);
-                    // TwoSum: (sh, sl) = hi + lo exactly
-                    const float sh = hi + lo;
-                    const float bb = sh - hi;
-                    const float sl = (hi - (sh - bb)) + (lo - bb);
-                    p.Cp[(size_t)i * p.ldc + j] = make_float2(sh * s, sl * s);
-                }
-            }
         } else {
-            // FP64 output, staged through shared memory (the operand stages are idle now: every
-            // MMA has completed, so every TMA load they consumed has landed):
-            // (1) each thread converts its row of the tile into T[row][col];
-            // (2) the four warps write row segments of C coalesced, adding the addends;
-            // (3) for a symmetric output they write the mirror from T's columns, coalesced.
-            constexpr int TLD = OZ_BN + 1;
-            double* T = reinterpret_cast<double*>(smem);
-            const int il = 32 * q + lane;
-            const float sA = (i < p.M) ? p.sa[i] : 0.0f;
-#pragma unroll 1
-            for (int c = cq / 32; c < (cq + OZ_EPI_COLS) / 32; ++c) {
+            const int il = 32 * q + lane;                          // tile row of this thread
+            const size_t tile_elems = (size_t)OZ_BM * OZ_BN;
+            // level sums of 32 columns starting at c * 32: hi = level 0 (exact), lo = levels 1-4
+            auto tmem_chunk = [&](int c, float (&hv)[32], float (&lv)[32]) {
                 uint32_t r0[32], r1[32], r2[32], r3[32];
                 const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(c * 32);
                 tmem_ld_32x32b_x32(ta, r0);
@@ -424,66 +395,146 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap* tmA, const CUten
                 tmem_ld_wait();
 #pragma unroll
                 for (int jj = 0; jj < 32; ++jj) {
-                    const int j = n0 + c * 32 + jj;
-                    const float s = (j < p.N) ? sA * p.sb[j] : 0.0f;
-                    const float hi = __uint_as_float(r0[jj]);
-                    const float lo = (__uint_as_float(r1[jj]) + __uint_as_float(r2[jj])) + __uint_as_float(r3[jj]);
-                    const float sh = hi + lo;
-                    const float bb = sh - hi;
-                    const float sl = (hi - (sh - bb)) + (lo - bb);
-                    T[il * TLD + c * 32 + jj] = f2d_bits(sh * s) + f2d_bits(sl * s);
+                    hv[jj] = __uint_as_float(r0[jj]);
+                    lv[jj] = (__uint_as_float(r1[jj]) + __uint_as_float(r2[jj])) + __uint_as_float(r3[jj]);
                 }
-            }
-            asm volatile("bar.sync 1, 256;" ::: "memory");
-            const double alpha = p.alpha;
-            // rows ew, ew+8, ..., in batches of 4 rows x 4 column groups (the whole tile width):
-            // 16 independent addend loads in flight per thread
-            for (int rb = 0; rb < OZ_BM / OZ_EPI_WARPS; rb += 4) {
-                double a1[4][OZ_BN / 32], a2[4][OZ_BN / 32];
+            };
+            bool run_epilogue = true;
+            if (nparts > 1) {
+                // split K: publish this part's sums, count arrivals; the last part finishes
+                float2* mine = p.ws + ((size_t)widx * nparts + part) * tile_elems;
+#pragma unroll 1
+                for (int c = cq / 32; c < (cq + OZ_EPI_COLS) / 32; ++c) {
+                    float hv[32], lv[32];
+                    tmem_chunk(c, hv, lv);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int gi = m0 + ew + OZ_EPI_WARPS * (rb + u);
-#pragma unroll
-                    for (int h = 0; h < OZ_BN / 32; ++h) {
-                        const int gj = n0 + lane + 32 * h;
-                        const bool in = gi < p.M && gj < p.N;
-                        const size_t off = (size_t)gi * p.ldc + gj;
-                        a1[u][h] = (in && p.D1) ? p.D1[off] : 0.0;
-                        a2[u][h] = (in && p.D2) ? p.D2[off] : 0.0;
-                    }
+                    for (int jj = 0; jj < 32; ++jj) mine[(size_t)il * OZ_BN + c * 32 + jj] = make_float2(hv[jj], lv[jj]);
                 }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int r = ew + OZ_EPI_WARPS * (rb + u);
-                    const int gi = m0 + r;
-                    if (gi >= p.M) continue;
-#pragma unroll
-                    for (int h = 0; h < OZ_BN / 32; ++h) {
-                        const int cc = lane + 32 * h;
-                        const int gj = n0 + cc;
-                        if (gj >= p.N || (p.tri && gi > gj)) continue;
-                        const size_t off = (size_t)gi * p.ldc + gj;
-                        double v = T[r * TLD + cc];
-                        if (alpha != 1.0) v *= alpha;
-                        if (p.D1) v += p.b1 * a1[u][h];
-                        if (p.D2) v += p.b2 * a2[u][h];
-                        if (p.D3) v += p.b3 * p.D3[off];
-                        p.Cd[off] = v;
-                        T[r * TLD + cc] = v;
-                    }
-                }
-            }
-            if (p.tri) {
+                __threadfence();
                 asm volatile("bar.sync 1, 256;" ::: "memory");
-                for (int cc = ew; cc < OZ_BN; cc += OZ_EPI_WARPS) {
-                    const int gj = n0 + cc;
-                    if (gj >= p.N) continue;
+                volatile int* flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+                if (ew == 0 && lane == 0) *flag = atomicAdd(p.ws_cnt + widx, 1);
+                asm volatile("bar.sync 1, 256;" ::: "memory");
+                run_epilogue = (*flag == nparts - 1);
+                if (run_epilogue) {
+                    __threadfence();
+                    if (ew == 0 && lane == 0) p.ws_cnt[widx] = 0;    // ready for the next launch
+                }
+            }
+            // level sums of a chunk: from TMEM, or the parts' sums added in part order
+            auto chunk = [&](int c, float (&hv)[32], float (&lv)[32]) {
+                if (nparts == 1) {
+                    tmem_chunk(c, hv, lv);
+                    return;
+                }
+                const float2* base = p.ws + (size_t)widx * nparts * tile_elems + (size_t)il * OZ_BN + c * 32;
 #pragma unroll
-                    for (int h = 0; h < OZ_BM / 32; ++h) {
-                        const int r = lane + 32 * h;
+                for (int jj = 0; jj < 32; ++jj) {
+                    hv[jj] = 0.0f;
+                    lv[jj] = 0.0f;
+                }
+                for (int pp = 0; pp < nparts; ++pp) {
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj) {
+                        const float2 v = base[pp * tile_elems + jj];
+                        hv[jj] += v.x;
+                        lv[jj] += v.y;
+                    }
+                }
+            };
+            if (run_epilogue && p.mode == OZ_OUT_PAIR) {
+                const float sA = (i < p.M) ? p.sa[i] : 0.0f;
+#pragma unroll 1
+                for (int c = cq / 32; c < (cq + OZ_EPI_COLS) / 32; ++c) {
+                    float hv[32], lv[32];
+                    chunk(c, hv, lv);
+                    if (i >= p.M) continue;
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj) {
+                        const int j = n0 + c * 32 + jj;
+                        if (j >= p.N) break;
+                        const float s = sA * p.sb[j];
+                        // TwoSum: (sh, sl) = hi + lo exactly
+                        const float sh = hv[jj] + lv[jj];
+                        const float bb = sh - hv[jj];
+                        const float sl = (hv[jj] - (sh - bb)) + (lv[jj] - bb);
+                        p.Cp[(size_t)i * p.ldc + j] = make_float2(sh * s, sl * s);
+                    }
+                }
+            } else if (run_epilogue) {
+                // FP64 output, staged through shared memory (the operand stages are idle now: every
+                // MMA has completed, so every TMA load they consumed has landed):
+                // (1) each thread converts its row segment of the tile into T[row][col];
+                // (2) the epilogue warps write row segments of C coalesced, adding the addends;
+                // (3) for a symmetric output they write the mirror from T's columns, coalesced.
+                constexpr int TLD = OZ_BN + 1;
+                double* T = reinterpret_cast<double*>(smem);
+                const float sA = (i < p.M) ? p.sa[i] : 0.0f;
+#pragma unroll 1
+                for (int c = cq / 32; c < (cq + OZ_EPI_COLS) / 32; ++c) {
+                    float hv[32], lv[32];
+                    chunk(c, hv, lv);
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj) {
+                        const int j = n0 + c * 32 + jj;
+                        const float s = (j < p.N) ? sA * p.sb[j] : 0.0f;
+                        const float sh = hv[jj] + lv[jj];
+                        const float bb = sh - hv[jj];
+                        const float sl = (hv[jj] - (sh - bb)) + (lv[jj] - bb);
+                        T[il * TLD + c * 32 + jj] = f2d_bits(sh * s) + f2d_bits(sl * s);
+                    }
+                }
+                asm volatile("bar.sync 1, 256;" ::: "memory");
+                const double alpha = p.alpha;
+                // rows ew, ew+8, ..., in batches of 4 rows x 4 column groups (the whole tile width):
+                // 16 independent addend loads in flight per thread
+                for (int rb = 0; rb < OZ_BM / OZ_EPI_WARPS; rb += 4) {
+                    double a1[4][OZ_BN / 32], a2[4][OZ_BN / 32];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int gi = m0 + ew + OZ_EPI_WARPS * (rb + u);
+#pragma unroll
+                        for (int h = 0; h < OZ_BN / 32; ++h) {
+                            const int gj = n0 + lane + 32 * h;
+                            const bool in = gi < p.M && gj < p.N;
+                            const size_t off = (size_t)gi * p.ldc + gj;
+                            a1[u][h] = (in && p.D1) ? p.D1[off] : 0.0;
+                            a2[u][h] = (in && p.D2) ? p.D2[off] : 0.0;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int r = ew + OZ_EPI_WARPS * (rb + u);
                         const int gi = m0 + r;
-                        if (gi >= p.M || gi >= gj) continue;
-                        p.Cd[(size_t)gj * p.ldc + gi] = T[r * TLD + cc];
+                        if (gi >= p.M) continue;
+#pragma unroll
+                        for (int h = 0; h < OZ_BN / 32; ++h) {
+                            const int cc = lane + 32 * h;
+                            const int gj = n0 + cc;
+                            if (gj >= p.N || (p.tri && gi > gj)) continue;
+                            const size_t off = (size_t)gi * p.ldc + gj;
+                            double v = T[r * TLD + cc];
+                            if (alpha != 1.0) v *= alpha;
+                            if (p.D1) v += p.b1 * a1[u][h];
+                            if (p.D2) v += p.b2 * a2[u][h];
+                            if (p.D3) v += p.b3 * p.D3[off];
+                            p.Cd[off] = v;
+                            T[r * TLD + cc] = v;
+                        }
+                    }
+                }
+                if (p.tri) {
+                    asm volatile("bar.sync 1, 256;" ::: "memory");
+                    for (int cc = ew; cc < OZ_BN; cc += OZ_EPI_WARPS) {
+                        const int gj = n0 + cc;
+                        if (gj >= p.N) continue;
+#pragma unroll
+                        for (int h = 0; h < OZ_BM / 32; ++h) {
+                            const int r = lane + 32 * h;
+                            const int gi = m0 + r;
+                            if (gi >= p.M || gi >= gj) continue;
+                            p.Cd[(size_t)gj * p.ldc + gi] = T[r * TLD + cc];
+                        }
                     }
                 }
             }
@@ -498,7 +549,14 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap* tmA, const CUten
 __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                              const __grid_constant__ CUtensorMap tmB,
                                                              const OzParams p) {
-    oz_gemm_tile(&tmA, &tmB, p, blockIdx.x);
+    const int b = blockIdx.x;
+    if (p.split_parts <= 1 || b < p.split_first) {
+        oz_gemm_tile(&tmA, &tmB, p, b, 0, 1, 0);
+    } else {
+        const int j = b - p.split_first;
+        oz_gemm_tile(&tmA, &tmB, p, p.split_first + j / p.split_parts, j % p.split_parts, p.split_parts,
+                     j / p.split_parts);
+    }
 }
 
 // Grouped form: the tiles of every problem laid end to end; a CTA finds its
@@ -513,7 +571,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_gemm_grouped_kernel(const
         if (d[mid].start <= b) lo = mid;
         else hi = mid - 1;
     }
-    oz_gemm_tile(&d[lo].tmA, &d[lo].tmB, d[lo].p, b - d[lo].start);
+    oz_gemm_tile(&d[lo].tmA, &d[lo].tmB, d[lo].p, b - d[lo].start, 0, 1, 0);
 }
 
 // ============================================================== host side
@@ -575,7 +633,24 @@ dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzPar
     }
     const int tmt = (p.M + OZ_BM - 1) / OZ_BM, tnt = (p.N + OZ_BN - 1) / OZ_BN;
     p.tiles_n = tnt;
-    const int grid = p.tri ? tnt * (tnt + 1) / 2 : tmt * tnt;
+    const int tiles = p.tri ? tnt * (tnt + 1) / 2 : tmt * tnt;
+    // split K of the last partial wave in two when it fills at most half of the SMs:
+    // the wave then takes about half a tile time instead of a whole one
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        DME_CUDA_TRY(cudaGetDevice(&dev));
+        DME_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int tail = tiles % nsm;
+    p.split_parts = 1;
+    p.split_first = tiles;
+    if (p.ws && p.ws_cnt && tiles > nsm && tail > 0 && tail <= OZ_SPLIT_MAX_TAIL && tail <= nsm / 2 &&
+        p.Kp / OZ_BK >= 16) {
+        p.split_parts = 2;
+        p.split_first = tiles - tail;
+    }
+    const int grid = p.split_first + (tiles - p.split_first) * p.split_parts;
     ozaki_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM_BYTES, st>>>(tA, tB, p);
     DME_CUDA_TRY(cudaGetLastError());
     return DME_OK;

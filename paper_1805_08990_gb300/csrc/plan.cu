@@ -219,6 +219,8 @@ dme_status split_cong(dme_plan_t p, const double* P, const SliceBuf& G, double* 
     a.ldc = n;
     a.Cp = p->U;
     a.status = p->status;
+    a.ws = p->kws;
+    a.ws_cnt = p->kcnt;
     {
         ProfScope ps(p, DME_KIND_SPLIT_GEMM);
         DME_TRY(launch_ozaki_gemm(G.tmap, p->psl.tmap, a, st));
@@ -246,6 +248,8 @@ dme_status split_cong(dme_plan_t p, const double* P, const SliceBuf& G, double* 
     b.D3 = D3;
     b.b3 = b3;
     b.status = p->status;
+    b.ws = p->kws;
+    b.ws_cnt = p->kcnt;
     ProfScope ps(p, DME_KIND_SPLIT_GEMM);
     return launch_ozaki_gemm(G.tmap, p->usl.tmap, b, st);
 }
@@ -645,6 +649,11 @@ dme_status dme::plan_create(const dme_plan_desc* d, const double* A, const doubl
         DME_TRY(alloc_slices(p, &p->psl, n, n, OZ_SLICES_B));
         DME_TRY(alloc_slices(p, &p->usl, n, n, OZ_SLICES_B));
         DME_TRY(palloc_t(p, &p->U, nn));
+        if (n > 1536) {    // only then does a GEMM have a full wave of tiles (split K of the tail)
+            DME_TRY(palloc_t(p, &p->kws, OZ_SPLIT_WS_FLOAT2));
+            DME_TRY(palloc_t(p, &p->kcnt, (size_t)OZ_SPLIT_MAX_TAIL));
+            DME_CUDA_TRY(cudaMemsetAsync(p->kcnt, 0, sizeof(int) * OZ_SPLIT_MAX_TAIL, st));
+        }
         if (gen) {
             DME_TRY(alloc_slices(p, &p->Ssl, n, n, OZ_SLICES_A));
             launch_slice_rows_f64(p->S, n, n, n, p->Ssl, st);

@@ -56,6 +56,8 @@ struct dme_plan_s {
     bool split = false;
     SliceBuf psl, usl, Ssl;    // split path: slices of P, of U = G P, and of S
     float2* U = nullptr;       // split path: G P as normalised (hi, lo) pairs
+    float2* kws = nullptr;     // split path: split-K workspace of the tail tiles
+    int* kcnt = nullptr;       // split path: split-K arrival counters
     // profiling: CUDA-event pairs around launches made outside graph capture
     bool prof = false;
     std::vector<cudaEvent_t> evpool;

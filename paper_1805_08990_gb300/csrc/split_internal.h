@@ -41,7 +41,18 @@ struct OzParams {
     double b1, b2, b3;
     int tiles_n;          // set by the launcher
     int* status;
+    // split-K of the last partial wave (single-problem launches only): tiles with index
+    // >= split_first run as split_parts CTAs over consecutive K ranges; each writes its
+    // level sums to ws and the last to arrive (counter in ws_cnt) adds them in part order
+    // and runs the epilogue.  ws: [tail tile][part][128 x 128] (level 0, levels 1-4).
+    float2* ws;
+    int* ws_cnt;
+    int split_first;      // set by the launcher
+    int split_parts;      // set by the launcher (1: no split)
 };
+
+constexpr int OZ_SPLIT_MAX_TAIL = 76;     // tail tiles that may be split (half of 152 SMs)
+constexpr size_t OZ_SPLIT_WS_FLOAT2 = (size_t)OZ_SPLIT_MAX_TAIL * 2 * 128 * 128;
 
 // One problem of a grouped split GEMM (tensor maps live in global memory).
 struct OzGroupDesc {

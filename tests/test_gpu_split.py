@@ -147,3 +147,20 @@ def test_split_rejects_n_above_4096():
     d = dme.make_desc(4097, eq=dme.DME_DLE, flows=("F12",), h=0.1, prec="split_bf16", q_is_factor=True, p=1)
     with pytest.raises(dme.DmeError):
         dme.dme_plan(d, A, A)
+
+
+def test_split_k_tail_tiles_match_oracle_and_repeat():
+    """n = 1664: the full GEMM has 169 tiles, so its last 17 run split in two
+    K halves whose sums meet in a workspace; the result must match the oracle
+    and repeat bit for bit."""
+    n = 1664
+    pr = _problem(n, seed=4)
+    tau = 0.01
+    plan = plan_for(pr, ["F12", "F3"], "strang", tau, prec="split_bf16")
+    P0 = W.random_psd(n, 21, rank=32)
+    P1, P2 = dev(P0), dev(P0)
+    plan.apply("F12", tau, P1)
+    plan.apply("F12", tau, P2)
+    assert torch.equal(P1, P2)
+    E, Wm = O.van_loan(pr.A, pr.Q, tau)
+    assert rel(host(P1), O.flow_T12(P0, E, Wm)) < SPLIT_TOL
