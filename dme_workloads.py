@@ -22,7 +22,7 @@ import numpy as np
 __all__ = [
     "laplacian_2d", "convection_diffusion_2d", "zero_pad", "Problem",
     "dle_heat", "dre_convdiff", "gdre_convdiff_padded", "dre_heat_large",
-    "random_psd", "serving_requests", "materialize", "SCHEMES",
+    "random_psd", "serving_requests", "materialize", "fe_heat_mass", "SCHEMES",
 ]
 
 
@@ -83,6 +83,7 @@ SCHEMES = {
     "F12F3": ["F12", "F3"], "F1F2F3": ["F1", "F2", "F3"], "F1F3F2": ["F1", "F3", "F2"],
     "F12F4": ["F12", "F4"], "F1F2F4": ["F1", "F2", "F4"], "F1F4F2": ["F1", "F4", "F2"],
     "F12F3F4": ["F12", "F3", "F4"], "F12F4F3": ["F12", "F4", "F3"],
+    "F1F2F3F4": ["F1", "F2", "F3", "F4"],
 }
 
 
@@ -158,6 +159,30 @@ def dre_heat_large(nx: int = 64, m: int = 8, p: int = 8, T: float = 1.0, seed: i
     C = rng.uniform(0.0, 1.0, size=(p, n))
     return Problem("dre_heat_large", A, C, np.zeros((n, n)), T, B=B, R=np.eye(m),
                    meta={"nx": nx, "seed": seed})
+
+
+def fe_heat_mass(nx: int = 10, m: int = 2, p: int = 3, T: float = 0.5, seed: int = 0,
+                 v: float = 5.0) -> Problem:
+    """Linear finite elements for u_t = Laplace(u) - v u_x on the unit square (nx
+    interior nodes per direction, tensor-product P1 basis): M x' = A x + B u with
+    M = M1 (x) M1, A = -(K1 (x) M1 + M1 (x) K1) - v M1 (x) G1,
+    M1 = dx tridiag(1/6, 2/3, 1/6), K1 = tridiag(-1, 2, -1)/dx,
+    G1 = tridiag(-1/2, 0, 1/2) (x index fastest).  The convection term makes A
+    non-symmetric and not commuting with M.  A synthetic stand-in for Example
+    4's mass and stiffness matrices.  The mass matrix is returned in meta["M"].
+    Draw order: B then C."""
+    dx = 1.0 / (nx + 1)
+    M1 = dx * _tridiag(nx, 1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0)
+    K1 = _tridiag(nx, -1.0, 2.0, -1.0) / dx
+    G1 = _tridiag(nx, -0.5, 0.0, 0.5)
+    M = np.kron(M1, M1)
+    A = -(np.kron(K1, M1) + np.kron(M1, K1)) - v * np.kron(M1, G1)
+    n = nx * nx
+    rng = np.random.default_rng(seed)
+    B = rng.standard_normal((n, m))
+    C = rng.uniform(0.0, 1.0, size=(p, n)) * dx
+    return Problem("fe_heat_mass", A, C, np.zeros((n, n)), T, B=B, R=np.eye(m),
+                   meta={"nx": nx, "M": M, "seed": seed})
 
 
 def serving_requests(count: int, seed: int = 0, n_min: int = 32, n_max: int = 1024,

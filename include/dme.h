@@ -92,6 +92,17 @@ dme_status dme_plan(const dme_plan_desc* desc, const double* A, const double* Qo
                     const double* B, const double* R, const double* S,
                     void* cuda_stream, dme_plan_t* out);
 
+/* A plan for the generalised state-space DRE/DLE of Example 4 (§5.1.4),
+ *     M^T P' M = A^T P M + M^T P A + Q - M^T P B R^{-1} B^T P M,
+ * which, after cancelling M^T and M, is the standard equation with
+ * A~ = A M^{-1} and Q~ = M^{-T} Q M^{-1} (the displayed equation of §5.1.4;
+ * its A M^{-1} is taken literally).  A~ and Q~ are formed on the device with
+ * an FP64 LU of M (n x n, invertible) and transposed solves; then the plan is
+ * built as by dme_plan.  S must be NULL.  DME_EINVAL also for a singular M. */
+dme_status dme_plan_mass(const dme_plan_desc* desc, const double* M, const double* A, const double* QorC,
+                         const double* B, const double* R, const double* S, void* cuda_stream,
+                         dme_plan_t* out);
+
 /* Export E_t = e^{tA} and W_t = int_0^t e^{sA^T} Q e^{sA} ds (Eq. full),
  * computing and caching them if t is new.  E_out / W_out: n x n, host or
  * device, either may be NULL. */
@@ -119,6 +130,12 @@ dme_status dme_step(dme_plan_t plan, double* P, int nsteps);
  * T/nsteps differs from desc.h the missing E_t, W_t are built first.
  * P0, P_out: n x n, host or device; P_out may equal P0. */
 dme_status dme_solve(dme_plan_t plan, const double* P0, double T, int nsteps, double* P_out);
+
+/* LQR feedback gain K = R^{-1} B^T P (§1: the optimal input is
+ * u(t) = -R^{-1} B^T P(T - t) x(t) when P solves the DRE with Q = C^T C).
+ * P: n x n symmetric, device memory.  K_out: m x n row-major, host or device.
+ * DME_EINVAL for a plan without B and R.  Synchronises the plan's stream. */
+dme_status dme_gain(dme_plan_t plan, const double* P, double* K_out);
 
 /* Bytes of device memory the plan holds. */
 size_t dme_plan_bytes(dme_plan_t plan);

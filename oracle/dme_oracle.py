@@ -57,7 +57,7 @@ import numpy as np
 __all__ = [
     "pade13_coefficients", "THETA13", "norm1", "expm", "van_loan",
     "flow_T1", "flow_T2", "flow_T12", "flow_T3", "flow_T4", "symmetrize",
-    "step_sequence", "Plan", "solve", "rel_fro",
+    "step_sequence", "Plan", "solve", "mass_transform", "lqr_gain", "rel_fro",
 ]
 
 # theta_13 of Higham (2005), Table 2.3: the largest ||X||_1 for which the
@@ -249,6 +249,25 @@ def solve(A, Q, P0, T, nsteps, comp="strang", flows=("F12",), B=None, R=None, S=
     for _ in range(nsteps):
         P = plan.step(P, comp, list(flows), h, t4_rule)
     return P
+
+
+def mass_transform(M, A, Q):
+    """Generalised state space (Example 4, §5.1.4): M^T P' M = A^T P M + M^T P A + Q
+    - M^T P B R^-1 B^T P M is, after cancelling M^T and M,
+    P' = M^-T A^T P + P A M^-1 + M^-T Q M^-1 - P B R^-1 B^T P: the standard DRE with
+    A~ = A M^-1 and Q~ = M^-T Q M^-1 (the displayed equation; its A M^-1 is
+    read literally).  Returns (A~, Q~)."""
+    M = np.asarray(M, dtype=np.float64)
+    At = np.linalg.solve(M.T, np.asarray(A, dtype=np.float64).T).T     # A M^-1
+    Y = np.linalg.solve(M.T, np.asarray(Q, dtype=np.float64))          # M^-T Q
+    Qt = np.linalg.solve(M.T, Y.T).T                                    # M^-T Q M^-1
+    return At, 0.5 * (Qt + Qt.T)
+
+
+def lqr_gain(P, B, R):
+    """K = R^{-1} B^T P: the optimal LQR input is u(t) = -K(T - t) x(t) with
+    K built from the DRE solution P (§1)."""
+    return np.linalg.solve(np.asarray(R, dtype=np.float64), np.asarray(B, dtype=np.float64).T @ P)
 
 
 def rel_fro(X, Y) -> float:

@@ -11,7 +11,7 @@ from .binding import (  # noqa: F401
     DME_KIND_SPLIT_GEMM, DME_KIND_SLICE, DME_KIND_FP64_GEMM, DME_KIND_RICCATI, dme_plan_profile, dme_plan_timing,
     DME_OK, DME_EINVAL, DME_ENOMEM, DME_ENOTSPD, DME_ECUDA, DME_ETIMEOUT, DME_EBUSY, DME_ENOTREADY,
     DmeError, LibraryNotBuilt, dme_plan_desc, make_desc, lib, header_functions,
-    dme_plan, dme_expm, dme_apply, dme_apply_async, dme_sync, dme_plan_kernels_per_step, dme_step, dme_solve, dme_plan_bytes, dme_plan_destroy,
+    dme_plan, dme_plan_mass, dme_expm, dme_apply, dme_apply_async, dme_sync, dme_plan_kernels_per_step, dme_step, dme_solve, dme_plan_bytes, dme_plan_destroy, dme_gain,
     dme_server_create, dme_submit, dme_poll, dme_server_stats, dme_server_destroy, dme_last_error,
     dme_gemm_split, dme_gemm_split_noalloc,
 )
@@ -26,7 +26,7 @@ class Plan:
     Q = C^T C (``q_is_factor``) or ``Q=...`` for a dense Q."""
 
     def __init__(self, A, C=None, h=1e-3, flows=("F12",), comp="strang", B=None, R=None, S=None,
-                 Q=None, prec="fp64", t4_rule=DME_T4_AUTO, slices=0, stream=None):
+                 Q=None, prec="fp64", t4_rule=DME_T4_AUTO, slices=0, stream=None, M=None):
         n = int(A.shape[0])
         m = 0 if B is None else int(B.shape[1])
         eq = ("g" if S is not None else "") + ("dre" if B is not None else "dle")
@@ -35,7 +35,10 @@ class Plan:
         self.n, self.m = n, m
         self.desc = make_desc(n, m=m, p=0 if C is None else int(C.shape[0]), eq=EQ_IDS[eq], comp=comp,
                               flows=flows, prec=prec, h=h, q_is_factor=Q is None, t4_rule=t4_rule, slices=slices)
-        self.handle = dme_plan(self.desc, A, C if Q is None else Q, B, R, S, stream)
+        if M is None:
+            self.handle = dme_plan(self.desc, A, C if Q is None else Q, B, R, S, stream)
+        else:
+            self.handle = dme_plan_mass(self.desc, M, A, C if Q is None else Q, B, R, S, stream)
 
     def expm(self, t, E_out=None, W_out=None):
         dme_expm(self.handle, t, E_out, W_out)
@@ -64,6 +67,9 @@ class Plan:
 
     def solve(self, P0, T, nsteps, P_out):
         dme_solve(self.handle, P0, T, nsteps, P_out)
+
+    def gain(self, P, K_out):
+        dme_gain(self.handle, P, K_out)
 
     @property
     def nbytes(self):

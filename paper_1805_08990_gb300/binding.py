@@ -55,6 +55,8 @@ _lock = threading.Lock()
 _SIGS = {
     "dme_plan": (C.c_int, [C.POINTER(dme_plan_desc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                            C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "dme_plan_mass": (C.c_int, [C.POINTER(dme_plan_desc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
     "dme_expm": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
     "dme_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p]),
     "dme_apply_async": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p]),
@@ -65,6 +67,7 @@ _SIGS = {
     "dme_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "dme_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_void_p]),
     "dme_plan_bytes": (C.c_size_t, [C.c_void_p]),
+    "dme_gain": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dme_plan_destroy": (C.c_int, [C.c_void_p]),
     "dme_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]),
     "dme_submit": (C.c_int, [C.c_void_p, C.POINTER(dme_plan_desc), C.c_void_p, C.c_void_p, C.c_void_p,
@@ -158,6 +161,15 @@ def dme_plan(desc: dme_plan_desc, A, QorC, B=None, R=None, S=None, stream=None) 
     return out.value
 
 
+def dme_plan_mass(desc: dme_plan_desc, M, A, QorC, B=None, R=None, S=None, stream=None) -> int:
+    keep: list = []
+    out = C.c_void_p()
+    st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib().dme_plan_mass(C.byref(desc), _ptr(M, keep), _ptr(A, keep), _ptr(QorC, keep), _ptr(B, keep),
+                               _ptr(R, keep), _ptr(S, keep), st, C.byref(out)), "dme_plan_mass")
+    return out.value
+
+
 def dme_expm(plan: int, t: float, E_out=None, W_out=None):
     _check(lib().dme_expm(plan, float(t), _out_ptr(E_out), _out_ptr(W_out)), "dme_expm")
 
@@ -199,6 +211,11 @@ def dme_step(plan: int, P, nsteps: int):
 def dme_solve(plan: int, P0, T: float, nsteps: int, P_out):
     keep: list = []
     _check(lib().dme_solve(plan, _ptr(P0, keep), float(T), int(nsteps), _out_ptr(P_out)), "dme_solve")
+
+
+def dme_gain(plan: int, P, K_out):
+    """K_out (m x n) = R^{-1} B^T P, the LQR feedback gain."""
+    _check(lib().dme_gain(plan, _out_ptr(P), _out_ptr(K_out)), "dme_gain")
 
 
 def dme_plan_bytes(plan: int) -> int:

@@ -107,5 +107,8 @@ RicItem make_ric_item(double* P, const double* Bt, int n, int m, double t, const
 // (riccati_desc_bytes() per problem, untouched until the kernels finish).
 dme_status launch_riccati_grouped(const std::vector<RicItem>& items, void* dev_desc, cudaStream_t st);
 size_t riccati_desc_bytes();
+// K (m x n) = R^{-1} B^T P from Bt = B L^{-T} and L (R = L L^T); work as for launch_riccati.
+dme_status launch_lqr_gain(const double* P, const double* Bt, const double* LR, int n, int m, double* work,
+                           double* K, cudaStream_t st);
 
 }  // namespace dme

@@ -382,6 +382,41 @@ dme_status launch_riccati_grouped(const std::vector<RicItem>& items, void* dev_d
 
 size_t riccati_desc_bytes() { return sizeof(RicDesc); }
 
+// K = R^{-1} B^T P for symmetric P, with R = L L^T and Bt = B L^{-T}:
+// B^T P = L Bt^T P = L Z^T (Z = P Bt), so K = L^{-T} Z^T, i.e. L^T K = Z^T,
+// solved by back substitution for each column j of K (one thread per column).
+__global__ void lqr_gain_kernel(const double* __restrict__ Z, const double* __restrict__ L, double* __restrict__ K,
+                                int n, int m) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double x[32];
+    for (int r = m - 1; r >= 0; --r) {
+        double s = Z[(size_t)j * m + r];
+        for (int c = r + 1; c < m; ++c) s -= L[c * m + r] * x[c];
+        x[r] = s / L[r * m + r];
+        K[(size_t)r * n + j] = x[r];
+    }
+}
+
+dme_status launch_lqr_gain(const double* P, const double* Bt, const double* LR, int n, int m, double* work,
+                           double* K, cudaStream_t st) {
+    RicBatch b;
+    std::memset(&b, 0, sizeof(b));
+    RicDesc& d = b.local[0];
+    d.P = const_cast<double*>(P);
+    d.Bt = Bt;
+    d.Z = work;
+    d.Y = d.Z + (size_t)n * m;
+    d.Gpart = d.Y + (size_t)n * m;
+    d.n = n;
+    d.m = m;
+    b.nd = 1;
+    riccati_z_kernel<<<rz_blocks(n), 256, 0, st>>>(b);       // Z = P Bt (P is only read)
+    lqr_gain_kernel<<<(n + 127) / 128, 128, 0, st>>>(d.Z, LR, K, n, m);
+    DME_CUDA_TRY(cudaGetLastError());
+    return DME_OK;
+}
+
 void launch_riccati(double* P, const double* Bt, int n, int m, double t, const double* Qadd, double q,
                     double* work, int* status, cudaStream_t st) {
     std::vector<RicItem> v{make_ric_item(P, Bt, n, m, t, Qadd, q, work, status)};

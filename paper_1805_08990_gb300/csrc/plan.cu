@@ -630,7 +630,8 @@ dme_status dme::plan_create(const dme_plan_desc* d, const double* A, const doubl
         TmpPool tp(st);
         double *Bd = nullptr, *Rd = nullptr;
         DME_TRY(tp.get(&Bd, (size_t)n * m));
-        DME_TRY(tp.get(&Rd, (size_t)m * m));
+        DME_TRY(palloc_t(p, &p->LR, (size_t)m * m));
+        Rd = p->LR;
         DME_CUDA_TRY(cudaMemcpyAsync(Bd, B, (size_t)n * m * sizeof(double), cudaMemcpyDefault, st));
         DME_CUDA_TRY(cudaMemcpyAsync(Rd, R, (size_t)m * m * sizeof(double), cudaMemcpyDefault, st));
         DME_TRY(palloc_t(p, &p->Bt, (size_t)n * m));
@@ -732,6 +733,70 @@ dme_status dme_plan(const dme_plan_desc* desc, const double* A, const double* Qo
     return guarded([&] { return plan_create(desc, A, QorC, B, R, S, cuda_stream, out); });
 }
 
+dme_status dme_plan_mass(const dme_plan_desc* desc, const double* M, const double* A, const double* QorC,
+                         const double* B, const double* R, const double* S, void* cuda_stream, dme_plan_t* out) {
+    if (!out) return set_error("out is NULL"), DME_EINVAL;
+    *out = nullptr;
+    set_error("");
+    if (!M) return set_error("dme_plan_mass: M is required"), DME_EINVAL;
+    if (S) return set_error("dme_plan_mass: the mass-matrix form has no S term"), DME_EINVAL;
+    DME_TRY(validate(desc, A, QorC, B, R, S));
+    return guarded([&]() -> dme_status {
+        const int n = desc->n;
+        const size_t nn = (size_t)n * n;
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+        bool own = false;
+        if (!st) {
+            DME_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            own = true;
+        }
+        std::unique_ptr<CUstream_st, void (*)(cudaStream_t)> sg(own ? st : nullptr, [](cudaStream_t x) {
+            if (x) {
+                cudaStreamSynchronize(x);
+                cudaStreamDestroy(x);
+            }
+        });
+        TmpPool tp(st);
+        double *LU, *At, *Qt, *X, *Y, *pivd, *stat;
+        DME_TRY(tp.get(&LU, nn));
+        DME_TRY(tp.get(&At, nn));
+        DME_TRY(tp.get(&Qt, nn));
+        DME_TRY(tp.get(&X, nn));
+        DME_TRY(tp.get(&Y, nn));
+        DME_TRY(tp.get(&pivd, (size_t)n));
+        DME_TRY(tp.get(&stat, 2));
+        int* piv = reinterpret_cast<int*>(pivd);
+        int* status = reinterpret_cast<int*>(stat);
+        DME_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+        DME_CUDA_TRY(cudaMemcpyAsync(LU, M, nn * sizeof(double), cudaMemcpyDefault, st));
+        DME_CUDA_TRY(cudaMemcpyAsync(Y, A, nn * sizeof(double), cudaMemcpyDefault, st));
+        if (desc->q_is_factor) {
+            double* C = nullptr;
+            DME_TRY(tp.get(&C, (size_t)desc->p * n));
+            DME_CUDA_TRY(cudaMemcpyAsync(C, QorC, (size_t)desc->p * n * sizeof(double), cudaMemcpyDefault, st));
+            DME_TRY(gemm1(gp(n, n, desc->p, C, n, 1, C, n, 0, Qt, n, 1.0), st));   // Q = C^T C
+        } else {
+            DME_CUDA_TRY(cudaMemcpyAsync(Qt, QorC, nn * sizeof(double), cudaMemcpyDefault, st));
+        }
+        launch_lu(LU, n, n, piv, status, st);                                      // P M = L U
+        launch_transpose(Y, X, n, n, n, n, st);                                    // X = A^T
+        launch_lu_solve(LU, n, n, piv, X, n, n, 1, st);                            // X = M^-T A^T
+        launch_transpose(X, At, n, n, n, n, st);                                   // A~ = A M^-1
+        launch_lu_solve(LU, n, n, piv, Qt, n, n, 1, st);                           // M^-T Q
+        launch_transpose(Qt, X, n, n, n, n, st);                                   // Q M^-1 (Q symmetric)
+        launch_lu_solve(LU, n, n, piv, X, n, n, 1, st);                            // Q~ = M^-T Q M^-1
+        launch_symmetrize(X, n, n, st);
+        DME_CUDA_TRY(cudaGetLastError());
+        int hs = 0;
+        DME_CUDA_TRY(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+        DME_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hs) return set_error("dme_plan_mass: M is singular"), DME_EINVAL;
+        dme_plan_desc d2 = *desc;
+        d2.q_is_factor = 0;
+        return plan_create(&d2, At, X, B, R, nullptr, cuda_stream, out);
+    });
+}
+
 dme_status dme_expm(dme_plan_t plan, double t, double* E_out, double* W_out) {
     if (!plan) return set_error("plan is NULL"), DME_EINVAL;
     if (!std::isfinite(t)) return set_error("t must be finite"), DME_EINVAL;
@@ -797,6 +862,18 @@ dme_status dme_sync(dme_plan_t plan) {
 }
 
 int dme_plan_kernels_per_step(dme_plan_t plan) { return plan ? plan->graph_kernels : -1; }
+
+dme_status dme_gain(dme_plan_t plan, const double* P, double* K_out) {
+    if (!plan || !P || !K_out) return set_error("plan, P and K_out are required"), DME_EINVAL;
+    if (!plan->Bt) return set_error("dme_gain needs a DRE/GDRE plan (B, R)"), DME_EINVAL;
+    return guarded([&]() -> dme_status {
+        const int n = plan->n, m = plan->m;
+        if (!plan->Kbuf) DME_TRY(palloc_t(plan, &plan->Kbuf, (size_t)m * n));
+        DME_TRY(launch_lqr_gain(P, plan->Bt, plan->LR, n, m, plan->rwork, plan->Kbuf, plan->st));
+        DME_CUDA_TRY(cudaMemcpyAsync(K_out, plan->Kbuf, sizeof(double) * m * n, cudaMemcpyDefault, plan->st));
+        return check_status(plan, "dme_gain");
+    });
+}
 
 dme_status dme_plan_profile(dme_plan_t plan, int enable) {
     if (!plan) return set_error("plan is NULL"), DME_EINVAL;

@@ -36,6 +36,8 @@ struct dme_plan_s {
     double* A = nullptr;
     double* Q = nullptr;
     double* Bt = nullptr;
+    double* LR = nullptr;      // Cholesky factor of R (m x m, lower)
+    double* Kbuf = nullptr;    // m x n LQR gain (allocated on first dme_gain)
     double* S = nullptr;
     double* X = nullptr;       // n x n congruence intermediate
     double* Xs = nullptr;      // n x n S-flow intermediates

@@ -237,3 +237,21 @@ def t4_local_errors(orc, rule, taus=(0.2, 0.1, 0.05), seed=6, n=5):
         exact = (sla.expm(tau * K) @ P0.ravel()).reshape(n, n)
         errs.append(orc.rel_fro(orc.flow_T4(P0, S, tau, rule), exact))
     return errs
+
+
+def mass_ode_reference(M, A, Q, P0, T, BRB=None, rtol=1e-13, atol=1e-15):
+    """P(T) of the generalised form M^T P' M = A^T P M + M^T P A + Q - M^T P BRB P M
+    (Example 4, before any cancellation), vec(P) with DOP853; P' is obtained
+    from the right-hand side by two solves with M^T and M."""
+    n = A.shape[0]
+
+    def rhs(_t, y):
+        P = y.reshape(n, n)
+        F = A.T @ P @ M + M.T @ P @ A + Q
+        if BRB is not None:
+            F = F - M.T @ P @ BRB @ P @ M
+        return np.linalg.solve(M.T, np.linalg.solve(M.T, F.T).T).ravel()
+
+    sol = si.solve_ivp(rhs, (0.0, T), np.asarray(P0, float).ravel(), method="DOP853", rtol=rtol, atol=atol)
+    assert sol.success, sol.message
+    return sol.y[:, -1].reshape(n, n)

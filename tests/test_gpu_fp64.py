@@ -132,7 +132,8 @@ def test_dre_convdiff_small_schemes(scheme, comp):
 
 
 @pytest.mark.parametrize("scheme,comp", [("F12F3F4", "strang"), ("F12F4F3", "lie"), ("F12F4", "strang"),
-                                         ("F1F2F4", "strang"), ("F1F4F2", "strang"), ("F1F4F2", "lie")])
+                                         ("F1F2F4", "strang"), ("F1F4F2", "strang"), ("F1F4F2", "lie"),
+                                         ("F1F2F3F4", "strang"), ("F1F2F3F4", "lie")])
 def test_generalised_schemes_padded(scheme, comp):
     pr = W.gdre_convdiff_padded(nx=8, n_pad=72, m=2, p=3)
     N = 8
@@ -228,3 +229,44 @@ def test_riccati_not_spd_on_device_is_reported():
     # the plan stays usable afterwards
     P = dev(W.random_psd(16, 1))
     plan.apply("F3", 0.1, P)
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (130, 3), (257, 8)])
+def test_lqr_gain_matches_oracle(n, m):
+    pr = _problem(n, m=m, with_S=False, seed=n)
+    plan = plan_for(pr, ["F12", "F3"], "strang", 0.1)
+    P0 = W.random_psd(n, 2 * n, scale=2.0)
+    K = np.empty((m, n))
+    plan.gain(dev(P0), K)
+    assert rel(K, O.lqr_gain(P0, pr.B, pr.R)) < FP64_TOL
+    with pytest.raises(dme.DmeError):
+        dle = dme.Plan(dev(pr.A), C=dev(pr.C), h=0.1, flows=["F12"])
+        dle.gain(dev(P0), K)
+
+
+@pytest.mark.parametrize("nx,prec", [(8, "fp64"), (11, "fp64"), (11, "split_bf16")])
+def test_mass_matrix_dre_matches_oracle(nx, prec):
+    """Example 4's generalised state space: the plan forms A M^-1 and M^-T Q M^-1
+    on the device; the solve matches the oracle's transform + scheme."""
+    pr = W.fe_heat_mass(nx=nx, m=2, p=3, T=0.2)
+    M = pr.meta["M"]
+    N = 16
+    plan = dme.Plan(dev(pr.A), C=dev(pr.C), h=pr.T / N, flows=["F12", "F3"], comp="strang", B=dev(pr.B),
+                    R=dev(pr.R), M=dev(M), prec=prec)
+    out = np.empty((pr.n, pr.n))
+    plan.solve(pr.P0, pr.T, N, out)
+    At, Qt = O.mass_transform(M, pr.A, pr.Q)
+    ref = O.solve(At, Qt, pr.P0, pr.T, N, "strang", ["F12", "F3"], B=pr.B, R=pr.R)
+    assert rel(out, ref) < (FP64_TOL if prec == "fp64" else 1e-7)
+
+
+def test_mass_matrix_plan_rejections():
+    pr = W.fe_heat_mass(nx=5, m=2, p=3)
+    M = pr.meta["M"].copy()
+    M[-1, :] = 0.0                                   # singular mass matrix
+    with pytest.raises(dme.DmeError) as ei:
+        dme.Plan(dev(pr.A), C=dev(pr.C), h=0.01, flows=["F12", "F3"], B=dev(pr.B), R=dev(pr.R), M=dev(M))
+    assert ei.value.status == dme.DME_EINVAL
+    with pytest.raises(dme.DmeError):
+        dme.Plan(dev(pr.A), C=dev(pr.C), h=0.01, flows=["F12", "F3", "F4"], B=dev(pr.B), R=dev(pr.R),
+                 S=dev(np.eye(pr.n)), M=dev(pr.meta["M"]))

@@ -128,7 +128,7 @@ def test_split_dle_heat_n256_full_config():
     assert rel(host(P), _oracle_solve(pr, ["F1", "F2"], "strang", 100)) < SPLIT_TOL
 
 
-@pytest.mark.parametrize("scheme,comp", [("F12F3F4", "strang"), ("F12F4", "lie")])
+@pytest.mark.parametrize("scheme,comp", [("F12F3F4", "strang"), ("F12F4", "lie"), ("F1F2F3F4", "strang")])
 def test_split_generalised_padded(scheme, comp):
     pr = W.gdre_convdiff_padded(nx=12, n_pad=160, m=2, p=3)
     N = 8

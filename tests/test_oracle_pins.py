@@ -176,7 +176,7 @@ def test_scalar_dre_small_R_inverse():
     ("F1F3F2", "strang", False, 1.9, 2.1), ("F12F3", "lie", False, 0.9, 1.15),
     ("F12F4", "strang", True, 1.9, 2.1), ("F1F2F4", "strang", True, 1.9, 2.1),
     ("F1F4F2", "strang", True, 1.9, 2.1), ("F12F3F4", "strang", True, 1.9, 2.1),
-    ("F12F4", "lie", True, 0.9, 1.15),
+    ("F12F4", "lie", True, 0.9, 1.15), ("F1F2F3F4", "strang", True, 1.9, 2.1),
 ])
 def test_matrix_schemes_order_against_ode(scheme, comp, with_S, lo, hi):
     errs = pins.scheme_errors_vs_ode(O, scheme, comp, with_S=with_S)
@@ -235,3 +235,43 @@ def test_long_horizon_reaches_algebraic_riccati_solution():
         errs.append(O.rel_fro(P, X))
     assert errs[1] < 1e-3
     assert 1.8 < math.log2(errs[0] / errs[1]) < 2.2
+
+
+def test_lqr_gain_scalar_steady_state_closes_the_loop():
+    """§1: u = -R^-1 B^T P x.  For the scalar DRE at steady state, p = (a + beta)/s
+    (s = b^2/r, beta = sqrt(a^2 + q s)), so the closed-loop pole a - b k is -beta."""
+    a, b, q, r = 0.7, 1.3, 2.0, 0.5
+    beta = math.sqrt(a * a + q * b * b / r)
+    p = pins.scalar_dre_exact(a, b, q, r, 40.0)
+    k = O.lqr_gain(np.array([[p]]), np.array([[b]]), np.array([[r]]))[0, 0]
+    assert abs(k - b * p / r) < 1e-14 * abs(k)
+    assert abs((a - b * k) + beta) < 1e-12
+
+
+def test_lqr_gain_from_long_horizon_stabilises():
+    A, Q, B, R, _ = pins.small_dre(seed=21, n=5, m=2)
+    A = A - (np.linalg.eigvals(A).real.max() - 0.5) * np.eye(5)    # open loop unstable (max Re = 0.5)
+    P = O.solve(A, Q, np.zeros((5, 5)), 15.0, 600, "strang", ["F12", "F3"], B=B, R=R)
+    K = O.lqr_gain(P, B, R)
+    assert np.linalg.eigvals(A).real.max() > 0
+    assert np.linalg.eigvals(A - B @ K).real.max() < 0
+
+
+def test_mass_transform_identity_and_ode():
+    """M = I leaves (A, Q) unchanged; with a finite-element mass matrix, Strang
+    F12F3 on (A M^-1, M^-T Q M^-1) converges with order 2 to the ODE solution of
+    the untransformed generalised form (which tells A M^-1 from M^-1 A)."""
+    pr = W.fe_heat_mass(nx=3, m=2, p=2, T=0.2)
+    At, Qt = O.mass_transform(np.eye(pr.n), pr.A, pr.Q)
+    assert np.allclose(At, pr.A, rtol=1e-15) and np.allclose(Qt, pr.Q, rtol=1e-15)
+    M = pr.meta["M"]
+    At, Qt = O.mass_transform(M, pr.A, pr.Q)
+    BRB = pr.B @ pr.B.T
+    ref = pins.mass_ode_reference(M, pr.A, pr.Q, pr.P0, pr.T, BRB=BRB)
+    errs = [O.rel_fro(O.solve(At, Qt, pr.P0, pr.T, N, "strang", ["F12", "F3"], B=pr.B, R=pr.R), ref)
+            for N in (32, 64, 128)]
+    assert all(1.85 < o < 2.15 for o in pins.observed_orders(errs)), errs
+    # the other reading (M^-1 A) solves a different equation
+    Aw = np.linalg.solve(M, pr.A)
+    wrong = O.solve(Aw, Qt, pr.P0, pr.T, 128, "strang", ["F12", "F3"], B=pr.B, R=pr.R)
+    assert O.rel_fro(wrong, ref) > 100 * errs[-1]
