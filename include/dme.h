@@ -72,6 +72,14 @@ typedef struct {
     int q_is_factor;    /* 1: QorC is C (p x n); 0: QorC is Q (n x n, symmetric)      */
     int t4_rule;        /* dme_t4_rule                                                */
     int slices;         /* DME_SPLIT_BF16: bf16 slices per operand, 0 = default (4)   */
+    int fsal;           /* 1: merge the outer half steps of consecutive Strang steps  */
+                        /*    (T_a(h/2) T_a(h/2) = T_a(h) for an exact outer flow; no */
+                        /*    F4 outside).  Same result up to rounding, one outer     */
+                        /*    sub-flow less per step.  0 = off.  Plans only.          */
+    int extrap;         /* q >= 2: extrapolated Strang of order 2q (§2 "higher-order  */
+                        /*    schemes"): P <- sum_k gamma_k (S_{h/k})^k P, k = 1..q,  */
+                        /*    gamma_k = prod_{j!=k} k^2/(k^2-j^2); q <= 4; Strang of  */
+                        /*    exact flows only (no F4).  0 or 1 = plain.  Plans only. */
 } dme_plan_desc;
 
 typedef struct dme_plan_s* dme_plan_t;

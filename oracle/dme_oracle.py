@@ -57,7 +57,8 @@ import numpy as np
 __all__ = [
     "pade13_coefficients", "THETA13", "norm1", "expm", "van_loan",
     "flow_T1", "flow_T2", "flow_T12", "flow_T3", "flow_T4", "symmetrize",
-    "step_sequence", "Plan", "solve", "mass_transform", "lqr_gain", "rel_fro",
+    "step_sequence", "Plan", "solve", "extrapolation_weights", "solve_extrapolated",
+    "mass_transform", "lqr_gain", "rel_fro",
 ]
 
 # theta_13 of Higham (2005), Table 2.3: the largest ||X||_1 for which the
@@ -248,6 +249,45 @@ def solve(A, Q, P0, T, nsteps, comp="strang", flows=("F12",), B=None, R=None, S=
     P = np.array(P0, dtype=np.float64, copy=True)
     for _ in range(nsteps):
         P = plan.step(P, comp, list(flows), h, t4_rule)
+    return P
+
+
+def extrapolation_weights(q: int) -> list[float]:
+    """Weights gamma_1..gamma_q of the extrapolated Strang scheme of order 2q
+    (the higher-order schemes mentioned in §2).  Strang of exact flows is
+    symmetric, so its global error expands in even powers of h; combining the
+    results of k steps of size h/k, k = 1..q, with weights that reproduce the
+    value at x = h^2 -> 0 of every polynomial of degree < q in x = (h/k)^2 is
+    the Lagrange basis at 0 on the nodes x_k = 1/k^2:
+    gamma_k = prod_{j != k} x_j / (x_j - x_k) = prod_{j != k} k^2 / (k^2 - j^2)."""
+    out = []
+    for k in range(1, q + 1):
+        g = Fraction(1)
+        for j in range(1, q + 1):
+            if j != k:
+                g *= Fraction(k * k, k * k - j * j)
+        out.append(float(g))
+    return out
+
+
+def solve_extrapolated(A, Q, P0, T, nsteps, q, flows=("F12", "F3"), B=None, R=None, plan: Plan | None = None):
+    """P(T) by N = nsteps steps of the extrapolated Strang scheme of order 2q:
+    P_{j+1} = sum_k gamma_k (S_{h/k})^k P_j, h = T/N.  Needs exact sub-flows
+    (no F4, whose midpoint rule is not symmetric)."""
+    if "F4" in flows:
+        raise ValueError("extrapolation needs a symmetric base scheme (no F4)")
+    plan = plan or Plan(A, Q, B, R)
+    gam = extrapolation_weights(q)
+    h = T / nsteps
+    P = np.array(P0, dtype=np.float64, copy=True)
+    for _ in range(nsteps):
+        acc = np.zeros_like(P)
+        for k in range(1, q + 1):
+            Y = P
+            for _ in range(k):
+                Y = plan.step(Y, "strang", list(flows), h / k)
+            acc = acc + gam[k - 1] * Y
+        P = acc
     return P
 
 

@@ -26,7 +26,7 @@ class Plan:
     Q = C^T C (``q_is_factor``) or ``Q=...`` for a dense Q."""
 
     def __init__(self, A, C=None, h=1e-3, flows=("F12",), comp="strang", B=None, R=None, S=None,
-                 Q=None, prec="fp64", t4_rule=DME_T4_AUTO, slices=0, stream=None, M=None):
+                 Q=None, prec="fp64", t4_rule=DME_T4_AUTO, slices=0, stream=None, M=None, fsal=False, extrap=0):
         n = int(A.shape[0])
         m = 0 if B is None else int(B.shape[1])
         eq = ("g" if S is not None else "") + ("dre" if B is not None else "dle")
@@ -34,7 +34,8 @@ class Plan:
             raise ValueError("give C (Q = C^T C) or Q")
         self.n, self.m = n, m
         self.desc = make_desc(n, m=m, p=0 if C is None else int(C.shape[0]), eq=EQ_IDS[eq], comp=comp,
-                              flows=flows, prec=prec, h=h, q_is_factor=Q is None, t4_rule=t4_rule, slices=slices)
+                              flows=flows, prec=prec, h=h, q_is_factor=Q is None, t4_rule=t4_rule, slices=slices,
+                              fsal=fsal, extrap=extrap)
         if M is None:
             self.handle = dme_plan(self.desc, A, C if Q is None else Q, B, R, S, stream)
         else:

@@ -46,7 +46,8 @@ class DmeError(RuntimeError):
 class dme_plan_desc(C.Structure):
     _fields_ = [("n", C.c_int), ("m", C.c_int), ("p", C.c_int), ("eq", C.c_int), ("comp", C.c_int),
                 ("nflows", C.c_int), ("flows", C.c_int * 4), ("prec", C.c_int), ("h", C.c_double),
-                ("q_is_factor", C.c_int), ("t4_rule", C.c_int), ("slices", C.c_int)]
+                ("q_is_factor", C.c_int), ("t4_rule", C.c_int), ("slices", C.c_int), ("fsal", C.c_int),
+                ("extrap", C.c_int)]
 
 
 _lib = None
@@ -135,7 +136,7 @@ def _ptr(x, keep: list):
 
 
 def make_desc(n, *, m=0, p=0, eq=DME_DLE, comp="strang", flows=("F12",), prec="fp64", h=1e-3,
-              q_is_factor=False, t4_rule=DME_T4_AUTO, slices=0) -> dme_plan_desc:
+              q_is_factor=False, t4_rule=DME_T4_AUTO, slices=0, fsal=False, extrap=0) -> dme_plan_desc:
     d = dme_plan_desc()
     d.n, d.m, d.p, d.eq = n, m, p, eq
     d.comp = COMP_IDS[comp] if isinstance(comp, str) else comp
@@ -148,6 +149,8 @@ def make_desc(n, *, m=0, p=0, eq=DME_DLE, comp="strang", flows=("F12",), prec="f
     d.q_is_factor = int(bool(q_is_factor))
     d.t4_rule = t4_rule
     d.slices = slices
+    d.fsal = int(bool(fsal))
+    d.extrap = int(extrap)
     return d
 
 

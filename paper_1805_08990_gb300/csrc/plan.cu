@@ -397,15 +397,30 @@ int t4_rule_of(const dme_plan_desc& d) {
 
 }  // namespace
 
-// Compile one step into ops.  T2 (P + tQ) is fused into the epilogue of the
-// op before it in the same step when there is one, else it is a standalone axpy.
-dme_status dme::build_ops(dme_plan_t p, double h) {
-    if (p->ops_h == h) return DME_OK;
-    std::vector<Op> ops;
-    for (auto& ft : step_sequence(p->d, h)) {
+namespace {
+
+// Weights of the extrapolated Strang scheme of order 2q (§2 "higher-order
+// schemes"): the Lagrange basis at x = 0 on the nodes x_k = 1/k^2, so that
+// sum_k gamma_k (S_{h/k})^k cancels the h^2 .. h^(2q-2) terms of Strang's even
+// error expansion: gamma_k = prod_{j != k} k^2 / (k^2 - j^2).
+double extrap_weight(int q, int k) {
+    double g = 1.0;
+    for (int j = 1; j <= q; ++j)
+        if (j != k) g *= static_cast<double>(k * k) / static_cast<double>(k * k - j * j);
+    return g;
+}
+
+// Append the ops of one flow sequence acting on state `buf`.  T2 (P + tQ) is
+// fused into the epilogue of the op before it in the same sequence when there
+// is one, else it is a standalone axpy.
+dme_status compile_seq(dme_plan_t p, const std::vector<std::pair<int, double>>& seq, int buf, std::vector<Op>& ops) {
+    const size_t first = ops.size();
+    for (auto& ft : seq) {
         Op o;
         std::memset(&o, 0, sizeof(o));
         o.tau = ft.second;
+        o.buf = buf;
+        o.src = -1;
         switch (ft.first) {
             case DME_F1:
             case DME_F12: {
@@ -418,7 +433,7 @@ dme_status dme::build_ops(dme_plan_t p, double h) {
                 break;
             }
             case DME_F2:
-                if (!ops.empty()) {
+                if (ops.size() > first) {
                     ops.back().qcoef += ft.second;
                 } else {
                     o.kind = OP_AXPY;
@@ -440,13 +455,78 @@ dme_status dme::build_ops(dme_plan_t p, double h) {
                 return DME_EINVAL;
         }
     }
-    p->ops = ops;
-    p->ops_h = h;
-    if (p->gexec) {
-        cudaGraphExecDestroy(p->gexec);
-        p->gexec = nullptr;
-        p->gP = nullptr;
+    return DME_OK;
+}
+
+Op state_op(int kind, int buf, int src, double c1, double c2) {
+    Op o;
+    std::memset(&o, 0, sizeof(o));
+    o.kind = kind;
+    o.buf = buf;
+    o.src = src;
+    o.c1 = c1;
+    o.c2 = c2;
+    return o;
+}
+
+void drop_graph(GraphSlot& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    g.P = nullptr;
+    g.kernels = -1;
+}
+
+}  // namespace
+
+// Compile one step of size h into ops (and, with fsal, its head / interior /
+// closing parts).  Extrapolated scheme of order 2q, one step:
+//   acc <- P; k = 1 Strang step of h on acc; acc <- g_1 acc
+//   for 1 < k < q: work <- P; k steps of h/k on work; acc <- acc + g_k work
+//   k = q steps of h/q on P; P <- g_q P + acc.
+dme_status dme::build_ops(dme_plan_t p, double h) {
+    if (p->ops_h == h) return DME_OK;
+    std::vector<Op> ops, head, body, tail;
+    const int q = p->d.extrap > 1 ? p->d.extrap : 1;
+    if (q == 1) {
+        DME_TRY(compile_seq(p, step_sequence(p->d, h), BUF_P, ops));
+    } else {
+        const size_t nn = (size_t)p->n * p->n;
+        if (!p->xacc) DME_TRY(palloc_t(p, &p->xacc, nn));
+        if (q >= 3 && !p->xwork) DME_TRY(palloc_t(p, &p->xwork, nn));
+        for (int k = 1; k <= q; ++k) {
+            const int buf = (k == q) ? BUF_P : (k == 1 ? BUF_ACC : BUF_WORK);
+            if (k < q) ops.push_back(state_op(OP_COPY, buf, BUF_P, 0.0, 0.0));
+            const auto seq = step_sequence(p->d, h / k);
+            for (int r = 0; r < k; ++r) DME_TRY(compile_seq(p, seq, buf, ops));
+            const double g = extrap_weight(q, k);
+            if (k == 1)
+                ops.push_back(state_op(OP_COMBINE, BUF_ACC, -1, g, 0.0));
+            else if (k < q)
+                ops.push_back(state_op(OP_COMBINE, BUF_ACC, BUF_WORK, 1.0, g));
+            else
+                ops.push_back(state_op(OP_COMBINE, BUF_P, BUF_ACC, g, 1.0));
+        }
     }
+    if (p->d.fsal) {
+        // Strang [f0(h/2), inner..., f0(h/2)]: head = f0(h/2) inner, body = f0(h) inner, tail = f0(h/2)
+        const auto seq = step_sequence(p->d, h);
+        const std::vector<std::pair<int, double>> inner(seq.begin() + 1, seq.end() - 1);
+        std::vector<std::pair<int, double>> hs{seq.front()}, bs{{seq.front().first, h}}, ts{seq.back()};
+        hs.insert(hs.end(), inner.begin(), inner.end());
+        bs.insert(bs.end(), inner.begin(), inner.end());
+        DME_TRY(compile_seq(p, hs, BUF_P, head));
+        DME_TRY(compile_seq(p, bs, BUF_P, body));
+        DME_TRY(compile_seq(p, ts, BUF_P, tail));
+    }
+    p->ops = ops;
+    p->ops_head = head;
+    p->ops_body = body;
+    p->ops_tail = tail;
+    p->ops_h = h;
+    drop_graph(p->g_step);
+    drop_graph(p->g_head);
+    drop_graph(p->g_body);
+    drop_graph(p->g_tail);
     return DME_OK;
 }
 
@@ -480,9 +560,19 @@ dme_status run_sflow_split(dme_plan_t p, double* P, double tau, int rule, double
 
 }  // namespace
 
-dme_status dme::run_op(dme_plan_t p, const Op& o, double* P) {
+dme_status dme::run_op(dme_plan_t p, const Op& o, double* Pcaller) {
     const int n = p->n;
     cudaStream_t st = p->st;
+    auto state = [&](int b) { return b == BUF_ACC ? p->xacc : (b == BUF_WORK ? p->xwork : Pcaller); };
+    double* P = state(o.buf);
+    if (o.kind == OP_COPY) {
+        DME_CUDA_TRY(cudaMemcpyAsync(P, state(o.src), (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        return DME_OK;
+    }
+    if (o.kind == OP_COMBINE) {
+        launch_lincomb(P, n, n, P, o.c1, o.src >= 0 ? state(o.src) : nullptr, o.c2, nullptr, 0.0, 0.0, st);
+        return DME_OK;
+    }
     if (p->split && o.kind == OP_CONG) {
         const EWEntry& e = p->ew[o.ew];
         return split_cong(p, P, e.Gsl, P, 1.0, o.wcoef != 0.0 ? e.W : nullptr, o.wcoef,
@@ -514,8 +604,8 @@ dme_status dme::run_op(dme_plan_t p, const Op& o, double* P) {
 
 namespace {
 
-dme_status run_step(dme_plan_t p, double* P) {
-    for (const Op& o : p->ops) DME_TRY(run_op(p, o, P));
+dme_status run_ops(dme_plan_t p, const std::vector<Op>& ops, double* P) {
+    for (const Op& o : ops) DME_TRY(run_op(p, o, P));
     DME_CUDA_TRY(cudaGetLastError());
     return DME_OK;
 }
@@ -540,6 +630,13 @@ dme_status validate(const dme_plan_desc* d, const double* A, const double* QorC,
     }
     if (ric && (d->m < 1 || d->m > 32 || !B || !R)) return set_error("DRE needs B, R and 1 <= m <= 32"), DME_EINVAL;
     if (gen && !S) return set_error("generalised equations need S"), DME_EINVAL;
+    bool has_f4 = false;
+    for (int i = 0; i < d->nflows; ++i) has_f4 = has_f4 || d->flows[i] == DME_F4;
+    if (d->extrap < 0 || d->extrap > 4) return set_error("extrap must be 0..4"), DME_EINVAL;
+    if (d->extrap > 1 && (d->comp != DME_STRANG || has_f4 || d->fsal))
+        return set_error("extrapolation needs Strang over exact flows (no F4) and fsal = 0"), DME_EINVAL;
+    if (d->fsal && (d->comp != DME_STRANG || d->nflows < 2 || d->flows[0] == DME_F4))
+        return set_error("fsal needs Strang with >= 2 flows and an exact outer flow (not F4)"), DME_EINVAL;
     return DME_OK;
 }
 
@@ -547,7 +644,8 @@ dme_status validate(const dme_plan_desc* d, const double* A, const double* QorC,
 
 void dme::free_plan(dme_plan_t p) {
     if (!p) return;
-    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    for (GraphSlot* g : {&p->g_step, &p->g_head, &p->g_body, &p->g_tail})
+        if (g->exec) cudaGraphExecDestroy(g->exec);
     if (p->st) cudaStreamSynchronize(p->st);
     for (auto& r : p->evrec) {
         cudaEventDestroy(r.a);
@@ -673,15 +771,18 @@ dme_status dme::plan_create(const dme_plan_desc* d, const double* A, const doubl
 
 namespace {
 
-dme_status step_graph(dme_plan_t p, double* P, int nsteps) {
-    if (!p->gexec || p->gP != P) {
-        if (p->gexec) {
-            cudaGraphExecDestroy(p->gexec);
-            p->gexec = nullptr;
+// Replay the op list `ops` `count` times on P from its CUDA graph (captured
+// on first use for this P).
+dme_status replay(dme_plan_t p, GraphSlot& slot, const std::vector<Op>& ops, double* P, int count) {
+    if (count <= 0) return DME_OK;
+    if (!slot.exec || slot.P != P) {
+        if (slot.exec) {
+            cudaGraphExecDestroy(slot.exec);
+            slot.exec = nullptr;
         }
         cudaGraph_t g = nullptr;
         DME_CUDA_TRY(cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal));
-        dme_status s = run_step(p, P);
+        dme_status s = run_ops(p, ops, P);
         cudaError_t e = cudaStreamEndCapture(p->st, &g);
         if (s != DME_OK) {
             if (g) cudaGraphDestroy(g);
@@ -698,14 +799,23 @@ dme_status step_graph(dme_plan_t p, double* P, int nsteps) {
                     if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
                 }
         }
-        p->graph_kernels = kernels;
-        e = cudaGraphInstantiate(&p->gexec, g, 0);
+        slot.kernels = kernels;
+        e = cudaGraphInstantiate(&slot.exec, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return set_error(std::string("graph instantiate: ") + cudaGetErrorString(e)), DME_ECUDA;
-        p->gP = P;
+        slot.P = P;
     }
-    for (int k = 0; k < nsteps; ++k) DME_CUDA_TRY(cudaGraphLaunch(p->gexec, p->st));
+    for (int k = 0; k < count; ++k) DME_CUDA_TRY(cudaGraphLaunch(slot.exec, p->st));
     return DME_OK;
+}
+
+// nsteps composition steps on P.  With fsal and nsteps >= 2 the outer half
+// steps of neighbouring steps are merged: head, nsteps - 1 interior parts, tail.
+dme_status step_graph(dme_plan_t p, double* P, int nsteps) {
+    if (!p->d.fsal || nsteps < 2) return replay(p, p->g_step, p->ops, P, nsteps);
+    DME_TRY(replay(p, p->g_head, p->ops_head, P, 1));
+    DME_TRY(replay(p, p->g_body, p->ops_body, P, nsteps - 1));
+    return replay(p, p->g_tail, p->ops_tail, P, 1);
 }
 
 template <typename F>
@@ -861,7 +971,10 @@ dme_status dme_sync(dme_plan_t plan) {
     return guarded([&] { return check_status(plan, "dme_sync"); });
 }
 
-int dme_plan_kernels_per_step(dme_plan_t plan) { return plan ? plan->graph_kernels : -1; }
+int dme_plan_kernels_per_step(dme_plan_t plan) {
+    if (!plan) return -1;
+    return plan->d.fsal && plan->g_body.exec ? plan->g_body.kernels : plan->g_step.kernels;
+}
 
 dme_status dme_gain(dme_plan_t plan, const double* P, double* K_out) {
     if (!plan || !P || !K_out) return set_error("plan, P and K_out are required"), DME_EINVAL;

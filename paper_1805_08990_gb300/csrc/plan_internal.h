@@ -17,7 +17,11 @@ struct EWEntry {
     SliceBuf Gsl;   // split path: slices of E^T (rows of E^T = columns of E)
 };
 
-enum OpKind { OP_CONG = 0, OP_AXPY = 1, OP_RICC = 2, OP_SFLOW = 3 };
+enum OpKind { OP_CONG = 0, OP_AXPY = 1, OP_RICC = 2, OP_SFLOW = 3, OP_COPY = 4, OP_COMBINE = 5 };
+
+// States an op acts on: the caller's P, and the two extra states of the
+// extrapolated scheme (accumulator and work copy).
+enum { BUF_P = 0, BUF_ACC = 1, BUF_WORK = 2 };
 
 struct Op {
     int kind;
@@ -26,6 +30,16 @@ struct Op {
     double wcoef;  // OP_CONG: coefficient of W (1 for T12, 0 for T1)
     double qcoef;  // fused T2: + qcoef Q
     int rule;      // OP_SFLOW: DME_T4_MIDPOINT / DME_T4_EULER
+    int buf;       // state the op updates (BUF_*)
+    int src;       // OP_COPY: buf <- src.  OP_COMBINE: buf <- c1 buf + c2 src (src < 0: none)
+    double c1, c2;
+};
+
+// An instantiated CUDA graph of one op list, valid for one state pointer.
+struct GraphSlot {
+    cudaGraphExec_t exec = nullptr;
+    double* P = nullptr;
+    int kernels = -1;
 };
 
 struct dme_plan_s {
@@ -48,13 +62,14 @@ struct dme_plan_s {
     int* status = nullptr;
     double normM = 0.0;
     std::vector<EWEntry> ew;
-    std::vector<Op> ops;
+    std::vector<Op> ops;                          // one step
+    std::vector<Op> ops_head, ops_body, ops_tail; // fsal: first, interior and closing parts
     double ops_h = -1.0;
+    double* xacc = nullptr;    // extrapolated scheme: accumulator state (n x n)
+    double* xwork = nullptr;   // extrapolated scheme with q >= 3: work state (n x n)
     std::vector<void*> allocs;
     size_t bytes = 0;
-    cudaGraphExec_t gexec = nullptr;
-    double* gP = nullptr;
-    int graph_kernels = -1;
+    GraphSlot g_step, g_head, g_body, g_tail;
     bool split = false;
     SliceBuf psl, usl, Ssl;    // split path: slices of P, of U = G P, and of S
     float2* U = nullptr;       // split path: G P as normalised (hi, lo) pairs

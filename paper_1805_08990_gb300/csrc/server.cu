@@ -392,6 +392,7 @@ dme_status dme_submit(dme_server_t s, const dme_plan_desc* desc, const double* A
     if (!s || !desc || !A || !QorC || !P0 || !ticket) return set_error("missing argument"), DME_EINVAL;
     if (!(T > 0.0) || nsteps < 1) return set_error("need T > 0 and nsteps >= 1"), DME_EINVAL;
     if (desc->prec != DME_FP64 && desc->prec != DME_SPLIT_BF16) return set_error("bad prec"), DME_EINVAL;
+    if (desc->fsal || desc->extrap > 1) return set_error("fsal and extrapolation are for plans only"), DME_EINVAL;
     if (desc->prec == DME_SPLIT_BF16 && desc->n > 4096) return set_error("split serving needs n <= 4096"), DME_EINVAL;
     for (int i = 0; i < desc->nflows; ++i)
         if (desc->flows[i] == DME_F4) return set_error("serving supports DLE/DRE schemes (no F4)"), DME_EINVAL;

@@ -270,3 +270,61 @@ def test_mass_matrix_plan_rejections():
     with pytest.raises(dme.DmeError):
         dme.Plan(dev(pr.A), C=dev(pr.C), h=0.01, flows=["F12", "F3", "F4"], B=dev(pr.B), R=dev(pr.R),
                  S=dev(np.eye(pr.n)), M=dev(pr.meta["M"]))
+
+
+# ---------------------------------------------------------------- FSAL merging, extrapolated Strang
+@pytest.mark.parametrize("prec", ["fp64", "split_bf16"])
+@pytest.mark.parametrize("scheme,N", [("F12F3", 12), ("F1F2F3", 7), ("F1F3F2", 2), ("F12F3", 1)])
+def test_fsal_matches_unmerged_oracle(prec, scheme, N):
+    """Merging T_a(h/2) T_a(h/2) of neighbouring Strang steps into T_a(h) is
+    exact for exact outer flows: the result is the unmerged scheme's."""
+    pr = W.dre_convdiff(nx=10, m=2, p=3)
+    flows = W.SCHEMES[scheme]
+    plan = plan_for(pr, flows, "strang", pr.T / N, prec=prec, fsal=True)
+    P = dev(pr.P0)
+    plan.step(P, N)
+    got = host(P)
+    ref = _oracle_solve(pr, flows, "strang", N)
+    assert rel(got, ref) < (FP64_TOL if prec == "fp64" else 1e-7)
+    assert np.array_equal(got, got.T)
+    if N >= 2:
+        plain = plan_for(pr, flows, "strang", pr.T / N, prec=prec)
+        plain.step(dev(pr.P0), 1)
+        assert plan.kernels_per_step() < plain.kernels_per_step()
+
+
+def test_fsal_dle_and_rejections():
+    pr = W.dle_heat(nx=9)
+    N = 10
+    plan = plan_for(pr, ["F1", "F2"], "strang", pr.T / N, fsal=True)
+    P = dev(pr.P0)
+    plan.step(P, N)
+    assert rel(host(P), _oracle_solve(pr, ["F1", "F2"], "strang", N)) < FP64_TOL
+    g = W.gdre_convdiff_padded(nx=5, n_pad=32, m=2, p=2)
+    for flows, comp in [(["F12", "F3"], "lie"), (["F12"], "strang"), (["F4", "F12"], "strang")]:
+        with pytest.raises(dme.DmeError):
+            plan_for(g, flows, comp, 0.01, fsal=True)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "split_bf16"])
+@pytest.mark.parametrize("q,scheme,N", [(2, "F12F3", 6), (3, "F12F3", 3), (4, "F1F2F3", 2), (2, "F1F2", 5)])
+def test_extrapolated_strang_matches_oracle(prec, q, scheme, N):
+    pr = W.dre_convdiff(nx=9, m=2, p=3) if "F3" in W.SCHEMES[scheme] else W.dle_heat(nx=9)
+    flows = W.SCHEMES[scheme]
+    plan = plan_for(pr, flows, "strang", pr.T / N, prec=prec, extrap=q)
+    P = dev(pr.P0)
+    plan.step(P, N)
+    got = host(P)
+    uses_B = "F3" in flows
+    ref = O.solve_extrapolated(pr.A, pr.Q, pr.P0, pr.T, N, q, flows=flows, B=pr.B if uses_B else None,
+                               R=pr.R if uses_B else None)
+    assert rel(got, ref) < (FP64_TOL if prec == "fp64" else 1e-7)
+    assert np.array_equal(got, got.T)
+
+
+def test_extrapolation_rejections():
+    g = W.gdre_convdiff_padded(nx=5, n_pad=32, m=2, p=2)
+    for flows, comp, q, fsal in [(["F12", "F3"], "lie", 2, False), (["F12", "F3", "F4"], "strang", 2, False),
+                                 (["F12", "F3"], "strang", 5, False), (["F12", "F3"], "strang", 2, True)]:
+        with pytest.raises(dme.DmeError):
+            plan_for(g, flows, comp, 0.01, extrap=q, fsal=fsal)

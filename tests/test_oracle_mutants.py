@@ -162,3 +162,27 @@ def test_order_pin_catches_rotated_strang_sequence():
     orders = pins.observed_orders(pins.scalar_dre_errors(mutant(step_sequence=_strang_wrong_order),
                                                           "F1F2F3", "strang"))
     assert min(orders) < 1.5
+
+
+def _weights_on_h_not_h2(q):
+    # the slip: Lagrange nodes 1/k (odd error terms) instead of 1/k^2
+    out = []
+    for k in range(1, q + 1):
+        g = 1.0
+        for j in range(1, q + 1):
+            if j != k:
+                g *= k / (k - j)
+        out.append(g)
+    return out
+
+
+def test_order_pin_catches_extrapolation_weights_on_h(monkeypatch):
+    import math
+    monkeypatch.setattr(core, "extrapolation_weights", _weights_on_h_not_h2)
+    A, Q, B, R = (np.array([[v]]) for v in (-1.0, 2.0, 1.0, 1.0))
+    exact = pins.scalar_dre_exact(-1.0, 1.0, 2.0, 1.0, 1.0)
+    errs = [abs(O.solve_extrapolated(A, Q, np.zeros((1, 1)), 1.0, 2 ** k, 2, B=B, R=R)[0, 0] - exact) / exact
+            for k in (2, 3, 4)]
+    ords = pins.observed_orders(errs)
+    assert not all(abs(o - 4.0) < 0.25 for o in ords), ords
+    assert all(math.isfinite(e) for e in errs)

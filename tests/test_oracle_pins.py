@@ -275,3 +275,38 @@ def test_mass_transform_identity_and_ode():
     Aw = np.linalg.solve(M, pr.A)
     wrong = O.solve(Aw, Qt, pr.P0, pr.T, 128, "strang", ["F12", "F3"], B=pr.B, R=pr.R)
     assert O.rel_fro(wrong, ref) > 100 * errs[-1]
+
+
+# ---------------------------------------------------------------- higher-order (extrapolated Strang)
+def test_extrapolation_weights_solve_the_moment_conditions():
+    """The weights reproduce constants and cancel the h^2, ..., h^(2q-2) error
+    terms: an independent Vandermonde solve of sum_k g_k k^(-2j) = [j == 0]."""
+    for q in (1, 2, 3, 4):
+        g = np.array(O.extrapolation_weights(q))
+        V = np.array([[float(k) ** (-2 * j) for k in range(1, q + 1)] for j in range(q)])
+        rhs = np.zeros(q)
+        rhs[0] = 1.0
+        assert np.allclose(g, np.linalg.solve(V, rhs), rtol=1e-13, atol=1e-13)
+    assert O.extrapolation_weights(2) == [-1.0 / 3.0, 4.0 / 3.0]
+
+
+@pytest.mark.parametrize("q,order", [(1, 2), (2, 4), (3, 6)])
+def test_extrapolated_strang_order_on_scalar_dre(q, order):
+    A, Q, B, R = (np.array([[v]]) for v in (-1.0, 2.0, 1.0, 1.0))
+    exact = pins.scalar_dre_exact(-1.0, 1.0, 2.0, 1.0, 1.0)
+    errs = [abs(O.solve_extrapolated(A, Q, np.zeros((1, 1)), 1.0, 2 ** k, q, B=B, R=R)[0, 0] - exact) / exact
+            for k in (2, 3, 4)]
+    ords = pins.observed_orders(errs)
+    assert all(abs(o - order) < 0.25 for o in ords), (errs, ords)
+
+
+def test_extrapolated_strang_order_on_matrix_dre():
+    A, Q, B, R, _ = pins.small_dre(seed=3)
+    n = A.shape[0]
+    ref = pins.ode_reference(A, Q, np.zeros((n, n)), 1.0, BRB=B @ np.linalg.solve(R, B.T))
+    errs = [O.rel_fro(O.solve_extrapolated(A, Q, np.zeros((n, n)), 1.0, 2 ** k, 2, B=B, R=R), ref)
+            for k in (2, 3, 4)]
+    ords = pins.observed_orders(errs)
+    assert all(abs(o - 4.0) < 0.35 for o in ords), (errs, ords)
+    with pytest.raises(ValueError):
+        O.solve_extrapolated(A, Q, np.zeros((n, n)), 1.0, 2, 2, flows=("F12", "F4"))
