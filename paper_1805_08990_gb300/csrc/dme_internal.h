@@ -57,10 +57,29 @@ struct GemmProb {
 
 constexpr int G64_BM = 64, G64_BN = 64, G64_BK = 16;
 
-// Enqueue a grouped FP64 GEMM over `probs` (host array); `dev_scratch` must
-// hold at least nprobs GemmProb and stay untouched until the kernel finished
-// (the launcher copies the descriptors there with cudaMemcpyAsync).
-dme_status gemm64_grouped(std::vector<GemmProb>& probs, GemmProb* dev_desc, cudaStream_t st);
+// Launch descriptors staged on the host and uploaded in one copy before the
+// launches that read them run (used when a launch sequence is captured into a
+// CUDA graph, where a per-launch host-to-device copy cannot be recorded).
+struct DescArena {
+    unsigned char* dev = nullptr;        // device block of `cap` bytes
+    size_t cap = 0;
+    std::vector<unsigned char> host;     // staged bytes; host[i] goes to dev[i]
+    // Stage `bytes` from src (256-byte aligned); returns the device address, or
+    // nullptr when the block is full.
+    void* put(const void* src, size_t bytes);
+};
+
+// Enqueue a grouped FP64 GEMM over `probs` (host array).  Descriptors of more
+// than 8 problems go to device memory: staged in `arena` when given, else
+// copied to `dev_desc` with cudaMemcpyAsync (which must then stay untouched
+// until the kernel finished).  `tile` is the square output tile, 32 or 64: both
+// accumulate every output over k in the same order, so they give bit-identical
+// results and the choice is purely a matter of speed.  The grid is persistent
+// (at most the resident CTA count; CTAs stride over the tiles).
+dme_status gemm64_grouped(std::vector<GemmProb>& probs, GemmProb* dev_desc, cudaStream_t st,
+                          DescArena* arena = nullptr, int tile = 64);
+// Query the persistent grid sizes ahead of any stream capture.
+void gemm64_prepare();
 
 // ---------------------------------------------------------------- small kernels
 void launch_axpy_sym(double* P, const double* Q, double a, int n, int ld, cudaStream_t st);
@@ -105,7 +124,8 @@ RicItem make_ric_item(double* P, const double* Bt, int n, int m, double t, const
                       double* work, int* status);
 // Grouped launch over independent problems; more than 8 need `dev_desc`
 // (riccati_desc_bytes() per problem, untouched until the kernels finish).
-dme_status launch_riccati_grouped(const std::vector<RicItem>& items, void* dev_desc, cudaStream_t st);
+dme_status launch_riccati_grouped(const std::vector<RicItem>& items, void* dev_desc, cudaStream_t st,
+                                  DescArena* arena = nullptr);
 size_t riccati_desc_bytes();
 // K (m x n) = R^{-1} B^T P from Bt = B L^{-T} and L (R = L L^T); work as for launch_riccati.
 dme_status launch_lqr_gain(const double* P, const double* Bt, const double* LR, int n, int m, double* work,

@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 namespace dme {
 
@@ -36,23 +37,27 @@ __device__ __forceinline__ void tile_coords(const GemmProb& pb, int lt, int& ti,
     }
 }
 
-__device__ __forceinline__ void gemm64_tile(const GemmProb& pb, int lt) {
-    __shared__ double As[G64_BK][G64_BM + 1];
-    __shared__ double Bs[G64_BK][G64_BN + 1];
+// One BM x BM output tile (BM = 32 or 64) with 256 threads, each holding a
+// TM x TM register tile (TM = BM / 16).  Every output is accumulated over k in
+// increasing order with fma, whatever BM is.
+template <int BM>
+__device__ __forceinline__ void gemm64_tile(const GemmProb& pb, int lt, double (&As)[G64_BK][BM + 1],
+                                            double (&Bs)[G64_BK][BM + 1]) {
+    constexpr int TM = BM / 16;
     int ti, tj;
     tile_coords(pb, lt, ti, tj);
-    const int row0 = ti * G64_BM, col0 = tj * G64_BN;
+    const int row0 = ti * BM, col0 = tj * BM;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    double acc[4][4];
+    double acc[TM][TM];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        for (int j = 0; j < TM; ++j) acc[i][j] = 0.0;
 
     for (int k0 = 0; k0 < pb.K; k0 += G64_BK) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int e = tid + 256 * q;
+        for (int q = 0; q < TM; ++q) {
+            const int e = tid + 256 * q;     // BM x 16 elements of each operand tile
             int r, k;
             double v = 0.0;
             if (!pb.transA) {
@@ -61,8 +66,8 @@ __device__ __forceinline__ void gemm64_tile(const GemmProb& pb, int lt) {
                 int gr = row0 + r, gk = k0 + k;
                 if (gr < pb.M && gk < pb.K) v = pb.A[(size_t)gr * pb.lda + gk];
             } else {
-                r = e & 63;
-                k = e >> 6;
+                r = e % BM;
+                k = e / BM;
                 int gr = row0 + r, gk = k0 + k;
                 if (gr < pb.M && gk < pb.K) v = pb.A[(size_t)gk * pb.lda + gr];
             }
@@ -70,8 +75,8 @@ __device__ __forceinline__ void gemm64_tile(const GemmProb& pb, int lt) {
             int c;
             double w = 0.0;
             if (!pb.transB) {
-                c = e & 63;
-                k = e >> 6;
+                c = e % BM;
+                k = e / BM;
                 int gc = col0 + c, gk = k0 + k;
                 if (gc < pb.N && gk < pb.K) w = pb.B[(size_t)gk * pb.ldb + gc];
             } else {
@@ -85,25 +90,25 @@ __device__ __forceinline__ void gemm64_tile(const GemmProb& pb, int lt) {
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < G64_BK; ++k) {
-            double a[4], b[4];
+            double a[TM], b[TM];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+            for (int i = 0; i < TM; ++i) a[i] = As[k][ty + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + 16 * j];
+            for (int j = 0; j < TM; ++j) b[j] = Bs[k][tx + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < TM; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
         __syncthreads();
     }
 
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < TM; ++i) {
         const int r = row0 + ty + 16 * i;
         if (r >= pb.M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < TM; ++j) {
             const int c = col0 + tx + 16 * j;
             if (c >= pb.N) continue;
             if (pb.tri && r > c) continue;
@@ -128,23 +133,32 @@ __device__ __forceinline__ int find_prob(const GemmProb* probs, int nprobs, int 
     return lo;
 }
 
-__global__ void __launch_bounds__(256) gemm64_batch_kernel(const __grid_constant__ GemmBatch batch) {
-    const int t = blockIdx.x;
-    const int ip = find_prob(batch.p, batch.nprobs, t);
-    gemm64_tile(batch.p[ip], t - batch.p[ip].tile_start);
+// Persistent: CTA b takes tiles b, b + gridDim.x, ... of the concatenated tile list.
+template <int BM>
+__global__ void __launch_bounds__(256) gemm64_batch_kernel(const __grid_constant__ GemmBatch batch, int total) {
+    __shared__ double As[G64_BK][BM + 1];
+    __shared__ double Bs[G64_BK][BM + 1];
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        const int ip = find_prob(batch.p, batch.nprobs, t);
+        gemm64_tile<BM>(batch.p[ip], t - batch.p[ip].tile_start, As, Bs);
+    }
 }
 
-__global__ void __launch_bounds__(256) gemm64_desc_kernel(const GemmProb* __restrict__ probs, int nprobs) {
-    const int t = blockIdx.x;
-    const int ip = find_prob(probs, nprobs, t);
-    GemmProb pb = probs[ip];
-    gemm64_tile(pb, t - pb.tile_start);
+template <int BM>
+__global__ void __launch_bounds__(256) gemm64_desc_kernel(const GemmProb* __restrict__ probs, int nprobs, int total) {
+    __shared__ double As[G64_BK][BM + 1];
+    __shared__ double Bs[G64_BK][BM + 1];
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        const int ip = find_prob(probs, nprobs, t);
+        GemmProb pb = probs[ip];
+        gemm64_tile<BM>(pb, t - pb.tile_start, As, Bs);
+    }
 }
 
-static int prepare_tiles(std::vector<GemmProb>& probs) {
+static int prepare_tiles(std::vector<GemmProb>& probs, int bm) {
     int total = 0;
     for (auto& p : probs) {
-        int tm = (p.M + G64_BM - 1) / G64_BM, tn = (p.N + G64_BN - 1) / G64_BN;
+        int tm = (p.M + bm - 1) / bm, tn = (p.N + bm - 1) / bm;
         p.tiles_n = tn;
         p.ntiles = (p.M <= 0 || p.N <= 0) ? 0 : (p.tri ? tn * (tn + 1) / 2 : tm * tn);
         p.tile_start = total;
@@ -153,36 +167,87 @@ static int prepare_tiles(std::vector<GemmProb>& probs) {
     return total;
 }
 
-dme_status gemm64_grouped(std::vector<GemmProb>& probs, GemmProb* dev_desc, cudaStream_t st) {
+void* DescArena::put(const void* src, size_t bytes) {
+    size_t off = (host.size() + 255) & ~size_t(255);
+    if (off + bytes > cap || !dev) return nullptr;
+    host.resize(off + bytes);
+    std::memcpy(host.data() + off, src, bytes);
+    return dev + off;
+}
+
+// Resident CTAs of a kernel on the whole device (persistent grid size).
+template <typename K>
+static int resident_ctas(K kernel, int threads) {
+    int dev = 0, nsm = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1 << 20;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1 << 20;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return nsm * per_sm;
+}
+
+template <int BM>
+static int batch_cap() {
+    static int cap = resident_ctas(gemm64_batch_kernel<BM>, 256);
+    return cap;
+}
+
+template <int BM>
+static int desc_cap() {
+    static int cap = resident_ctas(gemm64_desc_kernel<BM>, 256);
+    return cap;
+}
+
+void gemm64_prepare() {
+    batch_cap<32>();
+    batch_cap<64>();
+    desc_cap<32>();
+    desc_cap<64>();
+}
+
+template <int BM>
+static dme_status gemm64_launch(std::vector<GemmProb>& live, GemmProb* dev_desc, cudaStream_t st, DescArena* arena) {
+    const int total = prepare_tiles(live, BM);
+    if (total == 0) return DME_OK;
+    if ((int)live.size() <= kMaxBatch) {
+        const int cap = batch_cap<BM>();
+        GemmBatch b;
+        std::memset(&b, 0, sizeof(b));
+        b.nprobs = (int)live.size();
+        for (int i = 0; i < b.nprobs; ++i) b.p[i] = live[i];
+        gemm64_batch_kernel<BM><<<std::min(total, cap), 256, 0, st>>>(b, total);
+    } else {
+        const int cap = desc_cap<BM>();
+        const size_t bytes = live.size() * sizeof(GemmProb);
+        GemmProb* d = dev_desc;
+        if (arena) {
+            d = static_cast<GemmProb*>(arena->put(live.data(), bytes));
+            if (!d) return set_error("gemm64: descriptor arena full"), DME_ENOMEM;
+        } else {
+            if (!d) return set_error("gemm64: more than 8 problems need a device descriptor buffer"), DME_EINVAL;
+            DME_CUDA_TRY(cudaMemcpyAsync(d, live.data(), bytes, cudaMemcpyHostToDevice, st));
+        }
+        gemm64_desc_kernel<BM><<<std::min(total, cap), 256, 0, st>>>(d, (int)live.size(), total);
+    }
+    DME_CUDA_TRY(cudaGetLastError());
+    return DME_OK;
+}
+
+dme_status gemm64_grouped(std::vector<GemmProb>& probs, GemmProb* dev_desc, cudaStream_t st, DescArena* arena,
+                          int tile) {
     for (auto& p : probs) {
         if (p.tri && p.M != p.N) {
             set_error("gemm64: triangle mode needs M == N");
             return DME_EINVAL;
         }
     }
+    if (tile != 32 && tile != 64) return set_error("gemm64: tile must be 32 or 64"), DME_EINVAL;
     // drop empty problems, keep order
     std::vector<GemmProb> live;
     for (auto& p : probs)
         if (p.M > 0 && p.N > 0) live.push_back(p);
     if (live.empty()) return DME_OK;
-    const int total = prepare_tiles(live);
-    if (total == 0) return DME_OK;
-    if ((int)live.size() <= kMaxBatch) {
-        GemmBatch b;
-        b.nprobs = (int)live.size();
-        for (int i = 0; i < b.nprobs; ++i) b.p[i] = live[i];
-        gemm64_batch_kernel<<<total, 256, 0, st>>>(b);
-    } else {
-        if (!dev_desc) {
-            set_error("gemm64: more than 8 problems need a device descriptor buffer");
-            return DME_EINVAL;
-        }
-        DME_CUDA_TRY(cudaMemcpyAsync(dev_desc, live.data(), live.size() * sizeof(GemmProb),
-                                     cudaMemcpyHostToDevice, st));
-        gemm64_desc_kernel<<<total, 256, 0, st>>>(dev_desc, (int)live.size());
-    }
-    DME_CUDA_TRY(cudaGetLastError());
-    return DME_OK;
+    return tile == 32 ? gemm64_launch<32>(live, dev_desc, st, arena) : gemm64_launch<64>(live, dev_desc, st, arena);
 }
 
 // ============================================================== elementwise

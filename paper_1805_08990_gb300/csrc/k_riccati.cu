@@ -324,7 +324,8 @@ RicItem make_ric_item(double* P, const double* Bt, int n, int m, double t, const
     return it;
 }
 
-dme_status launch_riccati_grouped(const std::vector<RicItem>& items, void* dev_desc, cudaStream_t st) {
+dme_status launch_riccati_grouped(const std::vector<RicItem>& items, void* dev_desc, cudaStream_t st,
+                                  DescArena* arena) {
     if (items.empty()) return DME_OK;
     std::vector<RicDesc> ds(items.size());
     int sz = 0, sy = 0, su = 0;
@@ -359,11 +360,16 @@ dme_status launch_riccati_grouped(const std::vector<RicItem>& items, void* dev_d
         for (size_t k = 0; k < ds.size(); ++k) b.local[k] = ds[k];
         b.dev = nullptr;
     } else {
-        if (!dev_desc) {
-            set_error("grouped Riccati: more than 8 problems need a device descriptor buffer");
-            return DME_EINVAL;
+        if (arena) {
+            dev_desc = arena->put(ds.data(), ds.size() * sizeof(RicDesc));
+            if (!dev_desc) return set_error("grouped Riccati: descriptor arena full"), DME_ENOMEM;
+        } else {
+            if (!dev_desc) {
+                set_error("grouped Riccati: more than 8 problems need a device descriptor buffer");
+                return DME_EINVAL;
+            }
+            DME_CUDA_TRY(cudaMemcpyAsync(dev_desc, ds.data(), ds.size() * sizeof(RicDesc), cudaMemcpyHostToDevice, st));
         }
-        DME_CUDA_TRY(cudaMemcpyAsync(dev_desc, ds.data(), ds.size() * sizeof(RicDesc), cudaMemcpyHostToDevice, st));
         b.dev = reinterpret_cast<const RicDesc*>(dev_desc);
     }
     riccati_z_kernel<<<sz, 256, 0, st>>>(b);

@@ -658,7 +658,17 @@ dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzPar
 
 static bool g_attr_grouped_set = false;
 
-dme_status launch_ozaki_grouped(std::vector<OzGroupDesc>& items, OzGroupDesc* dev_desc, cudaStream_t st) {
+dme_status ozaki_grouped_prepare() {
+    if (!g_attr_grouped_set) {
+        DME_CUDA_TRY(cudaFuncSetAttribute(ozaki_gemm_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          OZ_SMEM_BYTES));
+        g_attr_grouped_set = true;
+    }
+    return DME_OK;
+}
+
+dme_status launch_ozaki_grouped(std::vector<OzGroupDesc>& items, OzGroupDesc* dev_desc, cudaStream_t st,
+                                DescArena* arena) {
     int total = 0;
     std::vector<OzGroupDesc> live;
     for (auto& it : items) {
@@ -680,9 +690,14 @@ dme_status launch_ozaki_grouped(std::vector<OzGroupDesc>& items, OzGroupDesc* de
                                           OZ_SMEM_BYTES));
         g_attr_grouped_set = true;
     }
-    DME_CUDA_TRY(cudaMemcpyAsync(dev_desc, live.data(), live.size() * sizeof(OzGroupDesc), cudaMemcpyHostToDevice,
-                                 st));
-    ozaki_gemm_grouped_kernel<<<total, OZ_THREADS, OZ_SMEM_BYTES, st>>>(dev_desc, (int)live.size());
+    OzGroupDesc* d = dev_desc;
+    if (arena) {
+        d = static_cast<OzGroupDesc*>(arena->put(live.data(), live.size() * sizeof(OzGroupDesc)));
+        if (!d) return set_error("ozaki grouped gemm: descriptor arena full"), DME_ENOMEM;
+    } else {
+        DME_CUDA_TRY(cudaMemcpyAsync(d, live.data(), live.size() * sizeof(OzGroupDesc), cudaMemcpyHostToDevice, st));
+    }
+    ozaki_gemm_grouped_kernel<<<total, OZ_THREADS, OZ_SMEM_BYTES, st>>>(d, (int)live.size());
     DME_CUDA_TRY(cudaGetLastError());
     return DME_OK;
 }

@@ -13,6 +13,13 @@
 //    with the slicing of P and U in between) and one grouped launch per
 //    Riccati kernel, covering all residents at that stage.  Requests admitted between rounds join the next
 //    round; finished ones leave after it.
+// A round is captured once into a CUDA graph for a given set of residents (its
+// launch descriptors staged in one device arena) and replayed until the set
+// changes; between host checks the stepper replays several rounds back to back
+// when no resident finishes and nobody waits for admission.  The FP64 grouped
+// GEMM's output tile (32 or 64) is chosen per group size by an online
+// autotuner that times both variants on the group's first P E product (which
+// only writes scratch); both tiles give bit-identical results.
 // Grouped kernels compute each problem's tiles exactly as they would alone
 // (no cross-request reduction), so a result is bit-identical alone or in a mix.
 // Latency is measured from dme_submit to the end of the round that finished it.
@@ -23,6 +30,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -77,11 +85,13 @@ struct dme_server_s {
     std::thread admit_thr, step_thr;
     cudaStream_t st = nullptr;
     int* dstat = nullptr;         // per-slot device status words
-    void* gdesc = nullptr;        // grouped GEMM descriptors
-    void* rdesc = nullptr;        // grouped Riccati descriptors
-    OzGroupDesc* odesc = nullptr; // grouped split-GEMM descriptors (2 x max_slots)
+    DescArena arena;              // launch descriptors of the captured round
+    GemmProb* tune_desc = nullptr;  // autotuner's descriptor buffer (max_slots)
+    cudaGraphExec_t round_exec = nullptr;
+    std::vector<Req*> round_members;   // the residents the captured round serves, in order
+    std::map<int, int> tile_choice;    // autotuner: ceil(log2(64-tiles of a group)) -> tile 32 / 64
     std::vector<double> lat_ms;
-    int completed = 0, failed = 0, rounds = 0;
+    int completed = 0, failed = 0, rounds = 0, graph_builds = 0, tuned = 0;
     double t_first = -1, t_last = 0;
     std::string stats;
 };
@@ -175,70 +185,149 @@ void admit_loop(dme_server_t s) {
     }
 }
 
-// One scheduler round over the resident requests: stage by stage, grouped launches.
-dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
+// Stage-by-stage work lists of one round.
+struct StageLists {
+    std::vector<GemmProb> g1, g2;
+    std::vector<RicItem> ric;
+    std::vector<Req*> sc;       // split-precision congruences
+    std::vector<Req*> axpy;     // standalone T2
+};
+
+dme_status stage_lists(dme_server_t s, std::vector<Req*>& res, size_t k, StageLists& L) {
+    for (Req* r : res) {
+        if (k >= r->plan->ops.size()) continue;
+        const Op& o = r->plan->ops[k];
+        dme_plan_t p = r->plan;
+        const int n = p->n;
+        if (o.kind == OP_CONG && p->split) {
+            L.sc.push_back(r);
+        } else if (o.kind == OP_CONG) {
+            const EWEntry& e = p->ew[o.ew];
+            GemmProb a;
+            std::memset(&a, 0, sizeof(a));
+            a.A = r->P;
+            a.B = e.E;
+            a.C = p->X;
+            a.M = a.N = a.K = n;
+            a.lda = a.ldb = a.ldc = a.ldd = n;
+            a.alpha = 1.0;
+            L.g1.push_back(a);
+            GemmProb b;
+            std::memset(&b, 0, sizeof(b));
+            b.A = e.E;
+            b.transA = 1;
+            b.B = p->X;
+            b.C = r->P;
+            b.M = b.N = b.K = n;
+            b.lda = b.ldb = b.ldc = b.ldd = n;
+            b.alpha = 1.0;
+            b.tri = 1;
+            if (o.wcoef != 0.0) {
+                b.D1 = e.W;
+                b.b1 = o.wcoef;
+            }
+            if (o.qcoef != 0.0) {
+                b.D2 = p->Q;
+                b.b2 = o.qcoef;
+            }
+            L.g2.push_back(b);
+        } else if (o.kind == OP_RICC) {
+            L.ric.push_back(make_ric_item(r->P, p->Bt, n, p->m, o.tau, o.qcoef != 0.0 ? p->Q : nullptr, o.qcoef,
+                                          p->rwork, s->dstat + r->slot));
+        } else if (o.kind == OP_AXPY) {
+            L.axpy.push_back(r);
+        } else {
+            set_error("serving: unsupported op");
+            return DME_EINVAL;
+        }
+    }
+    return DME_OK;
+}
+
+size_t round_stages(const std::vector<Req*>& res) {
     size_t stages = 0;
     for (Req* r : res) stages = std::max(stages, r->plan->ops.size());
+    return stages;
+}
+
+int tile_key(const std::vector<GemmProb>& g) {
+    long tiles = 0;
+    for (auto& p : g) tiles += (long)((p.M + 63) / 64) * ((p.N + 63) / 64);
+    int key = 0;
+    while ((1L << key) < tiles) ++key;
+    return key;
+}
+
+// Autotuner: for every FP64 group size class not seen before, time the grouped
+// P E product (it writes only each plan's scratch X) with 32- and 64-wide tiles
+// and keep the faster.  Runs eagerly, before the round is captured.
+dme_status tune_tiles(dme_server_t s, std::vector<Req*>& res) {
+    const size_t stages = round_stages(res);
     for (size_t k = 0; k < stages; ++k) {
-        std::vector<GemmProb> g1, g2;
-        std::vector<RicItem> ric;
-        std::vector<Req*> sc;                          // split-precision congruences at this stage
-        for (Req* r : res) {
-            if (k >= r->plan->ops.size()) continue;
-            const Op& o = r->plan->ops[k];
-            dme_plan_t p = r->plan;
-            const int n = p->n;
-            if (o.kind == OP_CONG && p->split) {
-                sc.push_back(r);
-            } else if (o.kind == OP_CONG) {
-                const EWEntry& e = p->ew[o.ew];
-                GemmProb a;
-                std::memset(&a, 0, sizeof(a));
-                a.A = r->P;
-                a.B = e.E;
-                a.C = p->X;
-                a.M = a.N = a.K = n;
-                a.lda = a.ldb = a.ldc = a.ldd = n;
-                a.alpha = 1.0;
-                g1.push_back(a);
-                GemmProb b;
-                std::memset(&b, 0, sizeof(b));
-                b.A = e.E;
-                b.transA = 1;
-                b.B = p->X;
-                b.C = r->P;
-                b.M = b.N = b.K = n;
-                b.lda = b.ldb = b.ldc = b.ldd = n;
-                b.alpha = 1.0;
-                b.tri = 1;
-                if (o.wcoef != 0.0) {
-                    b.D1 = e.W;
-                    b.b1 = o.wcoef;
-                }
-                if (o.qcoef != 0.0) {
-                    b.D2 = p->Q;
-                    b.b2 = o.qcoef;
-                }
-                g2.push_back(b);
-            } else if (o.kind == OP_RICC) {
-                ric.push_back(make_ric_item(r->P, p->Bt, n, p->m, o.tau, o.qcoef != 0.0 ? p->Q : nullptr, o.qcoef,
-                                            p->rwork, s->dstat + r->slot));
-            } else if (o.kind == OP_AXPY) {
-                launch_axpy_sym(r->P, p->Q, o.qcoef, n, n, s->st);
-            } else {
-                set_error("serving: unsupported op");
-                return DME_EINVAL;
+        StageLists L;
+        DME_TRY(stage_lists(s, res, k, L));
+        if (L.g1.empty()) continue;
+        const int key = tile_key(L.g1);
+        if (s->tile_choice.count(key)) continue;
+        cudaEvent_t a = nullptr, b = nullptr;
+        DME_CUDA_TRY(cudaEventCreate(&a));
+        DME_CUDA_TRY(cudaEventCreate(&b));
+        int best = 64;
+        float best_ms = 0.0f;
+        dme_status st = DME_OK;
+        for (int tile : {64, 32}) {
+            std::vector<GemmProb> g = L.g1;
+            st = gemm64_grouped(g, s->tune_desc, s->st, nullptr, tile);   // warm-up
+            float ms = 0.0f;
+            for (int rep = 0; rep < 3 && st == DME_OK; ++rep) {
+                g = L.g1;
+                cudaEventRecord(a, s->st);
+                st = gemm64_grouped(g, s->tune_desc, s->st, nullptr, tile);
+                cudaEventRecord(b, s->st);
+                cudaEventSynchronize(b);
+                float t = 0.0f;
+                cudaEventElapsedTime(&t, a, b);
+                ms = (rep == 0) ? t : std::min(ms, t);
+            }
+            if (st != DME_OK) break;
+            if (tile == 64 || ms < best_ms) {
+                best_ms = ms;
+                best = tile;
             }
         }
-        if (!g1.empty()) {
-            DME_TRY(gemm64_grouped(g1, reinterpret_cast<GemmProb*>(s->gdesc), s->st));
-            DME_TRY(gemm64_grouped(g2, reinterpret_cast<GemmProb*>(s->gdesc) + s->max_slots, s->st));
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        DME_TRY(st);
+        DME_CUDA_TRY(cudaStreamSynchronize(s->st));
+        s->tile_choice[key] = best;
+        s->tuned++;
+    }
+    return DME_OK;
+}
+
+// Enqueue one scheduler round over the residents: stage by stage, grouped
+// launches, descriptors staged in the arena (no host synchronisation: the
+// sequence is captured into a graph).
+dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
+    const size_t stages = round_stages(res);
+    for (size_t k = 0; k < stages; ++k) {
+        StageLists L;
+        DME_TRY(stage_lists(s, res, k, L));
+        for (Req* r : L.axpy) {
+            const Op& o = r->plan->ops[k];
+            launch_axpy_sym(r->P, r->plan->Q, o.qcoef, r->plan->n, r->plan->n, s->st);
         }
-        if (!sc.empty()) {
+        if (!L.g1.empty()) {
+            auto it = s->tile_choice.find(tile_key(L.g1));
+            const int tile = it == s->tile_choice.end() ? 64 : it->second;
+            DME_TRY(gemm64_grouped(L.g1, nullptr, s->st, &s->arena, tile));
+            DME_TRY(gemm64_grouped(L.g2, nullptr, s->st, &s->arena, tile));
+        }
+        if (!L.sc.empty()) {
             // the split congruence G P G^T of every request: slice P, grouped U = G P,
             // slice U, grouped G U^T (upper tiles, FP64 + W / tQ, mirrored)
             std::vector<OzGroupDesc> o1, o2;
-            for (Req* r : sc) {
+            for (Req* r : L.sc) {
                 dme_plan_t p = r->plan;
                 const Op& o = p->ops[k];
                 const EWEntry& e = p->ew[o.ew];
@@ -281,16 +370,47 @@ dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
                 b.p.status = s->dstat + r->slot;
                 o2.push_back(b);
             }
-            DME_TRY(launch_ozaki_grouped(o1, s->odesc, s->st));
-            for (Req* r : sc) launch_slice_rows_pair(r->plan->U, r->plan->n, r->plan->n, r->plan->n, r->plan->usl, s->st);
-            DME_TRY(launch_ozaki_grouped(o2, s->odesc + s->max_slots, s->st));
+            DME_TRY(launch_ozaki_grouped(o1, nullptr, s->st, &s->arena));
+            for (Req* r : L.sc)
+                launch_slice_rows_pair(r->plan->U, r->plan->n, r->plan->n, r->plan->n, r->plan->usl, s->st);
+            DME_TRY(launch_ozaki_grouped(o2, nullptr, s->st, &s->arena));
         }
-        if (!ric.empty()) DME_TRY(launch_riccati_grouped(ric, s->rdesc, s->st));
-        // descriptors are uploaded per launch from host memory: wait before the next stage reuses them
-        DME_CUDA_TRY(cudaStreamSynchronize(s->st));
+        if (!L.ric.empty()) DME_TRY(launch_riccati_grouped(L.ric, nullptr, s->st, &s->arena));
     }
+    DME_CUDA_TRY(cudaGetLastError());
     return DME_OK;
 }
+
+// (Re)capture the round for the current residents and upload its descriptors.
+dme_status build_round_graph(dme_server_t s, std::vector<Req*>& res) {
+    DME_CUDA_TRY(cudaStreamSynchronize(s->st));
+    if (s->round_exec) {
+        cudaGraphExecDestroy(s->round_exec);
+        s->round_exec = nullptr;
+    }
+    s->round_members.clear();
+    DME_TRY(tune_tiles(s, res));
+    s->arena.host.clear();
+    cudaGraph_t g = nullptr;
+    DME_CUDA_TRY(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+    dme_status st = run_round(s, res);
+    cudaError_t e = cudaStreamEndCapture(s->st, &g);
+    if (st != DME_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return set_error(std::string("serving: graph capture: ") + cudaGetErrorString(e)), DME_ECUDA;
+    e = cudaGraphInstantiate(&s->round_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return set_error(std::string("serving: graph instantiate: ") + cudaGetErrorString(e)), DME_ECUDA;
+    if (!s->arena.host.empty())
+        DME_CUDA_TRY(cudaMemcpy(s->arena.dev, s->arena.host.data(), s->arena.host.size(), cudaMemcpyHostToDevice));
+    s->round_members = res;
+    s->graph_builds++;
+    return DME_OK;
+}
+
+constexpr int kMaxRoundsPerCheck = 16;
 
 void step_loop(dme_server_t s) {
     std::vector<Req*> res;
@@ -303,7 +423,24 @@ void step_loop(dme_server_t s) {
             for (Req* r : s->ready) res.push_back(r);
             s->ready.clear();
         }
-        dme_status st = run_round(s, res);
+        dme_status st = DME_OK;
+        if (!s->round_exec || s->round_members != res) st = build_round_graph(s, res);
+        // rounds before the next host check: none of the residents finishes
+        // earlier, and one round only while requests wait for admission
+        int R = kMaxRoundsPerCheck;
+        for (Req* r : res) R = std::min(R, r->nsteps - r->done_steps);
+        {
+            std::lock_guard<std::mutex> g(s->mu);
+            if (!s->queue.empty() || !s->ready.empty()) R = 1;
+        }
+        R = std::max(R, 1);
+        for (int i = 0; i < R && st == DME_OK; ++i) {
+            cudaError_t e = cudaGraphLaunch(s->round_exec, s->st);
+            if (e != cudaSuccess) {
+                st = DME_ECUDA;
+                set_error(std::string("serving: graph launch: ") + cudaGetErrorString(e));
+            }
+        }
         std::string err = get_error();
         if (st == DME_OK) {
             cudaError_t e = cudaMemcpyAsync(hstat.data(), s->dstat, sizeof(int) * s->max_slots,
@@ -314,7 +451,7 @@ void step_loop(dme_server_t s) {
                 err = std::string("serving: ") + cudaGetErrorString(e);
             }
         }
-        s->rounds++;
+        s->rounds += R;
         std::vector<Req*> keep;
         for (Req* r : res) {
             dme_status rs = st;
@@ -325,7 +462,7 @@ void step_loop(dme_server_t s) {
                                            : "serving: device status " + std::to_string(hstat[r->slot]);
                 cudaMemsetAsync(s->dstat + r->slot, 0, sizeof(int), s->st);
             }
-            if (rs == DME_OK) r->done_steps++;
+            if (rs == DME_OK) r->done_steps += R;
             if (rs != DME_OK || r->done_steps >= r->nsteps) {
                 if (rs == DME_OK) {
                     r->out.resize((size_t)r->desc.n * r->desc.n);
@@ -366,17 +503,29 @@ dme_status dme_server_create(size_t hbm_budget_bytes, int max_slots, dme_server_
     cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&s->dstat, sizeof(int) * max_slots);
     if (e == cudaSuccess) e = cudaMemset(s->dstat, 0, sizeof(int) * max_slots);
-    if (e == cudaSuccess) e = cudaMalloc(&s->gdesc, sizeof(GemmProb) * 2 * max_slots);
-    if (e == cudaSuccess) e = cudaMalloc(&s->rdesc, riccati_desc_bytes() * max_slots);
-    if (e == cudaSuccess) e = cudaMalloc(&s->odesc, sizeof(OzGroupDesc) * 2 * max_slots);
+    // descriptors of up to kMaxStages stages: two GEMM groups, two split-GEMM
+    // groups and one Riccati group per stage, each put 256-byte aligned
+    constexpr size_t kMaxStages = 8;
+    s->arena.cap = kMaxStages * (2 * sizeof(GemmProb) * max_slots + 2 * sizeof(OzGroupDesc) * max_slots +
+                                 riccati_desc_bytes() * max_slots + 5 * 256);
+    if (e == cudaSuccess) e = cudaMalloc(&s->arena.dev, s->arena.cap);
+    if (e == cudaSuccess) e = cudaMalloc(&s->tune_desc, sizeof(GemmProb) * max_slots);
     if (e != cudaSuccess) {
         set_error(std::string("dme_server_create: ") + cudaGetErrorString(e));
         cudaGetLastError();
         if (s->st) cudaStreamDestroy(s->st);
         cudaFree(s->dstat);
-        cudaFree(s->gdesc);
-        cudaFree(s->rdesc);
-        cudaFree(s->odesc);
+        cudaFree(s->arena.dev);
+        cudaFree(s->tune_desc);
+        delete s;
+        return DME_ECUDA;
+    }
+    gemm64_prepare();
+    if (ozaki_grouped_prepare() != DME_OK) {
+        cudaStreamDestroy(s->st);
+        cudaFree(s->dstat);
+        cudaFree(s->arena.dev);
+        cudaFree(s->tune_desc);
         delete s;
         return DME_ECUDA;
     }
@@ -466,11 +615,14 @@ const char* dme_server_stats(dme_server_t s) {
     for (auto& kv : s->reqs)
         if (kv.second->state == Q_RESIDENT || kv.second->state == Q_PLANNING) ++resident;
     const double span = (s->t_first >= 0 && s->t_last > s->t_first) ? s->t_last - s->t_first : 0.0;
+    int t32 = 0;
+    for (auto& kv : s->tile_choice) t32 += kv.second == 32;
     char buf[512];
     snprintf(buf, sizeof(buf),
              "{\"completed\": %d, \"failed\": %d, \"resident\": %d, \"queued\": %d, \"rounds\": %d, "
+             "\"graph_builds\": %d, \"tuned_groups\": %d, \"tiles32\": %d, "
              "\"p50_ms\": %.3f, \"p99_ms\": %.3f, \"solves_per_s\": %.4f, \"reserved_bytes\": %zu}",
-             s->completed, s->failed, resident, queued, s->rounds, pct(0.5), pct(0.99),
+             s->completed, s->failed, resident, queued, s->rounds, s->graph_builds, s->tuned, t32, pct(0.5), pct(0.99),
              span > 0 ? s->completed / span : 0.0, s->reserved);
     s->stats = buf;
     return s->stats.c_str();
@@ -491,10 +643,10 @@ dme_status dme_server_destroy(dme_server_t s) {
         if (r->P && r->plan) cudaFreeAsync(r->P, r->plan->st);
         if (r->plan) free_plan(r->plan);
     }
+    if (s->round_exec) cudaGraphExecDestroy(s->round_exec);
     cudaFree(s->dstat);
-    cudaFree(s->gdesc);
-    cudaFree(s->rdesc);
-    cudaFree(s->odesc);
+    cudaFree(s->arena.dev);
+    cudaFree(s->tune_desc);
     cudaStreamDestroy(s->st);
     delete s;
     return DME_OK;

@@ -70,6 +70,10 @@ void launch_slice_rows_f64(const double* X, int rows, int cols, int ldx, const S
 void launch_slice_rows_pair(const float2* Xp, int rows, int cols, int ldx, const SliceBuf& sb, cudaStream_t st);
 dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzParams p, cudaStream_t st);
 // Grouped launch over independent problems; dev_desc holds items.size() descriptors.
-dme_status launch_ozaki_grouped(std::vector<OzGroupDesc>& items, OzGroupDesc* dev_desc, cudaStream_t st);
+// Set the grouped kernel's shared-memory attribute (before any stream capture).
+dme_status ozaki_grouped_prepare();
+// With `arena` the descriptors are staged there instead of copied to dev_desc.
+dme_status launch_ozaki_grouped(std::vector<OzGroupDesc>& items, OzGroupDesc* dev_desc, cudaStream_t st,
+                                DescArena* arena = nullptr);
 
 }  // namespace dme

@@ -290,7 +290,7 @@ def test_fsal_matches_unmerged_oracle(prec, scheme, N):
     if N >= 2:
         plain = plan_for(pr, flows, "strang", pr.T / N, prec=prec)
         plain.step(dev(pr.P0), 1)
-        assert plan.kernels_per_step() < plain.kernels_per_step()
+        assert plan.kernels_per_step < plain.kernels_per_step
 
 
 def test_fsal_dle_and_rejections():

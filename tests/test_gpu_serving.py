@@ -69,6 +69,9 @@ def test_serving_results_match_oracle_and_single_plan(server):
     st = json.loads(dme.dme_server_stats(server))
     assert st["completed"] == len(reqs) and st["failed"] == 0
     assert st["p99_ms"] >= st["p50_ms"] > 0
+    # rounds ran from captured graphs, and the FP64 tile autotuner saw every group size class
+    assert 1 <= st["graph_builds"] <= st["rounds"]
+    assert st["tuned_groups"] >= 1
 
 
 def test_result_is_identical_alone_and_in_a_mix(server):
