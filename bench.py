@@ -340,6 +340,8 @@ def run_ours(args):
     line["peaks_source"] = peaks_src
     if err6 is not None:
         line["split_rel_err_vs_fp64_gpu_after_6_steps"] = err6
+    if args.extras and rank == 0:
+        line["extras"] = extras_run(args, dme, pr, h, to_dev, stream, dev)
     if args.serving_requests > 0:
         line["serving"] = {"requests": args.serving_requests, "scheme": "strang F12F3", "max_slots": 32,
                            "workload": "n log-uniform 32..1024 (Laplacian or stable random A), m,p ~ U{1..8}, "
@@ -364,6 +366,47 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def extras_run(args, dme, pr, h, to_dev, stream, dev):
+    """Separately reported variants of the same workload (never the headline):
+    FSAL-merged Strang steps on the split path (same scheme up to rounding), and
+    the low-rank factored path (F1F2F3 Strang, no quadrature) with its final rank."""
+    import torch
+    out = {}
+    n = pr.n
+    K = args.split_steps
+    with torch.cuda.stream(stream):
+        plan = dme.Plan(to_dev(pr.A), C=to_dev(pr.C), h=h, flows=["F12", "F3"], comp="strang", B=to_dev(pr.B),
+                        R=to_dev(pr.R), prec="split_bf16", stream=stream, fsal=True)
+    P = torch.zeros(n, n, dtype=torch.float64, device=dev)
+    plan.step(P, 4)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.step(P, K)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    out["fsal_split"] = {"steps_per_s": K / (e0.elapsed_time(e1) / 1e3), "steps": K,
+                         "what": "Strang F12F3 with T12(h/2) T12(h/2) of neighbouring steps merged into T12(h)"}
+    plan.close()
+    t0 = time.perf_counter()
+    lr = dme.LowRankPlan(to_dev(pr.A), to_dev(pr.C), h=h, flows=["F1", "F2", "F3"], comp="strang",
+                         B=to_dev(pr.B), R=to_dev(pr.R), stream=stream)
+    plan_s = time.perf_counter() - t0
+    N = args.lowrank_steps
+    lr.solve(N * h, 4)                    # warm-up (and the rank the state settles at)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    r = lr.solve(N * h, N)
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    out["lowrank_fp64"] = {"steps_per_s": N / dt, "steps": N, "final_rank": r, "plan_s": plan_s,
+                           "what": "factored P = L diag(d) L^T, Strang F1F2F3 from P0 = 0, tol 1e-13, "
+                                   "host-timed (a rank read-back per compression)"}
+    lr.close()
+    return out
 
 
 def run_gemm_only(args):
@@ -403,6 +446,8 @@ def main():
     ap.add_argument("--gemm-only", type=int, default=0, help="profile target: split GEMM of this size alone")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--serving-requests", type=int, default=32, help="serving sample size (0: skip)")
+    ap.add_argument("--no-extras", dest="extras", action="store_false", help="skip the FSAL and low-rank lines")
+    ap.add_argument("--lowrank-steps", type=int, default=32)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

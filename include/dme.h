@@ -168,6 +168,41 @@ dme_status dme_plan_timing(dme_plan_t plan, int kind, double* ms, int* launches)
 
 dme_status dme_plan_destroy(dme_plan_t plan);
 
+/* ---- low-rank factored path (§2.1-2.3 factor forms, Alg. 1-4) -----------
+ * The state is kept as P = L diag(d) L^T (L n x r, d > 0) and never formed
+ * during the steps: T1 maps L to E_t^T L, T2 appends C^T with weights t,
+ * T12 maps L and appends the compressed Gauss-Legendre factor of W_t (Alg. 2),
+ * T3 updates the factor through an m x m eigenproblem ((I + t D L^T B R^-1 B^T L)^-1 D
+ * of §2.2 in square-root form), T4 appends sqrt(t) S L and sqrt(t/2) S (sqrt(t) S L)
+ * (midpoint) or sqrt(t) S L (Euler).  After every flow that appends columns the
+ * factor is compressed: the eigen-decomposition of P on the span of L (a Gram
+ * matrix and a Jacobi eigensolver), keeping eigenvalues > tol * max.  FP64 only;
+ * E_t is the dense exponential of the plan (n <= 16384).  P0 must be PSD. */
+typedef struct dme_lr_s* dme_lr_t;
+typedef struct {
+    int quad_nodes;     /* Gauss-Legendre nodes for W_t in T12 (0: 7), <= 64       */
+    int rmax;           /* column capacity before a compression (0: 224), <= 224  */
+    double tol;         /* relative eigenvalue truncation (0: 1e-13)             */
+} dme_lr_opts;
+
+/* Plan: as dme_plan with q_is_factor = 1 (C is p x n, Q = C^T C), prec =
+ * DME_FP64, fsal = 0, extrap <= 1.  opts may be NULL.  Errors as dme_plan. */
+dme_status dme_lr_plan(const dme_plan_desc* desc, const double* A, const double* C, const double* B,
+                       const double* R, const double* S, const dme_lr_opts* opts, void* cuda_stream,
+                       dme_lr_t* out);
+
+/* N = nsteps composition steps from P0 = L0 D0 L0^T (L0 n x r0, D0 r0 x r0
+ * symmetric PSD, host or device, row-major; r0 = 0 for P0 = 0), h = T/N.
+ * P_out (n x n, host or device) receives L diag(d) L^T unless NULL; *r_out the
+ * final rank unless NULL.  DME_ENOMEM if a factor outgrows rmax. */
+dme_status dme_lr_solve(dme_lr_t plan, const double* L0, const double* D0, int r0, double T, int nsteps,
+                        double* P_out, int* r_out);
+
+/* The current factors: L_out (n x r, row-major) and d_out (r), either NULL to skip. */
+dme_status dme_lr_factors(dme_lr_t plan, double* L_out, double* d_out, int* r);
+
+dme_status dme_lr_destroy(dme_lr_t plan);
+
 /* ---- serving: continuous batching of independent DRE/DLE solves ----------
  * A server owns one stream and a worker thread.  Requests are admitted into
  * slots while their device footprint (P, E, W and work buffers) fits in

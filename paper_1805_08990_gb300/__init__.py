@@ -11,7 +11,7 @@ from .binding import (  # noqa: F401
     DME_KIND_SPLIT_GEMM, DME_KIND_SLICE, DME_KIND_FP64_GEMM, DME_KIND_RICCATI, dme_plan_profile, dme_plan_timing,
     DME_OK, DME_EINVAL, DME_ENOMEM, DME_ENOTSPD, DME_ECUDA, DME_ETIMEOUT, DME_EBUSY, DME_ENOTREADY,
     DmeError, LibraryNotBuilt, dme_plan_desc, make_desc, lib, header_functions,
-    dme_plan, dme_plan_mass, dme_expm, dme_apply, dme_apply_async, dme_sync, dme_plan_kernels_per_step, dme_step, dme_solve, dme_plan_bytes, dme_plan_destroy, dme_gain,
+    dme_plan, dme_plan_mass, dme_lr_plan, dme_lr_solve, dme_lr_factors, dme_lr_destroy, dme_expm, dme_apply, dme_apply_async, dme_sync, dme_plan_kernels_per_step, dme_step, dme_solve, dme_plan_bytes, dme_plan_destroy, dme_gain,
     dme_server_create, dme_submit, dme_poll, dme_server_stats, dme_server_destroy, dme_last_error,
     dme_gemm_split, dme_gemm_split_noalloc,
 )
@@ -92,3 +92,45 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class LowRankPlan:
+    """Owning wrapper of a dme_lr_t: the factored (LDL^T) schemes.
+
+    ``LowRankPlan(A, C, h, flows=["F12", "F3"], B=B, R=R)``; ``solve(T, N, P_out=P)``
+    runs N steps from P0 = L0 D0 L0^T (0 if L0 is None), writes L diag(d) L^T to P_out
+    when given, and returns the final rank; ``factors()`` returns (L, d)."""
+
+    def __init__(self, A, C, h=1e-3, flows=("F1", "F2"), comp="strang", B=None, R=None, S=None,
+                 t4_rule=DME_T4_AUTO, quad_nodes=0, rmax=0, tol=0.0, stream=None):
+        n = int(A.shape[0])
+        m = 0 if B is None else int(B.shape[1])
+        eq = ("g" if S is not None else "") + ("dre" if B is not None else "dle")
+        self.n, self.m = n, m
+        self.desc = make_desc(n, m=m, p=int(C.shape[0]), eq=EQ_IDS[eq], comp=comp, flows=flows, prec="fp64", h=h,
+                              q_is_factor=True, t4_rule=t4_rule)
+        self.handle = dme_lr_plan(self.desc, A, C, B, R, S, quad_nodes, rmax, tol, stream)
+
+    def solve(self, T, nsteps, L0=None, D0=None, P_out=None):
+        r0 = 0 if L0 is None else int(L0.shape[1])
+        return dme_lr_solve(self.handle, L0, D0, r0, T, nsteps, P_out)
+
+    def factors(self):
+        import numpy as np
+        r = dme_lr_factors(self.handle)
+        L = np.empty((self.n, r))
+        d = np.empty(r)
+        if r:
+            dme_lr_factors(self.handle, L, d)
+        return L, d
+
+    def close(self):
+        if getattr(self, "handle", None):
+            dme_lr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

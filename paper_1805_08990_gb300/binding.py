@@ -50,6 +50,10 @@ class dme_plan_desc(C.Structure):
                 ("extrap", C.c_int)]
 
 
+class dme_lr_opts(C.Structure):
+    _fields_ = [("quad_nodes", C.c_int), ("rmax", C.c_int), ("tol", C.c_double)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -59,6 +63,12 @@ _SIGS = {
     "dme_plan_mass": (C.c_int, [C.POINTER(dme_plan_desc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
     "dme_expm": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
+    "dme_lr_plan": (C.c_int, [C.POINTER(dme_plan_desc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                              C.c_void_p, C.POINTER(dme_lr_opts), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "dme_lr_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p,
+                               C.POINTER(C.c_int)]),
+    "dme_lr_factors": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
+    "dme_lr_destroy": (C.c_int, [C.c_void_p]),
     "dme_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p]),
     "dme_apply_async": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p]),
     "dme_sync": (C.c_int, [C.c_void_p]),
@@ -171,6 +181,35 @@ def dme_plan_mass(desc: dme_plan_desc, M, A, QorC, B=None, R=None, S=None, strea
     _check(lib().dme_plan_mass(C.byref(desc), _ptr(M, keep), _ptr(A, keep), _ptr(QorC, keep), _ptr(B, keep),
                                _ptr(R, keep), _ptr(S, keep), st, C.byref(out)), "dme_plan_mass")
     return out.value
+
+
+def dme_lr_plan(desc: dme_plan_desc, A, C_factor, B=None, R=None, S=None, quad_nodes=0, rmax=0, tol=0.0,
+                stream=None) -> int:
+    keep: list = []
+    out = C.c_void_p()
+    opts = dme_lr_opts(int(quad_nodes), int(rmax), float(tol))
+    st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib().dme_lr_plan(C.byref(desc), _ptr(A, keep), _ptr(C_factor, keep), _ptr(B, keep), _ptr(R, keep),
+                             _ptr(S, keep), C.byref(opts), st, C.byref(out)), "dme_lr_plan")
+    return out.value
+
+
+def dme_lr_solve(plan: int, L0, D0, r0: int, T: float, nsteps: int, P_out=None) -> int:
+    keep: list = []
+    r = C.c_int(0)
+    _check(lib().dme_lr_solve(plan, _ptr(L0, keep) if r0 else None, _ptr(D0, keep) if r0 else None, int(r0),
+                              float(T), int(nsteps), _out_ptr(P_out), C.byref(r)), "dme_lr_solve")
+    return r.value
+
+
+def dme_lr_factors(plan: int, L_out=None, d_out=None) -> int:
+    r = C.c_int(0)
+    _check(lib().dme_lr_factors(plan, _out_ptr(L_out), _out_ptr(d_out), C.byref(r)), "dme_lr_factors")
+    return r.value
+
+
+def dme_lr_destroy(plan: int):
+    lib().dme_lr_destroy(plan)
 
 
 def dme_expm(plan: int, t: float, E_out=None, W_out=None):

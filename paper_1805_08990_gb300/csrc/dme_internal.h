@@ -104,6 +104,24 @@ void launch_small_cholesky(double* R, int m, int* status, cudaStream_t st);
 // Bt = B L^{-T} (rows of B solved against lower L), n x m.
 void launch_apply_linv_rows(const double* B, const double* L, double* Bt, int n, int m, cudaStream_t st);
 
+// ---------------------------------------------------------------- low-rank path
+constexpr int LR_MAX_RANK = 224;   // columns of L before a compression (shared-memory Jacobi)
+size_t jacobi_smem_bytes(int r);
+// Eigen-decomposition of the symmetric r x r matrix G: lam (r), V^T (r x r, ldv).
+dme_status launch_jacobi_eig(const double* G, int ldg, int r, double* Vt, int ldv, double* lam, int* status,
+                             cudaStream_t st);
+// Keep eigenvalues > tol * max, ordered decreasingly: d_out, k_out, and the
+// r x k basis T (columns = eigenvectors, times lambda^{-1/2} if inv_sqrt).
+void launch_lr_select(const double* lam, const double* Vt, int ldv, int r, double tol, int inv_sqrt, double* T,
+                      int ldt, double* d_out, int* k_out, cudaStream_t st);
+// F = V diag(psi(lam)) V^T (m x m) for the factored Riccati flow over t.
+void launch_ric_weights(const double* lam, const double* Vt, int ldv, int m, double t, double* F, int ldf,
+                        cudaStream_t st);
+// Y = alpha X (n x k block), columns scaled by sqrt(d[j]) when d is given.
+void launch_copy_cols(double* Y, int ldy, const double* X, int ldx, int n, int k, double alpha, const double* d,
+                      cudaStream_t st);
+void launch_fill(double* x, int k, double v, cudaStream_t st);
+
 // ---------------------------------------------------------------- Riccati (T3)
 // P <- P - t Z (I + t Bt^T Z)^{-1} Z^T + q * Qadd, Z = P Bt  (Woodbury form
 // of (I + t P Bt Bt^T)^{-1} P).  Work buffers sized by riccati_work_doubles.

@@ -1,0 +1,270 @@
+// Kernels of the low-rank (LDL^T) path: a one-CTA parallel Jacobi
+// eigensolver for the small symmetric systems of the column compression and
+// of the factored Riccati flow, the eigenvalue selection that builds the
+// compressed basis, and column scaling / copying helpers.
+//
+// The compression only needs the eigen-decomposition of an r x r Gram matrix
+// (r <= 224), so one CTA holds its upper triangle packed in shared memory and
+// applies r/2 disjoint rotations per sub-sweep (round-robin pairing); the
+// eigenvector matrix is accumulated transposed in global memory (rows p, q of
+// V^T change per rotation, so the updates are contiguous).
+#include "dme_internal.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace dme {
+
+namespace {
+
+__device__ __forceinline__ int pk(int a, int b, int r) {   // packed upper triangle, a <= b
+    return a * r - (a * (a - 1)) / 2 + (b - a);
+}
+
+__device__ __forceinline__ double pget(const double* A, int x, int y, int r) {
+    return x <= y ? A[pk(x, y, r)] : A[pk(y, x, r)];
+}
+
+__device__ __forceinline__ void pset(double* A, int x, int y, int r, double v) {
+    if (x <= y) A[pk(x, y, r)] = v;
+    else A[pk(y, x, r)] = v;
+}
+
+// Round-robin pairing of R (even) indices in sub-sweep t: index 0 stays, the
+// others rotate on a circle of R - 1 positions.
+__device__ __forceinline__ void rr_pair(int i, int t, int R, int& p, int& q) {
+    int a, b;
+    if (i == 0) {
+        a = 0;
+        b = 1 + (t % (R - 1));
+    } else {
+        a = 1 + ((i + t) % (R - 1));
+        b = 1 + ((R - 1 - i + t) % (R - 1));
+    }
+    p = min(a, b);
+    q = max(a, b);
+}
+
+constexpr int kJacobiSweeps = 60;
+
+// Symmetric eigen-decomposition of the r x r matrix G (only (G + G^T)/2 is
+// used): lam[i] = eigenvalue i, row i of V^T (ldv) = its eigenvector.  A
+// rotation is skipped when |a_pq| <= 1e-16 sqrt(|a_pp a_qq|); the sweeps stop
+// after one with no rotation (DEV_NONFINITE in *status after 60 sweeps or on a
+// non-finite entry).
+__global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double* __restrict__ G, int ldg, int r,
+                                                          double* __restrict__ Vt, int ldv, double* __restrict__ lam,
+                                                          int* status) {
+    extern __shared__ double sm[];
+    const int R = r + (r & 1), P = R / 2;
+    double* A = sm;
+    double* cs = A + (size_t)r * (r + 1) / 2;
+    double* sn = cs + P;
+    double* tt = sn + P;
+    int* pp = reinterpret_cast<int*>(tt + P);
+    int* qq = pp + P;
+    __shared__ int rotated;
+    __shared__ int bad;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) bad = 0;
+    for (int e = tid; e < r * r; e += nt) {
+        const int i = e / r, j = e % r;
+        if (i <= j) {
+            const double v = 0.5 * (G[(size_t)i * ldg + j] + G[(size_t)j * ldg + i]);
+            A[pk(i, j, r)] = v;
+            if (!isfinite(v)) bad = 1;
+        }
+        Vt[(size_t)i * ldv + j] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    if (bad) {
+        if (tid == 0) atomicOr(status, DEV_NONFINITE);
+        return;
+    }
+    int sweep = 0;
+    for (; sweep < kJacobiSweeps; ++sweep) {
+        if (tid == 0) rotated = 0;
+        __syncthreads();
+        for (int t = 0; t < R - 1; ++t) {
+            for (int i = tid; i < P; i += nt) {
+                int p, q;
+                rr_pair(i, t, R, p, q);
+                double c = 1.0, s = 0.0, tv = 0.0;
+                if (q < r) {
+                    const double apq = A[pk(p, q, r)];
+                    const double app = A[pk(p, p, r)], aqq = A[pk(q, q, r)];
+                    if (apq != 0.0 && fabs(apq) > 1e-16 * sqrt(fabs(app * aqq))) {
+                        const double th = (aqq - app) / (2.0 * apq);
+                        tv = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
+                        c = 1.0 / sqrt(1.0 + tv * tv);
+                        s = tv * c;
+                        rotated = 1;
+                    }
+                }
+                pp[i] = p;
+                qq[i] = q;
+                cs[i] = c;
+                sn[i] = s;
+                tt[i] = tv;
+            }
+            __syncthreads();
+            // every 2 x 2 block between pairs i <= j: X <- J_i^T X J_j
+            for (int e = tid; e < P * P; e += nt) {
+                const int i = e / P, j = e % P;
+                if (i > j) continue;
+                const int pi = pp[i], qi = qq[i], pj = pp[j], qj = qq[j];
+                const double ci = cs[i], si = sn[i], cj = cs[j], sj = sn[j];
+                if (si == 0.0 && sj == 0.0) continue;
+                if (i == j) {
+                    if (qi >= r) continue;
+                    const double apq = A[pk(pi, qi, r)];
+                    A[pk(pi, pi, r)] -= tt[i] * apq;
+                    A[pk(qi, qi, r)] += tt[i] * apq;
+                    A[pk(pi, qi, r)] = 0.0;
+                    continue;
+                }
+                const bool qiok = qi < r, qjok = qj < r;
+                const double x00 = pget(A, pi, pj, r);
+                const double x01 = qjok ? pget(A, pi, qj, r) : 0.0;
+                const double x10 = qiok ? pget(A, qi, pj, r) : 0.0;
+                const double x11 = (qiok && qjok) ? pget(A, qi, qj, r) : 0.0;
+                const double y00 = ci * x00 - si * x10, y01 = ci * x01 - si * x11;
+                const double y10 = si * x00 + ci * x10, y11 = si * x01 + ci * x11;
+                pset(A, pi, pj, r, cj * y00 - sj * y01);
+                if (qjok) pset(A, pi, qj, r, sj * y00 + cj * y01);
+                if (qiok) pset(A, qi, pj, r, cj * y10 - sj * y11);
+                if (qiok && qjok) pset(A, qi, qj, r, sj * y10 + cj * y11);
+            }
+            // V <- V J: rows p, q of V^T
+            for (int e = tid; e < P * r; e += nt) {
+                const int i = e / r, k = e % r;
+                const double s = sn[i];
+                if (s == 0.0) continue;
+                const double c = cs[i];
+                const int p = pp[i], q = qq[i];
+                const double vp = Vt[(size_t)p * ldv + k], vq = Vt[(size_t)q * ldv + k];
+                Vt[(size_t)p * ldv + k] = c * vp - s * vq;
+                Vt[(size_t)q * ldv + k] = s * vp + c * vq;
+            }
+            __syncthreads();
+        }
+        const int any = rotated;
+        __syncthreads();
+        if (!any) break;
+    }
+    for (int i = tid; i < r; i += nt) lam[i] = A[pk(i, i, r)];
+    if (tid == 0 && sweep == kJacobiSweeps) atomicOr(status, DEV_NONFINITE);
+}
+
+// Order the eigenvalues decreasingly and keep those above tol * max (max > 0):
+// k_out = their count, d_out[rank] = lambda, T[a][rank] = V[a][i] * w with
+// w = lambda^{-1/2} (inv_sqrt) or 1.  T has r rows (ldt).
+__global__ void __launch_bounds__(256) select_kernel(const double* __restrict__ lam, const double* __restrict__ Vt,
+                                                     int ldv, int r, double tol, int inv_sqrt, double* __restrict__ T,
+                                                     int ldt, double* __restrict__ d_out, int* k_out) {
+    __shared__ double smax;
+    __shared__ int kcount;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) {
+        double m = 0.0;
+        for (int i = 0; i < r; ++i) m = fmax(m, lam[i]);
+        smax = m;
+        kcount = 0;
+    }
+    __syncthreads();
+    const double thr = tol * smax;
+    for (int i = tid; i < r; i += nt) {
+        const double li = lam[i];
+        if (!(smax > 0.0) || !(li > thr)) continue;
+        int rank = 0;
+        for (int j = 0; j < r; ++j) {
+            const double lj = lam[j];
+            rank += (lj > li) || (lj == li && j < i);
+        }
+        atomicAdd(&kcount, 1);
+        d_out[rank] = li;
+        const double w = inv_sqrt ? 1.0 / sqrt(li) : 1.0;
+        for (int a = 0; a < r; ++a) T[(size_t)a * ldt + rank] = Vt[(size_t)i * ldv + a] * w;
+    }
+    __syncthreads();
+    if (tid == 0) *k_out = kcount;
+}
+
+// F = V diag(psi) V^T, psi_i = -t / (sqrt(1 + t l_i) (1 + sqrt(1 + t l_i))), l_i >= 0:
+// the matrix function with G F G^T = (I + t G G^T)^{-1/2} - I.
+__global__ void ric_weights_kernel(const double* __restrict__ lam, const double* __restrict__ Vt, int ldv, int m,
+                                   double t, double* __restrict__ F, int ldf) {
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int a = e / m, b = e % m;
+        double acc = 0.0;
+        for (int i = 0; i < m; ++i) {
+            const double l = fmax(lam[i], 0.0);
+            const double sq = sqrt(1.0 + t * l);
+            const double psi = -t / (sq * (1.0 + sq));
+            acc += Vt[(size_t)i * ldv + a] * psi * Vt[(size_t)i * ldv + b];
+        }
+        F[(size_t)a * ldf + b] = acc;
+    }
+}
+
+// Y[i][j] = alpha * X[i][j] * (d ? sqrt(d[j]) : 1) for an n x k block.
+__global__ void copy_cols_kernel(double* __restrict__ Y, int ldy, const double* __restrict__ X, int ldx, int n, int k,
+                                 double alpha, const double* __restrict__ d) {
+    const size_t total = (size_t)n * k;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / k), j = (int)(e % k);
+        double v = alpha * X[(size_t)i * ldx + j];
+        if (d) v *= sqrt(d[j]);
+        Y[(size_t)i * ldy + j] = v;
+    }
+}
+
+__global__ void fill_kernel(double* __restrict__ x, int k, double v) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) x[i] = v;
+}
+
+int grid_of(size_t total) { return (int)std::min<size_t>((total + 255) / 256, 152 * 8); }
+
+}  // namespace
+
+size_t jacobi_smem_bytes(int r) {
+    const int P = (r + (r & 1)) / 2;
+    return sizeof(double) * ((size_t)r * (r + 1) / 2 + 3 * (size_t)P) + sizeof(int) * 2 * (size_t)P;
+}
+
+dme_status launch_jacobi_eig(const double* G, int ldg, int r, double* Vt, int ldv, double* lam, int* status,
+                             cudaStream_t st) {
+    if (r < 1 || r > LR_MAX_RANK) return set_error("jacobi: size must be in [1, 224]"), DME_EINVAL;
+    static bool attr = false;
+    if (!attr) {
+        DME_CUDA_TRY(cudaFuncSetAttribute(jacobi_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)jacobi_smem_bytes(LR_MAX_RANK)));
+        attr = true;
+    }
+    jacobi_eig_kernel<<<1, 1024, jacobi_smem_bytes(r), st>>>(G, ldg, r, Vt, ldv, lam, status);
+    DME_CUDA_TRY(cudaGetLastError());
+    return DME_OK;
+}
+
+void launch_lr_select(const double* lam, const double* Vt, int ldv, int r, double tol, int inv_sqrt, double* T,
+                      int ldt, double* d_out, int* k_out, cudaStream_t st) {
+    select_kernel<<<1, 256, 0, st>>>(lam, Vt, ldv, r, tol, inv_sqrt, T, ldt, d_out, k_out);
+}
+
+void launch_ric_weights(const double* lam, const double* Vt, int ldv, int m, double t, double* F, int ldf,
+                        cudaStream_t st) {
+    ric_weights_kernel<<<1, 256, 0, st>>>(lam, Vt, ldv, m, t, F, ldf);
+}
+
+void launch_copy_cols(double* Y, int ldy, const double* X, int ldx, int n, int k, double alpha, const double* d,
+                      cudaStream_t st) {
+    if (n <= 0 || k <= 0) return;
+    copy_cols_kernel<<<grid_of((size_t)n * k), 256, 0, st>>>(Y, ldy, X, ldx, n, k, alpha, d);
+}
+
+void launch_fill(double* x, int k, double v, cudaStream_t st) {
+    if (k <= 0) return;
+    fill_kernel<<<grid_of((size_t)k), 256, 0, st>>>(x, k, v);
+}
+
+}  // namespace dme

@@ -1,0 +1,452 @@
+// Low-rank (factored) splitting schemes: the state P = L diag(d) L^T stays in
+// factored form and every sub-flow acts on the factors (§2.1-2.3 factor forms;
+// Alg. 1-4).  The dense FP64 plan underneath supplies the data (A, Q = C^T C,
+// Bt = B L_R^{-T}, S) and the exponentials E_t = e^{tA} of its Pade path.
+//
+//   T_1(t):  L <- E_t^T L                         (Eq. F_sol_LDL with e^{tA^T} = E_t^T)
+//   T_2(t):  L <- [L, C^T], d <- [d, t 1_p]       then compression
+//   T_12(t): L <- [E_t^T L, L_I], d <- [d, d_I]   then compression; (L_I, d_I) is the
+//            compressed Gauss-Legendre factor of W_t (Alg. 2), built once per t
+//   T_3(t):  with Lt = L diag(d)^{1/2} and G = Lt^T Bt (r x m):
+//            L <- Lt (I + t G G^T)^{-1/2} = Lt + (Lt G) F(G^T G) G^T, d <- 1, where
+//            F(x) = -t / (sqrt(1 + t x)(1 + sqrt(1 + t x))); equal to the §2.2 form
+//            L (I + t D L^T B R^{-1} B^T L)^{-1} D L^T by the push-through identity
+//   T_4(t):  L <- [L, sqrt(t) S L, sqrt(t/2) S (sqrt(t) S L)], d <- [d, d, d] (midpoint)
+//            or [L, sqrt(t) S L], [d, d] (Euler), then compression
+//   compression: Lt = L diag(d)^{1/2}; Lt^T Lt = V Lambda V^T (Jacobi);
+//            L <- Lt V_k Lambda_k^{-1/2}, d <- lambda_k for lambda > tol * max lambda,
+//            i.e. the eigen-decomposition of P restricted to its numerical range
+//            (the paper's reduced SVD followed by the small diagonalisation).
+// d stays positive throughout (P is positive semidefinite).
+#include "plan_internal.h"
+
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <utility>
+#include <vector>
+
+using namespace dme;
+
+namespace {
+
+struct WFactor {
+    double tau;
+    double* L;   // n x k, leading dimension k
+    double* d;   // k
+    int k;
+};
+
+}  // namespace
+
+struct dme_lr_s {
+    dme_plan_t P = nullptr;   // dense FP64 plan (data, E_t, stream, status)
+    int n = 0, m = 0, p = 0, rcap = 0, q = 7;
+    double tol = 1e-13;
+    double *L = nullptr, *L2 = nullptr, *d = nullptr, *d2 = nullptr;   // n x rcap, rcap
+    double* LQ = nullptr;                                            // C^T, n x p
+    double *G = nullptr, *Vt = nullptr, *lam = nullptr, *T = nullptr;  // rcap x rcap work
+    double *Gm = nullptr, *H = nullptr, *VtH = nullptr, *lamH = nullptr, *F = nullptr, *Y = nullptr, *Z = nullptr;
+    double* Pout = nullptr;   // n x n, allocated on the first dense output
+    int* kdev = nullptr;
+    std::vector<WFactor> wf;
+    std::vector<void*> allocs;
+    int r = 0;
+};
+
+namespace {
+
+dme_status lr_alloc(dme_lr_t lr, double** out, size_t count) {
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(out), std::max<size_t>(count, 1) * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("low-rank plan: cudaMalloc: ") + cudaGetErrorString(e));
+        return DME_ENOMEM;
+    }
+    lr->allocs.push_back(*out);
+    return DME_OK;
+}
+
+GemmProb mk(int M, int N, int K, const double* A, int lda, int tA, const double* B, int ldb, int tB, double* C,
+            int ldc, double alpha, int tri = 0, const double* D1 = nullptr, double b1 = 0.0) {
+    GemmProb g;
+    std::memset(&g, 0, sizeof(g));
+    g.A = A;
+    g.B = B;
+    g.C = C;
+    g.D1 = D1;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.lda = lda;
+    g.ldb = ldb;
+    g.ldc = ldc;
+    g.ldd = ldc;
+    g.alpha = alpha;
+    g.b1 = b1;
+    g.transA = tA;
+    g.transB = tB;
+    g.tri = tri;
+    return g;
+}
+
+dme_status gemm(const GemmProb& g, cudaStream_t st) {
+    if (g.M <= 0 || g.N <= 0) return DME_OK;
+    std::vector<GemmProb> v{g};
+    return gemm64_grouped(v, nullptr, st);
+}
+
+// Compress the factor (L, d) with r columns (leading dimension ld) in place;
+// L2 is an n x ld work buffer.  Reads the new rank back to the host.
+dme_status compress(dme_lr_t lr, double* L, double* L2, double* d, int ld, int& r) {
+    if (r == 0) return DME_OK;
+    cudaStream_t st = lr->P->st;
+    const int n = lr->n;
+    launch_copy_cols(L2, ld, L, ld, n, r, 1.0, d, st);                                     // Lt = L d^{1/2}
+    DME_TRY(gemm(mk(r, r, n, L2, ld, 1, L2, ld, 0, lr->G, lr->rcap, 1.0, 1), st));          // Lt^T Lt
+    DME_TRY(launch_jacobi_eig(lr->G, lr->rcap, r, lr->Vt, lr->rcap, lr->lam, lr->P->status, st));
+    launch_lr_select(lr->lam, lr->Vt, lr->rcap, r, lr->tol, 1, lr->T, lr->rcap, d, lr->kdev, st);
+    int k = 0;
+    DME_CUDA_TRY(cudaMemcpyAsync(&k, lr->kdev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DME_CUDA_TRY(cudaStreamSynchronize(st));
+    DME_TRY(gemm(mk(n, k, r, L2, ld, 0, lr->T, lr->rcap, 0, L, ld, 1.0), st));              // L = Lt V_k Lambda^-1/2
+    r = k;
+    return DME_OK;
+}
+
+dme_status need_cols(dme_lr_t lr, int cols) {
+    if (cols > lr->rcap)
+        return set_error("low-rank path: " + std::to_string(cols) + " columns exceed the capacity " +
+                         std::to_string(lr->rcap) + " (raise rmax up to 224, or tol)"),
+               DME_ENOMEM;
+    return DME_OK;
+}
+
+// Gauss-Legendre nodes and weights on [0, t] (Newton on the Legendre recurrence).
+void gauss_legendre(int q, double t, std::vector<double>& s, std::vector<double>& w) {
+    s.assign(q, 0.0);
+    w.assign(q, 0.0);
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < (q + 1) / 2; ++i) {
+        double x = std::cos(pi * (i + 0.75) / (q + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= q; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (q == 1) {
+                p1 = x;
+                p0 = 1.0;
+            }
+            dp = q * (x * p1 - p0) / (x * x - 1.0);
+            const double dx = p1 / dp;
+            x -= dx;
+            if (std::fabs(dx) < 1e-16) break;
+        }
+        {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= q; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (q == 1) p0 = 1.0, p1 = x;
+            dp = q * (x * p1 - p0) / (x * x - 1.0);
+        }
+        const double wi = 2.0 / ((1.0 - x * x) * dp * dp);
+        // nodes x_i (descending) and -x_i, mapped to [0, t]
+        s[i] = 0.5 * t * (1.0 + x);
+        s[q - 1 - i] = 0.5 * t * (1.0 - x);
+        w[i] = w[q - 1 - i] = 0.5 * t * wi;
+    }
+}
+
+dme_status wfactor(dme_lr_t lr, double tau, const WFactor** out) {
+    for (auto& f : lr->wf)
+        if (f.tau == tau) {
+            *out = &f;
+            return DME_OK;
+        }
+    cudaStream_t st = lr->P->st;
+    const int n = lr->n, p = lr->p, q = lr->q, k0 = q * p;
+    DME_TRY(need_cols(lr, k0));
+    std::vector<double> s, w;
+    gauss_legendre(q, tau, s, w);
+    // temporaries, freed (after the stream drained) when this function returns
+    struct Tmp {
+        cudaStream_t st;
+        std::vector<void*> v;
+        ~Tmp() {
+            cudaStreamSynchronize(st);
+            for (void* x : v) cudaFree(x);
+        }
+        dme_status get(double** o, size_t count) {
+            if (cudaMalloc(reinterpret_cast<void**>(o), count * sizeof(double)) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("low-rank plan: cudaMalloc (quadrature factor) failed");
+                return DME_ENOMEM;
+            }
+            v.push_back(*o);
+            return DME_OK;
+        }
+    } tmp{st, {}};
+    double *WL = nullptr, *WL2 = nullptr, *wd = nullptr;
+    DME_TRY(tmp.get(&WL, (size_t)n * lr->rcap));
+    DME_TRY(tmp.get(&WL2, (size_t)n * lr->rcap));
+    DME_TRY(tmp.get(&wd, (size_t)lr->rcap));
+    for (int k = 0; k < q; ++k) {
+        int idx;
+        DME_TRY(plan_ew(lr->P, s[k], &idx));
+        const double* E = lr->P->ew[idx].E;
+        DME_TRY(gemm(mk(n, p, n, E, n, 1, lr->LQ, p, 0, WL + (size_t)k * p, lr->rcap, 1.0), st));   // E_s^T C^T
+        launch_fill(wd + (size_t)k * p, p, w[k], st);
+    }
+    int r = k0;
+    DME_TRY(compress(lr, WL, WL2, wd, lr->rcap, r));
+    WFactor f;
+    f.tau = tau;
+    f.k = r;
+    DME_TRY(lr_alloc(lr, &f.L, (size_t)n * std::max(r, 1)));
+    DME_TRY(lr_alloc(lr, &f.d, (size_t)std::max(r, 1)));
+    launch_copy_cols(f.L, std::max(r, 1), WL, lr->rcap, n, r, 1.0, nullptr, st);
+    if (r > 0) DME_CUDA_TRY(cudaMemcpyAsync(f.d, wd, sizeof(double) * r, cudaMemcpyDeviceToDevice, st));
+    DME_CUDA_TRY(cudaStreamSynchronize(st));
+    lr->wf.push_back(f);
+    *out = &lr->wf.back();
+    return DME_OK;
+}
+
+dme_status lr_T1(dme_lr_t lr, double tau) {
+    if (lr->r == 0) return DME_OK;
+    int idx;
+    DME_TRY(plan_ew(lr->P, tau, &idx));
+    const double* E = lr->P->ew[idx].E;
+    DME_TRY(gemm(mk(lr->n, lr->r, lr->n, E, lr->n, 1, lr->L, lr->rcap, 0, lr->L2, lr->rcap, 1.0), lr->P->st));
+    std::swap(lr->L, lr->L2);
+    return DME_OK;
+}
+
+dme_status lr_append(dme_lr_t lr, const double* X, int ldx, int k, const double* dsrc, double dval) {
+    DME_TRY(need_cols(lr, lr->r + k));
+    cudaStream_t st = lr->P->st;
+    launch_copy_cols(lr->L + lr->r, lr->rcap, X, ldx, lr->n, k, 1.0, nullptr, st);
+    if (dsrc) DME_CUDA_TRY(cudaMemcpyAsync(lr->d + lr->r, dsrc, sizeof(double) * k, cudaMemcpyDeviceToDevice, st));
+    else launch_fill(lr->d + lr->r, k, dval, st);
+    lr->r += k;
+    return DME_OK;
+}
+
+dme_status lr_T2(dme_lr_t lr, double tau) {
+    DME_TRY(lr_append(lr, lr->LQ, lr->p, lr->p, nullptr, tau));
+    return compress(lr, lr->L, lr->L2, lr->d, lr->rcap, lr->r);
+}
+
+dme_status lr_T12(dme_lr_t lr, double tau) {
+    const WFactor* f = nullptr;
+    DME_TRY(wfactor(lr, tau, &f));
+    DME_TRY(lr_T1(lr, tau));
+    if (f->k > 0) DME_TRY(lr_append(lr, f->L, f->k, f->k, f->d, 0.0));
+    return compress(lr, lr->L, lr->L2, lr->d, lr->rcap, lr->r);
+}
+
+dme_status lr_T3(dme_lr_t lr, double tau) {
+    if (lr->r == 0) return DME_OK;
+    cudaStream_t st = lr->P->st;
+    const int n = lr->n, m = lr->m, r = lr->r, rc = lr->rcap;
+    launch_copy_cols(lr->L2, rc, lr->L, rc, n, r, 1.0, lr->d, st);                              // Lt
+    DME_TRY(gemm(mk(r, m, n, lr->L2, rc, 1, lr->P->Bt, m, 0, lr->Gm, m, 1.0), st));              // G = Lt^T Bt
+    DME_TRY(gemm(mk(m, m, r, lr->Gm, m, 1, lr->Gm, m, 0, lr->H, m, 1.0, 1), st));                // G^T G
+    DME_TRY(launch_jacobi_eig(lr->H, m, m, lr->VtH, m, lr->lamH, lr->P->status, st));
+    launch_ric_weights(lr->lamH, lr->VtH, m, m, tau, lr->F, m, st);                               // F(G^T G)
+    DME_TRY(gemm(mk(r, m, m, lr->Gm, m, 0, lr->F, m, 0, lr->Y, m, 1.0), st));                    // Y = G F
+    DME_TRY(gemm(mk(n, m, r, lr->L2, rc, 0, lr->Gm, m, 0, lr->Z, m, 1.0), st));                  // Z = Lt G
+    DME_TRY(gemm(mk(n, r, m, lr->Z, m, 0, lr->Y, m, 1, lr->L, rc, 1.0, 0, lr->L2, 1.0), st));    // L = Lt + Z Y^T
+    launch_fill(lr->d, r, 1.0, st);
+    return DME_OK;
+}
+
+dme_status lr_T4(dme_lr_t lr, double tau, int rule) {
+    if (lr->r == 0) return DME_OK;
+    cudaStream_t st = lr->P->st;
+    const int n = lr->n, r = lr->r, rc = lr->rcap;
+    const int blocks = rule == DME_T4_EULER ? 2 : 3;
+    DME_TRY(need_cols(lr, blocks * r));
+    const double* S = lr->P->S;
+    DME_TRY(gemm(mk(n, r, n, S, n, 0, lr->L, rc, 0, lr->L + r, rc, std::sqrt(tau)), st));              // sqrt(t) S L
+    if (blocks == 3)
+        DME_TRY(gemm(mk(n, r, n, S, n, 0, lr->L + r, rc, 0, lr->L + 2 * r, rc, std::sqrt(0.5 * tau)), st));
+    for (int b = 1; b < blocks; ++b)
+        DME_CUDA_TRY(cudaMemcpyAsync(lr->d + b * r, lr->d, sizeof(double) * r, cudaMemcpyDeviceToDevice, st));
+    lr->r = blocks * r;
+    return compress(lr, lr->L, lr->L2, lr->d, rc, lr->r);
+}
+
+int t4_rule(const dme_plan_desc& d) {
+    if (d.t4_rule == DME_T4_MIDPOINT || d.t4_rule == DME_T4_EULER) return d.t4_rule;
+    return d.comp == DME_STRANG ? DME_T4_MIDPOINT : DME_T4_EULER;
+}
+
+dme_status lr_apply(dme_lr_t lr, int flow, double tau) {
+    switch (flow) {
+        case DME_F1: return lr_T1(lr, tau);
+        case DME_F2: return lr_T2(lr, tau);
+        case DME_F12: return lr_T12(lr, tau);
+        case DME_F3: return lr_T3(lr, tau);
+        case DME_F4: return lr_T4(lr, tau, t4_rule(lr->P->d));
+    }
+    set_error("low-rank path: unknown flow");
+    return DME_EINVAL;
+}
+
+void lr_free(dme_lr_t lr) {
+    if (!lr) return;
+    if (lr->P) cudaStreamSynchronize(lr->P->st);
+    for (void* q : lr->allocs) cudaFree(q);
+    if (lr->P) free_plan(lr->P);
+    delete lr;
+}
+
+template <typename F>
+dme_status guarded(F&& f) {
+    try {
+        return f();
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return DME_ENOMEM;
+    } catch (...) {
+        set_error("internal error");
+        return DME_EINVAL;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+dme_status dme_lr_plan(const dme_plan_desc* desc, const double* A, const double* C, const double* B, const double* R,
+                       const double* S, const dme_lr_opts* opts, void* cuda_stream, dme_lr_t* out) {
+    if (!out) return set_error("out is NULL"), DME_EINVAL;
+    *out = nullptr;
+    set_error("");
+    if (!desc || !A || !C) return set_error("desc, A and C are required"), DME_EINVAL;
+    if (!desc->q_is_factor) return set_error("low-rank path: give Q as its factor C (q_is_factor = 1)"), DME_EINVAL;
+    if (desc->prec != DME_FP64) return set_error("low-rank path: prec must be DME_FP64"), DME_EINVAL;
+    if (desc->fsal || desc->extrap > 1) return set_error("low-rank path: no fsal / extrapolation"), DME_EINVAL;
+    const int q = opts && opts->quad_nodes > 0 ? opts->quad_nodes : 7;
+    const int rmax = opts && opts->rmax > 0 ? opts->rmax : LR_MAX_RANK;
+    const double tol = opts && opts->tol > 0.0 ? opts->tol : 1e-13;
+    if (q > 64 || rmax > LR_MAX_RANK || !(tol < 1.0))
+        return set_error("low-rank path: need quad_nodes <= 64, rmax <= 224, tol < 1"), DME_EINVAL;
+    if (desc->p > rmax) return set_error("low-rank path: p exceeds rmax"), DME_EINVAL;
+    DME_TRY(plan_validate(desc, A, C, B, R, S));
+    return guarded([&]() -> dme_status {
+        std::unique_ptr<dme_lr_s, void (*)(dme_lr_t)> lr(new dme_lr_s(), lr_free);
+        DME_TRY(plan_create(desc, A, C, B, R, S, cuda_stream, &lr->P));
+        lr->n = desc->n;
+        lr->m = desc->m;
+        lr->p = desc->p;
+        lr->q = q;
+        lr->rcap = rmax;
+        lr->tol = tol;
+        const size_t n = desc->n, rc = rmax, m = std::max(desc->m, 1);
+        cudaStream_t st = lr->P->st;
+        DME_TRY(lr_alloc(lr.get(), &lr->L, n * rc));
+        DME_TRY(lr_alloc(lr.get(), &lr->L2, n * rc));
+        DME_TRY(lr_alloc(lr.get(), &lr->d, rc));
+        DME_TRY(lr_alloc(lr.get(), &lr->d2, rc));
+        DME_TRY(lr_alloc(lr.get(), &lr->LQ, n * desc->p));
+        DME_TRY(lr_alloc(lr.get(), &lr->G, rc * rc));
+        DME_TRY(lr_alloc(lr.get(), &lr->Vt, rc * rc));
+        DME_TRY(lr_alloc(lr.get(), &lr->lam, rc));
+        DME_TRY(lr_alloc(lr.get(), &lr->T, rc * rc));
+        DME_TRY(lr_alloc(lr.get(), &lr->Gm, rc * m));
+        DME_TRY(lr_alloc(lr.get(), &lr->H, m * m));
+        DME_TRY(lr_alloc(lr.get(), &lr->VtH, m * m));
+        DME_TRY(lr_alloc(lr.get(), &lr->lamH, m));
+        DME_TRY(lr_alloc(lr.get(), &lr->F, m * m));
+        DME_TRY(lr_alloc(lr.get(), &lr->Y, rc * m));
+        DME_TRY(lr_alloc(lr.get(), &lr->Z, n * m));
+        double* kd = nullptr;
+        DME_TRY(lr_alloc(lr.get(), &kd, 1));
+        lr->kdev = reinterpret_cast<int*>(kd);
+        // L_Q = C^T (C is p x n)
+        double* Cd = nullptr;
+        DME_TRY(lr_alloc(lr.get(), &Cd, (size_t)desc->p * n));
+        DME_CUDA_TRY(cudaMemcpyAsync(Cd, C, sizeof(double) * desc->p * n, cudaMemcpyDefault, st));
+        launch_transpose(Cd, lr->LQ, desc->p, (int)n, (int)n, desc->p, st);
+        DME_CUDA_TRY(cudaStreamSynchronize(st));
+        DME_TRY(plan_check(lr->P, "dme_lr_plan"));
+        *out = lr.release();
+        return DME_OK;
+    });
+}
+
+dme_status dme_lr_solve(dme_lr_t lr, const double* L0, const double* D0, int r0, double T, int nsteps, double* P_out,
+                        int* r_out) {
+    if (!lr) return set_error("plan is NULL"), DME_EINVAL;
+    if (nsteps < 1 || !(T > 0.0) || !std::isfinite(T)) return set_error("need nsteps >= 1 and T > 0"), DME_EINVAL;
+    if (r0 < 0 || r0 > lr->rcap || (r0 > 0 && (!L0 || !D0)))
+        return set_error("need 0 <= r0 <= rmax and L0, D0 when r0 > 0"), DME_EINVAL;
+    return guarded([&]() -> dme_status {
+        cudaStream_t st = lr->P->st;
+        const int n = lr->n, rc = lr->rcap;
+        lr->r = 0;
+        if (r0 > 0) {
+            // P0 = L0 D0 L0^T with D0 symmetric: L0 V, d = eigenvalues (> 0), then compress
+            DME_CUDA_TRY(cudaMemcpy2DAsync(lr->L2, sizeof(double) * rc, L0, sizeof(double) * r0, sizeof(double) * r0, n,
+                                           cudaMemcpyDefault, st));
+            DME_CUDA_TRY(cudaMemcpy2DAsync(lr->G, sizeof(double) * rc, D0, sizeof(double) * r0, sizeof(double) * r0, r0,
+                                           cudaMemcpyDefault, st));
+            DME_TRY(launch_jacobi_eig(lr->G, rc, r0, lr->Vt, rc, lr->lam, lr->P->status, st));
+            launch_lr_select(lr->lam, lr->Vt, rc, r0, 0.0, 0, lr->T, rc, lr->d, lr->kdev, st);
+            int k = 0;
+            DME_CUDA_TRY(cudaMemcpyAsync(&k, lr->kdev, sizeof(int), cudaMemcpyDeviceToHost, st));
+            DME_CUDA_TRY(cudaStreamSynchronize(st));
+            DME_TRY(gemm(mk(n, k, r0, lr->L2, rc, 0, lr->T, rc, 0, lr->L, rc, 1.0), st));
+            lr->r = k;
+            DME_TRY(compress(lr, lr->L, lr->L2, lr->d, rc, lr->r));
+        }
+        const double h = T / nsteps;
+        const auto seq = plan_step_sequence(lr->P->d, h);
+        for (int s = 0; s < nsteps; ++s)
+            for (auto& ft : seq) DME_TRY(lr_apply(lr, ft.first, ft.second));
+        if (P_out) {
+            const size_t nn = (size_t)n * n;
+            if (!lr->Pout) DME_TRY(lr_alloc(lr, &lr->Pout, nn));
+            if (lr->r > 0) {
+                launch_copy_cols(lr->L2, rc, lr->L, rc, n, lr->r, 1.0, lr->d, st);
+                DME_TRY(gemm(mk(n, n, lr->r, lr->L2, rc, 0, lr->L2, rc, 1, lr->Pout, n, 1.0, 1), st));
+            } else {
+                DME_CUDA_TRY(cudaMemsetAsync(lr->Pout, 0, nn * sizeof(double), st));
+            }
+            DME_CUDA_TRY(cudaMemcpyAsync(P_out, lr->Pout, nn * sizeof(double), cudaMemcpyDefault, st));
+        }
+        if (r_out) *r_out = lr->r;
+        return plan_check(lr->P, "dme_lr_solve");
+    });
+}
+
+dme_status dme_lr_factors(dme_lr_t lr, double* L_out, double* d_out, int* r) {
+    if (!lr || !r) return set_error("plan and r are required"), DME_EINVAL;
+    return guarded([&]() -> dme_status {
+        cudaStream_t st = lr->P->st;
+        *r = lr->r;
+        if (lr->r > 0 && L_out)
+            DME_CUDA_TRY(cudaMemcpy2DAsync(L_out, sizeof(double) * lr->r, lr->L, sizeof(double) * lr->rcap,
+                                           sizeof(double) * lr->r, lr->n, cudaMemcpyDefault, st));
+        if (lr->r > 0 && d_out)
+            DME_CUDA_TRY(cudaMemcpyAsync(d_out, lr->d, sizeof(double) * lr->r, cudaMemcpyDefault, st));
+        DME_CUDA_TRY(cudaStreamSynchronize(st));
+        return DME_OK;
+    });
+}
+
+dme_status dme_lr_destroy(dme_lr_t lr) {
+    lr_free(lr);
+    return DME_OK;
+}
+
+}  // extern "C"

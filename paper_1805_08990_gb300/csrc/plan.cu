@@ -1125,3 +1125,13 @@ dme_status dme_gemm_split(int M, int N, int K, const double* A, const double* B,
 }
 
 }  // extern "C"
+
+dme_status dme::plan_ew(dme_plan_t p, double t, int* idx) { return compute_ew(p, t, idx); }
+dme_status dme::plan_check(dme_plan_t p, const char* where) { return check_status(p, where); }
+std::vector<std::pair<int, double>> dme::plan_step_sequence(const dme_plan_desc& d, double h) {
+    return step_sequence(d, h);
+}
+dme_status dme::plan_validate(const dme_plan_desc* d, const double* A, const double* QorC, const double* B,
+                              const double* R, const double* S) {
+    return validate(d, A, QorC, B, R, S);
+}

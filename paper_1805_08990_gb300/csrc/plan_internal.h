@@ -99,5 +99,14 @@ dme_status build_ops(dme_plan_t p, double h);
 dme_status run_op(dme_plan_t p, const Op& o, double* P);
 // Bytes reserved while a plan of this descriptor is built (persistent + transient).
 size_t plan_estimate_bytes(const dme_plan_desc& d);
+// E_t, W_t of the plan for step t (computed and cached on first use): index into p->ew.
+dme_status plan_ew(dme_plan_t p, double t, int* idx);
+// Report (and clear) the plan's device status word after synchronising its stream.
+dme_status plan_check(dme_plan_t p, const char* where);
+// The descriptor and pointer checks of dme_plan.
+dme_status plan_validate(const dme_plan_desc* d, const double* A, const double* QorC, const double* B,
+                         const double* R, const double* S);
+// One composition step of size h as (flow, t) pairs in application order.
+std::vector<std::pair<int, double>> plan_step_sequence(const dme_plan_desc& d, double h);
 
 }  // namespace dme

@@ -1,0 +1,111 @@
+"""Low-rank (LDL^T) CUDA path against the low-rank CPU oracle through the C ABI:
+P = L D L^T compared element by element (bar 1e-11, the FP64 path's), the rank
+and the kept eigenvalues, a general P0 = L0 D0 L0^T, and the error paths."""
+import numpy as np
+import pytest
+
+import dme_workloads as W
+import oracle as O
+import paper_1805_08990_gb300 as dme
+from gpu_util import FP64_TOL, dev, rel, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _gpu():
+    require_gpu()
+
+
+def _run(pr, flows, comp, N, q=7, tol=1e-13, L0=None, D0=None, T=None):
+    T = pr.T if T is None else T
+    uses_B = "F3" in flows
+    uses_S = "F4" in flows
+    B = pr.B if uses_B else None
+    R = pr.R if uses_B else None
+    S = pr.S if uses_S else None
+    plan = dme.LowRankPlan(dev(pr.A), dev(pr.C), h=T / N, flows=flows, comp=comp,
+                           B=None if B is None else dev(B), R=None if R is None else dev(R),
+                           S=None if S is None else dev(S), quad_nodes=q, tol=tol)
+    P = np.empty((pr.n, pr.n))
+    r = plan.solve(T, N, L0=L0, D0=D0, P_out=P)
+    L, d = plan.factors()
+    n = pr.n
+    Lo, Do = O.solve_lowrank(pr.A, pr.C, np.zeros((n, 0)) if L0 is None else L0,
+                             np.zeros((0, 0)) if D0 is None else D0, T, N, comp, flows, B=B, R=R, S=S,
+                             q=q, tol=tol)
+    return P, r, L, d, Lo, Do
+
+
+CASES = [
+    ("dle", ["F1", "F2"], "strang", 10),
+    ("dle", ["F1", "F2"], "lie", 6),
+    ("dre", ["F1", "F2", "F3"], "strang", 6),
+    ("dre", ["F12", "F3"], "strang", 5),
+    ("dre", ["F1", "F3", "F2"], "lie", 4),
+    ("dre", ["F12", "F3"], "lie", 3),
+    ("gdre", ["F12", "F3", "F4"], "strang", 3),
+    ("gdle", ["F1", "F2", "F4"], "lie", 3),
+]
+
+
+def _problem(kind):
+    if kind == "dle":
+        return W.dle_heat(nx=9)
+    if kind == "dre":
+        return W.dre_convdiff(nx=8, m=2, p=3)
+    return W.gdre_convdiff_padded(nx=6, n_pad=40, m=2, p=2)
+
+
+@pytest.mark.parametrize("kind,flows,comp,N", CASES)
+def test_lowrank_matches_oracle(kind, flows, comp, N):
+    pr = _problem(kind)
+    P, r, L, d, Lo, Do = _run(pr, flows, comp, N)
+    ref = O.ldl_product(Lo, Do)
+    assert rel(P, ref) < FP64_TOL
+    assert abs(r - Lo.shape[1]) <= 1
+    assert rel(L @ np.diag(d) @ L.T, P) < 1e-13
+    assert np.all(d > 0)
+
+
+def test_lowrank_kept_eigenvalues_match_oracle():
+    pr = W.dre_convdiff(nx=8, m=2, p=3)
+    P, r, L, d, Lo, Do = _run(pr, ["F1", "F3", "F2"], "lie", 4)    # each Lie step ends with T2 (compressed)
+    assert r == Lo.shape[1]
+    assert np.allclose(d, np.diag(Do), rtol=1e-10, atol=1e-13 * d.max())
+    assert np.allclose(L.T @ L, np.eye(r), atol=1e-10)
+
+
+def test_lowrank_general_initial_state():
+    pr = W.dre_convdiff(nx=7, m=2, p=2)
+    rng = np.random.default_rng(11)
+    L0 = rng.standard_normal((pr.n, 5))
+    G = rng.standard_normal((5, 5))
+    D0 = G @ G.T / 5 + 0.1 * np.eye(5)
+    P, r, L, d, Lo, Do = _run(pr, ["F12", "F3"], "strang", 4, L0=L0, D0=D0)
+    assert rel(P, O.ldl_product(Lo, Do)) < FP64_TOL
+
+
+def test_lowrank_equals_dense_gpu_path():
+    """With exact sub-flows (no quadrature) the factored scheme is the dense scheme."""
+    pr = W.dre_convdiff(nx=8, m=2, p=3)
+    flows, N = ["F1", "F2", "F3"], 8
+    P, *_ = _run(pr, flows, "strang", N, tol=1e-15)
+    dense = dme.Plan(dev(pr.A), C=dev(pr.C), h=pr.T / N, flows=flows, B=dev(pr.B), R=dev(pr.R))
+    Pd = np.empty((pr.n, pr.n))
+    dense.solve(pr.P0, pr.T, N, Pd)
+    assert rel(P, Pd) < 1e-11
+
+
+def test_lowrank_errors():
+    pr = W.dre_convdiff(nx=6, m=2, p=3)
+    with pytest.raises(dme.DmeError) as ei:
+        plan = dme.LowRankPlan(dev(pr.A), dev(pr.C), h=0.1, flows=["F12", "F3"], B=dev(pr.B), R=dev(pr.R), rmax=8)
+        plan.solve(1.0, 10, P_out=np.empty((pr.n, pr.n)))
+    assert ei.value.status in (dme.DME_ENOMEM,)
+    d = dme.make_desc(pr.n, m=2, p=3, eq=dme.DME_DRE, flows=["F12", "F3"], prec="split_bf16", h=0.1, q_is_factor=True)
+    with pytest.raises(dme.DmeError):
+        dme.dme_lr_plan(d, pr.A, pr.C, pr.B, pr.R)
+    d = dme.make_desc(pr.n, m=2, p=3, eq=dme.DME_DRE, flows=["F12", "F3"], h=0.1, q_is_factor=False)
+    with pytest.raises(dme.DmeError):
+        dme.dme_lr_plan(d, pr.A, pr.Q, pr.B, pr.R)
