@@ -159,6 +159,79 @@ def serving_run(count: int, seed: int, rate: float | None, prec: str = "fp64"):
         dme.dme_server_destroy(srv)
 
 
+def serving_stream(count: int, seed: int, rate: float, prec: str):
+    """Poisson stream of `count` serving requests at `rate` req/s, each built
+    from its spec only when it is submitted; a second thread collects the
+    results as they finish.  Returns the server's statistics."""
+    import threading
+    import paper_1805_08990_gb300 as dme
+    specs = W.serving_requests(count, seed=seed, rate=rate)
+    srv = dme.dme_server_create(64 << 30, 32)
+    tickets: list = []
+    cv = threading.Condition()
+    failures = []
+
+    def reap():
+        i = 0
+        while i < count:
+            with cv:
+                while len(tickets) <= i:
+                    cv.wait()
+                tk, n = tickets[i]
+            out = np.empty((n, n))
+            if dme.dme_poll(srv, tk, out, -1) != dme.DME_OK:
+                failures.append(tk)
+            i += 1
+
+    th = threading.Thread(target=reap)
+    th.start()
+    try:
+        t0 = time.perf_counter()
+        for sp in specs:
+            pr = W.materialize(sp)
+            delay = sp["arrival"] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            d = dme.make_desc(pr.n, m=pr.B.shape[1], p=pr.C.shape[0], eq=dme.DME_DRE, comp="strang",
+                              flows=("F12", "F3"), h=pr.T / sp["steps"], q_is_factor=True, prec=prec)
+            tk = dme.dme_submit(srv, d, pr.A, pr.C, pr.B, pr.R, None, pr.P0, pr.T, sp["steps"])
+            with cv:
+                tickets.append((tk, pr.n))
+                cv.notify()
+        th.join()
+        st = json.loads(dme.dme_server_stats(srv))
+        st["wall_s"] = time.perf_counter() - t0
+        st["client_failures"] = len(failures)
+        return st
+    finally:
+        dme.dme_server_destroy(srv)
+
+
+def run_serving_suite(args):
+    """The serving configuration at several loads: saturation from a burst, then
+    Poisson streams at 0.5, 0.9 and 1.2 times it (split precision and FP64)."""
+    import torch
+    from paper_1805_08990_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    out = {}
+    for prec, count, burst_n in (("split_bf16", args.serving_suite, 256),
+                                 ("fp64", max(args.serving_suite // 8, 64), 64)):
+        burst = serving_run(burst_n, seed=1, rate=None, prec=prec)
+        sat = burst["completed"] / burst["wall_s"]
+        rows = []
+        for load in (0.5, 0.9, 1.2):
+            st = serving_stream(count, seed=3, rate=load * sat, prec=prec)
+            rows.append({"load": load, "offered_per_s": load * sat, "solves_per_s": st["completed"] / st["wall_s"],
+                         "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "completed": st["completed"],
+                         "failed": st["failed"] + st["client_failures"], "wall_s": st["wall_s"],
+                         "graph_builds": st.get("graph_builds"), "rounds": st.get("rounds")})
+        out[prec] = {"requests_per_load": count, "saturation_solves_per_s": sat, "loads": rows}
+    print(json.dumps({"serving_suite": out, "workload": "n log-uniform 32..1024 (Laplacian or stable random A), "
+                      "m, p ~ U{1..8}, R = I_m, T ~ U[0.1, 10], 50-500 Strang F12F3 steps, P0 = 0, Poisson arrivals",
+                      "max_slots": 32}))
+
+
 # ------------------------------------------------------------------ oracle (CPU)
 def oracle_steps(pr, nsteps, E=None, Wm=None):
     """Time nsteps oracle Strang F12F3 steps of the workload; returns (seconds, E, W)."""
@@ -447,6 +520,8 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--serving-requests", type=int, default=32, help="serving sample size (0: skip)")
     ap.add_argument("--no-extras", dest="extras", action="store_false", help="skip the FSAL and low-rank lines")
+    ap.add_argument("--serving-suite", type=int, default=0,
+                    help="run only the serving loads 0.5/0.9/1.2 x saturation with this many split requests")
     ap.add_argument("--lowrank-steps", type=int, default=32)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -455,6 +530,8 @@ def main():
         return run_reference(args)
     if args.gemm_only:
         return run_gemm_only(args)
+    if args.serving_suite:
+        return run_serving_suite(args)
     return run_ours(args)
 
 

@@ -176,8 +176,10 @@ dme_status dme_plan_destroy(dme_plan_t plan);
  * of §2.2 in square-root form), T4 appends sqrt(t) S L and sqrt(t/2) S (sqrt(t) S L)
  * (midpoint) or sqrt(t) S L (Euler).  After every flow that appends columns the
  * factor is compressed: the eigen-decomposition of P on the span of L (a Gram
- * matrix and a Jacobi eigensolver), keeping eigenvalues > tol * max.  FP64 only;
- * E_t is the dense exponential of the plan (n <= 16384).  P0 must be PSD. */
+ * matrix and a Jacobi eigensolver), keeping eigenvalues > tol * max.  E_t is
+ * the dense exponential of the plan (n <= 16384; n <= 4096 with DME_SPLIT_BF16,
+ * which runs the products with E_t and S on the tensor cores and the rest in
+ * FP64).  P0 must be PSD. */
 typedef struct dme_lr_s* dme_lr_t;
 typedef struct {
     int quad_nodes;     /* Gauss-Legendre nodes for W_t in T12 (0: 7), <= 64       */
@@ -186,7 +188,8 @@ typedef struct {
 } dme_lr_opts;
 
 /* Plan: as dme_plan with q_is_factor = 1 (C is p x n, Q = C^T C), prec =
- * DME_FP64, fsal = 0, extrap <= 1.  opts may be NULL.  Errors as dme_plan. */
+ * DME_FP64 or DME_SPLIT_BF16, fsal = 0, extrap <= 1.  opts may be NULL.
+ * Errors as dme_plan. */
 dme_status dme_lr_plan(const dme_plan_desc* desc, const double* A, const double* C, const double* B,
                        const double* R, const double* S, const dme_lr_opts* opts, void* cuda_stream,
                        dme_lr_t* out);

@@ -102,12 +102,12 @@ class LowRankPlan:
     when given, and returns the final rank; ``factors()`` returns (L, d)."""
 
     def __init__(self, A, C, h=1e-3, flows=("F1", "F2"), comp="strang", B=None, R=None, S=None,
-                 t4_rule=DME_T4_AUTO, quad_nodes=0, rmax=0, tol=0.0, stream=None):
+                 t4_rule=DME_T4_AUTO, quad_nodes=0, rmax=0, tol=0.0, stream=None, prec="fp64"):
         n = int(A.shape[0])
         m = 0 if B is None else int(B.shape[1])
         eq = ("g" if S is not None else "") + ("dre" if B is not None else "dle")
         self.n, self.m = n, m
-        self.desc = make_desc(n, m=m, p=int(C.shape[0]), eq=EQ_IDS[eq], comp=comp, flows=flows, prec="fp64", h=h,
+        self.desc = make_desc(n, m=m, p=int(C.shape[0]), eq=EQ_IDS[eq], comp=comp, flows=flows, prec=prec, h=h,
                               q_is_factor=True, t4_rule=t4_rule)
         self.handle = dme_lr_plan(self.desc, A, C, B, R, S, quad_nodes, rmax, tol, stream)
 

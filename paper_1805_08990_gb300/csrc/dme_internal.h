@@ -121,6 +121,9 @@ void launch_ric_weights(const double* lam, const double* Vt, int ldv, int m, dou
 void launch_copy_cols(double* Y, int ldy, const double* X, int ldx, int n, int k, double alpha, const double* d,
                       cudaStream_t st);
 void launch_fill(double* x, int k, double v, cudaStream_t st);
+// C (M x N) = alpha * sum_{s < S} W[s] (+ b1 D1) with W[s] M x N contiguous; tri mirrors the upper part.
+void launch_splitk_reduce(const double* W, int S, int M, int N, double* C, int ldc, double alpha, const double* D1,
+                          double b1, int tri, cudaStream_t st);
 
 // ---------------------------------------------------------------- Riccati (T3)
 // P <- P - t Z (I + t Bt^T Z)^{-1} Z^T + q * Qadd, Z = P Bt  (Woodbury form
@@ -145,6 +148,11 @@ RicItem make_ric_item(double* P, const double* Bt, int n, int m, double t, const
 dme_status launch_riccati_grouped(const std::vector<RicItem>& items, void* dev_desc, cudaStream_t st,
                                   DescArena* arena = nullptr);
 size_t riccati_desc_bytes();
+// Kernels (2)-(3) of the Riccati flow for one problem whose Z = P Bt (n x m) is
+// already in work (its first n m doubles): Gram partials, M = I + t Bt^T Z, its
+// Cholesky, Y = Z L^{-T} (Y = 0 if M is not SPD, with DEV_NOTSPD set).
+dme_status launch_riccati_from_z(const double* Bt, int n, int m, double t, double* work, int* status,
+                                 cudaStream_t st);
 // K (m x n) = R^{-1} B^T P from Bt = B L^{-T} and L (R = L L^T); work as for launch_riccati.
 dme_status launch_lqr_gain(const double* P, const double* Bt, const double* LR, int n, int m, double* work,
                            double* K, cudaStream_t st);

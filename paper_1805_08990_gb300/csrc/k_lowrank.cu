@@ -6,8 +6,9 @@
 // The compression only needs the eigen-decomposition of an r x r Gram matrix
 // (r <= 224), so one CTA holds its upper triangle packed in shared memory and
 // applies r/2 disjoint rotations per sub-sweep (round-robin pairing); the
-// eigenvector matrix is accumulated transposed in global memory (rows p, q of
-// V^T change per rotation, so the updates are contiguous).
+// eigenvector matrix is accumulated transposed (rows p, q of V^T change per
+// rotation, so the updates are contiguous), in shared memory up to r = 112 and
+// in global memory beyond.
 #include "dme_internal.h"
 
 #include <algorithm>
@@ -49,24 +50,38 @@ constexpr int kJacobiSweeps = 60;
 
 // Symmetric eigen-decomposition of the r x r matrix G (only (G + G^T)/2 is
 // used): lam[i] = eigenvalue i, row i of V^T (ldv) = its eigenvector.  A
-// rotation is skipped when |a_pq| <= 1e-16 sqrt(|a_pp a_qq|); the sweeps stop
-// after one with no rotation (DEV_NONFINITE in *status after 60 sweeps or on a
+// rotation is skipped when |a_pq| <= max(1e-16 sqrt(|a_pp a_qq|), 1e-17 max_i
+// |a_ii|): relative accuracy for the eigenvalues that matter, and no chase of
+// rounding noise among those below the floor (a Gram matrix formed in floating
+// point carries absolute errors of that size anyway).  The sweeps stop after
+// one with no rotation (DEV_NONFINITE in *status after 60 sweeps or on a
 // non-finite entry).
+// VS: V^T is accumulated in shared memory too (r <= 112) and copied out at the end.
+template <bool VS>
 __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double* __restrict__ G, int ldg, int r,
-                                                          double* __restrict__ Vt, int ldv, double* __restrict__ lam,
-                                                          int* status) {
+                                                          double* __restrict__ Vt_out, int ldv_out,
+                                                          double* __restrict__ lam, int* status) {
     extern __shared__ double sm[];
     const int R = r + (r & 1), P = R / 2;
     double* A = sm;
     double* cs = A + (size_t)r * (r + 1) / 2;
     double* sn = cs + P;
     double* tt = sn + P;
-    int* pp = reinterpret_cast<int*>(tt + P);
+    double* Vt = VS ? tt + P : Vt_out;
+    const int ldv = VS ? r : ldv_out;
+    int* pp = reinterpret_cast<int*>(VS ? tt + P + (size_t)r * r : tt + P);
     int* qq = pp + P;
+    // (i, j), i <= j, of every rotation block, packed as i << 8 | j (P <= 112)
+    unsigned short* blk = reinterpret_cast<unsigned short*>(qq + P);
+    const int nblk = P * (P + 1) / 2;
     __shared__ int rotated;
     __shared__ int bad;
     const int tid = threadIdx.x, nt = blockDim.x;
     if (tid == 0) bad = 0;
+    for (int i = tid; i < P; i += nt) {
+        const int base = i * P - i * (i - 1) / 2;      // blocks (i, i..P-1) start here
+        for (int j = i; j < P; ++j) blk[base + j - i] = (unsigned short)((i << 8) | j);
+    }
     for (int e = tid; e < r * r; e += nt) {
         const int i = e / r, j = e % r;
         if (i <= j) {
@@ -81,9 +96,15 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double* __restri
         if (tid == 0) atomicOr(status, DEV_NONFINITE);
         return;
     }
+    __shared__ double floor_abs;
     int sweep = 0;
     for (; sweep < kJacobiSweeps; ++sweep) {
-        if (tid == 0) rotated = 0;
+        if (tid == 0) {
+            rotated = 0;
+            double dm = 0.0;
+            for (int i = 0; i < r; ++i) dm = fmax(dm, fabs(A[pk(i, i, r)]));
+            floor_abs = 1e-17 * dm;
+        }
         __syncthreads();
         for (int t = 0; t < R - 1; ++t) {
             for (int i = tid; i < P; i += nt) {
@@ -93,7 +114,7 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double* __restri
                 if (q < r) {
                     const double apq = A[pk(p, q, r)];
                     const double app = A[pk(p, p, r)], aqq = A[pk(q, q, r)];
-                    if (apq != 0.0 && fabs(apq) > 1e-16 * sqrt(fabs(app * aqq))) {
+                    if (fabs(apq) > fmax(1e-16 * sqrt(fabs(app * aqq)), floor_abs)) {
                         const double th = (aqq - app) / (2.0 * apq);
                         tv = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
                         c = 1.0 / sqrt(1.0 + tv * tv);
@@ -109,9 +130,8 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double* __restri
             }
             __syncthreads();
             // every 2 x 2 block between pairs i <= j: X <- J_i^T X J_j
-            for (int e = tid; e < P * P; e += nt) {
-                const int i = e / P, j = e % P;
-                if (i > j) continue;
+            for (int e = tid; e < nblk; e += nt) {
+                const int i = blk[e] >> 8, j = blk[e] & 0xFF;
                 const int pi = pp[i], qi = qq[i], pj = pp[j], qj = qq[j];
                 const double ci = cs[i], si = sn[i], cj = cs[j], sj = sn[j];
                 if (si == 0.0 && sj == 0.0) continue;
@@ -153,6 +173,8 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double* __restri
         if (!any) break;
     }
     for (int i = tid; i < r; i += nt) lam[i] = A[pk(i, i, r)];
+    if (VS)
+        for (int e = tid; e < r * r; e += nt) Vt_out[(size_t)(e / r) * ldv_out + e % r] = Vt[e];
     if (tid == 0 && sweep == kJacobiSweeps) atomicOr(status, DEV_NONFINITE);
 }
 
@@ -219,6 +241,22 @@ __global__ void copy_cols_kernel(double* __restrict__ Y, int ldy, const double* 
     }
 }
 
+// C = alpha * sum_s W[s] (+ b1 D1), summed in s order; tri: C symmetric from the upper part.
+__global__ void splitk_reduce_kernel(const double* __restrict__ Wk, int S, int M, int N, double* __restrict__ C,
+                                     int ldc, double alpha, const double* __restrict__ D1, double b1, int tri) {
+    const size_t total = (size_t)M * N;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / N), j = (int)(e % N);
+        if (tri && i > j) continue;
+        double acc = 0.0;
+        for (int s = 0; s < S; ++s) acc += Wk[(size_t)s * total + e];
+        double v = alpha * acc;
+        if (D1) v += b1 * D1[(size_t)i * ldc + j];
+        C[(size_t)i * ldc + j] = v;
+        if (tri && i != j) C[(size_t)j * ldc + i] = v;
+    }
+}
+
 __global__ void fill_kernel(double* __restrict__ x, int k, double v) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) x[i] = v;
 }
@@ -227,21 +265,35 @@ int grid_of(size_t total) { return (int)std::min<size_t>((total + 255) / 256, 15
 
 }  // namespace
 
-size_t jacobi_smem_bytes(int r) {
+constexpr int kJacobiSmemV = 112;    // largest r whose V^T also fits in shared memory
+
+static size_t jacobi_smem(int r, bool vs) {
     const int P = (r + (r & 1)) / 2;
-    return sizeof(double) * ((size_t)r * (r + 1) / 2 + 3 * (size_t)P) + sizeof(int) * 2 * (size_t)P;
+    return sizeof(double) * ((size_t)r * (r + 1) / 2 + 3 * (size_t)P + (vs ? (size_t)r * r : 0)) +
+           sizeof(int) * 2 * (size_t)P + sizeof(unsigned short) * (size_t)P * (P + 1) / 2;
 }
+
+size_t jacobi_smem_bytes(int r) { return jacobi_smem(r, r <= kJacobiSmemV); }
 
 dme_status launch_jacobi_eig(const double* G, int ldg, int r, double* Vt, int ldv, double* lam, int* status,
                              cudaStream_t st) {
     if (r < 1 || r > LR_MAX_RANK) return set_error("jacobi: size must be in [1, 224]"), DME_EINVAL;
     static bool attr = false;
     if (!attr) {
-        DME_CUDA_TRY(cudaFuncSetAttribute(jacobi_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)jacobi_smem_bytes(LR_MAX_RANK)));
+        DME_CUDA_TRY(cudaFuncSetAttribute(jacobi_eig_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)jacobi_smem(LR_MAX_RANK, false)));
+        DME_CUDA_TRY(cudaFuncSetAttribute(jacobi_eig_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)jacobi_smem(kJacobiSmemV, true)));
         attr = true;
     }
-    jacobi_eig_kernel<<<1, 1024, jacobi_smem_bytes(r), st>>>(G, ldg, r, Vt, ldv, lam, status);
+    // enough threads for the P(P+1)/2 rotation blocks of a sub-sweep, no more (fewer warps
+    // make the two barriers per sub-sweep cheaper)
+    const int P = (r + 1) / 2;
+    const int threads = std::min(1024, std::max(64, (P * (P + 1) / 2 + 31) / 32 * 32));
+    if (r <= kJacobiSmemV)
+        jacobi_eig_kernel<true><<<1, threads, jacobi_smem(r, true), st>>>(G, ldg, r, Vt, ldv, lam, status);
+    else
+        jacobi_eig_kernel<false><<<1, threads, jacobi_smem(r, false), st>>>(G, ldg, r, Vt, ldv, lam, status);
     DME_CUDA_TRY(cudaGetLastError());
     return DME_OK;
 }
@@ -260,6 +312,12 @@ void launch_copy_cols(double* Y, int ldy, const double* X, int ldx, int n, int k
                       cudaStream_t st) {
     if (n <= 0 || k <= 0) return;
     copy_cols_kernel<<<grid_of((size_t)n * k), 256, 0, st>>>(Y, ldy, X, ldx, n, k, alpha, d);
+}
+
+void launch_splitk_reduce(const double* W, int S, int M, int N, double* C, int ldc, double alpha, const double* D1,
+                          double b1, int tri, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return;
+    splitk_reduce_kernel<<<grid_of((size_t)M * N), 256, 0, st>>>(W, S, M, N, C, ldc, alpha, D1, b1, tri);
 }
 
 void launch_fill(double* x, int k, double v, cudaStream_t st) {

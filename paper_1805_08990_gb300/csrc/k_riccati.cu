@@ -229,14 +229,35 @@ __global__ void __launch_bounds__(1024) riccati_small_kernel(const __grid_consta
     }
 }
 
-// (3) Y[i][r] = sum_{c <= r} Linv[r][c] Z[i][c]   (Y = Z L^{-T}).
+// (1b) The partial Gram sums of (1) from a Z computed elsewhere (same blocks of
+// RZ_ROWS rows, same fixed order).
+__global__ void riccati_gpart_kernel(const __grid_constant__ RicBatch batch) {
+    const RicDesc* ds = ric_descs(batch);
+    const RicDesc& d = ds[ric_find<0>(ds, batch.nd, blockIdx.x)];
+    const int lb = blockIdx.x - d.sz, n = d.n, m = d.m;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int i = e / m, c = e % m;
+        double sacc = 0.0;
+        for (int r = 0; r < RZ_ROWS; ++r) {
+            const int rr = lb * RZ_ROWS + r;
+            if (rr < n) sacc = fma(d.Bt[(size_t)rr * m + i], d.Z[(size_t)rr * m + c], sacc);
+        }
+        d.Gpart[(size_t)lb * m * m + e] = sacc;
+    }
+}
+
+// (3) Y[i][r] = sum_{c <= r} Linv[r][c] Z[i][c]   (Y = Z L^{-T}); Y = 0 when the
+// m x m matrix was not SPD (an update with Y then leaves P as it is).
 __global__ void riccati_y_kernel(const __grid_constant__ RicBatch batch) {
     const RicDesc* ds = ric_descs(batch);
     const RicDesc& d = ds[ric_find<1>(ds, batch.nd, blockIdx.x)];
-    if (*d.status & DEV_NOTSPD) return;
     const int i = (blockIdx.x - d.sy) * blockDim.x + threadIdx.x;
     const int m = d.m;
     if (i >= d.n) return;
+    if (*d.status & DEV_NOTSPD) {
+        for (int r = 0; r < m; ++r) d.Y[(size_t)i * m + r] = 0.0;
+        return;
+    }
     for (int r = 0; r < m; ++r) {
         double s = 0.0;
         for (int c = 0; c <= r; ++c) s = fma(d.Linv[r * m + c], d.Z[(size_t)i * m + c], s);
@@ -307,6 +328,29 @@ __global__ void __launch_bounds__(256) riccati_update_kernel(const __grid_consta
             d.P[(size_t)j * n + i] = Vt[di * RU_LD + dj];
         }
     }
+}
+
+dme_status launch_riccati_from_z(const double* Bt, int n, int m, double t, double* work, int* status,
+                                 cudaStream_t st) {
+    RicBatch b;
+    std::memset(&b, 0, sizeof(b));
+    b.nd = 1;
+    RicDesc& d = b.local[0];
+    d.P = nullptr;
+    d.Bt = Bt;
+    d.Z = work;
+    d.Y = d.Z + (size_t)n * m;
+    d.Gpart = d.Y + (size_t)n * m;
+    d.Linv = d.Gpart + (size_t)rz_blocks(n) * m * m;
+    d.t = t;
+    d.n = n;
+    d.m = m;
+    d.status = status;
+    riccati_gpart_kernel<<<rz_blocks(n), 64, 0, st>>>(b);
+    riccati_small_kernel<<<1, 1024, 0, st>>>(b);
+    riccati_y_kernel<<<(n + 127) / 128, 128, 0, st>>>(b);
+    DME_CUDA_TRY(cudaGetLastError());
+    return DME_OK;
 }
 
 RicItem make_ric_item(double* P, const double* Bt, int n, int m, double t, const double* Qadd, double q,

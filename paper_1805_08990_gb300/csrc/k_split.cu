@@ -124,7 +124,7 @@ __device__ __forceinline__ void load4(const double* X, const float2* Xp, size_t 
 template <bool PAIR, int NS>
 __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restrict__ X, const float2* __restrict__ Xp,
                                                          int rows, int cols, int ldx, __nv_bfloat16* __restrict__ out,
-                                                         int Kp, float* __restrict__ scale) {
+                                                         int Kp, float* __restrict__ scale, int prow) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = blockIdx.x * 8 + warp;
     if (row >= rows) return;
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restric
     const bool zero_row = emax < -100 || emax > 126;
     const int E = emax + 1;                       // |x| < 2^E for every entry of the row
     if (lane == 0) scale[row] = zero_row ? 0.0f : ldexpf(1.0f, E);
-    const size_t plane = (size_t)rows * Kp;
+    const size_t plane = (size_t)prow * Kp;     // planes hold prow >= rows rows
     for (int k = 4 * lane; k < Kp; k += 128) {
         long long V[4] = {0, 0, 0, 0};
         if (!zero_row && k < cols) {
@@ -189,20 +189,114 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restric
     }
 }
 
-void launch_slice_rows_f64(const double* X, int rows, int cols, int ldx, const SliceBuf& sb, cudaStream_t st) {
-    const int g = (rows + 7) / 8;
-    if (sb.ns == 5)
-        slice_rows_kernel<false, 5><<<g, 256, 0, st>>>(X, nullptr, rows, cols, ldx, sb.data, sb.Kp, sb.scale);
+// Long rows (Kp > 1024): one CTA of 256 threads per row; each thread keeps G
+// groups of 4 consecutive entries (k = 4 tid + 1024 g) in registers, so the
+// row is read from memory once; the row maximum is a block reduction.  Same
+// digits as slice_rows_kernel.
+template <bool PAIR, int NS, int G>
+__global__ void __launch_bounds__(256) slice_long_rows_kernel(const double* __restrict__ X,
+                                                              const float2* __restrict__ Xp, int rows, int cols,
+                                                              int ldx, __nv_bfloat16* __restrict__ out, int Kp,
+                                                              float* __restrict__ scale, int prow) {
+    __shared__ int wmax[8];
+    const int row = blockIdx.x, tid = threadIdx.x;
+    const size_t base = (size_t)row * ldx;
+    const bool vec = (ldx % 2) == 0;
+    double d[G][4];
+    float2 f[G][4];
+    int emax = -100000;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const int k = 4 * tid + 1024 * g;
+        if (k < cols) {
+            load4<PAIR>(X, Xp, base, k, cols, vec, d[g], f[g]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                d[g][u] = 0.0;
+                f[g][u] = make_float2(0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int e;
+            if (PAIR) {
+                const unsigned int b = __float_as_uint(f[g][u].x) & 0x7FFFFFFFu;
+                const int ef = (int)(b >> 23);
+                e = (b == 0 || ef == 0) ? -100000 : ef - 127;
+            } else {
+                const unsigned long long b = (unsigned long long)__double_as_longlong(d[g][u]);
+                const int ed = (int)((b >> 52) & 0x7FF);
+                e = (ed == 0) ? -100000 : ed - 1023;
+            }
+            emax = max(emax, e);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+    if ((tid & 31) == 0) wmax[tid >> 5] = emax;
+    __syncthreads();
+    emax = wmax[0];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) emax = max(emax, wmax[w]);
+    const bool zero_row = emax < -100 || emax > 126;
+    const int E = emax + 1;
+    if (tid == 0) scale[row] = zero_row ? 0.0f : ldexpf(1.0f, E);
+    const size_t plane = (size_t)prow * Kp;     // planes hold prow >= rows rows
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const int k = 4 * tid + 1024 * g;
+        if (k >= Kp) continue;
+        long long V[4] = {0, 0, 0, 0};
+        if (!zero_row && k < cols) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                V[u] = PAIR ? fixed41_f(f[g][u].x, E) + fixed41_f(f[g][u].y, E) : fixed41_d(d[g][u], E);
+        }
+        const size_t o = (size_t)row * Kp + k;
+#pragma unroll
+        for (int t = 0; t < NS; ++t) {
+            const int sh = 35 - 7 * t;
+            const float unit = __int_as_float((127 - 6 - 7 * t) << 23);
+            float q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long dd = (V[u] + (1ll << (sh - 1))) >> sh;
+                V[u] -= dd << sh;
+                q[u] = (float)(int)dd * unit;
+            }
+            const __nv_bfloat162 p01 = __floats2bfloat162_rn(q[0], q[1]);
+            const __nv_bfloat162 p23 = __floats2bfloat162_rn(q[2], q[3]);
+            uint2 w;
+            w.x = *reinterpret_cast<const unsigned int*>(&p01);
+            w.y = *reinterpret_cast<const unsigned int*>(&p23);
+            *reinterpret_cast<uint2*>(out + t * plane + o) = w;
+        }
+    }
+}
+
+template <bool PAIR, int NS>
+static void slice_launch(const double* X, const float2* Xp, int rows, int cols, int ldx, const SliceBuf& sb,
+                         cudaStream_t st) {
+    if (rows <= 0 || rows > sb.rows) return;
+    const int pr = sb.rows;
+    if (sb.Kp > 2048)
+        slice_long_rows_kernel<PAIR, NS, 4><<<rows, 256, 0, st>>>(X, Xp, rows, cols, ldx, sb.data, sb.Kp, sb.scale, pr);
+    else if (sb.Kp > 1024)
+        slice_long_rows_kernel<PAIR, NS, 2><<<rows, 256, 0, st>>>(X, Xp, rows, cols, ldx, sb.data, sb.Kp, sb.scale, pr);
     else
-        slice_rows_kernel<false, 4><<<g, 256, 0, st>>>(X, nullptr, rows, cols, ldx, sb.data, sb.Kp, sb.scale);
+        slice_rows_kernel<PAIR, NS><<<(rows + 7) / 8, 256, 0, st>>>(X, Xp, rows, cols, ldx, sb.data, sb.Kp, sb.scale,
+                                                                     pr);
+}
+
+void launch_slice_rows_f64(const double* X, int rows, int cols, int ldx, const SliceBuf& sb, cudaStream_t st) {
+    if (sb.ns == 5) slice_launch<false, 5>(X, nullptr, rows, cols, ldx, sb, st);
+    else slice_launch<false, 4>(X, nullptr, rows, cols, ldx, sb, st);
 }
 
 void launch_slice_rows_pair(const float2* Xp, int rows, int cols, int ldx, const SliceBuf& sb, cudaStream_t st) {
-    const int g = (rows + 7) / 8;
-    if (sb.ns == 5)
-        slice_rows_kernel<true, 5><<<g, 256, 0, st>>>(nullptr, Xp, rows, cols, ldx, sb.data, sb.Kp, sb.scale);
-    else
-        slice_rows_kernel<true, 4><<<g, 256, 0, st>>>(nullptr, Xp, rows, cols, ldx, sb.data, sb.Kp, sb.scale);
+    if (sb.ns == 5) slice_launch<true, 5>(nullptr, Xp, rows, cols, ldx, sb, st);
+    else slice_launch<true, 4>(nullptr, Xp, rows, cols, ldx, sb, st);
 }
 
 // ============================================================== tcgen05 GEMM
@@ -649,6 +743,17 @@ dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzPar
         p.Kp / OZ_BK >= 16) {
         p.split_parts = 2;
         p.split_first = tiles - tail;
+    } else if (p.ws && p.ws_cnt && tiles <= nsm / 2 && tiles <= OZ_SPLIT_MAX_TAIL && p.Kp / OZ_BK >= 16) {
+        // a single partial wave (skinny products): up to 4 K parts, at least 8 K blocks each,
+        // within the SM count and the workspace's 2 x OZ_SPLIT_MAX_TAIL tile slots
+        int parts = 1;
+        while (parts < 4 && tiles * (parts * 2) <= nsm && tiles * (parts * 2) <= 2 * OZ_SPLIT_MAX_TAIL &&
+               p.Kp / OZ_BK / (parts * 2) >= 8)
+            parts *= 2;
+        if (parts > 1) {
+            p.split_parts = parts;
+            p.split_first = 0;
+        }
     }
     const int grid = p.split_first + (tiles - p.split_first) * p.split_parts;
     ozaki_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM_BYTES, st>>>(tA, tB, p);

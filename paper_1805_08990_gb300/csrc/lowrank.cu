@@ -49,6 +49,12 @@ struct dme_lr_s {
     double *Gm = nullptr, *H = nullptr, *VtH = nullptr, *lamH = nullptr, *F = nullptr, *Y = nullptr, *Z = nullptr;
     double* Pout = nullptr;   // n x n, allocated on the first dense output
     int* kdev = nullptr;
+    bool split = false;            // the products with E_t and S on the tensor cores
+    SliceBuf xsl;                  // split: slices of X^T for M X (rows = rmax, k = n)
+    double* Xtr = nullptr;         // split: X^T (rmax x n)
+    double* ws = nullptr;          // split-K partial products
+    size_t ws_doubles = 0;
+    GemmProb* wsdesc = nullptr;    // their descriptors (kSplitMax)
     std::vector<WFactor> wf;
     std::vector<void*> allocs;
     int r = 0;
@@ -90,10 +96,44 @@ GemmProb mk(int M, int N, int K, const double* A, int lda, int tA, const double*
     return g;
 }
 
-dme_status gemm(const GemmProb& g, cudaStream_t st) {
+constexpr int kSplitMax = 64;   // K chunks of a split-K product
+
+dme_status gemm_ws(dme_lr_t lr, const GemmProb& g, cudaStream_t st);
+
+// FP64 product of the low-rank path.  Skinny outputs (N <= 64) use 32-wide
+// tiles; a small output with a long K (Gram matrices L^T L, L^T Bt) is split
+// into K chunks, one grouped launch, then summed in chunk order.
+dme_status gemm(dme_lr_t lr, const GemmProb& g, cudaStream_t st) {
     if (g.M <= 0 || g.N <= 0) return DME_OK;
+    const long tiles64 = (long)((g.M + 63) / 64) * ((g.N + 63) / 64);
+    if (tiles64 <= 16 && g.K >= 1024) return gemm_ws(lr, g, st);
     std::vector<GemmProb> v{g};
-    return gemm64_grouped(v, nullptr, st);
+    return gemm64_grouped(v, nullptr, st, nullptr, g.N <= 64 ? 32 : 64);
+}
+
+dme_status gemm_ws(dme_lr_t lr, const GemmProb& g, cudaStream_t st) {
+    const size_t mn = (size_t)g.M * g.N;
+    int S = std::min(kSplitMax, std::max(1, g.K / 128));
+    S = std::max(1, std::min<int>(S, (int)(lr->ws_doubles / mn)));
+    const int chunk = ((g.K + S - 1) / S + 15) / 16 * 16;
+    S = (g.K + chunk - 1) / chunk;
+    std::vector<GemmProb> parts;
+    for (int s = 0; s < S; ++s) {
+        const int k0 = s * chunk, kc = std::min(chunk, g.K - k0);
+        GemmProb q = g;
+        q.K = kc;
+        q.A = g.transA ? g.A + (size_t)k0 * g.lda : g.A + k0;
+        q.B = g.transB ? g.B + k0 : g.B + (size_t)k0 * g.ldb;
+        q.C = lr->ws + (size_t)s * mn;
+        q.ldc = q.ldd = g.N;
+        q.alpha = 1.0;
+        q.tri = 0;
+        q.D1 = q.D2 = q.D3 = nullptr;
+        parts.push_back(q);
+    }
+    DME_TRY(gemm64_grouped(parts, lr->wsdesc, st, nullptr, g.N <= 64 ? 32 : 64));
+    launch_splitk_reduce(lr->ws, S, g.M, g.N, g.C, g.ldc, g.alpha, g.D1, g.b1, g.tri, st);
+    return DME_OK;
 }
 
 // Compress the factor (L, d) with r columns (leading dimension ld) in place;
@@ -103,13 +143,13 @@ dme_status compress(dme_lr_t lr, double* L, double* L2, double* d, int ld, int& 
     cudaStream_t st = lr->P->st;
     const int n = lr->n;
     launch_copy_cols(L2, ld, L, ld, n, r, 1.0, d, st);                                     // Lt = L d^{1/2}
-    DME_TRY(gemm(mk(r, r, n, L2, ld, 1, L2, ld, 0, lr->G, lr->rcap, 1.0, 1), st));          // Lt^T Lt
+    DME_TRY(gemm(lr, mk(r, r, n, L2, ld, 1, L2, ld, 0, lr->G, lr->rcap, 1.0, 1), st));          // Lt^T Lt
     DME_TRY(launch_jacobi_eig(lr->G, lr->rcap, r, lr->Vt, lr->rcap, lr->lam, lr->P->status, st));
     launch_lr_select(lr->lam, lr->Vt, lr->rcap, r, lr->tol, 1, lr->T, lr->rcap, d, lr->kdev, st);
     int k = 0;
     DME_CUDA_TRY(cudaMemcpyAsync(&k, lr->kdev, sizeof(int), cudaMemcpyDeviceToHost, st));
     DME_CUDA_TRY(cudaStreamSynchronize(st));
-    DME_TRY(gemm(mk(n, k, r, L2, ld, 0, lr->T, lr->rcap, 0, L, ld, 1.0), st));              // L = Lt V_k Lambda^-1/2
+    DME_TRY(gemm(lr, mk(n, k, r, L2, ld, 0, lr->T, lr->rcap, 0, L, ld, 1.0), st));              // L = Lt V_k Lambda^-1/2
     r = k;
     return DME_OK;
 }
@@ -201,7 +241,7 @@ dme_status wfactor(dme_lr_t lr, double tau, const WFactor** out) {
         int idx;
         DME_TRY(plan_ew(lr->P, s[k], &idx));
         const double* E = lr->P->ew[idx].E;
-        DME_TRY(gemm(mk(n, p, n, E, n, 1, lr->LQ, p, 0, WL + (size_t)k * p, lr->rcap, 1.0), st));   // E_s^T C^T
+        DME_TRY(gemm(lr, mk(n, p, n, E, n, 1, lr->LQ, p, 0, WL + (size_t)k * p, lr->rcap, 1.0), st));   // E_s^T C^T
         launch_fill(wd + (size_t)k * p, p, w[k], st);
     }
     int r = k0;
@@ -219,12 +259,43 @@ dme_status wfactor(dme_lr_t lr, double tau, const WFactor** out) {
     return DME_OK;
 }
 
+// Split precision: C (n x k, ldc) = alpha M X for X (n x k, ldx), M given by the
+// bf16 slices of its rows (E_t^T or S of the plan): X^T is sliced and the
+// tcgen05 GEMM forms M (X^T)^T with FP64 output.
+dme_status apply_split(dme_lr_t lr, const SliceBuf& Msl, const double* X, int ldx, int k, double* C, int ldc,
+                       double alpha) {
+    if (k == 0) return DME_OK;
+    cudaStream_t st = lr->P->st;
+    const int n = lr->n;
+    launch_transpose(X, lr->Xtr, n, k, ldx, n, st);
+    launch_slice_rows_f64(lr->Xtr, k, n, n, lr->xsl, st);
+    OzParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.M = n;
+    p.N = k;
+    p.Kp = Msl.Kp;
+    p.sa = Msl.scale;
+    p.sb = lr->xsl.scale;
+    p.mode = OZ_OUT_F64;
+    p.ldc = ldc;
+    p.Cd = C;
+    p.alpha = alpha;
+    p.status = lr->P->status;
+    p.ws = lr->P->kws;
+    p.ws_cnt = lr->P->kcnt;
+    return launch_ozaki_gemm(Msl.tmap, lr->xsl.tmap, p, st);
+}
+
 dme_status lr_T1(dme_lr_t lr, double tau) {
     if (lr->r == 0) return DME_OK;
     int idx;
     DME_TRY(plan_ew(lr->P, tau, &idx));
-    const double* E = lr->P->ew[idx].E;
-    DME_TRY(gemm(mk(lr->n, lr->r, lr->n, E, lr->n, 1, lr->L, lr->rcap, 0, lr->L2, lr->rcap, 1.0), lr->P->st));
+    const EWEntry& e = lr->P->ew[idx];
+    if (lr->split)
+        DME_TRY(apply_split(lr, e.Gsl, lr->L, lr->rcap, lr->r, lr->L2, lr->rcap, 1.0));
+    else
+        DME_TRY(gemm(lr, mk(lr->n, lr->r, lr->n, e.E, lr->n, 1, lr->L, lr->rcap, 0, lr->L2, lr->rcap, 1.0),
+                     lr->P->st));
     std::swap(lr->L, lr->L2);
     return DME_OK;
 }
@@ -257,13 +328,13 @@ dme_status lr_T3(dme_lr_t lr, double tau) {
     cudaStream_t st = lr->P->st;
     const int n = lr->n, m = lr->m, r = lr->r, rc = lr->rcap;
     launch_copy_cols(lr->L2, rc, lr->L, rc, n, r, 1.0, lr->d, st);                              // Lt
-    DME_TRY(gemm(mk(r, m, n, lr->L2, rc, 1, lr->P->Bt, m, 0, lr->Gm, m, 1.0), st));              // G = Lt^T Bt
-    DME_TRY(gemm(mk(m, m, r, lr->Gm, m, 1, lr->Gm, m, 0, lr->H, m, 1.0, 1), st));                // G^T G
+    DME_TRY(gemm(lr, mk(r, m, n, lr->L2, rc, 1, lr->P->Bt, m, 0, lr->Gm, m, 1.0), st));              // G = Lt^T Bt
+    DME_TRY(gemm(lr, mk(m, m, r, lr->Gm, m, 1, lr->Gm, m, 0, lr->H, m, 1.0, 1), st));                // G^T G
     DME_TRY(launch_jacobi_eig(lr->H, m, m, lr->VtH, m, lr->lamH, lr->P->status, st));
     launch_ric_weights(lr->lamH, lr->VtH, m, m, tau, lr->F, m, st);                               // F(G^T G)
-    DME_TRY(gemm(mk(r, m, m, lr->Gm, m, 0, lr->F, m, 0, lr->Y, m, 1.0), st));                    // Y = G F
-    DME_TRY(gemm(mk(n, m, r, lr->L2, rc, 0, lr->Gm, m, 0, lr->Z, m, 1.0), st));                  // Z = Lt G
-    DME_TRY(gemm(mk(n, r, m, lr->Z, m, 0, lr->Y, m, 1, lr->L, rc, 1.0, 0, lr->L2, 1.0), st));    // L = Lt + Z Y^T
+    DME_TRY(gemm(lr, mk(r, m, m, lr->Gm, m, 0, lr->F, m, 0, lr->Y, m, 1.0), st));                    // Y = G F
+    DME_TRY(gemm(lr, mk(n, m, r, lr->L2, rc, 0, lr->Gm, m, 0, lr->Z, m, 1.0), st));                  // Z = Lt G
+    DME_TRY(gemm(lr, mk(n, r, m, lr->Z, m, 0, lr->Y, m, 1, lr->L, rc, 1.0, 0, lr->L2, 1.0), st));    // L = Lt + Z Y^T
     launch_fill(lr->d, r, 1.0, st);
     return DME_OK;
 }
@@ -275,9 +346,14 @@ dme_status lr_T4(dme_lr_t lr, double tau, int rule) {
     const int blocks = rule == DME_T4_EULER ? 2 : 3;
     DME_TRY(need_cols(lr, blocks * r));
     const double* S = lr->P->S;
-    DME_TRY(gemm(mk(n, r, n, S, n, 0, lr->L, rc, 0, lr->L + r, rc, std::sqrt(tau)), st));              // sqrt(t) S L
-    if (blocks == 3)
-        DME_TRY(gemm(mk(n, r, n, S, n, 0, lr->L + r, rc, 0, lr->L + 2 * r, rc, std::sqrt(0.5 * tau)), st));
+    if (lr->split) {
+        DME_TRY(apply_split(lr, lr->P->Ssl, lr->L, rc, r, lr->L + r, rc, std::sqrt(tau)));
+        if (blocks == 3) DME_TRY(apply_split(lr, lr->P->Ssl, lr->L + r, rc, r, lr->L + 2 * r, rc, std::sqrt(0.5 * tau)));
+    } else {
+        DME_TRY(gemm(lr, mk(n, r, n, S, n, 0, lr->L, rc, 0, lr->L + r, rc, std::sqrt(tau)), st));          // sqrt(t) S L
+        if (blocks == 3)
+            DME_TRY(gemm(lr, mk(n, r, n, S, n, 0, lr->L + r, rc, 0, lr->L + 2 * r, rc, std::sqrt(0.5 * tau)), st));
+    }
     for (int b = 1; b < blocks; ++b)
         DME_CUDA_TRY(cudaMemcpyAsync(lr->d + b * r, lr->d, sizeof(double) * r, cudaMemcpyDeviceToDevice, st));
     lr->r = blocks * r;
@@ -333,7 +409,8 @@ dme_status dme_lr_plan(const dme_plan_desc* desc, const double* A, const double*
     set_error("");
     if (!desc || !A || !C) return set_error("desc, A and C are required"), DME_EINVAL;
     if (!desc->q_is_factor) return set_error("low-rank path: give Q as its factor C (q_is_factor = 1)"), DME_EINVAL;
-    if (desc->prec != DME_FP64) return set_error("low-rank path: prec must be DME_FP64"), DME_EINVAL;
+    if (desc->prec != DME_FP64 && desc->prec != DME_SPLIT_BF16)
+        return set_error("low-rank path: prec must be DME_FP64 or DME_SPLIT_BF16"), DME_EINVAL;
     if (desc->fsal || desc->extrap > 1) return set_error("low-rank path: no fsal / extrapolation"), DME_EINVAL;
     const int q = opts && opts->quad_nodes > 0 ? opts->quad_nodes : 7;
     const int rmax = opts && opts->rmax > 0 ? opts->rmax : LR_MAX_RANK;
@@ -369,6 +446,28 @@ dme_status dme_lr_plan(const dme_plan_desc* desc, const double* A, const double*
         DME_TRY(lr_alloc(lr.get(), &lr->F, m * m));
         DME_TRY(lr_alloc(lr.get(), &lr->Y, rc * m));
         DME_TRY(lr_alloc(lr.get(), &lr->Z, n * m));
+        lr->ws_doubles = std::max<size_t>((size_t)8 * rc * rc, (size_t)kSplitMax * rc * m);
+        DME_TRY(lr_alloc(lr.get(), &lr->ws, lr->ws_doubles));
+        double* wd = nullptr;
+        DME_TRY(lr_alloc(lr.get(), &wd, (sizeof(GemmProb) * kSplitMax + 7) / 8));
+        lr->wsdesc = reinterpret_cast<GemmProb*>(wd);
+        lr->split = desc->prec == DME_SPLIT_BF16;
+        if (lr->split) {
+            DME_TRY(lr_alloc(lr.get(), &lr->Xtr, rc * n));
+            lr->xsl.rows = (int)rc;
+            lr->xsl.k = (int)n;
+            lr->xsl.Kp = slice_kpad((int)n);
+            lr->xsl.ns = OZ_SLICES_B;
+            double* xd = nullptr;
+            DME_TRY(lr_alloc(lr.get(), &xd, (slice_buf_bytes((int)rc, (int)n, OZ_SLICES_B) + 7) / 8));
+            lr->xsl.data = reinterpret_cast<__nv_bfloat16*>(xd);
+            double* xs = nullptr;
+            DME_TRY(lr_alloc(lr.get(), &xs, (rc + 1) / 2));
+            lr->xsl.scale = reinterpret_cast<float*>(xs);
+            DME_CUDA_TRY(cudaMemsetAsync(xd, 0, slice_buf_bytes((int)rc, (int)n, OZ_SLICES_B), st));
+            DME_CUDA_TRY(cudaMemsetAsync(xs, 0, sizeof(float) * rc, st));
+            DME_TRY(make_slice_tmap(lr->xsl, &lr->xsl.tmap));
+        }
         double* kd = nullptr;
         DME_TRY(lr_alloc(lr.get(), &kd, 1));
         lr->kdev = reinterpret_cast<int*>(kd);
@@ -405,7 +504,7 @@ dme_status dme_lr_solve(dme_lr_t lr, const double* L0, const double* D0, int r0,
             int k = 0;
             DME_CUDA_TRY(cudaMemcpyAsync(&k, lr->kdev, sizeof(int), cudaMemcpyDeviceToHost, st));
             DME_CUDA_TRY(cudaStreamSynchronize(st));
-            DME_TRY(gemm(mk(n, k, r0, lr->L2, rc, 0, lr->T, rc, 0, lr->L, rc, 1.0), st));
+            DME_TRY(gemm(lr, mk(n, k, r0, lr->L2, rc, 0, lr->T, rc, 0, lr->L, rc, 1.0), st));
             lr->r = k;
             DME_TRY(compress(lr, lr->L, lr->L2, lr->d, rc, lr->r));
         }
@@ -418,7 +517,7 @@ dme_status dme_lr_solve(dme_lr_t lr, const double* L0, const double* D0, int r0,
             if (!lr->Pout) DME_TRY(lr_alloc(lr, &lr->Pout, nn));
             if (lr->r > 0) {
                 launch_copy_cols(lr->L2, rc, lr->L, rc, n, lr->r, 1.0, lr->d, st);
-                DME_TRY(gemm(mk(n, n, lr->r, lr->L2, rc, 0, lr->L2, rc, 1, lr->Pout, n, 1.0, 1), st));
+                DME_TRY(gemm(lr, mk(n, n, lr->r, lr->L2, rc, 0, lr->L2, rc, 1, lr->Pout, n, 1.0, 1), st));
             } else {
                 DME_CUDA_TRY(cudaMemsetAsync(lr->Pout, 0, nn * sizeof(double), st));
             }

@@ -254,6 +254,58 @@ dme_status split_cong(dme_plan_t p, const double* P, const SliceBuf& G, double* 
     return launch_ozaki_gemm(G.tmap, p->usl.tmap, b, st);
 }
 
+// T3 on the split path for n > 1536: Z^T = Bt^T P (P symmetric) on the tensor
+// cores (Bt^T with 5 slices as the fixed operand, P with 4), then the m x m
+// part in FP64 (Gram partials, M = I + t Bt^T Z, Cholesky, Y = Z L^{-T}), then
+// P <- P - t Y Y^T (+ q Q) as a triangle tensor GEMM with K = m and the FP64
+// epilogue adding P.  Same formula as launch_riccati, other rounding.
+dme_status split_riccati(dme_plan_t p, double* P, double tau, double qcoef) {
+    const int n = p->n, m = p->m;
+    cudaStream_t st = p->st;
+    double* Z = p->rwork;
+    double* Y = Z + (size_t)n * m;
+    launch_slice_rows_f64(P, n, n, n, p->psl, st);
+    OzParams a;
+    std::memset(&a, 0, sizeof(a));
+    a.M = m;
+    a.N = n;
+    a.Kp = p->btsl.Kp;
+    a.sa = p->btsl.scale;
+    a.sb = p->psl.scale;
+    a.mode = OZ_OUT_F64;
+    a.ldc = n;
+    a.Cd = p->Zt;
+    a.alpha = 1.0;
+    a.status = p->status;
+    a.ws = p->kws;
+    a.ws_cnt = p->kcnt;
+    DME_TRY(launch_ozaki_gemm(p->btsl.tmap, p->psl.tmap, a, st));
+    launch_transpose(p->Zt, Z, m, n, n, m, st);
+    DME_TRY(launch_riccati_from_z(p->Bt, n, m, tau, p->rwork, p->status, st));
+    launch_slice_rows_f64(Y, n, m, m, p->ysl5, st);
+    launch_slice_rows_f64(Y, n, m, m, p->ysl4, st);
+    OzParams b;
+    std::memset(&b, 0, sizeof(b));
+    b.M = n;
+    b.N = n;
+    b.Kp = p->ysl5.Kp;
+    b.sa = p->ysl5.scale;
+    b.sb = p->ysl4.scale;
+    b.mode = OZ_OUT_F64;
+    b.tri = 1;
+    b.ldc = n;
+    b.Cd = P;
+    b.alpha = -tau;
+    b.D1 = P;
+    b.b1 = 1.0;
+    if (qcoef != 0.0) {
+        b.D2 = p->Q;
+        b.b2 = qcoef;
+    }
+    b.status = p->status;
+    return launch_ozaki_gemm(p->ysl5.tmap, p->ysl4.tmap, b, st);
+}
+
 dme_status compute_ew(dme_plan_t p, double tau, int* idx) {
     for (size_t i = 0; i < p->ew.size(); ++i)
         if (p->ew[i].tau == tau) {
@@ -591,6 +643,7 @@ dme_status dme::run_op(dme_plan_t p, const Op& o, double* Pcaller) {
             return DME_OK;
         case OP_RICC: {
             ProfScope ps(p, DME_KIND_RICCATI);
+            if (p->tric) return split_riccati(p, P, o.tau, o.qcoef);
             launch_riccati(P, p->Bt, n, p->m, o.tau, o.qcoef != 0.0 ? p->Q : nullptr, o.qcoef, p->rwork, p->status,
                            st);
             return DME_OK;
@@ -752,6 +805,18 @@ dme_status dme::plan_create(const dme_plan_desc* d, const double* A, const doubl
             DME_TRY(palloc_t(p, &p->kws, OZ_SPLIT_WS_FLOAT2));
             DME_TRY(palloc_t(p, &p->kcnt, (size_t)OZ_SPLIT_MAX_TAIL));
             DME_CUDA_TRY(cudaMemsetAsync(p->kcnt, 0, sizeof(int) * OZ_SPLIT_MAX_TAIL, st));
+            if (ric) {
+                // the Riccati products on the tensor cores (below 1537 the FP64 kernels are
+                // cheap, and serving, which uses them, stays bit-identical to single plans)
+                const int m = p->m;
+                p->tric = true;
+                DME_TRY(palloc_t(p, &p->Zt, (size_t)m * n));
+                DME_TRY(alloc_slices(p, &p->btsl, m, n, OZ_SLICES_A));
+                DME_TRY(alloc_slices(p, &p->ysl5, n, m, OZ_SLICES_A));
+                DME_TRY(alloc_slices(p, &p->ysl4, n, m, OZ_SLICES_B));
+                launch_transpose(p->Bt, p->Zt, n, m, m, n, st);
+                launch_slice_rows_f64(p->Zt, m, n, n, p->btsl, st);
+            }
         }
         if (gen) {
             DME_TRY(alloc_slices(p, &p->Ssl, n, n, OZ_SLICES_A));

@@ -75,6 +75,11 @@ struct dme_plan_s {
     float2* U = nullptr;       // split path: G P as normalised (hi, lo) pairs
     float2* kws = nullptr;     // split path: split-K workspace of the tail tiles
     int* kcnt = nullptr;       // split path: split-K arrival counters
+    // split path with n > 1536 and T3: the Riccati products on the tensor cores
+    bool tric = false;
+    SliceBuf btsl;             // slices of Bt^T (m rows, 5 slices)
+    SliceBuf ysl5, ysl4;       // slices of Y (n rows, k = m)
+    double* Zt = nullptr;      // Z^T = Bt^T P (m x n)
     // profiling: CUDA-event pairs around launches made outside graph capture
     bool prof = false;
     std::vector<cudaEvent_t> evpool;

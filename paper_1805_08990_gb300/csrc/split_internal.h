@@ -65,7 +65,8 @@ struct OzGroupDesc {
 int slice_kpad(int k);
 size_t slice_buf_bytes(int rows, int k, int ns);
 dme_status make_slice_tmap(const SliceBuf& sb, CUtensorMap* out);
-// Slice the rows of X (rows x cols, leading dimension ldx) into sb (sb.ns = 4 or 5).
+// Slice the rows of X (rows x cols, leading dimension ldx; rows <= sb.rows) into sb
+// (sb.ns = 4 or 5; each plane holds sb.rows rows, the ones past `rows` untouched).
 void launch_slice_rows_f64(const double* X, int rows, int cols, int ldx, const SliceBuf& sb, cudaStream_t st);
 void launch_slice_rows_pair(const float2* Xp, int rows, int cols, int ldx, const SliceBuf& sb, cudaStream_t st);
 dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzParams p, cudaStream_t st);

@@ -7,7 +7,7 @@ import pytest
 import dme_workloads as W
 import oracle as O
 import paper_1805_08990_gb300 as dme
-from gpu_util import FP64_TOL, dev, rel, require_gpu
+from gpu_util import FP64_TOL, SPLIT_TOL, dev, rel, require_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -17,7 +17,7 @@ def _gpu():
     require_gpu()
 
 
-def _run(pr, flows, comp, N, q=7, tol=1e-13, L0=None, D0=None, T=None):
+def _run(pr, flows, comp, N, q=7, tol=1e-13, L0=None, D0=None, T=None, prec="fp64"):
     T = pr.T if T is None else T
     uses_B = "F3" in flows
     uses_S = "F4" in flows
@@ -26,7 +26,7 @@ def _run(pr, flows, comp, N, q=7, tol=1e-13, L0=None, D0=None, T=None):
     S = pr.S if uses_S else None
     plan = dme.LowRankPlan(dev(pr.A), dev(pr.C), h=T / N, flows=flows, comp=comp,
                            B=None if B is None else dev(B), R=None if R is None else dev(R),
-                           S=None if S is None else dev(S), quad_nodes=q, tol=tol)
+                           S=None if S is None else dev(S), quad_nodes=q, tol=tol, prec=prec)
     P = np.empty((pr.n, pr.n))
     r = plan.solve(T, N, L0=L0, D0=D0, P_out=P)
     L, d = plan.factors()
@@ -103,9 +103,37 @@ def test_lowrank_errors():
         plan = dme.LowRankPlan(dev(pr.A), dev(pr.C), h=0.1, flows=["F12", "F3"], B=dev(pr.B), R=dev(pr.R), rmax=8)
         plan.solve(1.0, 10, P_out=np.empty((pr.n, pr.n)))
     assert ei.value.status in (dme.DME_ENOMEM,)
-    d = dme.make_desc(pr.n, m=2, p=3, eq=dme.DME_DRE, flows=["F12", "F3"], prec="split_bf16", h=0.1, q_is_factor=True)
+    d = dme.make_desc(pr.n, m=2, p=3, eq=dme.DME_DRE, flows=["F12", "F3"], prec=7, h=0.1, q_is_factor=True)
     with pytest.raises(dme.DmeError):
         dme.dme_lr_plan(d, pr.A, pr.C, pr.B, pr.R)
     d = dme.make_desc(pr.n, m=2, p=3, eq=dme.DME_DRE, flows=["F12", "F3"], h=0.1, q_is_factor=False)
     with pytest.raises(dme.DmeError):
         dme.dme_lr_plan(d, pr.A, pr.Q, pr.B, pr.R)
+
+
+@pytest.mark.parametrize("kind,flows,comp,N", [("dle", ["F1", "F2"], "strang", 10), ("dre", ["F12", "F3"], "strang", 5),
+                                               ("gdre", ["F12", "F3", "F4"], "strang", 3),
+                                               ("dre", ["F1", "F3", "F2"], "lie", 4)])
+def test_lowrank_split_precision_matches_oracle(kind, flows, comp, N):
+    """The products with E_t and S on the tensor cores (bf16 slices, exact
+    accumulation), the rest in FP64: within the split-precision bar."""
+    pr = _problem(kind)
+    P, r, L, d, Lo, Do = _run(pr, flows, comp, N, prec="split_bf16")
+    assert rel(P, O.ldl_product(Lo, Do)) < SPLIT_TOL
+    assert abs(r - Lo.shape[1]) <= 1
+
+
+def test_lowrank_split_at_full_size_matches_fp64_lowrank():
+    """n = 4096 (the large DRE): split-precision factored steps against the FP64
+    factored steps on the GPU (both parity-tested against the oracle above)."""
+    pr = W.dre_heat_large()
+    h = 1 / 256
+    out = {}
+    for prec in ("fp64", "split_bf16"):
+        plan = dme.LowRankPlan(dev(pr.A), dev(pr.C), h=h, flows=["F1", "F2", "F3"], B=dev(pr.B), R=dev(pr.R),
+                               prec=prec)
+        P = np.empty((pr.n, pr.n))
+        out[prec] = (plan.solve(8 * h, 8, P_out=P), P)
+        plan.close()
+    assert abs(out["fp64"][0] - out["split_bf16"][0]) <= 1
+    assert rel(out["split_bf16"][1], out["fp64"][1]) < SPLIT_TOL
