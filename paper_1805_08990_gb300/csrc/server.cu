@@ -88,7 +88,8 @@ struct dme_server_s {
     DescArena arena;              // launch descriptors of the captured round
     GemmProb* tune_desc = nullptr;  // autotuner's descriptor buffer (max_slots)
     cudaGraphExec_t round_exec = nullptr;
-    std::vector<Req*> round_members;   // the residents the captured round serves, in order
+    std::vector<uint64_t> round_ids;   // ids of the residents the captured round serves, in order
+                                       // (ids, not addresses: a new request may reuse a freed Req's address)
     std::map<int, int> tile_choice;    // autotuner: ceil(log2(64-tiles of a group)) -> tile 32 / 64
     std::vector<double> lat_ms;
     int completed = 0, failed = 0, rounds = 0, graph_builds = 0, tuned = 0;
@@ -388,7 +389,7 @@ dme_status build_round_graph(dme_server_t s, std::vector<Req*>& res) {
         cudaGraphExecDestroy(s->round_exec);
         s->round_exec = nullptr;
     }
-    s->round_members.clear();
+    s->round_ids.clear();
     DME_TRY(tune_tiles(s, res));
     s->arena.host.clear();
     cudaGraph_t g = nullptr;
@@ -405,7 +406,7 @@ dme_status build_round_graph(dme_server_t s, std::vector<Req*>& res) {
     if (e != cudaSuccess) return set_error(std::string("serving: graph instantiate: ") + cudaGetErrorString(e)), DME_ECUDA;
     if (!s->arena.host.empty())
         DME_CUDA_TRY(cudaMemcpy(s->arena.dev, s->arena.host.data(), s->arena.host.size(), cudaMemcpyHostToDevice));
-    s->round_members = res;
+    for (Req* r : res) s->round_ids.push_back(r->id);
     s->graph_builds++;
     return DME_OK;
 }
@@ -424,7 +425,9 @@ void step_loop(dme_server_t s) {
             s->ready.clear();
         }
         dme_status st = DME_OK;
-        if (!s->round_exec || s->round_members != res) st = build_round_graph(s, res);
+        bool same = s->round_exec != nullptr && s->round_ids.size() == res.size();
+        for (size_t i = 0; same && i < res.size(); ++i) same = s->round_ids[i] == res[i]->id;
+        if (!same) st = build_round_graph(s, res);
         // rounds before the next host check: none of the residents finishes
         // earlier, and one round only while requests wait for admission
         int R = kMaxRoundsPerCheck;

@@ -168,3 +168,19 @@ def test_submit_rejections(server):
         dme.dme_submit(server, _desc(pr, 4), pr.A, pr.C, pr.B, pr.R, None, pr.P0, -1.0, 4)
     with pytest.raises(dme.DmeError):
         dme.dme_poll(server, 987654321, None, 0)
+
+
+def test_back_to_back_requests_get_their_own_round(server):
+    """One request at a time, each polled (and freed) before the next is
+    submitted: every result equals its single-plan solve bit for bit (a round
+    captured for an earlier request must never serve a later one, even when the
+    later request's bookkeeping lands at the freed address)."""
+    for k in range(6):
+        pr = W.dre_convdiff(nx=7, m=2, p=2, seed=20 + k)
+        N = 4 + k % 3
+        s, got = _poll(server, _submit(server, pr, N), pr.n)
+        assert s == dme.DME_OK
+        plan = dme.Plan(dev(pr.A), C=dev(pr.C), h=pr.T / N, flows=["F12", "F3"], B=dev(pr.B), R=dev(pr.R))
+        single = np.empty((pr.n, pr.n))
+        plan.solve(pr.P0, pr.T, N, single)
+        assert np.array_equal(got, single), k
