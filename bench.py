@@ -39,6 +39,11 @@ WORKLOAD = ("large dense DRE: 5-point Laplacian 64x64 (n=4096), B 4096x8 N(0,1),
 NOMINAL_FP64_TFLOPS = 1.25    # GB300 FP64 (non-tensor and tensor), the profiling recipe's nominal figure
 
 
+# DRAM bytes (read + write) of one full 4096^3 launch of the tensor kernel, from the
+# ncu capture summarised in profiles/ozaki_gemm_n4096_ncu.md (955.0 MB + 122.9 MB).
+OZAKI_FULL_LAUNCH_DRAM_BYTES = 1.0779e9
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -387,7 +392,11 @@ def run_ours(args):
         achieved = per_launch / (avg_ms / 1e3) / 1e12
         peak = peaks["bf16_tflops"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "ozaki_gemm_kernel (tcgen05 kind::f16, 2 launches per congruence)",
+                "traffic": OZAKI_FULL_LAUNCH_DRAM_BYTES,
+                "traffic_of": "one full n = 4096 product (dram__bytes_read.sum + dram__bytes_write.sum, ncu --set full, "
+                              "profiles/ozaki_gemm_n4096_ncu.md); its algorithmic bytes: slices of A and B 302 MB + "
+                              "output pairs 134 MB",
+                "kernel": "ozaki_gemm_kernel (tcgen05 kind::f16, 2 launches per congruence)",
                 "peak_source": f"bf16 dense burst, {peaks_src} (MEASURED_PEAKS.json)",
                 "avg_launch_ms": avg_ms,
                 "fp64_equivalent_tflops": cong_flops / (2 * avg_ms / 1e3) / 1e12,

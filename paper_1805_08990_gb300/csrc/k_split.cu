@@ -85,6 +85,30 @@ __device__ __forceinline__ long long fixed41_f(float f, int E) {
     return (b >> 31) ? -v : v;
 }
 
+// The NS base-2^7 digits of V (|V| < 2^41) with round-to-nearest,
+// d_t = round(r_t / 2^(35-7t)), r_{t+1} = r_t - d_t 2^(35-7t), in 32-bit
+// arithmetic: V = h 2^21 + l with 0 <= l < 2^21; digits 0 and 1 come from h
+// alone (l < 2^21 cannot change those floors), digit 2 is h plus the rounding
+// carry of l, and digits 3 and 4 come from the remainder l - carry 2^21.
+template <int NS>
+__device__ __forceinline__ void digits7(long long V, int (&dg)[5]) {
+    int h = (int)(V >> 21);
+    const int l = (int)(V - ((long long)h << 21));
+    int d = (h + (1 << 13)) >> 14;
+    h -= d << 14;
+    dg[0] = d;
+    d = (h + (1 << 6)) >> 7;
+    h -= d << 7;
+    dg[1] = d;
+    const int c = l >= (1 << 20) ? 1 : 0;
+    dg[2] = h + c;
+    int r = l - (c << 21);
+    d = (r + (1 << 13)) >> 14;
+    r -= d << 14;
+    dg[3] = d;
+    dg[4] = (r + (1 << 6)) >> 7;
+}
+
 // Load entries k .. k+3 of a row (zeros past `cols`); vector loads when the
 // row start is 16-byte aligned and the four entries are in range.
 template <bool PAIR>
@@ -168,17 +192,15 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restric
                 V[u] = PAIR ? fixed41_f(f[u].x, E) + fixed41_f(f[u].y, E) : fixed41_d(d[u], E);
         }
         const size_t o = (size_t)row * Kp + k;
+        int dg[4][5];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) digits7<NS>(V[u], dg[u]);
 #pragma unroll
         for (int t = 0; t < NS; ++t) {
-            const int sh = 35 - 7 * t;
             const float unit = __int_as_float((127 - 6 - 7 * t) << 23);     // 2^(-6-7t), exact
             float q[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const long long dd = (V[u] + (1ll << (sh - 1))) >> sh;
-                V[u] -= dd << sh;
-                q[u] = (float)(int)dd * unit;          // |dd| <= 64: exact in int and float
-            }
+            for (int u = 0; u < 4; ++u) q[u] = (float)dg[u][t] * unit;      // |d| <= 64: exact in float
             const __nv_bfloat162 p01 = __floats2bfloat162_rn(q[0], q[1]);
             const __nv_bfloat162 p23 = __floats2bfloat162_rn(q[2], q[3]);
             uint2 w;
@@ -254,17 +276,15 @@ __global__ void __launch_bounds__(256) slice_long_rows_kernel(const double* __re
                 V[u] = PAIR ? fixed41_f(f[g][u].x, E) + fixed41_f(f[g][u].y, E) : fixed41_d(d[g][u], E);
         }
         const size_t o = (size_t)row * Kp + k;
+        int dg[4][5];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) digits7<NS>(V[u], dg[u]);
 #pragma unroll
         for (int t = 0; t < NS; ++t) {
-            const int sh = 35 - 7 * t;
             const float unit = __int_as_float((127 - 6 - 7 * t) << 23);
             float q[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const long long dd = (V[u] + (1ll << (sh - 1))) >> sh;
-                V[u] -= dd << sh;
-                q[u] = (float)(int)dd * unit;
-            }
+            for (int u = 0; u < 4; ++u) q[u] = (float)dg[u][t] * unit;
             const __nv_bfloat162 p01 = __floats2bfloat162_rn(q[0], q[1]);
             const __nv_bfloat162 p23 = __floats2bfloat162_rn(q[2], q[3]);
             uint2 w;

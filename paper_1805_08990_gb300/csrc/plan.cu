@@ -131,9 +131,11 @@ dme_status cong64(int n, const double* P, const double* E, double* X, double* ou
 dme_status check_status(dme_plan_t p, const char* where) {
     DME_CUDA_TRY(cudaStreamSynchronize(p->st));
     int hs = 0;
-    DME_CUDA_TRY(cudaMemcpy(&hs, p->status, sizeof(int), cudaMemcpyDeviceToHost));
+    DME_CUDA_TRY(cudaMemcpyAsync(&hs, p->status, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+    DME_CUDA_TRY(cudaStreamSynchronize(p->st));
     if (hs) {
-        DME_CUDA_TRY(cudaMemset(p->status, 0, sizeof(int)));
+        DME_CUDA_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), p->st));
+        DME_CUDA_TRY(cudaStreamSynchronize(p->st));
         if (hs & DEV_NOTSPD) {
             set_error(std::string(where) + ": I_m + t Bt^T P Bt (or R) is not positive definite");
             return DME_ENOTSPD;

@@ -404,8 +404,14 @@ dme_status build_round_graph(dme_server_t s, std::vector<Req*>& res) {
     e = cudaGraphInstantiate(&s->round_exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return set_error(std::string("serving: graph instantiate: ") + cudaGetErrorString(e)), DME_ECUDA;
-    if (!s->arena.host.empty())
-        DME_CUDA_TRY(cudaMemcpy(s->arena.dev, s->arena.host.data(), s->arena.host.size(), cudaMemcpyHostToDevice));
+    // on the serving stream: the round's launches are ordered after the upload (a plain
+    // cudaMemcpy from pageable memory may return before its DMA lands, and the serving
+    // stream does not wait for the legacy stream it runs on)
+    if (!s->arena.host.empty()) {
+        DME_CUDA_TRY(cudaMemcpyAsync(s->arena.dev, s->arena.host.data(), s->arena.host.size(),
+                                     cudaMemcpyHostToDevice, s->st));
+        DME_CUDA_TRY(cudaStreamSynchronize(s->st));
+    }
     for (Req* r : res) s->round_ids.push_back(r->id);
     s->graph_builds++;
     return DME_OK;
@@ -505,7 +511,8 @@ dme_status dme_server_create(size_t hbm_budget_bytes, int max_slots, dme_server_
     for (int i = max_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
     cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&s->dstat, sizeof(int) * max_slots);
-    if (e == cudaSuccess) e = cudaMemset(s->dstat, 0, sizeof(int) * max_slots);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->dstat, 0, sizeof(int) * max_slots, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
     // descriptors of up to kMaxStages stages: two GEMM groups, two split-GEMM
     // groups and one Riccati group per stage, each put 256-byte aligned
     constexpr size_t kMaxStages = 8;
