@@ -26,9 +26,11 @@ dropped.  It is applied after every sub-flow that appends columns.
 
 Readings where the paper is silent: the quadrature is Gauss-Legendre with q
 nodes on [0, tau] (default q = 7); the truncation is relative to the largest
-eigenvalue of the compressed system with tol = 1e-13 by default; e^{s A^T} is
-the dense exponential of ``dme_oracle.expm`` (the paper applies it to L by
-Leja interpolation, which computes the same product up to its tolerance).
+eigenvalue of the compressed system with tol = 1e-13 by default.  e^{s A^T} L
+is either the dense exponential of ``dme_oracle.expm`` times L (action
+"dense") or, as in the paper, the Leja interpolation of ``dme_leja`` applied to
+L with A dense or sparse (action "leja"); the two agree to the interpolation's
+tolerance.
 """
 from __future__ import annotations
 
@@ -137,8 +139,11 @@ class LowRankPlan:
     """Problem data (A, Q = C^T C as L_Q = C^T, D_Q = I, B, R, S) and the per-tau
     caches of e^{tau A} and of the quadrature factor of W_tau."""
 
-    def __init__(self, A, C, B=None, R=None, S=None, q=7, tol=1e-13):
-        self.A = np.asarray(A, dtype=np.float64)
+    def __init__(self, A, C, B=None, R=None, S=None, q=7, tol=1e-13, action="dense"):
+        # action "dense": e^{tau A^T} L with the dense exponential; "leja": by
+        # Leja interpolation (dme_leja.leja_action), A dense or scipy sparse
+        self.action = action
+        self.A = A if (action == "leja" and hasattr(A, "tocsr")) else np.asarray(A, dtype=np.float64)
         C = np.asarray(C, dtype=np.float64)
         self.LQ = C.T.copy()
         self.DQ = np.eye(C.shape[0])
@@ -154,19 +159,40 @@ class LowRankPlan:
             self._E[key] = expm(key * self.A)
         return self._E[key]
 
+    def expAT(self, tau, L):
+        """e^{tau A^T} L (Eq. F_sol_LDL)."""
+        if self.action == "leja":
+            from .dme_leja import leja_action
+            return leja_action(self.A.T, L, tau) if L.shape[1] else L
+        return self.E(tau).T @ L
+
     def W(self, tau):
         key = float(tau)
         if key not in self._W:
-            self._W[key] = quadrature_factor(self.A, self.LQ, self.DQ, key, self.q, self.tol)
+            if self.action == "leja":
+                s, w = gauss_legendre(self.q, key)
+                p = self.DQ.shape[0]
+                LI = np.hstack([self.expAT(sk, self.LQ) for sk in s])
+                DI = np.zeros((self.q * p, self.q * p))
+                for k in range(self.q):
+                    DI[k * p:(k + 1) * p, k * p:(k + 1) * p] = w[k] * self.DQ
+                self._W[key] = compress(LI, DI, self.tol)
+            else:
+                self._W[key] = quadrature_factor(self.A, self.LQ, self.DQ, key, self.q, self.tol)
         return self._W[key]
 
     def apply(self, flow, tau, L, D, t4_rule="midpoint"):
         if flow == "F1":
-            return self.E(tau).T @ L, D
+            return self.expAT(tau, L), D
         if flow == "F2":
             return compress(*lr_T2(L, D, self.LQ, self.DQ, tau), self.tol)
         if flow == "F12":
-            return compress(*lr_T12(L, D, self.E(tau), *self.W(tau)), self.tol)
+            LI, DI = self.W(tau)
+            r, k = D.shape[0], DI.shape[0]
+            Dn = np.zeros((r + k, r + k))
+            Dn[:r, :r] = D
+            Dn[r:, r:] = DI
+            return compress(np.hstack([self.expAT(tau, L), LI]), Dn, self.tol)
         if flow == "F3":
             return lr_T3(L, D, self.B, self.R, tau)
         if flow == "F4":
@@ -181,11 +207,11 @@ class LowRankPlan:
 
 
 def solve_lowrank(A, C, L0, D0, T, nsteps, comp="strang", flows=("F1", "F2"), B=None, R=None, S=None,
-                  q=7, tol=1e-13, t4_rule=None, plan: LowRankPlan | None = None):
+                  q=7, tol=1e-13, t4_rule=None, plan: LowRankPlan | None = None, action="dense"):
     """(L, D) with L D L^T ~ P(T) after N = nsteps steps of the composition on
     the factors (Alg. 1-4), h = T/N, P_0 = L0 D0 L0^T."""
-    plan = plan or LowRankPlan(A, C, B, R, S, q, tol)
-    L = np.array(L0, dtype=np.float64, copy=True).reshape(np.asarray(A).shape[0], -1)
+    plan = plan or LowRankPlan(A, C, B, R, S, q, tol, action)
+    L = np.array(L0, dtype=np.float64, copy=True).reshape(A.shape[0], -1)
     D = np.array(D0, dtype=np.float64, copy=True).reshape(L.shape[1], L.shape[1])
     h = T / nsteps
     for _ in range(nsteps):

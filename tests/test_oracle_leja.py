@@ -1,0 +1,86 @@
+"""Pins of the Leja-interpolation oracle (the exponential's action on a block
+of vectors) against closed forms, scipy's dense exponential and sparse
+expm_multiply, eigenvalues, and the dense low-rank path.  CPU only."""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spl
+
+import dme_workloads as W
+import oracle as O
+
+
+def test_first_leja_points():
+    x = O.leja_points(5)
+    assert list(x[:3]) == [2.0, -2.0, 0.0]
+    # the fourth maximises |x - 2| |x + 2| |x| = |x (4 - x^2)|: x = +-2/sqrt(3)
+    assert abs(abs(x[3]) - 2 / math.sqrt(3)) < 4.0 / 20000
+    assert len(set(np.round(x, 12))) == 5
+
+
+def test_divided_differences_closed_forms():
+    for scale in (0.3, 1.0, 3.0):
+        x = np.array([0.5, -1.2])
+        dd = O.divided_differences_exp(x, scale)
+        assert abs(dd[0] - math.exp(scale * 0.5)) < 1e-15 * math.exp(scale * 0.5)
+        ref = (math.exp(scale * -1.2) - math.exp(scale * 0.5)) / (-1.2 - 0.5)
+        assert abs(dd[1] - ref) < 1e-14 * abs(ref)
+    # confluent limit: all points equal -> scale^k e^{scale x} / k!
+    dd = O.divided_differences_exp(np.full(6, 0.7), 2.0)
+    ref = [2.0 ** k * math.exp(1.4) / math.factorial(k) for k in range(6)]
+    assert np.allclose(dd, ref, rtol=1e-13)
+
+
+def test_gershgorin_interval_contains_the_spectrum():
+    pr = W.dre_convdiff(nx=6)
+    a, b = O.gershgorin_interval(pr.A)
+    ev = np.linalg.eigvals(pr.A)
+    assert np.all(ev.real >= a - 1e-9) and np.all(ev.real <= b + 1e-9)
+
+
+@pytest.mark.parametrize("tau", [1e-3, 1 / 64, 0.25])
+def test_leja_action_matches_dense_exponential(tau):
+    pr = W.dre_convdiff(nx=10)
+    V = np.random.default_rng(0).standard_normal((pr.n, 5))
+    ref = sla.expm(tau * pr.A.T) @ V
+    got = O.leja_action(pr.A.T, V, tau)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-12
+
+
+def test_leja_action_sparse_matches_expm_multiply():
+    pr = W.dle_heat(nx=40)
+    A = sp.csr_matrix(pr.A)
+    V = np.random.default_rng(1).standard_normal((pr.n, 3))
+    ref = spl.expm_multiply((1 / 512) * A.tocsc(), V)
+    got = O.leja_action(A, V, 1 / 512)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-12
+
+
+def test_lowrank_with_leja_action_equals_dense_lowrank():
+    pr = W.dre_convdiff(nx=8, m=2, p=3)
+    n = pr.n
+    for flows in (["F1", "F2", "F3"], ["F12", "F3"]):
+        L1, D1 = O.solve_lowrank(pr.A, pr.C, np.zeros((n, 0)), np.zeros((0, 0)), pr.T, 6, "strang", flows,
+                                 B=pr.B, R=pr.R, tol=1e-15)
+        L2, D2 = O.solve_lowrank(sp.csr_matrix(pr.A), pr.C, np.zeros((n, 0)), np.zeros((0, 0)), pr.T, 6, "strang",
+                                 flows, B=pr.B, R=pr.R, tol=1e-15, action="leja")
+        assert O.rel_fro(O.ldl_product(L2, D2), O.ldl_product(L1, D1)) < 1e-12
+
+
+def test_pin_catches_unscaled_divided_differences(monkeypatch):
+    import oracle.dme_leja as lj
+
+    def unscaled(x, scale=1.0):          # the slip: ones below the diagonal not scaled
+        m = len(x)
+        Z = np.diag(scale * np.asarray(x)) + np.diag(np.ones(m - 1), -1)
+        return O.expm(Z)[:, 0].copy()
+
+    monkeypatch.setattr(lj, "divided_differences_exp", unscaled)
+    pr = W.dre_convdiff(nx=10)
+    V = np.random.default_rng(0).standard_normal((pr.n, 5))
+    ref = sla.expm(pr.A.T / 64) @ V
+    got = O.leja_action(pr.A.T, V, 1 / 64)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) > 1e-3
