@@ -11,7 +11,7 @@ from .binding import (  # noqa: F401
     DME_KIND_SPLIT_GEMM, DME_KIND_SLICE, DME_KIND_FP64_GEMM, DME_KIND_RICCATI, dme_plan_profile, dme_plan_timing,
     DME_OK, DME_EINVAL, DME_ENOMEM, DME_ENOTSPD, DME_ECUDA, DME_ETIMEOUT, DME_EBUSY, DME_ENOTREADY,
     DmeError, LibraryNotBuilt, dme_plan_desc, make_desc, lib, header_functions,
-    dme_plan, dme_plan_mass, dme_lr_plan, dme_lr_solve, dme_lr_factors, dme_lr_destroy, dme_expm, dme_apply, dme_apply_async, dme_sync, dme_plan_kernels_per_step, dme_step, dme_solve, dme_plan_bytes, dme_plan_destroy, dme_gain,
+    dme_plan, dme_plan_mass, dme_lr_plan, dme_lr_plan_csr, dme_lr_solve, dme_lr_factors, dme_lr_destroy, dme_expm, dme_apply, dme_apply_async, dme_sync, dme_plan_kernels_per_step, dme_step, dme_solve, dme_plan_bytes, dme_plan_destroy, dme_gain,
     dme_server_create, dme_submit, dme_poll, dme_server_stats, dme_server_destroy, dme_last_error,
     dme_gemm_split, dme_gemm_split_noalloc,
 )
@@ -110,6 +110,22 @@ class LowRankPlan:
         self.desc = make_desc(n, m=m, p=int(C.shape[0]), eq=EQ_IDS[eq], comp=comp, flows=flows, prec=prec, h=h,
                               q_is_factor=True, t4_rule=t4_rule)
         self.handle = dme_lr_plan(self.desc, A, C, B, R, S, quad_nodes, rmax, tol, stream)
+
+    @classmethod
+    def from_csr(cls, A_csr, C, h=1e-3, flows=("F1", "F2"), comp="strang", B=None, R=None, quad_nodes=0, rmax=0,
+                 tol=0.0, stream=None):
+        """The factored path for a sparse A (scipy.sparse matrix or anything with
+        indptr / indices / data): e^{t A^T} L by Leja interpolation."""
+        self = cls.__new__(cls)
+        A_csr = A_csr.tocsr() if hasattr(A_csr, "tocsr") else A_csr
+        n = int(A_csr.shape[0])
+        m = 0 if B is None else int(B.shape[1])
+        self.n, self.m = n, m
+        self.desc = make_desc(n, m=m, p=int(C.shape[0]), eq=DME_DRE if B is not None else DME_DLE, comp=comp,
+                              flows=flows, prec="fp64", h=h, q_is_factor=True)
+        self.handle = dme_lr_plan_csr(self.desc, A_csr.indptr, A_csr.indices, A_csr.data, C, B, R, quad_nodes, rmax,
+                                      tol, stream)
+        return self
 
     def solve(self, T, nsteps, L0=None, D0=None, P_out=None):
         r0 = 0 if L0 is None else int(L0.shape[1])

@@ -65,6 +65,9 @@ _SIGS = {
     "dme_expm": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
     "dme_lr_plan": (C.c_int, [C.POINTER(dme_plan_desc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                               C.c_void_p, C.POINTER(dme_lr_opts), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "dme_lr_plan_csr": (C.c_int, [C.POINTER(dme_plan_desc), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(dme_lr_opts), C.c_void_p,
+                                  C.POINTER(C.c_void_p)]),
     "dme_lr_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p,
                                C.POINTER(C.c_int)]),
     "dme_lr_factors": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
@@ -191,6 +194,36 @@ def dme_lr_plan(desc: dme_plan_desc, A, C_factor, B=None, R=None, S=None, quad_n
     st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     _check(lib().dme_lr_plan(C.byref(desc), _ptr(A, keep), _ptr(C_factor, keep), _ptr(B, keep), _ptr(R, keep),
                              _ptr(S, keep), C.byref(opts), st, C.byref(out)), "dme_lr_plan")
+    return out.value
+
+
+def _iptr(x, keep: list):
+    """Raw pointer of an int32 C-contiguous array (torch tensor or numpy array)."""
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if x.dtype != torch.int32 or not x.is_contiguous():
+                x = x.to(torch.int32).contiguous()
+            keep.append(x)
+            return x.data_ptr()
+    except ImportError:
+        pass
+    import numpy as np
+    a = np.ascontiguousarray(x, dtype=np.int32)
+    keep.append(a)
+    return a.ctypes.data
+
+
+def dme_lr_plan_csr(desc: dme_plan_desc, indptr, indices, data, C_factor, B=None, R=None, quad_nodes=0, rmax=0,
+                    tol=0.0, stream=None) -> int:
+    keep: list = []
+    out = C.c_void_p()
+    opts = dme_lr_opts(int(quad_nodes), int(rmax), float(tol))
+    st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    nnz = int(len(data))
+    _check(lib().dme_lr_plan_csr(C.byref(desc), nnz, _iptr(indptr, keep), _iptr(indices, keep) if nnz else None,
+                                 _ptr(data, keep) if nnz else None, _ptr(C_factor, keep), _ptr(B, keep),
+                                 _ptr(R, keep), C.byref(opts), st, C.byref(out)), "dme_lr_plan_csr")
     return out.value
 
 

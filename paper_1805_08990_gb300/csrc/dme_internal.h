@@ -125,6 +125,14 @@ void launch_fill(double* x, int k, double v, cudaStream_t st);
 void launch_splitk_reduce(const double* W, int S, int M, int N, double* C, int ldc, double alpha, const double* D1,
                           double b1, int tri, cudaStream_t st);
 
+// One term of the Leja-interpolation series for e^{t A^T} on an n x r block
+// (A^T in CSR): Wn = (A^T W - c W) invg - xk W, Pacc += dk Wn; norms2[0..1] =
+// |Wn|_F^2, |Pacc|_F^2 (part: 2 leja_blocks(n) doubles of scratch).
+int leja_blocks(int n);
+void launch_leja_term(const int* ptr, const int* idx, const double* val, int n, int r, const double* W, double* Wn,
+                      int ldw, double* Pacc, int ldp, double c, double invg, double xk, double dk, double* part,
+                      double* norms2, cudaStream_t st);
+
 // ---------------------------------------------------------------- Riccati (T3)
 // P <- P - t Z (I + t Bt^T Z)^{-1} Z^T + q * Qadd, Z = P Bt  (Woodbury form
 // of (I + t P Bt Bt^T)^{-1} P).  Work buffers sized by riccati_work_doubles.

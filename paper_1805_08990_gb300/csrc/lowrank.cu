@@ -39,8 +39,30 @@ struct WFactor {
 
 }  // namespace
 
+struct LejaTab {          // e^{tau A^T} by Leja interpolation: per step length tau
+    double tau;
+    int s;                   // substeps
+    double scale;            // e^{t c}, t = tau / s
+    std::vector<double> dd;  // divided differences of exp(t g x) at the Leja points
+};
+
 struct dme_lr_s {
-    dme_plan_t P = nullptr;   // dense FP64 plan (data, E_t, stream, status)
+    dme_plan_t P = nullptr;   // dense plan (data, E_t); NULL for a sparse A
+    dme_plan_desc desc;       // the descriptor
+    cudaStream_t st = nullptr;
+    bool own_st = false;
+    int* status = nullptr;    // device status word (the dense plan's, or own)
+    const double* Bt = nullptr;   // B L_R^{-T} (n x m)
+    // sparse A: A^T in CSR (device), Gershgorin data and Leja tables
+    bool sparse = false;
+    int nnz = 0;
+    int *at_ptr = nullptr, *at_idx = nullptr;
+    double* at_val = nullptr;
+    double lc = 0.0, lg = 0.0;       // A^T = lc I + lg X, spectrum of X in [-2, 2] (Gershgorin)
+    std::vector<double> xi;          // Leja points
+    std::vector<LejaTab> ltab;
+    double *Wa = nullptr, *Wb = nullptr;   // Leja work (n x rcap)
+    double *lpart = nullptr, *lnorm = nullptr;  // per-block partial norms, per-term norms
     int n = 0, m = 0, p = 0, rcap = 0, q = 7;
     double tol = 1e-13;
     double *L = nullptr, *L2 = nullptr, *d = nullptr, *d2 = nullptr;   // n x rcap, rcap
@@ -140,11 +162,11 @@ dme_status gemm_ws(dme_lr_t lr, const GemmProb& g, cudaStream_t st) {
 // L2 is an n x ld work buffer.  Reads the new rank back to the host.
 dme_status compress(dme_lr_t lr, double* L, double* L2, double* d, int ld, int& r) {
     if (r == 0) return DME_OK;
-    cudaStream_t st = lr->P->st;
+    cudaStream_t st = lr->st;
     const int n = lr->n;
     launch_copy_cols(L2, ld, L, ld, n, r, 1.0, d, st);                                     // Lt = L d^{1/2}
     DME_TRY(gemm(lr, mk(r, r, n, L2, ld, 1, L2, ld, 0, lr->G, lr->rcap, 1.0, 1), st));          // Lt^T Lt
-    DME_TRY(launch_jacobi_eig(lr->G, lr->rcap, r, lr->Vt, lr->rcap, lr->lam, lr->P->status, st));
+    DME_TRY(launch_jacobi_eig(lr->G, lr->rcap, r, lr->Vt, lr->rcap, lr->lam, lr->status, st));
     launch_lr_select(lr->lam, lr->Vt, lr->rcap, r, lr->tol, 1, lr->T, lr->rcap, d, lr->kdev, st);
     int k = 0;
     DME_CUDA_TRY(cudaMemcpyAsync(&k, lr->kdev, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -204,13 +226,139 @@ void gauss_legendre(int q, double t, std::vector<double>& s, std::vector<double>
     }
 }
 
+// ---------------------------------------------------------------- Leja action (sparse A)
+constexpr int kLejaTerms = 80;        // interpolation points per substep
+constexpr double kLejaRho = 4.0;      // largest t g per substep
+constexpr double kLejaTol = 1e-15;    // series stops after two terms below tol |p|
+constexpr int kLejaGrid = 20001;      // candidate points for the greedy Leja sequence
+
+// Leja points of [-2, 2] from 2: x_k maximises prod_{i<k} |x - x_i| over a grid.
+std::vector<double> leja_points_host(int m) {
+    std::vector<double> xs(kLejaGrid), lp(kLejaGrid);
+    const double step = 4.0 / (kLejaGrid - 1);
+    for (int i = 0; i < kLejaGrid; ++i) {
+        xs[i] = -2.0 + i * step;
+        lp[i] = std::log(std::fabs(xs[i] - 2.0));
+    }
+    std::vector<double> pts{2.0};
+    for (int k = 1; k < m; ++k) {
+        int best = 0;
+        for (int i = 1; i < kLejaGrid; ++i)
+            if (lp[i] > lp[best]) best = i;
+        pts.push_back(xs[best]);
+        for (int i = 0; i < kLejaGrid; ++i) lp[i] += std::log(std::fabs(xs[i] - xs[best]));
+    }
+    return pts;
+}
+
+// First column of exp(a Z), Z lower bidiagonal with x on the diagonal and ones
+// below: the divided differences of exp(a x) at x_0, x_1, ... (Opitz).  Taylor
+// series of degree 30 after scaling to 1-norm <= 1/2, then repeated squaring
+// (lower-triangular products).
+std::vector<double> dd_exp_host(const std::vector<double>& x, double a) {
+    const int m = (int)x.size();
+    std::vector<double> M((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i) {
+        M[(size_t)i * m + i] = a * x[i];
+        if (i > 0) M[(size_t)i * m + i - 1] = a;
+    }
+    double nrm = 0.0;
+    for (int j = 0; j < m; ++j) nrm = std::max(nrm, std::fabs(M[(size_t)j * m + j]) + (j + 1 < m ? std::fabs(a) : 0.0));
+    int sq = 0;
+    while (nrm > 0.5) {
+        nrm *= 0.5;
+        ++sq;
+    }
+    const double f = std::ldexp(1.0, -sq);
+    for (double& v : M) v *= f;
+    auto mul = [m](const std::vector<double>& X, const std::vector<double>& Y) {
+        std::vector<double> Zm((size_t)m * m, 0.0);
+        for (int i = 0; i < m; ++i)
+            for (int k = 0; k <= i; ++k) {
+                const double xv = X[(size_t)i * m + k];
+                if (xv == 0.0) continue;
+                for (int j = 0; j <= k; ++j) Zm[(size_t)i * m + j] += xv * Y[(size_t)k * m + j];
+            }
+        return Zm;
+    };
+    std::vector<double> E((size_t)m * m, 0.0), T((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i) E[(size_t)i * m + i] = T[(size_t)i * m + i] = 1.0;
+    for (int k = 1; k <= 30; ++k) {
+        T = mul(T, M);
+        for (double& v : T) v /= k;
+        for (size_t e = 0; e < E.size(); ++e) E[e] += T[e];
+    }
+    for (int i = 0; i < sq; ++i) E = mul(E, E);
+    std::vector<double> col(m);
+    for (int i = 0; i < m; ++i) col[i] = E[(size_t)i * m];
+    return col;
+}
+
+const LejaTab& leja_table(dme_lr_t lr, double tau) {
+    for (auto& t : lr->ltab)
+        if (t.tau == tau) return t;
+    LejaTab t;
+    t.tau = tau;
+    t.s = std::max(1, (int)std::ceil(tau * lr->lg / kLejaRho));
+    const double sub = tau / t.s;
+    t.scale = std::exp(sub * lr->lc);
+    t.dd = dd_exp_host(lr->xi, sub * lr->lg);
+    lr->ltab.push_back(t);
+    return lr->ltab.back();
+}
+
+// Y (n x k, ldy) = e^{tau A^T} X (n x k, ldx) by Leja interpolation; Y may be X.
+dme_status leja_apply(dme_lr_t lr, const double* X, int ldx, int k, double* Y, int ldy, double tau) {
+    if (k == 0) return DME_OK;
+    cudaStream_t st = lr->st;
+    const int n = lr->n, rc = lr->rcap;
+    if (!(lr->lg > 0.0)) {                              // A = c I
+        launch_copy_cols(Y, ldy, X, ldx, n, k, std::exp(tau * lr->lc), nullptr, st);
+        return DME_OK;
+    }
+    const LejaTab& tb = leja_table(lr, tau);
+    const double invg = 1.0 / lr->lg;
+    launch_copy_cols(lr->Wa, rc, X, ldx, n, k, 1.0, nullptr, st);
+    std::vector<double> h(16);
+    for (int sub = 0; sub < tb.s; ++sub) {
+        launch_copy_cols(Y, ldy, lr->Wa, rc, n, k, tb.dd[0], nullptr, st);   // p = d_0 v
+        double* W = lr->Wa;
+        double* Wn = lr->Wb;
+        int small = 0;
+        bool done = false;
+        for (int base = 1; base < kLejaTerms && !done; base += 8) {
+            const int cnt = std::min(8, kLejaTerms - base);
+            for (int j = 0; j < cnt; ++j) {
+                const int kk = base + j;
+                launch_leja_term(lr->at_ptr, lr->at_idx, lr->at_val, n, k, W, Wn, rc, Y, ldy, lr->lc, invg,
+                                 lr->xi[kk - 1], tb.dd[kk], lr->lpart, lr->lnorm + 2 * j, st);
+                std::swap(W, Wn);
+            }
+            DME_CUDA_TRY(cudaMemcpyAsync(h.data(), lr->lnorm, sizeof(double) * 2 * cnt, cudaMemcpyDeviceToHost, st));
+            DME_CUDA_TRY(cudaStreamSynchronize(st));
+            for (int j = 0; j < cnt && !done; ++j) {
+                const double term = std::fabs(tb.dd[base + j]) * std::sqrt(h[2 * j]);
+                if (term <= kLejaTol * std::sqrt(h[2 * j + 1])) {
+                    if (++small == 2) done = true;
+                } else {
+                    small = 0;
+                }
+            }
+        }
+        if (sub + 1 < tb.s) launch_copy_cols(lr->Wa, rc, Y, ldy, n, k, tb.scale, nullptr, st);   // next v
+        else launch_copy_cols(Y, ldy, Y, ldy, n, k, tb.scale, nullptr, st);
+    }
+    DME_CUDA_TRY(cudaGetLastError());
+    return DME_OK;
+}
+
 dme_status wfactor(dme_lr_t lr, double tau, const WFactor** out) {
     for (auto& f : lr->wf)
         if (f.tau == tau) {
             *out = &f;
             return DME_OK;
         }
-    cudaStream_t st = lr->P->st;
+    cudaStream_t st = lr->st;
     const int n = lr->n, p = lr->p, q = lr->q, k0 = q * p;
     DME_TRY(need_cols(lr, k0));
     std::vector<double> s, w;
@@ -238,10 +386,14 @@ dme_status wfactor(dme_lr_t lr, double tau, const WFactor** out) {
     DME_TRY(tmp.get(&WL2, (size_t)n * lr->rcap));
     DME_TRY(tmp.get(&wd, (size_t)lr->rcap));
     for (int k = 0; k < q; ++k) {
-        int idx;
-        DME_TRY(plan_ew(lr->P, s[k], &idx));
-        const double* E = lr->P->ew[idx].E;
-        DME_TRY(gemm(lr, mk(n, p, n, E, n, 1, lr->LQ, p, 0, WL + (size_t)k * p, lr->rcap, 1.0), st));   // E_s^T C^T
+        if (lr->sparse) {
+            DME_TRY(leja_apply(lr, lr->LQ, p, p, WL + (size_t)k * p, lr->rcap, s[k]));                 // e^{s A^T} C^T
+        } else {
+            int idx;
+            DME_TRY(plan_ew(lr->P, s[k], &idx));
+            const double* E = lr->P->ew[idx].E;
+            DME_TRY(gemm(lr, mk(n, p, n, E, n, 1, lr->LQ, p, 0, WL + (size_t)k * p, lr->rcap, 1.0), st));   // E_s^T C^T
+        }
         launch_fill(wd + (size_t)k * p, p, w[k], st);
     }
     int r = k0;
@@ -265,7 +417,7 @@ dme_status wfactor(dme_lr_t lr, double tau, const WFactor** out) {
 dme_status apply_split(dme_lr_t lr, const SliceBuf& Msl, const double* X, int ldx, int k, double* C, int ldc,
                        double alpha) {
     if (k == 0) return DME_OK;
-    cudaStream_t st = lr->P->st;
+    cudaStream_t st = lr->st;
     const int n = lr->n;
     launch_transpose(X, lr->Xtr, n, k, ldx, n, st);
     launch_slice_rows_f64(lr->Xtr, k, n, n, lr->xsl, st);
@@ -280,7 +432,7 @@ dme_status apply_split(dme_lr_t lr, const SliceBuf& Msl, const double* X, int ld
     p.ldc = ldc;
     p.Cd = C;
     p.alpha = alpha;
-    p.status = lr->P->status;
+    p.status = lr->status;
     p.ws = lr->P->kws;
     p.ws_cnt = lr->P->kcnt;
     return launch_ozaki_gemm(Msl.tmap, lr->xsl.tmap, p, st);
@@ -288,6 +440,11 @@ dme_status apply_split(dme_lr_t lr, const SliceBuf& Msl, const double* X, int ld
 
 dme_status lr_T1(dme_lr_t lr, double tau) {
     if (lr->r == 0) return DME_OK;
+    if (lr->sparse) {
+        DME_TRY(leja_apply(lr, lr->L, lr->rcap, lr->r, lr->L2, lr->rcap, tau));
+        std::swap(lr->L, lr->L2);
+        return DME_OK;
+    }
     int idx;
     DME_TRY(plan_ew(lr->P, tau, &idx));
     const EWEntry& e = lr->P->ew[idx];
@@ -295,14 +452,14 @@ dme_status lr_T1(dme_lr_t lr, double tau) {
         DME_TRY(apply_split(lr, e.Gsl, lr->L, lr->rcap, lr->r, lr->L2, lr->rcap, 1.0));
     else
         DME_TRY(gemm(lr, mk(lr->n, lr->r, lr->n, e.E, lr->n, 1, lr->L, lr->rcap, 0, lr->L2, lr->rcap, 1.0),
-                     lr->P->st));
+                     lr->st));
     std::swap(lr->L, lr->L2);
     return DME_OK;
 }
 
 dme_status lr_append(dme_lr_t lr, const double* X, int ldx, int k, const double* dsrc, double dval) {
     DME_TRY(need_cols(lr, lr->r + k));
-    cudaStream_t st = lr->P->st;
+    cudaStream_t st = lr->st;
     launch_copy_cols(lr->L + lr->r, lr->rcap, X, ldx, lr->n, k, 1.0, nullptr, st);
     if (dsrc) DME_CUDA_TRY(cudaMemcpyAsync(lr->d + lr->r, dsrc, sizeof(double) * k, cudaMemcpyDeviceToDevice, st));
     else launch_fill(lr->d + lr->r, k, dval, st);
@@ -325,12 +482,12 @@ dme_status lr_T12(dme_lr_t lr, double tau) {
 
 dme_status lr_T3(dme_lr_t lr, double tau) {
     if (lr->r == 0) return DME_OK;
-    cudaStream_t st = lr->P->st;
+    cudaStream_t st = lr->st;
     const int n = lr->n, m = lr->m, r = lr->r, rc = lr->rcap;
     launch_copy_cols(lr->L2, rc, lr->L, rc, n, r, 1.0, lr->d, st);                              // Lt
-    DME_TRY(gemm(lr, mk(r, m, n, lr->L2, rc, 1, lr->P->Bt, m, 0, lr->Gm, m, 1.0), st));              // G = Lt^T Bt
+    DME_TRY(gemm(lr, mk(r, m, n, lr->L2, rc, 1, lr->Bt, m, 0, lr->Gm, m, 1.0), st));              // G = Lt^T Bt
     DME_TRY(gemm(lr, mk(m, m, r, lr->Gm, m, 1, lr->Gm, m, 0, lr->H, m, 1.0, 1), st));                // G^T G
-    DME_TRY(launch_jacobi_eig(lr->H, m, m, lr->VtH, m, lr->lamH, lr->P->status, st));
+    DME_TRY(launch_jacobi_eig(lr->H, m, m, lr->VtH, m, lr->lamH, lr->status, st));
     launch_ric_weights(lr->lamH, lr->VtH, m, m, tau, lr->F, m, st);                               // F(G^T G)
     DME_TRY(gemm(lr, mk(r, m, m, lr->Gm, m, 0, lr->F, m, 0, lr->Y, m, 1.0), st));                    // Y = G F
     DME_TRY(gemm(lr, mk(n, m, r, lr->L2, rc, 0, lr->Gm, m, 0, lr->Z, m, 1.0), st));                  // Z = Lt G
@@ -341,7 +498,7 @@ dme_status lr_T3(dme_lr_t lr, double tau) {
 
 dme_status lr_T4(dme_lr_t lr, double tau, int rule) {
     if (lr->r == 0) return DME_OK;
-    cudaStream_t st = lr->P->st;
+    cudaStream_t st = lr->st;
     const int n = lr->n, r = lr->r, rc = lr->rcap;
     const int blocks = rule == DME_T4_EULER ? 2 : 3;
     DME_TRY(need_cols(lr, blocks * r));
@@ -371,7 +528,7 @@ dme_status lr_apply(dme_lr_t lr, int flow, double tau) {
         case DME_F2: return lr_T2(lr, tau);
         case DME_F12: return lr_T12(lr, tau);
         case DME_F3: return lr_T3(lr, tau);
-        case DME_F4: return lr_T4(lr, tau, t4_rule(lr->P->d));
+        case DME_F4: return lr_T4(lr, tau, t4_rule(lr->desc));
     }
     set_error("low-rank path: unknown flow");
     return DME_EINVAL;
@@ -379,10 +536,24 @@ dme_status lr_apply(dme_lr_t lr, int flow, double tau) {
 
 void lr_free(dme_lr_t lr) {
     if (!lr) return;
-    if (lr->P) cudaStreamSynchronize(lr->P->st);
+    if (lr->st) cudaStreamSynchronize(lr->st);
     for (void* q : lr->allocs) cudaFree(q);
     if (lr->P) free_plan(lr->P);
+    if (lr->own_st && lr->st) cudaStreamDestroy(lr->st);
     delete lr;
+}
+
+// Report and clear the device status word (synchronises the stream).
+dme_status lr_check(dme_lr_t lr, const char* where) {
+    if (lr->P) return plan_check(lr->P, where);
+    int hs = 0;
+    DME_CUDA_TRY(cudaMemcpyAsync(&hs, lr->status, sizeof(int), cudaMemcpyDeviceToHost, lr->st));
+    DME_CUDA_TRY(cudaStreamSynchronize(lr->st));
+    if (!hs) return DME_OK;
+    DME_CUDA_TRY(cudaMemsetAsync(lr->status, 0, sizeof(int), lr->st));
+    DME_CUDA_TRY(cudaStreamSynchronize(lr->st));
+    if (hs & DEV_NOTSPD) return set_error(std::string(where) + ": R is not positive definite"), DME_ENOTSPD;
+    return set_error(std::string(where) + ": device status " + std::to_string(hs)), DME_ECUDA;
 }
 
 template <typename F>
@@ -402,6 +573,83 @@ dme_status guarded(F&& f) {
 
 extern "C" {
 
+}  // extern "C"
+
+namespace {
+
+dme_status lr_opts(const dme_lr_opts* opts, int* q, int* rmax, double* tol) {
+    *q = opts && opts->quad_nodes > 0 ? opts->quad_nodes : 7;
+    *rmax = opts && opts->rmax > 0 ? opts->rmax : LR_MAX_RANK;
+    *tol = opts && opts->tol > 0.0 ? opts->tol : 1e-13;
+    if (*q > 64 || *rmax > LR_MAX_RANK || !(*tol < 1.0))
+        return set_error("low-rank path: need quad_nodes <= 64, rmax <= 224, tol < 1"), DME_EINVAL;
+    return DME_OK;
+}
+
+// Buffers shared by the dense and the sparse forms, and L_Q = C^T.
+dme_status lr_setup(dme_lr_t lr, const dme_plan_desc* desc, const double* C, int q, int rmax, double tol) {
+    lr->desc = *desc;
+    lr->n = desc->n;
+    lr->m = desc->m;
+    lr->p = desc->p;
+    lr->q = q;
+    lr->rcap = rmax;
+    lr->tol = tol;
+    const size_t n = desc->n, rc = rmax, m = std::max(desc->m, 1);
+    cudaStream_t st = lr->st;
+    DME_TRY(lr_alloc(lr, &lr->L, n * rc));
+    DME_TRY(lr_alloc(lr, &lr->L2, n * rc));
+    DME_TRY(lr_alloc(lr, &lr->d, rc));
+    DME_TRY(lr_alloc(lr, &lr->d2, rc));
+    DME_TRY(lr_alloc(lr, &lr->LQ, n * desc->p));
+    DME_TRY(lr_alloc(lr, &lr->G, rc * rc));
+    DME_TRY(lr_alloc(lr, &lr->Vt, rc * rc));
+    DME_TRY(lr_alloc(lr, &lr->lam, rc));
+    DME_TRY(lr_alloc(lr, &lr->T, rc * rc));
+    DME_TRY(lr_alloc(lr, &lr->Gm, rc * m));
+    DME_TRY(lr_alloc(lr, &lr->H, m * m));
+    DME_TRY(lr_alloc(lr, &lr->VtH, m * m));
+    DME_TRY(lr_alloc(lr, &lr->lamH, m));
+    DME_TRY(lr_alloc(lr, &lr->F, m * m));
+    DME_TRY(lr_alloc(lr, &lr->Y, rc * m));
+    DME_TRY(lr_alloc(lr, &lr->Z, n * m));
+    lr->ws_doubles = std::max<size_t>((size_t)8 * rc * rc, (size_t)kSplitMax * rc * m);
+    DME_TRY(lr_alloc(lr, &lr->ws, lr->ws_doubles));
+    double* wd = nullptr;
+    DME_TRY(lr_alloc(lr, &wd, (sizeof(GemmProb) * kSplitMax + 7) / 8));
+    lr->wsdesc = reinterpret_cast<GemmProb*>(wd);
+    lr->split = desc->prec == DME_SPLIT_BF16;
+    if (lr->split) {
+        DME_TRY(lr_alloc(lr, &lr->Xtr, rc * n));
+        lr->xsl.rows = (int)rc;
+        lr->xsl.k = (int)n;
+        lr->xsl.Kp = slice_kpad((int)n);
+        lr->xsl.ns = OZ_SLICES_B;
+        double* xd = nullptr;
+        DME_TRY(lr_alloc(lr, &xd, (slice_buf_bytes((int)rc, (int)n, OZ_SLICES_B) + 7) / 8));
+        lr->xsl.data = reinterpret_cast<__nv_bfloat16*>(xd);
+        double* xs = nullptr;
+        DME_TRY(lr_alloc(lr, &xs, (rc + 1) / 2));
+        lr->xsl.scale = reinterpret_cast<float*>(xs);
+        DME_CUDA_TRY(cudaMemsetAsync(xd, 0, slice_buf_bytes((int)rc, (int)n, OZ_SLICES_B), st));
+        DME_CUDA_TRY(cudaMemsetAsync(xs, 0, sizeof(float) * rc, st));
+        DME_TRY(make_slice_tmap(lr->xsl, &lr->xsl.tmap));
+    }
+    double* kd = nullptr;
+    DME_TRY(lr_alloc(lr, &kd, 1));
+    lr->kdev = reinterpret_cast<int*>(kd);
+    double* Cd = nullptr;
+    DME_TRY(lr_alloc(lr, &Cd, (size_t)desc->p * n));
+    DME_CUDA_TRY(cudaMemcpyAsync(Cd, C, sizeof(double) * desc->p * n, cudaMemcpyDefault, st));
+    launch_transpose(Cd, lr->LQ, desc->p, (int)n, (int)n, desc->p, st);
+    DME_CUDA_TRY(cudaStreamSynchronize(st));
+    return DME_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 dme_status dme_lr_plan(const dme_plan_desc* desc, const double* A, const double* C, const double* B, const double* R,
                        const double* S, const dme_lr_opts* opts, void* cuda_stream, dme_lr_t* out) {
     if (!out) return set_error("out is NULL"), DME_EINVAL;
@@ -412,72 +660,140 @@ dme_status dme_lr_plan(const dme_plan_desc* desc, const double* A, const double*
     if (desc->prec != DME_FP64 && desc->prec != DME_SPLIT_BF16)
         return set_error("low-rank path: prec must be DME_FP64 or DME_SPLIT_BF16"), DME_EINVAL;
     if (desc->fsal || desc->extrap > 1) return set_error("low-rank path: no fsal / extrapolation"), DME_EINVAL;
-    const int q = opts && opts->quad_nodes > 0 ? opts->quad_nodes : 7;
-    const int rmax = opts && opts->rmax > 0 ? opts->rmax : LR_MAX_RANK;
-    const double tol = opts && opts->tol > 0.0 ? opts->tol : 1e-13;
-    if (q > 64 || rmax > LR_MAX_RANK || !(tol < 1.0))
-        return set_error("low-rank path: need quad_nodes <= 64, rmax <= 224, tol < 1"), DME_EINVAL;
+    int q, rmax;
+    double tol;
+    DME_TRY(lr_opts(opts, &q, &rmax, &tol));
     if (desc->p > rmax) return set_error("low-rank path: p exceeds rmax"), DME_EINVAL;
     DME_TRY(plan_validate(desc, A, C, B, R, S));
     return guarded([&]() -> dme_status {
         std::unique_ptr<dme_lr_s, void (*)(dme_lr_t)> lr(new dme_lr_s(), lr_free);
         DME_TRY(plan_create(desc, A, C, B, R, S, cuda_stream, &lr->P));
-        lr->n = desc->n;
-        lr->m = desc->m;
-        lr->p = desc->p;
-        lr->q = q;
-        lr->rcap = rmax;
-        lr->tol = tol;
-        const size_t n = desc->n, rc = rmax, m = std::max(desc->m, 1);
-        cudaStream_t st = lr->P->st;
-        DME_TRY(lr_alloc(lr.get(), &lr->L, n * rc));
-        DME_TRY(lr_alloc(lr.get(), &lr->L2, n * rc));
-        DME_TRY(lr_alloc(lr.get(), &lr->d, rc));
-        DME_TRY(lr_alloc(lr.get(), &lr->d2, rc));
-        DME_TRY(lr_alloc(lr.get(), &lr->LQ, n * desc->p));
-        DME_TRY(lr_alloc(lr.get(), &lr->G, rc * rc));
-        DME_TRY(lr_alloc(lr.get(), &lr->Vt, rc * rc));
-        DME_TRY(lr_alloc(lr.get(), &lr->lam, rc));
-        DME_TRY(lr_alloc(lr.get(), &lr->T, rc * rc));
-        DME_TRY(lr_alloc(lr.get(), &lr->Gm, rc * m));
-        DME_TRY(lr_alloc(lr.get(), &lr->H, m * m));
-        DME_TRY(lr_alloc(lr.get(), &lr->VtH, m * m));
-        DME_TRY(lr_alloc(lr.get(), &lr->lamH, m));
-        DME_TRY(lr_alloc(lr.get(), &lr->F, m * m));
-        DME_TRY(lr_alloc(lr.get(), &lr->Y, rc * m));
-        DME_TRY(lr_alloc(lr.get(), &lr->Z, n * m));
-        lr->ws_doubles = std::max<size_t>((size_t)8 * rc * rc, (size_t)kSplitMax * rc * m);
-        DME_TRY(lr_alloc(lr.get(), &lr->ws, lr->ws_doubles));
-        double* wd = nullptr;
-        DME_TRY(lr_alloc(lr.get(), &wd, (sizeof(GemmProb) * kSplitMax + 7) / 8));
-        lr->wsdesc = reinterpret_cast<GemmProb*>(wd);
-        lr->split = desc->prec == DME_SPLIT_BF16;
-        if (lr->split) {
-            DME_TRY(lr_alloc(lr.get(), &lr->Xtr, rc * n));
-            lr->xsl.rows = (int)rc;
-            lr->xsl.k = (int)n;
-            lr->xsl.Kp = slice_kpad((int)n);
-            lr->xsl.ns = OZ_SLICES_B;
-            double* xd = nullptr;
-            DME_TRY(lr_alloc(lr.get(), &xd, (slice_buf_bytes((int)rc, (int)n, OZ_SLICES_B) + 7) / 8));
-            lr->xsl.data = reinterpret_cast<__nv_bfloat16*>(xd);
-            double* xs = nullptr;
-            DME_TRY(lr_alloc(lr.get(), &xs, (rc + 1) / 2));
-            lr->xsl.scale = reinterpret_cast<float*>(xs);
-            DME_CUDA_TRY(cudaMemsetAsync(xd, 0, slice_buf_bytes((int)rc, (int)n, OZ_SLICES_B), st));
-            DME_CUDA_TRY(cudaMemsetAsync(xs, 0, sizeof(float) * rc, st));
-            DME_TRY(make_slice_tmap(lr->xsl, &lr->xsl.tmap));
+        lr->st = lr->P->st;
+        lr->status = lr->P->status;
+        lr->Bt = lr->P->Bt;
+        DME_TRY(lr_setup(lr.get(), desc, C, q, rmax, tol));
+        DME_TRY(lr_check(lr.get(), "dme_lr_plan"));
+        *out = lr.release();
+        return DME_OK;
+    });
+}
+
+dme_status dme_lr_plan_csr(const dme_plan_desc* desc, int nnz, const int* rowptr, const int* colidx,
+                           const double* vals, const double* C, const double* B, const double* R,
+                           const dme_lr_opts* opts, void* cuda_stream, dme_lr_t* out) {
+    if (!out) return set_error("out is NULL"), DME_EINVAL;
+    *out = nullptr;
+    set_error("");
+    if (!desc || !rowptr || (nnz > 0 && (!colidx || !vals)) || !C)
+        return set_error("desc, the CSR arrays and C are required"), DME_EINVAL;
+    if (nnz < 0) return set_error("nnz must be >= 0"), DME_EINVAL;
+    if (!desc->q_is_factor) return set_error("low-rank path: give Q as its factor C (q_is_factor = 1)"), DME_EINVAL;
+    if (desc->prec != DME_FP64) return set_error("sparse low-rank path: prec must be DME_FP64"), DME_EINVAL;
+    if (desc->fsal || desc->extrap > 1) return set_error("low-rank path: no fsal / extrapolation"), DME_EINVAL;
+    if (desc->eq != DME_DLE && desc->eq != DME_DRE) return set_error("sparse low-rank path: DLE or DRE"), DME_EINVAL;
+    if (desc->n < 1 || desc->nflows < 1 || desc->nflows > 4) return set_error("bad n or nflows"), DME_EINVAL;
+    if (desc->comp != DME_LIE && desc->comp != DME_STRANG) return set_error("bad comp"), DME_EINVAL;
+    if (!(desc->h > 0.0) || !std::isfinite(desc->h)) return set_error("h must be positive"), DME_EINVAL;
+    const bool ric = desc->eq == DME_DRE;
+    for (int i = 0; i < desc->nflows; ++i) {
+        const int f = desc->flows[i];
+        if (f != DME_F1 && f != DME_F2 && f != DME_F12 && f != DME_F3)
+            return set_error("sparse low-rank path: flows F1, F2, F12, F3"), DME_EINVAL;
+        if (f == DME_F3 && !ric) return set_error("F3 needs eq = DRE"), DME_EINVAL;
+    }
+    if (ric && (desc->m < 1 || desc->m > 32 || !B || !R)) return set_error("DRE needs B, R and 1 <= m <= 32"), DME_EINVAL;
+    if (desc->p < 1) return set_error("p must be >= 1"), DME_EINVAL;
+    int q, rmax;
+    double tol;
+    DME_TRY(lr_opts(opts, &q, &rmax, &tol));
+    if (desc->p > rmax) return set_error("low-rank path: p exceeds rmax"), DME_EINVAL;
+    return guarded([&]() -> dme_status {
+        const int n = desc->n;
+        // the CSR arrays on the host (they may be device pointers), checked
+        std::vector<int> ptr(n + 1), idx(nnz);
+        std::vector<double> val(nnz);
+        DME_CUDA_TRY(cudaMemcpy(ptr.data(), rowptr, sizeof(int) * (n + 1), cudaMemcpyDefault));
+        if (nnz) {
+            DME_CUDA_TRY(cudaMemcpy(idx.data(), colidx, sizeof(int) * nnz, cudaMemcpyDefault));
+            DME_CUDA_TRY(cudaMemcpy(val.data(), vals, sizeof(double) * nnz, cudaMemcpyDefault));
         }
-        double* kd = nullptr;
-        DME_TRY(lr_alloc(lr.get(), &kd, 1));
-        lr->kdev = reinterpret_cast<int*>(kd);
-        // L_Q = C^T (C is p x n)
-        double* Cd = nullptr;
-        DME_TRY(lr_alloc(lr.get(), &Cd, (size_t)desc->p * n));
-        DME_CUDA_TRY(cudaMemcpyAsync(Cd, C, sizeof(double) * desc->p * n, cudaMemcpyDefault, st));
-        launch_transpose(Cd, lr->LQ, desc->p, (int)n, (int)n, desc->p, st);
-        DME_CUDA_TRY(cudaStreamSynchronize(st));
-        DME_TRY(plan_check(lr->P, "dme_lr_plan"));
+        if (ptr[0] != 0 || ptr[n] != nnz) return set_error("CSR: rowptr[0] must be 0 and rowptr[n] = nnz"), DME_EINVAL;
+        for (int i = 0; i < n; ++i)
+            if (ptr[i + 1] < ptr[i]) return set_error("CSR: rowptr must be non-decreasing"), DME_EINVAL;
+        for (int e = 0; e < nnz; ++e)
+            if (idx[e] < 0 || idx[e] >= n) return set_error("CSR: column index out of range"), DME_EINVAL;
+        // A^T in CSR (a counting sort by column)
+        std::vector<int> tptr(n + 1, 0), tidx(nnz);
+        std::vector<double> tval(nnz);
+        for (int e = 0; e < nnz; ++e) tptr[idx[e] + 1]++;
+        for (int i = 0; i < n; ++i) tptr[i + 1] += tptr[i];
+        std::vector<int> fill(tptr.begin(), tptr.end() - 1);
+        for (int i = 0; i < n; ++i)
+            for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
+                const int dst = fill[idx[e]]++;
+                tidx[dst] = i;
+                tval[dst] = val[e];
+            }
+        std::unique_ptr<dme_lr_s, void (*)(dme_lr_t)> lr(new dme_lr_s(), lr_free);
+        lr->sparse = true;
+        lr->nnz = nnz;
+        // Gershgorin interval of A^T (rows of A^T): A^T = c I + g X, X's spectrum in [-2, 2]
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double di = 0.0, ri = 0.0;
+            for (int e = tptr[i]; e < tptr[i + 1]; ++e) {
+                if (tidx[e] == i) di += tval[e];
+                else ri += std::fabs(tval[e]);
+            }
+            if (i == 0 || di - ri < a) a = di - ri;
+            if (i == 0 || di + ri > b) b = di + ri;
+        }
+        lr->lc = 0.5 * (a + b);
+        lr->lg = 0.25 * (b - a);
+        lr->xi = leja_points_host(kLejaTerms);
+        if (cuda_stream) {
+            lr->st = reinterpret_cast<cudaStream_t>(cuda_stream);
+        } else {
+            DME_CUDA_TRY(cudaStreamCreateWithFlags(&lr->st, cudaStreamNonBlocking));
+            lr->own_st = true;
+        }
+        cudaStream_t st = lr->st;
+        double* sd = nullptr;
+        DME_TRY(lr_alloc(lr.get(), &sd, 1));
+        lr->status = reinterpret_cast<int*>(sd);
+        DME_CUDA_TRY(cudaMemsetAsync(lr->status, 0, sizeof(int), st));
+        double *tp = nullptr, *ti = nullptr;
+        DME_TRY(lr_alloc(lr.get(), &tp, ((size_t)n + 2) / 2));
+        DME_TRY(lr_alloc(lr.get(), &ti, ((size_t)nnz + 1) / 2));
+        DME_TRY(lr_alloc(lr.get(), &lr->at_val, (size_t)nnz));
+        lr->at_ptr = reinterpret_cast<int*>(tp);
+        lr->at_idx = reinterpret_cast<int*>(ti);
+        DME_CUDA_TRY(cudaMemcpyAsync(lr->at_ptr, tptr.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st));
+        if (nnz) {
+            DME_CUDA_TRY(cudaMemcpyAsync(lr->at_idx, tidx.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, st));
+            DME_CUDA_TRY(cudaMemcpyAsync(lr->at_val, tval.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
+        }
+        DME_CUDA_TRY(cudaStreamSynchronize(st));       // the host copies above go out of scope
+        if (ric) {
+            const int m = desc->m;
+            double *Bd = nullptr, *Rd = nullptr, *Btd = nullptr;
+            DME_TRY(lr_alloc(lr.get(), &Bd, (size_t)n * m));
+            DME_TRY(lr_alloc(lr.get(), &Rd, (size_t)m * m));
+            DME_TRY(lr_alloc(lr.get(), &Btd, (size_t)n * m));
+            DME_CUDA_TRY(cudaMemcpyAsync(Bd, B, sizeof(double) * n * m, cudaMemcpyDefault, st));
+            DME_CUDA_TRY(cudaMemcpyAsync(Rd, R, sizeof(double) * m * m, cudaMemcpyDefault, st));
+            launch_small_cholesky(Rd, m, lr->status, st);
+            launch_apply_linv_rows(Bd, Rd, Btd, n, m, st);
+            lr->Bt = Btd;
+            DME_TRY(lr_check(lr.get(), "dme_lr_plan_csr (Cholesky of R)"));
+        }
+        DME_TRY(lr_setup(lr.get(), desc, C, q, rmax, tol));
+        const size_t rc = rmax;
+        DME_TRY(lr_alloc(lr.get(), &lr->Wa, (size_t)n * rc));
+        DME_TRY(lr_alloc(lr.get(), &lr->Wb, (size_t)n * rc));
+        DME_TRY(lr_alloc(lr.get(), &lr->lpart, 2 * (size_t)leja_blocks(n)));
+        DME_TRY(lr_alloc(lr.get(), &lr->lnorm, 16));
+        DME_TRY(lr_check(lr.get(), "dme_lr_plan_csr"));
         *out = lr.release();
         return DME_OK;
     });
@@ -490,7 +806,7 @@ dme_status dme_lr_solve(dme_lr_t lr, const double* L0, const double* D0, int r0,
     if (r0 < 0 || r0 > lr->rcap || (r0 > 0 && (!L0 || !D0)))
         return set_error("need 0 <= r0 <= rmax and L0, D0 when r0 > 0"), DME_EINVAL;
     return guarded([&]() -> dme_status {
-        cudaStream_t st = lr->P->st;
+        cudaStream_t st = lr->st;
         const int n = lr->n, rc = lr->rcap;
         lr->r = 0;
         if (r0 > 0) {
@@ -499,7 +815,7 @@ dme_status dme_lr_solve(dme_lr_t lr, const double* L0, const double* D0, int r0,
                                            cudaMemcpyDefault, st));
             DME_CUDA_TRY(cudaMemcpy2DAsync(lr->G, sizeof(double) * rc, D0, sizeof(double) * r0, sizeof(double) * r0, r0,
                                            cudaMemcpyDefault, st));
-            DME_TRY(launch_jacobi_eig(lr->G, rc, r0, lr->Vt, rc, lr->lam, lr->P->status, st));
+            DME_TRY(launch_jacobi_eig(lr->G, rc, r0, lr->Vt, rc, lr->lam, lr->status, st));
             launch_lr_select(lr->lam, lr->Vt, rc, r0, 0.0, 0, lr->T, rc, lr->d, lr->kdev, st);
             int k = 0;
             DME_CUDA_TRY(cudaMemcpyAsync(&k, lr->kdev, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -509,9 +825,10 @@ dme_status dme_lr_solve(dme_lr_t lr, const double* L0, const double* D0, int r0,
             DME_TRY(compress(lr, lr->L, lr->L2, lr->d, rc, lr->r));
         }
         const double h = T / nsteps;
-        const auto seq = plan_step_sequence(lr->P->d, h);
+        const auto seq = plan_step_sequence(lr->desc, h);
         for (int s = 0; s < nsteps; ++s)
             for (auto& ft : seq) DME_TRY(lr_apply(lr, ft.first, ft.second));
+        if (P_out && n > 16384) return set_error("dme_lr_solve: P_out needs n <= 16384 (use dme_lr_factors)"), DME_EINVAL;
         if (P_out) {
             const size_t nn = (size_t)n * n;
             if (!lr->Pout) DME_TRY(lr_alloc(lr, &lr->Pout, nn));
@@ -524,14 +841,14 @@ dme_status dme_lr_solve(dme_lr_t lr, const double* L0, const double* D0, int r0,
             DME_CUDA_TRY(cudaMemcpyAsync(P_out, lr->Pout, nn * sizeof(double), cudaMemcpyDefault, st));
         }
         if (r_out) *r_out = lr->r;
-        return plan_check(lr->P, "dme_lr_solve");
+        return lr_check(lr, "dme_lr_solve");
     });
 }
 
 dme_status dme_lr_factors(dme_lr_t lr, double* L_out, double* d_out, int* r) {
     if (!lr || !r) return set_error("plan and r are required"), DME_EINVAL;
     return guarded([&]() -> dme_status {
-        cudaStream_t st = lr->P->st;
+        cudaStream_t st = lr->st;
         *r = lr->r;
         if (lr->r > 0 && L_out)
             DME_CUDA_TRY(cudaMemcpy2DAsync(L_out, sizeof(double) * lr->r, lr->L, sizeof(double) * lr->rcap,

@@ -255,3 +255,35 @@ def mass_ode_reference(M, A, Q, P0, T, BRB=None, rtol=1e-13, atol=1e-15):
     sol = si.solve_ivp(rhs, (0.0, T), np.asarray(P0, float).ravel(), method="DOP853", rtol=rtol, atol=atol)
     assert sol.success, sol.message
     return sol.y[:, -1].reshape(n, n)
+
+
+def dle_exact_apply_stencil_laplacian(nx, c, t, X, chunk=1024):
+    """P(t) X for the DLE with A = the unscaled 5-point Dirichlet stencil on an
+    nx x nx grid (x index fastest; eigenvalues 2cos(k pi h) + 2cos(l pi h) - 4,
+    h = 1/(nx+1)), Q = c c^T and P0 = 0, without forming P: in the sine basis
+    V (the orthonormal DST-I in each direction), P = V (q q^T o Phi) V^T with
+    q = V^T c and Phi_ij = expm1((l_i + l_j) t) / (l_i + l_j), applied in row
+    chunks of Phi."""
+    import scipy.fft as sf
+    n = nx * nx
+    h = 1.0 / (nx + 1)
+    k = np.arange(1, nx + 1)
+    l1 = 2.0 * np.cos(k * np.pi * h) - 2.0
+    lam = (l1[:, None] + l1[None, :]).ravel()        # index (iy, ix) -> iy * nx + ix
+
+    def vt(v):
+        return sf.dstn(v.reshape(nx, nx), type=1, norm="ortho").ravel()
+
+    q = vt(np.asarray(c, dtype=np.float64))
+    X = np.atleast_2d(np.asarray(X, dtype=np.float64).T).T
+    out = np.empty_like(X)
+    for j in range(X.shape[1]):
+        y = q * vt(X[:, j])
+        z = np.empty(n)
+        for i0 in range(0, n, chunk):
+            L = lam[i0:i0 + chunk, None] + lam[None, :]
+            with np.errstate(divide="ignore", invalid="ignore"):
+                phi = np.where(np.abs(L) > 0, np.expm1(L * t) / L, t)
+            z[i0:i0 + chunk] = phi @ y
+        out[:, j] = vt(q * z)      # V is symmetric: V = V^T
+    return out

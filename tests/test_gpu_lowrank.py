@@ -137,3 +137,75 @@ def test_lowrank_split_at_full_size_matches_fp64_lowrank():
         plan.close()
     assert abs(out["fp64"][0] - out["split_bf16"][0]) <= 1
     assert rel(out["split_bf16"][1], out["fp64"][1]) < SPLIT_TOL
+
+
+# ---------------------------------------------------------------- sparse A: Leja interpolation
+import scipy.sparse as sp   # noqa: E402
+
+
+def _csr_run(pr, flows, comp, N, q=7, tol=1e-13):
+    A = sp.csr_matrix(pr.A)
+    uses_B = "F3" in flows
+    B = pr.B if uses_B else None
+    R = pr.R if uses_B else None
+    plan = dme.LowRankPlan.from_csr(A, pr.C, h=pr.T / N, flows=flows, comp=comp, B=B, R=R, quad_nodes=q, tol=tol)
+    P = np.empty((pr.n, pr.n))
+    r = plan.solve(pr.T, N, P_out=P)
+    Lo, Do = O.solve_lowrank(A, pr.C, np.zeros((pr.n, 0)), np.zeros((0, 0)), pr.T, N, comp, flows, B=B, R=R,
+                             q=q, tol=tol, action="leja")
+    return P, r, Lo, Do, plan
+
+
+@pytest.mark.parametrize("kind,flows,comp,N", [("dle", ["F1", "F2"], "strang", 10), ("dre", ["F12", "F3"], "strang", 5),
+                                               ("dre", ["F1", "F3", "F2"], "lie", 4), ("dre", ["F1", "F2", "F3"], "strang", 6)])
+def test_sparse_lowrank_matches_leja_oracle(kind, flows, comp, N):
+    pr = _problem(kind)
+    P, r, Lo, Do, _ = _csr_run(pr, flows, comp, N)
+    assert rel(P, O.ldl_product(Lo, Do)) < FP64_TOL
+    assert abs(r - Lo.shape[1]) <= 1
+
+
+def test_sparse_lowrank_equals_dense_lowrank_gpu():
+    pr = W.dre_convdiff(nx=8, m=2, p=3)
+    P, *_ = _csr_run(pr, ["F1", "F2", "F3"], "strang", 6, tol=1e-15)
+    Pd, *_ = _run(pr, ["F1", "F2", "F3"], "strang", 6, tol=1e-15)
+    assert rel(P, Pd) < 1e-11
+
+
+def test_sparse_lowrank_beyond_the_dense_limit_matches_closed_form():
+    """n = 130^2 = 16900 (past the dense path's 16384): the DLE for the unscaled
+    5-point stencil with Q = c c^T, T12 steps (exact flow, W by quadrature), the
+    factored result applied to random vectors against the exact solution in the
+    sine basis (DST)."""
+    import pins
+    nx = 130
+    n = nx * nx
+    T1 = sp.diags([np.full(nx - 1, 1.0), np.full(nx, -2.0), np.full(nx - 1, 1.0)], [-1, 0, 1])
+    I1 = sp.identity(nx)
+    A = (sp.kron(I1, T1) + sp.kron(T1, I1)).tocsr()
+    c = np.random.default_rng(5).uniform(0.0, 1.0, n)
+    T, N = 0.5, 5
+    plan = dme.LowRankPlan.from_csr(A, c[None, :], h=T / N, flows=["F12"], comp="strang", quad_nodes=7)
+    r = plan.solve(T, N)
+    L, d = plan.factors()
+    assert 1 <= r <= 224 and np.all(d > 0)
+    X = np.random.default_rng(6).standard_normal((n, 1))
+    got = L @ (d[:, None] * (L.T @ X))
+    ref = pins.dle_exact_apply_stencil_laplacian(nx, c, T, X)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-10
+    with pytest.raises(dme.DmeError):
+        plan.solve(T, N, P_out=np.empty((1, 1)))
+
+
+def test_sparse_lowrank_rejects_malformed_csr():
+    pr = W.dre_convdiff(nx=5, m=2, p=2)
+    A = sp.csr_matrix(pr.A)
+    bad = A.indices.copy()
+    bad[3] = pr.n + 7
+    d = dme.make_desc(pr.n, m=2, p=2, eq=dme.DME_DRE, flows=["F12", "F3"], h=0.1, q_is_factor=True)
+    with pytest.raises(dme.DmeError) as ei:
+        dme.dme_lr_plan_csr(d, A.indptr, bad, A.data, pr.C, pr.B, pr.R)
+    assert ei.value.status == dme.DME_EINVAL
+    d4 = dme.make_desc(pr.n, m=2, p=2, eq=dme.DME_GDRE, flows=["F12", "F3", "F4"], h=0.1, q_is_factor=True)
+    with pytest.raises(dme.DmeError):
+        dme.dme_lr_plan_csr(d4, A.indptr, A.indices, A.data, pr.C, pr.B, pr.R)

@@ -84,3 +84,17 @@ def test_pin_catches_unscaled_divided_differences(monkeypatch):
     ref = sla.expm(pr.A.T / 64) @ V
     got = O.leja_action(pr.A.T, V, 1 / 64)
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) > 1e-3
+
+
+def test_stencil_laplacian_dle_closed_form_helper():
+    """The DST-based exact DLE product used at large n, against the dense
+    eigenbasis closed form at a small size."""
+    import pins
+    nx = 6
+    A = W.laplacian_2d(nx) / (nx + 1) ** 2
+    c = np.random.default_rng(2).uniform(0, 1, nx * nx)
+    lam, V = np.linalg.eigh(A)
+    P = pins.dle_exact_symmetric(V, lam, np.outer(c, c), np.zeros_like(A), 0.7)
+    X = np.random.default_rng(3).standard_normal((nx * nx, 2))
+    got = pins.dle_exact_apply_stencil_laplacian(nx, c, 0.7, X)
+    assert np.linalg.norm(got - P @ X) / np.linalg.norm(P @ X) < 1e-13
