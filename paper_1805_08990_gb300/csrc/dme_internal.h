@@ -106,10 +106,13 @@ void launch_apply_linv_rows(const double* B, const double* L, double* Bt, int n,
 
 // ---------------------------------------------------------------- low-rank path
 constexpr int LR_MAX_RANK = 224;   // columns of L before a compression (shared-memory Jacobi)
+constexpr int LR_JACOBI_F32_MAX = 176;   // largest size of the single-precision Jacobi pass
 size_t jacobi_smem_bytes(int r);
 // Eigen-decomposition of the symmetric r x r matrix G: lam (r), V^T (r x r, ldv).
+// fp32: a single-precision pass (converged to about 1e-7), a starting basis for
+// the double-precision one; the output is double either way.
 dme_status launch_jacobi_eig(const double* G, int ldg, int r, double* Vt, int ldv, double* lam, int* status,
-                             cudaStream_t st);
+                             cudaStream_t st, bool fp32 = false);
 // Keep eigenvalues > tol * max, ordered decreasingly: d_out, k_out, and the
 // r x k basis T (columns = eigenvectors, times lambda^{-1/2} if inv_sqrt).
 void launch_lr_select(const double* lam, const double* Vt, int ldv, int r, double tol, int inv_sqrt, double* T,
@@ -121,6 +124,14 @@ void launch_ric_weights(const double* lam, const double* Vt, int ldv, int m, dou
 void launch_copy_cols(double* Y, int ldy, const double* X, int ldx, int n, int k, double alpha, const double* d,
                       cudaStream_t st);
 void launch_fill(double* x, int k, double v, cudaStream_t st);
+// part[s] (M x N) = sum over rows k in [s chunk, (s+1) chunk) of X[k]^T Y[k], for
+// X (K x M), Y (K x N), M N <= 1024; ceil(K / chunk) partial products.
+void launch_tsgemm(const double* X, int ldx, int M, const double* Y, int ldy, int N, int K, int chunk, double* part,
+                   cudaStream_t st);
+// C (n x N) = alpha X op(T) (+ beta D, leading dimension ldc) for a tall X (n x K)
+// and a small op(T) (K x N; T^T stored when tT), K, N <= 64; C must not overlap X.
+void launch_tall_small(const double* X, int ldx, int n, int K, const double* Tm, int ldt, int tT, int N, double* C,
+                       int ldc, double alpha, const double* D, double beta, cudaStream_t st);
 // C (M x N) = alpha * sum_{s < S} W[s] (+ b1 D1) with W[s] M x N contiguous; tri mirrors the upper part.
 void launch_splitk_reduce(const double* W, int S, int M, int N, double* C, int ldc, double alpha, const double* D1,
                           double b1, int tri, cudaStream_t st);
@@ -129,6 +140,7 @@ void launch_splitk_reduce(const double* W, int S, int M, int N, double* C, int l
 // (A^T in CSR): Wn = (A^T W - c W) invg - xk W, Pacc += dk Wn; norms2[0..1] =
 // |Wn|_F^2, |Pacc|_F^2 (part: 2 leja_blocks(n) doubles of scratch).
 int leja_blocks(int n);
+int leja_part_blocks(int n, int rmax);   // partial-norm slots the term kernels may use
 void launch_leja_term(const int* ptr, const int* idx, const double* val, int n, int r, const double* W, double* Wn,
                       int ldw, double* Pacc, int ldp, double c, double invg, double xk, double dk, double* part,
                       double* norms2, cudaStream_t st);

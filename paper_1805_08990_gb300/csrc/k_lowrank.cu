@@ -22,11 +22,13 @@ __device__ __forceinline__ int pk(int a, int b, int r) {   // packed upper trian
     return a * r - (a * (a - 1)) / 2 + (b - a);
 }
 
-__device__ __forceinline__ double pget(const double* A, int x, int y, int r) {
+template <typename T>
+__device__ __forceinline__ T pget(const T* A, int x, int y, int r) {
     return x <= y ? A[pk(x, y, r)] : A[pk(y, x, r)];
 }
 
-__device__ __forceinline__ void pset(double* A, int x, int y, int r, double v) {
+template <typename T>
+__device__ __forceinline__ void pset(T* A, int x, int y, int r, T v) {
     if (x <= y) A[pk(x, y, r)] = v;
     else A[pk(y, x, r)] = v;
 }
@@ -56,19 +58,23 @@ constexpr int kJacobiSweeps = 60;
 // point carries absolute errors of that size anyway).  The sweeps stop after
 // one with no rotation (DEV_NONFINITE in *status after 60 sweeps or on a
 // non-finite entry).
-// VS: V^T is accumulated in shared memory too (r <= 112) and copied out at the end.
-template <bool VS>
+// T: the arithmetic (float for a fast first pass, double for the result).
+// VS: V^T is accumulated in shared memory too (r <= 112 for double) and copied
+// out at the end; otherwise in global memory (Vt_out, double only).
+template <typename T, bool VS>
 __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double* __restrict__ G, int ldg, int r,
                                                           double* __restrict__ Vt_out, int ldv_out,
                                                           double* __restrict__ lam, int* status) {
-    extern __shared__ double sm[];
+    extern __shared__ __align__(16) unsigned char jsm[];
     const int R = r + (r & 1), P = R / 2;
-    double* A = sm;
-    double* cs = A + (size_t)r * (r + 1) / 2;
-    double* sn = cs + P;
-    double* tt = sn + P;
-    double* Vt = VS ? tt + P : Vt_out;
+    T* A = reinterpret_cast<T*>(jsm);
+    T* cs = A + (size_t)r * (r + 1) / 2;
+    T* sn = cs + P;
+    T* tt = sn + P;
+    T* Vt = VS ? tt + P : reinterpret_cast<T*>(Vt_out);
     const int ldv = VS ? r : ldv_out;
+    constexpr T kRel = sizeof(T) == 4 ? T(1e-7) : T(1e-16);
+    constexpr T kFloor = sizeof(T) == 4 ? T(1e-8) : T(1e-17);
     int* pp = reinterpret_cast<int*>(VS ? tt + P + (size_t)r * r : tt + P);
     int* qq = pp + P;
     // (i, j), i <= j, of every rotation block, packed as i << 8 | j (P <= 112)
@@ -76,6 +82,7 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double* __restri
     const int nblk = P * (P + 1) / 2;
     __shared__ int rotated;
     __shared__ int bad;
+    __shared__ T floor_abs;
     const int tid = threadIdx.x, nt = blockDim.x;
     if (tid == 0) bad = 0;
     for (int i = tid; i < P; i += nt) {
@@ -86,38 +93,37 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double* __restri
         const int i = e / r, j = e % r;
         if (i <= j) {
             const double v = 0.5 * (G[(size_t)i * ldg + j] + G[(size_t)j * ldg + i]);
-            A[pk(i, j, r)] = v;
+            A[pk(i, j, r)] = (T)v;
             if (!isfinite(v)) bad = 1;
         }
-        Vt[(size_t)i * ldv + j] = (i == j) ? 1.0 : 0.0;
+        Vt[(size_t)i * ldv + j] = (i == j) ? T(1) : T(0);
     }
     __syncthreads();
     if (bad) {
         if (tid == 0) atomicOr(status, DEV_NONFINITE);
         return;
     }
-    __shared__ double floor_abs;
     int sweep = 0;
     for (; sweep < kJacobiSweeps; ++sweep) {
         if (tid == 0) {
             rotated = 0;
-            double dm = 0.0;
-            for (int i = 0; i < r; ++i) dm = fmax(dm, fabs(A[pk(i, i, r)]));
-            floor_abs = 1e-17 * dm;
+            T dm = 0;
+            for (int i = 0; i < r; ++i) dm = max(dm, abs(A[pk(i, i, r)]));
+            floor_abs = kFloor * dm;
         }
         __syncthreads();
         for (int t = 0; t < R - 1; ++t) {
             for (int i = tid; i < P; i += nt) {
                 int p, q;
                 rr_pair(i, t, R, p, q);
-                double c = 1.0, s = 0.0, tv = 0.0;
+                T c = 1, s = 0, tv = 0;
                 if (q < r) {
-                    const double apq = A[pk(p, q, r)];
-                    const double app = A[pk(p, p, r)], aqq = A[pk(q, q, r)];
-                    if (fabs(apq) > fmax(1e-16 * sqrt(fabs(app * aqq)), floor_abs)) {
-                        const double th = (aqq - app) / (2.0 * apq);
-                        tv = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
-                        c = 1.0 / sqrt(1.0 + tv * tv);
+                    const T apq = A[pk(p, q, r)];
+                    const T app = A[pk(p, p, r)], aqq = A[pk(q, q, r)];
+                    if (abs(apq) > max(kRel * sqrt(abs(app * aqq)), floor_abs)) {
+                        const T th = (aqq - app) / (T(2) * apq);
+                        tv = (th >= T(0) ? T(1) : T(-1)) / (abs(th) + sqrt(T(1) + th * th));
+                        c = T(1) / sqrt(T(1) + tv * tv);
                         s = tv * c;
                         rotated = 1;
                     }
@@ -133,23 +139,23 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double* __restri
             for (int e = tid; e < nblk; e += nt) {
                 const int i = blk[e] >> 8, j = blk[e] & 0xFF;
                 const int pi = pp[i], qi = qq[i], pj = pp[j], qj = qq[j];
-                const double ci = cs[i], si = sn[i], cj = cs[j], sj = sn[j];
-                if (si == 0.0 && sj == 0.0) continue;
+                const T ci = cs[i], si = sn[i], cj = cs[j], sj = sn[j];
+                if (si == T(0) && sj == T(0)) continue;
                 if (i == j) {
                     if (qi >= r) continue;
-                    const double apq = A[pk(pi, qi, r)];
+                    const T apq = A[pk(pi, qi, r)];
                     A[pk(pi, pi, r)] -= tt[i] * apq;
                     A[pk(qi, qi, r)] += tt[i] * apq;
-                    A[pk(pi, qi, r)] = 0.0;
+                    A[pk(pi, qi, r)] = T(0);
                     continue;
                 }
                 const bool qiok = qi < r, qjok = qj < r;
-                const double x00 = pget(A, pi, pj, r);
-                const double x01 = qjok ? pget(A, pi, qj, r) : 0.0;
-                const double x10 = qiok ? pget(A, qi, pj, r) : 0.0;
-                const double x11 = (qiok && qjok) ? pget(A, qi, qj, r) : 0.0;
-                const double y00 = ci * x00 - si * x10, y01 = ci * x01 - si * x11;
-                const double y10 = si * x00 + ci * x10, y11 = si * x01 + ci * x11;
+                const T x00 = pget(A, pi, pj, r);
+                const T x01 = qjok ? pget(A, pi, qj, r) : T(0);
+                const T x10 = qiok ? pget(A, qi, pj, r) : T(0);
+                const T x11 = (qiok && qjok) ? pget(A, qi, qj, r) : T(0);
+                const T y00 = ci * x00 - si * x10, y01 = ci * x01 - si * x11;
+                const T y10 = si * x00 + ci * x10, y11 = si * x01 + ci * x11;
                 pset(A, pi, pj, r, cj * y00 - sj * y01);
                 if (qjok) pset(A, pi, qj, r, sj * y00 + cj * y01);
                 if (qiok) pset(A, qi, pj, r, cj * y10 - sj * y11);
@@ -158,11 +164,11 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double* __restri
             // V <- V J: rows p, q of V^T
             for (int e = tid; e < P * r; e += nt) {
                 const int i = e / r, k = e % r;
-                const double s = sn[i];
-                if (s == 0.0) continue;
-                const double c = cs[i];
+                const T s = sn[i];
+                if (s == T(0)) continue;
+                const T c = cs[i];
                 const int p = pp[i], q = qq[i];
-                const double vp = Vt[(size_t)p * ldv + k], vq = Vt[(size_t)q * ldv + k];
+                const T vp = Vt[(size_t)p * ldv + k], vq = Vt[(size_t)q * ldv + k];
                 Vt[(size_t)p * ldv + k] = c * vp - s * vq;
                 Vt[(size_t)q * ldv + k] = s * vp + c * vq;
             }
@@ -172,10 +178,10 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double* __restri
         __syncthreads();
         if (!any) break;
     }
-    for (int i = tid; i < r; i += nt) lam[i] = A[pk(i, i, r)];
+    for (int i = tid; i < r; i += nt) lam[i] = (double)A[pk(i, i, r)];
     if (VS)
-        for (int e = tid; e < r * r; e += nt) Vt_out[(size_t)(e / r) * ldv_out + e % r] = Vt[e];
-    if (tid == 0 && sweep == kJacobiSweeps) atomicOr(status, DEV_NONFINITE);
+        for (int e = tid; e < r * r; e += nt) Vt_out[(size_t)(e / r) * ldv_out + e % r] = (double)Vt[e];
+    if (tid == 0 && sweep == kJacobiSweeps && sizeof(T) == 8) atomicOr(status, DEV_NONFINITE);
 }
 
 // Order the eigenvalues decreasingly and keep those above tol * max (max > 0):
@@ -257,6 +263,81 @@ __global__ void splitk_reduce_kernel(const double* __restrict__ Wk, int S, int M
     }
 }
 
+// Partial products of X^T Y for tall X (K x M) and Y (K x N), M N <= 1024:
+// block s sums the rows [s chunk, (s + 1) chunk).  The 256 threads form G =
+// 256 / E groups (E = M N rounded up to a power of two, at least 32 so a group
+// is whole warps, or 256 / 4 entries per thread when M N > 256); group g takes
+// the rows k0 + g, k0 + g + G, ..., and the groups' sums are added in group
+// order in shared memory.  part: [S][M][N].
+__global__ void __launch_bounds__(256) tsgemm_kernel(const double* __restrict__ X, int ldx, int M,
+                                                     const double* __restrict__ Y, int ldy, int N, int K, int chunk,
+                                                     double* __restrict__ part) {
+    __shared__ double red[1024];
+    const int k0 = blockIdx.x * chunk, k1 = min(K, k0 + chunk);
+    const int MN = M * N;
+    int E = 32;
+    while (E < MN && E < 256) E <<= 1;
+    const int per = (MN + 255) / 256;                 // entries per thread when E = 256
+    const int G = 256 / E;
+    const int g = threadIdx.x / E, t = threadIdx.x % E;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int ea[4], eb[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int e = t + E * u;
+        ea[u] = e < MN ? e / N : 0;
+        eb[u] = e < MN ? e % N : 0;
+    }
+    for (int k = k0 + g; k < k1; k += G) {
+        const double* xr = X + (size_t)k * ldx;
+        const double* yr = Y + (size_t)k * ldy;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (u < per && t + E * u < MN) acc[u] = fma(xr[ea[u]], yr[eb[u]], acc[u]);
+    }
+    if (G == 1) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = t + E * u;
+            if (u < per && e < MN) part[(size_t)blockIdx.x * MN + e] = acc[u];
+        }
+        return;
+    }
+    // G > 1: E <= 128, one entry per thread
+    red[threadIdx.x] = acc[0];
+    __syncthreads();
+    if (g == 0 && t < MN) {
+        double v = red[t];
+        for (int q = 1; q < G; ++q) v += red[q * E + t];
+        part[(size_t)blockIdx.x * MN + t] = v;
+    }
+}
+
+// C (n x N, ldc) = alpha X op(T) (+ beta D) for X n x K (ldx) and a small op(T)
+// (K x N; T stored K x N, or N x K when tT, leading dimension ldt; K, N <= 64)
+// staged in shared memory; one thread per output entry.
+__global__ void __launch_bounds__(256) tall_small_kernel(const double* __restrict__ X, int ldx, int n, int K,
+                                                         const double* __restrict__ Tm, int ldt, int tT, int N,
+                                                         double* __restrict__ C, int ldc, double alpha,
+                                                         const double* __restrict__ D, double beta) {
+    __shared__ double sT[64 * 64];
+    for (int e = threadIdx.x; e < K * N; e += blockDim.x) {
+        const int k = e / N, j = e % N;
+        sT[e] = tT ? Tm[(size_t)j * ldt + k] : Tm[(size_t)k * ldt + j];
+    }
+    __syncthreads();
+    const size_t total = (size_t)n * N;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / N), j = (int)(e % N);
+        const double* xr = X + (size_t)i * ldx;
+        double acc = 0.0;
+        for (int k = 0; k < K; ++k) acc = fma(xr[k], sT[k * N + j], acc);
+        double v = alpha * acc;
+        if (D) v += beta * D[(size_t)i * ldc + j];
+        C[(size_t)i * ldc + j] = v;
+    }
+}
+
 __global__ void fill_kernel(double* __restrict__ x, int k, double v) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) x[i] = v;
 }
@@ -265,35 +346,48 @@ int grid_of(size_t total) { return (int)std::min<size_t>((total + 255) / 256, 15
 
 }  // namespace
 
-constexpr int kJacobiSmemV = 112;    // largest r whose V^T also fits in shared memory
+constexpr int kJacobiSmemV = 112;    // largest r whose V^T also fits in shared memory (double)
+constexpr int kJacobiF32Max = LR_JACOBI_F32_MAX;   // single-precision pass: V^T in shared memory
 
+template <typename T>
 static size_t jacobi_smem(int r, bool vs) {
     const int P = (r + (r & 1)) / 2;
-    return sizeof(double) * ((size_t)r * (r + 1) / 2 + 3 * (size_t)P + (vs ? (size_t)r * r : 0)) +
+    return sizeof(T) * ((size_t)r * (r + 1) / 2 + 3 * (size_t)P + (vs ? (size_t)r * r : 0)) +
            sizeof(int) * 2 * (size_t)P + sizeof(unsigned short) * (size_t)P * (P + 1) / 2;
 }
 
-size_t jacobi_smem_bytes(int r) { return jacobi_smem(r, r <= kJacobiSmemV); }
+size_t jacobi_smem_bytes(int r) { return jacobi_smem<double>(r, r <= kJacobiSmemV); }
 
 dme_status launch_jacobi_eig(const double* G, int ldg, int r, double* Vt, int ldv, double* lam, int* status,
-                             cudaStream_t st) {
+                             cudaStream_t st, bool fp32) {
     if (r < 1 || r > LR_MAX_RANK) return set_error("jacobi: size must be in [1, 224]"), DME_EINVAL;
+    if (fp32 && r > kJacobiF32Max) return set_error("jacobi: the single-precision pass needs r <= 176"), DME_EINVAL;
     static bool attr = false;
     if (!attr) {
-        DME_CUDA_TRY(cudaFuncSetAttribute(jacobi_eig_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)jacobi_smem(LR_MAX_RANK, false)));
-        DME_CUDA_TRY(cudaFuncSetAttribute(jacobi_eig_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)jacobi_smem(kJacobiSmemV, true)));
+        DME_CUDA_TRY(cudaFuncSetAttribute(jacobi_eig_kernel<double, false>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)jacobi_smem<double>(LR_MAX_RANK, false)));
+        DME_CUDA_TRY(cudaFuncSetAttribute(jacobi_eig_kernel<double, true>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)jacobi_smem<double>(kJacobiSmemV, true)));
+        DME_CUDA_TRY(cudaFuncSetAttribute(jacobi_eig_kernel<float, true>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)jacobi_smem<float>(kJacobiF32Max, true)));
         attr = true;
     }
     // enough threads for the P(P+1)/2 rotation blocks of a sub-sweep, no more (fewer warps
     // make the two barriers per sub-sweep cheaper)
     const int P = (r + 1) / 2;
     const int threads = std::min(1024, std::max(64, (P * (P + 1) / 2 + 31) / 32 * 32));
-    if (r <= kJacobiSmemV)
-        jacobi_eig_kernel<true><<<1, threads, jacobi_smem(r, true), st>>>(G, ldg, r, Vt, ldv, lam, status);
+    if (fp32)
+        jacobi_eig_kernel<float, true><<<1, threads, jacobi_smem<float>(r, true), st>>>(G, ldg, r, Vt, ldv, lam,
+                                                                                     status);
+    else if (r <= kJacobiSmemV)
+        jacobi_eig_kernel<double, true><<<1, threads, jacobi_smem<double>(r, true), st>>>(G, ldg, r, Vt, ldv, lam,
+                                                                                       status);
     else
-        jacobi_eig_kernel<false><<<1, threads, jacobi_smem(r, false), st>>>(G, ldg, r, Vt, ldv, lam, status);
+        jacobi_eig_kernel<double, false><<<1, threads, jacobi_smem<double>(r, false), st>>>(G, ldg, r, Vt, ldv,
+                                                                                         lam, status);
     DME_CUDA_TRY(cudaGetLastError());
     return DME_OK;
 }
@@ -314,10 +408,55 @@ void launch_copy_cols(double* Y, int ldy, const double* X, int ldx, int n, int k
     copy_cols_kernel<<<grid_of((size_t)n * k), 256, 0, st>>>(Y, ldy, X, ldx, n, k, alpha, d);
 }
 
+// Many partials of a small result: one block per entry, strided sums then a
+// fixed tree (deterministic); same outputs as splitk_reduce_kernel.
+__global__ void __launch_bounds__(256) splitk_reduce_wide_kernel(const double* __restrict__ Wk, int S, int M, int N,
+                                                                 double* __restrict__ C, int ldc, double alpha,
+                                                                 const double* __restrict__ D1, double b1, int tri) {
+    __shared__ double red[256];
+    const size_t total = (size_t)M * N;
+    const int e = blockIdx.x;
+    const int i = e / N, j = e % N;
+    if (tri && i > j) return;
+    double acc = 0.0;
+    for (int s = threadIdx.x; s < S; s += 256) acc += Wk[(size_t)s * total + e];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double v = alpha * red[0];
+        if (D1) v += b1 * D1[(size_t)i * ldc + j];
+        C[(size_t)i * ldc + j] = v;
+        if (tri && i != j) C[(size_t)j * ldc + i] = v;
+    }
+}
+
 void launch_splitk_reduce(const double* W, int S, int M, int N, double* C, int ldc, double alpha, const double* D1,
                           double b1, int tri, cudaStream_t st) {
     if (M <= 0 || N <= 0) return;
+    if (S >= 64 && (size_t)M * N <= 4096) {
+        splitk_reduce_wide_kernel<<<M * N, 256, 0, st>>>(W, S, M, N, C, ldc, alpha, D1, b1, tri);
+        return;
+    }
     splitk_reduce_kernel<<<grid_of((size_t)M * N), 256, 0, st>>>(W, S, M, N, C, ldc, alpha, D1, b1, tri);
+}
+
+void launch_tsgemm(const double* X, int ldx, int M, const double* Y, int ldy, int N, int K, int chunk, double* part,
+                   cudaStream_t st) {
+    const int S = (K + chunk - 1) / chunk;
+    if (S <= 0 || M * N <= 0) return;
+    tsgemm_kernel<<<S, 256, 0, st>>>(X, ldx, M, Y, ldy, N, K, chunk, part);
+}
+
+void launch_tall_small(const double* X, int ldx, int n, int K, const double* Tm, int ldt, int tT, int N, double* C,
+                       int ldc, double alpha, const double* D, double beta, cudaStream_t st) {
+    if (n <= 0 || N <= 0) return;
+    const size_t total = (size_t)n * N;
+    const int grid = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
+    tall_small_kernel<<<grid, 256, 0, st>>>(X, ldx, n, K, Tm, ldt, tT, N, C, ldc, alpha, D, beta);
 }
 
 void launch_fill(double* x, int k, double v, cudaStream_t st) {

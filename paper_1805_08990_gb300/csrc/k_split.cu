@@ -146,12 +146,10 @@ __device__ __forceinline__ void load4(const double* X, const float2* Xp, size_t 
 // d_t = round(r_t / 2^(35-7t)), r_{t+1} = r_t - d_t 2^(35-7t).
 // Each lane handles 4 consecutive entries (32-byte loads, 8-byte stores per plane).
 template <bool PAIR, int NS>
-__global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restrict__ X, const float2* __restrict__ Xp,
-                                                         int rows, int cols, int ldx, __nv_bfloat16* __restrict__ out,
-                                                         int Kp, float* __restrict__ scale, int prow) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * 8 + warp;
-    if (row >= rows) return;
+__device__ __forceinline__ void slice_row_warp(const double* __restrict__ X, const float2* __restrict__ Xp, int row,
+                                               int cols, int ldx, __nv_bfloat16* __restrict__ out, int Kp,
+                                               float* __restrict__ scale, int prow) {
+    const int lane = threadIdx.x & 31;
     const size_t base = (size_t)row * ldx;
     const bool vec = (ldx % 2) == 0;
     double d[4];
@@ -209,6 +207,32 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restric
             *reinterpret_cast<uint2*>(out + t * plane + o) = w;
         }
     }
+}
+
+template <bool PAIR, int NS>
+__global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restrict__ X, const float2* __restrict__ Xp,
+                                                         int rows, int cols, int ldx, __nv_bfloat16* __restrict__ out,
+                                                         int Kp, float* __restrict__ scale, int prow) {
+    const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (row >= rows) return;
+    slice_row_warp<PAIR, NS>(X, Xp, row, cols, ldx, out, Kp, scale, prow);
+}
+
+// Grouped slicing (serving): the rows of several problems laid end to end,
+// a warp per row; warp w finds its problem by a binary search over row0.
+template <bool PAIR, int NS>
+__global__ void __launch_bounds__(256) slice_rows_grouped_kernel(const SliceDesc* __restrict__ d, int nd,
+                                                                 int total_rows) {
+    const int g = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (g >= total_rows) return;
+    int lo = 0, hi = nd - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d[mid].row0 <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    const SliceDesc& q = d[lo];
+    slice_row_warp<PAIR, NS>(q.X, q.Xp, g - q.row0, q.cols, q.ldx, q.out, q.Kp, q.scale, q.prow);
 }
 
 // Long rows (Kp > 1024): one CTA of 256 threads per row; each thread keeps G
@@ -307,6 +331,23 @@ static void slice_launch(const double* X, const float2* Xp, int rows, int cols, 
     else
         slice_rows_kernel<PAIR, NS><<<(rows + 7) / 8, 256, 0, st>>>(X, Xp, rows, cols, ldx, sb.data, sb.Kp, sb.scale,
                                                                      pr);
+}
+
+dme_status launch_slice_grouped(std::vector<SliceDesc>& items, bool pair, cudaStream_t st, DescArena* arena) {
+    int total = 0;
+    for (auto& it : items) {
+        if (it.ns != 4 || it.rows <= 0) return set_error("grouped slicing: 4 slices and rows > 0"), DME_EINVAL;
+        it.row0 = total;
+        total += it.rows;
+    }
+    if (total == 0) return DME_OK;
+    const SliceDesc* dd = static_cast<const SliceDesc*>(arena->put(items.data(), items.size() * sizeof(SliceDesc)));
+    if (!dd) return set_error("grouped slicing: descriptor arena full"), DME_ENOMEM;
+    const int grid = (total + 7) / 8;
+    if (pair) slice_rows_grouped_kernel<true, 4><<<grid, 256, 0, st>>>(dd, (int)items.size(), total);
+    else slice_rows_grouped_kernel<false, 4><<<grid, 256, 0, st>>>(dd, (int)items.size(), total);
+    DME_CUDA_TRY(cudaGetLastError());
+    return DME_OK;
 }
 
 void launch_slice_rows_f64(const double* X, int rows, int cols, int ldx, const SliceBuf& sb, cudaStream_t st) {

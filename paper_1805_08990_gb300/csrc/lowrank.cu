@@ -68,6 +68,7 @@ struct dme_lr_s {
     double *L = nullptr, *L2 = nullptr, *d = nullptr, *d2 = nullptr;   // n x rcap, rcap
     double* LQ = nullptr;                                            // C^T, n x p
     double *G = nullptr, *Vt = nullptr, *lam = nullptr, *T = nullptr;  // rcap x rcap work
+    double *J1 = nullptr, *J2 = nullptr, *J3 = nullptr, *J4 = nullptr;  // rcap x rcap eigensolver work
     double *Gm = nullptr, *H = nullptr, *VtH = nullptr, *lamH = nullptr, *F = nullptr, *Y = nullptr, *Z = nullptr;
     double* Pout = nullptr;   // n x n, allocated on the first dense output
     int* kdev = nullptr;
@@ -127,6 +128,21 @@ dme_status gemm_ws(dme_lr_t lr, const GemmProb& g, cudaStream_t st);
 // into K chunks, one grouped launch, then summed in chunk order.
 dme_status gemm(dme_lr_t lr, const GemmProb& g, cudaStream_t st) {
     if (g.M <= 0 || g.N <= 0) return DME_OK;
+    if (g.transA && !g.transB && g.M * g.N <= 1024 && g.K >= 1024) {
+        // X^T Y of two tall blocks with a small result: row chunks summed per CTA
+        const size_t mn = (size_t)g.M * g.N;
+        const int smax = (int)std::min<size_t>(2048, lr->ws_doubles / mn);
+        const int chunk = std::max(64, (g.K + smax - 1) / smax);
+        const int S = (g.K + chunk - 1) / chunk;
+        launch_tsgemm(g.A, g.lda, g.M, g.B, g.ldb, g.N, g.K, chunk, lr->ws, st);
+        launch_splitk_reduce(lr->ws, S, g.M, g.N, g.C, g.ldc, g.alpha, g.D1, g.b1, g.tri, st);
+        return DME_OK;
+    }
+    if (!g.transA && !g.tri && !g.D2 && !g.D3 && g.K <= 64 && g.N <= 64 && g.M >= 2048 && g.C != g.A) {
+        // tall X times a small matrix: one thread per output entry, the small factor in shared memory
+        launch_tall_small(g.A, g.lda, g.M, g.K, g.B, g.ldb, g.transB, g.N, g.C, g.ldc, g.alpha, g.D1, g.b1, st);
+        return DME_OK;
+    }
     const long tiles64 = (long)((g.M + 63) / 64) * ((g.N + 63) / 64);
     if (tiles64 <= 16 && g.K >= 1024) return gemm_ws(lr, g, st);
     std::vector<GemmProb> v{g};
@@ -158,6 +174,31 @@ dme_status gemm_ws(dme_lr_t lr, const GemmProb& g, cudaStream_t st) {
     return DME_OK;
 }
 
+// Eigen-decomposition of the r x r Gram matrix lr->G: eigenvalues in lr->lam,
+// eigenvectors in the rows of lr->Vt.  Two passes for 8 <= r <= 176: a
+// single-precision Jacobi solve gives X (rows about orthonormal to 1e-7); two
+// Newton-Schulz steps X <- (3X - (X X^T) X) / 2 make the rows orthonormal in
+// FP64; the FP64 Jacobi solver then diagonalises X G X^T, which is diagonal to
+// about 1e-7 already, in a few sweeps; the eigenvectors are the rows of V2 X.
+dme_status eig_gram(dme_lr_t lr, int r) {
+    cudaStream_t st = lr->st;
+    const int rc = lr->rcap;
+    if (r < 8 || r > LR_JACOBI_F32_MAX)
+        return launch_jacobi_eig(lr->G, rc, r, lr->Vt, rc, lr->lam, lr->status, st);
+    DME_TRY(launch_jacobi_eig(lr->G, rc, r, lr->J1, rc, lr->lam, lr->status, st, true));
+    double* X = lr->J1;
+    double* Xn = lr->J3;
+    for (int it = 0; it < 2; ++it) {
+        DME_TRY(gemm(lr, mk(r, r, r, X, rc, 0, X, rc, 1, lr->J2, rc, 1.0, 1), st));                  // X X^T
+        DME_TRY(gemm(lr, mk(r, r, r, lr->J2, rc, 0, X, rc, 0, Xn, rc, -0.5, 0, X, 1.5), st));        // (3X - YX)/2
+        std::swap(X, Xn);
+    }
+    DME_TRY(gemm(lr, mk(r, r, r, lr->G, rc, 0, X, rc, 1, lr->J2, rc, 1.0), st));                     // G X^T
+    DME_TRY(gemm(lr, mk(r, r, r, X, rc, 0, lr->J2, rc, 0, lr->J4, rc, 1.0, 1), st));                 // X G X^T
+    DME_TRY(launch_jacobi_eig(lr->J4, rc, r, lr->J2, rc, lr->lam, lr->status, st));
+    return gemm(lr, mk(r, r, r, lr->J2, rc, 0, X, rc, 0, lr->Vt, rc, 1.0), st);                      // V2 X
+}
+
 // Compress the factor (L, d) with r columns (leading dimension ld) in place;
 // L2 is an n x ld work buffer.  Reads the new rank back to the host.
 dme_status compress(dme_lr_t lr, double* L, double* L2, double* d, int ld, int& r) {
@@ -166,7 +207,7 @@ dme_status compress(dme_lr_t lr, double* L, double* L2, double* d, int ld, int& 
     const int n = lr->n;
     launch_copy_cols(L2, ld, L, ld, n, r, 1.0, d, st);                                     // Lt = L d^{1/2}
     DME_TRY(gemm(lr, mk(r, r, n, L2, ld, 1, L2, ld, 0, lr->G, lr->rcap, 1.0, 1), st));          // Lt^T Lt
-    DME_TRY(launch_jacobi_eig(lr->G, lr->rcap, r, lr->Vt, lr->rcap, lr->lam, lr->status, st));
+    DME_TRY(eig_gram(lr, r));
     launch_lr_select(lr->lam, lr->Vt, lr->rcap, r, lr->tol, 1, lr->T, lr->rcap, d, lr->kdev, st);
     int k = 0;
     DME_CUDA_TRY(cudaMemcpyAsync(&k, lr->kdev, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -606,6 +647,10 @@ dme_status lr_setup(dme_lr_t lr, const dme_plan_desc* desc, const double* C, int
     DME_TRY(lr_alloc(lr, &lr->Vt, rc * rc));
     DME_TRY(lr_alloc(lr, &lr->lam, rc));
     DME_TRY(lr_alloc(lr, &lr->T, rc * rc));
+    DME_TRY(lr_alloc(lr, &lr->J1, rc * rc));
+    DME_TRY(lr_alloc(lr, &lr->J2, rc * rc));
+    DME_TRY(lr_alloc(lr, &lr->J3, rc * rc));
+    DME_TRY(lr_alloc(lr, &lr->J4, rc * rc));
     DME_TRY(lr_alloc(lr, &lr->Gm, rc * m));
     DME_TRY(lr_alloc(lr, &lr->H, m * m));
     DME_TRY(lr_alloc(lr, &lr->VtH, m * m));
@@ -791,7 +836,7 @@ dme_status dme_lr_plan_csr(const dme_plan_desc* desc, int nnz, const int* rowptr
         const size_t rc = rmax;
         DME_TRY(lr_alloc(lr.get(), &lr->Wa, (size_t)n * rc));
         DME_TRY(lr_alloc(lr.get(), &lr->Wb, (size_t)n * rc));
-        DME_TRY(lr_alloc(lr.get(), &lr->lpart, 2 * (size_t)leja_blocks(n)));
+        DME_TRY(lr_alloc(lr.get(), &lr->lpart, 2 * (size_t)leja_part_blocks(n, rmax)));
         DME_TRY(lr_alloc(lr.get(), &lr->lnorm, 16));
         DME_TRY(lr_check(lr.get(), "dme_lr_plan_csr"));
         *out = lr.release();

@@ -328,12 +328,38 @@ dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
             // the split congruence G P G^T of every request: slice P, grouped U = G P,
             // slice U, grouped G U^T (upper tiles, FP64 + W / tQ, mirrored)
             std::vector<OzGroupDesc> o1, o2;
+            std::vector<SliceDesc> s1, s2;
+            for (Req* r : L.sc) {
+                dme_plan_t p = r->plan;
+                const int n = p->n;
+                SliceDesc a;
+                std::memset(&a, 0, sizeof(a));
+                a.X = r->P;
+                a.rows = n;
+                a.cols = n;
+                a.ldx = n;
+                a.out = p->psl.data;
+                a.Kp = p->psl.Kp;
+                a.ns = p->psl.ns;
+                a.prow = p->psl.rows;
+                a.scale = p->psl.scale;
+                s1.push_back(a);
+                SliceDesc b = a;
+                b.X = nullptr;
+                b.Xp = p->U;
+                b.out = p->usl.data;
+                b.Kp = p->usl.Kp;
+                b.ns = p->usl.ns;
+                b.prow = p->usl.rows;
+                b.scale = p->usl.scale;
+                s2.push_back(b);
+            }
+            DME_TRY(launch_slice_grouped(s1, false, s->st, &s->arena));
             for (Req* r : L.sc) {
                 dme_plan_t p = r->plan;
                 const Op& o = p->ops[k];
                 const EWEntry& e = p->ew[o.ew];
                 const int n = p->n;
-                launch_slice_rows_f64(r->P, n, n, n, p->psl, s->st);
                 OzGroupDesc a;
                 std::memset(&a, 0, sizeof(a));
                 a.tmA = e.Gsl.tmap;
@@ -372,8 +398,7 @@ dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
                 o2.push_back(b);
             }
             DME_TRY(launch_ozaki_grouped(o1, nullptr, s->st, &s->arena));
-            for (Req* r : L.sc)
-                launch_slice_rows_pair(r->plan->U, r->plan->n, r->plan->n, r->plan->n, r->plan->usl, s->st);
+            DME_TRY(launch_slice_grouped(s2, true, s->st, &s->arena));
             DME_TRY(launch_ozaki_grouped(o2, nullptr, s->st, &s->arena));
         }
         if (!L.ric.empty()) DME_TRY(launch_riccati_grouped(L.ric, nullptr, s->st, &s->arena));
@@ -517,7 +542,7 @@ dme_status dme_server_create(size_t hbm_budget_bytes, int max_slots, dme_server_
     // groups and one Riccati group per stage, each put 256-byte aligned
     constexpr size_t kMaxStages = 8;
     s->arena.cap = kMaxStages * (2 * sizeof(GemmProb) * max_slots + 2 * sizeof(OzGroupDesc) * max_slots +
-                                 riccati_desc_bytes() * max_slots + 5 * 256);
+                                 2 * sizeof(SliceDesc) * max_slots + riccati_desc_bytes() * max_slots + 7 * 256);
     if (e == cudaSuccess) e = cudaMalloc(&s->arena.dev, s->arena.cap);
     if (e == cudaSuccess) e = cudaMalloc(&s->tune_desc, sizeof(GemmProb) * max_slots);
     if (e != cudaSuccess) {

@@ -62,6 +62,17 @@ struct OzGroupDesc {
     int start;            // first tile index (set by the launcher)
 };
 
+// One problem of a grouped slicing launch (rows of X or of pair matrix Xp).
+struct SliceDesc {
+    const double* X;
+    const float2* Xp;
+    int rows, cols, ldx;
+    __nv_bfloat16* out;
+    int Kp, ns, prow;
+    float* scale;
+    int row0;             // set by the launcher
+};
+
 int slice_kpad(int k);
 size_t slice_buf_bytes(int rows, int k, int ns);
 dme_status make_slice_tmap(const SliceBuf& sb, CUtensorMap* out);
@@ -69,6 +80,9 @@ dme_status make_slice_tmap(const SliceBuf& sb, CUtensorMap* out);
 // (sb.ns = 4 or 5; each plane holds sb.rows rows, the ones past `rows` untouched).
 void launch_slice_rows_f64(const double* X, int rows, int cols, int ldx, const SliceBuf& sb, cudaStream_t st);
 void launch_slice_rows_pair(const float2* Xp, int rows, int cols, int ldx, const SliceBuf& sb, cudaStream_t st);
+// One launch slicing the rows of every item (4 slices each; pair: the items are
+// (hi, lo) float pairs, else FP64), descriptors staged in the arena.
+dme_status launch_slice_grouped(std::vector<SliceDesc>& items, bool pair, cudaStream_t st, DescArena* arena);
 dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzParams p, cudaStream_t st);
 // Grouped launch over independent problems; dev_desc holds items.size() descriptors.
 // Set the grouped kernel's shared-memory attribute (before any stream capture).
