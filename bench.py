@@ -212,6 +212,61 @@ def serving_stream(count: int, seed: int, rate: float, prec: str):
         dme.dme_server_destroy(srv)
 
 
+def run_config_suite(args):
+    """Steps/s of the other workload configurations (FP64 and split precision),
+    with the work per step and the rate it corresponds to: the plain DLE
+    (n = 256, Strang F1F2, h = T/100), the DRE order-study operator (n = 1024,
+    Strang and Lie F12F3, h = T/256), and the padded generalised DRE (n = 2048,
+    Strang F12F3F4, h = T/128).  Device-timed with CUDA events; one line of JSON."""
+    import torch
+    import paper_1805_08990_gb300 as dme
+    from paper_1805_08990_gb300 import build
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def t(x):
+        return None if x is None else torch.as_tensor(x, dtype=torch.float64, device=dev)
+
+    cases = [
+        ("plain DLE, Laplacian 16x16 (n=256), Strang F1F2, h = T/100", W.dle_heat(), ["F1", "F2"], "strang", 100,
+         lambda n: 2 * 3.0 * n ** 3),
+        ("DRE, convection-diffusion 32x32 (n=1024), Strang F12F3, h = T/256", W.dre_convdiff(), ["F12", "F3"],
+         "strang", 256, lambda n: 2 * 3.0 * n ** 3),
+        ("DRE, convection-diffusion 32x32 (n=1024), Lie F12F3, h = T/256", W.dre_convdiff(), ["F12", "F3"], "lie",
+         256, lambda n: 3.0 * n ** 3),
+        ("GDRE, convection-diffusion 45x45 padded to n=2048, Strang F12F3F4, h = T/128", W.gdre_convdiff_padded(),
+         ["F12", "F3", "F4"], "strang", 128, lambda n: 4 * 3.0 * n ** 3),
+    ]
+    rows = []
+    for name, pr, flows, comp, N, flops in cases:
+        row = {"workload": name, "n": pr.n}
+        for prec, kprec in (("fp64", "fp64"), ("split", "split_bf16")):
+            uses_B, uses_S = "F3" in flows, "F4" in flows
+            with torch.cuda.stream(stream):
+                plan = dme.Plan(t(pr.A), C=t(pr.C), h=pr.T / N, flows=flows, comp=comp,
+                                B=t(pr.B) if uses_B else None, R=t(pr.R) if uses_B else None,
+                                S=t(pr.S) if uses_S else None, prec=kprec, stream=stream)
+            P = torch.zeros(pr.n, pr.n, dtype=torch.float64, device=dev)
+            steps = min(N, 32) if prec == "fp64" else N
+            plan.step(P, 3)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.step(P, steps)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / steps
+            row[prec] = {"steps_per_s": 1e3 / ms, "ms_per_step": ms, "kernels_per_step": plan.kernels_per_step,
+                         "congruence_flop_per_step": flops(pr.n),
+                         "fp64_equivalent_tflops": flops(pr.n) / (ms / 1e3) / 1e12}
+            plan.close()
+        rows.append(row)
+    print(json.dumps({"config_suite": rows, "note": "flop counts are the congruences' 3 n^3 each (P E and the "
+                      "upper triangle of E^T X); split rows run 14 bf16 slice products per congruence flop"}))
+
+
 def run_serving_suite(args):
     """The serving configuration at several loads: saturation from a burst, then
     Poisson streams at 0.5, 0.9 and 1.2 times it (split precision and FP64)."""
@@ -559,6 +614,8 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--serving-requests", type=int, default=32, help="serving sample size (0: skip)")
     ap.add_argument("--no-extras", dest="extras", action="store_false", help="skip the FSAL and low-rank lines")
+    ap.add_argument("--config-suite", action="store_true",
+                    help="run only the steps/s of the other workload configurations")
     ap.add_argument("--serving-suite", type=int, default=0,
                     help="run only the serving loads 0.5/0.9/1.2 x saturation with this many split requests")
     ap.add_argument("--lowrank-steps", type=int, default=32)
@@ -572,6 +629,8 @@ def main():
         return run_gemm_only(args)
     if args.serving_suite:
         return run_serving_suite(args)
+    if args.config_suite:
+        return run_config_suite(args)
     return run_ours(args)
 
 

@@ -246,6 +246,19 @@ dme_status dme_submit(dme_server_t srv, const dme_plan_desc* desc, const double*
  * request's own error status (e.g. DME_ENOTSPD) once it has failed. */
 dme_status dme_poll(dme_server_t srv, uint64_t ticket, double* P_out, int64_t timeout_us);
 
+/* As dme_submit for a DRE, and the LQR feedback gains along the solve (§1: the
+ * optimal input is u = -R^{-1} B^T P(T - t) x): after every step k = 1..nsteps
+ * the server forms K_k = R^{-1} B^T P_k (m x n) on the device.  DME_EINVAL
+ * unless desc is a DRE/GDRE. */
+dme_status dme_submit_gain(dme_server_t server, const dme_plan_desc* desc, const double* A, const double* QorC,
+                           const double* B, const double* R, const double* S, const double* P0, double T,
+                           int nsteps, uint64_t* ticket);
+
+/* As dme_poll, and K_out (host, nsteps x m x n, row-major, step-major) receives
+ * the gains of a request submitted with dme_submit_gain (DME_EINVAL for another
+ * request; either output may be NULL). */
+dme_status dme_poll_gain(dme_server_t server, uint64_t ticket, double* P_out, double* K_out, int64_t timeout_us);
+
 /* Server statistics as a JSON object (completed, failed, resident, queued,
  * p50/p99 latency in ms, solves/s); the string stays valid until the next call. */
 const char* dme_server_stats(dme_server_t srv);

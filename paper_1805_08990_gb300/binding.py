@@ -87,6 +87,9 @@ _SIGS = {
     "dme_submit": (C.c_int, [C.c_void_p, C.POINTER(dme_plan_desc), C.c_void_p, C.c_void_p, C.c_void_p,
                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_uint64)]),
     "dme_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int64]),
+    "dme_submit_gain": (C.c_int, [C.c_void_p, C.POINTER(dme_plan_desc), C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_uint64)]),
+    "dme_poll_gain": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_int64]),
     "dme_server_stats": (C.c_char_p, [C.c_void_p]),
     "dme_server_destroy": (C.c_int, [C.c_void_p]),
     "dme_last_error": (C.c_char_p, []),
@@ -322,6 +325,23 @@ def dme_poll(srv: int, ticket: int, P_out=None, timeout_us: int = -1) -> int:
     if s in (DME_OK, DME_ENOTREADY, DME_ETIMEOUT):
         return s
     raise DmeError(s, "dme_poll", last_error())
+
+
+def dme_submit_gain(srv: int, desc: dme_plan_desc, A, QorC, B, R, S, P0, T: float, nsteps: int) -> int:
+    keep: list = []
+    tk = C.c_uint64()
+    _check(lib().dme_submit_gain(srv, C.byref(desc), _ptr(A, keep), _ptr(QorC, keep), _ptr(B, keep),
+                                 _ptr(R, keep), _ptr(S, keep), _ptr(P0, keep), float(T), int(nsteps), C.byref(tk)),
+           "dme_submit_gain")
+    return tk.value
+
+
+def dme_poll_gain(srv: int, ticket: int, P_out=None, K_out=None, timeout_us: int = -1) -> int:
+    """As dme_poll; K_out (nsteps x m x n) receives the gains K_k = R^-1 B^T P_k."""
+    s = lib().dme_poll_gain(srv, C.c_uint64(ticket), _out_ptr(P_out), _out_ptr(K_out), C.c_int64(timeout_us))
+    if s in (DME_OK, DME_ENOTREADY, DME_ETIMEOUT):
+        return s
+    raise DmeError(s, "dme_poll_gain", last_error())
 
 
 def dme_server_stats(srv: int) -> str:

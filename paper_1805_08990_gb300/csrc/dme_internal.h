@@ -173,6 +173,10 @@ size_t riccati_desc_bytes();
 // Cholesky, Y = Z L^{-T} (Y = 0 if M is not SPD, with DEV_NOTSPD set).
 dme_status launch_riccati_from_z(const double* Bt, int n, int m, double t, double* work, int* status,
                                  cudaStream_t st);
+// As launch_lqr_gain, into Kbase + (*ctr) m n (skipped once *ctr >= cap), then
+// ++*ctr on the device: for a launch sequence replayed once per step.
+dme_status launch_lqr_gain_hist(const double* P, const double* Bt, const double* LR, int n, int m, double* work,
+                                double* Kbase, int* ctr, int cap, cudaStream_t st);
 // K (m x n) = R^{-1} B^T P from Bt = B L^{-T} and L (R = L L^T); work as for launch_riccati.
 dme_status launch_lqr_gain(const double* P, const double* Bt, const double* LR, int n, int m, double* work,
                            double* K, cudaStream_t st);

@@ -448,6 +448,47 @@ __global__ void lqr_gain_kernel(const double* __restrict__ Z, const double* __re
     }
 }
 
+// The gain of step *ctr into Kbase + (*ctr) m n, then ++*ctr (a single thread,
+// after the gain kernel in stream order): one record per replayed step.
+__global__ void lqr_gain_hist_kernel(const double* __restrict__ Z, const double* __restrict__ L,
+                                     double* __restrict__ Kbase, int n, int m, const int* __restrict__ ctr,
+                                     int cap) {
+    const int k = *ctr;
+    if (k >= cap) return;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double* K = Kbase + (size_t)k * m * n;
+    double x[32];
+    for (int r = m - 1; r >= 0; --r) {
+        double s = Z[(size_t)j * m + r];
+        for (int c = r + 1; c < m; ++c) s -= L[c * m + r] * x[c];
+        x[r] = s / L[r * m + r];
+        K[(size_t)r * n + j] = x[r];
+    }
+}
+
+__global__ void counter_inc_kernel(int* ctr) { *ctr += 1; }
+
+dme_status launch_lqr_gain_hist(const double* P, const double* Bt, const double* LR, int n, int m, double* work,
+                                double* Kbase, int* ctr, int cap, cudaStream_t st) {
+    RicBatch b;
+    std::memset(&b, 0, sizeof(b));
+    RicDesc& d = b.local[0];
+    d.P = const_cast<double*>(P);
+    d.Bt = Bt;
+    d.Z = work;
+    d.Y = d.Z + (size_t)n * m;
+    d.Gpart = d.Y + (size_t)n * m;
+    d.n = n;
+    d.m = m;
+    b.nd = 1;
+    riccati_z_kernel<<<rz_blocks(n), 256, 0, st>>>(b);       // Z = P Bt (P is only read)
+    lqr_gain_hist_kernel<<<(n + 127) / 128, 128, 0, st>>>(d.Z, LR, Kbase, n, m, ctr, cap);
+    counter_inc_kernel<<<1, 1, 0, st>>>(ctr);
+    DME_CUDA_TRY(cudaGetLastError());
+    return DME_OK;
+}
+
 dme_status launch_lqr_gain(const double* P, const double* Bt, const double* LR, int n, int m, double* work,
                            double* K, cudaStream_t st) {
     RicBatch b;

@@ -62,6 +62,10 @@ struct Req {
     int done_steps = 0;
     size_t reserved = 0;
     std::vector<double> out;
+    bool gain = false;              // record K_k = R^{-1} B^T P_k after every step
+    double* Kh = nullptr;           // gain history on the device (nsteps x m x n)
+    int* kctr = nullptr;            // steps recorded so far (device)
+    std::vector<double> kout;
     dme_status status = DME_OK;
     std::string err;
     double t_submit = 0, t_done = 0;
@@ -118,6 +122,10 @@ void finish(dme_server_t s, Req* r, dme_status st, const std::string& err) {
 void release(dme_server_t s, Req* r) {
     if (r->P && r->plan) cudaFreeAsync(r->P, r->plan->st);
     r->P = nullptr;
+    if (r->Kh && r->plan) cudaFreeAsync(r->Kh, r->plan->st);
+    if (r->kctr && r->plan) cudaFreeAsync(r->kctr, r->plan->st);
+    r->Kh = nullptr;
+    r->kctr = nullptr;
     if (r->plan) free_plan(r->plan);
     r->plan = nullptr;
     std::lock_guard<std::mutex> g(s->mu);
@@ -158,6 +166,12 @@ void admit_loop(dme_server_t s) {
             r->plan = p;
             cudaError_t e = cudaMallocAsync(&r->P, nn * sizeof(double), p->st);
             if (e == cudaSuccess) e = cudaMemcpyAsync(r->P, r->P0.data(), nn * sizeof(double), cudaMemcpyHostToDevice, p->st);
+            if (e == cudaSuccess && r->gain) {
+                const size_t kn = (size_t)r->nsteps * r->desc.m * r->desc.n;
+                e = cudaMallocAsync(&r->Kh, kn * sizeof(double), p->st);
+                if (e == cudaSuccess) e = cudaMallocAsync(&r->kctr, sizeof(int), p->st);
+                if (e == cudaSuccess) e = cudaMemsetAsync(r->kctr, 0, sizeof(int), p->st);
+            }
             if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
             if (e != cudaSuccess) {
                 cudaGetLastError();
@@ -177,7 +191,8 @@ void admit_loop(dme_server_t s) {
         std::vector<double>().swap(r->QC);
         std::vector<double>().swap(r->P0);
         std::lock_guard<std::mutex> g(s->mu);
-        const size_t actual = p->bytes + nn * sizeof(double);
+        const size_t actual = p->bytes + nn * sizeof(double) +
+                              (r->gain ? (size_t)r->nsteps * r->desc.m * r->desc.n * sizeof(double) : 0);
         s->reserved = s->reserved - r->reserved + actual;
         r->reserved = actual;
         r->state = Q_RESIDENT;
@@ -403,6 +418,12 @@ dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
         }
         if (!L.ric.empty()) DME_TRY(launch_riccati_grouped(L.ric, nullptr, s->st, &s->arena));
     }
+    // after the step: the gain of every request that records it (the launches read
+    // the device step counter, so the captured round stays valid for every replay)
+    for (Req* r : res)
+        if (r->gain)
+            DME_TRY(launch_lqr_gain_hist(r->P, r->plan->Bt, r->plan->LR, r->plan->n, r->plan->m, r->plan->rwork,
+                                         r->Kh, r->kctr, r->nsteps, s->st));
     DME_CUDA_TRY(cudaGetLastError());
     return DME_OK;
 }
@@ -502,6 +523,11 @@ void step_loop(dme_server_t s) {
                     r->out.resize((size_t)r->desc.n * r->desc.n);
                     cudaError_t e = cudaMemcpyAsync(r->out.data(), r->P, r->out.size() * sizeof(double),
                                                     cudaMemcpyDeviceToHost, s->st);
+                    if (e == cudaSuccess && r->gain) {
+                        r->kout.resize((size_t)r->nsteps * r->desc.m * r->desc.n);
+                        e = cudaMemcpyAsync(r->kout.data(), r->Kh, r->kout.size() * sizeof(double),
+                                            cudaMemcpyDeviceToHost, s->st);
+                    }
                     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
                     if (e != cudaSuccess) {
                         rs = DME_ECUDA;
@@ -570,9 +596,36 @@ dme_status dme_server_create(size_t hbm_budget_bytes, int max_slots, dme_server_
     return DME_OK;
 }
 
+}  // extern "C"
+
+namespace {
+dme_status submit_impl(dme_server_t s, const dme_plan_desc* desc, const double* A, const double* QorC,
+                       const double* B, const double* R, const double* S, const double* P0, double T, int nsteps,
+                       bool gain, uint64_t* ticket);
+}
+
+extern "C" {
+
 dme_status dme_submit(dme_server_t s, const dme_plan_desc* desc, const double* A, const double* QorC,
                       const double* B, const double* R, const double* S, const double* P0, double T, int nsteps,
                       uint64_t* ticket) {
+    return submit_impl(s, desc, A, QorC, B, R, S, P0, T, nsteps, false, ticket);
+}
+
+dme_status dme_submit_gain(dme_server_t s, const dme_plan_desc* desc, const double* A, const double* QorC,
+                           const double* B, const double* R, const double* S, const double* P0, double T,
+                           int nsteps, uint64_t* ticket) {
+    if (!desc || (desc->eq != DME_DRE && desc->eq != DME_GDRE))
+        return set_error("dme_submit_gain: the gain needs a DRE (B, R)"), DME_EINVAL;
+    return submit_impl(s, desc, A, QorC, B, R, S, P0, T, nsteps, true, ticket);
+}
+
+}  // extern "C"
+
+namespace {
+dme_status submit_impl(dme_server_t s, const dme_plan_desc* desc, const double* A, const double* QorC,
+                       const double* B, const double* R, const double* S, const double* P0, double T, int nsteps,
+                       bool gain, uint64_t* ticket) {
     if (!s || !desc || !A || !QorC || !P0 || !ticket) return set_error("missing argument"), DME_EINVAL;
     if (!(T > 0.0) || nsteps < 1) return set_error("need T > 0 and nsteps >= 1"), DME_EINVAL;
     if (desc->prec != DME_FP64 && desc->prec != DME_SPLIT_BF16) return set_error("bad prec"), DME_EINVAL;
@@ -601,6 +654,7 @@ dme_status dme_submit(dme_server_t s, const dme_plan_desc* desc, const double* A
         if (S) r->S.assign(S, S + nn);
         r->T = T;
         r->nsteps = nsteps;
+        r->gain = gain;
         std::lock_guard<std::mutex> g(s->mu);
         if (plan_estimate_bytes(r->desc) > s->budget)
             return set_error("request footprint exceeds the server's HBM budget"), DME_ENOMEM;
@@ -618,7 +672,7 @@ dme_status dme_submit(dme_server_t s, const dme_plan_desc* desc, const double* A
     }
 }
 
-dme_status dme_poll(dme_server_t s, uint64_t ticket, double* P_out, int64_t timeout_us) {
+dme_status poll_impl(dme_server_t s, uint64_t ticket, double* P_out, double* K_out, int64_t timeout_us) {
     if (!s) return set_error("server is NULL"), DME_EINVAL;
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->reqs.find(ticket);
@@ -634,10 +688,27 @@ dme_status dme_poll(dme_server_t s, uint64_t ticket, double* P_out, int64_t time
         }
     }
     dme_status st = r->status;
+    if (st == DME_OK && K_out && !r->gain) {
+        set_error("dme_poll_gain: the request was not submitted with dme_submit_gain");
+        st = DME_EINVAL;
+    }
     if (st == DME_OK && P_out) std::memcpy(P_out, r->out.data(), r->out.size() * sizeof(double));
-    if (st != DME_OK) set_error(r->err);
+    if (st == DME_OK && K_out) std::memcpy(K_out, r->kout.data(), r->kout.size() * sizeof(double));
+    if (r->status != DME_OK) set_error(r->err);
     s->reqs.erase(it);
     return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+dme_status dme_poll(dme_server_t s, uint64_t ticket, double* P_out, int64_t timeout_us) {
+    return poll_impl(s, ticket, P_out, nullptr, timeout_us);
+}
+
+dme_status dme_poll_gain(dme_server_t s, uint64_t ticket, double* P_out, double* K_out, int64_t timeout_us) {
+    return poll_impl(s, ticket, P_out, K_out, timeout_us);
 }
 
 const char* dme_server_stats(dme_server_t s) {

@@ -184,3 +184,35 @@ def test_back_to_back_requests_get_their_own_round(server):
         single = np.empty((pr.n, pr.n))
         plan.solve(pr.P0, pr.T, N, single)
         assert np.array_equal(got, single), k
+
+
+def test_gain_history_in_serving(server):
+    """dme_submit_gain: the gains K_k = R^-1 B^T P_k after every step, recorded on
+    the device inside the captured rounds; against the single plan's states and
+    its dme_gain (bit for bit) and against the oracle's gain of the oracle's
+    states; a mix of gain and plain requests; a DLE is refused."""
+    pr = W.dre_convdiff(nx=8, m=3, p=2, seed=4)
+    N = 6
+    d = _desc(pr, N)
+    tk = dme.dme_submit_gain(server, d, pr.A, pr.C, pr.B, pr.R, None, pr.P0, pr.T, N)
+    others = [_submit(server, q, n) for q, n in _requests()[:3]]
+    Pout = np.empty((pr.n, pr.n))
+    K = np.empty((N, pr.B.shape[1], pr.n))
+    assert dme.dme_poll_gain(server, tk, Pout, K, -1) == dme.DME_OK
+    plan = dme.Plan(dev(pr.A), C=dev(pr.C), h=pr.T / N, flows=["F12", "F3"], B=dev(pr.B), R=dev(pr.R))
+    P = dev(pr.P0)
+    Kk = torch.empty(pr.B.shape[1], pr.n, dtype=torch.float64, device=P.device)
+    Po = pr.P0.copy()
+    for k in range(N):
+        plan.step(P, 1)
+        plan.gain(P, Kk)
+        assert np.array_equal(K[k], Kk.cpu().numpy()), k
+        Po = O.solve(pr.A, pr.Q, Po, pr.T / N, 1, "strang", ["F12", "F3"], B=pr.B, R=pr.R)
+        ref = O.lqr_gain(Po, pr.B, pr.R)
+        assert rel(K[k], ref) < FP64_TOL
+    assert np.array_equal(Pout, P.cpu().numpy())
+    for t in others:
+        assert dme.dme_poll(server, t, None, -1) == dme.DME_OK
+    dl = W.dle_heat(nx=5)
+    with pytest.raises(dme.DmeError):
+        dme.dme_submit_gain(server, _desc(dl, 4, flows=("F12",)), dl.A, dl.C, None, None, None, dl.P0, dl.T, 4)
