@@ -37,3 +37,35 @@ def test_large_dre_two_steps(case, prec, tol):
     got = host(P)
     assert rel(got, ref) < tol
     assert np.array_equal(got, got.T)
+
+
+@pytest.fixture(scope="module")
+def gdre_case():
+    """The generalised DRE configuration at full size: convection-diffusion
+    45 x 45 zero-padded to n = 2048, dense S on the active block, B 2048 x 4,
+    R = I_4, C 5 x 2048, Strang F12F3F4 with h = T/128, two steps from a PSD
+    state supported on the active block."""
+    require_gpu()
+    pr = W.gdre_convdiff_padded()
+    h = pr.T / 128
+    na = pr.meta["n_active"]
+    P0 = np.zeros((pr.n, pr.n))
+    P0[:na, :na] = W.random_psd(na, 23, rank=32, scale=1.0)
+    plan = O.Plan(pr.A, pr.Q, pr.B, pr.R, pr.S)
+    P = P0
+    for _ in range(STEPS):
+        P = plan.step(P, "strang", ["F12", "F3", "F4"], h)
+    return pr, h, P0, P
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", FP64_TOL), ("split_bf16", SPLIT_TOL)])
+def test_generalised_dre_n2048_two_steps(gdre_case, prec, tol):
+    pr, h, P0, ref = gdre_case
+    plan = plan_for(pr, ["F12", "F3", "F4"], "strang", h, prec=prec)
+    P = dev(P0)
+    plan.step(P, STEPS)
+    got = host(P)
+    assert rel(got, ref) < tol
+    assert np.array_equal(got, got.T)
+    na = pr.meta["n_active"]
+    assert np.all(got[na:, :] == 0) and np.all(got[:, na:] == 0)
