@@ -23,6 +23,7 @@ __all__ = [
     "laplacian_2d", "convection_diffusion_2d", "zero_pad", "Problem",
     "dle_heat", "dre_convdiff", "gdre_convdiff_padded", "dre_heat_large",
     "random_psd", "serving_requests", "materialize", "fe_heat_mass", "SCHEMES",
+    "stochastic_heat_csr", "gdre_stochastic_heat",
 ]
 
 
@@ -147,6 +148,55 @@ def gdre_convdiff_padded(nx: int = 45, n_pad: int = 2048, m: int = 4, p: int = 5
     return Problem("gdre_convdiff_padded", A, zero_pad(C_a, p, n), np.zeros((n, n)), T,
                    B=zero_pad(B_a, n, m), R=np.eye(m), S=zero_pad(S_a, n, n),
                    meta={"nx": nx, "n_active": na, "seed": seed})
+
+
+def stochastic_heat_csr(nx: int, control: bool = True):
+    """Sparse data in the shape of the stochastic heat transfer problem of
+    Example 2 (§5.1.2), on an nx x nx interior grid (dx = 1/(nx+1), n = nx^2):
+    no randomness is drawn.
+
+    * Laplacian with homogeneous Dirichlet conditions on the south (j = 0) and
+      north (j = nx-1) edges.
+    * West edge (i = 0): the control enters as the boundary value x = u, so
+      B (n x 1) holds 1/dx^2 in the west-edge rows.  Without control (the
+      generalised DLE of the example) B is None and that edge is homogeneous
+      Dirichlet, which leaves A unchanged.
+    * East edge (i = nx-1): the Robin condition n . grad x = 0.5 (0.5 + dW/dt) x
+      with a ghost value; its deterministic part gives the diagonal
+      (-3 + 0.25 dx)/dx^2 there, its noise part S = diag(0.5/dx) on the
+      east-edge rows (nx nonzeros), zero elsewhere.
+    * C = (1/n) (1, ..., 1), the mean; T = 1/2.
+
+    Returns (A, B, S, C, T) with A and S scipy.sparse CSR matrices."""
+    import scipy.sparse as sp
+    n = nx * nx
+    dx = 1.0 / (nx + 1)
+    T1 = sp.diags([np.ones(nx - 1), -2.0 * np.ones(nx), np.ones(nx - 1)], [-1, 0, 1])
+    I = sp.identity(nx)
+    east = np.arange(nx) * nx + (nx - 1)
+    west = np.arange(nx) * nx
+    # the east diagonal moves from -4/dx^2 to (-3 + 0.25 dx)/dx^2
+    A = (sp.kron(I, T1, format="csr") + sp.kron(T1, I, format="csr")) / (dx * dx)
+    A = (A + sp.csr_matrix((np.full(nx, (1.0 + 0.25 * dx) / (dx * dx)), (east, east)), shape=(n, n))).tocsr()
+    A.eliminate_zeros()
+    A.sort_indices()
+    S = sp.csr_matrix((np.full(nx, 0.5 / dx), (east, east)), shape=(n, n))
+    B = None
+    if control:
+        B = np.zeros((n, 1))
+        B[west, 0] = 1.0 / (dx * dx)
+    C = np.full((1, n), 1.0 / n)
+    return A, B, S, C, 0.5
+
+
+def gdre_stochastic_heat(nx: int = 10, control: bool = True) -> Problem:
+    """``stochastic_heat_csr`` as a dense Problem (GDRE with R = I_1, or the
+    GDLE when control is False); P0 = 0."""
+    A, B, S, C, T = stochastic_heat_csr(nx, control)
+    n = nx * nx
+    return Problem("gdre_stochastic_heat" if control else "gdle_stochastic_heat", A.toarray(), C,
+                   np.zeros((n, n)), T, B=B, R=np.eye(1) if control else None, S=S.toarray(),
+                   meta={"nx": nx, "control": control})
 
 
 def dre_heat_large(nx: int = 64, m: int = 8, p: int = 8, T: float = 1.0, seed: int = 0) -> Problem:

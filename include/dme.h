@@ -196,19 +196,23 @@ dme_status dme_lr_plan(const dme_plan_desc* desc, const double* A, const double*
 
 /* The factored path for a sparse A, which is never formed densely: A in CSR
  * (rowptr n + 1, colidx and vals nnz, 0-based, host or device, copied), C
- * (p x n) and, for a DRE, B and R as in dme_plan.  e^{t A^T} L is applied by
+ * (p x n) and, for a DRE / GDRE, B and R as in dme_plan.  e^{t A^T} L is applied by
  * Newton interpolation at Leja points (the action the paper computes with
  * `expleja`, §3): a Gershgorin interval [a, b] of A^T, A^T = c I + g X with
  * X's spectrum in [-2, 2], substeps of length t with t g <= 4, at most 80
  * Leja points per substep, and the series stopped after two terms below
- * 1e-15 times the partial sum (Frobenius norms).  desc: q_is_factor = 1, prec
- * = DME_FP64, eq DLE or DRE, flows among F1, F2, F12 (W_t by Gauss-Legendre
- * quadrature, each node's exponential again by Leja interpolation) and F3.
- * n is not limited to 16384; dme_lr_solve's P_out must then be NULL.
- * DME_EINVAL for a malformed CSR matrix (column index out of range, rowptr
- * not non-decreasing from 0 to nnz). */
+ * 1e-15 times the partial sum (Frobenius norms).  For GDLE / GDRE, S (of the
+ * S P S^T term, Eq. lyapGen; n x n) is given in CSR too (nnz_s, s_rowptr,
+ * s_colidx, s_vals, same conventions and checks; ignored for DLE / DRE) and
+ * T4 forms S L and S^2 L by a sparse product (§2.3).  desc: q_is_factor = 1,
+ * prec = DME_FP64, flows among F1, F2, F12 (W_t by Gauss-Legendre quadrature,
+ * each node's exponential again by Leja interpolation), F3 (DRE / GDRE) and
+ * F4 (GDLE / GDRE).  n is not limited to 16384; dme_lr_solve's P_out must
+ * then be NULL.  DME_EINVAL for a malformed CSR matrix (column index out of
+ * range, rowptr not non-decreasing from 0 to nnz). */
 dme_status dme_lr_plan_csr(const dme_plan_desc* desc, int nnz, const int* rowptr, const int* colidx,
-                           const double* vals, const double* C, const double* B, const double* R,
+                           const double* vals, const double* C, const double* B, const double* R, int nnz_s,
+                           const int* s_rowptr, const int* s_colidx, const double* s_vals,
                            const dme_lr_opts* opts, void* cuda_stream, dme_lr_t* out);
 
 /* N = nsteps composition steps from P0 = L0 D0 L0^T (L0 n x r0, D0 r0 x r0

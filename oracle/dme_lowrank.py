@@ -149,7 +149,7 @@ class LowRankPlan:
         self.DQ = np.eye(C.shape[0])
         self.B = None if B is None else np.asarray(B, dtype=np.float64)
         self.R = None if R is None else np.asarray(R, dtype=np.float64)
-        self.S = None if S is None else np.asarray(S, dtype=np.float64)
+        self.S = None if S is None else (S.tocsr() if hasattr(S, "tocsr") else np.asarray(S, dtype=np.float64))
         self.q, self.tol = q, tol
         self._E, self._W = {}, {}
 

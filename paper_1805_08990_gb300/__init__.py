@@ -113,19 +113,25 @@ class LowRankPlan:
         self.handle = dme_lr_plan(self.desc, A, C, B, R, S, quad_nodes, rmax, tol, stream)
 
     @classmethod
-    def from_csr(cls, A_csr, C, h=1e-3, flows=("F1", "F2"), comp="strang", B=None, R=None, quad_nodes=0, rmax=0,
-                 tol=0.0, stream=None):
-        """The factored path for a sparse A (scipy.sparse matrix or anything with
-        indptr / indices / data): e^{t A^T} L by Leja interpolation."""
+    def from_csr(cls, A_csr, C, h=1e-3, flows=("F1", "F2"), comp="strang", B=None, R=None, S_csr=None,
+                 t4_rule=DME_T4_AUTO, quad_nodes=0, rmax=0, tol=0.0, stream=None):
+        """The factored path for a sparse A (and, for the generalised equations,
+        a sparse S; scipy.sparse matrices or anything with indptr / indices /
+        data): e^{t A^T} L by Leja interpolation, S L by a sparse product."""
         self = cls.__new__(cls)
         A_csr = A_csr.tocsr() if hasattr(A_csr, "tocsr") else A_csr
         n = int(A_csr.shape[0])
         m = 0 if B is None else int(B.shape[1])
         self.n, self.m = n, m
-        self.desc = make_desc(n, m=m, p=int(C.shape[0]), eq=DME_DRE if B is not None else DME_DLE, comp=comp,
-                              flows=flows, prec="fp64", h=h, q_is_factor=True)
+        eq = ("g" if S_csr is not None else "") + ("dre" if B is not None else "dle")
+        self.desc = make_desc(n, m=m, p=int(C.shape[0]), eq=EQ_IDS[eq], comp=comp, flows=flows, prec="fp64", h=h,
+                              q_is_factor=True, t4_rule=t4_rule)
+        s3 = None
+        if S_csr is not None:
+            S_csr = S_csr.tocsr() if hasattr(S_csr, "tocsr") else S_csr
+            s3 = (S_csr.indptr, S_csr.indices, S_csr.data)
         self.handle = dme_lr_plan_csr(self.desc, A_csr.indptr, A_csr.indices, A_csr.data, C, B, R, quad_nodes, rmax,
-                                      tol, stream)
+                                      tol, stream, S_csr=s3)
         return self
 
     def solve(self, T, nsteps, L0=None, D0=None, P_out=None):

@@ -66,8 +66,8 @@ _SIGS = {
     "dme_lr_plan": (C.c_int, [C.POINTER(dme_plan_desc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                               C.c_void_p, C.POINTER(dme_lr_opts), C.c_void_p, C.POINTER(C.c_void_p)]),
     "dme_lr_plan_csr": (C.c_int, [C.POINTER(dme_plan_desc), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
-                                  C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(dme_lr_opts), C.c_void_p,
-                                  C.POINTER(C.c_void_p)]),
+                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.POINTER(dme_lr_opts), C.c_void_p, C.POINTER(C.c_void_p)]),
     "dme_lr_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p,
                                C.POINTER(C.c_int)]),
     "dme_lr_factors": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
@@ -218,15 +218,23 @@ def _iptr(x, keep: list):
 
 
 def dme_lr_plan_csr(desc: dme_plan_desc, indptr, indices, data, C_factor, B=None, R=None, quad_nodes=0, rmax=0,
-                    tol=0.0, stream=None) -> int:
+                    tol=0.0, stream=None, S_csr=None) -> int:
+    """S_csr: (indptr, indices, data) of S for the generalised equations, else None."""
     keep: list = []
     out = C.c_void_p()
     opts = dme_lr_opts(int(quad_nodes), int(rmax), float(tol))
     st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     nnz = int(len(data))
+    nnz_s, sp, si, sv = 0, None, None, None
+    if S_csr is not None:
+        nnz_s = int(len(S_csr[2]))
+        sp = _iptr(S_csr[0], keep)
+        si = _iptr(S_csr[1], keep) if nnz_s else None
+        sv = _ptr(S_csr[2], keep) if nnz_s else None
     _check(lib().dme_lr_plan_csr(C.byref(desc), nnz, _iptr(indptr, keep), _iptr(indices, keep) if nnz else None,
                                  _ptr(data, keep) if nnz else None, _ptr(C_factor, keep), _ptr(B, keep),
-                                 _ptr(R, keep), C.byref(opts), st, C.byref(out)), "dme_lr_plan_csr")
+                                 _ptr(R, keep), nnz_s, sp, si, sv, C.byref(opts), st, C.byref(out)),
+           "dme_lr_plan_csr")
     return out.value
 
 

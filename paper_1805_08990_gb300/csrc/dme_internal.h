@@ -114,9 +114,12 @@ size_t jacobi_smem_bytes(int r);
 dme_status launch_jacobi_eig(const double* G, int ldg, int r, double* Vt, int ldv, double* lam, int* status,
                              cudaStream_t st, bool fp32 = false);
 // Keep eigenvalues > tol * max, ordered decreasingly: d_out, k_out, and the
-// r x k basis T (columns = eigenvectors, times lambda^{-1/2} if inv_sqrt).
+// r x k basis T (columns = eigenvectors, times lambda^{-1/2} if inv_sqrt; row a
+// also times sqrt(rowscale[a]) when rowscale is given, which may alias d_out).
 void launch_lr_select(const double* lam, const double* Vt, int ldv, int r, double tol, int inv_sqrt, double* T,
-                      int ldt, double* d_out, int* k_out, cudaStream_t st);
+                      int ldt, double* d_out, int* k_out, cudaStream_t st, const double* rowscale = nullptr);
+// G_ij *= sqrt(d_i d_j) for the r x r matrix G.
+void launch_sym_scale(double* G, int ldg, int r, const double* d, cudaStream_t st);
 // F = V diag(psi(lam)) V^T (m x m) for the factored Riccati flow over t.
 void launch_ric_weights(const double* lam, const double* Vt, int ldv, int m, double t, double* F, int ldf,
                         cudaStream_t st);
@@ -125,9 +128,10 @@ void launch_copy_cols(double* Y, int ldy, const double* X, int ldx, int n, int k
                       cudaStream_t st);
 void launch_fill(double* x, int k, double v, cudaStream_t st);
 // part[s] (M x N) = sum over rows k in [s chunk, (s+1) chunk) of X[k]^T Y[k], for
-// X (K x M), Y (K x N), M N <= 1024; ceil(K / chunk) partial products.
+// X (K x M), Y (K x N), M N <= 1024; ceil(K / chunk) partial products.  sym
+// (with X = Y): only entries i <= j are formed and written, M (M+1)/2 <= 1024.
 void launch_tsgemm(const double* X, int ldx, int M, const double* Y, int ldy, int N, int K, int chunk, double* part,
-                   cudaStream_t st);
+                   cudaStream_t st, int sym = 0);
 // C (n x N) = alpha X op(T) (+ beta D, leading dimension ldc) for a tall X (n x K)
 // and a small op(T) (K x N; T^T stored when tT), K, N <= 64; C must not overlap X.
 void launch_tall_small(const double* X, int ldx, int n, int K, const double* Tm, int ldt, int tT, int N, double* C,
@@ -136,14 +140,40 @@ void launch_tall_small(const double* X, int ldx, int n, int K, const double* Tm,
 void launch_splitk_reduce(const double* W, int S, int M, int N, double* C, int ldc, double alpha, const double* D1,
                           double b1, int tri, cudaStream_t st);
 
-// One term of the Leja-interpolation series for e^{t A^T} on an n x r block
-// (A^T in CSR): Wn = (A^T W - c W) invg - xk W, Pacc += dk Wn; norms2[0..1] =
-// |Wn|_F^2, |Pacc|_F^2 (part: 2 leja_blocks(n) doubles of scratch).
-int leja_blocks(int n);
-int leja_part_blocks(int n, int rmax);   // partial-norm slots the term kernels may use
-void launch_leja_term(const int* ptr, const int* idx, const double* val, int n, int r, const double* W, double* Wn,
-                      int ldw, double* Pacc, int ldp, double c, double invg, double xk, double dk, double* part,
-                      double* norms2, cudaStream_t st);
+// Y (n x r, ldy) = alpha S X for S in CSR and X (n x r, ldx); Y must not overlap X.
+void launch_spmm(const int* ptr, const int* idx, const double* val, int n, int r, const double* X, int ldx, double* Y,
+                 int ldy, double alpha, cudaStream_t st);
+
+// Y (n x r, ldy) = e^{t A^T} X (n x r, ldx) by Newton interpolation at Leja
+// points, all substeps in one persistent cooperative launch: per substep
+// p = d_0 v, w_{k+1} = (A^T w_k - c w_k) invg - xi_k w_k, p += d_{k+1} w_{k+1}
+// (val holds the values of A^T already multiplied by invg = 1/g),
+// stopping after two consecutive terms with |d_k| |w_k|_F <= tol |p|_F (at most
+// `terms` - 1 terms), then v = scale p.  Y may be X.  Wa, Wb: n x r scratch
+// (ldw); part: 4 leja_grid_max() doubles; sums: 4 doubles; bar: 2 unsigned.
+struct LejaCall {
+    const int* ptr;
+    const int* idx;
+    const double* val;
+    int n, r;
+    const double* X;
+    int ldx;
+    double* Y;
+    int ldy;
+    double* Wa;
+    double* Wb;
+    int ldw;
+    double c, invg, scale, tol;
+    int substeps, terms;
+    const double* xi;    // host, `terms` Leja points
+    const double* dd;    // host, `terms` divided differences
+    double* part;
+    double* sums;
+    unsigned* bar;
+    int* status;         // DEV_TIMEOUT if a grid barrier wait ran out
+};
+int leja_grid_max();
+dme_status launch_leja_apply(const LejaCall& c, cudaStream_t st);
 
 // ---------------------------------------------------------------- Riccati (T3)
 // P <- P - t Z (I + t Bt^T Z)^{-1} Z^T + q * Qadd, Z = P Bt  (Woodbury form

@@ -189,10 +189,12 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double* __restri
 // w = lambda^{-1/2} (inv_sqrt) or 1.  T has r rows (ldt).
 __global__ void __launch_bounds__(256) select_kernel(const double* __restrict__ lam, const double* __restrict__ Vt,
                                                      int ldv, int r, double tol, int inv_sqrt, double* __restrict__ T,
-                                                     int ldt, double* __restrict__ d_out, int* k_out) {
+                                                     int ldt, double* d_out, int* k_out, const double* rowscale) {
     __shared__ double smax;
     __shared__ int kcount;
+    __shared__ double rs[LR_MAX_RANK];   // sqrt(rowscale), read before d_out (which may alias it) is written
     const int tid = threadIdx.x, nt = blockDim.x;
+    for (int a = tid; a < r; a += nt) rs[a] = rowscale ? sqrt(rowscale[a]) : 1.0;
     if (tid == 0) {
         double m = 0.0;
         for (int i = 0; i < r; ++i) m = fmax(m, lam[i]);
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__(256) select_kernel(const double* __restrict__ 
         atomicAdd(&kcount, 1);
         d_out[rank] = li;
         const double w = inv_sqrt ? 1.0 / sqrt(li) : 1.0;
-        for (int a = 0; a < r; ++a) T[(size_t)a * ldt + rank] = Vt[(size_t)i * ldv + a] * w;
+        for (int a = 0; a < r; ++a) T[(size_t)a * ldt + rank] = Vt[(size_t)i * ldv + a] * w * rs[a];
     }
     __syncthreads();
     if (tid == 0) *k_out = kcount;
@@ -236,14 +238,50 @@ __global__ void ric_weights_kernel(const double* __restrict__ lam, const double*
 }
 
 // Y[i][j] = alpha * X[i][j] * (d ? sqrt(d[j]) : 1) for an n x k block.
-__global__ void copy_cols_kernel(double* __restrict__ Y, int ldy, const double* __restrict__ X, int ldx, int n, int k,
-                                 double alpha, const double* __restrict__ d) {
-    const size_t total = (size_t)n * k;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e / k), j = (int)(e % k);
-        double v = alpha * X[(size_t)i * ldx + j];
-        if (d) v *= sqrt(d[j]);
-        Y[(size_t)i * ldy + j] = v;
+// The entries (i, j) of an n x k block a thread visits in a grid-stride loop over
+// e = i k + j, walked without a division per entry.
+struct BlockEntries {
+    int i0, j0, di, dj;
+    __device__ BlockEntries(int k) {
+        const size_t first = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+        const size_t stride = (size_t)gridDim.x * blockDim.x;
+        i0 = (int)(first / k);
+        j0 = (int)(first % k);
+        di = (int)(stride / k);
+        dj = (int)(stride % k);
+    }
+    __device__ __forceinline__ void next(int& i, int& j, int k) const {
+        i += di;
+        j += dj;
+        if (j >= k) {
+            j -= k;
+            ++i;
+        }
+    }
+};
+
+// Y = alpha X diag(d)^{1/2} (d NULL: alpha X); the column scales are formed once
+// per block (a square root per entry would be FP64-issue bound).
+__global__ void __launch_bounds__(256) copy_cols_kernel(double* __restrict__ Y, int ldy, const double* __restrict__ X,
+                                                        int ldx, int n, int k, double alpha,
+                                                        const double* __restrict__ d) {
+    __shared__ double sc[LR_MAX_RANK];
+    const bool staged = k <= LR_MAX_RANK;
+    if (staged)
+        for (int j = threadIdx.x; j < k; j += blockDim.x) sc[j] = d ? alpha * sqrt(d[j]) : alpha;
+    __syncthreads();
+    const BlockEntries it(k);
+    for (int i = it.i0, j = it.j0; i < n; it.next(i, j, k)) {
+        const double s = staged ? sc[j] : (d ? alpha * sqrt(d[j]) : alpha);
+        Y[(size_t)i * ldy + j] = s * X[(size_t)i * ldx + j];
+    }
+}
+
+// G_ij *= sqrt(d_i d_j): the Gram matrix of L diag(d)^{1/2} from that of L.
+__global__ void sym_scale_kernel(double* __restrict__ G, int ldg, int r, const double* __restrict__ d) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x) {
+        const int i = e / r, j = e % r;
+        G[(size_t)i * ldg + j] *= sqrt(d[i]) * sqrt(d[j]);
     }
 }
 
@@ -271,10 +309,11 @@ __global__ void splitk_reduce_kernel(const double* __restrict__ Wk, int S, int M
 // order in shared memory.  part: [S][M][N].
 __global__ void __launch_bounds__(256) tsgemm_kernel(const double* __restrict__ X, int ldx, int M,
                                                      const double* __restrict__ Y, int ldy, int N, int K, int chunk,
-                                                     double* __restrict__ part) {
+                                                     double* __restrict__ part, int sym) {
     __shared__ double red[1024];
     const int k0 = blockIdx.x * chunk, k1 = min(K, k0 + chunk);
-    const int MN = M * N;
+    // sym (X = Y, M = N): only the M (M + 1) / 2 entries i <= j (half the FP64 FMAs)
+    const int MN = sym ? M * (M + 1) / 2 : M * N;
     int E = 32;
     while (E < MN && E < 256) E <<= 1;
     const int per = (MN + 255) / 256;                 // entries per thread when E = 256
@@ -285,8 +324,20 @@ __global__ void __launch_bounds__(256) tsgemm_kernel(const double* __restrict__ 
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int e = t + E * u;
-        ea[u] = e < MN ? e / N : 0;
-        eb[u] = e < MN ? e % N : 0;
+        ea[u] = 0;
+        eb[u] = 0;
+        if (e < MN && !sym) {
+            ea[u] = e / N;
+            eb[u] = e % N;
+        } else if (e < MN) {                          // e-th entry of the upper triangle, row by row
+            int i = 0, rem = e;
+            while (rem >= M - i) {
+                rem -= M - i;
+                ++i;
+            }
+            ea[u] = i;
+            eb[u] = i + rem;
+        }
     }
     for (int k = k0 + g; k < k1; k += G) {
         const double* xr = X + (size_t)k * ldx;
@@ -295,11 +346,12 @@ __global__ void __launch_bounds__(256) tsgemm_kernel(const double* __restrict__ 
         for (int u = 0; u < 4; ++u)
             if (u < per && t + E * u < MN) acc[u] = fma(xr[ea[u]], yr[eb[u]], acc[u]);
     }
+    const size_t base = (size_t)blockIdx.x * M * N;   // part keeps the [M][N] layout (sym: i <= j written)
     if (G == 1) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int e = t + E * u;
-            if (u < per && e < MN) part[(size_t)blockIdx.x * MN + e] = acc[u];
+            if (u < per && e < MN) part[base + (size_t)ea[u] * N + eb[u]] = acc[u];
         }
         return;
     }
@@ -309,7 +361,7 @@ __global__ void __launch_bounds__(256) tsgemm_kernel(const double* __restrict__ 
     if (g == 0 && t < MN) {
         double v = red[t];
         for (int q = 1; q < G; ++q) v += red[q * E + t];
-        part[(size_t)blockIdx.x * MN + t] = v;
+        part[base + (size_t)ea[0] * N + eb[0]] = v;
     }
 }
 
@@ -326,9 +378,8 @@ __global__ void __launch_bounds__(256) tall_small_kernel(const double* __restric
         sT[e] = tT ? Tm[(size_t)j * ldt + k] : Tm[(size_t)k * ldt + j];
     }
     __syncthreads();
-    const size_t total = (size_t)n * N;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e / N), j = (int)(e % N);
+    const BlockEntries it(N);
+    for (int i = it.i0, j = it.j0; i < n; it.next(i, j, N)) {
         const double* xr = X + (size_t)i * ldx;
         double acc = 0.0;
         for (int k = 0; k < K; ++k) acc = fma(xr[k], sT[k * N + j], acc);
@@ -393,8 +444,13 @@ dme_status launch_jacobi_eig(const double* G, int ldg, int r, double* Vt, int ld
 }
 
 void launch_lr_select(const double* lam, const double* Vt, int ldv, int r, double tol, int inv_sqrt, double* T,
-                      int ldt, double* d_out, int* k_out, cudaStream_t st) {
-    select_kernel<<<1, 256, 0, st>>>(lam, Vt, ldv, r, tol, inv_sqrt, T, ldt, d_out, k_out);
+                      int ldt, double* d_out, int* k_out, cudaStream_t st, const double* rowscale) {
+    select_kernel<<<1, 256, 0, st>>>(lam, Vt, ldv, r, tol, inv_sqrt, T, ldt, d_out, k_out, rowscale);
+}
+
+void launch_sym_scale(double* G, int ldg, int r, const double* d, cudaStream_t st) {
+    if (r <= 0) return;
+    sym_scale_kernel<<<std::min(1024, (r * r + 255) / 256), 256, 0, st>>>(G, ldg, r, d);
 }
 
 void launch_ric_weights(const double* lam, const double* Vt, int ldv, int m, double t, double* F, int ldf,
@@ -445,10 +501,10 @@ void launch_splitk_reduce(const double* W, int S, int M, int N, double* C, int l
 }
 
 void launch_tsgemm(const double* X, int ldx, int M, const double* Y, int ldy, int N, int K, int chunk, double* part,
-                   cudaStream_t st) {
+                   cudaStream_t st, int sym) {
     const int S = (K + chunk - 1) / chunk;
     if (S <= 0 || M * N <= 0) return;
-    tsgemm_kernel<<<S, 256, 0, st>>>(X, ldx, M, Y, ldy, N, K, chunk, part);
+    tsgemm_kernel<<<S, 256, 0, st>>>(X, ldx, M, Y, ldy, N, K, chunk, part, sym && X == Y && ldx == ldy && M == N);
 }
 
 void launch_tall_small(const double* X, int ldx, int n, int K, const double* Tm, int ldt, int tT, int N, double* C,

@@ -57,12 +57,14 @@ struct dme_lr_s {
     bool sparse = false;
     int nnz = 0;
     int *at_ptr = nullptr, *at_idx = nullptr;
-    double* at_val = nullptr;
+    double* at_val = nullptr;   // values of A^T / g
+    int *s_ptr = nullptr, *s_idx = nullptr;   // sparse S (CSR, device), for T4
+    double* s_val = nullptr;
     double lc = 0.0, lg = 0.0;       // A^T = lc I + lg X, spectrum of X in [-2, 2] (Gershgorin)
     std::vector<double> xi;          // Leja points
     std::vector<LejaTab> ltab;
     double *Wa = nullptr, *Wb = nullptr;   // Leja work (n x rcap)
-    double *lpart = nullptr, *lnorm = nullptr;  // per-block partial norms, per-term norms
+    double *lpart = nullptr, *lnorm = nullptr;  // per-block partial norms; norms and grid-barrier words
     int n = 0, m = 0, p = 0, rcap = 0, q = 7;
     double tol = 1e-13;
     double *L = nullptr, *L2 = nullptr, *d = nullptr, *d2 = nullptr;   // n x rcap, rcap
@@ -128,13 +130,15 @@ dme_status gemm_ws(dme_lr_t lr, const GemmProb& g, cudaStream_t st);
 // into K chunks, one grouped launch, then summed in chunk order.
 dme_status gemm(dme_lr_t lr, const GemmProb& g, cudaStream_t st) {
     if (g.M <= 0 || g.N <= 0) return DME_OK;
-    if (g.transA && !g.transB && g.M * g.N <= 1024 && g.K >= 1024) {
+    const bool sym = g.tri && g.A == g.B && g.lda == g.ldb && g.M == g.N;
+    if (g.transA && !g.transB && (g.M * g.N <= 1024 || (sym && g.M * (g.M + 1) / 2 <= 1024)) && g.K >= 1024) {
         // X^T Y of two tall blocks with a small result: row chunks summed per CTA
+        // (a Gram matrix X^T X: its upper triangle only)
         const size_t mn = (size_t)g.M * g.N;
         const int smax = (int)std::min<size_t>(2048, lr->ws_doubles / mn);
         const int chunk = std::max(64, (g.K + smax - 1) / smax);
         const int S = (g.K + chunk - 1) / chunk;
-        launch_tsgemm(g.A, g.lda, g.M, g.B, g.ldb, g.N, g.K, chunk, lr->ws, st);
+        launch_tsgemm(g.A, g.lda, g.M, g.B, g.ldb, g.N, g.K, chunk, lr->ws, st, sym);
         launch_splitk_reduce(lr->ws, S, g.M, g.N, g.C, g.ldc, g.alpha, g.D1, g.b1, g.tri, st);
         return DME_OK;
     }
@@ -201,18 +205,23 @@ dme_status eig_gram(dme_lr_t lr, int r) {
 
 // Compress the factor (L, d) with r columns (leading dimension ld) in place;
 // L2 is an n x ld work buffer.  Reads the new rank back to the host.
-dme_status compress(dme_lr_t lr, double* L, double* L2, double* d, int ld, int& r) {
+// With Lt = L diag(d)^{1/2}, Lt is never formed: its Gram matrix is diag(d)^{1/2}
+// (L^T L) diag(d)^{1/2}, and the new factor Lt V_k Lambda^{-1/2} is L times the
+// small matrix diag(d)^{1/2} V_k Lambda^{-1/2}, written to L2; the two buffers
+// then trade places (L names the result).
+dme_status compress(dme_lr_t lr, double*& L, double*& L2, double* d, int ld, int& r) {
     if (r == 0) return DME_OK;
     cudaStream_t st = lr->st;
     const int n = lr->n;
-    launch_copy_cols(L2, ld, L, ld, n, r, 1.0, d, st);                                     // Lt = L d^{1/2}
-    DME_TRY(gemm(lr, mk(r, r, n, L2, ld, 1, L2, ld, 0, lr->G, lr->rcap, 1.0, 1), st));          // Lt^T Lt
+    DME_TRY(gemm(lr, mk(r, r, n, L, ld, 1, L, ld, 0, lr->G, lr->rcap, 1.0, 1), st));            // L^T L
+    launch_sym_scale(lr->G, lr->rcap, r, d, st);                                              // Lt^T Lt
     DME_TRY(eig_gram(lr, r));
-    launch_lr_select(lr->lam, lr->Vt, lr->rcap, r, lr->tol, 1, lr->T, lr->rcap, d, lr->kdev, st);
+    launch_lr_select(lr->lam, lr->Vt, lr->rcap, r, lr->tol, 1, lr->T, lr->rcap, d, lr->kdev, st, d);
     int k = 0;
     DME_CUDA_TRY(cudaMemcpyAsync(&k, lr->kdev, sizeof(int), cudaMemcpyDeviceToHost, st));
     DME_CUDA_TRY(cudaStreamSynchronize(st));
-    DME_TRY(gemm(lr, mk(n, k, r, L2, ld, 0, lr->T, lr->rcap, 0, L, ld, 1.0), st));              // L = Lt V_k Lambda^-1/2
+    DME_TRY(gemm(lr, mk(n, k, r, L, ld, 0, lr->T, lr->rcap, 0, L2, ld, 1.0), st));              // Lt V_k Lambda^-1/2
+    std::swap(L, L2);
     r = k;
     return DME_OK;
 }
@@ -358,37 +367,32 @@ dme_status leja_apply(dme_lr_t lr, const double* X, int ldx, int k, double* Y, i
         return DME_OK;
     }
     const LejaTab& tb = leja_table(lr, tau);
-    const double invg = 1.0 / lr->lg;
-    launch_copy_cols(lr->Wa, rc, X, ldx, n, k, 1.0, nullptr, st);
-    std::vector<double> h(16);
-    for (int sub = 0; sub < tb.s; ++sub) {
-        launch_copy_cols(Y, ldy, lr->Wa, rc, n, k, tb.dd[0], nullptr, st);   // p = d_0 v
-        double* W = lr->Wa;
-        double* Wn = lr->Wb;
-        int small = 0;
-        bool done = false;
-        for (int base = 1; base < kLejaTerms && !done; base += 8) {
-            const int cnt = std::min(8, kLejaTerms - base);
-            for (int j = 0; j < cnt; ++j) {
-                const int kk = base + j;
-                launch_leja_term(lr->at_ptr, lr->at_idx, lr->at_val, n, k, W, Wn, rc, Y, ldy, lr->lc, invg,
-                                 lr->xi[kk - 1], tb.dd[kk], lr->lpart, lr->lnorm + 2 * j, st);
-                std::swap(W, Wn);
-            }
-            DME_CUDA_TRY(cudaMemcpyAsync(h.data(), lr->lnorm, sizeof(double) * 2 * cnt, cudaMemcpyDeviceToHost, st));
-            DME_CUDA_TRY(cudaStreamSynchronize(st));
-            for (int j = 0; j < cnt && !done; ++j) {
-                const double term = std::fabs(tb.dd[base + j]) * std::sqrt(h[2 * j]);
-                if (term <= kLejaTol * std::sqrt(h[2 * j + 1])) {
-                    if (++small == 2) done = true;
-                } else {
-                    small = 0;
-                }
-            }
-        }
-        if (sub + 1 < tb.s) launch_copy_cols(lr->Wa, rc, Y, ldy, n, k, tb.scale, nullptr, st);   // next v
-        else launch_copy_cols(Y, ldy, Y, ldy, n, k, tb.scale, nullptr, st);
-    }
+    LejaCall c;
+    c.ptr = lr->at_ptr;
+    c.idx = lr->at_idx;
+    c.val = lr->at_val;
+    c.n = n;
+    c.r = k;
+    c.X = X;
+    c.ldx = ldx;
+    c.Y = Y;
+    c.ldy = ldy;
+    c.Wa = lr->Wa;
+    c.Wb = lr->Wb;
+    c.ldw = rc;
+    c.c = lr->lc;
+    c.invg = 1.0 / lr->lg;
+    c.scale = tb.scale;
+    c.tol = kLejaTol;
+    c.substeps = tb.s;
+    c.terms = kLejaTerms;
+    c.xi = lr->xi.data();
+    c.dd = tb.dd.data();
+    c.part = lr->lpart;
+    c.sums = lr->lnorm;
+    c.bar = reinterpret_cast<unsigned*>(lr->lnorm + 4);
+    c.status = lr->status;
+    DME_TRY(launch_leja_apply(c, st));
     DME_CUDA_TRY(cudaGetLastError());
     return DME_OK;
 }
@@ -543,6 +547,16 @@ dme_status lr_T4(dme_lr_t lr, double tau, int rule) {
     const int n = lr->n, r = lr->r, rc = lr->rcap;
     const int blocks = rule == DME_T4_EULER ? 2 : 3;
     DME_TRY(need_cols(lr, blocks * r));
+    if (lr->sparse) {
+        launch_spmm(lr->s_ptr, lr->s_idx, lr->s_val, n, r, lr->L, rc, lr->L + r, rc, std::sqrt(tau), st);
+        if (blocks == 3)
+            launch_spmm(lr->s_ptr, lr->s_idx, lr->s_val, n, r, lr->L + r, rc, lr->L + 2 * r, rc, std::sqrt(0.5 * tau),
+                        st);
+        for (int b = 1; b < blocks; ++b)
+            DME_CUDA_TRY(cudaMemcpyAsync(lr->d + b * r, lr->d, sizeof(double) * r, cudaMemcpyDeviceToDevice, st));
+        lr->r = blocks * r;
+        return compress(lr, lr->L, lr->L2, lr->d, rc, lr->r);
+    }
     const double* S = lr->P->S;
     if (lr->split) {
         DME_TRY(apply_split(lr, lr->P->Ssl, lr->L, rc, r, lr->L + r, rc, std::sqrt(tau)));
@@ -594,6 +608,7 @@ dme_status lr_check(dme_lr_t lr, const char* where) {
     DME_CUDA_TRY(cudaMemsetAsync(lr->status, 0, sizeof(int), lr->st));
     DME_CUDA_TRY(cudaStreamSynchronize(lr->st));
     if (hs & DEV_NOTSPD) return set_error(std::string(where) + ": R is not positive definite"), DME_ENOTSPD;
+    if (hs & DEV_TIMEOUT) return set_error(std::string(where) + ": a bounded device wait ran out"), DME_ECUDA;
     return set_error(std::string(where) + ": device status " + std::to_string(hs)), DME_ECUDA;
 }
 
@@ -724,8 +739,9 @@ dme_status dme_lr_plan(const dme_plan_desc* desc, const double* A, const double*
 }
 
 dme_status dme_lr_plan_csr(const dme_plan_desc* desc, int nnz, const int* rowptr, const int* colidx,
-                           const double* vals, const double* C, const double* B, const double* R,
-                           const dme_lr_opts* opts, void* cuda_stream, dme_lr_t* out) {
+                           const double* vals, const double* C, const double* B, const double* R, int nnz_s,
+                           const int* s_rowptr, const int* s_colidx, const double* s_vals, const dme_lr_opts* opts,
+                           void* cuda_stream, dme_lr_t* out) {
     if (!out) return set_error("out is NULL"), DME_EINVAL;
     *out = nullptr;
     set_error("");
@@ -735,16 +751,18 @@ dme_status dme_lr_plan_csr(const dme_plan_desc* desc, int nnz, const int* rowptr
     if (!desc->q_is_factor) return set_error("low-rank path: give Q as its factor C (q_is_factor = 1)"), DME_EINVAL;
     if (desc->prec != DME_FP64) return set_error("sparse low-rank path: prec must be DME_FP64"), DME_EINVAL;
     if (desc->fsal || desc->extrap > 1) return set_error("low-rank path: no fsal / extrapolation"), DME_EINVAL;
-    if (desc->eq != DME_DLE && desc->eq != DME_DRE) return set_error("sparse low-rank path: DLE or DRE"), DME_EINVAL;
+    const bool gen = desc->eq == DME_GDLE || desc->eq == DME_GDRE;
+    if (gen && (!s_rowptr || nnz_s < 0 || (nnz_s > 0 && (!s_colidx || !s_vals))))
+        return set_error("sparse low-rank path: generalised equations need S in CSR"), DME_EINVAL;
     if (desc->n < 1 || desc->nflows < 1 || desc->nflows > 4) return set_error("bad n or nflows"), DME_EINVAL;
     if (desc->comp != DME_LIE && desc->comp != DME_STRANG) return set_error("bad comp"), DME_EINVAL;
     if (!(desc->h > 0.0) || !std::isfinite(desc->h)) return set_error("h must be positive"), DME_EINVAL;
-    const bool ric = desc->eq == DME_DRE;
+    const bool ric = desc->eq == DME_DRE || desc->eq == DME_GDRE;
     for (int i = 0; i < desc->nflows; ++i) {
         const int f = desc->flows[i];
-        if (f != DME_F1 && f != DME_F2 && f != DME_F12 && f != DME_F3)
-            return set_error("sparse low-rank path: flows F1, F2, F12, F3"), DME_EINVAL;
-        if (f == DME_F3 && !ric) return set_error("F3 needs eq = DRE"), DME_EINVAL;
+        if (f < DME_F1 || f > DME_F4) return set_error("bad flow id"), DME_EINVAL;
+        if (f == DME_F3 && !ric) return set_error("F3 needs eq = DRE or GDRE"), DME_EINVAL;
+        if (f == DME_F4 && !gen) return set_error("F4 needs eq = GDLE or GDRE"), DME_EINVAL;
     }
     if (ric && (desc->m < 1 || desc->m > 32 || !B || !R)) return set_error("DRE needs B, R and 1 <= m <= 32"), DME_EINVAL;
     if (desc->p < 1) return set_error("p must be >= 1"), DME_EINVAL;
@@ -796,6 +814,9 @@ dme_status dme_lr_plan_csr(const dme_plan_desc* desc, int nnz, const int* rowptr
         lr->lc = 0.5 * (a + b);
         lr->lg = 0.25 * (b - a);
         lr->xi = leja_points_host(kLejaTerms);
+        // the device copy of A^T holds A^T / g (the Leja recurrence's operator up to the shift)
+        if (lr->lg > 0.0)
+            for (double& v : tval) v /= lr->lg;
         if (cuda_stream) {
             lr->st = reinterpret_cast<cudaStream_t>(cuda_stream);
         } else {
@@ -819,6 +840,33 @@ dme_status dme_lr_plan_csr(const dme_plan_desc* desc, int nnz, const int* rowptr
             DME_CUDA_TRY(cudaMemcpyAsync(lr->at_val, tval.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
         }
         DME_CUDA_TRY(cudaStreamSynchronize(st));       // the host copies above go out of scope
+        if (gen) {
+            // S in CSR: checked on the host, then copied as given (T4 applies S, not S^T)
+            std::vector<int> sp(n + 1), si(nnz_s);
+            std::vector<double> sv(nnz_s);
+            DME_CUDA_TRY(cudaMemcpy(sp.data(), s_rowptr, sizeof(int) * (n + 1), cudaMemcpyDefault));
+            if (nnz_s) {
+                DME_CUDA_TRY(cudaMemcpy(si.data(), s_colidx, sizeof(int) * nnz_s, cudaMemcpyDefault));
+                DME_CUDA_TRY(cudaMemcpy(sv.data(), s_vals, sizeof(double) * nnz_s, cudaMemcpyDefault));
+            }
+            if (sp[0] != 0 || sp[n] != nnz_s) return set_error("CSR of S: rowptr[0] must be 0, rowptr[n] = nnz"), DME_EINVAL;
+            for (int i = 0; i < n; ++i)
+                if (sp[i + 1] < sp[i]) return set_error("CSR of S: rowptr must be non-decreasing"), DME_EINVAL;
+            for (int e = 0; e < nnz_s; ++e)
+                if (si[e] < 0 || si[e] >= n) return set_error("CSR of S: column index out of range"), DME_EINVAL;
+            double *p1 = nullptr, *p2 = nullptr;
+            DME_TRY(lr_alloc(lr.get(), &p1, ((size_t)n + 2) / 2));
+            DME_TRY(lr_alloc(lr.get(), &p2, ((size_t)nnz_s + 1) / 2));
+            DME_TRY(lr_alloc(lr.get(), &lr->s_val, (size_t)nnz_s));
+            lr->s_ptr = reinterpret_cast<int*>(p1);
+            lr->s_idx = reinterpret_cast<int*>(p2);
+            DME_CUDA_TRY(cudaMemcpyAsync(lr->s_ptr, sp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st));
+            if (nnz_s) {
+                DME_CUDA_TRY(cudaMemcpyAsync(lr->s_idx, si.data(), sizeof(int) * nnz_s, cudaMemcpyHostToDevice, st));
+                DME_CUDA_TRY(cudaMemcpyAsync(lr->s_val, sv.data(), sizeof(double) * nnz_s, cudaMemcpyHostToDevice, st));
+            }
+            DME_CUDA_TRY(cudaStreamSynchronize(st));
+        }
         if (ric) {
             const int m = desc->m;
             double *Bd = nullptr, *Rd = nullptr, *Btd = nullptr;
@@ -836,8 +884,8 @@ dme_status dme_lr_plan_csr(const dme_plan_desc* desc, int nnz, const int* rowptr
         const size_t rc = rmax;
         DME_TRY(lr_alloc(lr.get(), &lr->Wa, (size_t)n * rc));
         DME_TRY(lr_alloc(lr.get(), &lr->Wb, (size_t)n * rc));
-        DME_TRY(lr_alloc(lr.get(), &lr->lpart, 2 * (size_t)leja_part_blocks(n, rmax)));
-        DME_TRY(lr_alloc(lr.get(), &lr->lnorm, 16));
+        DME_TRY(lr_alloc(lr.get(), &lr->lpart, 4 * (size_t)leja_grid_max()));
+        DME_TRY(lr_alloc(lr.get(), &lr->lnorm, 8));   // 4 sums, then the barrier words
         DME_TRY(lr_check(lr.get(), "dme_lr_plan_csr"));
         *out = lr.release();
         return DME_OK;

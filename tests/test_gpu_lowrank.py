@@ -197,6 +197,34 @@ def test_sparse_lowrank_beyond_the_dense_limit_matches_closed_form():
         plan.solve(T, N, P_out=np.empty((1, 1)))
 
 
+@pytest.mark.parametrize("control,flows,comp,N", [(True, ["F12", "F3", "F4"], "strang", 4),
+                                                  (True, ["F1", "F2", "F3", "F4"], "lie", 5),
+                                                  (False, ["F1", "F2", "F4"], "strang", 4)])
+def test_sparse_generalised_lowrank_matches_leja_oracle(control, flows, comp, N):
+    """Example 2's structure (stochastic heat transfer): sparse A and sparse S
+    (the Robin-edge noise), B on the control edge, C the mean."""
+    A, B, S, C, T = W.stochastic_heat_csr(8, control)
+    R = np.eye(1) if control else None
+    plan = dme.LowRankPlan.from_csr(A, C, h=T / N, flows=flows, comp=comp, B=B, R=R, S_csr=S, tol=1e-13)
+    n = A.shape[0]
+    P = np.empty((n, n))
+    r = plan.solve(T, N, P_out=P)
+    Lo, Do = O.solve_lowrank(A, C, np.zeros((n, 0)), np.zeros((0, 0)), T, N, comp, flows, B=B, R=R, S=S,
+                             tol=1e-13, action="leja")
+    assert rel(P, O.ldl_product(Lo, Do)) < FP64_TOL
+    assert abs(r - Lo.shape[1]) <= 1
+
+
+def test_sparse_generalised_lowrank_equals_dense_lowrank_gpu():
+    pr = W.gdre_stochastic_heat(8, True)
+    A, B, S, C, T = W.stochastic_heat_csr(8, True)
+    plan = dme.LowRankPlan.from_csr(A, C, h=T / 5, flows=["F12", "F3", "F4"], B=B, R=np.eye(1), S_csr=S, tol=1e-15)
+    P = np.empty((pr.n, pr.n))
+    plan.solve(T, 5, P_out=P)
+    Pd, *_ = _run(pr, ["F12", "F3", "F4"], "strang", 5, tol=1e-15)
+    assert rel(P, Pd) < 1e-11
+
+
 def test_sparse_lowrank_rejects_malformed_csr():
     pr = W.dre_convdiff(nx=5, m=2, p=2)
     A = sp.csr_matrix(pr.A)
@@ -208,4 +236,10 @@ def test_sparse_lowrank_rejects_malformed_csr():
     assert ei.value.status == dme.DME_EINVAL
     d4 = dme.make_desc(pr.n, m=2, p=2, eq=dme.DME_GDRE, flows=["F12", "F3", "F4"], h=0.1, q_is_factor=True)
     with pytest.raises(dme.DmeError):
-        dme.dme_lr_plan_csr(d4, A.indptr, A.indices, A.data, pr.C, pr.B, pr.R)
+        dme.dme_lr_plan_csr(d4, A.indptr, A.indices, A.data, pr.C, pr.B, pr.R)     # S missing
+    with pytest.raises(dme.DmeError) as ei:
+        dme.dme_lr_plan_csr(d4, A.indptr, A.indices, A.data, pr.C, pr.B, pr.R, S_csr=(A.indptr, bad, A.data))
+    assert ei.value.status == dme.DME_EINVAL
+    d1 = dme.make_desc(pr.n, m=2, p=2, eq=dme.DME_DRE, flows=["F12", "F3", "F4"], h=0.1, q_is_factor=True)
+    with pytest.raises(dme.DmeError):
+        dme.dme_lr_plan_csr(d1, A.indptr, A.indices, A.data, pr.C, pr.B, pr.R)     # F4 needs GDLE / GDRE

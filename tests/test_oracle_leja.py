@@ -98,3 +98,39 @@ def test_stencil_laplacian_dle_closed_form_helper():
     X = np.random.default_rng(3).standard_normal((nx * nx, 2))
     got = pins.dle_exact_apply_stencil_laplacian(nx, c, 0.7, X)
     assert np.linalg.norm(got - P @ X) / np.linalg.norm(P @ X) < 1e-13
+
+
+def test_sparse_generalised_factored_oracle_equals_dense_form():
+    """The factored oracle with sparse A and S (Leja action, sparse S L) against
+    the same oracle with dense A and S and the dense exponential (Example 2's
+    structure, GDRE, Strang F12 F3 F4)."""
+    import dme_workloads as W
+    from oracle.dme_lowrank import solve_lowrank, ldl_product
+    A, B, S, C, T = W.stochastic_heat_csr(6, True)
+    n = A.shape[0]
+    z, z0 = np.zeros((n, 0)), np.zeros((0, 0))
+    flows = ["F12", "F3", "F4"]
+    Ls, Ds = solve_lowrank(A, C, z, z0, T, 4, "strang", flows, B=B, R=np.eye(1), S=S, tol=1e-15, action="leja")
+    Ld, Dd = solve_lowrank(A.toarray(), C, z, z0, T, 4, "strang", flows, B=B, R=np.eye(1), S=S.toarray(),
+                           tol=1e-15, action="dense")
+    Ps, Pd = ldl_product(Ls, Ds), ldl_product(Ld, Dd)
+    assert np.linalg.norm(Ps - Pd) / np.linalg.norm(Pd) < 1e-11
+
+
+def test_stochastic_heat_data_structure():
+    """Generator shape checks: A symmetric with the Robin diagonal on the east
+    edge only, S diagonal on that edge, B on the west edge, C the mean."""
+    import dme_workloads as W
+    nx = 7
+    A, B, S, C, T = W.stochastic_heat_csr(nx, True)
+    Ad = A.toarray()
+    dx = 1.0 / (nx + 1)
+    assert np.allclose(Ad, Ad.T)
+    east = [nx - 1 + nx * j for j in range(nx)]
+    d = np.diag(Ad) * dx * dx
+    assert np.allclose(d[east], -3.0 + 0.25 * dx)
+    assert np.allclose(np.delete(d, east), -4.0)
+    assert S.nnz == nx and np.allclose(S.diagonal()[east], 0.5 / dx)
+    assert np.count_nonzero(B) == nx and np.allclose(B[::nx, 0], 1.0 / (dx * dx))
+    assert np.isclose(C.sum(), 1.0) and T == 0.5
+    assert W.stochastic_heat_csr(nx, False)[1] is None
