@@ -550,15 +550,9 @@ def extras_run(args, dme, pr, h, to_dev, stream, dev):
     lr.close()
     # the factored path past the dense limit: sparse A, e^{tA^T} L by Leja interpolation
     try:
-        import scipy.sparse as sps
         nx = args.sparse_nx
-        T1 = sps.diags([np.full(nx - 1, 1.0), np.full(nx, -2.0), np.full(nx - 1, 1.0)], [-1, 0, 1])
-        I1 = sps.identity(nx)
-        As = (sps.kron(I1, T1) + sps.kron(T1, I1)).tocsr()
+        As, Bs, Cs = sparse_problem(nx)
         ns = nx * nx
-        rng = np.random.default_rng(0)
-        Bs = rng.standard_normal((ns, 4))
-        Cs = rng.uniform(0.0, 1.0, (2, ns))
         hs = 0.01
         t0 = time.perf_counter()
         sl = dme.LowRankPlan.from_csr(As, Cs, h=hs, flows=["F1", "F2", "F3"], comp="strang", B=Bs, R=np.eye(4),
@@ -604,6 +598,57 @@ def extras_run(args, dme, pr, h, to_dev, stream, dev):
     return out
 
 
+def sparse_problem(nx):
+    """The sparse low-rank extra's DRE: the unscaled 5-point stencil on an nx x nx
+    grid, B n x 4 N(0,1), R = I, C 2 x n U(0,1) (seed 0)."""
+    import scipy.sparse as sps
+    T1 = sps.diags([np.full(nx - 1, 1.0), np.full(nx, -2.0), np.full(nx - 1, 1.0)], [-1, 0, 1])
+    I1 = sps.identity(nx)
+    As = (sps.kron(I1, T1) + sps.kron(T1, I1)).tocsr()
+    rng = np.random.default_rng(0)
+    Bs = rng.standard_normal((nx * nx, 4))
+    Cs = rng.uniform(0.0, 1.0, (2, nx * nx))
+    return As, Bs, Cs
+
+
+def run_lowrank_only(args):
+    """Profile target: one low-rank configuration alone, its timed steps inside the
+    NVTX range "lr".  fp64 / split: the large dense DRE (n = 4096, Strang F1F2F3,
+    h = 1/256, FP64 or split-precision products), 8 warm-up steps; sparse: the
+    sparse DRE of sparse_problem (n = sparse_nx^2, Strang F1F2F3, h = 0.01), 4
+    warm-up steps.  Then --lowrank-steps timed steps."""
+    import torch
+    import paper_1805_08990_gb300 as dme
+    from paper_1805_08990_gb300 import build
+    build.build()
+    mode = args.lowrank_only
+    if mode == "sparse":
+        As, Bs, Cs = sparse_problem(args.sparse_nx)
+        h, warm = 0.01, 4
+        lr = dme.LowRankPlan.from_csr(As, Cs, h=h, flows=["F1", "F2", "F3"], comp="strang", B=Bs, R=np.eye(4))
+        n = As.shape[0]
+    else:
+        pr = W.dre_heat_large()
+        h, warm = 1.0 / 256, 8
+        dev = torch.device("cuda")
+        to_dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)   # noqa: E731
+        lr = dme.LowRankPlan(to_dev(pr.A), to_dev(pr.C), h=h, flows=["F1", "F2", "F3"], comp="strang",
+                             B=to_dev(pr.B), R=to_dev(pr.R), prec="split_bf16" if mode == "split" else "fp64")
+        n = pr.n
+    lr.solve(warm * h, warm)
+    torch.cuda.synchronize()
+    N = args.lowrank_steps
+    torch.cuda.nvtx.range_push("lr")
+    t0 = time.perf_counter()
+    r = lr.solve(N * h, N)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"lowrank_only": mode, "n": n, "steps": N, "ms_per_step": dt / N * 1e3, "rank": r}))
+    lr.close()
+    return 0
+
+
 def run_gemm_only(args):
     """The split-precision tensor-core product alone: C = A B^T, A, B seeded
     N(0,1) of size N x N (inputs and their slices exceed L2 at N = 4096)."""
@@ -640,6 +685,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--gemm-only", type=int, default=0, help="profile target: split GEMM of this size alone")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--lowrank-only", default="", choices=["", "fp64", "split", "sparse"],
+                    help="profile target: one low-rank configuration alone (--lowrank-steps timed steps)")
     ap.add_argument("--serving-requests", type=int, default=32, help="serving sample size (0: skip)")
     ap.add_argument("--no-extras", dest="extras", action="store_false", help="skip the FSAL and low-rank lines")
     ap.add_argument("--config-suite", action="store_true",
@@ -654,6 +701,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.lowrank_only:
+        return run_lowrank_only(args)
     if args.gemm_only:
         return run_gemm_only(args)
     if args.serving_suite:
