@@ -1,10 +1,11 @@
 // Serving: continuous batching of independent DLE/DRE solves on one GPU.
 //
-// Two host threads share a request table under one mutex:
-//  * the admission thread takes queued requests while a slot is free and the
-//    request's device footprint fits in the HBM budget, and builds its plan
-//    (problem data, Q, Bt, E_t, W_t) on the plan's own stream, so planning
-//    overlaps with stepping on the GPU;
+// Host threads share a request table under one mutex:
+//  * admission threads (kAdmitThreads of them) take queued requests while a
+//    slot is free and the request's device footprint fits in the HBM budget,
+//    and build their plans (problem data, Q, Bt, E_t, W_t) each on the plan's
+//    own stream, so plans overlap one another and the stepping on the GPU (a
+//    small plan is bound by launch latency, not by the GPU's throughput);
 //  * the stepper thread owns the resident requests and runs scheduler rounds:
 //    each round advances every resident request by one composition step.  The
 //    ops of all residents are executed stage by stage with grouped kernels:
@@ -86,7 +87,8 @@ struct dme_server_s {
     size_t reserved = 0;
     uint64_t next_id = 1;
     bool stop = false;
-    std::thread admit_thr, step_thr;
+    std::vector<std::thread> admit_thrs;
+    std::thread step_thr;
     cudaStream_t st = nullptr;
     int* dstat = nullptr;         // per-slot device status words
     DescArena arena;              // launch descriptors of the captured round
@@ -135,6 +137,8 @@ void release(dme_server_t s, Req* r) {
     r->slot = -1;
     s->cv.notify_all();
 }
+
+constexpr int kAdmitThreads = 4;
 
 void admit_loop(dme_server_t s) {
     for (;;) {
@@ -590,7 +594,7 @@ dme_status dme_server_create(size_t hbm_budget_bytes, int max_slots, dme_server_
         delete s;
         return DME_ECUDA;
     }
-    s->admit_thr = std::thread(admit_loop, s);
+    for (int i = 0; i < kAdmitThreads; ++i) s->admit_thrs.emplace_back(admit_loop, s);
     s->step_thr = std::thread(step_loop, s);
     *out = s;
     return DME_OK;
@@ -741,7 +745,8 @@ dme_status dme_server_destroy(dme_server_t s) {
         s->stop = true;
         s->cv.notify_all();
     }
-    if (s->admit_thr.joinable()) s->admit_thr.join();
+    for (auto& t : s->admit_thrs)
+        if (t.joinable()) t.join();
     if (s->step_thr.joinable()) s->step_thr.join();
     cudaStreamSynchronize(s->st);
     for (auto& kv : s->reqs) {
