@@ -134,6 +134,34 @@ def replica_value(steps_per_rank: int, ms_max: float, world_size: int) -> float:
     return world_size * steps_per_rank / (ms_max / 1e3)
 
 
+FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (nominal; no measured figure in the peaks file)
+
+
+def serving_work(specs):
+    """Algorithmic work of the stepping of these requests (Strang F12F3, one
+    step = two congruences and T3): FP64 flops 6 n^3 + 3 n^2 m per step (the
+    congruence 2 n^3 + n^3 with the symmetric half, Z = P Bt and the update
+    of T3); tensor flops of the split path 2 x 2 x 14 x 2 n^3 per step (two
+    slice-pair GEMMs of 14 bf16 products per congruence)."""
+    f64 = sum(sp["steps"] * (6.0 * sp["n"] ** 3 + 3.0 * sp["n"] ** 2 * sp["m"]) for sp in specs)
+    tens = sum(sp["steps"] * 112.0 * sp["n"] ** 3 for sp in specs)
+    return f64, tens
+
+
+def serving_roofline(st, prec, peaks):
+    """Fraction of the roofline the served stepping work reaches over a run's wall
+    time (planning overlaps it and is not counted as work)."""
+    if prec == "fp64":
+        ach = st["work_fp64_flops"] / st["wall_s"] / 1e12
+        return {"bound": "fp64", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_NOMINAL_TFLOPS, "peak_source": "GB300 FP64 nominal"}
+    ach = st["work_tensor_flops"] / st["wall_s"] / 1e12
+    pk = peaks["bf16_tflops_sustained"]
+    return {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+            "fp64_equiv_tflops": st["work_fp64_flops"] / st["wall_s"] / 1e12,
+            "peak_source": "bf16 dense sustained, MEASURED_PEAKS.json"}
+
+
 def serving_run(count: int, seed: int, rate: float | None, prec: str = "fp64"):
     """Submit `count` requests of the serving stream (n log-uniform 32..1024,
     Laplacian or stable random A, m, p ~ U{1..8}, T ~ U[0.1, 10], 50-500 Strang
@@ -161,6 +189,7 @@ def serving_run(count: int, seed: int, rate: float | None, prec: str = "fp64"):
         st = json.loads(dme.dme_server_stats(srv))
         st["wall_s"] = wall
         st["steps_total"] = int(sum(sp["steps"] for sp in specs))
+        st["work_fp64_flops"], st["work_tensor_flops"] = serving_work(specs)
         return st
     finally:
         dme.dme_server_destroy(srv)
@@ -209,6 +238,7 @@ def serving_stream(count: int, seed: int, rate: float, prec: str):
         st = json.loads(dme.dme_server_stats(srv))
         st["wall_s"] = time.perf_counter() - t0
         st["client_failures"] = len(failures)
+        st["work_fp64_flops"], st["work_tensor_flops"] = serving_work(specs)
         return st
     finally:
         dme.dme_server_destroy(srv)
@@ -281,14 +311,17 @@ def run_serving_suite(args):
                                  ("fp64", max(args.serving_suite // 8, 64), 64)):
         burst = serving_run(burst_n, seed=1, rate=None, prec=prec)
         sat = burst["completed"] / burst["wall_s"]
+        peaks, _ = load_peaks()
         rows = []
         for load in (0.5, 0.9, 1.2):
             st = serving_stream(count, seed=3, rate=load * sat, prec=prec)
             rows.append({"load": load, "offered_per_s": load * sat, "solves_per_s": st["completed"] / st["wall_s"],
                          "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "completed": st["completed"],
                          "failed": st["failed"] + st["client_failures"], "wall_s": st["wall_s"],
-                         "graph_builds": st.get("graph_builds"), "rounds": st.get("rounds")})
-        out[prec] = {"requests_per_load": count, "saturation_solves_per_s": sat, "loads": rows}
+                         "graph_builds": st.get("graph_builds"), "rounds": st.get("rounds"),
+                         "roofline": serving_roofline(st, prec, peaks)})
+        out[prec] = {"requests_per_load": count, "saturation_solves_per_s": sat,
+                     "saturation_roofline": serving_roofline(burst, prec, peaks), "loads": rows}
     print(json.dumps({"serving_suite": out, "workload": "n log-uniform 32..1024 (Laplacian or stable random A), "
                       "m, p ~ U{1..8}, R = I_m, T ~ U[0.1, 10], 50-500 Strang F12F3 steps, P0 = 0, Poisson arrivals",
                       "max_slots": 32}))
@@ -496,7 +529,8 @@ def run_ours(args):
             line["serving"][prec] = {
                 "saturation_solves_per_s": sat, "poisson_rate": 0.9 * sat,
                 "solves_per_s": live["completed"] / live["wall_s"], "p50_ms": live["p50_ms"],
-                "p99_ms": live["p99_ms"], "burst_p50_ms": burst["p50_ms"], "burst_p99_ms": burst["p99_ms"]}
+                "p99_ms": live["p99_ms"], "burst_p50_ms": burst["p50_ms"], "burst_p99_ms": burst["p99_ms"],
+                "roofline": serving_roofline(burst, prec, peaks)}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         secs, _, _ = oracle_steps(pr, args.cpu_steps)
         line["cpu_baseline"] = {"value": args.cpu_steps / secs, "unit": "steps/s", "cores": os.cpu_count(),

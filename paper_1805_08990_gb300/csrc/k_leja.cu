@@ -9,11 +9,11 @@
 // cooperative launch runs every term of every substep of an application.  Each
 // thread owns the same entries (row, j) throughout; a term is a grid-stride
 // pass (SpMM row, recurrence, accumulation, per-block partial norms) followed
-// by a grid barrier whose last arriving block sums the partials in a fixed
-// order, so every block takes the same, reproducible stopping decision.  The
-// barrier's waits are bounded: on a timeout the kernel sets DEV_TIMEOUT in the
-// status word and returns.
+// by a grid barrier (grid_sync.cuh) whose last arriving block sums the
+// partials in a fixed order, so every block takes the same, reproducible
+// stopping decision.
 #include "dme_internal.h"
+#include "grid_sync.cuh"
 
 #include <algorithm>
 
@@ -22,17 +22,6 @@ namespace dme {
 namespace {
 
 constexpr int LJ_THREADS = 256;
-constexpr unsigned LJ_SPIN_LIMIT = 1u << 22;   // barrier polls (with a short sleep each) before giving up
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
 // Block sum of two values; the result is valid in every thread.
 __device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
@@ -56,22 +45,13 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
     }
 }
 
-// Grid barrier number `b` (1, 2, ... in every block).  If part != nullptr the
-// last block to arrive first sums part[2i], part[2i+1] over the grid (fixed
-// order) into sums[0..1].  Returns false after a timeout (status set).
+// Grid barrier number `b`.  If part != nullptr the last block to arrive first
+// sums part[2i], part[2i+1] over the grid (fixed order) into sums[0..1].
+// Returns false after a timeout (status set).
 __device__ bool grid_barrier(unsigned* bar, unsigned b, const double* part, double* sums, int* status,
                              double* sh) {
     __shared__ int s_last, s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned old = atomicAdd(&bar[0], 1u);
-        s_last = old == b * gridDim.x - 1;
-        s_ok = 1;
-    }
-    __syncthreads();
-    if (s_last) {
-        __threadfence();
+    if (gs_arrive(bar, b, &s_last)) {
         if (part) {
             double a = 0.0, p = 0.0;
             for (int i = threadIdx.x; i < (int)gridDim.x; i += LJ_THREADS) {
@@ -84,24 +64,11 @@ __device__ bool grid_barrier(unsigned* bar, unsigned b, const double* part, doub
                 sums[1] = p;
             }
         }
+        gs_release(bar, b);
         __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            st_release_u32(&bar[1], b);
-        }
-    } else if (threadIdx.x == 0) {
-        unsigned it = 0;
-        while (ld_acquire_u32(&bar[1]) < b) {
-            if (++it > LJ_SPIN_LIMIT) {
-                atomicOr(status, DEV_TIMEOUT);
-                s_ok = 0;
-                break;
-            }
-            __nanosleep(64);
-        }
+        return true;
     }
-    __syncthreads();
-    return s_ok != 0;
+    return gs_wait(bar, b, status, &s_ok);
 }
 
 struct LejaArgs {

@@ -115,9 +115,13 @@ GemmProb gp(int M, int N, int K, const double* A, int lda, int tA, const double*
     return g;
 }
 
+// One FP64 product; 32-wide output tiles when 64-wide ones would not fill one
+// wave of the SMs (both tile shapes give bit-identical results).
 dme_status gemm1(const GemmProb& g, cudaStream_t st) {
     std::vector<GemmProb> v{g};
-    return gemm64_grouped(v, nullptr, st);
+    long tiles64 = (long)((g.M + 63) / 64) * ((g.N + 63) / 64);
+    if (g.tri) tiles64 = (tiles64 + (g.M + 63) / 64) / 2;
+    return gemm64_grouped(v, nullptr, st, nullptr, tiles64 < 152 ? 32 : 64);
 }
 
 // out = G^T P G + addends, symmetric, with G = E (so out = E^T P E); X is n x n work.
@@ -343,9 +347,8 @@ dme_status compute_ew(dme_plan_t p, double tau, int* idx) {
     DME_TRY(tp.get(&U12, nn));
     DME_TRY(tp.get(&V22, nn));
     DME_TRY(tp.get(&V12, nn));
-    double* pivd = nullptr;
-    DME_TRY(tp.get(&pivd, (size_t)std::max(n, 1)));
-    int* piv = reinterpret_cast<int*>(pivd);
+    double* gjw = nullptr;
+    DME_TRY(tp.get(&gjw, gj_work_doubles()));
 
     // X = sc M:  X22 = sc A, X12 = sc Q, X11 = -X22^T (implicit)
     launch_lincomb(X22, n, n, p->A, sc, nullptr, 0, nullptr, 0, 0.0, st);
@@ -380,20 +383,18 @@ dme_status compute_ew(dme_plan_t p, double tau, int* idx) {
     launch_lincomb(p12, n, n, V12, 1.0, U12, 1.0, nullptr, 0, 0.0, st);
     launch_lincomb(q22, n, n, V22, 1.0, U22, -1.0, nullptr, 0, 0.0, st);
     launch_lincomb(q12, n, n, V12, 1.0, U12, -1.0, nullptr, 0, 0.0, st);
-    // R22 = q22^{-1} p22
+    // R22 = q22^{-1} p22 (Gauss-Jordan with partial pivoting on a copy of q22)
     LUq = B22;
     R22 = B12;
     launch_lincomb(LUq, n, n, q22, 1.0, nullptr, 0, nullptr, 0, 0.0, st);
     launch_lincomb(R22, n, n, p22, 1.0, nullptr, 0, nullptr, 0, 0.0, st);
-    launch_lu(LUq, n, n, piv, p->status, st);
-    launch_lu_solve(LUq, n, n, piv, R22, n, n, 0, st);
+    DME_TRY(launch_gj_solve(LUq, n, n, R22, n, n, gjw, p->status, st));
     // R12 = p22^{-T} (p12 - q12 R22)
     R12 = C12;
     DME_TRY(gemm1(gp(n, n, n, q12, n, 0, R22, n, 0, R12, n, -1.0, 0, p12, 1.0), st));
     LUp = C22;
-    launch_lincomb(LUp, n, n, p22, 1.0, nullptr, 0, nullptr, 0, 0.0, st);
-    launch_lu(LUp, n, n, piv, p->status, st);
-    launch_lu_solve(LUp, n, n, piv, R12, n, n, 1, st);
+    launch_transpose(p22, LUp, n, n, n, n, st);
+    DME_TRY(launch_gj_solve(LUp, n, n, R12, n, n, gjw, p->status, st));
     // E = R22, W = R22^T R12 (symmetrised), then s doublings
     double* E = Y22;
     double* Wm = Y12;
