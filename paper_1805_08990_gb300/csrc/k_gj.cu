@@ -223,13 +223,13 @@ __global__ void __launch_bounds__(GJ_THREADS) gj_kernel(const GJArgs a) {
 constexpr size_t kGJMaxSmem = 200 * 1024;   // largest staged pivot row
 
 int gj_sms() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
+    static const int sms = [] {
+        int dev = 0, c = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
-    return std::max(sms, 1);
+        cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+        return std::max(c, 1);
+    }();
+    return sms;
 }
 
 // Blocks per SM, at most four (the grid is sized by the rows anyway).
@@ -246,11 +246,9 @@ size_t gj_work_doubles() { return 2 * (size_t)gj_sms() * 4 + 4; }
 dme_status launch_gj_solve(double* M, int n, int ldm, double* B, int nrhs, int ldb, double* work, int* status,
                            cudaStream_t st) {
     if (n <= 0) return DME_OK;
-    static bool attr = false;
-    if (!attr) {
-        DME_CUDA_TRY(cudaFuncSetAttribute(gj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGJMaxSmem));
-        attr = true;
-    }
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(gj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGJMaxSmem);
+    DME_CUDA_TRY(attr);
     const size_t row = sizeof(double) * ((size_t)n + nrhs);
     const bool staged = row <= kGJMaxSmem;
     const size_t smem = staged ? row : 0;

@@ -196,15 +196,14 @@ void launch_spmm(const int* ptr, const int* idx, const double* val, int n, int r
 }
 
 int leja_grid_max() {
-    static int g = 0;
-    if (!g) {
+    static const int g = [] {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, leja_persistent_kernel, LJ_THREADS, 0);
         // as many resident blocks as fit, up to eight per SM
-        g = std::max(1, sms * std::max(1, std::min(per, 8)));
-    }
+        return std::max(1, sms * std::max(1, std::min(per, 8)));
+    }();
     return g;
 }
 

@@ -413,19 +413,20 @@ dme_status launch_jacobi_eig(const double* G, int ldg, int r, double* Vt, int ld
                              cudaStream_t st, bool fp32) {
     if (r < 1 || r > LR_MAX_RANK) return set_error("jacobi: size must be in [1, 224]"), DME_EINVAL;
     if (fp32 && r > kJacobiF32Max) return set_error("jacobi: the single-precision pass needs r <= 176"), DME_EINVAL;
-    static bool attr = false;
-    if (!attr) {
-        DME_CUDA_TRY(cudaFuncSetAttribute(jacobi_eig_kernel<double, false>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)jacobi_smem<double>(LR_MAX_RANK, false)));
-        DME_CUDA_TRY(cudaFuncSetAttribute(jacobi_eig_kernel<double, true>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)jacobi_smem<double>(kJacobiSmemV, true)));
-        DME_CUDA_TRY(cudaFuncSetAttribute(jacobi_eig_kernel<float, true>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)jacobi_smem<float>(kJacobiF32Max, true)));
-        attr = true;
-    }
+    // shared-memory limits, set once (thread-safe static initialisation)
+    static const cudaError_t attr = [] {
+        cudaError_t e = cudaFuncSetAttribute(jacobi_eig_kernel<double, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)jacobi_smem<double>(LR_MAX_RANK, false));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(jacobi_eig_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)jacobi_smem<double>(kJacobiSmemV, true));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(jacobi_eig_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)jacobi_smem<float>(kJacobiF32Max, true));
+        return e;
+    }();
+    DME_CUDA_TRY(attr);
     // enough threads for the P(P+1)/2 rotation blocks of a sub-sweep, no more (fewer warps
     // make the two barriers per sub-sweep cheaper)
     const int P = (r + 1) / 2;

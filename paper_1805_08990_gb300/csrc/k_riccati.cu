@@ -419,12 +419,9 @@ dme_status launch_riccati_grouped(const std::vector<RicItem>& items, void* dev_d
     riccati_z_kernel<<<sz, 256, 0, st>>>(b);
     riccati_small_kernel<<<b.nd, 1024, 0, st>>>(b);
     riccati_y_kernel<<<sy, 128, 0, st>>>(b);
-    static bool attr_set = false;
-    if (!attr_set) {
-        DME_CUDA_TRY(cudaFuncSetAttribute(riccati_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)RU_SMEM));
-        attr_set = true;
-    }
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(riccati_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RU_SMEM);
+    DME_CUDA_TRY(attr);
     riccati_update_kernel<<<su, 256, RU_SMEM, st>>>(b);
     DME_CUDA_TRY(cudaGetLastError());
     return DME_OK;

@@ -769,7 +769,6 @@ int slice_kpad(int k) { return (k + OZ_BK - 1) / OZ_BK * OZ_BK; }
 
 size_t slice_buf_bytes(int rows, int k, int ns) { return (size_t)ns * rows * slice_kpad(k) * 2; }
 
-static bool g_attr_set = false;
 
 dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzParams p, cudaStream_t st) {
     if (p.M <= 0 || p.N <= 0) return DME_OK;
@@ -781,22 +780,20 @@ dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzPar
         set_error("ozaki gemm: triangle mode needs M == N");
         return DME_EINVAL;
     }
-    if (!g_attr_set) {
-        DME_CUDA_TRY(cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          OZ_SMEM_BYTES));
-        g_attr_set = true;
-    }
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
+    DME_CUDA_TRY(attr);
     const int tmt = (p.M + OZ_BM - 1) / OZ_BM, tnt = (p.N + OZ_BN - 1) / OZ_BN;
     p.tiles_n = tnt;
     const int tiles = p.tri ? tnt * (tnt + 1) / 2 : tmt * tnt;
     // split K of the last partial wave in two when it fills at most half of the SMs:
     // the wave then takes about half a tile time instead of a whole one
-    static int nsm = 0;
-    if (nsm == 0) {
-        int dev = 0;
-        DME_CUDA_TRY(cudaGetDevice(&dev));
-        DME_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    }
+    static const int nsm = [] {
+        int dev = 0, c = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+        return std::max(c, 1);
+    }();
     const int tail = tiles % nsm;
     p.split_parts = 1;
     p.split_first = tiles;
@@ -822,14 +819,10 @@ dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzPar
     return DME_OK;
 }
 
-static bool g_attr_grouped_set = false;
-
 dme_status ozaki_grouped_prepare() {
-    if (!g_attr_grouped_set) {
-        DME_CUDA_TRY(cudaFuncSetAttribute(ozaki_gemm_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          OZ_SMEM_BYTES));
-        g_attr_grouped_set = true;
-    }
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(ozaki_gemm_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
+    DME_CUDA_TRY(attr);
     return DME_OK;
 }
 
@@ -851,11 +844,7 @@ dme_status launch_ozaki_grouped(std::vector<OzGroupDesc>& items, OzGroupDesc* de
         live.push_back(it);
     }
     if (total == 0) return DME_OK;
-    if (!g_attr_grouped_set) {
-        DME_CUDA_TRY(cudaFuncSetAttribute(ozaki_gemm_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          OZ_SMEM_BYTES));
-        g_attr_grouped_set = true;
-    }
+    DME_TRY(ozaki_grouped_prepare());
     OzGroupDesc* d = dev_desc;
     if (arena) {
         d = static_cast<OzGroupDesc*>(arena->put(live.data(), live.size() * sizeof(OzGroupDesc)));
