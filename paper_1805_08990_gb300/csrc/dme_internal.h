@@ -91,19 +91,12 @@ void launch_symmetrize(double* X, int n, int ld, cudaStream_t st);   // X = (X +
 void launch_block_norm1(const double* A, const double* Q, int n, double* colsum_out, cudaStream_t st);
 void launch_max_reduce(const double* x, int len, double* out, cudaStream_t st);
 
-// Dense LU with partial pivoting, in place, unblocked right-looking
-// (one pivot kernel and one trailing-update kernel per column).
-void launch_lu(double* A, int n, int ld, int* piv, int* status, cudaStream_t st);
 // B (n x nrhs, ldb) <- M^{-1} B by Gauss-Jordan elimination with partial
 // pivoting in one cooperative launch (M, n x n with ldm, is overwritten).
 // work: gj_work_doubles() doubles.  A zero pivot column sets DEV_SINGULAR.
 dme_status launch_gj_solve(double* M, int n, int ldm, double* B, int nrhs, int ldb, double* work, int* status,
                            cudaStream_t st);
 size_t gj_work_doubles();
-// Solve (from an LU in place in LU with pivots piv) op(A0) X = B for n x nrhs B, in place.
-// trans = 0: A0 X = B.  trans = 1: A0^T X = B.
-void launch_lu_solve(const double* LU, int n, int ld, const int* piv, double* B, int nrhs, int ldb,
-                     int trans, cudaStream_t st);
 
 // Cholesky of a small SPD matrix (m <= 32) in place (lower), one warp.
 void launch_small_cholesky(double* R, int m, int* status, cudaStream_t st);

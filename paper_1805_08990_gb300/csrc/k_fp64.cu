@@ -252,11 +252,8 @@ dme_status gemm64_grouped(std::vector<GemmProb>& probs, GemmProb* dev_desc, cuda
 
 // ============================================================== elementwise
 __global__ void axpy_kernel(double* P, const double* Q, double a, int n, int ld) {
-    size_t total = (size_t)n * n;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        size_t i = e / n, j = e % n;
-        P[i * ld + j] += a * Q[i * ld + j];
-    }
+    for (int i = blockIdx.x; i < n; i += gridDim.x)
+        for (int j = threadIdx.x; j < n; j += blockDim.x) P[(size_t)i * ld + j] += a * Q[(size_t)i * ld + j];
 }
 
 static int grid_for(size_t total, int block = 256) {
@@ -265,7 +262,8 @@ static int grid_for(size_t total, int block = 256) {
 }
 
 void launch_axpy_sym(double* P, const double* Q, double a, int n, int ld, cudaStream_t st) {
-    axpy_kernel<<<grid_for((size_t)n * n), 256, 0, st>>>(P, Q, a, n, ld);
+    if (n <= 0) return;
+    axpy_kernel<<<std::min(n, 152 * 16), 256, 0, st>>>(P, Q, a, n, ld);
 }
 
 __global__ void transpose_kernel(const double* X, double* Y, int rows, int cols, int ldx, int ldy) {
@@ -301,40 +299,40 @@ void launch_scale_add_identity(double* X, double a, double c, int n, int ld, cud
     scale_add_identity_kernel<<<grid_for((size_t)n * n), 256, 0, st>>>(X, a, c, n, ld);
 }
 
+// A block per row (grid-stride over rows), threads over the columns.
 __global__ void lincomb_kernel(double* Y, int n, int ld, const double* X1, double c1, const double* X2,
                                double c2, const double* X3, double c3, double cI) {
-    size_t total = (size_t)n * n;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        size_t i = e / n, j = e % n, off = i * ld + j;
-        double v = 0.0;
-        if (X1) v += c1 * X1[off];
-        if (X2) v += c2 * X2[off];
-        if (X3) v += c3 * X3[off];
-        if (i == j) v += cI;
-        Y[off] = v;
-    }
+    for (int i = blockIdx.x; i < n; i += gridDim.x)
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const size_t off = (size_t)i * ld + j;
+            double v = 0.0;
+            if (X1) v += c1 * X1[off];
+            if (X2) v += c2 * X2[off];
+            if (X3) v += c3 * X3[off];
+            if (i == j) v += cI;
+            Y[off] = v;
+        }
 }
 
 void launch_lincomb(double* Y, int n, int ld, const double* X1, double c1, const double* X2, double c2,
                     const double* X3, double c3, double cI, cudaStream_t st) {
-    lincomb_kernel<<<grid_for((size_t)n * n), 256, 0, st>>>(Y, n, ld, X1, c1, X2, c2, X3, c3, cI);
+    if (n <= 0) return;
+    lincomb_kernel<<<std::min(n, 152 * 16), 256, 0, st>>>(Y, n, ld, X1, c1, X2, c2, X3, c3, cI);
 }
 
 __global__ void symmetrize_kernel(double* X, int n, int ld) {
-    // one thread per pair (i < j): both entries get the same average
-    size_t total = (size_t)n * n;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        size_t i = e / n, j = e % n;
-        if (i < j) {
-            double v = 0.5 * (X[i * ld + j] + X[j * ld + i]);
-            X[i * ld + j] = v;
-            X[j * ld + i] = v;
+    // a block per row i, threads over j > i: both entries of a pair get the same average
+    for (int i = blockIdx.x; i < n; i += gridDim.x)
+        for (int j = i + 1 + threadIdx.x; j < n; j += blockDim.x) {
+            const double v = 0.5 * (X[(size_t)i * ld + j] + X[(size_t)j * ld + i]);
+            X[(size_t)i * ld + j] = v;
+            X[(size_t)j * ld + i] = v;
         }
-    }
 }
 
 void launch_symmetrize(double* X, int n, int ld, cudaStream_t st) {
-    symmetrize_kernel<<<grid_for((size_t)n * n), 256, 0, st>>>(X, n, ld);
+    if (n <= 0) return;
+    symmetrize_kernel<<<std::min(n, 152 * 16), 256, 0, st>>>(X, n, ld);
 }
 
 // Column abs-sums of the Van Loan matrix [[-A^T, Q], [0, A]] (2n columns).
@@ -369,145 +367,6 @@ __global__ void max_reduce_kernel(const double* x, int len, double* out) {
 
 void launch_max_reduce(const double* x, int len, double* out, cudaStream_t st) {
     max_reduce_kernel<<<1, 1024, 0, st>>>(x, len, out);
-}
-
-// ============================================================== LU (partial pivoting)
-// Step k: pick the pivot row p = argmax_{i >= k} |A[i][k]| (smallest i on ties),
-// swap rows k and p over all columns, replace A[i][k] (i > k) by the multipliers.
-__global__ void __launch_bounds__(1024) lu_pivot_kernel(double* A, int n, int ld, int k, int* piv, int* status) {
-    __shared__ double sv[1024];
-    __shared__ int si[1024];
-    double best = -1.0;
-    int bi = n;
-    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-        double v = fabs(A[(size_t)i * ld + k]);
-        if (v > best) {
-            best = v;
-            bi = i;
-        }
-    }
-    sv[threadIdx.x] = best;
-    si[threadIdx.x] = bi;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            double o = sv[threadIdx.x + s];
-            int oi = si[threadIdx.x + s];
-            if (o > sv[threadIdx.x] || (o == sv[threadIdx.x] && oi < si[threadIdx.x])) {
-                sv[threadIdx.x] = o;
-                si[threadIdx.x] = oi;
-            }
-        }
-        __syncthreads();
-    }
-    const int p = si[0];
-    const double pv = sv[0];
-    if (threadIdx.x == 0) {
-        // a zero or NaN column keeps row k (piv stays a valid row index) and flags the status
-        piv[k] = (pv > 0.0 && p < n) ? p : k;
-        if (!(pv > 0.0)) atomicOr(status, DEV_SINGULAR);
-    }
-    if (!(pv > 0.0)) return;
-    if (p != k) {
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            double a = A[(size_t)k * ld + j];
-            A[(size_t)k * ld + j] = A[(size_t)p * ld + j];
-            A[(size_t)p * ld + j] = a;
-        }
-    }
-    __syncthreads();
-    const double d = A[(size_t)k * ld + k];
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[(size_t)i * ld + k] /= d;
-}
-
-// Trailing update A[i][j] -= A[i][k] * A[k][j] for i, j > k.
-__global__ void lu_update_kernel(double* A, int n, int ld, int k) {
-    const int j = k + 1 + blockIdx.x * 32 + threadIdx.x;
-    const int i0 = k + 1 + blockIdx.y * 32;
-    if (j >= n) return;
-    const double akj = A[(size_t)k * ld + j];
-    for (int di = threadIdx.y; di < 32; di += 8) {
-        int i = i0 + di;
-        if (i < n) A[(size_t)i * ld + j] -= A[(size_t)i * ld + k] * akj;
-    }
-}
-
-void launch_lu(double* A, int n, int ld, int* piv, int* status, cudaStream_t st) {
-    for (int k = 0; k < n; ++k) {
-        lu_pivot_kernel<<<1, 1024, 0, st>>>(A, n, ld, k, piv, status);
-        int rest = n - k - 1;
-        if (rest > 0) {
-            dim3 g((rest + 31) / 32, (rest + 31) / 32), b(32, 8);
-            lu_update_kernel<<<g, b, 0, st>>>(A, n, ld, k);
-        }
-    }
-}
-
-// B[i][:] -= c_i * B[k][:] for i in [r0, r1); c_i = LU[i][k] (colmode) or LU[k][i].
-__global__ void tri_update_kernel(const double* LU, int ld, int k, double* B, int ldb, int nrhs, int r0, int r1,
-                                  int rowcoef) {
-    const int j = blockIdx.x * 32 + threadIdx.x;
-    const int i0 = r0 + blockIdx.y * 32;
-    if (j >= nrhs) return;
-    const double bk = B[(size_t)k * ldb + j];
-    for (int di = threadIdx.y; di < 32; di += 8) {
-        int i = i0 + di;
-        if (i < r1) {
-            double c = rowcoef ? LU[(size_t)k * ld + i] : LU[(size_t)i * ld + k];
-            B[(size_t)i * ldb + j] -= c * bk;
-        }
-    }
-}
-
-__global__ void row_div_kernel(double* B, int ldb, int k, int nrhs, const double* LU, int ld) {
-    const double d = LU[(size_t)k * ld + k];
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nrhs; j += gridDim.x * blockDim.x)
-        B[(size_t)k * ldb + j] /= d;
-}
-
-// Row interchanges, applied in order k = 0..n-1 (forward) or n-1..0 (reverse).
-__global__ void apply_swaps_kernel(double* B, int ldb, int nrhs, const int* piv, int n, int reverse) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= nrhs) return;
-    for (int s = 0; s < n; ++s) {
-        int k = reverse ? n - 1 - s : s;
-        int p = piv[k];
-        if (p != k) {
-            double a = B[(size_t)k * ldb + j];
-            B[(size_t)k * ldb + j] = B[(size_t)p * ldb + j];
-            B[(size_t)p * ldb + j] = a;
-        }
-    }
-}
-
-static void tri_update(const double* LU, int ld, int k, double* B, int ldb, int nrhs, int r0, int r1, int rowcoef,
-                       cudaStream_t st) {
-    if (r1 <= r0) return;
-    dim3 g((nrhs + 31) / 32, (r1 - r0 + 31) / 32), b(32, 8);
-    tri_update_kernel<<<g, b, 0, st>>>(LU, ld, k, B, ldb, nrhs, r0, r1, rowcoef);
-}
-
-// P A0 = L U.  trans = 0: A0 X = B -> swaps, L y = b (unit lower), U x = y.
-// trans = 1: A0^T X = B -> U^T y = b, L^T z = y, x = P^T z (swaps reversed).
-void launch_lu_solve(const double* LU, int n, int ld, const int* piv, double* B, int nrhs, int ldb, int trans,
-                     cudaStream_t st) {
-    const int sg = (nrhs + 255) / 256;
-    const int rg = std::min((nrhs + 255) / 256, 64);
-    if (!trans) {
-        apply_swaps_kernel<<<sg, 256, 0, st>>>(B, ldb, nrhs, piv, n, 0);
-        for (int k = 0; k < n; ++k) tri_update(LU, ld, k, B, ldb, nrhs, k + 1, n, 0, st);
-        for (int k = n - 1; k >= 0; --k) {
-            row_div_kernel<<<rg, 256, 0, st>>>(B, ldb, k, nrhs, LU, ld);
-            tri_update(LU, ld, k, B, ldb, nrhs, 0, k, 0, st);
-        }
-    } else {
-        for (int k = 0; k < n; ++k) {
-            row_div_kernel<<<rg, 256, 0, st>>>(B, ldb, k, nrhs, LU, ld);
-            tri_update(LU, ld, k, B, ldb, nrhs, k + 1, n, 1, st);   // (U^T)[i][k] = U[k][i]
-        }
-        for (int k = n - 1; k >= 0; --k) tri_update(LU, ld, k, B, ldb, nrhs, 0, k, 1, st);  // (L^T)[i][k] = L[k][i]
-        apply_swaps_kernel<<<sg, 256, 0, st>>>(B, ldb, nrhs, piv, n, 1);
-    }
 }
 
 // ============================================================== small Cholesky

@@ -935,18 +935,18 @@ dme_status dme_plan_mass(const dme_plan_desc* desc, const double* M, const doubl
             }
         });
         TmpPool tp(st);
-        double *LU, *At, *Qt, *X, *Y, *pivd, *stat;
-        DME_TRY(tp.get(&LU, nn));
+        double *Mt, *At, *Qt, *X, *Y, *Mi, *gjw, *stat;
+        DME_TRY(tp.get(&Mt, nn));
         DME_TRY(tp.get(&At, nn));
         DME_TRY(tp.get(&Qt, nn));
         DME_TRY(tp.get(&X, nn));
         DME_TRY(tp.get(&Y, nn));
-        DME_TRY(tp.get(&pivd, (size_t)n));
+        DME_TRY(tp.get(&Mi, nn));
+        DME_TRY(tp.get(&gjw, gj_work_doubles()));
         DME_TRY(tp.get(&stat, 2));
-        int* piv = reinterpret_cast<int*>(pivd);
         int* status = reinterpret_cast<int*>(stat);
         DME_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
-        DME_CUDA_TRY(cudaMemcpyAsync(LU, M, nn * sizeof(double), cudaMemcpyDefault, st));
+        DME_CUDA_TRY(cudaMemcpyAsync(X, M, nn * sizeof(double), cudaMemcpyDefault, st));
         DME_CUDA_TRY(cudaMemcpyAsync(Y, A, nn * sizeof(double), cudaMemcpyDefault, st));
         if (desc->q_is_factor) {
             double* C = nullptr;
@@ -956,13 +956,13 @@ dme_status dme_plan_mass(const dme_plan_desc* desc, const double* M, const doubl
         } else {
             DME_CUDA_TRY(cudaMemcpyAsync(Qt, QorC, nn * sizeof(double), cudaMemcpyDefault, st));
         }
-        launch_lu(LU, n, n, piv, status, st);                                      // P M = L U
-        launch_transpose(Y, X, n, n, n, n, st);                                    // X = A^T
-        launch_lu_solve(LU, n, n, piv, X, n, n, 1, st);                            // X = M^-T A^T
-        launch_transpose(X, At, n, n, n, n, st);                                   // A~ = A M^-1
-        launch_lu_solve(LU, n, n, piv, Qt, n, n, 1, st);                           // M^-T Q
-        launch_transpose(Qt, X, n, n, n, n, st);                                   // Q M^-1 (Q symmetric)
-        launch_lu_solve(LU, n, n, piv, X, n, n, 1, st);                            // Q~ = M^-T Q M^-1
+        // M^-T by Gauss-Jordan with partial pivoting (a mass matrix is well conditioned)
+        launch_transpose(X, Mt, n, n, n, n, st);                                   // Mt = M^T
+        launch_lincomb(Mi, n, n, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0, 1.0, st);   // Mi = I
+        DME_TRY(launch_gj_solve(Mt, n, n, Mi, n, n, gjw, status, st));             // Mi = M^-T
+        DME_TRY(gemm1(gp(n, n, n, Y, n, 0, Mi, n, 1, At, n, 1.0), st));           // A~ = A M^-1
+        DME_TRY(gemm1(gp(n, n, n, Qt, n, 0, Mi, n, 1, Y, n, 1.0), st));           // Q M^-1
+        DME_TRY(gemm1(gp(n, n, n, Mi, n, 0, Y, n, 0, X, n, 1.0), st));            // Q~ = M^-T Q M^-1
         launch_symmetrize(X, n, n, st);
         DME_CUDA_TRY(cudaGetLastError());
         int hs = 0;
