@@ -27,6 +27,7 @@
 #include "plan_internal.h"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -98,7 +99,9 @@ struct dme_server_s {
                                        // (ids, not addresses: a new request may reuse a freed Req's address)
     std::map<int, int> tile_choice;    // autotuner: ceil(log2(64-tiles of a group)) -> tile 32 / 64
     std::vector<double> lat_ms;
-    int completed = 0, failed = 0, rounds = 0, graph_builds = 0, tuned = 0;
+    int completed = 0, failed = 0, tuned = 0;
+    std::atomic<int> rounds{0}, graph_builds{0};   // written by the stepper, read by dme_server_stats
+    double build_s = 0.0;   // host time spent building round graphs (stepper thread; under mu)
     double t_first = -1, t_last = 0;
     std::string stats;
 };
@@ -319,6 +322,7 @@ dme_status tune_tiles(dme_server_t s, std::vector<Req*>& res) {
         cudaEventDestroy(b);
         DME_TRY(st);
         DME_CUDA_TRY(cudaStreamSynchronize(s->st));
+        std::lock_guard<std::mutex> g(s->mu);   // dme_server_stats reads the map
         s->tile_choice[key] = best;
         s->tuned++;
     }
@@ -483,14 +487,21 @@ void step_loop(dme_server_t s) {
         dme_status st = DME_OK;
         bool same = s->round_exec != nullptr && s->round_ids.size() == res.size();
         for (size_t i = 0; same && i < res.size(); ++i) same = s->round_ids[i] == res[i]->id;
-        if (!same) st = build_round_graph(s, res);
+        if (!same) {
+            const double t0 = now_s();
+            st = build_round_graph(s, res);
+            std::lock_guard<std::mutex> g(s->mu);
+            s->build_s += now_s() - t0;
+        }
         // rounds before the next host check: none of the residents finishes
-        // earlier, and one round only while requests wait for admission
+        // earlier, and one round only while a planned request waits to join (a
+        // queued one can only be admitted when a slot frees, which the first
+        // rule catches, or is being planned, which takes longer than a round)
         int R = kMaxRoundsPerCheck;
         for (Req* r : res) R = std::min(R, r->nsteps - r->done_steps);
         {
             std::lock_guard<std::mutex> g(s->mu);
-            if (!s->queue.empty() || !s->ready.empty()) R = 1;
+            if (!s->ready.empty()) R = 1;
         }
         R = std::max(R, 1);
         for (int i = 0; i < R && st == DME_OK; ++i) {
@@ -730,9 +741,11 @@ const char* dme_server_stats(dme_server_t s) {
     char buf[512];
     snprintf(buf, sizeof(buf),
              "{\"completed\": %d, \"failed\": %d, \"resident\": %d, \"queued\": %d, \"rounds\": %d, "
-             "\"graph_builds\": %d, \"tuned_groups\": %d, \"tiles32\": %d, "
+             "\"graph_builds\": %d, \"graph_build_ms\": %.1f, \"tuned_groups\": %d, \"tiles32\": %d, "
              "\"p50_ms\": %.3f, \"p99_ms\": %.3f, \"solves_per_s\": %.4f, \"reserved_bytes\": %zu}",
-             s->completed, s->failed, resident, queued, s->rounds, s->graph_builds, s->tuned, t32, pct(0.5), pct(0.99),
+             s->completed, s->failed, resident, queued, s->rounds.load(), s->graph_builds.load(), s->build_s * 1e3,
+             s->tuned, t32,
+             pct(0.5), pct(0.99),
              span > 0 ? s->completed / span : 0.0, s->reserved);
     s->stats = buf;
     return s->stats.c_str();
