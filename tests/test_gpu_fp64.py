@@ -260,6 +260,26 @@ def test_mass_matrix_dre_matches_oracle(nx, prec):
     assert rel(out, ref) < (FP64_TOL if prec == "fp64" else 1e-7)
 
 
+@pytest.mark.parametrize("nx", [7, 12])
+def test_mass_matrix_needing_row_exchanges(nx):
+    """A mass matrix with its rows reversed (zero diagonal away from the middle):
+    the device's Gauss-Jordan inversion must exchange rows at almost every
+    column.  The plan's (E_t, W_t) for A M^-1 and M^-T Q M^-1 against the
+    oracle's transform (LU solves) and Van Loan exponential."""
+    pr = W.fe_heat_mass(nx=nx, m=2, p=3)
+    M = np.ascontiguousarray(pr.meta["M"][::-1])
+    assert np.count_nonzero(np.diag(M)) < pr.n // 2
+    tau = 1e-3
+    plan = dme.Plan(dev(pr.A), C=dev(pr.C), h=tau, flows=["F12"], M=dev(M))
+    E = np.empty((pr.n, pr.n))
+    Wm = np.empty((pr.n, pr.n))
+    plan.expm(tau, E, Wm)
+    At, Qt = O.mass_transform(M, pr.A, pr.Q)
+    E_ref, W_ref = O.van_loan(At, Qt, tau)
+    assert rel(E, E_ref) < FP64_TOL
+    assert rel(Wm, W_ref) < FP64_TOL
+
+
 def test_mass_matrix_plan_rejections():
     pr = W.fe_heat_mass(nx=5, m=2, p=3)
     M = pr.meta["M"].copy()
