@@ -84,7 +84,6 @@ void gemm64_prepare();
 // ---------------------------------------------------------------- small kernels
 void launch_axpy_sym(double* P, const double* Q, double a, int n, int ld, cudaStream_t st);
 void launch_transpose(const double* X, double* Y, int rows, int cols, int ldx, int ldy, cudaStream_t st);
-void launch_scale_add_identity(double* X, double a, double c, int n, int ld, cudaStream_t st);  // X = a X + c I
 void launch_lincomb(double* Y, int n, int ld, const double* X1, double c1, const double* X2, double c2,
                     const double* X3, double c3, double cI, cudaStream_t st);  // Y = c1X1+c2X2+c3X3+cI I
 void launch_symmetrize(double* X, int n, int ld, cudaStream_t st);   // X = (X + X^T)/2

@@ -256,10 +256,6 @@ __global__ void axpy_kernel(double* P, const double* Q, double a, int n, int ld)
         for (int j = threadIdx.x; j < n; j += blockDim.x) P[(size_t)i * ld + j] += a * Q[(size_t)i * ld + j];
 }
 
-static int grid_for(size_t total, int block = 256) {
-    size_t g = (total + block - 1) / block;
-    return (int)std::min<size_t>(std::max<size_t>(g, 1), 152 * 16);
-}
 
 void launch_axpy_sym(double* P, const double* Q, double a, int n, int ld, cudaStream_t st) {
     if (n <= 0) return;
@@ -285,19 +281,6 @@ void launch_transpose(const double* X, double* Y, int rows, int cols, int ldx, i
     transpose_kernel<<<g, b, 0, st>>>(X, Y, rows, cols, ldx, ldy);
 }
 
-__global__ void scale_add_identity_kernel(double* X, double a, double c, int n, int ld) {
-    size_t total = (size_t)n * n;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        size_t i = e / n, j = e % n;
-        double v = a * X[i * ld + j];
-        if (i == j) v += c;
-        X[i * ld + j] = v;
-    }
-}
-
-void launch_scale_add_identity(double* X, double a, double c, int n, int ld, cudaStream_t st) {
-    scale_add_identity_kernel<<<grid_for((size_t)n * n), 256, 0, st>>>(X, a, c, n, ld);
-}
 
 // A block per row (grid-stride over rows), threads over the columns.
 __global__ void lincomb_kernel(double* Y, int n, int ld, const double* X1, double c1, const double* X2,
