@@ -281,6 +281,17 @@ dme_status dme_server_destroy(dme_server_t srv);
 dme_status dme_gemm_split(int M, int N, int K, const double* A, const double* B, double* C,
                           void* cuda_stream);
 
+/* B <- M^{-1} B for a dense n x n M and an n x nrhs B (float64, row-major,
+ * host or device memory; M is copied and left unchanged): Gauss-Jordan
+ * elimination with partial pivoting (largest |entry| of the column, the
+ * smallest row on ties) in one cooperative launch with one grid barrier per
+ * column, the kernel of the plan's Pade step (the denominator systems
+ * q R = p of the [13/13] approximant, Eq. full) and of dme_plan_mass.
+ * Synchronises `cuda_stream` (NULL: a stream of its own).  DME_EINVAL if
+ * n < 1, nrhs < 0, a pointer is NULL, or a pivot column is zero or not finite
+ * (M singular; B is then undefined). */
+dme_status dme_dense_solve(const double* M, int n, double* B, int nrhs, void* cuda_stream);
+
 /* dme_gemm_split without any device allocation, for callers that cannot
  * call cudaMalloc: code whose device memory is owned by a host application's
  * own allocator, or loops that must not pay cudaMalloc's implicit device

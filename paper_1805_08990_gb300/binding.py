@@ -94,6 +94,7 @@ _SIGS = {
     "dme_server_destroy": (C.c_int, [C.c_void_p]),
     "dme_last_error": (C.c_char_p, []),
     "dme_gemm_split": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dme_dense_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
     "dme_gemm_split_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p]),
 }
@@ -369,6 +370,16 @@ def dme_gemm_split(A, B, C_out, stream=None):
     st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     _check(lib().dme_gemm_split(int(M), int(N), int(K), _ptr(A, keep), _ptr(B, keep), _out_ptr(C_out), st),
            "dme_gemm_split")
+
+
+def dme_dense_solve(M, B_inout, stream=None):
+    """B_inout <- M^{-1} B_inout (Gauss-Jordan with partial pivoting on the
+    device; M n x n, B n x nrhs, float64, host or device; M is not modified)."""
+    n = int(M.shape[0])
+    nrhs = int(B_inout.shape[1]) if len(B_inout.shape) == 2 else 1
+    keep: list = []
+    st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib().dme_dense_solve(_ptr(M, keep), n, _out_ptr(B_inout), nrhs, st), "dme_dense_solve")
 
 
 def dme_gemm_split_noalloc(A, B, C_out, stream=None):

@@ -975,6 +975,46 @@ dme_status dme_plan_mass(const dme_plan_desc* desc, const double* M, const doubl
     });
 }
 
+dme_status dme_dense_solve(const double* M, int n, double* B, int nrhs, void* cuda_stream) {
+    set_error("");
+    if (!M || !B || n < 1 || nrhs < 0) return set_error("dme_dense_solve: need M, B, n >= 1, nrhs >= 0"), DME_EINVAL;
+    if (nrhs == 0) return DME_OK;
+    return guarded([&]() -> dme_status {
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+        bool own = false;
+        if (!st) {
+            DME_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            own = true;
+        }
+        std::unique_ptr<CUstream_st, void (*)(cudaStream_t)> sg(own ? st : nullptr, [](cudaStream_t x) {
+            if (x) {
+                cudaStreamSynchronize(x);
+                cudaStreamDestroy(x);
+            }
+        });
+        TmpPool tp(st);
+        const size_t nn = (size_t)n * n, nb = (size_t)n * nrhs;
+        double *Md, *Bd, *gjw, *stat;
+        DME_TRY(tp.get(&Md, nn));
+        DME_TRY(tp.get(&Bd, nb));
+        DME_TRY(tp.get(&gjw, gj_work_doubles()));
+        DME_TRY(tp.get(&stat, 2));
+        int* status = reinterpret_cast<int*>(stat);
+        DME_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+        DME_CUDA_TRY(cudaMemcpyAsync(Md, M, nn * sizeof(double), cudaMemcpyDefault, st));
+        DME_CUDA_TRY(cudaMemcpyAsync(Bd, B, nb * sizeof(double), cudaMemcpyDefault, st));
+        DME_TRY(launch_gj_solve(Md, n, n, Bd, nrhs, nrhs, gjw, status, st));
+        int hs = 0;
+        DME_CUDA_TRY(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+        DME_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hs & DEV_SINGULAR) return set_error("dme_dense_solve: M is singular"), DME_EINVAL;
+        if (hs) return set_error("dme_dense_solve: device status " + std::to_string(hs)), DME_ECUDA;
+        DME_CUDA_TRY(cudaMemcpyAsync(B, Bd, nb * sizeof(double), cudaMemcpyDefault, st));
+        DME_CUDA_TRY(cudaStreamSynchronize(st));
+        return DME_OK;
+    });
+}
+
 dme_status dme_expm(dme_plan_t plan, double t, double* E_out, double* W_out) {
     if (!plan) return set_error("plan is NULL"), DME_EINVAL;
     if (!std::isfinite(t)) return set_error("t must be finite"), DME_EINVAL;

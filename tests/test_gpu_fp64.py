@@ -348,3 +348,39 @@ def test_extrapolation_rejections():
                                  (["F12", "F3"], "strang", 5, False), (["F12", "F3"], "strang", 2, True)]:
         with pytest.raises(dme.DmeError):
             plan_for(g, flows, comp, 0.01, extrap=q, fsal=fsal)
+
+
+# ---------------------------------------------------------------- the dense solve of the Pade step
+@pytest.mark.parametrize("n,nrhs", [(1, 3), (37, 5), (200, 300), (64, 26000)])
+def test_dense_solve_matches_numpy(n, nrhs):
+    """Gauss-Jordan with partial pivoting (the plan's Pade solves) against numpy's
+    LU solve; (64, 26000) leaves the pivot row too long for shared memory, so
+    the unstaged path of the kernel runs."""
+    rng = np.random.default_rng(n + nrhs)
+    M = rng.standard_normal((n, n)) + n ** 0.5 * np.eye(n)
+    B = rng.standard_normal((n, nrhs))
+    X = B.copy()
+    dme.dme_dense_solve(M, X)
+    ref = np.linalg.solve(M, B)
+    assert rel(X, ref) < 1e-12
+    Md, Xd = dev(M), dev(B)
+    dme.dme_dense_solve(Md, Xd)
+    assert rel(host(Xd), ref) < 1e-12
+    assert np.array_equal(host(Md), M)
+
+
+def test_dense_solve_pivots_and_rejects_singular():
+    n = 50
+    rng = np.random.default_rng(3)
+    P = np.eye(n)[rng.permutation(n)]
+    M = P @ (3.0 * np.eye(n) + 0.1 * rng.standard_normal((n, n)))   # dominant entries off the diagonal
+    assert np.count_nonzero(np.argmax(np.abs(M), axis=0) != np.arange(n)) > n // 2
+    B = rng.standard_normal((n, 4))
+    X = B.copy()
+    dme.dme_dense_solve(M, X)
+    assert rel(X, np.linalg.solve(M, B)) < 1e-11
+    S = M.copy()
+    S[:, 7] = 0.0                                          # a zero column: singular
+    with pytest.raises(dme.DmeError) as ei:
+        dme.dme_dense_solve(S, B.copy())
+    assert ei.value.status == dme.DME_EINVAL
