@@ -96,6 +96,13 @@ void launch_max_reduce(const double* x, int len, double* out, cudaStream_t st);
 dme_status launch_gj_solve(double* M, int n, int ldm, double* B, int nrhs, int ldb, double* work, int* status,
                            cudaStream_t st);
 size_t gj_work_doubles();
+// A cooperative launch of a kernel whose blocks wait on one another at grid
+// barriers: it needs all its blocks resident, and two such kernels running at
+// once (plans built on several host threads) could each hold part of the GPU
+// while waiting for the rest.  So these launches are serialised process-wide:
+// the stream's earlier work is waited for, then the kernel is launched and
+// waited for under one mutex.  Synchronises st; not for use under capture.
+dme_status coop_launch(const void* func, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t st);
 
 // Cholesky of a small SPD matrix (m <= 32) in place (lower), one warp.
 void launch_small_cholesky(double* R, int m, int* status, cudaStream_t st);

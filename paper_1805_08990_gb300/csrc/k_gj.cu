@@ -17,6 +17,7 @@
 #include "grid_sync.cuh"
 
 #include <algorithm>
+#include <mutex>
 
 namespace dme {
 
@@ -241,6 +242,15 @@ int gj_blocks_per_sm(size_t smem) {
 
 }  // namespace
 
+dme_status coop_launch(const void* func, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t st) {
+    static std::mutex mu;
+    DME_CUDA_TRY(cudaStreamSynchronize(st));
+    std::lock_guard<std::mutex> g(mu);
+    DME_CUDA_TRY(cudaLaunchCooperativeKernel(func, grid, block, args, smem, st));
+    DME_CUDA_TRY(cudaStreamSynchronize(st));
+    return DME_OK;
+}
+
 size_t gj_work_doubles() { return 2 * (size_t)gj_sms() * 4 + 4; }
 
 dme_status launch_gj_solve(double* M, int n, int ldm, double* B, int nrhs, int ldb, double* work, int* status,
@@ -272,9 +282,7 @@ dme_status launch_gj_solve(double* M, int n, int ldm, double* B, int nrhs, int l
     a.staged = staged ? 1 : 0;
     DME_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), st));
     void* args[] = {&a};
-    DME_CUDA_TRY(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(gj_kernel), dim3(grid), dim3(GJ_THREADS),
-                                             args, smem, st));
-    return DME_OK;
+    return coop_launch(reinterpret_cast<const void*>(gj_kernel), dim3(grid), dim3(GJ_THREADS), args, smem, st);
 }
 
 }  // namespace dme

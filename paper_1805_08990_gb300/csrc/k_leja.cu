@@ -250,8 +250,8 @@ dme_status launch_leja_apply(const LejaCall& c, cudaStream_t st) {
         }
         DME_CUDA_TRY(cudaMemsetAsync(c.bar, 0, 2 * sizeof(unsigned), st));
         void* args[] = {&a};
-        DME_CUDA_TRY(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(leja_persistent_kernel), dim3(grid),
-                                                 dim3(LJ_THREADS), args, 0, st));
+        DME_TRY(coop_launch(reinterpret_cast<const void*>(leja_persistent_kernel), dim3(grid), dim3(LJ_THREADS),
+                            args, 0, st));
     }
     return DME_OK;
 }
