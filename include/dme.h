@@ -292,6 +292,13 @@ dme_status dme_gemm_split(int M, int N, int K, const double* A, const double* B,
  * (M singular; B is then undefined). */
 dme_status dme_dense_solve(const double* M, int n, double* B, int nrhs, void* cuda_stream);
 
+/* Self-test of the library's bounded device waits: one GPU block waits at a
+ * grid barrier whose release word nothing ever writes, using the same wait as
+ * the persistent kernels (a poll limit, then DEV_TIMEOUT in a status word and
+ * return).  *timed_out = 1 when the wait gave up and reported it (takes about
+ * a second); the context stays usable.  DME_EINVAL if timed_out is NULL. */
+dme_status dme_wait_selftest(int* timed_out);
+
 /* dme_gemm_split without any device allocation, for callers that cannot
  * call cudaMalloc: code whose device memory is owned by a host application's
  * own allocator, or loops that must not pay cudaMalloc's implicit device

@@ -14,7 +14,7 @@ from .binding import (  # noqa: F401
     dme_plan, dme_plan_mass, dme_lr_plan, dme_lr_plan_csr, dme_lr_solve, dme_lr_factors, dme_lr_destroy, dme_expm, dme_apply, dme_apply_async, dme_sync, dme_plan_kernels_per_step, dme_step, dme_solve, dme_plan_bytes, dme_plan_destroy, dme_gain,
     dme_server_create, dme_submit, dme_poll, dme_submit_gain, dme_poll_gain, dme_server_stats, dme_server_destroy,
     dme_last_error,
-    dme_gemm_split, dme_gemm_split_noalloc, dme_dense_solve,
+    dme_gemm_split, dme_gemm_split_noalloc, dme_dense_solve, dme_wait_selftest,
 )
 
 EQ_IDS = {"dle": DME_DLE, "dre": DME_DRE, "gdle": DME_GDLE, "gdre": DME_GDRE}

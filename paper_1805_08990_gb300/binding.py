@@ -95,6 +95,7 @@ _SIGS = {
     "dme_last_error": (C.c_char_p, []),
     "dme_gemm_split": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dme_dense_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
+    "dme_wait_selftest": (C.c_int, [C.POINTER(C.c_int)]),
     "dme_gemm_split_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p]),
 }
@@ -380,6 +381,14 @@ def dme_dense_solve(M, B_inout, stream=None):
     keep: list = []
     st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     _check(lib().dme_dense_solve(_ptr(M, keep), n, _out_ptr(B_inout), nrhs, st), "dme_dense_solve")
+
+
+def dme_wait_selftest() -> bool:
+    """True when a device wait that can never be satisfied gave up with its
+    timeout status (the bounded waits of the persistent kernels)."""
+    t = C.c_int(0)
+    _check(lib().dme_wait_selftest(C.byref(t)), "dme_wait_selftest")
+    return bool(t.value)
 
 
 def dme_gemm_split_noalloc(A, B, C_out, stream=None):

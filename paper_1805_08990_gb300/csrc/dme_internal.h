@@ -96,6 +96,9 @@ void launch_max_reduce(const double* x, int len, double* out, cudaStream_t st);
 dme_status launch_gj_solve(double* M, int n, int ldm, double* B, int nrhs, int ldb, double* work, int* status,
                            cudaStream_t st);
 size_t gj_work_doubles();
+// Self-test of the bounded grid-barrier wait: one block waits for a release
+// that never comes; *timed_out = 1 once the wait gave up with DEV_TIMEOUT.
+dme_status wait_timeout_selftest(int* timed_out);
 // A cooperative launch of a kernel whose blocks wait on one another at grid
 // barriers: it needs all its blocks resident, and two such kernels running at
 // once (plans built on several host threads) could each hold part of the GPU

@@ -17,6 +17,8 @@
 #include "grid_sync.cuh"
 
 #include <algorithm>
+#include <functional>
+#include <memory>
 #include <mutex>
 
 namespace dme {
@@ -240,7 +242,34 @@ int gj_blocks_per_sm(size_t smem) {
     return std::max(0, std::min(per, 4));
 }
 
+// One block waits at a grid barrier whose release word nothing writes: the
+// bounded wait of grid_sync.cuh must give up and report DEV_TIMEOUT.
+__global__ void wait_timeout_selftest_kernel(unsigned* bar, int* status) {
+    __shared__ int s_ok;
+    gs_wait(bar, 1u, status, &s_ok);
+}
+
 }  // namespace
+
+dme_status wait_timeout_selftest(int* timed_out) {
+    cudaStream_t st = nullptr;
+    DME_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    std::unique_ptr<CUstream_st, void (*)(cudaStream_t)> sg(st, [](cudaStream_t x) { cudaStreamDestroy(x); });
+    int* words = nullptr;
+    DME_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&words), 4 * sizeof(int), st));
+    std::unique_ptr<int, std::function<void(int*)>> wg(words, [st](int* p) {
+        cudaFreeAsync(p, st);
+        cudaStreamSynchronize(st);
+    });
+    DME_CUDA_TRY(cudaMemsetAsync(words, 0, 4 * sizeof(int), st));
+    wait_timeout_selftest_kernel<<<1, 32, 0, st>>>(reinterpret_cast<unsigned*>(words), words + 2);
+    DME_CUDA_TRY(cudaGetLastError());
+    int hs = 0;
+    DME_CUDA_TRY(cudaMemcpyAsync(&hs, words + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DME_CUDA_TRY(cudaStreamSynchronize(st));
+    *timed_out = (hs & DEV_TIMEOUT) ? 1 : 0;
+    return DME_OK;
+}
 
 dme_status coop_launch(const void* func, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t st) {
     static std::mutex mu;

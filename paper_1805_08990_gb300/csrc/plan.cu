@@ -975,6 +975,13 @@ dme_status dme_plan_mass(const dme_plan_desc* desc, const double* M, const doubl
     });
 }
 
+dme_status dme_wait_selftest(int* timed_out) {
+    set_error("");
+    if (!timed_out) return set_error("dme_wait_selftest: timed_out is NULL"), DME_EINVAL;
+    *timed_out = 0;
+    return guarded([&]() -> dme_status { return wait_timeout_selftest(timed_out); });
+}
+
 dme_status dme_dense_solve(const double* M, int n, double* B, int nrhs, void* cuda_stream) {
     set_error("");
     if (!M || !B || n < 1 || nrhs < 0) return set_error("dme_dense_solve: need M, B, n >= 1, nrhs >= 0"), DME_EINVAL;

@@ -384,3 +384,12 @@ def test_dense_solve_pivots_and_rejects_singular():
     with pytest.raises(dme.DmeError) as ei:
         dme.dme_dense_solve(S, B.copy())
     assert ei.value.status == dme.DME_EINVAL
+
+
+def test_bounded_device_wait_gives_up_and_reports():
+    """A grid-barrier wait that nothing releases (the wait of the persistent
+    kernels) stops at its poll limit with DEV_TIMEOUT; the context stays usable."""
+    assert dme.dme_wait_selftest()
+    X = np.eye(3)
+    dme.dme_dense_solve(2.0 * np.eye(3), X)
+    assert np.allclose(X, 0.5 * np.eye(3))
