@@ -52,10 +52,12 @@ constexpr int kJacobiSweeps = 60;
 
 // Symmetric eigen-decomposition of the r x r matrix G (only (G + G^T)/2 is
 // used): lam[i] = eigenvalue i, row i of V^T (ldv) = its eigenvector.  A
-// rotation is skipped when |a_pq| <= max(1e-16 sqrt(|a_pp a_qq|), 1e-17 max_i
-// |a_ii|): relative accuracy for the eigenvalues that matter, and no chase of
-// rounding noise among those below the floor (a Gram matrix formed in floating
-// point carries absolute errors of that size anyway).  The sweeps stop after
+// rotation is skipped when |a_pq| <= max(1e-14 sqrt(|a_pp a_qq|), 1e-15 max_i
+// |a_ii|): what the compression drops with the off-diagonal part is then below
+// 1e-14 of the kept terms (the factored path's bar is 1e-11), the FP64 pass
+// after the single-precision one (off-diagonal about 1e-7) needs one rotating
+// sweep instead of two, and rounding noise below the floor is not chased (a
+// Gram matrix formed in floating point carries absolute errors of that size).  The sweeps stop after
 // one with no rotation (DEV_NONFINITE in *status after 60 sweeps or on a
 // non-finite entry).
 // T: the arithmetic (float for a fast first pass, double for the result).
@@ -73,8 +75,8 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double* __restri
     T* tt = sn + P;
     T* Vt = VS ? tt + P : reinterpret_cast<T*>(Vt_out);
     const int ldv = VS ? r : ldv_out;
-    constexpr T kRel = sizeof(T) == 4 ? T(1e-7) : T(1e-16);
-    constexpr T kFloor = sizeof(T) == 4 ? T(1e-8) : T(1e-17);
+    constexpr T kRel = sizeof(T) == 4 ? T(1e-7) : T(1e-14);
+    constexpr T kFloor = sizeof(T) == 4 ? T(1e-8) : T(1e-15);
     int* pp = reinterpret_cast<int*>(VS ? tt + P + (size_t)r * r : tt + P);
     int* qq = pp + P;
     // (i, j), i <= j, of every rotation block, packed as i << 8 | j (P <= 112)
