@@ -393,3 +393,26 @@ def test_bounded_device_wait_gives_up_and_reports():
     X = np.eye(3)
     dme.dme_dense_solve(2.0 * np.eye(3), X)
     assert np.allclose(X, 0.5 * np.eye(3))
+
+
+# ---------------------------------------------------------------- golden fixtures (tests/golden/)
+def test_cuda_path_reproduces_golden_fixtures():
+    """The stored oracle values of tests/golden/ (scalar DRE, Lie and Strang
+    F12F3 at N = 8..64; the 3 x 3-grid DLE after 10 F12 steps) from the CUDA
+    path: FP64 to 1e-11, the split path to 1e-7."""
+    import test_golden as G
+    p, _, vals = G.load_scalar()
+    A, C, B, R = (np.array([[p["a"]]]), np.array([[math.sqrt(p["q"])]]), np.array([[p["b"]]]),
+                  np.array([[p["r"]]]))
+    for (comp, N), v in vals.items():
+        plan = dme.Plan(dev(A), C=dev(C), h=p["T"] / N, flows=["F12", "F3"], comp=comp, B=dev(B), R=dev(R))
+        out = np.zeros((1, 1))
+        plan.solve(np.zeros((1, 1)), p["T"], N, out)
+        assert abs(out[0, 0] - v) <= FP64_TOL * abs(v), (comp, N)
+    P = G.load_dle()
+    pr = W.dle_heat(nx=3, T=0.1)
+    for prec, tol in (("fp64", FP64_TOL), ("split_bf16", 1e-7)):
+        plan = dme.Plan(dev(pr.A), C=dev(pr.C), h=pr.T / 10, flows=["F12"], comp="strang", prec=prec)
+        out = np.empty((9, 9))
+        plan.solve(pr.P0, pr.T, 10, out)
+        assert rel(out, P) < tol, prec
