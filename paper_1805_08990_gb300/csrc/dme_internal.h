@@ -100,12 +100,16 @@ size_t gj_work_doubles();
 // that never comes; *timed_out = 1 once the wait gave up with DEV_TIMEOUT.
 dme_status wait_timeout_selftest(int* timed_out);
 // A cooperative launch of a kernel whose blocks wait on one another at grid
-// barriers: it needs all its blocks resident, and two such kernels running at
-// once (plans built on several host threads) could each hold part of the GPU
-// while waiting for the rest.  So these launches are serialised process-wide:
-// the stream's earlier work is waited for, then the kernel is launched and
-// waited for under one mutex.  Synchronises st; not for use under capture.
-dme_status coop_launch(const void* func, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t st);
+// barriers: it needs all its blocks resident, and such kernels running at once
+// (plans built on several host threads) could each hold part of the GPU while
+// waiting for the rest.  So these launches are admitted process-wide: kernels
+// that fit at least 4 blocks per SM (blocks_per_sm) run together while their
+// grids sum to at most 4 blocks per SM, which every mix of them can hold at
+// once; any other runs alone.  The stream's earlier work is waited for before
+// admission, the kernel's completion before release.  Synchronises st; not for
+// use under capture.
+dme_status coop_launch(const void* func, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t st,
+                       int blocks_per_sm);
 
 // Cholesky of a small SPD matrix (m <= 32) in place (lower), one warp.
 void launch_small_cholesky(double* R, int m, int* status, cudaStream_t st);

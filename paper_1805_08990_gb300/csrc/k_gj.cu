@@ -17,6 +17,7 @@
 #include "grid_sync.cuh"
 
 #include <algorithm>
+#include <condition_variable>
 #include <functional>
 #include <memory>
 #include <mutex>
@@ -271,12 +272,29 @@ dme_status wait_timeout_selftest(int* timed_out) {
     return DME_OK;
 }
 
-dme_status coop_launch(const void* func, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t st) {
+dme_status coop_launch(const void* func, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t st,
+                       int blocks_per_sm) {
+    // Admission: kernels with at least 4 blocks per SM run together while their grids sum
+    // to at most 4 blocks per SM (every such mix is co-resident); any other launch runs alone.
     static std::mutex mu;
+    static std::condition_variable cv;
+    static long inflight = 0;
+    const long cap = 4L * gj_sms();
+    const long weight = (blocks_per_sm >= 4 && (long)grid.x <= cap) ? (long)grid.x : cap;
     DME_CUDA_TRY(cudaStreamSynchronize(st));
-    std::lock_guard<std::mutex> g(mu);
-    DME_CUDA_TRY(cudaLaunchCooperativeKernel(func, grid, block, args, smem, st));
-    DME_CUDA_TRY(cudaStreamSynchronize(st));
+    {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] { return inflight == 0 || inflight + weight <= cap; });
+        inflight += weight;
+    }
+    cudaError_t e = cudaLaunchCooperativeKernel(func, grid, block, args, smem, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    {
+        std::lock_guard<std::mutex> g(mu);
+        inflight -= weight;
+    }
+    cv.notify_all();
+    if (e != cudaSuccess) return set_error(std::string("cooperative launch: ") + cudaGetErrorString(e)), DME_ECUDA;
     return DME_OK;
 }
 
@@ -311,7 +329,8 @@ dme_status launch_gj_solve(double* M, int n, int ldm, double* B, int nrhs, int l
     a.staged = staged ? 1 : 0;
     DME_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), st));
     void* args[] = {&a};
-    return coop_launch(reinterpret_cast<const void*>(gj_kernel), dim3(grid), dim3(GJ_THREADS), args, smem, st);
+    return coop_launch(reinterpret_cast<const void*>(gj_kernel), dim3(grid), dim3(GJ_THREADS), args, smem, st,
+                       per);
 }
 
 }  // namespace dme

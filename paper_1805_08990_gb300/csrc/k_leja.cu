@@ -195,14 +195,23 @@ void launch_spmm(const int* ptr, const int* idx, const double* val, int n, int r
     spmm_kernel<<<grid, 256, 0, st>>>(ptr, idx, val, n, r, X, ldx, Y, ldy, alpha);
 }
 
+// Resident blocks per SM (at most eight) and the SM count.
+static int leja_per_sm() {
+    static const int per = [] {
+        int p = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, leja_persistent_kernel, LJ_THREADS, 0);
+        return std::max(1, std::min(p, 8));
+    }();
+    return per;
+}
+
 int leja_grid_max() {
     static const int g = [] {
-        int dev = 0, sms = 0, per = 0;
+        int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, leja_persistent_kernel, LJ_THREADS, 0);
         // as many resident blocks as fit, up to eight per SM
-        return std::max(1, sms * std::max(1, std::min(per, 8)));
+        return std::max(1, sms) * leja_per_sm();
     }();
     return g;
 }
@@ -251,7 +260,7 @@ dme_status launch_leja_apply(const LejaCall& c, cudaStream_t st) {
         DME_CUDA_TRY(cudaMemsetAsync(c.bar, 0, 2 * sizeof(unsigned), st));
         void* args[] = {&a};
         DME_TRY(coop_launch(reinterpret_cast<const void*>(leja_persistent_kernel), dim3(grid), dim3(LJ_THREADS),
-                            args, 0, st));
+                            args, 0, st, leja_per_sm()));
     }
     return DME_OK;
 }
