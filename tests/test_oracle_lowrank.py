@@ -156,8 +156,30 @@ def _compress_without_sigma(L, D, tol=1e-13):
     return U @ Y, np.diag(lam)
 
 
+def _t4_transposed_S(L, D, S, tau, rule="midpoint"):
+    St = np.ascontiguousarray(S.T)                                  # S^T L instead of S L
+    SL = St @ L
+    blocks = [L, math.sqrt(tau) * SL, (tau / math.sqrt(2.0)) * (St @ SL)]
+    r = D.shape[0]
+    Dn = np.zeros((3 * r, 3 * r))
+    for i in range(3):
+        Dn[i * r:(i + 1) * r, i * r:(i + 1) * r] = D
+    return np.hstack(blocks), Dn
+
+
+def _t4_s2_of_new_block(L, D, S, tau, rule="midpoint"):
+    SL = S @ L
+    blocks = [L, math.sqrt(tau) * SL, (tau / math.sqrt(2.0)) * (S @ (math.sqrt(tau) * SL))]   # S^2 of the scaled block
+    r = D.shape[0]
+    Dn = np.zeros((3 * r, 3 * r))
+    for i in range(3):
+        Dn[i * r:(i + 1) * r, i * r:(i + 1) * r] = D
+    return np.hstack(blocks), Dn
+
+
 @pytest.mark.parametrize("name,fn", [("lr_T4", _t4_without_sqrt), ("lr_T3", _t3_wrong_side),
-                                     ("compress", _compress_without_sigma)])
+                                     ("compress", _compress_without_sigma), ("lr_T4", _t4_transposed_S),
+                                     ("lr_T4", _t4_s2_of_new_block)])
 def test_pins_catch_planted_lowrank_mistakes(monkeypatch, name, fn):
     import oracle.dme_lowrank as lr
     monkeypatch.setattr(lr, name, fn)
