@@ -40,6 +40,7 @@ NOMINAL_FP64_TFLOPS = 1.25    # GB300 FP64 (non-tensor and tensor), the profilin
 
 
 FP64_MAX_STEPS = 16
+SPLIT_PAIRS = 14          # bf16 slice products per output of the split kernel
 
 # DRAM bytes (read + write) of one full 4096^3 launch of the tensor kernel, from the
 # ncu capture summarised in profiles/ozaki_gemm_n4096_ncu.md (955.0 MB + 122.9 MB).
@@ -368,6 +369,41 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+FULL_STEPS = 256          # the configuration's whole solve: T = 1, h = T/256
+
+
+def roofline_split(n, avg_ms, pairs, peak, peak_src, traffic, cong_ms, slice_ms):
+    """Roofline of the split tensor kernel.  Algorithmic work (the measurement
+    table's count for the bf16 split path): 6 bf16 products per FP64 product,
+    i.e. per congruence 6 x (2 n^3 + n^3) tensor flops over its two launches
+    (P E full, E^T X upper triangle), 9 n^3 per launch on average.  The slice
+    products the kernel actually issues (pairs x 3 n^3 per congruence) give the
+    tensor-pipe figure, reported beside it as slice_pipe_*."""
+    per_launch = 6 * 3.0 * n ** 3 / 2
+    achieved = per_launch / (avg_ms / 1e3) / 1e12
+    pipe = pairs * 3.0 * n ** 3 / 2 / (avg_ms / 1e3) / 1e12
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic,
+            "traffic_of": "one full n = 4096 product of the tensor kernel (dram__bytes_read.sum + "
+                          "dram__bytes_write.sum, ncu, profiles/ozaki_gemm_n4096_ncu.md), or null when the kernel "
+                          "changed since that capture",
+            "kernel": "ozaki_gemm_kernel (tcgen05 kind::f16, 2 launches per congruence)",
+            "work": "algorithmic: 6 bf16 products x (2n^3 + n^3) per congruence = 9 n^3 tensor flops per launch",
+            "peak_source": f"bf16 dense burst, {peak_src} (MEASURED_PEAKS.json)",
+            "avg_launch_ms": avg_ms, "slice_pairs": pairs, "slice_pipe_tflops": pipe, "slice_pipe_frac": pipe / peak,
+            "fp64_equivalent_tflops": 3.0 * n ** 3 / (2 * avg_ms / 1e3) / 1e12,
+            "congruence_ms": cong_ms, "slice_ms_per_congruence": slice_ms}
+
+
+def are_residual(P, A, Q, Bt):
+    """Relative algebraic Riccati residual ||A^T P + P A + Q - P Bt Bt^T P||_F / ||Q||_F
+    (diagnostic of the state at T = 1, computed with torch in float64)."""
+    import torch
+    Z = P @ Bt
+    R = A.T @ P + P @ A + Q - Z @ Z.T
+    return (torch.linalg.norm(R) / torch.linalg.norm(Q)).item()
+
+
 def run_ours(args):
     import torch
     rank, ws, local, dist = dist_init()
@@ -380,7 +416,7 @@ def run_ours(args):
     pr = W.dre_heat_large()
     n = pr.n
     K, Wu = args.steps, args.warmup
-    h = pr.T / 256
+    h = pr.T / FULL_STEPS
     stream = torch.cuda.Stream(device=dev)
 
     def to_dev(x):
@@ -390,8 +426,13 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
     results = {}
+    states = {}
     precs = ["fp64", "split"] if args.prec == "both" else [args.prec]
+    head = "split" if "split" in precs else "fp64"
     for prec in precs:
         kprec = "fp64" if prec == "fp64" else "split_bf16"
         t0 = time.perf_counter()
@@ -403,23 +444,45 @@ def run_ours(args):
         # the headline (split) arm times exactly K steps; the FP64 comparison arm (about 0.36 s
         # per step at n = 4096) at most FP64_MAX_STEPS of them, reported under its own key
         steps = min(K, FP64_MAX_STEPS) if prec == "fp64" else (args.split_steps or K)
-        warm = Wu
-        plan.step(P, warm)
+        plan.step(P, Wu)
         torch.cuda.synchronize(dev)
         barrier()
         torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        # one CUDA event after every step (graph replays enqueued back to back, no host sync)
+        evs = [ev() for _ in range(steps + 1)]
+        full = []
         with ClockSampler(local) as clk:
             torch.cuda.nvtx.range_push("timed")
-            e0.record(stream)
-            plan.step(P, steps)
-            e1.record(stream)
+            evs[0].record(stream)
+            for i in range(steps):
+                plan.step_async(P, 1)
+                evs[i + 1].record(stream)
             torch.cuda.synchronize(dev)
             torch.cuda.nvtx.range_pop()
-        barrier()
+            plan.sync()
+            barrier()
+            torch.cuda.synchronize(dev)
+            if prec == head:
+                # the configuration's whole solve (T = 1, 256 steps from P0 = 0), median of
+                # args.solve_reps CUDA-event windows enqueued back to back
+                for _ in range(args.solve_reps if prec == "split" else 1):
+                    a, b = ev(), ev()
+                    with torch.cuda.stream(stream):
+                        P.zero_()
+                    a.record(stream)
+                    plan.step_async(P, FULL_STEPS)
+                    b.record(stream)
+                    full.append((a, b))
+                torch.cuda.synchronize(dev)
+                plan.sync()
+        window_ms = evs[0].elapsed_time(evs[-1])
+        per_step = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+        ms = replica_max_ms(window_ms, dist, dev)
+        full_ms = [a.elapsed_time(b) for a, b in full]
+        if prec != head:
+            plan.step(P, FULL_STEPS - Wu - steps)     # continue the same trajectory to T = 1 (untimed)
         torch.cuda.synchronize(dev)
-        ms = replica_max_ms(e0.elapsed_time(e1), dist, dev)
+        states[prec] = P.clone()
         kps = plan.kernels_per_step
         # dominant kernel: the congruence E^T P E (+ W) applied alone; the library brackets each of
         # its launches with CUDA events on the plan's stream (profiling mode), read back per kind
@@ -430,8 +493,7 @@ def run_ours(args):
         plan.profile(True)
         for kind in range(4):
             plan.timing(kind)
-        c0 = torch.cuda.Event(enable_timing=True)
-        c1 = torch.cuda.Event(enable_timing=True)
+        c0, c1 = ev(), ev()
         c0.record(stream)
         for _ in range(R):
             plan.apply_async("F12", 0.5 * h, Pc)
@@ -442,33 +504,22 @@ def run_ours(args):
         kind = dme.DME_KIND_FP64_GEMM if prec == "fp64" else dme.DME_KIND_SPLIT_GEMM
         k_ms, k_launch = plan.timing(kind)
         s_ms, s_launch = plan.timing(dme.DME_KIND_SLICE)
-        # end to end through the C ABI with host buffers: H2D of P0, K steps, D2H of P(T)
-        P0h = torch.zeros(n, n, dtype=torch.float64).pin_memory()
-        Ph = torch.empty(n, n, dtype=torch.float64).pin_memory()
-        plan.solve(P0h, steps * h, steps, Ph)        # E, W for this h already cached
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        plan.solve(P0h, steps * h, steps, Ph)
-        e2e_s = time.perf_counter() - t0
-        # accuracy probe: the state after exactly 6 steps from P0 = 0 (FP64: warm-up 3 + timed 3)
-        if prec == "fp64" and warm + steps == 6:
-            P6 = P.clone()
-        else:
-            P6 = torch.zeros(n, n, dtype=torch.float64, device=dev)
-            plan.step(P6, 6)
-        results[prec + "_P6"] = P6
+        e2e_s = None
+        if prec == head:
+            # end to end through the C ABI with host buffers: H2D of P0, K steps, D2H of P(T)
+            P0h = torch.zeros(n, n, dtype=torch.float64).pin_memory()
+            Ph = torch.empty(n, n, dtype=torch.float64).pin_memory()
+            plan.solve(P0h, steps * h, steps, Ph)        # E, W for this h already cached
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            plan.solve(P0h, steps * h, steps, Ph)
+            e2e_s = time.perf_counter() - t0
         results[prec] = {"ms": ms, "steps": steps, "kps": kps, "cong_ms": cong_ms, "plan_s": plan_s,
-                         "e2e_s": e2e_s, "clocks": clk.summary(), "P": P, "bytes": plan.nbytes,
+                         "e2e_s": e2e_s, "clocks": clk.summary(), "bytes": plan.nbytes,
                          "kernel_ms": k_ms, "kernel_launches": k_launch, "slice_ms": s_ms, "slice_launches": s_launch,
-                         "R": R}
+                         "R": R, "per_step_ms": per_step, "full_ms": full_ms}
         plan.close()
 
-    err6 = None
-    if "fp64_P6" in results and "split_P6" in results:
-        a, b = results["split_P6"], results["fp64_P6"]
-        err6 = (torch.linalg.norm(a - b) / torch.linalg.norm(b)).item()
-    results = {k: v for k, v in results.items() if not k.endswith("_P6")}
-    head = "split" if "split" in results else "fp64"
     r = results[head]
     value = replica_value(r["steps"], r["ms"], ws)
     cong_flops = 3.0 * n ** 3          # P E (2n^3) + upper triangle of E^T X (n^3)
@@ -479,25 +530,14 @@ def run_ours(args):
                 "kernel": "gemm64_batch_kernel (congruence, 2 launches)",
                 "peak_source": "nominal GB300 FP64 rate (profiling recipe table)"}
     else:
-        # 14 bf16 slice products per output; per congruence one full GEMM (2n^3) and one triangle (n^3)
         avg_ms = r["kernel_ms"] / max(r["kernel_launches"], 1)
-        per_launch = 14 * cong_flops / 2
-        achieved = per_launch / (avg_ms / 1e3) / 1e12
-        peak = peaks["bf16_tflops"]
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": OZAKI_FULL_LAUNCH_DRAM_BYTES,
-                "traffic_of": "one full n = 4096 product (dram__bytes_read.sum + dram__bytes_write.sum, ncu --set full, "
-                              "profiles/ozaki_gemm_n4096_ncu.md); its algorithmic bytes: slices of A and B 302 MB + "
-                              "output pairs 134 MB",
-                "kernel": "ozaki_gemm_kernel (tcgen05 kind::f16, 2 launches per congruence)",
-                "peak_source": f"bf16 dense burst, {peaks_src} (MEASURED_PEAKS.json)",
-                "avg_launch_ms": avg_ms,
-                "fp64_equivalent_tflops": cong_flops / (2 * avg_ms / 1e3) / 1e12,
-                "congruence_ms": r["cong_ms"], "slice_ms_per_congruence": r["slice_ms"] / max(r["R"], 1)}
+        roof = roofline_split(n, avg_ms, SPLIT_PAIRS, peaks["bf16_tflops"], peaks_src, OZAKI_FULL_LAUNCH_DRAM_BYTES,
+                              r["cong_ms"], r["slice_ms"] / max(r["R"], 1))
+    med_step = statistics.median(r["per_step_ms"])
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": r["steps"], "warmup": Wu,
         "ms_per_step": r["ms"] / r["steps"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if head == "fp64" else "bf16 slices (5x4, exact f32 accumulation) -> f64",
+        "dtype": "f64" if head == "fp64" else "bf16 slices (exact f32 leading level) -> f64",
         "data": "synthetic (seeded generators; no datasets or weights)",
         "config": {"workload": WORKLOAD, "prec": head, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "working set P,E,W,X = 536 MB > L2 (no flush)", "plan_s": r["plan_s"],
@@ -508,14 +548,35 @@ def run_ours(args):
                 "what": f"dme_solve with pinned host P0 and P_out, {r['steps']} steps per call"},
         "gpu_launches": r["kps"] * r["steps"],
         "clocks": r["clocks"],
+        "median_step_ms": med_step,
+        "median_steps_per_s": 1e3 / med_step,
+        "timing": f"value = K steps / one CUDA-event window around K graph replays on the plan's stream; "
+                  f"median_step_ms = median of the K per-step event intervals",
     }
+    if r["full_ms"]:
+        fm = statistics.median(r["full_ms"])
+        line["full_solve"] = {"steps": FULL_STEPS, "T": pr.T, "windows": len(r["full_ms"]), "median_ms": fm,
+                              "min_ms": min(r["full_ms"]), "max_ms": max(r["full_ms"]),
+                              "steps_per_s": FULL_STEPS / (fm / 1e3), "solves_per_s": 1e3 / fm,
+                              "what": "P0 = 0 to T = 1 (256 Strang F12F3 steps), median of CUDA-event windows "
+                                      "around dme_step_async, clocks sampled over all windows"}
     for prec, rr in results.items():
         line[f"{prec}_steps_per_s"] = replica_value(rr["steps"], rr["ms"], ws)
         line[f"{prec}_steps_timed"] = rr["steps"]
         line[f"{prec}_plan_s"] = rr["plan_s"]
     line["peaks_source"] = peaks_src
-    if err6 is not None:
-        line["split_rel_err_vs_fp64_gpu_after_6_steps"] = err6
+    # accuracy at the configuration's horizon: both states are P(T = 1) from P0 = 0 after 256 steps
+    Ad, Qd, Bd = to_dev(pr.A), to_dev(pr.Q), to_dev(pr.B)
+    acc = {"steps": FULL_STEPS, "T": pr.T}
+    for prec, Pt in states.items():
+        acc[f"{prec}_are_residual"] = are_residual(Pt, Ad, Qd, Bd)
+    if "fp64" in states and "split" in states:
+        a, b = states["split"], states["fp64"]
+        acc["split_rel_err_vs_fp64"] = (torch.linalg.norm(a - b) / torch.linalg.norm(b)).item()
+    acc["what"] = ("relative Frobenius distance of the split-precision state from the FP64 GPU state at T = 1 "
+                   "(256 steps each from P0 = 0; the FP64 path is tied to the oracle at this size by the parity "
+                   "tests), and ||A^T P + P A + Q - P B R^-1 B^T P||_F / ||Q||_F of each")
+    line["accuracy"] = acc
     if args.extras and rank == 0:
         line["extras"] = extras_run(args, dme, pr, h, to_dev, stream, dev)
     if args.serving_requests > 0:
@@ -534,15 +595,69 @@ def run_ours(args):
                 "p99_ms": live["p99_ms"], "burst_p50_ms": burst["p50_ms"], "burst_p99_ms": burst["p99_ms"],
                 "roofline": serving_roofline(burst, prec, peaks)}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        secs, _, _ = oracle_steps(pr, args.cpu_steps)
-        line["cpu_baseline"] = {"value": args.cpu_steps / secs, "unit": "steps/s", "cores": os.cpu_count(),
-                                "kind": "oracle",
-                                "sample": f"{args.cpu_steps} oracle Strang F12F3 steps at n=4096 (numpy/OpenBLAS, "
-                                          "FP64); the oracle's own 2n x 2n expm for E, W is untimed"}
+        line["cpu_baseline"] = cpu_baseline_run(pr, args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+def cpu_baseline_run(pr, args):
+    """The oracle timed on the host cores: its own 2n x 2n exponential for E, W
+    (all threads, untimed), then, in a fresh process per thread count (1 and
+    nproc, set through OMP/OpenBLAS variables before numpy loads), one warm-up
+    Strang F12F3 step and args.cpu_runs timed steps; the median step time."""
+    import shutil
+    import tempfile
+    import oracle as O
+    h = pr.T / FULL_STEPS
+    t0 = time.perf_counter()
+    E, Wm = O.van_loan(pr.A, pr.Q, 0.5 * h)
+    plan_s = time.perf_counter() - t0
+    d = tempfile.mkdtemp(prefix="dme_oracle_")
+    try:
+        np.save(os.path.join(d, "E.npy"), E)
+        np.save(os.path.join(d, "W.npy"), Wm)
+        nproc = os.cpu_count() or 1
+        runs = {}
+        for threads in (1, nproc):
+            env = dict(os.environ)
+            for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+                env[k] = str(threads)
+            out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", d,
+                                  "--cpu-runs", str(args.cpu_runs)], env=env, capture_output=True, text=True,
+                                 timeout=1200)
+            if out.returncode != 0:
+                raise RuntimeError(f"oracle worker failed: {out.stderr[-400:]}")
+            runs[threads] = json.loads(out.stdout.strip().splitlines()[-1])["step_s"]
+    finally:
+        shutil.rmtree(d, ignore_errors=True)
+    med = {t: statistics.median(v) for t, v in runs.items()}
+    return {"value": 1.0 / med[nproc], "unit": "steps/s", "cores": nproc, "kind": "oracle",
+            "sample": f"the oracle (numpy/OpenBLAS, FP64) on the n = 4096 Strang F12F3 workload: 1 warm-up step, "
+                      f"then the median of {args.cpu_runs} single timed steps, in a fresh process per thread "
+                      f"count; its own 2n x 2n exponential for E, W ({plan_s:.1f} s, all threads) untimed",
+            "single_thread": {"value": 1.0 / med[1], "unit": "steps/s", "cores": 1, "step_s": runs[1]},
+            "step_s": runs[nproc]}
+
+
+def cpu_worker(args):
+    """Child process of cpu_baseline_run: time oracle steps with E, W from disk."""
+    import oracle as O
+    pr = W.dre_heat_large()
+    h = pr.T / FULL_STEPS
+    E = np.load(os.path.join(args.cpu_worker, "E.npy"))
+    Wm = np.load(os.path.join(args.cpu_worker, "W.npy"))
+    plan = O.Plan(pr.A, pr.Q, pr.B, pr.R)
+    plan._ew[float(0.5 * h)] = (E, Wm)
+    P = plan.step(np.array(pr.P0), "strang", ["F12", "F3"], h)        # warm-up
+    times = []
+    for _ in range(args.cpu_runs):
+        t0 = time.perf_counter()
+        P = plan.step(P, "strang", ["F12", "F3"], h)
+        times.append(time.perf_counter() - t0)
+    print(json.dumps({"step_s": times}), flush=True)
     return 0
 
 
@@ -717,7 +832,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="both", choices=["fp64", "split", "both"])
     ap.add_argument("--split-steps", type=int, default=0, help="override K for the split arm (0: K)")
-    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--cpu-runs", type=int, default=3, help="timed oracle steps per thread count (median)")
+    ap.add_argument("--cpu-worker", default="", help=argparse.SUPPRESS)
+    ap.add_argument("--solve-reps", type=int, default=10, help="CUDA-event windows of the whole 256-step solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--gemm-only", type=int, default=0, help="profile target: split GEMM of this size alone")
     ap.add_argument("--reps", type=int, default=3)
@@ -735,6 +852,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.cpu_worker:
+        return cpu_worker(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.lowrank_only:

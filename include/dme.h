@@ -51,16 +51,21 @@ typedef enum { DME_DLE = 0, DME_DRE = 1, DME_GDLE = 2, DME_GDRE = 3 } dme_eq;
 typedef enum { DME_F1 = 1, DME_F2 = 2, DME_F12 = 3, DME_F3 = 4, DME_F4 = 5 } dme_flow;
 typedef enum { DME_LIE = 1, DME_STRANG = 2 } dme_comp;
 /* DME_FP64: every product in float64 on the FP64 pipe.
+ * DME_SPLIT_TF32: reserved; not built.  A TF32 slice carries an 11-bit digit,
+ *   so the fp32 tensor-core sum of K products of two such digits is exact
+ *   only for K <= 4; plans asking for it fail with DME_EINVAL and say so in
+ *   dme_last_error().
  * DME_SPLIT_BF16: congruences (T1, T12, T4) as error-free bf16 slice products
- *   on tcgen05 tensor cores accumulated exactly in fp32 (Ozaki splitting),
- *   combined in fp64; n <= 4096.  The Riccati update with its m x m solve, the
- *   expm (Pade chain, denominator solve, squaring) stay fp64. */
-typedef enum { DME_FP64 = 0, DME_SPLIT_BF16 = 1 } dme_prec;
+ *   on tcgen05 tensor cores accumulated in fp32, exactly for the leading
+ *   level (Ozaki splitting), combined in fp64; n <= 4096.  The Riccati m x m
+ *   solve, the Pade denominator solve and the squarings of the exponential
+ *   stay fp64. */
+typedef enum { DME_FP64 = 0, DME_SPLIT_TF32 = 1, DME_SPLIT_BF16 = 2 } dme_prec;
 /* T4 rule; AUTO = midpoint for Strang, explicit Euler for Lie (§2.3). */
 typedef enum { DME_T4_AUTO = 0, DME_T4_MIDPOINT = 1, DME_T4_EULER = 2 } dme_t4_rule;
 
 typedef struct {
-    int n;              /* state dimension, 1 <= n <= 16384                          */
+    int n;              /* state dimension, 1 <= n <= 16384 (<= 4096 with DME_SPLIT_BF16) */
     int m;              /* columns of B (DRE/GDRE), 0 otherwise, m <= 32             */
     int p;              /* rows of C when q_is_factor = 1 (Q = C^T C)                 */
     int eq;             /* dme_eq                                                     */
@@ -133,6 +138,12 @@ dme_status dme_sync(dme_plan_t plan);
  * composition with the plan's h, in place.  Steps are replayed from a CUDA
  * graph captured on first use for this P. */
 dme_status dme_step(dme_plan_t plan, double* P, int nsteps);
+
+/* dme_step without the final synchronisation: the nsteps graph replays are
+ * only enqueued on the plan's stream (the first call for a new P captures the
+ * graph, as dme_step does).  Device-side failures are reported by the next
+ * dme_sync (or any synchronising call) on the plan. */
+dme_status dme_step_async(dme_plan_t plan, double* P, int nsteps);
 
 /* P_out = P_N, N = nsteps steps of size h = T/nsteps from P0 (§2).  If
  * T/nsteps differs from desc.h the missing E_t, W_t are built first.
@@ -310,11 +321,15 @@ dme_status dme_wait_selftest(int* timed_out);
  *   (5 M + 4 N) * roundup(K, 32) * 2 bytes of slices plus the row scales must
  *   fit in it (e.g. M = N = K = 640), otherwise DME_EINVAL with the sizes.
  * The first call on a device looks up that array's device address (with the
- * device current) and caches it; make that first call before any stream
- * capture.  Every call shares the one array and finds the previous call's
+ * device current) and caches it for the life of the process; make that first
+ * call before any stream capture.  After a cudaDeviceReset the cached address
+ * no longer names the array, so this entry point must not be used across a
+ * device reset.  Every call shares the one array and finds the previous call's
  * contents there: calls on the same device that overlap on the GPU (two
  * streams, or two host threads) race and must be serialised by the caller.
- * Synchronises `cuda_stream`. */
+ * Each call enqueues its work on `cuda_stream` (NULL: the legacy default
+ * stream), then waits for that stream to finish before it returns, to read the
+ * kernel's status word. */
 dme_status dme_gemm_split_noalloc(int M, int N, int K, const double* A, const double* B, double* C,
                                   void* cuda_stream);
 

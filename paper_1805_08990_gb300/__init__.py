@@ -7,11 +7,11 @@ load the library; the first call does, and fails loudly if it is not built.
 """
 from .binding import (  # noqa: F401
     DME_DLE, DME_DRE, DME_GDLE, DME_GDRE, DME_F1, DME_F2, DME_F12, DME_F3, DME_F4,
-    DME_LIE, DME_STRANG, DME_FP64, DME_SPLIT_BF16, DME_T4_AUTO, DME_T4_MIDPOINT, DME_T4_EULER,
+    DME_LIE, DME_STRANG, DME_FP64, DME_SPLIT_TF32, DME_SPLIT_BF16, DME_T4_AUTO, DME_T4_MIDPOINT, DME_T4_EULER,
     DME_KIND_SPLIT_GEMM, DME_KIND_SLICE, DME_KIND_FP64_GEMM, DME_KIND_RICCATI, dme_plan_profile, dme_plan_timing,
     DME_OK, DME_EINVAL, DME_ENOMEM, DME_ENOTSPD, DME_ECUDA, DME_ETIMEOUT, DME_EBUSY, DME_ENOTREADY,
     DmeError, LibraryNotBuilt, dme_plan_desc, make_desc, lib, header_functions,
-    dme_plan, dme_plan_mass, dme_lr_plan, dme_lr_plan_csr, dme_lr_solve, dme_lr_factors, dme_lr_destroy, dme_expm, dme_apply, dme_apply_async, dme_sync, dme_plan_kernels_per_step, dme_step, dme_solve, dme_plan_bytes, dme_plan_destroy, dme_gain,
+    dme_plan, dme_plan_mass, dme_lr_plan, dme_lr_plan_csr, dme_lr_solve, dme_lr_factors, dme_lr_destroy, dme_expm, dme_apply, dme_apply_async, dme_sync, dme_plan_kernels_per_step, dme_step, dme_step_async, dme_solve, dme_plan_bytes, dme_plan_destroy, dme_gain,
     dme_server_create, dme_submit, dme_poll, dme_submit_gain, dme_poll_gain, dme_server_stats, dme_server_destroy,
     dme_last_error,
     dme_gemm_split, dme_gemm_split_noalloc, dme_dense_solve, dme_wait_selftest,
@@ -66,6 +66,9 @@ class Plan:
 
     def step(self, P, nsteps=1):
         dme_step(self.handle, P, nsteps)
+
+    def step_async(self, P, nsteps=1):
+        dme_step_async(self.handle, P, nsteps)
 
     def solve(self, P0, T, nsteps, P_out):
         dme_solve(self.handle, P0, T, nsteps, P_out)

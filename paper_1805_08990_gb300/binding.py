@@ -23,13 +23,13 @@ STATUS_NAMES = ["DME_OK", "DME_EINVAL", "DME_ENOMEM", "DME_ENOTSPD", "DME_ECUDA"
 DME_DLE, DME_DRE, DME_GDLE, DME_GDRE = range(4)
 DME_F1, DME_F2, DME_F12, DME_F3, DME_F4 = 1, 2, 3, 4, 5
 DME_LIE, DME_STRANG = 1, 2
-DME_FP64, DME_SPLIT_BF16 = 0, 1
+DME_FP64, DME_SPLIT_TF32, DME_SPLIT_BF16 = 0, 1, 2
 DME_T4_AUTO, DME_T4_MIDPOINT, DME_T4_EULER = 0, 1, 2
 DME_KIND_SPLIT_GEMM, DME_KIND_SLICE, DME_KIND_FP64_GEMM, DME_KIND_RICCATI = 0, 1, 2, 3
 
 FLOW_IDS = {"F1": DME_F1, "F2": DME_F2, "F12": DME_F12, "F3": DME_F3, "F4": DME_F4}
 COMP_IDS = {"lie": DME_LIE, "strang": DME_STRANG}
-PREC_IDS = {"fp64": DME_FP64, "split_bf16": DME_SPLIT_BF16}
+PREC_IDS = {"fp64": DME_FP64, "split_tf32": DME_SPLIT_TF32, "split_bf16": DME_SPLIT_BF16}
 
 
 class LibraryNotBuilt(RuntimeError):
@@ -79,6 +79,7 @@ _SIGS = {
     "dme_plan_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "dme_plan_timing": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "dme_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "dme_step_async": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "dme_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_void_p]),
     "dme_plan_bytes": (C.c_size_t, [C.c_void_p]),
     "dme_gain": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -296,6 +297,10 @@ def dme_step(plan: int, P, nsteps: int):
     _check(lib().dme_step(plan, _out_ptr(P), int(nsteps)), "dme_step")
 
 
+def dme_step_async(plan: int, P, nsteps: int):
+    _check(lib().dme_step_async(plan, _out_ptr(P), int(nsteps)), "dme_step_async")
+
+
 def dme_solve(plan: int, P0, T: float, nsteps: int, P_out):
     keep: list = []
     _check(lib().dme_solve(plan, _ptr(P0, keep), float(T), int(nsteps), _out_ptr(P_out)), "dme_solve")
@@ -363,14 +368,38 @@ def dme_server_destroy(srv: int):
         _check(lib().dme_server_destroy(srv), "dme_server_destroy")
 
 
-def dme_gemm_split(A, B, C_out, stream=None):
-    """C_out = A @ B.T on the split-precision tensor-core path (device tensors)."""
+def _gemm_operands(where: str, A, B, C_out):
+    """(M, N, K) of C_out = A @ B.T after checking that A (M x K), B (N x K) and
+    C_out (M x N) are float64 C-contiguous CUDA tensors on the current device.
+    Anything else raises DmeError(DME_EINVAL) before the library is called: a
+    host pointer or a smaller C_out would otherwise reach the device kernels,
+    and a silent conversion would allocate."""
+    import torch
+
+    def bad(msg):
+        return DmeError(DME_EINVAL, where, msg)
+
+    for name, x in (("A", A), ("B", B), ("C_out", C_out)):
+        if not isinstance(x, torch.Tensor):
+            raise bad(f"{name} must be a torch CUDA tensor")
+        if x.dtype != torch.float64 or not x.is_contiguous() or x.dim() != 2:
+            raise bad(f"{name} must be a contiguous 2-D float64 tensor")
+        if not x.is_cuda or x.device.index != torch.cuda.current_device():
+            raise bad(f"{name} must live on the current CUDA device")
     M, K = A.shape
     N = B.shape[0]
-    keep: list = []
+    if B.shape[1] != K:
+        raise bad(f"A is {M} x {K} but B is {tuple(B.shape)}: both need K = {K} columns")
+    if tuple(C_out.shape) != (M, N):
+        raise bad(f"C_out is {tuple(C_out.shape)}, expected ({M}, {N})")
+    return int(M), int(N), int(K)
+
+
+def dme_gemm_split(A, B, C_out, stream=None):
+    """C_out = A @ B.T on the split-precision tensor-core path (device tensors)."""
+    M, N, K = _gemm_operands("dme_gemm_split", A, B, C_out)
     st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
-    _check(lib().dme_gemm_split(int(M), int(N), int(K), _ptr(A, keep), _ptr(B, keep), _out_ptr(C_out), st),
-           "dme_gemm_split")
+    _check(lib().dme_gemm_split(M, N, K, A.data_ptr(), B.data_ptr(), C_out.data_ptr(), st), "dme_gemm_split")
 
 
 def dme_dense_solve(M, B_inout, stream=None):
@@ -393,12 +422,11 @@ def dme_wait_selftest() -> bool:
 
 def dme_gemm_split_noalloc(A, B, C_out, stream=None):
     """C_out = A @ B.T like dme_gemm_split, with the library's fixed 8 MiB
-    device scratch instead of any allocation (see include/dme.h)."""
-    M, K = A.shape
-    N = B.shape[0]
-    keep: list = []
+    device scratch instead of any allocation (see include/dme.h).  The operands
+    are passed as they are (never converted or copied)."""
+    M, N, K = _gemm_operands("dme_gemm_split_noalloc", A, B, C_out)
     st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
-    _check(lib().dme_gemm_split_noalloc(int(M), int(N), int(K), _ptr(A, keep), _ptr(B, keep), _out_ptr(C_out), st),
+    _check(lib().dme_gemm_split_noalloc(M, N, K, A.data_ptr(), B.data_ptr(), C_out.data_ptr(), st),
            "dme_gemm_split_noalloc")
 
 

@@ -718,7 +718,8 @@ dme_status dme_lr_plan(const dme_plan_desc* desc, const double* A, const double*
     if (!desc || !A || !C) return set_error("desc, A and C are required"), DME_EINVAL;
     if (!desc->q_is_factor) return set_error("low-rank path: give Q as its factor C (q_is_factor = 1)"), DME_EINVAL;
     if (desc->prec != DME_FP64 && desc->prec != DME_SPLIT_BF16)
-        return set_error("low-rank path: prec must be DME_FP64 or DME_SPLIT_BF16"), DME_EINVAL;
+        return set_error("low-rank path: prec must be DME_FP64 or DME_SPLIT_BF16 (DME_SPLIT_TF32 is not built)"),
+               DME_EINVAL;
     if (desc->fsal || desc->extrap > 1) return set_error("low-rank path: no fsal / extrapolation"), DME_EINVAL;
     int q, rmax;
     double tol;

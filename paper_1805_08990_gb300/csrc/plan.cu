@@ -673,6 +673,10 @@ dme_status validate(const dme_plan_desc* d, const double* A, const double* QorC,
     if (d->eq < DME_DLE || d->eq > DME_GDRE) return set_error("bad eq"), DME_EINVAL;
     if (d->comp != DME_LIE && d->comp != DME_STRANG) return set_error("bad comp"), DME_EINVAL;
     if (d->nflows < 1 || d->nflows > 4) return set_error("nflows must be 1..4"), DME_EINVAL;
+    if (d->prec == DME_SPLIT_TF32)
+        return set_error("DME_SPLIT_TF32 is not built: an 11-bit TF32 digit keeps the fp32 tensor-core sum of "
+                         "K digit products exact only for K <= 4 (use DME_SPLIT_BF16)"),
+               DME_EINVAL;
     if (d->prec != DME_FP64 && d->prec != DME_SPLIT_BF16) return set_error("bad prec"), DME_EINVAL;
     if (!(d->h > 0.0) || !std::isfinite(d->h)) return set_error("h must be positive and finite"), DME_EINVAL;
     if (d->q_is_factor && (d->p < 1 || d->p > 16384)) return set_error("p must be >= 1 with q_is_factor"), DME_EINVAL;
@@ -1139,6 +1143,17 @@ dme_status dme_step(dme_plan_t plan, double* P, int nsteps) {
         DME_TRY(build_ops(plan, plan->d.h));
         DME_TRY(step_graph(plan, P, nsteps));
         return check_status(plan, "dme_step");
+    });
+}
+
+dme_status dme_step_async(dme_plan_t plan, double* P, int nsteps) {
+    if (!plan || !P) return set_error("plan and P are required"), DME_EINVAL;
+    if (nsteps < 0) return set_error("nsteps must be >= 0"), DME_EINVAL;
+    return guarded([&]() -> dme_status {
+        DME_TRY(build_ops(plan, plan->d.h));
+        DME_TRY(step_graph(plan, P, nsteps));
+        DME_CUDA_TRY(cudaGetLastError());
+        return DME_OK;
     });
 }
 

@@ -643,6 +643,10 @@ dme_status submit_impl(dme_server_t s, const dme_plan_desc* desc, const double* 
                        bool gain, uint64_t* ticket) {
     if (!s || !desc || !A || !QorC || !P0 || !ticket) return set_error("missing argument"), DME_EINVAL;
     if (!(T > 0.0) || nsteps < 1) return set_error("need T > 0 and nsteps >= 1"), DME_EINVAL;
+    if (desc->prec == DME_SPLIT_TF32)
+        return set_error("DME_SPLIT_TF32 is not built (an 11-bit TF32 digit breaks exact fp32 accumulation "
+                         "beyond K = 4); use DME_SPLIT_BF16"),
+               DME_EINVAL;
     if (desc->prec != DME_FP64 && desc->prec != DME_SPLIT_BF16) return set_error("bad prec"), DME_EINVAL;
     if (desc->fsal || desc->extrap > 1) return set_error("fsal and extrapolation are for plans only"), DME_EINVAL;
     if (desc->prec == DME_SPLIT_BF16 && desc->n > 4096) return set_error("split serving needs n <= 4096"), DME_EINVAL;

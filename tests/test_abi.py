@@ -77,3 +77,23 @@ def test_make_desc_fields():
     assert (d.n, d.m, d.p, d.eq, d.comp, d.nflows) == (7, 2, 3, dme.DME_DRE, dme.DME_LIE, 3)
     assert list(d.flows)[:3] == [dme.DME_F1, dme.DME_F3, dme.DME_F2]
     assert d.h == 0.25 and d.q_is_factor == 1
+
+
+def test_enum_values_follow_the_boundary_table(tmp_path):
+    """dme_prec keeps the boundary's numbering: FP64 = 0, SPLIT_TF32 = 1 (reserved,
+    rejected), SPLIT_BF16 = 2; the binding's constants match the C header."""
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    names = ["DME_FP64", "DME_SPLIT_TF32", "DME_SPLIT_BF16", "DME_DLE", "DME_DRE", "DME_GDLE", "DME_GDRE",
+             "DME_F1", "DME_F2", "DME_F12", "DME_F3", "DME_F4", "DME_LIE", "DME_STRANG", "DME_OK", "DME_EINVAL",
+             "DME_ENOTREADY"]
+    src = tmp_path / "enums.c"
+    body = "\n".join(f'printf("{n} %d\\n", (int){n});' for n in names)
+    src.write_text('#include <stdio.h>\n#include "dme.h"\nint main(void){\n' + body + '\nreturn 0;}\n')
+    exe = tmp_path / "enums"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    got = dict(zip(out[0::2], map(int, out[1::2])))
+    assert (got["DME_FP64"], got["DME_SPLIT_TF32"], got["DME_SPLIT_BF16"]) == (0, 1, 2)
+    for n in names:
+        assert got[n] == getattr(binding, n), n

@@ -61,3 +61,32 @@ def test_serving_stream_is_seeded_and_in_range(seed):
     # log-uniform n: about half of the requests below the geometric midpoint sqrt(32 * 1024) = 181
     below = sum(s["n"] < 181 for s in a) / len(a)
     assert 0.35 < below < 0.65
+
+
+def test_split_roofline_counts_the_algorithmic_products():
+    """frac uses 6 bf16 products per FP64 product (9 n^3 per launch on average);
+    the pairs the kernel issues only enter slice_pipe_*."""
+    n, ms = 4096, 0.8312
+    r = bench.roofline_split(n, ms, 14, 1920.7, "measured", None, 1.8, 0.12)
+    assert math.isclose(r["achieved"], 9.0 * n ** 3 / (ms / 1e3) / 1e12)
+    assert math.isclose(r["frac"], r["achieved"] / 1920.7)
+    assert 0.38 < r["frac"] < 0.40                      # the figure recomputed by hand for 0.8312 ms
+    assert math.isclose(r["slice_pipe_tflops"], 14 / 6 * r["achieved"])
+    assert math.isclose(r["fp64_equivalent_tflops"], r["achieved"] / 6)
+
+
+def test_are_residual_is_zero_at_the_care_solution():
+    """The diagnostic is the relative residual of the algebraic Riccati equation:
+    zero (to rounding) at scipy's stabilising solution."""
+    import scipy.linalg as sl
+    import torch
+    rng = np.random.default_rng(5)
+    n, m = 12, 3
+    A = W.laplacian_2d(4) if n == 16 else -np.eye(n) * 3 + 0.3 * rng.standard_normal((n, n))
+    Bt = rng.standard_normal((n, m))
+    C = rng.uniform(0, 1, (2, n))
+    Q = C.T @ C
+    X = sl.solve_continuous_are(A, Bt, Q, np.eye(m))
+    t = lambda x: torch.as_tensor(x, dtype=torch.float64)    # noqa: E731
+    assert bench.are_residual(t(X), t(A), t(Q), t(Bt)) < 1e-12
+    assert bench.are_residual(t(X * 1.01), t(A), t(Q), t(Bt)) > 1e-4

@@ -69,3 +69,42 @@ def test_generalised_dre_n2048_two_steps(gdre_case, prec, tol):
     assert np.array_equal(got, got.T)
     na = pr.meta["n_active"]
     assert np.all(got[na:, :] == 0) and np.all(got[:, na:] == 0)
+
+
+def _are_residual(P, pr):
+    A, Q, Bt = dev(pr.A), dev(pr.Q), dev(pr.B)          # R = I: Bt = B
+    Z = P @ Bt
+    R = A.T @ P + P @ A + Q - Z @ Z.T
+    return (torch.linalg.norm(R) / torch.linalg.norm(Q)).item()
+
+
+def test_large_dre_whole_horizon_split_vs_fp64():
+    """The configuration's whole solve, 256 Strang F12F3 steps from P0 = 0 to
+    T = 1: the split-precision state stays within 1e-7 of the FP64 GPU state
+    (itself tied to the oracle at this size above) at the full horizon.  Both
+    have the same algebraic Riccati residual, and halving h shrinks it (the
+    Strang state approaches the ARE solution, which the exact state reaches by
+    T = 1, as the oracle pins on a small grid at order two)."""
+    require_gpu()
+    pr = W.dre_heat_large()
+    N = 256
+    out = {}
+    for prec in ("fp64", "split_bf16"):
+        plan = plan_for(pr, ["F12", "F3"], "strang", pr.T / N, prec=prec)
+        P = torch.zeros(pr.n, pr.n, dtype=torch.float64, device="cuda")
+        plan.step(P, N)
+        out[prec] = P
+        if prec == "split_bf16":
+            plan2 = plan_for(pr, ["F12", "F3"], "strang", pr.T / (2 * N), prec=prec)
+            P2 = torch.zeros_like(P)
+            plan2.step(P2, 2 * N)
+            res_fine = _are_residual(P2, pr)
+            plan2.close()
+        plan.close()
+    a, b = out["split_bf16"], out["fp64"]
+    err = (torch.linalg.norm(a - b) / torch.linalg.norm(b)).item()
+    assert err < SPLIT_TOL, err
+    assert torch.equal(a, a.T)
+    r64, rsp = _are_residual(b, pr), _are_residual(a, pr)
+    assert abs(rsp - r64) <= 1e-6 * r64
+    assert res_fine < rsp / 2.5

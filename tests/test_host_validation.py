@@ -81,6 +81,8 @@ def test_plan_rejections_by_field():
     assert "extrapolation" in _einval(dme.dme_plan, d, A, C, B, R, S)      # F4 is not an exact flow
     d = _desc(prec="split_bf16", n=4097)
     assert "4096" in _einval(dme.dme_plan, d, A, C, B, R, None)
+    d = _desc(prec="split_tf32")
+    assert "DME_SPLIT_TF32 is not built" in _einval(dme.dme_plan, d, A, C, B, R, None)
 
 
 def test_plan_requires_data():
@@ -102,3 +104,19 @@ def test_server_and_solve_rejections():
     assert "max_slots" in _einval(dme.dme_server_create, 1 << 30, 0)
     assert "budget" in _einval(dme.dme_server_create, 0, 4)
     assert "nrhs" in _einval(dme.dme_dense_solve, np.zeros((0, 0)), np.zeros((0, 1)))
+
+
+def test_split_gemm_bindings_reject_bad_operands_before_any_call():
+    """dme_gemm_split and dme_gemm_split_noalloc take only float64 contiguous
+    CUDA tensors of matching shapes; anything else is refused on the host
+    (a host pointer or a short C_out would otherwise reach device kernels)."""
+    import torch
+    a = torch.zeros(4, 3, dtype=torch.float64)
+    b = torch.zeros(5, 3, dtype=torch.float64)
+    c = torch.zeros(4, 5, dtype=torch.float64)
+    for f in (dme.dme_gemm_split, dme.dme_gemm_split_noalloc):
+        for args in ((a, b, c), (a.numpy(), b, c), (a, b, c.float()), (a, b, c[:, :4]), (a, b[:, :2], c),
+                     (a.t(), b, c)):
+            with pytest.raises(dme.DmeError) as ei:
+                f(*args)
+            assert ei.value.status == dme.DME_EINVAL

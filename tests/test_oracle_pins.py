@@ -237,6 +237,20 @@ def test_long_horizon_reaches_algebraic_riccati_solution():
     assert 1.8 < math.log2(errs[0] / errs[1]) < 2.2
 
 
+def test_large_dre_shape_at_T1_approaches_the_are_solution_at_order_two():
+    """The large dense DRE's shape (Laplacian, B n x 8, C 8 x n, P0 = 0, T = 1)
+    on an 8 x 8 grid: the exact state at T = 1 is the stabilising ARE solution
+    up to e^(-2 * 2 pi^2) ~ 1e-17, so the Strang F12F3 state's distance to it is
+    the splitting error, O(h^2): it shrinks about four-fold per halving of h."""
+    pr = W.dre_heat_large(nx=8)
+    X = sla.solve_continuous_are(pr.A, pr.B, pr.Q, pr.R)
+    errs = [O.rel_fro(O.solve(pr.A, pr.Q, pr.P0, pr.T, N, "strang", ["F12", "F3"], B=pr.B, R=pr.R), X)
+            for N in (128, 256, 512)]
+    assert errs[2] < 1e-3
+    for a, b in zip(errs, errs[1:]):
+        assert 1.8 < math.log2(a / b) < 2.2
+
+
 def test_lqr_gain_scalar_steady_state_closes_the_loop():
     """§1: u = -R^-1 B^T P x.  For the scalar DRE at steady state, p = (a + beta)/s
     (s = b^2/r, beta = sqrt(a^2 + q s)), so the closed-loop pole a - b k is -beta."""
