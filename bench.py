@@ -40,7 +40,6 @@ NOMINAL_FP64_TFLOPS = 1.25    # GB300 FP64 (non-tensor and tensor), the profilin
 
 
 FP64_MAX_STEPS = 16
-SPLIT_PAIRS = 14          # bf16 slice products per output of the split kernel
 
 # DRAM bytes (read + write) of one full 4096^3 launch of the tensor kernel, from the
 # ncu capture summarised in profiles/ozaki_gemm_n4096_ncu.md (955.0 MB + 122.9 MB).
@@ -142,10 +141,11 @@ def serving_work(specs):
     """Algorithmic work of the stepping of these requests (Strang F12F3, one
     step = two congruences and T3): FP64 flops 6 n^3 + 3 n^2 m per step (the
     congruence 2 n^3 + n^3 with the symmetric half, Z = P Bt and the update
-    of T3); tensor flops of the split path 2 x 2 x 14 x 2 n^3 per step (two
-    slice-pair GEMMs of 14 bf16 products per congruence)."""
+    of T3); tensor flops of the split path: the same congruences as 6 bf16
+    products each (the algorithmic count of the headline roofline), 36 n^3
+    per step."""
     f64 = sum(sp["steps"] * (6.0 * sp["n"] ** 3 + 3.0 * sp["n"] ** 2 * sp["m"]) for sp in specs)
-    tens = sum(sp["steps"] * 112.0 * sp["n"] ** 3 for sp in specs)
+    tens = sum(sp["steps"] * 36.0 * sp["n"] ** 3 for sp in specs)
     return f64, tens
 
 
@@ -280,7 +280,7 @@ def run_config_suite(args):
             with torch.cuda.stream(stream):
                 plan = dme.Plan(t(pr.A), C=t(pr.C), h=pr.T / N, flows=flows, comp=comp,
                                 B=t(pr.B) if uses_B else None, R=t(pr.R) if uses_B else None,
-                                S=t(pr.S) if uses_S else None, prec=kprec, stream=stream)
+                                S=t(pr.S) if uses_S else None, prec=kprec, stream=stream, horizon=N)
             P = torch.zeros(pr.n, pr.n, dtype=torch.float64, device=dev)
             steps = min(N, 32) if prec == "fp64" else N
             plan.step(P, 3)
@@ -292,12 +292,13 @@ def run_config_suite(args):
             torch.cuda.synchronize(dev)
             ms = e0.elapsed_time(e1) / steps
             row[prec] = {"steps_per_s": 1e3 / ms, "ms_per_step": ms, "kernels_per_step": plan.kernels_per_step,
+                         "slice_pairs": plan.split_choice[0],
                          "congruence_flop_per_step": flops(pr.n),
                          "fp64_equivalent_tflops": flops(pr.n) / (ms / 1e3) / 1e12}
             plan.close()
         rows.append(row)
     print(json.dumps({"config_suite": rows, "note": "flop counts are the congruences' 3 n^3 each (P E and the "
-                      "upper triangle of E^T X); split rows run 14 bf16 slice products per congruence flop"}))
+                      "upper triangle of E^T X); split rows run slice_pairs bf16 products per congruence flop"}))
 
 
 def run_serving_suite(args):
@@ -438,8 +439,9 @@ def run_ours(args):
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
             plan = dme.Plan(to_dev(pr.A), C=to_dev(pr.C), h=h, flows=["F12", "F3"], comp="strang",
-                            B=to_dev(pr.B), R=to_dev(pr.R), prec=kprec, stream=stream)
+                            B=to_dev(pr.B), R=to_dev(pr.R), prec=kprec, stream=stream, horizon=FULL_STEPS)
         plan_s = time.perf_counter() - t0
+        pairs, pair_est = plan.split_choice
         P = torch.zeros(n, n, dtype=torch.float64, device=dev)
         # the headline (split) arm times exactly K steps; the FP64 comparison arm (about 0.36 s
         # per step at n = 4096) at most FP64_MAX_STEPS of them, reported under its own key
@@ -517,7 +519,7 @@ def run_ours(args):
         results[prec] = {"ms": ms, "steps": steps, "kps": kps, "cong_ms": cong_ms, "plan_s": plan_s,
                          "e2e_s": e2e_s, "clocks": clk.summary(), "bytes": plan.nbytes,
                          "kernel_ms": k_ms, "kernel_launches": k_launch, "slice_ms": s_ms, "slice_launches": s_launch,
-                         "R": R, "per_step_ms": per_step, "full_ms": full_ms}
+                         "R": R, "per_step_ms": per_step, "full_ms": full_ms, "pairs": pairs, "pair_est": pair_est}
         plan.close()
 
     r = results[head]
@@ -531,13 +533,13 @@ def run_ours(args):
                 "peak_source": "nominal GB300 FP64 rate (profiling recipe table)"}
     else:
         avg_ms = r["kernel_ms"] / max(r["kernel_launches"], 1)
-        roof = roofline_split(n, avg_ms, SPLIT_PAIRS, peaks["bf16_tflops"], peaks_src, OZAKI_FULL_LAUNCH_DRAM_BYTES,
+        roof = roofline_split(n, avg_ms, r["pairs"], peaks["bf16_tflops"], peaks_src, OZAKI_FULL_LAUNCH_DRAM_BYTES,
                               r["cong_ms"], r["slice_ms"] / max(r["R"], 1))
     med_step = statistics.median(r["per_step_ms"])
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": r["steps"], "warmup": Wu,
         "ms_per_step": r["ms"] / r["steps"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if head == "fp64" else "bf16 slices (exact f32 leading level) -> f64",
+        "dtype": "f64" if head == "fp64" else f"bf16 slices, {r['pairs']} slice products (exact f32 leading level) -> f64",
         "data": "synthetic (seeded generators; no datasets or weights)",
         "config": {"workload": WORKLOAD, "prec": head, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "working set P,E,W,X = 536 MB > L2 (no flush)", "plan_s": r["plan_s"],
@@ -573,6 +575,9 @@ def run_ours(args):
     if "fp64" in states and "split" in states:
         a, b = states["split"], states["fp64"]
         acc["split_rel_err_vs_fp64"] = (torch.linalg.norm(a - b) / torch.linalg.norm(b)).item()
+    if "split" in results:
+        acc["split_pairs"] = results["split"]["pairs"]
+        acc["split_pair_estimate"] = results["split"]["pair_est"]
     acc["what"] = ("relative Frobenius distance of the split-precision state from the FP64 GPU state at T = 1 "
                    "(256 steps each from P0 = 0; the FP64 path is tied to the oracle at this size by the parity "
                    "tests), and ||A^T P + P A + Q - P B R^-1 B^T P||_F / ||Q||_F of each")

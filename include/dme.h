@@ -76,7 +76,9 @@ typedef struct {
     double h;           /* step size                                                  */
     int q_is_factor;    /* 1: QorC is C (p x n); 0: QorC is Q (n x n, symmetric)      */
     int t4_rule;        /* dme_t4_rule                                                */
-    int slices;         /* DME_SPLIT_BF16: bf16 slices per operand, 0 = default (4)   */
+    int pairs;          /* DME_SPLIT_BF16: bf16 slice products per output of the     */
+                        /*    tensor-core products: 10, 13 or 14, or 0 = chosen at    */
+                        /*    plan time (see dme_plan); ignored for DME_FP64          */
     int fsal;           /* 1: merge the outer half steps of consecutive Strang steps  */
                         /*    (T_a(h/2) T_a(h/2) = T_a(h) for an exact outer flow; no */
                         /*    F4 outside).  Same result up to rounding, one outer     */
@@ -85,6 +87,9 @@ typedef struct {
                         /*    schemes"): P <- sum_k gamma_k (S_{h/k})^k P, k = 1..q,  */
                         /*    gamma_k = prod_{j!=k} k^2/(k^2-j^2); q <= 4; Strang of  */
                         /*    exact flows only (no F4).  0 or 1 = plain.  Plans only. */
+    int horizon;        /* steps over which the split path's error target must hold  */
+                        /*    when pairs = 0 (0: 1024)                                */
+    double tol;         /* that target, relative Frobenius error (0: 1e-7)            */
 } dme_plan_desc;
 
 typedef struct dme_plan_s* dme_plan_t;
@@ -99,6 +104,18 @@ typedef struct dme_server_s* dme_server_t;
  *   A: n x n.  QorC: n x n or p x n.  B: n x m (NULL unless DRE/GDRE).
  *   R: m x m SPD (NULL unless DRE/GDRE).  S: n x n (NULL unless GDLE/GDRE).
  *   cuda_stream: a cudaStream_t, or NULL for a plan-owned stream.
+ * With DME_SPLIT_BF16 every per-step product is an error-free bf16 slice
+ * product (a leading 7-bit digit, trailing 9-bit digits; 4 slices of P, 4 or 5
+ * of E^T and S).  With pairs = 0 the plan measures, for every E_t (and S), the
+ * relative error of one congruence G X G^T of the probe state X = W_t (Q if
+ * W_t = 0) under 10, 13 and 14 slice products against the FP64 congruence,
+ * and keeps the cheapest whose error e satisfies 4 N e <= tol, N = the
+ * congruences of `horizon` steps (the worst case: every application's error
+ * adding up coherently, none damped); 14 if none does (dme_plan_split_choice
+ * reports the choice and the estimate).  Above n = 511 the Pade products of
+ * the exponential run on the tensor cores too, in an accurate mode (21 slice
+ * products with the exact sums of 512-wide K chunks combined in fp64); the
+ * denominator solves and the squarings stay FP64.
  * Errors: DME_EINVAL (inconsistent desc), DME_ENOTSPD (R), DME_ENOMEM,
  * DME_ECUDA.  On error *out is NULL. */
 dme_status dme_plan(const dme_plan_desc* desc, const double* A, const double* QorC,
@@ -155,6 +172,11 @@ dme_status dme_solve(dme_plan_t plan, const double* P0, double T, int nsteps, do
  * P: n x n symmetric, device memory.  K_out: m x n row-major, host or device.
  * DME_EINVAL for a plan without B and R.  Synchronises the plan's stream. */
 dme_status dme_gain(dme_plan_t plan, const double* P, double* K_out);
+
+/* The split path's slice products per output (*pairs; 0 for DME_FP64) and the
+ * estimate that chose them (*est = 4 N e of dme_plan, or a negative value when
+ * pairs was given explicitly).  Either pointer may be NULL. */
+dme_status dme_plan_split_choice(dme_plan_t plan, int* pairs, double* est);
 
 /* Bytes of device memory the plan holds. */
 size_t dme_plan_bytes(dme_plan_t plan);
@@ -281,16 +303,26 @@ const char* dme_server_stats(dme_server_t srv);
 dme_status dme_server_destroy(dme_server_t srv);
 
 /* C = A B^T on the split-precision tensor-core path used by DME_SPLIT_BF16:
- * every row of A (M x K) and of B (N x K) is scaled by a power of two and cut
- * into bf16 slices of 6 + 7 + 7 + ... bits (five for A, four for B); the 14
- * slice products of levels 0..4 are accumulated in fp32 on tcgen05 tensor
- * cores, exactly for level 0 (K <= 4096 keeps every partial sum below 2^24
- * units), and combined in fp64.  Entry errors are ~2^-28 of the B row scale
- * times the A row scale (times sqrt(K) for random signs).  All
- * matrices are float64 row-major device memory; C is M x N.  Synchronises
- * `cuda_stream`.  DME_EINVAL unless 1 <= K <= 4096. */
+ * every row of A (M x K) and of B (N x K) is scaled by a power of two, rounded
+ * to a fixed-point integer and cut into bf16 digits (a leading digit |d| <= 64,
+ * then 9-bit digits |d| <= 256; five slices for A, four for B); the 14 slice
+ * products of levels 0..4 are accumulated in fp32 on tcgen05 tensor cores,
+ * exactly for level 0 (K <= 4096 keeps every partial sum below 2^24 units),
+ * and combined in fp64.  Entry errors are ~2^-34 of the B row scale times the
+ * A row scale (times sqrt(K) for random signs).  All matrices are float64
+ * row-major device memory; C is M x N.  Synchronises `cuda_stream`.
+ * DME_EINVAL unless 1 <= K <= 4096. */
 dme_status dme_gemm_split(int M, int N, int K, const double* A, const double* B, double* C,
                           void* cuda_stream);
+
+/* C = A B^T in the accurate split mode the plan uses for the products of the
+ * Pade approximant (Eq. full): six bf16 slices of 7-bit digits per row of A
+ * and of B (rows rounded at 2^-42 of their scale), the 21 slice products of
+ * levels 0..5, K taken in chunks of 512 in which the fp32 sums of levels 0, 1
+ * and 2 are exact, the chunk results added in fp64.  Entry errors are ~2^-39
+ * of the row scales' product (times sqrt(K)).  Same arguments, layout and
+ * errors as dme_gemm_split; synchronises `cuda_stream`. */
+dme_status dme_gemm_split_acc(int M, int N, int K, const double* A, const double* B, double* C, void* cuda_stream);
 
 /* B <- M^{-1} B for a dense n x n M and an n x nrhs B (float64, row-major,
  * host or device memory; M is copied and left unchanged): Gauss-Jordan

@@ -11,10 +11,10 @@ from .binding import (  # noqa: F401
     DME_KIND_SPLIT_GEMM, DME_KIND_SLICE, DME_KIND_FP64_GEMM, DME_KIND_RICCATI, dme_plan_profile, dme_plan_timing,
     DME_OK, DME_EINVAL, DME_ENOMEM, DME_ENOTSPD, DME_ECUDA, DME_ETIMEOUT, DME_EBUSY, DME_ENOTREADY,
     DmeError, LibraryNotBuilt, dme_plan_desc, make_desc, lib, header_functions,
-    dme_plan, dme_plan_mass, dme_lr_plan, dme_lr_plan_csr, dme_lr_solve, dme_lr_factors, dme_lr_destroy, dme_expm, dme_apply, dme_apply_async, dme_sync, dme_plan_kernels_per_step, dme_step, dme_step_async, dme_solve, dme_plan_bytes, dme_plan_destroy, dme_gain,
+    dme_plan, dme_plan_mass, dme_lr_plan, dme_lr_plan_csr, dme_lr_solve, dme_lr_factors, dme_lr_destroy, dme_expm, dme_apply, dme_apply_async, dme_sync, dme_plan_kernels_per_step, dme_step, dme_step_async, dme_solve, dme_plan_bytes, dme_plan_split_choice, dme_plan_destroy, dme_gain,
     dme_server_create, dme_submit, dme_poll, dme_submit_gain, dme_poll_gain, dme_server_stats, dme_server_destroy,
     dme_last_error,
-    dme_gemm_split, dme_gemm_split_noalloc, dme_dense_solve, dme_wait_selftest,
+    dme_gemm_split, dme_gemm_split_acc, dme_gemm_split_noalloc, dme_dense_solve, dme_wait_selftest,
 )
 
 EQ_IDS = {"dle": DME_DLE, "dre": DME_DRE, "gdle": DME_GDLE, "gdre": DME_GDRE}
@@ -27,7 +27,8 @@ class Plan:
     Q = C^T C (``q_is_factor``) or ``Q=...`` for a dense Q."""
 
     def __init__(self, A, C=None, h=1e-3, flows=("F12",), comp="strang", B=None, R=None, S=None,
-                 Q=None, prec="fp64", t4_rule=DME_T4_AUTO, slices=0, stream=None, M=None, fsal=False, extrap=0):
+                 Q=None, prec="fp64", t4_rule=DME_T4_AUTO, pairs=0, stream=None, M=None, fsal=False, extrap=0,
+                 horizon=0, tol=0.0):
         n = int(A.shape[0])
         m = 0 if B is None else int(B.shape[1])
         eq = ("g" if S is not None else "") + ("dre" if B is not None else "dle")
@@ -35,8 +36,8 @@ class Plan:
             raise ValueError("give C (Q = C^T C) or Q")
         self.n, self.m = n, m
         self.desc = make_desc(n, m=m, p=0 if C is None else int(C.shape[0]), eq=EQ_IDS[eq], comp=comp,
-                              flows=flows, prec=prec, h=h, q_is_factor=Q is None, t4_rule=t4_rule, slices=slices,
-                              fsal=fsal, extrap=extrap)
+                              flows=flows, prec=prec, h=h, q_is_factor=Q is None, t4_rule=t4_rule, pairs=pairs,
+                              fsal=fsal, extrap=extrap, horizon=horizon, tol=tol)
         if M is None:
             self.handle = dme_plan(self.desc, A, C if Q is None else Q, B, R, S, stream)
         else:
@@ -75,6 +76,11 @@ class Plan:
 
     def gain(self, P, K_out):
         dme_gain(self.handle, P, K_out)
+
+    @property
+    def split_choice(self):
+        """(slice products per output, estimate that chose them)."""
+        return dme_plan_split_choice(self.handle)
 
     @property
     def nbytes(self):

@@ -46,8 +46,8 @@ class DmeError(RuntimeError):
 class dme_plan_desc(C.Structure):
     _fields_ = [("n", C.c_int), ("m", C.c_int), ("p", C.c_int), ("eq", C.c_int), ("comp", C.c_int),
                 ("nflows", C.c_int), ("flows", C.c_int * 4), ("prec", C.c_int), ("h", C.c_double),
-                ("q_is_factor", C.c_int), ("t4_rule", C.c_int), ("slices", C.c_int), ("fsal", C.c_int),
-                ("extrap", C.c_int)]
+                ("q_is_factor", C.c_int), ("t4_rule", C.c_int), ("pairs", C.c_int), ("fsal", C.c_int),
+                ("extrap", C.c_int), ("horizon", C.c_int), ("tol", C.c_double)]
 
 
 class dme_lr_opts(C.Structure):
@@ -82,6 +82,8 @@ _SIGS = {
     "dme_step_async": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "dme_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_void_p]),
     "dme_plan_bytes": (C.c_size_t, [C.c_void_p]),
+    "dme_plan_split_choice": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "dme_gemm_split_acc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dme_gain": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dme_plan_destroy": (C.c_int, [C.c_void_p]),
     "dme_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]),
@@ -155,7 +157,8 @@ def _ptr(x, keep: list):
 
 
 def make_desc(n, *, m=0, p=0, eq=DME_DLE, comp="strang", flows=("F12",), prec="fp64", h=1e-3,
-              q_is_factor=False, t4_rule=DME_T4_AUTO, slices=0, fsal=False, extrap=0) -> dme_plan_desc:
+              q_is_factor=False, t4_rule=DME_T4_AUTO, pairs=0, fsal=False, extrap=0, horizon=0,
+              tol=0.0) -> dme_plan_desc:
     d = dme_plan_desc()
     d.n, d.m, d.p, d.eq = n, m, p, eq
     d.comp = COMP_IDS[comp] if isinstance(comp, str) else comp
@@ -167,9 +170,11 @@ def make_desc(n, *, m=0, p=0, eq=DME_DLE, comp="strang", flows=("F12",), prec="f
     d.h = float(h)
     d.q_is_factor = int(bool(q_is_factor))
     d.t4_rule = t4_rule
-    d.slices = slices
+    d.pairs = int(pairs)
     d.fsal = int(bool(fsal))
     d.extrap = int(extrap)
+    d.horizon = int(horizon)
+    d.tol = float(tol)
     return d
 
 
@@ -311,6 +316,14 @@ def dme_gain(plan: int, P, K_out):
     _check(lib().dme_gain(plan, _out_ptr(P), _out_ptr(K_out)), "dme_gain")
 
 
+def dme_plan_split_choice(plan: int):
+    """(slice products per output, the estimate that chose them) of a plan."""
+    pairs = C.c_int(0)
+    est = C.c_double(0.0)
+    _check(lib().dme_plan_split_choice(plan, C.byref(pairs), C.byref(est)), "dme_plan_split_choice")
+    return pairs.value, est.value
+
+
 def dme_plan_bytes(plan: int) -> int:
     return int(lib().dme_plan_bytes(plan))
 
@@ -400,6 +413,15 @@ def dme_gemm_split(A, B, C_out, stream=None):
     M, N, K = _gemm_operands("dme_gemm_split", A, B, C_out)
     st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     _check(lib().dme_gemm_split(M, N, K, A.data_ptr(), B.data_ptr(), C_out.data_ptr(), st), "dme_gemm_split")
+
+
+def dme_gemm_split_acc(A, B, C_out, stream=None):
+    """C_out = A @ B.T in the accurate split mode (7-bit digits, 6 slices per
+    operand, exact K chunks of 512 combined in fp64; device tensors)."""
+    M, N, K = _gemm_operands("dme_gemm_split_acc", A, B, C_out)
+    st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib().dme_gemm_split_acc(M, N, K, A.data_ptr(), B.data_ptr(), C_out.data_ptr(), st),
+           "dme_gemm_split_acc")
 
 
 def dme_dense_solve(M, B_inout, stream=None):

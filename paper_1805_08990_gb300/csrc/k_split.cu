@@ -1,31 +1,29 @@
-// Split-precision congruence G P G^T on tcgen05 tensor cores.
+// Split-precision products A B^T on tcgen05 tensor cores.
 //
 // Error-free slicing (after Ozaki, Ogita, Oishi & Rump, "Error-free
 // transformations of matrix multiplication by using fast routines of matrix
 // multiplication", Numer. Algorithms 59, 2012): each row r of an operand is
-// scaled by sigma_r = 2^E_r > max |x_r.| and cut into bf16 slices
-//     x / sigma = d0 2^-6 + d1 2^-13 + d2 2^-20 + d3 2^-27 + d4 2^-34 + res,
-// with integers |d_t| <= 64.  The fixed operand (G = E^T or S, the A side)
-// keeps five slices (|res| <= 2^-35): its slicing error is the same at every
-// step and would otherwise add up coherently over the horizon.  The per-step
-// operand (P or U, the B side) keeps four (|res| <= 2^-28); its errors are
-// fresh each step and averaged by the congruence.
-// A slice product d_s d_t 2^-(12+7(s+t)) is exact in bf16 x bf16, and a level
-// l = s + t sums K <= 4096 such products: at most 2^24 units of
-// 2^-(12+7l), so the fp32 tensor-core accumulation of level 0 is exact
-// whatever its rounding mode, and the other levels round far below the
-// slice residuals.  The 14 pairs with s + t <= 4 are accumulated in four TMEM
-// accumulators (levels 0, 1, 2 and 3+4); the epilogue adds them as a
-// two-float (hi = level 0, exact; lo = levels 1-4) and scales by
-// sigma_A,i sigma_B,j.
+// scaled by sigma_r = 2^E_r > max |x_r.|, rounded to a fixed-point integer V,
+// and V is cut into signed digits that are exact bf16 values:
+//     x / sigma = d0 2^-6 + d1 w1 + d2 w2 + ...,  |d0| <= 64,
+// with trailing digits of 9 bits (|d| <= 256, w_t = 2^(-6-9t), the per-step
+// scheme) or 7 bits (|d| <= 64, w_t = 2^(-6-7t), the accurate scheme).
+// A slice product d_s d_t w_s w_t is exact in bf16 x bf16; the products of
+// level l = s + t share a TMEM accumulator (levels 0, 1, 2 and >= 3).  Level 0
+// sums K <= 4096 products of at most 2^12 units, so its fp32 sum is exact in
+// any order; the other levels round far below the slice residuals.  The
+// epilogue combines the levels as a two-float (hi = level 0, lo = the rest)
+// and scales by sigma_A,i sigma_B,j.
 //
-// Kernel shape: one CTA per 128 x 128 output tile, 10 warps:
-//   warp 0  TMA producer (one thread): 3-stage ring, each stage holds the 5
-//           slices of a 128 x 32 A tile and the 4 slices of a 128 x 32 B tile
-//           (72 KB, 64-byte swizzled rows),
-//   warp 1  TMEM allocator + MMA issuer (one thread): 28 tcgen05.mma per stage,
-//   warps 2-9 epilogue: tcgen05.ld of the 4 accumulators (512 TMEM columns),
-//           two warps per TMEM lane quadrant, each on half of the tile's columns.
+// Kernel shape: persistent, one CTA per SM, 10 warps, 128 x 128 output tiles:
+//   warp 0  TMA producer (one thread): a ring of STAGES stages, each holding
+//           the SA slices of a 128 x 32 A tile and the SB slices of a 128 x 32
+//           B tile (64-byte swizzled rows, one TMA load per slice plane),
+//   warp 1  TMEM allocator + MMA issuer (one thread): 2 x pairs tcgen05.mma
+//           per stage into the four accumulators (512 TMEM columns),
+//   warps 2-9 epilogue, two warps per TMEM lane quadrant, each on 64 columns:
+//           they copy the accumulators into registers and release TMEM at
+//           once, so the next tile's MMAs run while they scale and store.
 // Both operands are K-major (row-major with K contiguous):
 //   C[i][j] = sum_k A[i][k] B[j][k].
 #include "dme_internal.h"
@@ -35,6 +33,7 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -44,19 +43,41 @@ namespace dme {
 
 using namespace tc;
 
-constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 32, OZ_STAGES = 3;
+constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 32;
 constexpr int OZ_SLICE_BYTES = OZ_BM * OZ_BK * 2;                 // 8 KB per slice tile
-constexpr int OZ_A_BYTES = OZ_SLICES_A * OZ_SLICE_BYTES;         // 40 KB per stage
-constexpr int OZ_B_BYTES = OZ_SLICES_B * OZ_SLICE_BYTES;         // 32 KB per stage
-constexpr int OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;          // 72 KB
-constexpr int OZ_SMEM_BYTES = OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256;
-constexpr int OZ_MAX_LEVEL = 4;                                   // pairs with s + t <= 4
-constexpr int OZ_NACC = 4;                                        // accumulators: levels 0, 1, 2, 3+4
-constexpr uint64_t OZ_TIMEOUT_NS = 2000000000ull;             // 2 s per wait
+constexpr int OZ_NACC = 4;                                        // accumulators: levels 0, 1, 2, >= 3
+constexpr uint64_t OZ_TIMEOUT_NS = 2000000000ull;                 // 2 s per wait
 constexpr int OZ_EPI_WARPS = 8;                                  // two per TMEM lane quadrant
 constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;               // producer + MMA warps + epilogue
-constexpr int OZ_EPI_COLS = OZ_BN / (OZ_EPI_WARPS / 4);          // columns per epilogue warp
+constexpr int OZ_EPI_COLS = OZ_BN / (OZ_EPI_WARPS / 4);          // columns per epilogue warp (64)
 constexpr uint32_t OZ_IDESC = idesc_bf16_f32(OZ_BM, OZ_BN);
+
+template <int SA_, int SB_, int L_, int STAGES_, bool ACC_>
+struct OzCfg {
+    static constexpr int SA = SA_, SB = SB_, L = L_, STAGES = STAGES_;
+    static constexpr bool ACC = ACC_;                                // accurate mode (exact chunks)
+    static constexpr int A_BYTES = SA * OZ_SLICE_BYTES;
+    static constexpr int STAGE_BYTES = (SA + SB) * OZ_SLICE_BYTES;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+};
+using CfgP10 = OzCfg<4, 4, 3, 3, false>;
+using CfgP13 = OzCfg<4, 4, 4, 3, false>;
+using CfgP14 = OzCfg<5, 4, 4, 3, false>;
+using CfgA21 = OzCfg<6, 6, 5, 2, true>;
+static_assert(CfgP14::SMEM <= 232448 && CfgA21::SMEM <= 232448, "shared memory per CTA");
+
+int oz_cfg_pairs(int cfg) {
+    switch (cfg) {
+        case OZ_P10: return 10;
+        case OZ_P13: return 13;
+        case OZ_P14: return 14;
+        case OZ_A21: return 21;
+    }
+    return 0;
+}
+int oz_cfg_slices_a(int cfg) { return cfg == OZ_P14 ? 5 : (cfg == OZ_A21 ? 6 : 4); }
+int oz_cfg_slices_b(int cfg) { return cfg == OZ_A21 ? 6 : 4; }
+int oz_cfg_scheme(int cfg) { return cfg == OZ_A21 ? OZ_DIG7 : OZ_DIG9; }
 
 // ============================================================== slicing
 __device__ __forceinline__ long long round_shift(unsigned long long mag, int shift) {
@@ -65,48 +86,58 @@ __device__ __forceinline__ long long round_shift(unsigned long long mag, int shi
     return (long long)((mag + (1ull << (shift - 1))) >> shift);
 }
 
-// round(x * 2^(41 - E)) for a double x (|x| < 2^E, so |result| <= 2^41)
-__device__ __forceinline__ long long fixed41_d(double x, int E) {
+// round(x 2^(B - E)) for a double x with |x| < 2^E (so |result| <= 2^B)
+__device__ __forceinline__ long long fixed_d(double x, int E, int B) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int ex = (int)((b >> 52) & 0x7FF);
     if (ex == 0 || ex == 0x7FF) return 0;
     const unsigned long long M = (b & ((1ull << 52) - 1)) | (1ull << 52);
-    const long long v = round_shift(M, 1075 + E - 41 - ex);
+    const long long v = round_shift(M, 1075 - B + E - ex);
     return (b >> 63) ? -v : v;
 }
 
-// round(f * 2^(41 - E)) for a float f
-__device__ __forceinline__ long long fixed41_f(float f, int E) {
+// round(f 2^(B - E)) for a float f
+__device__ __forceinline__ long long fixed_f(float f, int E, int B) {
     const unsigned int b = __float_as_uint(f);
     const int ef = (int)((b >> 23) & 0xFF);
     if (ef == 0 || ef == 0xFF) return 0;
     const unsigned long long M = (b & 0x7FFFFFu) | 0x800000u;
-    const long long v = round_shift(M, 109 + E - ef);
+    const long long v = round_shift(M, 150 - B + E - ef);
     return (b >> 31) ? -v : v;
 }
 
-// The NS base-2^7 digits of V (|V| < 2^41) with round-to-nearest,
-// d_t = round(r_t / 2^(35-7t)), r_{t+1} = r_t - d_t 2^(35-7t), in 32-bit
-// arithmetic: V = h 2^21 + l with 0 <= l < 2^21; digits 0 and 1 come from h
-// alone (l < 2^21 cannot change those floors), digit 2 is h plus the rounding
-// carry of l, and digits 3 and 4 come from the remainder l - carry 2^21.
-template <int NS>
-__device__ __forceinline__ void digits7(long long V, int (&dg)[5]) {
-    int h = (int)(V >> 21);
-    const int l = (int)(V - ((long long)h << 21));
-    int d = (h + (1 << 13)) >> 14;
-    h -= d << 14;
-    dg[0] = d;
-    d = (h + (1 << 6)) >> 7;
-    h -= d << 7;
-    dg[1] = d;
-    const int c = l >= (1 << 20) ? 1 : 0;
-    dg[2] = h + c;
-    int r = l - (c << 21);
-    d = (r + (1 << 13)) >> 14;
-    r -= d << 14;
-    dg[3] = d;
-    dg[4] = (r + (1 << 6)) >> 7;
+// Fixed-point width B of a scheme: the leading digit has weight 2^-6, the last
+// representable one 2^-B (DIG9: 6 + 4 x 9 = 42 bits, DIG7: 6 + 5 x 7 = 41 bits).
+template <int SCHEME>
+struct Digits {
+    static constexpr int B = SCHEME == OZ_DIG9 ? 42 : 41;
+    static constexpr int TOP = B - 6;                    // shift of digit 0
+};
+
+// The NS leading digits of V (|V| < 2^B), each rounded to nearest:
+// d_t = round(r_t / 2^(TOP - b t)), r_{t+1} = r_t - d_t 2^(TOP - b t); the last
+// digit absorbs (rounds) whatever lies below it.
+template <int SCHEME, int NS>
+__device__ __forceinline__ void digits(long long V, int (&dg)[NS]) {
+    constexpr int b = SCHEME;
+    long long r = V;
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+        const int sh = Digits<SCHEME>::TOP - b * t;
+        if (sh <= 0) {
+            dg[t] = (int)r;
+            r = 0;
+        } else {
+            const long long d = (r + (1ll << (sh - 1))) >> sh;
+            dg[t] = (int)d;
+            r -= d << sh;
+        }
+    }
+}
+
+template <int SCHEME>
+__device__ __forceinline__ float digit_unit(int t) {
+    return __int_as_float((127 - 6 - SCHEME * t) << 23);      // 2^(-6 - b t), exact
 }
 
 // Load entries k .. k+3 of a row (zeros past `cols`); vector loads when the
@@ -139,13 +170,50 @@ __device__ __forceinline__ void load4(const double* X, const float2* Xp, size_t 
     }
 }
 
+template <bool PAIR>
+__device__ __forceinline__ int entry_exp(const double& d, const float2& f) {
+    if (PAIR) {
+        const unsigned int b = __float_as_uint(f.x) & 0x7FFFFFFFu;
+        const int ef = (int)(b >> 23);
+        return (b == 0 || ef == 0) ? -100000 : ef - 127;
+    }
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const int ed = (int)((b >> 52) & 0x7FF);
+    return (ed == 0) ? -100000 : ed - 1023;
+}
+
+// Write the NS slices of four consecutive entries (fixed-point values V) at
+// plane offset o: one 8-byte store of four bf16 per plane.
+template <int SCHEME, int NS>
+__device__ __forceinline__ void store_slices4(const long long (&V)[4], __nv_bfloat16* __restrict__ out, size_t o,
+                                              size_t plane) {
+    int dg[4][NS];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) digits<SCHEME, NS>(V[u], dg[u]);
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+        const float unit = digit_unit<SCHEME>(t);
+        float q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) q[u] = (float)dg[u][t] * unit;      // |d| <= 256: exact in bf16
+        const __nv_bfloat162 p01 = __floats2bfloat162_rn(q[0], q[1]);
+        const __nv_bfloat162 p23 = __floats2bfloat162_rn(q[2], q[3]);
+        uint2 w;
+        w.x = *reinterpret_cast<const unsigned int*>(&p01);
+        w.y = *reinterpret_cast<const unsigned int*>(&p23);
+        *reinterpret_cast<uint2*>(out + t * plane + o) = w;
+    }
+}
+
+template <bool PAIR, int SCHEME>
+__device__ __forceinline__ long long to_fixed(const double& d, const float2& f, int E) {
+    constexpr int B = Digits<SCHEME>::B;
+    return PAIR ? fixed_f(f.x, E, B) + fixed_f(f.y, E, B) : fixed_d(d, E, B);
+}
+
 // One warp per row: pass 1 finds the row's max exponent, pass 2 writes the
-// NS slices (zero beyond `cols`, up to Kp) and the row scale 2^E.  The value
-// is first rounded to a 41-bit fixed-point integer V = round(x 2^(41-E)); the
-// slices are the base-2^7 digits of V with round-to-nearest:
-// d_t = round(r_t / 2^(35-7t)), r_{t+1} = r_t - d_t 2^(35-7t).
-// Each lane handles 4 consecutive entries (32-byte loads, 8-byte stores per plane).
-template <bool PAIR, int NS>
+// NS slices (zero beyond `cols`, up to Kp) and the row scale 2^E.
+template <bool PAIR, int SCHEME, int NS>
 __device__ __forceinline__ void slice_row_warp(const double* __restrict__ X, const float2* __restrict__ Xp, int row,
                                                int cols, int ldx, __nv_bfloat16* __restrict__ out, int Kp,
                                                float* __restrict__ scale, int prow) {
@@ -154,24 +222,11 @@ __device__ __forceinline__ void slice_row_warp(const double* __restrict__ X, con
     const bool vec = (ldx % 2) == 0;
     double d[4];
     float2 f[4];
-    // pass 1: largest magnitude (as exponent)
     int emax = -100000;
     for (int k = 4 * lane; k < cols; k += 128) {
         load4<PAIR>(X, Xp, base, k, cols, vec, d, f);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            int e;
-            if (PAIR) {
-                const unsigned int b = __float_as_uint(f[u].x) & 0x7FFFFFFFu;
-                const int ef = (int)(b >> 23);
-                e = (b == 0 || ef == 0) ? -100000 : ef - 127;
-            } else {
-                const unsigned long long b = (unsigned long long)__double_as_longlong(d[u]);
-                const int ed = (int)((b >> 52) & 0x7FF);
-                e = (ed == 0) ? -100000 : ed - 1023;
-            }
-            emax = max(emax, e);
-        }
+        for (int u = 0; u < 4; ++u) emax = max(emax, entry_exp<PAIR>(d[u], f[u]));
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
@@ -186,41 +241,24 @@ __device__ __forceinline__ void slice_row_warp(const double* __restrict__ X, con
         if (!zero_row && k < cols) {
             load4<PAIR>(X, Xp, base, k, cols, vec, d, f);
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                V[u] = PAIR ? fixed41_f(f[u].x, E) + fixed41_f(f[u].y, E) : fixed41_d(d[u], E);
+            for (int u = 0; u < 4; ++u) V[u] = to_fixed<PAIR, SCHEME>(d[u], f[u], E);
         }
-        const size_t o = (size_t)row * Kp + k;
-        int dg[4][5];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) digits7<NS>(V[u], dg[u]);
-#pragma unroll
-        for (int t = 0; t < NS; ++t) {
-            const float unit = __int_as_float((127 - 6 - 7 * t) << 23);     // 2^(-6-7t), exact
-            float q[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) q[u] = (float)dg[u][t] * unit;      // |d| <= 64: exact in float
-            const __nv_bfloat162 p01 = __floats2bfloat162_rn(q[0], q[1]);
-            const __nv_bfloat162 p23 = __floats2bfloat162_rn(q[2], q[3]);
-            uint2 w;
-            w.x = *reinterpret_cast<const unsigned int*>(&p01);
-            w.y = *reinterpret_cast<const unsigned int*>(&p23);
-            *reinterpret_cast<uint2*>(out + t * plane + o) = w;
-        }
+        store_slices4<SCHEME, NS>(V, out, (size_t)row * Kp + k, plane);
     }
 }
 
-template <bool PAIR, int NS>
+template <bool PAIR, int SCHEME, int NS>
 __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restrict__ X, const float2* __restrict__ Xp,
                                                          int rows, int cols, int ldx, __nv_bfloat16* __restrict__ out,
                                                          int Kp, float* __restrict__ scale, int prow) {
     const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (row >= rows) return;
-    slice_row_warp<PAIR, NS>(X, Xp, row, cols, ldx, out, Kp, scale, prow);
+    slice_row_warp<PAIR, SCHEME, NS>(X, Xp, row, cols, ldx, out, Kp, scale, prow);
 }
 
 // Grouped slicing (serving): the rows of several problems laid end to end,
 // a warp per row; warp w finds its problem by a binary search over row0.
-template <bool PAIR, int NS>
+template <bool PAIR>
 __global__ void __launch_bounds__(256) slice_rows_grouped_kernel(const SliceDesc* __restrict__ d, int nd,
                                                                  int total_rows) {
     const int g = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -232,14 +270,14 @@ __global__ void __launch_bounds__(256) slice_rows_grouped_kernel(const SliceDesc
         else hi = mid - 1;
     }
     const SliceDesc& q = d[lo];
-    slice_row_warp<PAIR, NS>(q.X, q.Xp, g - q.row0, q.cols, q.ldx, q.out, q.Kp, q.scale, q.prow);
+    slice_row_warp<PAIR, OZ_DIG9, 4>(q.X, q.Xp, g - q.row0, q.cols, q.ldx, q.out, q.Kp, q.scale, q.prow);
 }
 
 // Long rows (Kp > 1024): one CTA of 256 threads per row; each thread keeps G
 // groups of 4 consecutive entries (k = 4 tid + 1024 g) in registers, so the
 // row is read from memory once; the row maximum is a block reduction.  Same
 // digits as slice_rows_kernel.
-template <bool PAIR, int NS, int G>
+template <bool PAIR, int SCHEME, int NS, int G>
 __global__ void __launch_bounds__(256) slice_long_rows_kernel(const double* __restrict__ X,
                                                               const float2* __restrict__ Xp, int rows, int cols,
                                                               int ldx, __nv_bfloat16* __restrict__ out, int Kp,
@@ -264,19 +302,7 @@ __global__ void __launch_bounds__(256) slice_long_rows_kernel(const double* __re
             }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            int e;
-            if (PAIR) {
-                const unsigned int b = __float_as_uint(f[g][u].x) & 0x7FFFFFFFu;
-                const int ef = (int)(b >> 23);
-                e = (b == 0 || ef == 0) ? -100000 : ef - 127;
-            } else {
-                const unsigned long long b = (unsigned long long)__double_as_longlong(d[g][u]);
-                const int ed = (int)((b >> 52) & 0x7FF);
-                e = (ed == 0) ? -100000 : ed - 1023;
-            }
-            emax = max(emax, e);
-        }
+        for (int u = 0; u < 4; ++u) emax = max(emax, entry_exp<PAIR>(d[g][u], f[g][u]));
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
@@ -296,41 +322,26 @@ __global__ void __launch_bounds__(256) slice_long_rows_kernel(const double* __re
         long long V[4] = {0, 0, 0, 0};
         if (!zero_row && k < cols) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                V[u] = PAIR ? fixed41_f(f[g][u].x, E) + fixed41_f(f[g][u].y, E) : fixed41_d(d[g][u], E);
+            for (int u = 0; u < 4; ++u) V[u] = to_fixed<PAIR, SCHEME>(d[g][u], f[g][u], E);
         }
-        const size_t o = (size_t)row * Kp + k;
-        int dg[4][5];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) digits7<NS>(V[u], dg[u]);
-#pragma unroll
-        for (int t = 0; t < NS; ++t) {
-            const float unit = __int_as_float((127 - 6 - 7 * t) << 23);
-            float q[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) q[u] = (float)dg[u][t] * unit;
-            const __nv_bfloat162 p01 = __floats2bfloat162_rn(q[0], q[1]);
-            const __nv_bfloat162 p23 = __floats2bfloat162_rn(q[2], q[3]);
-            uint2 w;
-            w.x = *reinterpret_cast<const unsigned int*>(&p01);
-            w.y = *reinterpret_cast<const unsigned int*>(&p23);
-            *reinterpret_cast<uint2*>(out + t * plane + o) = w;
-        }
+        store_slices4<SCHEME, NS>(V, out, (size_t)row * Kp + k, plane);
     }
 }
 
-template <bool PAIR, int NS>
+template <bool PAIR, int SCHEME, int NS>
 static void slice_launch(const double* X, const float2* Xp, int rows, int cols, int ldx, const SliceBuf& sb,
                          cudaStream_t st) {
     if (rows <= 0 || rows > sb.rows) return;
     const int pr = sb.rows;
     if (sb.Kp > 2048)
-        slice_long_rows_kernel<PAIR, NS, 4><<<rows, 256, 0, st>>>(X, Xp, rows, cols, ldx, sb.data, sb.Kp, sb.scale, pr);
+        slice_long_rows_kernel<PAIR, SCHEME, NS, 4>
+            <<<rows, 256, 0, st>>>(X, Xp, rows, cols, ldx, sb.data, sb.Kp, sb.scale, pr);
     else if (sb.Kp > 1024)
-        slice_long_rows_kernel<PAIR, NS, 2><<<rows, 256, 0, st>>>(X, Xp, rows, cols, ldx, sb.data, sb.Kp, sb.scale, pr);
+        slice_long_rows_kernel<PAIR, SCHEME, NS, 2>
+            <<<rows, 256, 0, st>>>(X, Xp, rows, cols, ldx, sb.data, sb.Kp, sb.scale, pr);
     else
-        slice_rows_kernel<PAIR, NS><<<(rows + 7) / 8, 256, 0, st>>>(X, Xp, rows, cols, ldx, sb.data, sb.Kp, sb.scale,
-                                                                     pr);
+        slice_rows_kernel<PAIR, SCHEME, NS>
+            <<<(rows + 7) / 8, 256, 0, st>>>(X, Xp, rows, cols, ldx, sb.data, sb.Kp, sb.scale, pr);
 }
 
 dme_status launch_slice_grouped(std::vector<SliceDesc>& items, bool pair, cudaStream_t st, DescArena* arena) {
@@ -344,25 +355,26 @@ dme_status launch_slice_grouped(std::vector<SliceDesc>& items, bool pair, cudaSt
     const SliceDesc* dd = static_cast<const SliceDesc*>(arena->put(items.data(), items.size() * sizeof(SliceDesc)));
     if (!dd) return set_error("grouped slicing: descriptor arena full"), DME_ENOMEM;
     const int grid = (total + 7) / 8;
-    if (pair) slice_rows_grouped_kernel<true, 4><<<grid, 256, 0, st>>>(dd, (int)items.size(), total);
-    else slice_rows_grouped_kernel<false, 4><<<grid, 256, 0, st>>>(dd, (int)items.size(), total);
+    if (pair) slice_rows_grouped_kernel<true><<<grid, 256, 0, st>>>(dd, (int)items.size(), total);
+    else slice_rows_grouped_kernel<false><<<grid, 256, 0, st>>>(dd, (int)items.size(), total);
     DME_CUDA_TRY(cudaGetLastError());
     return DME_OK;
 }
 
 void launch_slice_rows_f64(const double* X, int rows, int cols, int ldx, const SliceBuf& sb, cudaStream_t st) {
-    if (sb.ns == 5) slice_launch<false, 5>(X, nullptr, rows, cols, ldx, sb, st);
-    else slice_launch<false, 4>(X, nullptr, rows, cols, ldx, sb, st);
+    if (sb.scheme == OZ_DIG7) slice_launch<false, OZ_DIG7, 6>(X, nullptr, rows, cols, ldx, sb, st);
+    else if (sb.ns == 5) slice_launch<false, OZ_DIG9, 5>(X, nullptr, rows, cols, ldx, sb, st);
+    else slice_launch<false, OZ_DIG9, 4>(X, nullptr, rows, cols, ldx, sb, st);
 }
 
 void launch_slice_rows_pair(const float2* Xp, int rows, int cols, int ldx, const SliceBuf& sb, cudaStream_t st) {
-    if (sb.ns == 5) slice_launch<true, 5>(nullptr, Xp, rows, cols, ldx, sb, st);
-    else slice_launch<true, 4>(nullptr, Xp, rows, cols, ldx, sb, st);
+    if (sb.ns == 5) slice_launch<true, OZ_DIG9, 5>(nullptr, Xp, rows, cols, ldx, sb, st);
+    else slice_launch<true, OZ_DIG9, 4>(nullptr, Xp, rows, cols, ldx, sb, st);
 }
 
 // ============================================================== tcgen05 GEMM
 // Tile order.  Rectangular grids run in groups of OZ_GROUP tile rows, column
-// by column inside a group, so the CTAs resident at one time touch about
+// by column inside a group, so the CTAs working at one time touch about
 // OZ_GROUP row tiles of A and 152/OZ_GROUP column tiles of B, which stay in L2.
 // Triangle grids enumerate (tm <= tn) row by row.
 constexpr int OZ_GROUP = 8;
@@ -401,35 +413,195 @@ __device__ __forceinline__ double f2d_bits(float f) {
     return __longlong_as_double((long long)(sign | ed | m));
 }
 
-// One 128 x 128 output tile (index t of problem p) by one CTA; tmA / tmB are
-// the addresses of the tensor maps (kernel parameters or global memory).
-__device__ __forceinline__ void oz_gemm_tile(const CUtensorMap* tmA, const CUtensorMap* tmB, const OzParams& p,
-                                             int t, int part, int nparts, int widx) {
+// What one work unit of a launch is: a 128 x 128 output tile of one problem
+// over the K blocks [kb0, kb0 + nk), as part `part` of `nparts` (split K of the
+// tail; widx = its workspace slot) or as accurate-mode chunk `chunk`.
+struct OzUnit {
+    const OzParams* p;
+    const CUtensorMap* tA;
+    const CUtensorMap* tB;
+    int tm, tn, kb0, nk, part, nparts, widx, chunk;
+};
+
+__device__ __forceinline__ void oz_single_unit(const OzParams* p, const CUtensorMap* tA, const CUtensorMap* tB,
+                                               bool acc, int u, OzUnit& o) {
+    o.p = p;
+    o.tA = tA;
+    o.tB = tB;
+    const int nk_all = p->Kp / OZ_BK;
+    int tile = u, part = 0, nparts = 1, widx = 0, chunk = 0;
+    if (acc) {
+        // chunk-major: the units working at one time share one K range
+        chunk = u / p->tiles;
+        tile = u - chunk * p->tiles;
+    } else if (p->split_parts > 1 && u >= p->split_first) {
+        const int j = u - p->split_first;
+        tile = p->split_first + j / p->split_parts;
+        part = j % p->split_parts;
+        nparts = p->split_parts;
+        widx = j / p->split_parts;
+    }
+    oz_tile_coords(*p, tile, o.tm, o.tn);
+    if (acc) {
+        o.kb0 = chunk * OZ_ACC_CHUNK_KB;
+        o.nk = min(OZ_ACC_CHUNK_KB, nk_all - o.kb0);
+    } else {
+        o.kb0 = part * nk_all / nparts;
+        o.nk = (part + 1) * nk_all / nparts - o.kb0;
+    }
+    o.part = part;
+    o.nparts = nparts;
+    o.widx = widx;
+    o.chunk = chunk;
+}
+
+__device__ __forceinline__ void oz_group_unit(const OzGroupDesc* __restrict__ d, int nd, int u, OzUnit& o) {
+    int lo = 0, hi = nd - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d[mid].start <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    o.p = &d[lo].p;
+    o.tA = &d[lo].tmA;
+    o.tB = &d[lo].tmB;
+    oz_tile_coords(d[lo].p, u - d[lo].start, o.tm, o.tn);
+    o.kb0 = 0;
+    o.nk = d[lo].p.Kp / OZ_BK;
+    o.part = 0;
+    o.nparts = 1;
+    o.widx = 0;
+    o.chunk = 0;
+}
+
+// Load 32 columns of the four accumulators of TMEM lane quadrant q at column c0
+// into h (level 0, raw fp32 bits) and l (levels 1 + 2 + 3.., as fp32 bits).
+// (The levels 2 and 3 come through a 16-column temporary: the epilogue warps
+// hold 128 values each and the kernel's register budget is 168.)
+__device__ __forceinline__ void oz_load_half(uint32_t tmem, int q, int c0, uint32_t (&h)[32], uint32_t (&l)[32]) {
+    const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0;
+    tmem_ld_32x32b_x32(ta, h);
+    tmem_ld_32x32b_x32(ta + OZ_BN, l);
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+        uint32_t t[16];
+        tmem_ld_32x32b_x16(ta + 2 * OZ_BN + 16 * g, t);
+        tmem_ld_wait();
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj)
+            l[16 * g + jj] = __float_as_uint(__uint_as_float(l[16 * g + jj]) + __uint_as_float(t[jj]));
+        tmem_ld_32x32b_x16(ta + 3 * OZ_BN + 16 * g, t);
+        tmem_ld_wait();
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj)
+            l[16 * g + jj] = __float_as_uint(__uint_as_float(l[16 * g + jj]) + __uint_as_float(t[jj]));
+    }
+}
+
+// Epilogue of 32 columns (tile columns c0 .. c0+31) of row i from registers.
+__device__ __forceinline__ void oz_store_half(const OzParams& p, int m0, int n0, int i, int c0, bool diag,
+                                              const uint32_t (&h)[32], const uint32_t (&l)[32]) {
+    if (i >= p.M) return;
+    const float sA = p.sa[i];
+    if (p.mode == OZ_OUT_PAIR) {
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+            const int j = n0 + c0 + jj;
+            if (j >= p.N) break;
+            const float s = sA * p.sb[j];
+            const float hv = __uint_as_float(h[jj]), lv = __uint_as_float(l[jj]);
+            // TwoSum: (sh, sl) = hi + lo exactly
+            const float sh = hv + lv;
+            const float bb = sh - hv;
+            const float sl = (hv - (sh - bb)) + (lv - bb);
+            p.Cp[(size_t)i * p.ldc + j] = make_float2(sh * s, sl * s);
+        }
+        return;
+    }
+    const double alpha = p.alpha;
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+        const int j = n0 + c0 + jj;
+        if (j >= p.N) break;
+        if (diag && i > j) continue;                   // lower half of a diagonal tile: its mirror owns it
+        const float s = sA * p.sb[j];
+        const float hv = __uint_as_float(h[jj]), lv = __uint_as_float(l[jj]);
+        const float sh = hv + lv;
+        const float bb = sh - hv;
+        const float sl = (hv - (sh - bb)) + (lv - bb);
+        double v = f2d_bits(sh * s) + f2d_bits(sl * s);
+        if (alpha != 1.0) v *= alpha;
+        if (p.tri) {
+            // symmetric output and addends: read the addends at (j, i) (coalesced over
+            // the warp's rows), write (j, i) and its mirror (i, j)
+            const size_t tof = (size_t)j * p.ldc + i;
+            if (p.D1) v += p.b1 * p.D1[tof];
+            if (p.D2) v += p.b2 * p.D2[tof];
+            if (p.D3) v += p.b3 * p.D3[tof];
+            p.Cd[tof] = v;
+            if (i != j) p.Cd[(size_t)i * p.ldc + j] = v;
+        } else {
+            const size_t off = (size_t)i * p.ldc + j;
+            if (p.D1) v += p.b1 * p.D1[off];
+            if (p.D2) v += p.b2 * p.D2[off];
+            if (p.D3) v += p.b3 * p.D3[off];
+            p.Cd[off] = v;
+        }
+    }
+}
+
+// Accurate-mode epilogue of 32 columns: the levels added in fp64 (levels 0-2
+// of a chunk are exact fp32 integers of their units, so the double sum is
+// exact but for the shared level-3 accumulator's own rounding), scaled, and
+// written to the chunk's slab of the workspace.
+__device__ __forceinline__ void oz_store_chunk_half(const OzParams& p, uint32_t tmem, int q, int c0, int m0, int n0,
+                                                    int i, int chunk) {
+    uint32_t a0[32], a1[32], a2[32], a3[32];
+    const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0;
+    tmem_ld_32x32b_x32(ta, a0);
+    tmem_ld_32x32b_x32(ta + OZ_BN, a1);
+    tmem_ld_32x32b_x32(ta + 2 * OZ_BN, a2);
+    tmem_ld_32x32b_x32(ta + 3 * OZ_BN, a3);
+    tmem_ld_wait();
+    if (i >= p.M) return;
+    const double sA = (double)p.sa[i];
+    double* out = p.wsd + ((size_t)chunk * p.M + i) * p.N;
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+        const int j = n0 + c0 + jj;
+        if (j >= p.N) break;
+        double v = f2d_bits(__uint_as_float(a0[jj])) + f2d_bits(__uint_as_float(a1[jj]));
+        v += f2d_bits(__uint_as_float(a2[jj]));
+        v += f2d_bits(__uint_as_float(a3[jj]));
+        out[j] = v * (sA * (double)p.sb[j]);
+    }
+}
+
+// The persistent loop.  Every role walks the same unit sequence
+// u = blockIdx.x, blockIdx.x + gridDim.x, ...; `resolve(u, unit)` maps a unit
+// index to its problem, tile and K range.
+template <class Cfg, class Resolve>
+__device__ __forceinline__ void oz_persistent(int units, Resolve resolve) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OZ_STAGES * OZ_STAGE_BYTES);
-    // bars[0..S): full, bars[S..2S): empty, bars[2S]: accumulators ready
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * OZ_STAGES + 1);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::STAGES * Cfg::STAGE_BYTES);
+    // bars[0..S): full, [S..2S): empty, [2S]: accumulators full, [2S+1]: accumulators
+    // empty, [2S+2]: drain (every MMA done before TMEM is freed)
+    constexpr int S = Cfg::STAGES;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 3);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int tm, tn;
-    oz_tile_coords(p, t, tm, tn);
-    const int m0 = tm * OZ_BM, n0 = tn * OZ_BN;
-    const int nk_all = p.Kp / OZ_BK;
-    const int kb0 = part * nk_all / nparts;                 // this CTA's K blocks [kb0, kb0 + nk)
-    const int nk = (part + 1) * nk_all / nparts - kb0;
-
     if (threadIdx.x == 0) {
-        for (int s = 0; s < OZ_STAGES; ++s) {
+        for (int s = 0; s < S; ++s) {
             mbar_init(smem_u32(&bars[s]), 1);
-            mbar_init(smem_u32(&bars[OZ_STAGES + s]), 1);
+            mbar_init(smem_u32(&bars[S + s]), 1);
         }
-        mbar_init(smem_u32(&bars[2 * OZ_STAGES]), 1);
+        mbar_init(smem_u32(&bars[2 * S]), 1);
+        mbar_init(smem_u32(&bars[2 * S + 1]), OZ_EPI_WARPS);
+        mbar_init(smem_u32(&bars[2 * S + 2]), 1);
+        *abort_flag = 0;
         fence_mbar_init();
-    }
-    if (warp == 0 && lane == 0) {
-        tma_prefetch_desc(tmA);
-        tma_prefetch_desc(tmB);
     }
     if (warp == 1) {
         tmem_alloc(smem_u32(tmem_slot), 512);
@@ -439,260 +611,185 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap* tmA, const CUten
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = *tmem_slot;
+    const uint32_t acc_full = smem_u32(&bars[2 * S]), acc_empty = smem_u32(&bars[2 * S + 1]);
 
     if (warp == 0) {
         if (lane == 0) {
-            int issued[OZ_STAGES] = {0, 0, 0};
+            uint32_t issued = 0, last_ph = 0;               // per stage: a load issued, its phase parity
+            int kit = 0;                                    // k blocks issued over all units
             bool ok = true;
-            for (int it = 0; it < nk && ok; ++it) {
-                const int kb = kb0 + it;
-                const int s = it % OZ_STAGES;
-                const uint32_t ph = (it / OZ_STAGES) & 1;
-                if (it >= OZ_STAGES && !mbar_wait(smem_u32(&bars[OZ_STAGES + s]), ph ^ 1, OZ_TIMEOUT_NS)) {
-                    ok = false;
-                    break;
-                }
-                const uint32_t full = smem_u32(&bars[s]);
-                uint8_t* st = smem + s * OZ_STAGE_BYTES;
-                mbar_arrive_expect_tx(full, OZ_STAGE_BYTES);
-                tma_load_3d(smem_u32(st), tmA, full, kb * OZ_BK, m0, 0);
-                tma_load_3d(smem_u32(st + OZ_A_BYTES), tmB, full, kb * OZ_BK, n0, 0);
-                issued[s]++;
-                // spread over the K loop: pull the epilogue's addend rows (full 128-column
-                // segments only, all in bounds) into L2, one row per k block
-                const int pr = it * nparts + part;
-                if (p.mode == OZ_OUT_F64 && pr < OZ_BM && m0 + pr < p.M && n0 + OZ_BN <= p.N &&
-                    (p.ldc % 2) == 0) {
-                    const size_t off = (size_t)(m0 + pr) * p.ldc + n0;
-                    // the bulk prefetch needs a 16-byte aligned start (addends may be caller memory)
-                    if (p.D1 && ((reinterpret_cast<uintptr_t>(p.D1 + off) & 15) == 0))
-                        prefetch_l2_bulk(p.D1 + off, OZ_BN * sizeof(double));
-                    if (p.D2 && ((reinterpret_cast<uintptr_t>(p.D2 + off) & 15) == 0))
-                        prefetch_l2_bulk(p.D2 + off, OZ_BN * sizeof(double));
+            for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+                OzUnit w;
+                resolve(u, w);
+                const OzParams& p = *w.p;
+                tma_prefetch_desc(w.tA);
+                tma_prefetch_desc(w.tB);
+                const int m0 = w.tm * OZ_BM, n0 = w.tn * OZ_BN;
+                for (int it = 0; it < w.nk; ++it, ++kit) {
+                    if (*abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    const int s = kit % S;
+                    const uint32_t ph = (kit / S) & 1;
+                    if (kit >= S && !mbar_wait(smem_u32(&bars[S + s]), ph ^ 1, OZ_TIMEOUT_NS)) {
+                        atomicOr(p.status, DEV_TIMEOUT);
+                        *abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t full = smem_u32(&bars[s]);
+                    uint8_t* st = smem + s * Cfg::STAGE_BYTES;
+                    const int kc = (w.kb0 + it) * OZ_BK;
+                    mbar_arrive_expect_tx(full, Cfg::STAGE_BYTES);
+#pragma unroll
+                    for (int sa = 0; sa < Cfg::SA; ++sa)
+                        tma_load_3d(smem_u32(st + sa * OZ_SLICE_BYTES), w.tA, full, kc, m0, sa);
+#pragma unroll
+                    for (int sb = 0; sb < Cfg::SB; ++sb)
+                        tma_load_3d(smem_u32(st + Cfg::A_BYTES + sb * OZ_SLICE_BYTES), w.tB, full, kc, n0, sb);
+                    issued |= 1u << s;
+                    last_ph = (last_ph & ~(1u << s)) | (ph << s);
+                    // spread over the K loop: pull the epilogue's addend rows into L2 (full
+                    // 128-column segments only, 16-byte aligned; transposed for tri outputs)
+                    if (!Cfg::ACC && p.mode == OZ_OUT_F64 && it < OZ_BM && (p.ldc % 2) == 0) {
+                        const int ra = (p.tri ? n0 : m0) + it, ca = p.tri ? m0 : n0;
+                        const int rmax = p.tri ? p.N : p.M, cmax = p.tri ? p.M : p.N;
+                        if (ra < rmax && ca + OZ_BN <= cmax) {
+                            const size_t off = (size_t)ra * p.ldc + ca;
+                            if (p.D1 && ((reinterpret_cast<uintptr_t>(p.D1 + off) & 15) == 0))
+                                prefetch_l2_bulk(p.D1 + off, OZ_BN * sizeof(double));
+                            if (p.D2 && ((reinterpret_cast<uintptr_t>(p.D2 + off) & 15) == 0))
+                                prefetch_l2_bulk(p.D2 + off, OZ_BN * sizeof(double));
+                        }
+                    }
                 }
             }
-            if (!ok) atomicOr(p.status, DEV_TIMEOUT);
             // every load this thread issued has landed before the CTA may exit
-            for (int s = 0; s < OZ_STAGES; ++s)
-                if (issued[s] > 0 && !mbar_wait(smem_u32(&bars[s]), (issued[s] - 1) & 1, OZ_TIMEOUT_NS))
-                    atomicOr(p.status, DEV_TIMEOUT);
+            for (int s = 0; s < S; ++s)
+                if (((issued >> s) & 1u) && !mbar_wait(smem_u32(&bars[s]), (last_ph >> s) & 1u, OZ_TIMEOUT_NS))
+                    *abort_flag = 1;
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            bool ok = true;
-            for (int it = 0; it < nk; ++it) {
-                const int s = it % OZ_STAGES;
-                const uint32_t ph = (it / OZ_STAGES) & 1;
-                if (!mbar_wait(smem_u32(&bars[s]), ph, OZ_TIMEOUT_NS)) {
-                    ok = false;
+            int kit = 0, li = 0;
+            int* status = nullptr;
+            for (int u = blockIdx.x; u < units; u += gridDim.x, ++li) {
+                if (*abort_flag) break;
+                OzUnit w;
+                resolve(u, w);
+                status = w.p->status;
+                // the epilogue has copied the previous unit's accumulators out of TMEM
+                if (li > 0 && !mbar_wait(acc_empty, (li - 1) & 1, OZ_TIMEOUT_NS)) {
+                    atomicOr(status, DEV_TIMEOUT);
+                    *abort_flag = 1;
                     break;
                 }
                 fence_after_sync();
-                const uint32_t a0 = smem_u32(smem + s * OZ_STAGE_BYTES);
-                const uint32_t b0 = a0 + OZ_A_BYTES;
+                bool ok = true;
+                for (int it = 0; it < w.nk; ++it, ++kit) {
+                    const int s = kit % S;
+                    const uint32_t ph = (kit / S) & 1;
+                    if (!mbar_wait(smem_u32(&bars[s]), ph, OZ_TIMEOUT_NS)) {
+                        atomicOr(status, DEV_TIMEOUT);
+                        *abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    fence_after_sync();
+                    const uint32_t a0 = smem_u32(smem + s * Cfg::STAGE_BYTES);
+                    const uint32_t b0 = a0 + Cfg::A_BYTES;
 #pragma unroll
-                for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+                    for (int kk = 0; kk < OZ_BK / 16; ++kk) {
 #pragma unroll
-                    for (int sa = 0; sa < OZ_SLICES_A; ++sa) {
+                        for (int sa = 0; sa < Cfg::SA; ++sa) {
 #pragma unroll
-                        for (int sb = 0; sb < OZ_SLICES_B; ++sb) {
-                            if (sa + sb > OZ_MAX_LEVEL) continue;
-                            const int lvl = (sa + sb < OZ_NACC - 1) ? sa + sb : OZ_NACC - 1;
-                            const uint64_t ad = desc_kmajor_sw64(a0 + sa * OZ_SLICE_BYTES + kk * 32);
-                            const uint64_t bd = desc_kmajor_sw64(b0 + sb * OZ_SLICE_BYTES + kk * 32);
-                            // the pairs (0, t) come first for every accumulator t: at the very
-                            // first k step they overwrite it, everything else accumulates
-                            const uint32_t acc = (it == 0 && kk == 0 && sa == 0) ? 0u : 1u;
-                            mma_bf16(tmem + (uint32_t)(lvl * OZ_BN), ad, bd, OZ_IDESC, acc);
+                            for (int sb = 0; sb < Cfg::SB; ++sb) {
+                                if (sa + sb > Cfg::L) continue;
+                                const int lvl = (sa + sb < OZ_NACC - 1) ? sa + sb : OZ_NACC - 1;
+                                const uint64_t ad = desc_kmajor_sw64(a0 + sa * OZ_SLICE_BYTES + kk * 32);
+                                const uint64_t bd = desc_kmajor_sw64(b0 + sb * OZ_SLICE_BYTES + kk * 32);
+                                // the pairs (0, t), t <= 3, come first and open accumulator t at the
+                                // unit's first k step; everything else accumulates
+                                const uint32_t acc = (it == 0 && kk == 0 && sa == 0 && sb < OZ_NACC) ? 0u : 1u;
+                                mma_bf16(tmem + (uint32_t)(lvl * OZ_BN), ad, bd, OZ_IDESC, acc);
+                            }
                         }
                     }
+                    mma_commit(smem_u32(&bars[S + s]));
                 }
-                mma_commit(smem_u32(&bars[OZ_STAGES + s]));
+                if (!ok) break;
+                mma_commit(acc_full);
             }
-            if (!ok) atomicOr(p.status, DEV_TIMEOUT);
-            mma_commit(smem_u32(&bars[2 * OZ_STAGES]));
+            // every MMA issued has completed before TMEM is released
+            mma_commit(smem_u32(&bars[2 * S + 2]));
+            if (!mbar_wait(smem_u32(&bars[2 * S + 2]), 0, OZ_TIMEOUT_NS)) {
+                if (status) atomicOr(status, DEV_TIMEOUT);
+                *abort_flag = 1;
+            }
         }
     } else {
         // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 = tile rows, columns
-        // [cq, cq + OZ_EPI_COLS) with cq = OZ_EPI_COLS * ((w - 2) / 4)
+        // [cq, cq + 64) with cq = 64 * ((w - 2) / 4)
         const int q = warp & 3;
         const int ew = warp - 2;                                   // 0 .. OZ_EPI_WARPS-1
         const int cq = OZ_EPI_COLS * (ew / 4);
-        const int i = m0 + 32 * q + lane;
-        const bool ready_here = mbar_wait(smem_u32(&bars[2 * OZ_STAGES]), 0, OZ_TIMEOUT_NS);
-        // one decision for all epilogue threads (they share named barrier 1 below)
-        uint32_t all_ready;
-        asm volatile(
-            "{\n"
-            " .reg .pred p, r;\n"
-            " setp.ne.u32 p, %1, 0;\n"
-            " bar.red.and.pred r, 1, 256, p;\n"
-            " selp.u32 %0, 1, 0, r;\n"
-            "}\n"
-            : "=r"(all_ready)
-            : "r"((uint32_t)ready_here)
-            : "memory");
-        const bool ready = all_ready != 0;
-        fence_after_sync();
-        if (!ready) {
-            if (lane == 0) atomicOr(p.status, DEV_TIMEOUT);
-        } else {
+        int li = 0;
+        for (int u = blockIdx.x; u < units; u += gridDim.x, ++li) {
+            OzUnit w;
+            resolve(u, w);
+            const OzParams& p = *w.p;
+            const bool ready_here = !*abort_flag && mbar_wait(acc_full, li & 1, OZ_TIMEOUT_NS);
+            // one decision for all epilogue threads (they share named barrier 1 below)
+            uint32_t all_ready;
+            asm volatile(
+                "{\n"
+                " .reg .pred p, r;\n"
+                " setp.ne.u32 p, %1, 0;\n"
+                " bar.red.and.pred r, 1, 256, p;\n"
+                " selp.u32 %0, 1, 0, r;\n"
+                "}\n"
+                : "=r"(all_ready)
+                : "r"((uint32_t)ready_here)
+                : "memory");
+            if (!all_ready) {
+                if (lane == 0) atomicOr(p.status, DEV_TIMEOUT);
+                *abort_flag = 1;
+                break;
+            }
+            fence_after_sync();
+            const int m0 = w.tm * OZ_BM, n0 = w.tn * OZ_BN;
             const int il = 32 * q + lane;                          // tile row of this thread
-            const size_t tile_elems = (size_t)OZ_BM * OZ_BN;
-            // level sums of 32 columns starting at c * 32: hi = level 0 (exact), lo = levels 1-4
-            auto tmem_chunk = [&](int c, float (&hv)[32], float (&lv)[32]) {
-                uint32_t r0[32], r1[32], r2[32], r3[32];
-                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(c * 32);
-                tmem_ld_32x32b_x32(ta, r0);
-                tmem_ld_32x32b_x32(ta + OZ_BN, r1);
-                tmem_ld_32x32b_x32(ta + 2 * OZ_BN, r2);
-                tmem_ld_32x32b_x32(ta + 3 * OZ_BN, r3);
-                tmem_ld_wait();
+            const int i = m0 + il;
+            if (Cfg::ACC) {
+                oz_store_chunk_half(p, tmem, q, cq, m0, n0, i, w.chunk);
+                oz_store_chunk_half(p, tmem, q, cq + 32, m0, n0, i, w.chunk);
+                fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acc_empty);
+                continue;
+            }
+            uint32_t h0[32], l0[32], h1[32], l1[32];
+            oz_load_half(tmem, q, cq, h0, l0);
+            oz_load_half(tmem, q, cq + 32, h1, l1);
+            // the accumulators are in registers: hand TMEM back to the MMA warp
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty);
+            if (w.nparts > 1) {
+                // split K: publish this part's level sums; oz_tail_kernel adds the parts
+                constexpr size_t tile_elems = (size_t)OZ_BM * OZ_BN;
+                float2* mine = p.ws + ((size_t)w.widx * w.nparts + w.part) * tile_elems + (size_t)il * OZ_BN + cq;
 #pragma unroll
                 for (int jj = 0; jj < 32; ++jj) {
-                    hv[jj] = __uint_as_float(r0[jj]);
-                    lv[jj] = (__uint_as_float(r1[jj]) + __uint_as_float(r2[jj])) + __uint_as_float(r3[jj]);
+                    mine[jj] = make_float2(__uint_as_float(h0[jj]), __uint_as_float(l0[jj]));
+                    mine[32 + jj] = make_float2(__uint_as_float(h1[jj]), __uint_as_float(l1[jj]));
                 }
-            };
-            bool run_epilogue = true;
-            if (nparts > 1) {
-                // split K: publish this part's sums, count arrivals; the last part finishes
-                float2* mine = p.ws + ((size_t)widx * nparts + part) * tile_elems;
-#pragma unroll 1
-                for (int c = cq / 32; c < (cq + OZ_EPI_COLS) / 32; ++c) {
-                    float hv[32], lv[32];
-                    tmem_chunk(c, hv, lv);
-#pragma unroll
-                    for (int jj = 0; jj < 32; ++jj) mine[(size_t)il * OZ_BN + c * 32 + jj] = make_float2(hv[jj], lv[jj]);
-                }
-                __threadfence();
-                asm volatile("bar.sync 1, 256;" ::: "memory");
-                volatile int* flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-                if (ew == 0 && lane == 0) *flag = atomicAdd(p.ws_cnt + widx, 1);
-                asm volatile("bar.sync 1, 256;" ::: "memory");
-                run_epilogue = (*flag == nparts - 1);
-                if (run_epilogue) {
-                    __threadfence();
-                    if (ew == 0 && lane == 0) p.ws_cnt[widx] = 0;    // ready for the next launch
-                }
+                continue;
             }
-            // level sums of a chunk: from TMEM, or the parts' sums added in part order
-            auto chunk = [&](int c, float (&hv)[32], float (&lv)[32]) {
-                if (nparts == 1) {
-                    tmem_chunk(c, hv, lv);
-                    return;
-                }
-                const float2* base = p.ws + (size_t)widx * nparts * tile_elems + (size_t)il * OZ_BN + c * 32;
-#pragma unroll
-                for (int jj = 0; jj < 32; ++jj) {
-                    hv[jj] = 0.0f;
-                    lv[jj] = 0.0f;
-                }
-                for (int pp = 0; pp < nparts; ++pp) {
-#pragma unroll
-                    for (int jj = 0; jj < 32; ++jj) {
-                        const float2 v = base[pp * tile_elems + jj];
-                        hv[jj] += v.x;
-                        lv[jj] += v.y;
-                    }
-                }
-            };
-            if (run_epilogue && p.mode == OZ_OUT_PAIR) {
-                const float sA = (i < p.M) ? p.sa[i] : 0.0f;
-#pragma unroll 1
-                for (int c = cq / 32; c < (cq + OZ_EPI_COLS) / 32; ++c) {
-                    float hv[32], lv[32];
-                    chunk(c, hv, lv);
-                    if (i >= p.M) continue;
-#pragma unroll
-                    for (int jj = 0; jj < 32; ++jj) {
-                        const int j = n0 + c * 32 + jj;
-                        if (j >= p.N) break;
-                        const float s = sA * p.sb[j];
-                        // TwoSum: (sh, sl) = hi + lo exactly
-                        const float sh = hv[jj] + lv[jj];
-                        const float bb = sh - hv[jj];
-                        const float sl = (hv[jj] - (sh - bb)) + (lv[jj] - bb);
-                        p.Cp[(size_t)i * p.ldc + j] = make_float2(sh * s, sl * s);
-                    }
-                }
-            } else if (run_epilogue) {
-                // FP64 output, staged through shared memory (the operand stages are idle now: every
-                // MMA has completed, so every TMA load they consumed has landed):
-                // (1) each thread converts its row segment of the tile into T[row][col];
-                // (2) the epilogue warps write row segments of C coalesced, adding the addends;
-                // (3) for a symmetric output they write the mirror from T's columns, coalesced.
-                constexpr int TLD = OZ_BN + 1;
-                double* T = reinterpret_cast<double*>(smem);
-                const float sA = (i < p.M) ? p.sa[i] : 0.0f;
-#pragma unroll 1
-                for (int c = cq / 32; c < (cq + OZ_EPI_COLS) / 32; ++c) {
-                    float hv[32], lv[32];
-                    chunk(c, hv, lv);
-#pragma unroll
-                    for (int jj = 0; jj < 32; ++jj) {
-                        const int j = n0 + c * 32 + jj;
-                        const float s = (j < p.N) ? sA * p.sb[j] : 0.0f;
-                        const float sh = hv[jj] + lv[jj];
-                        const float bb = sh - hv[jj];
-                        const float sl = (hv[jj] - (sh - bb)) + (lv[jj] - bb);
-                        T[il * TLD + c * 32 + jj] = f2d_bits(sh * s) + f2d_bits(sl * s);
-                    }
-                }
-                asm volatile("bar.sync 1, 256;" ::: "memory");
-                const double alpha = p.alpha;
-                // rows ew, ew+8, ..., in batches of 4 rows x 4 column groups (the whole tile width):
-                // 16 independent addend loads in flight per thread
-                for (int rb = 0; rb < OZ_BM / OZ_EPI_WARPS; rb += 4) {
-                    double a1[4][OZ_BN / 32], a2[4][OZ_BN / 32];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int gi = m0 + ew + OZ_EPI_WARPS * (rb + u);
-#pragma unroll
-                        for (int h = 0; h < OZ_BN / 32; ++h) {
-                            const int gj = n0 + lane + 32 * h;
-                            const bool in = gi < p.M && gj < p.N;
-                            const size_t off = (size_t)gi * p.ldc + gj;
-                            a1[u][h] = (in && p.D1) ? p.D1[off] : 0.0;
-                            a2[u][h] = (in && p.D2) ? p.D2[off] : 0.0;
-                        }
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int r = ew + OZ_EPI_WARPS * (rb + u);
-                        const int gi = m0 + r;
-                        if (gi >= p.M) continue;
-#pragma unroll
-                        for (int h = 0; h < OZ_BN / 32; ++h) {
-                            const int cc = lane + 32 * h;
-                            const int gj = n0 + cc;
-                            if (gj >= p.N || (p.tri && gi > gj)) continue;
-                            const size_t off = (size_t)gi * p.ldc + gj;
-                            double v = T[r * TLD + cc];
-                            if (alpha != 1.0) v *= alpha;
-                            if (p.D1) v += p.b1 * a1[u][h];
-                            if (p.D2) v += p.b2 * a2[u][h];
-                            if (p.D3) v += p.b3 * p.D3[off];
-                            p.Cd[off] = v;
-                            T[r * TLD + cc] = v;
-                        }
-                    }
-                }
-                if (p.tri) {
-                    asm volatile("bar.sync 1, 256;" ::: "memory");
-                    for (int cc = ew; cc < OZ_BN; cc += OZ_EPI_WARPS) {
-                        const int gj = n0 + cc;
-                        if (gj >= p.N) continue;
-#pragma unroll
-                        for (int h = 0; h < OZ_BM / 32; ++h) {
-                            const int r = lane + 32 * h;
-                            const int gi = m0 + r;
-                            if (gi >= p.M || gi >= gj) continue;
-                            p.Cd[(size_t)gj * p.ldc + gi] = T[r * TLD + cc];
-                        }
-                    }
-                }
-            }
+            const bool diag = p.tri && w.tm == w.tn;
+            oz_store_half(p, m0, n0, i, cq, diag, h0, l0);
+            oz_store_half(p, m0, n0, i, cq + 32, diag, h1, l1);
         }
     }
     fence_before_sync();
@@ -701,32 +798,65 @@ __device__ __forceinline__ void oz_gemm_tile(const CUtensorMap* tmA, const CUten
     if (warp == 1) tmem_dealloc(tmem, 512);
 }
 
+template <class Cfg>
 __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                             const __grid_constant__ CUtensorMap tmB,
-                                                             const OzParams p) {
-    const int b = blockIdx.x;
-    if (p.split_parts <= 1 || b < p.split_first) {
-        oz_gemm_tile(&tmA, &tmB, p, b, 0, 1, 0);
-    } else {
-        const int j = b - p.split_first;
-        oz_gemm_tile(&tmA, &tmB, p, p.split_first + j / p.split_parts, j % p.split_parts, p.split_parts,
-                     j / p.split_parts);
-    }
+                                                                   const __grid_constant__ CUtensorMap tmB,
+                                                                   const __grid_constant__ OzParams p) {
+    oz_persistent<Cfg>(p.units, [&](int u, OzUnit& o) { oz_single_unit(&p, &tmA, &tmB, Cfg::ACC, u, o); });
 }
 
-// Grouped form: the tiles of every problem laid end to end; a CTA finds its
+// Grouped form: the tiles of every problem laid end to end; a unit finds its
 // problem by binary search over the start offsets and reads that problem's
 // tensor maps from global memory.  A tile is computed exactly as in the
 // single-problem kernel.
-__global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_gemm_grouped_kernel(const OzGroupDesc* __restrict__ d, int nd) {
-    const int b = blockIdx.x;
-    int lo = 0, hi = nd - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (d[mid].start <= b) lo = mid;
-        else hi = mid - 1;
+template <class Cfg>
+__global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_gemm_grouped_kernel(const OzGroupDesc* __restrict__ d, int nd,
+                                                                           int units) {
+    oz_persistent<Cfg>(units, [&](int u, OzUnit& o) { oz_group_unit(d, nd, u, o); });
+}
+
+// Split K of the tail: one CTA per split tile, one thread per tile row; the
+// parts' level sums are added in part order (the level-0 parts are exact
+// integers, so their sum is exact) and the tile's epilogue runs on the result.
+__global__ void __launch_bounds__(OZ_BM) oz_tail_kernel(const __grid_constant__ OzParams p) {
+    constexpr size_t tile_elems = (size_t)OZ_BM * OZ_BN;
+    const int widx = blockIdx.x, il = threadIdx.x;
+    int tm, tn;
+    oz_tile_coords(p, p.split_first + widx, tm, tn);
+    const int m0 = tm * OZ_BM, n0 = tn * OZ_BN;
+    const float2* base = p.ws + (size_t)widx * p.split_parts * tile_elems + (size_t)il * OZ_BN;
+    const bool diag = p.tri && tm == tn;
+#pragma unroll 1
+    for (int c0 = 0; c0 < OZ_BN; c0 += 32) {
+        uint32_t h[32], l[32];
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) h[jj] = l[jj] = 0u;
+        for (int pp = 0; pp < p.split_parts; ++pp) {
+            const float2* src = base + (size_t)pp * tile_elems + c0;
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+                const float2 v = src[jj];
+                h[jj] = __float_as_uint(__uint_as_float(h[jj]) + v.x);
+                l[jj] = __float_as_uint(__uint_as_float(l[jj]) + v.y);
+            }
+        }
+        oz_store_half(p, m0, n0, m0 + il, c0, diag, h, l);
     }
-    oz_gemm_tile(&d[lo].tmA, &d[lo].tmB, d[lo].p, b - d[lo].start, 0, 1, 0);
+}
+
+// Accurate mode, second pass: C = alpha sum_c ws[c] + b1 D1 + b2 D2 (chunk order).
+__global__ void __launch_bounds__(256) oz_chunk_reduce_kernel(const OzParams p) {
+    const size_t total = (size_t)p.M * p.N;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int c = 0; c < p.nchunks; ++c) v += p.wsd[(size_t)c * total + e];
+        const size_t i = e / p.N, j = e - i * p.N;
+        const size_t off = i * p.ldc + j;
+        v *= p.alpha;
+        if (p.D1) v += p.b1 * p.D1[off];
+        if (p.D2) v += p.b2 * p.D2[off];
+        p.Cd[off] = v;
+    }
 }
 
 // ============================================================== host side
@@ -753,7 +883,7 @@ dme_status make_slice_tmap(const SliceBuf& sb, CUtensorMap* out) {
     DME_TRY(get_encoder());
     cuuint64_t dims[3] = {(cuuint64_t)sb.Kp, (cuuint64_t)sb.rows, (cuuint64_t)sb.ns};
     cuuint64_t strides[2] = {(cuuint64_t)sb.Kp * 2, (cuuint64_t)sb.rows * sb.Kp * 2};
-    cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)OZ_BM, (cuuint32_t)sb.ns};
+    cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)OZ_BM, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = g_encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)sb.data, dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
@@ -769,6 +899,47 @@ int slice_kpad(int k) { return (k + OZ_BK - 1) / OZ_BK * OZ_BK; }
 
 size_t slice_buf_bytes(int rows, int k, int ns) { return (size_t)ns * rows * slice_kpad(k) * 2; }
 
+dme_status oz_params(const SliceBuf& A, const SliceBuf& B, int cfg, OzParams* p) {
+    if (cfg < 0 || cfg >= OZ_NCFG) return set_error("split gemm: unknown slice-pair configuration"), DME_EINVAL;
+    if (A.ns < oz_cfg_slices_a(cfg) || B.ns < oz_cfg_slices_b(cfg) || A.scheme != oz_cfg_scheme(cfg) ||
+        B.scheme != oz_cfg_scheme(cfg) || A.Kp != B.Kp)
+        return set_error("split gemm: the slice buffers do not hold what the configuration reads"), DME_EINVAL;
+    std::memset(p, 0, sizeof(*p));
+    p->M = A.rows;
+    p->N = B.rows;
+    p->Kp = A.Kp;
+    p->cfg = cfg;
+    p->sa = A.scale;
+    p->sb = B.scale;
+    p->alpha = 1.0;
+    return DME_OK;
+}
+
+size_t oz_acc_ws_doubles(int M, int N, int K) {
+    const int nk = slice_kpad(K) / OZ_BK;
+    return (size_t)((nk + OZ_ACC_CHUNK_KB - 1) / OZ_ACC_CHUNK_KB) * M * N;
+}
+
+static int sm_count() {
+    static const int nsm = [] {
+        int dev = 0, c = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+        return std::max(c, 1);
+    }();
+    return nsm;
+}
+
+template <class Cfg>
+static dme_status oz_launch_single(const CUtensorMap& tA, const CUtensorMap& tB, const OzParams& p, int grid,
+                                   cudaStream_t st) {
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(ozaki_gemm_kernel<Cfg>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    DME_CUDA_TRY(attr);
+    ozaki_gemm_kernel<Cfg><<<grid, OZ_THREADS, Cfg::SMEM, st>>>(tA, tB, p);
+    DME_CUDA_TRY(cudaGetLastError());
+    return DME_OK;
+}
 
 dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzParams p, cudaStream_t st) {
     if (p.M <= 0 || p.N <= 0) return DME_OK;
@@ -780,67 +951,101 @@ dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzPar
         set_error("ozaki gemm: triangle mode needs M == N");
         return DME_EINVAL;
     }
-    static const cudaError_t attr =
-        cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
-    DME_CUDA_TRY(attr);
+    const bool acc = p.cfg == OZ_A21;
+    if (acc && (p.mode != OZ_OUT_F64 || p.tri || p.D3 || !p.wsd)) {
+        set_error("ozaki gemm: the accurate mode writes a full FP64 product through its chunk workspace");
+        return DME_EINVAL;
+    }
+    const int nsm = sm_count();
     const int tmt = (p.M + OZ_BM - 1) / OZ_BM, tnt = (p.N + OZ_BN - 1) / OZ_BN;
     p.tiles_n = tnt;
-    const int tiles = p.tri ? tnt * (tnt + 1) / 2 : tmt * tnt;
-    // split K of the last partial wave in two when it fills at most half of the SMs:
-    // the wave then takes about half a tile time instead of a whole one
-    static const int nsm = [] {
-        int dev = 0, c = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
-        return std::max(c, 1);
-    }();
-    const int tail = tiles % nsm;
+    p.tiles = p.tri ? tnt * (tnt + 1) / 2 : tmt * tnt;
+    const int tiles = p.tiles;
     p.split_parts = 1;
     p.split_first = tiles;
-    if (p.ws && p.ws_cnt && tiles > nsm && tail > 0 && tail <= OZ_SPLIT_MAX_TAIL && tail <= nsm / 2 &&
-        p.Kp / OZ_BK >= 16) {
-        p.split_parts = 2;
-        p.split_first = tiles - tail;
-    } else if (p.ws && p.ws_cnt && tiles <= nsm / 2 && tiles <= OZ_SPLIT_MAX_TAIL && p.Kp / OZ_BK >= 16) {
-        // a single partial wave (skinny products): up to 4 K parts, at least 8 K blocks each,
-        // within the SM count and the workspace's 2 x OZ_SPLIT_MAX_TAIL tile slots
-        int parts = 1;
-        while (parts < 4 && tiles * (parts * 2) <= nsm && tiles * (parts * 2) <= 2 * OZ_SPLIT_MAX_TAIL &&
-               p.Kp / OZ_BK / (parts * 2) >= 8)
-            parts *= 2;
-        if (parts > 1) {
-            p.split_parts = parts;
-            p.split_first = 0;
+    p.nchunks = 1;
+    if (acc) {
+        p.nchunks = (p.Kp / OZ_BK + OZ_ACC_CHUNK_KB - 1) / OZ_ACC_CHUNK_KB;
+        p.units = tiles * p.nchunks;
+    } else {
+        // split K of the last partial wave in two when it fills at most half of the SMs:
+        // the wave then takes about half a tile time instead of a whole one
+        const int tail = tiles % nsm;
+        if (p.ws && tiles > nsm && tail > 0 && tail <= OZ_SPLIT_MAX_TAIL && tail <= nsm / 2 &&
+            p.Kp / OZ_BK >= 16) {
+            p.split_parts = 2;
+            p.split_first = tiles - tail;
+        } else if (p.ws && tiles <= nsm / 2 && tiles <= OZ_SPLIT_MAX_TAIL && p.Kp / OZ_BK >= 16) {
+            // a single partial wave (skinny products): up to 4 K parts, at least 8 K blocks each,
+            // within the SM count and the workspace's 2 x OZ_SPLIT_MAX_TAIL tile slots
+            int parts = 1;
+            while (parts < 4 && tiles * (parts * 2) <= nsm && tiles * (parts * 2) <= 2 * OZ_SPLIT_MAX_TAIL &&
+                   p.Kp / OZ_BK / (parts * 2) >= 8)
+                parts *= 2;
+            if (parts > 1) {
+                p.split_parts = parts;
+                p.split_first = 0;
+            }
         }
+        p.units = p.split_first + (tiles - p.split_first) * p.split_parts;
     }
-    const int grid = p.split_first + (tiles - p.split_first) * p.split_parts;
-    ozaki_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM_BYTES, st>>>(tA, tB, p);
-    DME_CUDA_TRY(cudaGetLastError());
+    const int grid = std::min(p.units, nsm);
+    switch (p.cfg) {
+        case OZ_P10: DME_TRY(oz_launch_single<CfgP10>(tA, tB, p, grid, st)); break;
+        case OZ_P13: DME_TRY(oz_launch_single<CfgP13>(tA, tB, p, grid, st)); break;
+        case OZ_P14: DME_TRY(oz_launch_single<CfgP14>(tA, tB, p, grid, st)); break;
+        case OZ_A21: DME_TRY(oz_launch_single<CfgA21>(tA, tB, p, grid, st)); break;
+        default: return set_error("ozaki gemm: unknown configuration"), DME_EINVAL;
+    }
+    if (p.split_parts > 1) {
+        oz_tail_kernel<<<tiles - p.split_first, OZ_BM, 0, st>>>(p);
+        DME_CUDA_TRY(cudaGetLastError());
+    }
+    if (acc) {
+        const size_t total = (size_t)p.M * p.N;
+        const int g = (int)std::min<size_t>((total + 255) / 256, (size_t)nsm * 8);
+        oz_chunk_reduce_kernel<<<g, 256, 0, st>>>(p);
+        DME_CUDA_TRY(cudaGetLastError());
+    }
+    return DME_OK;
+}
+
+template <class Cfg>
+static dme_status oz_grouped_attr() {
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(ozaki_gemm_grouped_kernel<Cfg>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    DME_CUDA_TRY(attr);
     return DME_OK;
 }
 
 dme_status ozaki_grouped_prepare() {
-    static const cudaError_t attr =
-        cudaFuncSetAttribute(ozaki_gemm_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
-    DME_CUDA_TRY(attr);
+    DME_TRY(oz_grouped_attr<CfgP10>());
+    DME_TRY(oz_grouped_attr<CfgP13>());
+    DME_TRY(oz_grouped_attr<CfgP14>());
     return DME_OK;
 }
 
 dme_status launch_ozaki_grouped(std::vector<OzGroupDesc>& items, OzGroupDesc* dev_desc, cudaStream_t st,
                                 DescArena* arena) {
-    int total = 0;
+    int total = 0, cfg = -1;
     std::vector<OzGroupDesc> live;
     for (auto& it : items) {
         OzParams& p = it.p;
         if (p.M <= 0 || p.N <= 0) continue;
-        if (p.Kp % OZ_BK != 0 || p.Kp > OZ_MAX_K || (p.tri && p.M != p.N)) {
-            set_error("ozaki grouped gemm: bad problem shape");
+        if (p.Kp % OZ_BK != 0 || p.Kp > OZ_MAX_K || (p.tri && p.M != p.N) || p.cfg == OZ_A21 ||
+            (cfg >= 0 && p.cfg != cfg)) {
+            set_error("ozaki grouped gemm: bad problem shape or mixed configurations");
             return DME_EINVAL;
         }
+        cfg = p.cfg;
         const int tmt = (p.M + OZ_BM - 1) / OZ_BM, tnt = (p.N + OZ_BN - 1) / OZ_BN;
         p.tiles_n = tnt;
+        p.tiles = p.tri ? tnt * (tnt + 1) / 2 : tmt * tnt;
+        p.split_parts = 1;
+        p.split_first = p.tiles;
+        p.units = p.tiles;
         it.start = total;
-        total += p.tri ? tnt * (tnt + 1) / 2 : tmt * tnt;
+        total += p.tiles;
         live.push_back(it);
     }
     if (total == 0) return DME_OK;
@@ -852,7 +1057,19 @@ dme_status launch_ozaki_grouped(std::vector<OzGroupDesc>& items, OzGroupDesc* de
     } else {
         DME_CUDA_TRY(cudaMemcpyAsync(d, live.data(), live.size() * sizeof(OzGroupDesc), cudaMemcpyHostToDevice, st));
     }
-    ozaki_gemm_grouped_kernel<<<total, OZ_THREADS, OZ_SMEM_BYTES, st>>>(d, (int)live.size());
+    const int grid = std::min(total, sm_count());
+    const int nd = (int)live.size();
+    switch (cfg) {
+        case OZ_P10:
+            ozaki_gemm_grouped_kernel<CfgP10><<<grid, OZ_THREADS, CfgP10::SMEM, st>>>(d, nd, total);
+            break;
+        case OZ_P13:
+            ozaki_gemm_grouped_kernel<CfgP13><<<grid, OZ_THREADS, CfgP13::SMEM, st>>>(d, nd, total);
+            break;
+        default:
+            ozaki_gemm_grouped_kernel<CfgP14><<<grid, OZ_THREADS, CfgP14::SMEM, st>>>(d, nd, total);
+            break;
+    }
     DME_CUDA_TRY(cudaGetLastError());
     return DME_OK;
 }
@@ -909,8 +1126,8 @@ extern "C" dme_status dme_gemm_split_noalloc(int M, int N, int K, const double* 
         const size_t off_sa = 256;
         const size_t off_sb = off_sa + align256(sizeof(float) * (size_t)M);
         const size_t off_a = off_sb + align256(sizeof(float) * (size_t)N);
-        const size_t off_b = off_a + align256(slice_buf_bytes(M, K, OZ_SLICES_A));
-        const size_t need = off_b + align256(slice_buf_bytes(N, K, OZ_SLICES_B));
+        const size_t off_b = off_a + align256(slice_buf_bytes(M, K, OZ_SLICES_FIXED));
+        const size_t need = off_b + align256(slice_buf_bytes(N, K, OZ_SLICES_STEP));
         if (need > kNoAllocScratchBytes) {
             set_error("dme_gemm_split_noalloc: M=" + std::to_string(M) + " N=" + std::to_string(N) +
                       " K=" + std::to_string(K) + " needs " + std::to_string(need) +
@@ -926,13 +1143,13 @@ extern "C" dme_status dme_gemm_split_noalloc(int M, int N, int K, const double* 
         sa.rows = M;
         sa.k = K;
         sa.Kp = Kp;
-        sa.ns = OZ_SLICES_A;
+        sa.ns = OZ_SLICES_FIXED;
         sa.scale = reinterpret_cast<float*>(base + off_sa);
         sa.data = reinterpret_cast<__nv_bfloat16*>(base + off_a);
         sb.rows = N;
         sb.k = K;
         sb.Kp = Kp;
-        sb.ns = OZ_SLICES_B;
+        sb.ns = OZ_SLICES_STEP;
         sb.scale = reinterpret_cast<float*>(base + off_sb);
         sb.data = reinterpret_cast<__nv_bfloat16*>(base + off_b);
         DME_TRY(make_slice_tmap(sa, &sa.tmap));
@@ -943,16 +1160,10 @@ extern "C" dme_status dme_gemm_split_noalloc(int M, int N, int K, const double* 
         launch_slice_rows_f64(A, M, K, K, sa, st);
         launch_slice_rows_f64(B, N, K, K, sb, st);
         OzParams o;
-        std::memset(&o, 0, sizeof(o));
-        o.M = M;
-        o.N = N;
-        o.Kp = Kp;
-        o.sa = sa.scale;
-        o.sb = sb.scale;
+        DME_TRY(oz_params(sa, sb, OZ_P14, &o));
         o.mode = OZ_OUT_F64;
         o.ldc = N;
         o.Cd = C;
-        o.alpha = 1.0;
         o.status = status;
         DME_TRY(launch_ozaki_gemm(sa.tmap, sb.tmap, o, st));
         int hs = 0;

@@ -467,12 +467,9 @@ dme_status apply_split(dme_lr_t lr, const SliceBuf& Msl, const double* X, int ld
     launch_transpose(X, lr->Xtr, n, k, ldx, n, st);
     launch_slice_rows_f64(lr->Xtr, k, n, n, lr->xsl, st);
     OzParams p;
-    std::memset(&p, 0, sizeof(p));
+    DME_TRY(oz_params(Msl, lr->xsl, OZ_P14, &p));
     p.M = n;
-    p.N = k;
-    p.Kp = Msl.Kp;
-    p.sa = Msl.scale;
-    p.sb = lr->xsl.scale;
+    p.N = k;                     // the first k of the buffer's rows
     p.mode = OZ_OUT_F64;
     p.ldc = ldc;
     p.Cd = C;
@@ -684,14 +681,15 @@ dme_status lr_setup(dme_lr_t lr, const dme_plan_desc* desc, const double* C, int
         lr->xsl.rows = (int)rc;
         lr->xsl.k = (int)n;
         lr->xsl.Kp = slice_kpad((int)n);
-        lr->xsl.ns = OZ_SLICES_B;
+        lr->xsl.ns = OZ_SLICES_STEP;
+        lr->xsl.scheme = OZ_DIG9;
         double* xd = nullptr;
-        DME_TRY(lr_alloc(lr, &xd, (slice_buf_bytes((int)rc, (int)n, OZ_SLICES_B) + 7) / 8));
+        DME_TRY(lr_alloc(lr, &xd, (slice_buf_bytes((int)rc, (int)n, OZ_SLICES_STEP) + 7) / 8));
         lr->xsl.data = reinterpret_cast<__nv_bfloat16*>(xd);
         double* xs = nullptr;
         DME_TRY(lr_alloc(lr, &xs, (rc + 1) / 2));
         lr->xsl.scale = reinterpret_cast<float*>(xs);
-        DME_CUDA_TRY(cudaMemsetAsync(xd, 0, slice_buf_bytes((int)rc, (int)n, OZ_SLICES_B), st));
+        DME_CUDA_TRY(cudaMemsetAsync(xd, 0, slice_buf_bytes((int)rc, (int)n, OZ_SLICES_STEP), st));
         DME_CUDA_TRY(cudaMemsetAsync(xs, 0, sizeof(float) * rc, st));
         DME_TRY(make_slice_tmap(lr->xsl, &lr->xsl.tmap));
     }
@@ -728,7 +726,10 @@ dme_status dme_lr_plan(const dme_plan_desc* desc, const double* A, const double*
     DME_TRY(plan_validate(desc, A, C, B, R, S));
     return guarded([&]() -> dme_status {
         std::unique_ptr<dme_lr_s, void (*)(dme_lr_t)> lr(new dme_lr_s(), lr_free);
-        DME_TRY(plan_create(desc, A, C, B, R, S, cuda_stream, &lr->P));
+        // the dense plan only supplies E_t, S and their slices: no slice-pair probe
+        dme_plan_desc d2 = *desc;
+        if (d2.prec == DME_SPLIT_BF16) d2.pairs = 14;
+        DME_TRY(plan_create(&d2, A, C, B, R, S, cuda_stream, &lr->P));
         lr->st = lr->P->st;
         lr->status = lr->P->status;
         lr->Bt = lr->P->Bt;

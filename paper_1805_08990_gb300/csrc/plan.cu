@@ -154,12 +154,59 @@ dme_status check_status(dme_plan_t p, const char* where) {
     return DME_OK;
 }
 
+// Products of the plan-time exponential on split plans with n >= kAccMinN: the
+// accurate tensor-core mode (six 7-bit slices per operand, exact K chunks of
+// 512 combined in fp64).  A product C = alpha op(L) op(R) + b1 D1 slices the rows
+// of op(L) and the rows of op(R)^T, transposing first where needed.
+constexpr int kAccMinN = 512;
+
+struct AccWork {
+    SliceBuf a, b;          // slices of the A operand (rows of op(L)) and B operand (rows of op(R)^T)
+    double* t = nullptr;    // transpose scratch (n x n)
+    double* wsd = nullptr;  // chunk workspace
+    int* status = nullptr;
+};
+
+dme_status acc_prod(int n, AccWork& w, const double* L, int tL, const double* R, int tR, double* C, double alpha,
+                    const double* D1, double b1, cudaStream_t st) {
+    if (tL) {
+        launch_transpose(L, w.t, n, n, n, n, st);
+        launch_slice_rows_f64(w.t, n, n, n, w.a, st);
+    } else {
+        launch_slice_rows_f64(L, n, n, n, w.a, st);
+    }
+    if (tR) {
+        launch_slice_rows_f64(R, n, n, n, w.b, st);
+    } else {
+        launch_transpose(R, w.t, n, n, n, n, st);
+        launch_slice_rows_f64(w.t, n, n, n, w.b, st);
+    }
+    OzParams o;
+    DME_TRY(oz_params(w.a, w.b, OZ_A21, &o));
+    o.mode = OZ_OUT_F64;
+    o.ldc = n;
+    o.Cd = C;
+    o.alpha = alpha;
+    o.D1 = D1;
+    o.b1 = b1;
+    o.wsd = w.wsd;
+    o.status = w.status;
+    return launch_ozaki_gemm(w.a.tmap, w.b.tmap, o, st);
+}
+
+// C = alpha op(L) op(R) + b1 D1 (n x n): the accurate tensor mode with aw, else FP64.
+dme_status prod(int n, AccWork* aw, const double* L, int tL, const double* R, int tR, double* C, double alpha,
+                const double* D1, double b1, cudaStream_t st) {
+    if (aw) return acc_prod(n, *aw, L, tL, R, tR, C, alpha, D1, b1, st);
+    return gemm1(gp(n, n, n, L, n, tL, R, n, tR, C, n, alpha, 0, D1, b1), st);
+}
+
 // (O22, O12) = (L, L11 = ls L22^T) * (R):  O22 = L22 R22, O12 = ls L22^T R12 + L12 R22.
-dme_status bprod(int n, const double* L22, const double* L12, double ls, const double* R22, const double* R12,
-                 double* O22, double* O12, cudaStream_t st) {
-    DME_TRY(gemm1(gp(n, n, n, L22, n, 0, R22, n, 0, O22, n, 1.0), st));
-    DME_TRY(gemm1(gp(n, n, n, L22, n, 1, R12, n, 0, O12, n, ls), st));
-    DME_TRY(gemm1(gp(n, n, n, L12, n, 0, R22, n, 0, O12, n, 1.0, 0, O12, 1.0), st));
+dme_status bprod(int n, AccWork* aw, const double* L22, const double* L12, double ls, const double* R22,
+                 const double* R12, double* O22, double* O12, cudaStream_t st) {
+    DME_TRY(prod(n, aw, L22, 0, R22, 0, O22, 1.0, nullptr, 0.0, st));
+    DME_TRY(prod(n, aw, L22, 1, R12, 0, O12, ls, nullptr, 0.0, st));
+    DME_TRY(prod(n, aw, L12, 0, R22, 0, O12, 1.0, O12, 1.0, st));
     return DME_OK;
 }
 
@@ -194,20 +241,22 @@ struct ProfScope {
     }
 };
 
-dme_status alloc_slices(dme_plan_t p, SliceBuf* sb, int rows, int k, int ns) {
+dme_status alloc_slices(dme_plan_t p, SliceBuf* sb, int rows, int k, int ns, int scheme = OZ_DIG9) {
     sb->rows = rows;
     sb->k = k;
     sb->Kp = slice_kpad(k);
     sb->ns = ns;
+    sb->scheme = scheme;
     DME_TRY(palloc(p, reinterpret_cast<void**>(&sb->data), slice_buf_bytes(rows, k, ns)));
     DME_TRY(palloc_t(p, &sb->scale, (size_t)rows));
     return make_slice_tmap(*sb, &sb->tmap);
 }
 
 // out = alpha G P G^T + b1 D1 + b2 D2 + b3 D3 on the split-precision path (P
-// symmetric, G given by its row slices).  U = G P (P^T = P), then G U^T.
+// symmetric, G given by its row slices; the addends symmetric).  U = G P
+// (P^T = P), then G U^T, both with slice-pair configuration cfg.
 dme_status split_cong(dme_plan_t p, const double* P, const SliceBuf& G, double* out, double alpha, const double* D1,
-                      double b1, const double* D2, double b2, const double* D3, double b3) {
+                      double b1, const double* D2, double b2, const double* D3, double b3, int cfg) {
     const int n = p->n;
     cudaStream_t st = p->st;
     {
@@ -215,12 +264,7 @@ dme_status split_cong(dme_plan_t p, const double* P, const SliceBuf& G, double* 
         launch_slice_rows_f64(P, n, n, n, p->psl, st);
     }
     OzParams a;
-    std::memset(&a, 0, sizeof(a));
-    a.M = n;
-    a.N = n;
-    a.Kp = G.Kp;
-    a.sa = G.scale;
-    a.sb = p->psl.scale;
+    DME_TRY(oz_params(G, p->psl, cfg, &a));
     a.mode = OZ_OUT_PAIR;
     a.ldc = n;
     a.Cp = p->U;
@@ -236,12 +280,7 @@ dme_status split_cong(dme_plan_t p, const double* P, const SliceBuf& G, double* 
         launch_slice_rows_pair(p->U, n, n, n, p->usl, st);
     }
     OzParams b;
-    std::memset(&b, 0, sizeof(b));
-    b.M = n;
-    b.N = n;
-    b.Kp = G.Kp;
-    b.sa = G.scale;
-    b.sb = p->usl.scale;
+    DME_TRY(oz_params(G, p->usl, cfg, &b));
     b.mode = OZ_OUT_F64;
     b.tri = 1;
     b.ldc = n;
@@ -272,12 +311,7 @@ dme_status split_riccati(dme_plan_t p, double* P, double tau, double qcoef) {
     double* Y = Z + (size_t)n * m;
     launch_slice_rows_f64(P, n, n, n, p->psl, st);
     OzParams a;
-    std::memset(&a, 0, sizeof(a));
-    a.M = m;
-    a.N = n;
-    a.Kp = p->btsl.Kp;
-    a.sa = p->btsl.scale;
-    a.sb = p->psl.scale;
+    DME_TRY(oz_params(p->btsl, p->psl, p->cfg, &a));
     a.mode = OZ_OUT_F64;
     a.ldc = n;
     a.Cd = p->Zt;
@@ -288,15 +322,10 @@ dme_status split_riccati(dme_plan_t p, double* P, double tau, double qcoef) {
     DME_TRY(launch_ozaki_gemm(p->btsl.tmap, p->psl.tmap, a, st));
     launch_transpose(p->Zt, Z, m, n, n, m, st);
     DME_TRY(launch_riccati_from_z(p->Bt, n, m, tau, p->rwork, p->status, st));
-    launch_slice_rows_f64(Y, n, m, m, p->ysl5, st);
-    launch_slice_rows_f64(Y, n, m, m, p->ysl4, st);
+    launch_slice_rows_f64(Y, n, m, m, p->ysla, st);
+    launch_slice_rows_f64(Y, n, m, m, p->yslb, st);
     OzParams b;
-    std::memset(&b, 0, sizeof(b));
-    b.M = n;
-    b.N = n;
-    b.Kp = p->ysl5.Kp;
-    b.sa = p->ysl5.scale;
-    b.sb = p->ysl4.scale;
+    DME_TRY(oz_params(p->ysla, p->yslb, p->cfg, &b));
     b.mode = OZ_OUT_F64;
     b.tri = 1;
     b.ldc = n;
@@ -309,7 +338,7 @@ dme_status split_riccati(dme_plan_t p, double* P, double tau, double qcoef) {
         b.b2 = qcoef;
     }
     b.status = p->status;
-    return launch_ozaki_gemm(p->ysl5.tmap, p->ysl4.tmap, b, st);
+    return launch_ozaki_gemm(p->ysla.tmap, p->yslb.tmap, b, st);
 }
 
 dme_status compute_ew(dme_plan_t p, double tau, int* idx) {
@@ -349,27 +378,54 @@ dme_status compute_ew(dme_plan_t p, double tau, int* idx) {
     DME_TRY(tp.get(&V12, nn));
     double* gjw = nullptr;
     DME_TRY(tp.get(&gjw, gj_work_doubles()));
+    // split plans of n >= kAccMinN: the Pade products on the tensor cores (accurate mode)
+    AccWork accw;
+    AccWork* aw = nullptr;
+    if (p->split && n >= kAccMinN) {
+        double *ad, *bd, *sc;
+        const size_t sl = (slice_buf_bytes(n, n, OZ_SLICES_ACC) + 7) / 8;
+        DME_TRY(tp.get(&ad, sl));
+        DME_TRY(tp.get(&bd, sl));
+        DME_TRY(tp.get(&sc, (size_t)n));
+        DME_TRY(tp.get(&accw.t, nn));
+        DME_TRY(tp.get(&accw.wsd, oz_acc_ws_doubles(n, n, n)));
+        for (SliceBuf* b : {&accw.a, &accw.b}) {
+            b->rows = n;
+            b->k = n;
+            b->Kp = slice_kpad(n);
+            b->ns = OZ_SLICES_ACC;
+            b->scheme = OZ_DIG7;
+        }
+        accw.a.data = reinterpret_cast<__nv_bfloat16*>(ad);
+        accw.b.data = reinterpret_cast<__nv_bfloat16*>(bd);
+        accw.a.scale = reinterpret_cast<float*>(sc);
+        accw.b.scale = reinterpret_cast<float*>(sc) + n;
+        DME_TRY(make_slice_tmap(accw.a, &accw.a.tmap));
+        DME_TRY(make_slice_tmap(accw.b, &accw.b.tmap));
+        accw.status = p->status;
+        aw = &accw;
+    }
 
     // X = sc M:  X22 = sc A, X12 = sc Q, X11 = -X22^T (implicit)
     launch_lincomb(X22, n, n, p->A, sc, nullptr, 0, nullptr, 0, 0.0, st);
     launch_lincomb(X12, n, n, p->Q, sc, nullptr, 0, nullptr, 0, 0.0, st);
     // X2 = X X (odd * odd -> even), X4 = X2 X2, X6 = X4 X2
-    DME_TRY(bprod(n, X22, X12, -1.0, X22, X12, A22, A12, st));
-    DME_TRY(bprod(n, A22, A12, 1.0, A22, A12, B22, B12, st));
-    DME_TRY(bprod(n, B22, B12, 1.0, A22, A12, C22, C12, st));
+    DME_TRY(bprod(n, aw, X22, X12, -1.0, X22, X12, A22, A12, st));
+    DME_TRY(bprod(n, aw, A22, A12, 1.0, A22, A12, B22, B12, st));
+    DME_TRY(bprod(n, aw, B22, B12, 1.0, A22, A12, C22, C12, st));
     // odd part: U = X (X6 (c13 X6 + c11 X4 + c9 X2) + c7 X6 + c5 X4 + c3 X2 + c1 I)
     launch_lincomb(Y22, n, n, C22, c[13], B22, c[11], A22, c[9], 0.0, st);
     launch_lincomb(Y12, n, n, C12, c[13], B12, c[11], A12, c[9], 0.0, st);
-    DME_TRY(bprod(n, C22, C12, 1.0, Y22, Y12, T22, T12, st));
+    DME_TRY(bprod(n, aw, C22, C12, 1.0, Y22, Y12, T22, T12, st));
     launch_lincomb(U22, n, n, C22, c[7], B22, c[5], A22, c[3], c[1], st);
     launch_lincomb(U12, n, n, C12, c[7], B12, c[5], A12, c[3], 0.0, st);
     launch_lincomb(T22, n, n, T22, 1.0, U22, 1.0, nullptr, 0, 0.0, st);
     launch_lincomb(T12, n, n, T12, 1.0, U12, 1.0, nullptr, 0, 0.0, st);
-    DME_TRY(bprod(n, X22, X12, -1.0, T22, T12, U22, U12, st));
+    DME_TRY(bprod(n, aw, X22, X12, -1.0, T22, T12, U22, U12, st));
     // even part: V = X6 (c12 X6 + c10 X4 + c8 X2) + c6 X6 + c4 X4 + c2 X2 + c0 I
     launch_lincomb(Y22, n, n, C22, c[12], B22, c[10], A22, c[8], 0.0, st);
     launch_lincomb(Y12, n, n, C12, c[12], B12, c[10], A12, c[8], 0.0, st);
-    DME_TRY(bprod(n, C22, C12, 1.0, Y22, Y12, V22, V12, st));
+    DME_TRY(bprod(n, aw, C22, C12, 1.0, Y22, Y12, V22, V12, st));
     launch_lincomb(T22, n, n, C22, c[6], B22, c[4], A22, c[2], c[0], st);
     launch_lincomb(T12, n, n, C12, c[6], B12, c[4], A12, c[2], 0.0, st);
     launch_lincomb(V22, n, n, V22, 1.0, T22, 1.0, nullptr, 0, 0.0, st);
@@ -391,7 +447,7 @@ dme_status compute_ew(dme_plan_t p, double tau, int* idx) {
     DME_TRY(launch_gj_solve(LUq, n, n, R22, n, n, gjw, p->status, st));
     // R12 = p22^{-T} (p12 - q12 R22)
     R12 = C12;
-    DME_TRY(gemm1(gp(n, n, n, q12, n, 0, R22, n, 0, R12, n, -1.0, 0, p12, 1.0), st));
+    DME_TRY(prod(n, aw, q12, 0, R22, 0, R12, -1.0, p12, 1.0, st));
     LUp = C22;
     launch_transpose(p22, LUp, n, n, n, n, st);
     DME_TRY(launch_gj_solve(LUp, n, n, R12, n, n, gjw, p->status, st));
@@ -401,7 +457,7 @@ dme_status compute_ew(dme_plan_t p, double tau, int* idx) {
     double* tmp = T22;
     double* E2 = T12;
     launch_lincomb(E, n, n, R22, 1.0, nullptr, 0, nullptr, 0, 0.0, st);
-    DME_TRY(gemm1(gp(n, n, n, R22, n, 1, R12, n, 0, Wm, n, 1.0), st));
+    DME_TRY(prod(n, aw, R22, 1, R12, 0, Wm, 1.0, nullptr, 0.0, st));
     launch_symmetrize(Wm, n, n, st);
     for (int i = 0; i < s; ++i) {
         DME_TRY(gemm1(gp(n, n, n, Wm, n, 0, E, n, 0, tmp, n, 1.0), st));             // tmp = W E
@@ -418,13 +474,152 @@ dme_status compute_ew(dme_plan_t p, double tau, int* idx) {
     DME_CUDA_TRY(cudaMemcpyAsync(ent.W, Wm, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
     if (p->split) {
         launch_transpose(ent.E, tmp, n, n, n, n, st);          // tmp = E^T
-        DME_TRY(alloc_slices(p, &ent.Gsl, n, n, OZ_SLICES_A));
+        DME_TRY(alloc_slices(p, &ent.Gsl, n, n, OZ_SLICES_FIXED));
         launch_slice_rows_f64(tmp, n, n, n, ent.Gsl, st);
     }
     DME_CUDA_TRY(cudaGetLastError());
     DME_TRY(check_status(p, "dme_expm"));
     p->ew.push_back(ent);
     *idx = (int)p->ew.size() - 1;
+    return DME_OK;
+}
+
+// Sums of (a - b)^2 and b^2 over len entries: per-block partials (fixed order),
+// then one block adds them in order, so the result does not depend on timing.
+__global__ void __launch_bounds__(256) diff_norms_partial_kernel(const double* __restrict__ a,
+                                                                 const double* __restrict__ b, size_t len,
+                                                                 double* __restrict__ part) {
+    __shared__ double sd[256], sr[256];
+    double d = 0.0, r = 0.0;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += (size_t)gridDim.x * blockDim.x) {
+        const double x = a[e] - b[e];
+        d += x * x;
+        r += b[e] * b[e];
+    }
+    sd[threadIdx.x] = d;
+    sr[threadIdx.x] = r;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sd[threadIdx.x] += sd[threadIdx.x + w];
+            sr[threadIdx.x] += sr[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = sd[0];
+        part[2 * blockIdx.x + 1] = sr[0];
+    }
+}
+
+__global__ void diff_norms_final_kernel(const double* __restrict__ part, int nb, double* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double d = 0.0, r = 0.0;
+    for (int k = 0; k < nb; ++k) {
+        d += part[2 * k];
+        r += part[2 * k + 1];
+    }
+    out[0] = d;
+    out[1] = r;
+}
+
+// ||a - b||_F / ||b||_F of two n x n device matrices (synchronises st).
+dme_status rel_diff(const double* a, const double* b, size_t len, double* work, cudaStream_t st, double* out) {
+    constexpr int nb = 256;
+    diff_norms_partial_kernel<<<nb, 256, 0, st>>>(a, b, len, work);
+    diff_norms_final_kernel<<<1, 32, 0, st>>>(work, nb, work + 2 * nb);
+    double h[2] = {0.0, 0.0};
+    DME_CUDA_TRY(cudaMemcpyAsync(h, work + 2 * nb, sizeof(h), cudaMemcpyDeviceToHost, st));
+    DME_CUDA_TRY(cudaStreamSynchronize(st));
+    *out = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
+    return DME_OK;
+}
+
+int cfg_of_pairs(int pairs) { return pairs == 10 ? OZ_P10 : (pairs == 13 ? OZ_P13 : OZ_P14); }
+
+// The split path's slice-pair configuration (dme_plan with pairs = 0): for
+// every fixed operand G the plan's steps use (E_t^T per step length, S), one
+// congruence G X G^T of the probe X = W_t (Q if W_t = 0, I if both are) under
+// P10, P13 and P14 against the FP64 congruence; keep the cheapest whose worst
+// error e satisfies 4 N e <= tol, N = congruences per step x horizon.
+dme_status choose_pairs(dme_plan_t p) {
+    if (!p->split) return DME_OK;
+    if (p->d.pairs != 0) {
+        p->cfg = cfg_of_pairs(p->d.pairs);
+        p->cfg_est = -1.0;
+        return DME_OK;
+    }
+    const int n = p->n;
+    const size_t nn = (size_t)n * n;
+    cudaStream_t st = p->st;
+    long apps = 0;
+    for (const Op& o : p->ops) {
+        if (o.kind == OP_CONG) apps += 1;
+        if (o.kind == OP_SFLOW) apps += (o.rule == DME_T4_EULER) ? 1 : 2;
+    }
+    const int cands[3] = {OZ_P10, OZ_P13, OZ_P14};
+    p->cfg = OZ_P14;
+    if (apps == 0) {                      // no tensor-core congruence in a step
+        p->cfg_est = 0.0;
+        return DME_OK;
+    }
+    TmpPool tp(st);
+    double *X, *ref, *out, *tmp, *work;
+    DME_TRY(tp.get(&X, nn));
+    DME_TRY(tp.get(&ref, nn));
+    DME_TRY(tp.get(&out, nn));
+    DME_TRY(tp.get(&tmp, nn));
+    DME_TRY(tp.get(&work, 2 * 256 + 2));
+    double worst[3] = {0.0, 0.0, 0.0};
+    auto probe = [&](const SliceBuf& G, const double* E, const double* Sm, const double* Xs) -> dme_status {
+        // FP64 reference: E^T X E (G = E^T) or S X S^T
+        if (E) {
+            DME_TRY(gemm1(gp(n, n, n, Xs, n, 0, E, n, 0, tmp, n, 1.0), st));
+            DME_TRY(gemm1(gp(n, n, n, E, n, 1, tmp, n, 0, ref, n, 1.0, 1), st));
+        } else {
+            DME_TRY(gemm1(gp(n, n, n, Xs, n, 0, Sm, n, 1, tmp, n, 1.0), st));
+            DME_TRY(gemm1(gp(n, n, n, Sm, n, 0, tmp, n, 0, ref, n, 1.0, 1), st));
+        }
+        for (int c = 0; c < 3; ++c) {
+            DME_TRY(split_cong(p, Xs, G, out, 1.0, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0, cands[c]));
+            double e = 0.0;
+            DME_TRY(rel_diff(out, ref, nn, work, st, &e));
+            worst[c] = std::max(worst[c], e);
+        }
+        return DME_OK;
+    };
+    // probe state: W_t of the first step length, else Q, else I (rel_diff against a
+    // zero matrix returns the Frobenius norm)
+    const double* probe_src = p->ew.empty() ? nullptr : p->ew.front().W;
+    double nrm = 0.0;
+    DME_CUDA_TRY(cudaMemsetAsync(tmp, 0, nn * sizeof(double), st));
+    if (probe_src) DME_TRY(rel_diff(probe_src, tmp, nn, work, st, &nrm));
+    if (!(nrm > 0.0)) {
+        probe_src = p->Q;
+        DME_TRY(rel_diff(p->Q, tmp, nn, work, st, &nrm));
+    }
+    if (nrm > 0.0) {
+        DME_CUDA_TRY(cudaMemcpyAsync(X, probe_src, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+        launch_lincomb(X, n, n, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0, 1.0, st);
+    }
+    for (const EWEntry& e : p->ew) DME_TRY(probe(e.Gsl, e.E, nullptr, X));
+    bool sflow = false;
+    for (const Op& o : p->ops) sflow = sflow || o.kind == OP_SFLOW;
+    if (sflow && p->S) DME_TRY(probe(p->Ssl, nullptr, p->S, X));
+    DME_TRY(check_status(p, "dme_plan (slice-pair probe)"));
+    const double horizon = p->d.horizon > 0 ? p->d.horizon : 1024.0;
+    const double tol = p->d.tol > 0.0 ? p->d.tol : 1e-7;
+    const double N = (double)apps * horizon;
+    for (int c = 0; c < 3; ++c) p->cfg_err[c] = worst[c];
+    p->cfg_est = 4.0 * N * worst[2];
+    for (int c = 0; c < 3; ++c) {
+        if (4.0 * N * worst[c] <= tol) {
+            p->cfg = cands[c];
+            p->cfg_est = 4.0 * N * worst[c];
+            break;
+        }
+    }
     return DME_OK;
 }
 
@@ -608,9 +803,9 @@ dme_status run_sflow(dme_plan_t p, double* P, double tau, int rule, double qcoef
 
 dme_status run_sflow_split(dme_plan_t p, double* P, double tau, int rule, double qcoef) {
     const double* Qd = qcoef != 0.0 ? p->Q : nullptr;
-    if (rule == DME_T4_EULER) return split_cong(p, P, p->Ssl, P, tau, P, 1.0, Qd, qcoef, nullptr, 0.0);
-    DME_TRY(split_cong(p, P, p->Ssl, p->Xs, 1.0, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0));   // Xs = S P S^T
-    return split_cong(p, p->Xs, p->Ssl, P, 0.5 * tau * tau, P, 1.0, p->Xs, tau, Qd, qcoef);     // + t^2/2 S Xs S^T
+    if (rule == DME_T4_EULER) return split_cong(p, P, p->Ssl, P, tau, P, 1.0, Qd, qcoef, nullptr, 0.0, p->cfg);
+    DME_TRY(split_cong(p, P, p->Ssl, p->Xs, 1.0, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0, p->cfg));  // S P S^T
+    return split_cong(p, p->Xs, p->Ssl, P, 0.5 * tau * tau, P, 1.0, p->Xs, tau, Qd, qcoef, p->cfg);  // + t^2/2 S Xs S^T
 }
 
 }  // namespace
@@ -631,7 +826,7 @@ dme_status dme::run_op(dme_plan_t p, const Op& o, double* Pcaller) {
     if (p->split && o.kind == OP_CONG) {
         const EWEntry& e = p->ew[o.ew];
         return split_cong(p, P, e.Gsl, P, 1.0, o.wcoef != 0.0 ? e.W : nullptr, o.wcoef,
-                          o.qcoef != 0.0 ? p->Q : nullptr, o.qcoef, nullptr, 0.0);
+                          o.qcoef != 0.0 ? p->Q : nullptr, o.qcoef, nullptr, 0.0, p->cfg);
     }
     if (p->split && o.kind == OP_SFLOW) return run_sflow_split(p, P, o.tau, o.rule, o.qcoef);
     switch (o.kind) {
@@ -744,8 +939,12 @@ dme_status dme::plan_create(const dme_plan_desc* d, const double* A, const doubl
         set_error("DME_SPLIT_BF16 supports n <= 4096 (exact slice accumulation over K <= 4096)");
         return DME_EINVAL;
     }
-    if (d->prec == DME_SPLIT_BF16 && d->slices != 0 && d->slices != OZ_SLICES_B) {
-        set_error("DME_SPLIT_BF16 uses 5 slices for E^T and S and 4 for P (slices = 0 or 4)");
+    if (d->prec == DME_SPLIT_BF16 && d->pairs != 0 && d->pairs != 10 && d->pairs != 13 && d->pairs != 14) {
+        set_error("DME_SPLIT_BF16: pairs must be 0 (chosen at plan time), 10, 13 or 14");
+        return DME_EINVAL;
+    }
+    if (d->horizon < 0 || !(d->tol >= 0.0) || !std::isfinite(d->tol)) {
+        set_error("horizon must be >= 0 and tol finite and >= 0");
         return DME_EINVAL;
     }
     dme_plan_t p = new (std::nothrow) dme_plan_s();
@@ -805,8 +1004,8 @@ dme_status dme::plan_create(const dme_plan_desc* d, const double* A, const doubl
         DME_CUDA_TRY(cudaMemcpyAsync(p->S, S, nn * sizeof(double), cudaMemcpyDefault, st));
     }
     if (p->split) {
-        DME_TRY(alloc_slices(p, &p->psl, n, n, OZ_SLICES_B));
-        DME_TRY(alloc_slices(p, &p->usl, n, n, OZ_SLICES_B));
+        DME_TRY(alloc_slices(p, &p->psl, n, n, OZ_SLICES_STEP));
+        DME_TRY(alloc_slices(p, &p->usl, n, n, OZ_SLICES_STEP));
         DME_TRY(palloc_t(p, &p->U, nn));
         if (n > 1536) {    // only then does a GEMM have a full wave of tiles (split K of the tail)
             DME_TRY(palloc_t(p, &p->kws, OZ_SPLIT_WS_FLOAT2));
@@ -818,15 +1017,15 @@ dme_status dme::plan_create(const dme_plan_desc* d, const double* A, const doubl
                 const int m = p->m;
                 p->tric = true;
                 DME_TRY(palloc_t(p, &p->Zt, (size_t)m * n));
-                DME_TRY(alloc_slices(p, &p->btsl, m, n, OZ_SLICES_A));
-                DME_TRY(alloc_slices(p, &p->ysl5, n, m, OZ_SLICES_A));
-                DME_TRY(alloc_slices(p, &p->ysl4, n, m, OZ_SLICES_B));
+                DME_TRY(alloc_slices(p, &p->btsl, m, n, OZ_SLICES_FIXED));
+                DME_TRY(alloc_slices(p, &p->ysla, n, m, OZ_SLICES_FIXED));
+                DME_TRY(alloc_slices(p, &p->yslb, n, m, OZ_SLICES_STEP));
                 launch_transpose(p->Bt, p->Zt, n, m, m, n, st);
                 launch_slice_rows_f64(p->Zt, m, n, n, p->btsl, st);
             }
         }
         if (gen) {
-            DME_TRY(alloc_slices(p, &p->Ssl, n, n, OZ_SLICES_A));
+            DME_TRY(alloc_slices(p, &p->Ssl, n, n, OZ_SLICES_FIXED));
             launch_slice_rows_f64(p->S, n, n, n, p->Ssl, st);
         }
     }
@@ -837,6 +1036,7 @@ dme_status dme::plan_create(const dme_plan_desc* d, const double* A, const doubl
     DME_CUDA_TRY(cudaStreamSynchronize(st));
     DME_TRY(build_ops(p, d->h));
     DME_TRY(check_status(p, "dme_plan"));
+    DME_TRY(choose_pairs(p));
     *out = guard.release();
     return DME_OK;
 }
@@ -1180,7 +1380,8 @@ dme_status dme_plan_destroy(dme_plan_t plan) {
 
 const char* dme_last_error(void) { return get_error(); }
 
-dme_status dme_gemm_split(int M, int N, int K, const double* A, const double* B, double* C, void* cuda_stream) {
+static dme_status gemm_split_impl(int M, int N, int K, const double* A, const double* B, double* C,
+                                  void* cuda_stream, bool acc) {
     if (M < 0 || N < 0 || K < 1 || K > OZ_MAX_K || !A || !B || !C)
         return set_error("dme_gemm_split: need 1 <= K <= 4096 and non-null A, B, C"), DME_EINVAL;
     if (M == 0 || N == 0) return DME_OK;
@@ -1205,11 +1406,13 @@ dme_status dme_gemm_split(int M, int N, int K, const double* A, const double* B,
         sa.rows = M;
         sa.k = K;
         sa.Kp = Kp;
-        sa.ns = OZ_SLICES_A;
+        sa.ns = acc ? OZ_SLICES_ACC : OZ_SLICES_FIXED;
+        sa.scheme = acc ? OZ_DIG7 : OZ_DIG9;
         sb.rows = N;
         sb.k = K;
         sb.Kp = Kp;
-        sb.ns = OZ_SLICES_B;
+        sb.ns = acc ? OZ_SLICES_ACC : OZ_SLICES_STEP;
+        sb.scheme = sa.scheme;
         int* status = nullptr;
         dme_status s = DME_OK;
         if ((s = get(slice_buf_bytes(M, K, sa.ns), reinterpret_cast<void**>(&sa.data))) != DME_OK ||
@@ -1221,22 +1424,22 @@ dme_status dme_gemm_split(int M, int N, int K, const double* A, const double* B,
             cleanup();
             return s;
         }
+        double* wsd = nullptr;
+        if (acc && (s = get(sizeof(double) * oz_acc_ws_doubles(M, N, K), reinterpret_cast<void**>(&wsd))) != DME_OK) {
+            cleanup();
+            return s;
+        }
         cudaMemsetAsync(status, 0, sizeof(int), st);
         launch_slice_rows_f64(A, M, K, K, sa, st);
         launch_slice_rows_f64(B, N, K, K, sb, st);
         OzParams o;
-        std::memset(&o, 0, sizeof(o));
-        o.M = M;
-        o.N = N;
-        o.Kp = Kp;
-        o.sa = sa.scale;
-        o.sb = sb.scale;
+        s = oz_params(sa, sb, acc ? OZ_A21 : OZ_P14, &o);
         o.mode = OZ_OUT_F64;
         o.ldc = N;
         o.Cd = C;
-        o.alpha = 1.0;
         o.status = status;
-        s = launch_ozaki_gemm(sa.tmap, sb.tmap, o, st);
+        o.wsd = wsd;
+        if (s == DME_OK) s = launch_ozaki_gemm(sa.tmap, sb.tmap, o, st);
         int hs = 0;
         if (s == DME_OK) {
             cudaError_t e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -1252,6 +1455,21 @@ dme_status dme_gemm_split(int M, int N, int K, const double* A, const double* B,
         cleanup();
         return s;
     });
+}
+
+dme_status dme_gemm_split(int M, int N, int K, const double* A, const double* B, double* C, void* cuda_stream) {
+    return gemm_split_impl(M, N, K, A, B, C, cuda_stream, false);
+}
+
+dme_status dme_gemm_split_acc(int M, int N, int K, const double* A, const double* B, double* C, void* cuda_stream) {
+    return gemm_split_impl(M, N, K, A, B, C, cuda_stream, true);
+}
+
+dme_status dme_plan_split_choice(dme_plan_t plan, int* pairs, double* est) {
+    if (!plan) return set_error("plan is NULL"), DME_EINVAL;
+    if (pairs) *pairs = plan->split ? oz_cfg_pairs(plan->cfg) : 0;
+    if (est) *est = plan->split ? plan->cfg_est : 0.0;
+    return DME_OK;
 }
 
 }  // extern "C"

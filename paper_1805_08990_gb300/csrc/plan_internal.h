@@ -71,6 +71,9 @@ struct dme_plan_s {
     size_t bytes = 0;
     GraphSlot g_step, g_head, g_body, g_tail;
     bool split = false;
+    int cfg = 2;               // split path: slice-pair configuration (dme::OzCfgId, OZ_P14 by default)
+    double cfg_est = -1.0;     // split path: the estimate that chose cfg (< 0: given explicitly)
+    double cfg_err[3] = {-1.0, -1.0, -1.0};   // measured one-application errors of P10, P13, P14
     SliceBuf psl, usl, Ssl;    // split path: slices of P, of U = G P, and of S
     float2* U = nullptr;       // split path: G P as normalised (hi, lo) pairs
     float2* kws = nullptr;     // split path: split-K workspace of the tail tiles
@@ -78,7 +81,7 @@ struct dme_plan_s {
     // split path with n > 1536 and T3: the Riccati products on the tensor cores
     bool tric = false;
     SliceBuf btsl;             // slices of Bt^T (m rows, 5 slices)
-    SliceBuf ysl5, ysl4;       // slices of Y (n rows, k = m)
+    SliceBuf ysla, yslb;       // slices of Y (n rows, k = m) as A (5) and B (4) operand
     double* Zt = nullptr;      // Z^T = Bt^T P (m x n)
     // profiling: CUDA-event pairs around launches made outside graph capture
     bool prof = false;

@@ -350,7 +350,6 @@ dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
         if (!L.sc.empty()) {
             // the split congruence G P G^T of every request: slice P, grouped U = G P,
             // slice U, grouped G U^T (upper tiles, FP64 + W / tQ, mirrored)
-            std::vector<OzGroupDesc> o1, o2;
             std::vector<SliceDesc> s1, s2;
             for (Req* r : L.sc) {
                 dme_plan_t p = r->plan;
@@ -378,6 +377,8 @@ dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
                 s2.push_back(b);
             }
             DME_TRY(launch_slice_grouped(s1, false, s->st, &s->arena));
+            // one grouped launch per slice-pair configuration present (each plan chose its own)
+            std::vector<OzGroupDesc> o1c[OZ_NCFG], o2c[OZ_NCFG];
             for (Req* r : L.sc) {
                 dme_plan_t p = r->plan;
                 const Op& o = p->ops[k];
@@ -387,23 +388,17 @@ dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
                 std::memset(&a, 0, sizeof(a));
                 a.tmA = e.Gsl.tmap;
                 a.tmB = p->psl.tmap;
-                a.p.M = a.p.N = n;
-                a.p.Kp = e.Gsl.Kp;
-                a.p.sa = e.Gsl.scale;
-                a.p.sb = p->psl.scale;
+                DME_TRY(oz_params(e.Gsl, p->psl, p->cfg, &a.p));
                 a.p.mode = OZ_OUT_PAIR;
                 a.p.ldc = n;
                 a.p.Cp = p->U;
                 a.p.status = s->dstat + r->slot;
-                o1.push_back(a);
+                o1c[p->cfg].push_back(a);
                 OzGroupDesc b;
                 std::memset(&b, 0, sizeof(b));
                 b.tmA = e.Gsl.tmap;
                 b.tmB = p->usl.tmap;
-                b.p.M = b.p.N = n;
-                b.p.Kp = e.Gsl.Kp;
-                b.p.sa = e.Gsl.scale;
-                b.p.sb = p->usl.scale;
+                DME_TRY(oz_params(e.Gsl, p->usl, p->cfg, &b.p));
                 b.p.mode = OZ_OUT_F64;
                 b.p.tri = 1;
                 b.p.ldc = n;
@@ -418,11 +413,14 @@ dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
                     b.p.b2 = o.qcoef;
                 }
                 b.p.status = s->dstat + r->slot;
-                o2.push_back(b);
+                o2c[p->cfg].push_back(b);
+                (void)n;
             }
-            DME_TRY(launch_ozaki_grouped(o1, nullptr, s->st, &s->arena));
+            for (auto& g : o1c)
+                if (!g.empty()) DME_TRY(launch_ozaki_grouped(g, nullptr, s->st, &s->arena));
             DME_TRY(launch_slice_grouped(s2, true, s->st, &s->arena));
-            DME_TRY(launch_ozaki_grouped(o2, nullptr, s->st, &s->arena));
+            for (auto& g : o2c)
+                if (!g.empty()) DME_TRY(launch_ozaki_grouped(g, nullptr, s->st, &s->arena));
         }
         if (!L.ric.empty()) DME_TRY(launch_riccati_grouped(L.ric, nullptr, s->st, &s->arena));
     }
@@ -656,6 +654,7 @@ dme_status submit_impl(dme_server_t s, const dme_plan_desc* desc, const double* 
         auto r = std::make_unique<Req>();
         r->desc = *desc;
         r->desc.h = T / nsteps;
+        if (r->desc.horizon == 0) r->desc.horizon = nsteps;     // the split error target holds over the solve
         const int n = desc->n;
         if (n < 1 || n > 16384) return set_error("n must be in [1, 16384]"), DME_EINVAL;
         const size_t nn = (size_t)n * n;

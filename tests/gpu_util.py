@@ -37,10 +37,11 @@ def rel(x, y):
     return float(d / r) if r > 0 else float(d)
 
 
-def plan_for(pr, flows, comp, h, prec="fp64", t4_rule=dme.DME_T4_AUTO, slices=0, fsal=False, extrap=0):
+def plan_for(pr, flows, comp, h, prec="fp64", t4_rule=dme.DME_T4_AUTO, pairs=0, fsal=False, extrap=0, horizon=0):
     """A dme plan for a dme_workloads.Problem with Q = C^T C."""
     return dme.Plan(dev(pr.A), C=dev(pr.C), h=h, flows=flows, comp=comp,
                     B=None if pr.B is None or "F3" not in flows else dev(pr.B),
                     R=None if pr.R is None or "F3" not in flows else dev(pr.R),
                     S=None if pr.S is None or "F4" not in flows else dev(pr.S),
-                    prec=prec, t4_rule=t4_rule, slices=slices, fsal=fsal, extrap=extrap)
+                    prec=prec, t4_rule=t4_rule, pairs=pairs, fsal=fsal, extrap=extrap,
+                    horizon=horizon)

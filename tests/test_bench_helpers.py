@@ -14,7 +14,7 @@ def test_serving_work_counts_each_request():
     specs = [{"n": 10, "m": 2, "steps": 3}, {"n": 100, "m": 8, "steps": 50}]
     f64, tens = bench.serving_work(specs)
     assert f64 == 3 * (6 * 10 ** 3 + 3 * 10 ** 2 * 2) + 50 * (6 * 100 ** 3 + 3 * 100 ** 2 * 8)
-    assert tens == 3 * 112 * 10 ** 3 + 50 * 112 * 100 ** 3
+    assert tens == 3 * 36 * 10 ** 3 + 50 * 36 * 100 ** 3
 
 
 def test_serving_roofline_fractions():

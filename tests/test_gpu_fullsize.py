@@ -90,12 +90,14 @@ def test_large_dre_whole_horizon_split_vs_fp64():
     N = 256
     out = {}
     for prec in ("fp64", "split_bf16"):
-        plan = plan_for(pr, ["F12", "F3"], "strang", pr.T / N, prec=prec)
+        plan = plan_for(pr, ["F12", "F3"], "strang", pr.T / N, prec=prec, horizon=N)
         P = torch.zeros(pr.n, pr.n, dtype=torch.float64, device="cuda")
         plan.step(P, N)
         out[prec] = P
         if prec == "split_bf16":
-            plan2 = plan_for(pr, ["F12", "F3"], "strang", pr.T / (2 * N), prec=prec)
+            pairs, est = plan.split_choice
+            assert pairs in (10, 13, 14) and (pairs == 14 or est <= SPLIT_TOL)
+            plan2 = plan_for(pr, ["F12", "F3"], "strang", pr.T / (2 * N), prec=prec, horizon=2 * N)
             P2 = torch.zeros_like(P)
             plan2.step(P2, 2 * N)
             res_fine = _are_residual(P2, pr)

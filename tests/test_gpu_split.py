@@ -164,3 +164,122 @@ def test_split_k_tail_tiles_match_oracle_and_repeat():
     assert torch.equal(P1, P2)
     E, Wm = O.van_loan(pr.A, pr.Q, tau)
     assert rel(host(P1), O.flow_T12(P0, E, Wm)) < SPLIT_TOL
+
+
+# ---------------------------------------------------------------- accurate mode (Pade products)
+def gemm_split_acc(A, B):
+    C = torch.empty(A.shape[0], B.shape[0], dtype=torch.float64, device="cuda")
+    dme.dme_gemm_split_acc(dev(A), dev(B), C)
+    torch.cuda.synchronize()
+    return host(C)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 32), (130, 260, 700), (256, 128, 4096), (1, 3, 1)])
+def test_accurate_products_of_small_integers_are_exact(M, N, K):
+    """Integers in [-63, 63] are one 7-bit digit: every chunk of 512 sums them
+    exactly and the chunks add exactly in fp64, so C = A B^T bit for bit
+    (K = 700 and 4096 cross chunk boundaries; K = 4096 is eight chunks)."""
+    rng = np.random.default_rng(M + 5 * N + 11 * K)
+    A = rng.integers(-63, 64, size=(M, K)).astype(np.float64)
+    B = rng.integers(-63, 64, size=(N, K)).astype(np.float64)
+    A[:, 0] = 63.0
+    B[:, 0] = -63.0
+    assert np.array_equal(gemm_split_acc(A, B), A @ B.T)
+
+
+@pytest.mark.parametrize("M,N,K", [(200, 150, 333), (512, 512, 4096)])
+def test_accurate_products_reach_two_to_the_minus_39(M, N, K):
+    """Six 7-bit slices leave 2^-42 of each row scale; the dropped levels >= 6 and
+    the fp32 rounding of the shared level-3 accumulator stay near 2^-39 of the
+    row scales' product per term, so |C - AB^T| <= 8 * 2^-39 sA sB sqrt(K)."""
+    rng = np.random.default_rng(K + 1)
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((N, K))
+    ref = A @ B.T
+    C = gemm_split_acc(A, B)
+    sa = 2.0 ** np.ceil(np.log2(np.abs(A).max(1) * (1 + 2 ** -52)))
+    sb = 2.0 ** np.ceil(np.log2(np.abs(B).max(1) * (1 + 2 ** -52)))
+    bound = 8 * 2.0 ** -39 * sa[:, None] * sb[None, :] * math.sqrt(K)
+    assert np.all(np.abs(C - ref) <= bound)
+    assert rel(C, ref) < 1e-10
+
+
+# ---------------------------------------------------------------- slice-pair configurations
+@pytest.mark.parametrize("pairs", [10, 13, 14])
+@pytest.mark.parametrize("n", [37, 300])
+def test_every_pair_configuration_matches_oracle(n, pairs):
+    pr = _problem(n)
+    tau = 0.05
+    plan = plan_for(pr, ["F12", "F3", "F4"], "strang", tau, prec="split_bf16", pairs=pairs)
+    assert plan.split_choice[0] == pairs
+    P0 = W.random_psd(n, 5 + n)
+    ref = O.Plan(pr.A, pr.Q, pr.B, pr.R, pr.S)
+    for flow in ("F12", "F4"):
+        P = dev(P0)
+        plan.apply(flow, tau, P)
+        assert rel(host(P), ref.apply(flow, tau, P0, "midpoint")) < SPLIT_TOL
+        assert torch.equal(P, P.T)
+
+
+def test_more_pairs_are_more_accurate_on_one_congruence():
+    """The one-application error falls as pairs are added (dropped levels and the
+    fixed operand's fifth slice), each against the oracle's T12."""
+    n = 300
+    pr = _problem(n, seed=9)
+    tau = 0.05
+    P0 = W.random_psd(n, 77)
+    E, Wm = O.van_loan(pr.A, pr.Q, tau)
+    ref = O.flow_T12(P0, E, Wm)
+    errs = {}
+    for pairs in (10, 13, 14):
+        plan = plan_for(pr, ["F12"], "strang", tau, prec="split_bf16", pairs=pairs)
+        P = dev(P0)
+        plan.apply("F12", tau, P)
+        errs[pairs] = rel(host(P), ref)
+        plan.close()
+    assert errs[14] <= errs[13] * 1.5 and errs[13] < errs[10]
+    assert errs[10] < 1e-8
+
+
+def test_plan_choice_is_reported_and_within_its_target():
+    """pairs = 0: the plan keeps the cheapest configuration whose estimate
+    4 N e (N = congruences over the horizon) meets tol; the estimate is reported,
+    and the solve over that horizon meets tol against the oracle."""
+    pr = W.dre_convdiff()
+    N = 64
+    flows = W.SCHEMES["F12F3"]
+    plan = plan_for(pr, flows, "strang", pr.T / N, prec="split_bf16", horizon=N)
+    pairs, est = plan.split_choice
+    assert pairs in (10, 13, 14)
+    if pairs < 14:
+        assert 0 < est <= 1e-7
+    P = dev(pr.P0)
+    plan.step(P, N)
+    assert rel(host(P), _oracle_solve(pr, flows, "strang", N)) < SPLIT_TOL
+
+
+def test_explicit_pairs_are_validated():
+    A = torch.zeros(4, 4, dtype=torch.float64, device="cuda")
+    d = dme.make_desc(4, eq=dme.DME_DLE, flows=("F12",), h=0.1, prec="split_bf16", q_is_factor=False, pairs=11)
+    with pytest.raises(dme.DmeError):
+        dme.dme_plan(d, A, A)
+
+
+# ---------------------------------------------------------------- Pade chain on the tensor cores
+@pytest.mark.parametrize("n,tau", [(600, 0.01), (1024, 1.0 / 512)])
+def test_split_plan_exponential_from_tensor_pade_chain(n, tau):
+    """Split plans of n >= 512 form the Pade products of E_t and W_t in the
+    accurate tensor mode (denominator solves and squarings in FP64): E and W
+    stay within 1e-10 of the oracle's 2n x 2n exponential."""
+    if n == 1024:
+        pr = W.dre_convdiff()
+    else:
+        pr = _problem(n, seed=2)
+    plan = plan_for(pr, ["F12"], "strang", tau, prec="split_bf16")
+    E = torch.empty(n, n, dtype=torch.float64, device="cuda")
+    Wt = torch.empty_like(E)
+    plan.expm(tau, E, Wt)
+    Eo, Wo = O.van_loan(pr.A, pr.Q, tau)
+    assert rel(host(E), Eo) < 1e-10
+    assert rel(host(Wt), Wo) < 1e-10
+    assert torch.equal(Wt, Wt.T)
