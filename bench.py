@@ -442,6 +442,7 @@ def run_ours(args):
                             B=to_dev(pr.B), R=to_dev(pr.R), prec=kprec, stream=stream, horizon=FULL_STEPS)
         plan_s = time.perf_counter() - t0
         pairs, pair_est = plan.split_choice
+        probe = plan.split_probe if prec == "split" else None
         P = torch.zeros(n, n, dtype=torch.float64, device=dev)
         # the headline (split) arm times exactly K steps; the FP64 comparison arm (about 0.36 s
         # per step at n = 4096) at most FP64_MAX_STEPS of them, reported under its own key
@@ -519,7 +520,8 @@ def run_ours(args):
         results[prec] = {"ms": ms, "steps": steps, "kps": kps, "cong_ms": cong_ms, "plan_s": plan_s,
                          "e2e_s": e2e_s, "clocks": clk.summary(), "bytes": plan.nbytes,
                          "kernel_ms": k_ms, "kernel_launches": k_launch, "slice_ms": s_ms, "slice_launches": s_launch,
-                         "R": R, "per_step_ms": per_step, "full_ms": full_ms, "pairs": pairs, "pair_est": pair_est}
+                         "R": R, "per_step_ms": per_step, "full_ms": full_ms, "pairs": pairs, "pair_est": pair_est,
+                         "probe": probe}
         plan.close()
 
     r = results[head]
@@ -578,6 +580,11 @@ def run_ours(args):
     if "split" in results:
         acc["split_pairs"] = results["split"]["pairs"]
         acc["split_pair_estimate"] = results["split"]["pair_est"]
+        errs, rho = results["split"]["probe"]
+        acc["split_probe"] = {"one_congruence_err": {"10": errs[0], "13": errs[1], "14": errs[2]},
+                              "step_contraction": rho,
+                              "rule": "cheapest pairs with 4 e c (1 + rho + ... + rho^255) <= 1e-7, c = 2 "
+                                      "congruences per step"}
     acc["what"] = ("relative Frobenius distance of the split-precision state from the FP64 GPU state at T = 1 "
                    "(256 steps each from P0 = 0; the FP64 path is tied to the oracle at this size by the parity "
                    "tests), and ||A^T P + P A + Q - P B R^-1 B^T P||_F / ||Q||_F of each")
@@ -805,6 +812,36 @@ def run_lowrank_only(args):
     return 0
 
 
+def run_cong_only(args):
+    """Profile target: the split plan of the bench workload (n = 4096, its slice
+    products chosen for the 256-step horizon) applying the congruence
+    T12(h/2) (E^T P E + W: two tensor-kernel launches) --reps times to a PSD
+    state, inside the NVTX range "cong"."""
+    import torch
+    import paper_1805_08990_gb300 as dme
+    from paper_1805_08990_gb300 import build
+    build.build()
+    dev = torch.device("cuda")
+    pr = W.dre_heat_large()
+    h = pr.T / FULL_STEPS
+    t = lambda x: torch.as_tensor(x, dtype=torch.float64, device=dev)   # noqa: E731
+    plan = dme.Plan(t(pr.A), C=t(pr.C), h=h, flows=["F12", "F3"], comp="strang", B=t(pr.B), R=t(pr.R),
+                    prec="split_bf16", horizon=FULL_STEPS, pairs=args.pairs)
+    P = t(W.random_psd(pr.n, 3, rank=64))
+    plan.apply("F12", 0.5 * h, P)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("cong")
+    t0 = time.perf_counter()
+    for _ in range(args.reps):
+        plan.apply_async("F12", 0.5 * h, P)
+    plan.sync()
+    dt = (time.perf_counter() - t0) / args.reps
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"cong_only": pr.n, "pairs": plan.split_choice[0], "ms_per_congruence": dt * 1e3}))
+    plan.close()
+    return 0
+
+
 def run_gemm_only(args):
     """The split-precision tensor-core product alone: C = A B^T, A, B seeded
     N(0,1) of size N x N (inputs and their slices exceed L2 at N = 4096)."""
@@ -843,6 +880,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--gemm-only", type=int, default=0, help="profile target: split GEMM of this size alone")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--cong-only", action="store_true", help="profile target: the split congruence at n = 4096")
+    ap.add_argument("--pairs", type=int, default=0, help="--cong-only: slice products (0: the plan's choice)")
     ap.add_argument("--lowrank-only", default="", choices=["", "fp64", "split", "sparse"],
                     help="profile target: one low-rank configuration alone (--lowrank-steps timed steps)")
     ap.add_argument("--serving-requests", type=int, default=32, help="serving sample size (0: skip)")
@@ -865,6 +904,8 @@ def main():
         return run_lowrank_only(args)
     if args.gemm_only:
         return run_gemm_only(args)
+    if args.cong_only:
+        return run_cong_only(args)
     if args.serving_suite:
         return run_serving_suite(args)
     if args.config_suite:

@@ -178,6 +178,12 @@ dme_status dme_gain(dme_plan_t plan, const double* P, double* K_out);
  * pairs was given explicitly).  Either pointer may be NULL. */
 dme_status dme_plan_split_choice(dme_plan_t plan, int* pairs, double* est);
 
+/* What the choice of dme_plan_split_choice rests on (pairs = 0 and
+ * DME_SPLIT_BF16 only, else DME_EINVAL): err[0..2] the measured relative
+ * errors of one congruence with 10, 13 and 14 slice products, *rho the
+ * contraction of one step.  Either pointer may be NULL. */
+dme_status dme_plan_split_probe(dme_plan_t plan, double* err, double* rho);
+
 /* Bytes of device memory the plan holds. */
 size_t dme_plan_bytes(dme_plan_t plan);
 

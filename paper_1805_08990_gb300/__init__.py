@@ -11,7 +11,7 @@ from .binding import (  # noqa: F401
     DME_KIND_SPLIT_GEMM, DME_KIND_SLICE, DME_KIND_FP64_GEMM, DME_KIND_RICCATI, dme_plan_profile, dme_plan_timing,
     DME_OK, DME_EINVAL, DME_ENOMEM, DME_ENOTSPD, DME_ECUDA, DME_ETIMEOUT, DME_EBUSY, DME_ENOTREADY,
     DmeError, LibraryNotBuilt, dme_plan_desc, make_desc, lib, header_functions,
-    dme_plan, dme_plan_mass, dme_lr_plan, dme_lr_plan_csr, dme_lr_solve, dme_lr_factors, dme_lr_destroy, dme_expm, dme_apply, dme_apply_async, dme_sync, dme_plan_kernels_per_step, dme_step, dme_step_async, dme_solve, dme_plan_bytes, dme_plan_split_choice, dme_plan_destroy, dme_gain,
+    dme_plan, dme_plan_mass, dme_lr_plan, dme_lr_plan_csr, dme_lr_solve, dme_lr_factors, dme_lr_destroy, dme_expm, dme_apply, dme_apply_async, dme_sync, dme_plan_kernels_per_step, dme_step, dme_step_async, dme_solve, dme_plan_bytes, dme_plan_split_choice, dme_plan_split_probe, dme_plan_destroy, dme_gain,
     dme_server_create, dme_submit, dme_poll, dme_submit_gain, dme_poll_gain, dme_server_stats, dme_server_destroy,
     dme_last_error,
     dme_gemm_split, dme_gemm_split_acc, dme_gemm_split_noalloc, dme_dense_solve, dme_wait_selftest,
@@ -81,6 +81,11 @@ class Plan:
     def split_choice(self):
         """(slice products per output, estimate that chose them)."""
         return dme_plan_split_choice(self.handle)
+
+    @property
+    def split_probe(self):
+        """([one-congruence errors of 10, 13, 14 slice products], step contraction)."""
+        return dme_plan_split_probe(self.handle)
 
     @property
     def nbytes(self):

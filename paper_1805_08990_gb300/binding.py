@@ -83,6 +83,7 @@ _SIGS = {
     "dme_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_void_p]),
     "dme_plan_bytes": (C.c_size_t, [C.c_void_p]),
     "dme_plan_split_choice": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "dme_plan_split_probe": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "dme_gemm_split_acc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dme_gain": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dme_plan_destroy": (C.c_int, [C.c_void_p]),
@@ -322,6 +323,14 @@ def dme_plan_split_choice(plan: int):
     est = C.c_double(0.0)
     _check(lib().dme_plan_split_choice(plan, C.byref(pairs), C.byref(est)), "dme_plan_split_choice")
     return pairs.value, est.value
+
+
+def dme_plan_split_probe(plan: int):
+    """([err of 10, 13, 14 slice products for one congruence], step contraction rho)."""
+    err = (C.c_double * 3)()
+    rho = C.c_double(0.0)
+    _check(lib().dme_plan_split_probe(plan, err, C.byref(rho)), "dme_plan_split_probe")
+    return list(err), rho.value
 
 
 def dme_plan_bytes(plan: int) -> int:

@@ -537,11 +537,78 @@ dme_status rel_diff(const double* a, const double* b, size_t len, double* work, 
 
 int cfg_of_pairs(int pairs) { return pairs == 10 ? OZ_P10 : (pairs == 13 ? OZ_P13 : OZ_P14); }
 
+__global__ void fill_kernel(double* x, int n, double v) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = v;
+}
+
+// out[0] = x . z, out[1] = z . z (one block, fixed order).
+__global__ void __launch_bounds__(1024) dot2_kernel(const double* __restrict__ x, const double* __restrict__ z, int n,
+                                                    double* __restrict__ out) {
+    __shared__ double sa[1024], sb[1024];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        a += x[i] * z[i];
+        b += z[i] * z[i];
+    }
+    sa[threadIdx.x] = a;
+    sb[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sa[threadIdx.x] += sa[threadIdx.x + w];
+            sb[threadIdx.x] += sb[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sa[0];
+        out[1] = sb[0];
+    }
+}
+
+// x = z / ||z|| with ||z||^2 = nrm[1] (left unchanged if z = 0).
+__global__ void normalize_kernel(const double* __restrict__ z, int n, const double* __restrict__ nrm,
+                                 double* __restrict__ x) {
+    const double s = nrm[1] > 0.0 ? rsqrt(nrm[1]) : 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (s > 0.0) x[i] = z[i] * s;
+}
+
+// The largest eigenvalue of M^T M (M n x n), i.e. ||M||_2^2, by 48 steps of the
+// power iteration from the unit vector of equal entries, returned as the last
+// Rayleigh quotient: an estimate from below that converges to the eigenvalue.
+dme_status norm2_sq(const double* M, int n, double* work, cudaStream_t st, double* out) {
+    double* x = work;
+    double* y = x + n;
+    double* z = y + n;
+    double* s = z + n;
+    fill_kernel<<<(n + 255) / 256, 256, 0, st>>>(x, n, 1.0 / std::sqrt((double)n));
+    for (int it = 0; it < 48; ++it) {
+        DME_TRY(gemm1(gp(n, 1, n, M, n, 0, x, 1, 0, y, 1, 1.0), st));        // y = M x
+        DME_TRY(gemm1(gp(n, 1, n, M, n, 1, y, 1, 0, z, 1, 1.0), st));        // z = M^T y
+        dot2_kernel<<<1, 1024, 0, st>>>(x, z, n, s);                          // x.z = Rayleigh quotient
+        normalize_kernel<<<(n + 255) / 256, 256, 0, st>>>(z, n, s, x);
+    }
+    double h[2] = {0.0, 0.0};
+    DME_CUDA_TRY(cudaMemcpyAsync(h, s, sizeof(h), cudaMemcpyDeviceToHost, st));
+    DME_CUDA_TRY(cudaStreamSynchronize(st));
+    *out = h[0];
+    return DME_OK;
+}
+
 // The split path's slice-pair configuration (dme_plan with pairs = 0): for
 // every fixed operand G the plan's steps use (E_t^T per step length, S), one
 // congruence G X G^T of the probe X = W_t (Q if W_t = 0, I if both are) under
-// P10, P13 and P14 against the FP64 congruence; keep the cheapest whose worst
-// error e satisfies 4 N e <= tol, N = congruences per step x horizon.
+// P10, P13 and P14 against the FP64 congruence gives the worst relative error
+// e of one application.  An error made at some step reaches the end of the
+// horizon through the later steps, which shrink it at most by
+// rho = prod ||E_t||_2^2 over the step's congruences (times 1 + t ||S||^2 +
+// t^2 ||S||^4 / 2 per S-flow; T2 and T3 counted as 1, and rho = 1 for the
+// extrapolated schemes), so the estimate of the error over H steps is
+//     4 e c (1 + rho + ... + rho^(H-1)),   c = congruences per step
+// (the worst case of errors adding up in phase; the factor 4 covers the
+// probe standing in for the states of the solve).  The cheapest configuration
+// whose estimate is within tol is kept.
 dme_status choose_pairs(dme_plan_t p) {
     if (!p->split) return DME_OK;
     if (p->d.pairs != 0) {
@@ -608,9 +675,23 @@ dme_status choose_pairs(dme_plan_t p) {
     for (const Op& o : p->ops) sflow = sflow || o.kind == OP_SFLOW;
     if (sflow && p->S) DME_TRY(probe(p->Ssl, nullptr, p->S, X));
     DME_TRY(check_status(p, "dme_plan (slice-pair probe)"));
-    const double horizon = p->d.horizon > 0 ? p->d.horizon : 1024.0;
+    // contraction of one step: ||E_t||_2^2 per congruence, the S-flow's growth
+    std::vector<double> e2(p->ew.size(), 1.0);
+    for (size_t k = 0; k < p->ew.size(); ++k) DME_TRY(norm2_sq(p->ew[k].E, n, tmp, st, &e2[k]));
+    double s2 = 0.0;
+    if (sflow && p->S) DME_TRY(norm2_sq(p->S, n, tmp, st, &s2));
+    double rho = 1.0;
+    for (const Op& o : p->ops) {
+        if (o.kind == OP_CONG) rho *= e2[o.ew];
+        if (o.kind == OP_SFLOW)
+            rho *= 1.0 + std::fabs(o.tau) * s2 + (o.rule == DME_T4_EULER ? 0.0 : 0.5 * o.tau * o.tau * s2 * s2);
+    }
+    if (p->d.extrap > 1 || !(rho >= 0.0)) rho = 1.0;
+    const int H = p->d.horizon > 0 ? p->d.horizon : 1024;
     const double tol = p->d.tol > 0.0 ? p->d.tol : 1e-7;
-    const double N = (double)apps * horizon;
+    const double G = rho < 1.0 ? (1.0 - std::pow(rho, (double)H)) / (1.0 - rho) : (double)H;
+    const double N = (double)apps * G;
+    p->cfg_rho = rho;
     for (int c = 0; c < 3; ++c) p->cfg_err[c] = worst[c];
     p->cfg_est = 4.0 * N * worst[2];
     for (int c = 0; c < 3; ++c) {
@@ -1469,6 +1550,17 @@ dme_status dme_plan_split_choice(dme_plan_t plan, int* pairs, double* est) {
     if (!plan) return set_error("plan is NULL"), DME_EINVAL;
     if (pairs) *pairs = plan->split ? oz_cfg_pairs(plan->cfg) : 0;
     if (est) *est = plan->split ? plan->cfg_est : 0.0;
+    return DME_OK;
+}
+
+dme_status dme_plan_split_probe(dme_plan_t plan, double* err, double* rho) {
+    if (!plan) return set_error("plan is NULL"), DME_EINVAL;
+    if (!plan->split || plan->d.pairs != 0 || plan->cfg_est < 0.0)
+        return set_error("dme_plan_split_probe: the plan did not choose its slice products (pairs = 0, split)"),
+               DME_EINVAL;
+    if (err)
+        for (int c = 0; c < 3; ++c) err[c] = plan->cfg_err[c];
+    if (rho) *rho = plan->cfg_rho;
     return DME_OK;
 }
 

@@ -74,6 +74,7 @@ struct dme_plan_s {
     int cfg = 2;               // split path: slice-pair configuration (dme::OzCfgId, OZ_P14 by default)
     double cfg_est = -1.0;     // split path: the estimate that chose cfg (< 0: given explicitly)
     double cfg_err[3] = {-1.0, -1.0, -1.0};   // measured one-application errors of P10, P13, P14
+    double cfg_rho = 1.0;      // the step's contraction used by the estimate
     SliceBuf psl, usl, Ssl;    // split path: slices of P, of U = G P, and of S
     float2* U = nullptr;       // split path: G P as normalised (hi, lo) pairs
     float2* kws = nullptr;     // split path: split-K workspace of the tail tiles

@@ -151,8 +151,9 @@ def test_split_precision_requests_in_a_mix(server):
         ref = O.solve(pr.A, pr.Q, pr.P0, pr.T, N, "strang", ["F12", "F3"], B=pr.B, R=pr.R)
         assert rel(got, ref) < (SPLIT_TOL if pc == "split_bf16" else FP64_TOL)
         if pc == "split_bf16":
+            # the server gives a request the horizon of its own solve (nsteps steps)
             plan = dme.Plan(dev(pr.A), C=dev(pr.C), h=pr.T / N, flows=["F12", "F3"], B=dev(pr.B), R=dev(pr.R),
-                            prec="split_bf16")
+                            prec="split_bf16", horizon=N)
             single = np.empty((pr.n, pr.n))
             plan.solve(pr.P0, pr.T, N, single)
             assert np.array_equal(got, single)
