@@ -574,10 +574,15 @@ __global__ void normalize_kernel(const double* __restrict__ z, int n, const doub
         if (s > 0.0) x[i] = z[i] * s;
 }
 
+// Doubles of norm2_sq's work vector.
+size_t norm2_work_doubles(int n) { return 3 * (size_t)n + 2; }
+
 // The largest eigenvalue of M^T M (M n x n), i.e. ||M||_2^2, by 48 steps of the
 // power iteration from the unit vector of equal entries, returned as the last
 // Rayleigh quotient: an estimate from below that converges to the eigenvalue.
-dme_status norm2_sq(const double* M, int n, double* work, cudaStream_t st, double* out) {
+// work: norm2_work_doubles(n) doubles (x, y, z and two scalars).
+dme_status norm2_sq(const double* M, int n, double* work, size_t work_len, cudaStream_t st, double* out) {
+    if (work_len < norm2_work_doubles(n)) return set_error("norm2_sq: work vector too short"), DME_EINVAL;
     double* x = work;
     double* y = x + n;
     double* z = y + n;
@@ -631,12 +636,14 @@ dme_status choose_pairs(dme_plan_t p) {
         return DME_OK;
     }
     TmpPool tp(st);
-    double *X, *ref, *out, *tmp, *work;
+    double *X, *ref, *out, *tmp, *work, *vec;
     DME_TRY(tp.get(&X, nn));
     DME_TRY(tp.get(&ref, nn));
     DME_TRY(tp.get(&out, nn));
     DME_TRY(tp.get(&tmp, nn));
     DME_TRY(tp.get(&work, 2 * 256 + 2));
+    const size_t vec_len = norm2_work_doubles(n);
+    DME_TRY(tp.get(&vec, vec_len));
     double worst[3] = {0.0, 0.0, 0.0};
     auto probe = [&](const SliceBuf& G, const double* E, const double* Sm, const double* Xs) -> dme_status {
         // FP64 reference: E^T X E (G = E^T) or S X S^T
@@ -677,9 +684,9 @@ dme_status choose_pairs(dme_plan_t p) {
     DME_TRY(check_status(p, "dme_plan (slice-pair probe)"));
     // contraction of one step: ||E_t||_2^2 per congruence, the S-flow's growth
     std::vector<double> e2(p->ew.size(), 1.0);
-    for (size_t k = 0; k < p->ew.size(); ++k) DME_TRY(norm2_sq(p->ew[k].E, n, tmp, st, &e2[k]));
+    for (size_t k = 0; k < p->ew.size(); ++k) DME_TRY(norm2_sq(p->ew[k].E, n, vec, vec_len, st, &e2[k]));
     double s2 = 0.0;
-    if (sflow && p->S) DME_TRY(norm2_sq(p->S, n, tmp, st, &s2));
+    if (sflow && p->S) DME_TRY(norm2_sq(p->S, n, vec, vec_len, st, &s2));
     double rho = 1.0;
     for (const Op& o : p->ops) {
         if (o.kind == OP_CONG) rho *= e2[o.ew];
