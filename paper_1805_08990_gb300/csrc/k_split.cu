@@ -815,32 +815,50 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_gemm_grouped_kernel(const
     oz_persistent<Cfg>(units, [&](int u, OzUnit& o) { oz_group_unit(d, nd, u, o); });
 }
 
-// Split K of the tail: one CTA per split tile, one thread per tile row; the
-// parts' level sums are added in part order (the level-0 parts are exact
-// integers, so their sum is exact) and the tile's epilogue runs on the result.
-__global__ void __launch_bounds__(OZ_BM) oz_tail_kernel(const __grid_constant__ OzParams p) {
+// Split K of the tail: the parts' level sums added in part order (the level-0
+// parts are exact integers, so their sum is exact), then the epilogue of one
+// element.  Block (tail tile, group of 8 tile rows) of 8 warps: warp w takes
+// tile row 8 g + w and its lanes 32 consecutive columns at a time, so the
+// workspace reads, the addend reads (at (i, j): tri addends are symmetric)
+// and the row-direction stores are coalesced; the element arithmetic is
+// oz_store_half's, so a split tile gives what an unsplit one would from the
+// same level sums.
+__global__ void __launch_bounds__(256) oz_tail_kernel(const __grid_constant__ OzParams p) {
     constexpr size_t tile_elems = (size_t)OZ_BM * OZ_BN;
-    const int widx = blockIdx.x, il = threadIdx.x;
+    const int widx = blockIdx.x;
+    const int il = blockIdx.y * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     int tm, tn;
     oz_tile_coords(p, p.split_first + widx, tm, tn);
-    const int m0 = tm * OZ_BM, n0 = tn * OZ_BN;
-    const float2* base = p.ws + (size_t)widx * p.split_parts * tile_elems + (size_t)il * OZ_BN;
+    const int i = tm * OZ_BM + il;
+    if (i >= p.M) return;
     const bool diag = p.tri && tm == tn;
-#pragma unroll 1
+    const float sA = p.sa[i];
+    const float2* base = p.ws + (size_t)widx * p.split_parts * tile_elems + (size_t)il * OZ_BN;
     for (int c0 = 0; c0 < OZ_BN; c0 += 32) {
-        uint32_t h[32], l[32];
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) h[jj] = l[jj] = 0u;
+        const int jl = c0 + lane, j = tn * OZ_BN + jl;
+        if (j >= p.N || (diag && i > j)) continue;
+        float hv = 0.f, lv = 0.f;
         for (int pp = 0; pp < p.split_parts; ++pp) {
-            const float2* src = base + (size_t)pp * tile_elems + c0;
-#pragma unroll
-            for (int jj = 0; jj < 32; ++jj) {
-                const float2 v = src[jj];
-                h[jj] = __float_as_uint(__uint_as_float(h[jj]) + v.x);
-                l[jj] = __float_as_uint(__uint_as_float(l[jj]) + v.y);
-            }
+            const float2 v = base[(size_t)pp * tile_elems + jl];
+            hv += v.x;
+            lv += v.y;
         }
-        oz_store_half(p, m0, n0, m0 + il, c0, diag, h, l);
+        const float s = sA * p.sb[j];
+        const float sh = hv + lv;
+        const float bb = sh - hv;
+        const float sl = (hv - (sh - bb)) + (lv - bb);
+        const size_t off = (size_t)i * p.ldc + j;
+        if (p.mode == OZ_OUT_PAIR) {
+            p.Cp[off] = make_float2(sh * s, sl * s);
+            continue;
+        }
+        double v = f2d_bits(sh * s) + f2d_bits(sl * s);
+        if (p.alpha != 1.0) v *= p.alpha;
+        if (p.D1) v += p.b1 * p.D1[off];
+        if (p.D2) v += p.b2 * p.D2[off];
+        if (p.D3) v += p.b3 * p.D3[off];
+        p.Cd[off] = v;
+        if (p.tri && i != j) p.Cd[(size_t)j * p.ldc + i] = v;
     }
 }
 
@@ -998,7 +1016,7 @@ dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzPar
         default: return set_error("ozaki gemm: unknown configuration"), DME_EINVAL;
     }
     if (p.split_parts > 1) {
-        oz_tail_kernel<<<tiles - p.split_first, OZ_BM, 0, st>>>(p);
+        oz_tail_kernel<<<dim3(tiles - p.split_first, OZ_BM / 8), 256, 0, st>>>(p);
         DME_CUDA_TRY(cudaGetLastError());
     }
     if (acc) {
