@@ -102,6 +102,9 @@ struct dme_server_s {
     int completed = 0, failed = 0, tuned = 0;
     std::atomic<int> rounds{0}, graph_builds{0};   // written by the stepper, read by dme_server_stats
     double build_s = 0.0;   // host time spent building round graphs (stepper thread; under mu)
+    double plan_s = 0.0;    // wall time of the admission threads' plan builds, summed (under mu)
+    int planned = 0;
+    int pairs_hist[3] = {0, 0, 0};   // split plans by slice products chosen: 10, 13, 14 (under mu)
     double t_first = -1, t_last = 0;
     std::string stats;
 };
@@ -167,7 +170,9 @@ void admit_loop(dme_server_t s) {
         const double* Bp = r->B.empty() ? nullptr : r->B.data();
         const double* Rp = r->R.empty() ? nullptr : r->R.data();
         const double* Sp = r->S.empty() ? nullptr : r->S.data();
+        const double tp0 = now_s();
         dme_status st = plan_create(&r->desc, r->A.data(), r->QC.data(), Bp, Rp, Sp, nullptr, &p);
+        const double tp1 = now_s();
         const size_t nn = (size_t)r->desc.n * r->desc.n;
         if (st == DME_OK) {
             r->plan = p;
@@ -198,6 +203,9 @@ void admit_loop(dme_server_t s) {
         std::vector<double>().swap(r->QC);
         std::vector<double>().swap(r->P0);
         std::lock_guard<std::mutex> g(s->mu);
+        s->plan_s += tp1 - tp0;
+        s->planned++;
+        if (p->split) s->pairs_hist[p->cfg == OZ_P10 ? 0 : (p->cfg == OZ_P13 ? 1 : 2)]++;
         const size_t actual = p->bytes + nn * sizeof(double) +
                               (r->gain ? (size_t)r->nsteps * r->desc.m * r->desc.n * sizeof(double) : 0);
         s->reserved = s->reserved - r->reserved + actual;
@@ -741,15 +749,17 @@ const char* dme_server_stats(dme_server_t s) {
     const double span = (s->t_first >= 0 && s->t_last > s->t_first) ? s->t_last - s->t_first : 0.0;
     int t32 = 0;
     for (auto& kv : s->tile_choice) t32 += kv.second == 32;
-    char buf[512];
+    char buf[768];
     snprintf(buf, sizeof(buf),
              "{\"completed\": %d, \"failed\": %d, \"resident\": %d, \"queued\": %d, \"rounds\": %d, "
              "\"graph_builds\": %d, \"graph_build_ms\": %.1f, \"tuned_groups\": %d, \"tiles32\": %d, "
-             "\"p50_ms\": %.3f, \"p99_ms\": %.3f, \"solves_per_s\": %.4f, \"reserved_bytes\": %zu}",
+             "\"p50_ms\": %.3f, \"p99_ms\": %.3f, \"solves_per_s\": %.4f, \"reserved_bytes\": %zu, "
+             "\"plans\": %d, \"plan_ms_mean\": %.3f, \"split_pairs_10_13_14\": [%d, %d, %d]}",
              s->completed, s->failed, resident, queued, s->rounds.load(), s->graph_builds.load(), s->build_s * 1e3,
              s->tuned, t32,
              pct(0.5), pct(0.99),
-             span > 0 ? s->completed / span : 0.0, s->reserved);
+             span > 0 ? s->completed / span : 0.0, s->reserved, s->planned,
+             s->planned ? 1e3 * s->plan_s / s->planned : 0.0, s->pairs_hist[0], s->pairs_hist[1], s->pairs_hist[2]);
     s->stats = buf;
     return s->stats.c_str();
 }
