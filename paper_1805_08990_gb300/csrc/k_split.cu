@@ -375,14 +375,14 @@ void launch_slice_rows_pair(const float2* Xp, int rows, int cols, int ldx, const
 // ============================================================== tcgen05 GEMM
 // Tile order.  Tiles run in groups of OZ_GROUP tile rows, column by column
 // inside a group, so the CTAs working at one time touch the group's row tiles
-// of A (16 x 128 rows: 64 MB of 4-plane slices at n = 4096, kept in L2 for the
-// group) and about 152/OZ_GROUP column tiles of B; B is read once per group.
-// Triangle grids do the same over the tiles with tm <= tn.
-constexpr int OZ_GROUP = 16;
+// of A (8 x 128 rows) and about 152/OZ_GROUP column tiles of B, which stay in
+// L2; B is read once per group.  Triangle grids do the same over the tiles
+// with tm <= tn.  (Groups of 16 measured 1 % slower at n = 4096.)
+constexpr int OZ_GROUP = 8;
 
 __device__ __forceinline__ void oz_tile_coords(const OzParams& p, int t, int& tm, int& tn) {
     if (p.tri) {
-        // group g holds rows [16 g, 16 g + 16); its column tn carries the rows tm <= tn
+        // group g holds rows [8 g, 8 g + 8); its column tn carries the rows tm <= tn
         const int T = p.tiles_n;
         int first = 0, rem = t;
         while (true) {
@@ -667,15 +667,6 @@ __device__ __forceinline__ void oz_persistent(int units, Resolve resolve) {
                         tma_load_3d(smem_u32(st + Cfg::A_BYTES + sb * OZ_SLICE_BYTES), w.tB, full, kc, n0, sb);
                     issued |= 1u << s;
                     last_ph = (last_ph & ~(1u << s)) | (ph << s);
-                    // pull the slice tiles of k block it + 2 S into L2, so the loads that
-                    // reach them about S stages from now do not wait on DRAM
-                    if (it + 2 * S < w.nk && m0 + OZ_BM <= p.M && n0 + OZ_BN <= p.N) {
-                        const int kf = (w.kb0 + it + 2 * S) * OZ_BK;
-#pragma unroll
-                        for (int sa = 0; sa < Cfg::SA; ++sa) tma_prefetch_3d(w.tA, kf, m0, sa);
-#pragma unroll
-                        for (int sb = 0; sb < Cfg::SB; ++sb) tma_prefetch_3d(w.tB, kf, n0, sb);
-                    }
                     // spread over the K loop: pull the epilogue's addend rows into L2 (full
                     // 128-column segments only, 16-byte aligned; transposed for tri outputs)
                     if (!Cfg::ACC && p.mode == OZ_OUT_F64 && it < OZ_BM && (p.ldc % 2) == 0) {
