@@ -52,13 +52,20 @@ constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;               // producer + M
 constexpr int OZ_EPI_COLS = OZ_BN / (OZ_EPI_WARPS / 4);          // columns per epilogue warp (64)
 constexpr uint32_t OZ_IDESC = idesc_bf16_f32(OZ_BM, OZ_BN);
 
+// Epilogue staging buffer: 32 tile columns x 128 rows of 8-byte outputs (row
+// stride 129 words), through which the epilogue writes row segments coalesced.
+constexpr int OZ_EPI_STAGE_BYTES = 32 * (OZ_BM + 1) * 8;
+
 template <int SA_, int SB_, int L_, int STAGES_, bool ACC_>
 struct OzCfg {
     static constexpr int SA = SA_, SB = SB_, L = L_, STAGES = STAGES_;
     static constexpr bool ACC = ACC_;                                // accurate mode (exact chunks)
     static constexpr int A_BYTES = SA * OZ_SLICE_BYTES;
     static constexpr int STAGE_BYTES = (SA + SB) * OZ_SLICE_BYTES;
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+    // the staged epilogue when the buffer fits beside the stage ring
+    static constexpr bool STAGED_EPI = !ACC && STAGES * STAGE_BYTES + OZ_EPI_STAGE_BYTES + 1024 + 256 <= 232448;
+    static constexpr int EPI_BYTES = STAGED_EPI ? OZ_EPI_STAGE_BYTES : 0;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_BYTES + 1024 + 256;
 };
 using CfgP10 = OzCfg<4, 4, 3, 3, false>;
 using CfgP13 = OzCfg<4, 4, 4, 3, false>;
@@ -567,6 +574,80 @@ __device__ __forceinline__ void oz_store_half(const OzParams& p, int m0, int n0,
     }
 }
 
+// Staged epilogue of one 16-column round: the thread of tile row il holds the
+// level sums of columns c0 + h0 .. c0 + h0 + 15 (entries h0 .. h0 + 15 of h, l).
+// Phase 1: each thread forms its 16 outputs (FP64 value or normalised pair);
+// a triangle output also goes straight to its mirror (j, i), coalesced over the
+// warp's rows, with the symmetric addends read at (j, i); every output is put
+// in the staging buffer T (16 columns of the two warps of a lane quadrant, so
+// T holds 32 tile columns).  Phase 2: the 256 epilogue threads write the 128
+// staged row segments (i, j) coalesced (non-triangle F64 outputs add their
+// addends here, read at (i, j)).  Two named-barrier syncs per round.
+__device__ __forceinline__ void oz_store_staged(const OzParams& p, int m0, int n0, int il, int c0, int h0, bool diag,
+                                                const uint32_t (&h)[32], const uint32_t (&l)[32], uint64_t* T,
+                                                int ew, int lane) {
+    const int i = m0 + il;
+    const int slot = (ew / 4) * 16;                        // T columns of this warp pair: 0..15 or 16..31
+    if (i < p.M) {
+        const float sA = p.sa[i];
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+            const int j = n0 + c0 + h0 + jj;
+            if (j >= p.N) break;
+            const float s = sA * p.sb[j];
+            const float hv = __uint_as_float(h[h0 + jj]), lv = __uint_as_float(l[h0 + jj]);
+            const float sh = hv + lv;
+            const float bb = sh - hv;
+            const float sl = (hv - (sh - bb)) + (lv - bb);
+            uint64_t word;
+            if (p.mode == OZ_OUT_PAIR) {
+                const float2 v = make_float2(sh * s, sl * s);
+                word = *reinterpret_cast<const uint64_t*>(&v);
+            } else {
+                double v = f2d_bits(sh * s) + f2d_bits(sl * s);
+                if (p.alpha != 1.0) v *= p.alpha;
+                if (p.tri) {
+                    if (diag && i > j) continue;               // its mirror (j, i) owns this entry
+                    const size_t tof = (size_t)j * p.ldc + i;
+                    if (p.D1) v += p.b1 * p.D1[tof];
+                    if (p.D2) v += p.b2 * p.D2[tof];
+                    if (p.D3) v += p.b3 * p.D3[tof];
+                    p.Cd[tof] = v;
+                }
+                word = (uint64_t)__double_as_longlong(v);
+            }
+            T[(slot + jj) * (OZ_BM + 1) + il] = word;
+        }
+    }
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+    // phase 2: warp ew writes tile rows 16 ew .. 16 ew + 15; lanes 0-15 the first warp
+    // pair's 16 columns (tile columns c0' + h0 ..), lanes 16-31 the second pair's (c0' + 64)
+    const int half = lane >> 4, jl = lane & 15;
+    const int cbase = (c0 - (ew / 4) * 64) + half * 64 + h0;   // tile column of this lane's slot
+    const int j = n0 + cbase + jl;
+#pragma unroll 4
+    for (int r = 0; r < 16; ++r) {
+        const int rl = 16 * ew + r;
+        const int gi = m0 + rl;
+        if (gi >= p.M || j >= p.N) continue;
+        if (p.tri && (gi >= j)) continue;            // (i, i) and below: written in phase 1 (or by the mirror)
+        const uint64_t word = T[(half * 16 + jl) * (OZ_BM + 1) + rl];
+        const size_t off = (size_t)gi * p.ldc + j;
+        if (p.mode == OZ_OUT_PAIR) {
+            p.Cp[off] = *reinterpret_cast<const float2*>(&word);
+        } else {
+            double v = __longlong_as_double((long long)word);
+            if (!p.tri) {
+                if (p.D1) v += p.b1 * p.D1[off];
+                if (p.D2) v += p.b2 * p.D2[off];
+                if (p.D3) v += p.b3 * p.D3[off];
+            }
+            p.Cd[off] = v;
+        }
+    }
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+}
+
 // Accurate-mode epilogue of 32 columns: the levels added in fp64 (levels 0-2
 // of a chunk are exact fp32 integers of their units, so the double sum is
 // exact but for the shared level-3 accumulator's own rounding), scaled, and
@@ -601,7 +682,8 @@ template <class Cfg, class Resolve>
 __device__ __forceinline__ void oz_persistent(int units, Resolve resolve) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::STAGES * Cfg::STAGE_BYTES);
+    uint64_t* stage_T = reinterpret_cast<uint64_t*>(smem + Cfg::STAGES * Cfg::STAGE_BYTES);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::STAGES * Cfg::STAGE_BYTES + Cfg::EPI_BYTES);
     // bars[0..S): full, [S..2S): empty, [2S]: accumulators full, [2S+1]: accumulators
     // empty, [2S+2]: drain (every MMA done before TMEM is freed)
     constexpr int S = Cfg::STAGES;
@@ -805,8 +887,15 @@ __device__ __forceinline__ void oz_persistent(int units, Resolve resolve) {
                 continue;
             }
             const bool diag = p.tri && w.tm == w.tn;
-            oz_store_half(p, m0, n0, i, cq, diag, h0, l0);
-            oz_store_half(p, m0, n0, i, cq + 32, diag, h1, l1);
+            if (Cfg::STAGED_EPI) {
+                oz_store_staged(p, m0, n0, il, cq, 0, diag, h0, l0, stage_T, ew, lane);
+                oz_store_staged(p, m0, n0, il, cq, 16, diag, h0, l0, stage_T, ew, lane);
+                oz_store_staged(p, m0, n0, il, cq + 32, 0, diag, h1, l1, stage_T, ew, lane);
+                oz_store_staged(p, m0, n0, il, cq + 32, 16, diag, h1, l1, stage_T, ew, lane);
+            } else {
+                oz_store_half(p, m0, n0, i, cq, diag, h0, l0);
+                oz_store_half(p, m0, n0, i, cq + 32, diag, h1, l1);
+            }
         }
     }
     fence_before_sync();
