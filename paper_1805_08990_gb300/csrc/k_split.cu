@@ -590,33 +590,49 @@ __device__ __forceinline__ void oz_store_staged(const OzParams& p, int m0, int n
     const int slot = (ew / 4) * 16;                        // T columns of this warp pair: 0..15 or 16..31
     if (i < p.M) {
         const float sA = p.sa[i];
+        // four columns at a time: their addends are loaded before any of the four
+        // stores (an in-place update may alias Cd and D1, which would otherwise
+        // serialise every load behind the previous store)
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-            const int j = n0 + c0 + h0 + jj;
-            if (j >= p.N) break;
-            const float s = sA * p.sb[j];
-            const float hv = __uint_as_float(h[h0 + jj]), lv = __uint_as_float(l[h0 + jj]);
-            const float sh = hv + lv;
-            const float bb = sh - hv;
-            const float sl = (hv - (sh - bb)) + (lv - bb);
-            uint64_t word;
-            if (p.mode == OZ_OUT_PAIR) {
-                const float2 v = make_float2(sh * s, sl * s);
-                word = *reinterpret_cast<const uint64_t*>(&v);
-            } else {
-                double v = f2d_bits(sh * s) + f2d_bits(sl * s);
-                if (p.alpha != 1.0) v *= p.alpha;
-                if (p.tri) {
-                    if (diag && i > j) continue;               // its mirror (j, i) owns this entry
-                    const size_t tof = (size_t)j * p.ldc + i;
-                    if (p.D1) v += p.b1 * p.D1[tof];
-                    if (p.D2) v += p.b2 * p.D2[tof];
-                    if (p.D3) v += p.b3 * p.D3[tof];
-                    p.Cd[tof] = v;
-                }
-                word = (uint64_t)__double_as_longlong(v);
+        for (int g = 0; g < 16; g += 4) {
+            double a1[4], a2[4], a3[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = n0 + c0 + h0 + g + u;
+                const bool in = p.mode == OZ_OUT_F64 && p.tri && j < p.N && !(diag && i > j);
+                const size_t tof = (size_t)j * p.ldc + i;
+                a1[u] = (in && p.D1) ? p.D1[tof] : 0.0;
+                a2[u] = (in && p.D2) ? p.D2[tof] : 0.0;
+                a3[u] = (in && p.D3) ? p.D3[tof] : 0.0;
             }
-            T[(slot + jj) * (OZ_BM + 1) + il] = word;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int jj = g + u;
+                const int j = n0 + c0 + h0 + jj;
+                if (j >= p.N) break;
+                const float s = sA * p.sb[j];
+                const float hv = __uint_as_float(h[h0 + jj]), lv = __uint_as_float(l[h0 + jj]);
+                const float sh = hv + lv;
+                const float bb = sh - hv;
+                const float sl = (hv - (sh - bb)) + (lv - bb);
+                uint64_t word;
+                if (p.mode == OZ_OUT_PAIR) {
+                    const float2 v = make_float2(sh * s, sl * s);
+                    word = *reinterpret_cast<const uint64_t*>(&v);
+                } else {
+                    double v = f2d_bits(sh * s) + f2d_bits(sl * s);
+                    if (p.alpha != 1.0) v *= p.alpha;
+                    if (p.tri) {
+                        if (diag && i > j) continue;           // its mirror (j, i) owns this entry
+                        if (p.D1) v += p.b1 * a1[u];
+                        if (p.D2) v += p.b2 * a2[u];
+                        if (p.D3) v += p.b3 * a3[u];
+                        p.Cd[(size_t)j * p.ldc + i] = v;
+                    }
+                    word = (uint64_t)__double_as_longlong(v);
+                }
+                T[(slot + jj) * (OZ_BM + 1) + il] = word;
+            }
         }
     }
     asm volatile("bar.sync 1, 256;" ::: "memory");
@@ -749,12 +765,15 @@ __device__ __forceinline__ void oz_persistent(int units, Resolve resolve) {
                         tma_load_3d(smem_u32(st + Cfg::A_BYTES + sb * OZ_SLICE_BYTES), w.tB, full, kc, n0, sb);
                     issued |= 1u << s;
                     last_ph = (last_ph & ~(1u << s)) | (ph << s);
-                    // spread over the K loop: pull the epilogue's addend rows into L2 (full
-                    // 128-column segments only, 16-byte aligned; transposed for tri outputs)
-                    if (!Cfg::ACC && p.mode == OZ_OUT_F64 && it < OZ_BM && (p.ldc % 2) == 0) {
-                        const int ra = (p.tri ? n0 : m0) + it, ca = p.tri ? m0 : n0;
-                        const int rmax = p.tri ? p.N : p.M, cmax = p.tri ? p.M : p.N;
-                        if (ra < rmax && ca + OZ_BN <= cmax) {
+                    // pull the epilogue's addend rows into L2: spread over the K loop, and all
+                    // of them at the last k block of a short one (full 128-column segments
+                    // only, 16-byte aligned; transposed for tri outputs)
+                    if (!Cfg::ACC && p.mode == OZ_OUT_F64 && (p.ldc % 2) == 0 && (p.D1 || p.D2)) {
+                        const int r0 = it, r1 = (it == w.nk - 1) ? OZ_BM : min(it + 1, OZ_BM);
+                        for (int rr = r0; rr < r1; ++rr) {
+                            const int ra = (p.tri ? n0 : m0) + rr, ca = p.tri ? m0 : n0;
+                            const int rmax = p.tri ? p.N : p.M, cmax = p.tri ? p.M : p.N;
+                            if (ra >= rmax || ca + OZ_BN > cmax) continue;
                             const size_t off = (size_t)ra * p.ldc + ca;
                             if (p.D1 && ((reinterpret_cast<uintptr_t>(p.D1 + off) & 15) == 0))
                                 prefetch_l2_bulk(p.D1 + off, OZ_BN * sizeof(double));
