@@ -41,9 +41,10 @@ NOMINAL_FP64_TFLOPS = 1.25    # GB300 FP64 (non-tensor and tensor), the profilin
 
 FP64_MAX_STEPS = 16
 
-# DRAM bytes (read + write) of one full 4096^3 launch of the tensor kernel, from the
-# ncu capture summarised in profiles/ozaki_gemm_n4096_ncu.md (955.0 MB + 122.9 MB).
-OZAKI_FULL_LAUNCH_DRAM_BYTES = 1.0779e9
+# DRAM bytes (read + write) of one full 4096^3 launch of the tensor kernel as it is
+# now, from the ncu capture summarised in profiles/ozaki_gemm_n4096_ncu.md; None while
+# the kernel has changed since the last capture.
+OZAKI_FULL_LAUNCH_DRAM_BYTES = None
 
 
 def load_peaks():
@@ -207,6 +208,7 @@ def serving_stream(count: int, seed: int, rate: float, prec: str):
     tickets: list = []
     cv = threading.Condition()
     failures = []
+    busy = [0]
 
     def reap():
         i = 0
@@ -231,7 +233,15 @@ def serving_stream(count: int, seed: int, rate: float, prec: str):
                 time.sleep(delay)
             d = dme.make_desc(pr.n, m=pr.B.shape[1], p=pr.C.shape[0], eq=dme.DME_DRE, comp="strang",
                               flows=("F12", "F3"), h=pr.T / sp["steps"], q_is_factor=True, prec=prec)
-            tk = dme.dme_submit(srv, d, pr.A, pr.C, pr.B, pr.R, None, pr.P0, pr.T, sp["steps"])
+            while True:          # a full queue pushes back: retry until the server takes the request
+                try:
+                    tk = dme.dme_submit(srv, d, pr.A, pr.C, pr.B, pr.R, None, pr.P0, pr.T, sp["steps"])
+                    break
+                except dme.DmeError as e:
+                    if e.status != dme.DME_EBUSY:
+                        raise
+                    busy[0] += 1
+                    time.sleep(0.005)
             with cv:
                 tickets.append((tk, pr.n))
                 cv.notify()
@@ -239,6 +249,7 @@ def serving_stream(count: int, seed: int, rate: float, prec: str):
         st = json.loads(dme.dme_server_stats(srv))
         st["wall_s"] = time.perf_counter() - t0
         st["client_failures"] = len(failures)
+        st["busy_retries"] = busy[0]
         st["work_fp64_flops"], st["work_tensor_flops"] = serving_work(specs)
         return st
     finally:
@@ -310,7 +321,7 @@ def run_serving_suite(args):
     torch.cuda.set_device(0)
     out = {}
     for prec, count, burst_n in (("split_bf16", args.serving_suite, 256),
-                                 ("fp64", max(args.serving_suite // 8, 64), 64)):
+                                 ("fp64", args.serving_suite_fp64 or max(args.serving_suite // 8, 64), 64)):
         serving_run(8, seed=4, rate=None, prec=prec)       # warm-up (module loading, first launches), untimed
         burst = serving_run(burst_n, seed=1, rate=None, prec=prec)
         sat = burst["completed"] / burst["wall_s"]
@@ -322,8 +333,12 @@ def run_serving_suite(args):
                          "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "completed": st["completed"],
                          "failed": st["failed"] + st["client_failures"], "wall_s": st["wall_s"],
                          "graph_builds": st.get("graph_builds"), "rounds": st.get("rounds"),
+                         "busy_retries": st.get("busy_retries"), "plan_ms_mean": st.get("plan_ms_mean"),
+                         "split_pairs_10_13_14": st.get("split_pairs_10_13_14"),
                          "roofline": serving_roofline(st, prec, peaks)})
-        out[prec] = {"requests_per_load": count, "saturation_solves_per_s": sat,
+        out[prec] = {"requests_per_load": count, "saturation_solves_per_s": sat, "burst_requests": burst_n,
+                     "burst_plan_ms_mean": burst.get("plan_ms_mean"),
+                     "burst_split_pairs_10_13_14": burst.get("split_pairs_10_13_14"),
                      "saturation_roofline": serving_roofline(burst, prec, peaks), "loads": rows}
     print(json.dumps({"serving_suite": out, "workload": "n log-uniform 32..1024 (Laplacian or stable random A), "
                       "m, p ~ U{1..8}, R = I_m, T ~ U[0.1, 10], 50-500 Strang F12F3 steps, P0 = 0, Poisson arrivals",
@@ -605,6 +620,7 @@ def run_ours(args):
                 "saturation_solves_per_s": sat, "poisson_rate": 0.9 * sat,
                 "solves_per_s": live["completed"] / live["wall_s"], "p50_ms": live["p50_ms"],
                 "p99_ms": live["p99_ms"], "burst_p50_ms": burst["p50_ms"], "burst_p99_ms": burst["p99_ms"],
+                "plan_ms_mean": burst.get("plan_ms_mean"), "split_pairs_10_13_14": burst.get("split_pairs_10_13_14"),
                 "roofline": serving_roofline(burst, prec, peaks)}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_run(pr, args)
@@ -890,6 +906,8 @@ def main():
                     help="run only the steps/s of the other workload configurations")
     ap.add_argument("--serving-suite", type=int, default=0,
                     help="run only the serving loads 0.5/0.9/1.2 x saturation with this many split requests")
+    ap.add_argument("--serving-suite-fp64", type=int, default=0,
+                    help="FP64 requests per load of the serving suite (0: an eighth of the split count)")
     ap.add_argument("--lowrank-steps", type=int, default=32)
     ap.add_argument("--sparse-nx", type=int, default=1000, help="grid of the sparse low-rank extra (n = nx^2)")
     ap.add_argument("--example2-nx", type=int, default=150, help="grid of the stochastic heat extras (n = nx^2)")
