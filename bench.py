@@ -596,7 +596,7 @@ def run_ours(args):
         acc["split_pairs"] = results["split"]["pairs"]
         acc["split_pair_estimate"] = results["split"]["pair_est"]
         errs, rho = results["split"]["probe"]
-        acc["split_probe"] = {"one_congruence_err": {"10": errs[0], "13": errs[1], "14": errs[2]},
+        acc["split_probe"] = {"one_congruence_err": {k: e for k, e in zip(("10", "13", "14"), errs) if e >= 0},
                               "step_contraction": rho,
                               "rule": "cheapest pairs with 4 e c (1 + rho + ... + rho^255) <= 1e-7, c = 2 "
                                       "congruences per step"}

@@ -106,16 +106,19 @@ typedef struct dme_server_s* dme_server_t;
  *   cuda_stream: a cudaStream_t, or NULL for a plan-owned stream.
  * With DME_SPLIT_BF16 every per-step product is an error-free bf16 slice
  * product (a leading 7-bit digit, trailing 9-bit digits; 4 slices of P, 4 or 5
- * of E^T and S).  With pairs = 0 the plan measures, for every E_t (and S), the
- * relative error of one congruence G X G^T of the probe state X = W_t (Q if
- * W_t = 0) under 10, 13 and 14 slice products against the FP64 congruence,
- * and keeps the cheapest whose error e satisfies 4 N e <= tol, N = the
- * congruences of `horizon` steps (the worst case: every application's error
- * adding up coherently, none damped); 14 if none does (dme_plan_split_choice
- * reports the choice and the estimate).  Above n = 511 the Pade products of
- * the exponential run on the tensor cores too, in an accurate mode (21 slice
- * products with the exact sums of 512-wide K chunks combined in fp64); the
- * denominator solves and the squarings stay FP64.
+ * of E^T and S).  With pairs = 0 the plan chooses how many slice products to
+ * run: it measures the relative error e of one congruence G X G^T of the
+ * probe state X = W_t (Q if W_t = 0) against the FP64 congruence, for every
+ * fixed operand G (E_t^T, S), and the contraction rho of one step (the
+ * product of ||E_t||_2^2 over the step's congruences, by power iteration;
+ * 1 + t||S||^2 + t^2||S||^4/2 per S-flow), and keeps the first of 10, 13, 14
+ * products whose estimate 4 e c (1 + rho + ... + rho^(horizon-1)) is within
+ * tol (c congruences per step: every application's error adding up in phase,
+ * damped only by the flow); 14 if none is.  dme_plan_split_choice and
+ * dme_plan_split_probe report the choice and its inputs.  Above n = 511 the
+ * Pade products of the exponential run on the tensor cores too, in an
+ * accurate mode (21 slice products with the exact sums of 512-wide K chunks
+ * combined in fp64); the denominator solves and the squarings stay FP64.
  * Errors: DME_EINVAL (inconsistent desc), DME_ENOTSPD (R), DME_ENOMEM,
  * DME_ECUDA.  On error *out is NULL. */
 dme_status dme_plan(const dme_plan_desc* desc, const double* A, const double* QorC,
@@ -180,8 +183,10 @@ dme_status dme_plan_split_choice(dme_plan_t plan, int* pairs, double* est);
 
 /* What the choice of dme_plan_split_choice rests on (pairs = 0 and
  * DME_SPLIT_BF16 only, else DME_EINVAL): err[0..2] the measured relative
- * errors of one congruence with 10, 13 and 14 slice products, *rho the
- * contraction of one step.  Either pointer may be NULL. */
+ * errors of one congruence with 10, 13 and 14 slice products (the plan tries
+ * them in that order and stops at the first that meets the target, so the
+ * ones after it read -1), *rho the contraction of one step.  Either pointer
+ * may be NULL. */
 dme_status dme_plan_split_probe(dme_plan_t plan, double* err, double* rho);
 
 /* Bytes of device memory the plan holds. */

@@ -541,9 +541,34 @@ __global__ void fill_kernel(double* x, int n, double v) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = v;
 }
 
-// out[0] = x . z, out[1] = z . z (one block, fixed order).
-__global__ void __launch_bounds__(1024) dot2_kernel(const double* __restrict__ x, const double* __restrict__ z, int n,
-                                                    double* __restrict__ out) {
+// y = M x (M n x n row-major): a warp per row.
+__global__ void __launch_bounds__(256) gemv_rows_kernel(const double* __restrict__ M, const double* __restrict__ x,
+                                                        int n, double* __restrict__ y) {
+    const int lane = threadIdx.x & 31;
+    for (int r = blockIdx.x * 8 + (threadIdx.x >> 5); r < n; r += gridDim.x * 8) {
+        double a = 0.0;
+        for (int k = lane; k < n; k += 32) a += M[(size_t)r * n + k] * x[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+        if (lane == 0) y[r] = a;
+    }
+}
+
+// z = M^T y: a thread per column (coalesced over the columns of each row).
+__global__ void __launch_bounds__(256) gemv_cols_kernel(const double* __restrict__ M, const double* __restrict__ y,
+                                                        int n, double* __restrict__ z) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        double a = 0.0;
+        for (int r = 0; r < n; ++r) a += M[(size_t)r * n + c] * y[r];
+        z[c] = a;
+    }
+}
+
+// One block: rq[0] = x . z (the Rayleigh quotient of M^T M at the unit x), then
+// x = z / ||z|| (fixed-order reductions; x left unchanged if z = 0).
+__global__ void __launch_bounds__(1024) rayleigh_normalize_kernel(double* __restrict__ x,
+                                                                  const double* __restrict__ z, int n,
+                                                                  double* __restrict__ rq) {
     __shared__ double sa[1024], sb[1024];
     double a = 0.0, b = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -560,24 +585,18 @@ __global__ void __launch_bounds__(1024) dot2_kernel(const double* __restrict__ x
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        out[0] = sa[0];
-        out[1] = sb[0];
+    const double xz = sa[0], zz = sb[0];
+    if (threadIdx.x == 0) rq[0] = xz;
+    if (zz > 0.0) {
+        const double sc = rsqrt(zz);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = z[i] * sc;
     }
-}
-
-// x = z / ||z|| with ||z||^2 = nrm[1] (left unchanged if z = 0).
-__global__ void normalize_kernel(const double* __restrict__ z, int n, const double* __restrict__ nrm,
-                                 double* __restrict__ x) {
-    const double s = nrm[1] > 0.0 ? rsqrt(nrm[1]) : 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        if (s > 0.0) x[i] = z[i] * s;
 }
 
 // Doubles of norm2_sq's work vector.
 size_t norm2_work_doubles(int n) { return 3 * (size_t)n + 2; }
 
-// The largest eigenvalue of M^T M (M n x n), i.e. ||M||_2^2, by 48 steps of the
+// The largest eigenvalue of M^T M (M n x n), i.e. ||M||_2^2, by 20 steps of the
 // power iteration from the unit vector of equal entries, returned as the last
 // Rayleigh quotient: an estimate from below that converges to the eigenvalue.
 // work: norm2_work_doubles(n) doubles (x, y, z and two scalars).
@@ -587,25 +606,27 @@ dme_status norm2_sq(const double* M, int n, double* work, size_t work_len, cudaS
     double* y = x + n;
     double* z = y + n;
     double* s = z + n;
+    const int gr = std::min((n + 7) / 8, 1024), gc = std::min((n + 255) / 256, 1024);
     fill_kernel<<<(n + 255) / 256, 256, 0, st>>>(x, n, 1.0 / std::sqrt((double)n));
-    for (int it = 0; it < 48; ++it) {
-        DME_TRY(gemm1(gp(n, 1, n, M, n, 0, x, 1, 0, y, 1, 1.0), st));        // y = M x
-        DME_TRY(gemm1(gp(n, 1, n, M, n, 1, y, 1, 0, z, 1, 1.0), st));        // z = M^T y
-        dot2_kernel<<<1, 1024, 0, st>>>(x, z, n, s);                          // x.z = Rayleigh quotient
-        normalize_kernel<<<(n + 255) / 256, 256, 0, st>>>(z, n, s, x);
+    for (int it = 0; it < 20; ++it) {
+        gemv_rows_kernel<<<gr, 256, 0, st>>>(M, x, n, y);                     // y = M x
+        gemv_cols_kernel<<<gc, 256, 0, st>>>(M, y, n, z);                     // z = M^T y
+        rayleigh_normalize_kernel<<<1, 1024, 0, st>>>(x, z, n, s);            // rq = x.z; x = z/|z|
     }
-    double h[2] = {0.0, 0.0};
-    DME_CUDA_TRY(cudaMemcpyAsync(h, s, sizeof(h), cudaMemcpyDeviceToHost, st));
+    DME_CUDA_TRY(cudaGetLastError());
+    double h = 0.0;
+    DME_CUDA_TRY(cudaMemcpyAsync(&h, s, sizeof(h), cudaMemcpyDeviceToHost, st));
     DME_CUDA_TRY(cudaStreamSynchronize(st));
-    *out = h[0];
+    *out = h;
     return DME_OK;
 }
 
 // The split path's slice-pair configuration (dme_plan with pairs = 0): for
 // every fixed operand G the plan's steps use (E_t^T per step length, S), one
 // congruence G X G^T of the probe X = W_t (Q if W_t = 0, I if both are) under
-// P10, P13 and P14 against the FP64 congruence gives the worst relative error
-// e of one application.  An error made at some step reaches the end of the
+// P10, P13 and P14 (cheapest first, stopping at the first that meets the
+// target) against the FP64 congruence gives the worst relative error e of one
+// application.  An error made at some step reaches the end of the
 // horizon through the later steps, which shrink it at most by
 // rho = prod ||E_t||_2^2 over the step's congruences (times 1 + t ||S||^2 +
 // t^2 ||S||^4 / 2 per S-flow; T2 and T3 counted as 1, and rho = 1 for the
@@ -636,52 +657,15 @@ dme_status choose_pairs(dme_plan_t p) {
         return DME_OK;
     }
     TmpPool tp(st);
-    double *X, *ref, *out, *tmp, *work, *vec;
+    double *X, *out, *tmp, *work, *vec;
     DME_TRY(tp.get(&X, nn));
-    DME_TRY(tp.get(&ref, nn));
     DME_TRY(tp.get(&out, nn));
     DME_TRY(tp.get(&tmp, nn));
     DME_TRY(tp.get(&work, 2 * 256 + 2));
     const size_t vec_len = norm2_work_doubles(n);
     DME_TRY(tp.get(&vec, vec_len));
-    double worst[3] = {0.0, 0.0, 0.0};
-    auto probe = [&](const SliceBuf& G, const double* E, const double* Sm, const double* Xs) -> dme_status {
-        // FP64 reference: E^T X E (G = E^T) or S X S^T
-        if (E) {
-            DME_TRY(gemm1(gp(n, n, n, Xs, n, 0, E, n, 0, tmp, n, 1.0), st));
-            DME_TRY(gemm1(gp(n, n, n, E, n, 1, tmp, n, 0, ref, n, 1.0, 1), st));
-        } else {
-            DME_TRY(gemm1(gp(n, n, n, Xs, n, 0, Sm, n, 1, tmp, n, 1.0), st));
-            DME_TRY(gemm1(gp(n, n, n, Sm, n, 0, tmp, n, 0, ref, n, 1.0, 1), st));
-        }
-        for (int c = 0; c < 3; ++c) {
-            DME_TRY(split_cong(p, Xs, G, out, 1.0, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0, cands[c]));
-            double e = 0.0;
-            DME_TRY(rel_diff(out, ref, nn, work, st, &e));
-            worst[c] = std::max(worst[c], e);
-        }
-        return DME_OK;
-    };
-    // probe state: W_t of the first step length, else Q, else I (rel_diff against a
-    // zero matrix returns the Frobenius norm)
-    const double* probe_src = p->ew.empty() ? nullptr : p->ew.front().W;
-    double nrm = 0.0;
-    DME_CUDA_TRY(cudaMemsetAsync(tmp, 0, nn * sizeof(double), st));
-    if (probe_src) DME_TRY(rel_diff(probe_src, tmp, nn, work, st, &nrm));
-    if (!(nrm > 0.0)) {
-        probe_src = p->Q;
-        DME_TRY(rel_diff(p->Q, tmp, nn, work, st, &nrm));
-    }
-    if (nrm > 0.0) {
-        DME_CUDA_TRY(cudaMemcpyAsync(X, probe_src, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    } else {
-        launch_lincomb(X, n, n, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0, 1.0, st);
-    }
-    for (const EWEntry& e : p->ew) DME_TRY(probe(e.Gsl, e.E, nullptr, X));
     bool sflow = false;
     for (const Op& o : p->ops) sflow = sflow || o.kind == OP_SFLOW;
-    if (sflow && p->S) DME_TRY(probe(p->Ssl, nullptr, p->S, X));
-    DME_TRY(check_status(p, "dme_plan (slice-pair probe)"));
     // contraction of one step: ||E_t||_2^2 per congruence, the S-flow's growth
     std::vector<double> e2(p->ew.size(), 1.0);
     for (size_t k = 0; k < p->ew.size(); ++k) DME_TRY(norm2_sq(p->ew[k].E, n, vec, vec_len, st, &e2[k]));
@@ -699,15 +683,55 @@ dme_status choose_pairs(dme_plan_t p) {
     const double G = rho < 1.0 ? (1.0 - std::pow(rho, (double)H)) / (1.0 - rho) : (double)H;
     const double N = (double)apps * G;
     p->cfg_rho = rho;
-    for (int c = 0; c < 3; ++c) p->cfg_err[c] = worst[c];
-    p->cfg_est = 4.0 * N * worst[2];
-    for (int c = 0; c < 3; ++c) {
-        if (4.0 * N * worst[c] <= tol) {
-            p->cfg = cands[c];
-            p->cfg_est = 4.0 * N * worst[c];
-            break;
-        }
+    // probe state: W_t of the first step length, else Q, else I (rel_diff against a
+    // zero matrix returns the Frobenius norm)
+    const double* probe_src = p->ew.empty() ? nullptr : p->ew.front().W;
+    double nrm = 0.0;
+    DME_CUDA_TRY(cudaMemsetAsync(tmp, 0, nn * sizeof(double), st));
+    if (probe_src) DME_TRY(rel_diff(probe_src, tmp, nn, work, st, &nrm));
+    if (!(nrm > 0.0)) {
+        probe_src = p->Q;
+        DME_TRY(rel_diff(p->Q, tmp, nn, work, st, &nrm));
     }
+    if (nrm > 0.0) {
+        DME_CUDA_TRY(cudaMemcpyAsync(X, probe_src, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+        launch_lincomb(X, n, n, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0, 1.0, st);
+    }
+    // FP64 references of the probe congruence for every fixed operand: E_t^T X E_t, S X S^T
+    std::vector<double*> refs;
+    std::vector<const SliceBuf*> gs;
+    for (const EWEntry& e : p->ew) {
+        double* r = nullptr;
+        DME_TRY(tp.get(&r, nn));
+        DME_TRY(gemm1(gp(n, n, n, X, n, 0, e.E, n, 0, tmp, n, 1.0), st));
+        DME_TRY(gemm1(gp(n, n, n, e.E, n, 1, tmp, n, 0, r, n, 1.0, 1), st));
+        refs.push_back(r);
+        gs.push_back(&e.Gsl);
+    }
+    if (sflow && p->S) {
+        double* r = nullptr;
+        DME_TRY(tp.get(&r, nn));
+        DME_TRY(gemm1(gp(n, n, n, X, n, 0, p->S, n, 1, tmp, n, 1.0), st));
+        DME_TRY(gemm1(gp(n, n, n, p->S, n, 0, tmp, n, 0, r, n, 1.0, 1), st));
+        refs.push_back(r);
+        gs.push_back(&p->Ssl);
+    }
+    // the candidates cheapest first; the first whose estimate meets tol is kept
+    for (int c = 0; c < 3; ++c) {
+        double worst = 0.0;
+        for (size_t k = 0; k < refs.size(); ++k) {
+            DME_TRY(split_cong(p, X, *gs[k], out, 1.0, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0, cands[c]));
+            double e = 0.0;
+            DME_TRY(rel_diff(out, refs[k], nn, work, st, &e));
+            worst = std::max(worst, e);
+        }
+        p->cfg_err[c] = worst;
+        p->cfg = cands[c];
+        p->cfg_est = 4.0 * N * worst;
+        if (p->cfg_est <= tol) break;
+    }
+    DME_TRY(check_status(p, "dme_plan (slice-pair probe)"));
     return DME_OK;
 }
 
