@@ -108,8 +108,9 @@ typedef struct dme_server_s* dme_server_t;
  * product (a leading 7-bit digit, trailing 9-bit digits; 4 slices of P, 4 or 5
  * of E^T and S).  With pairs = 0 the plan chooses how many slice products to
  * run: it measures the relative error e of one congruence G X G^T of the
- * probe state X = W_t (Q if W_t = 0) against the FP64 congruence, for every
- * fixed operand G (E_t^T, S), and the contraction rho of one step (the
+ * probe state X = W_t (Q if W_t = 0) against the FP64 congruence (from n = 512
+ * the accurate mode's below), for every fixed operand G (E_t^T, S), and the
+ * contraction rho of one step (the
  * product of ||E_t||_2^2 over the step's congruences, by power iteration;
  * 1 + t||S||^2 + t^2||S||^4/2 per S-flow), and keeps the first of 10, 13, 14
  * products whose estimate 4 e c (1 + rho + ... + rho^(horizon-1)) is within

@@ -194,6 +194,33 @@ dme_status acc_prod(int n, AccWork& w, const double* L, int tL, const double* R,
     return launch_ozaki_gemm(w.a.tmap, w.b.tmap, o, st);
 }
 
+// Scratch of the accurate mode for n x n products, from a plan-time pool.
+dme_status acc_setup(TmpPool& tp, int n, int* status, AccWork* w) {
+    const size_t nn = (size_t)n * n;
+    double *ad, *bd, *sc;
+    const size_t sl = (slice_buf_bytes(n, n, OZ_SLICES_ACC) + 7) / 8;
+    DME_TRY(tp.get(&ad, sl));
+    DME_TRY(tp.get(&bd, sl));
+    DME_TRY(tp.get(&sc, (size_t)n));
+    DME_TRY(tp.get(&w->t, nn));
+    DME_TRY(tp.get(&w->wsd, oz_acc_ws_doubles(n, n, n)));
+    for (SliceBuf* b : {&w->a, &w->b}) {
+        b->rows = n;
+        b->k = n;
+        b->Kp = slice_kpad(n);
+        b->ns = OZ_SLICES_ACC;
+        b->scheme = OZ_DIG7;
+    }
+    w->a.data = reinterpret_cast<__nv_bfloat16*>(ad);
+    w->b.data = reinterpret_cast<__nv_bfloat16*>(bd);
+    w->a.scale = reinterpret_cast<float*>(sc);
+    w->b.scale = reinterpret_cast<float*>(sc) + n;
+    DME_TRY(make_slice_tmap(w->a, &w->a.tmap));
+    DME_TRY(make_slice_tmap(w->b, &w->b.tmap));
+    w->status = status;
+    return DME_OK;
+}
+
 // C = alpha op(L) op(R) + b1 D1 (n x n): the accurate tensor mode with aw, else FP64.
 dme_status prod(int n, AccWork* aw, const double* L, int tL, const double* R, int tR, double* C, double alpha,
                 const double* D1, double b1, cudaStream_t st) {
@@ -382,27 +409,7 @@ dme_status compute_ew(dme_plan_t p, double tau, int* idx) {
     AccWork accw;
     AccWork* aw = nullptr;
     if (p->split && n >= kAccMinN) {
-        double *ad, *bd, *sc;
-        const size_t sl = (slice_buf_bytes(n, n, OZ_SLICES_ACC) + 7) / 8;
-        DME_TRY(tp.get(&ad, sl));
-        DME_TRY(tp.get(&bd, sl));
-        DME_TRY(tp.get(&sc, (size_t)n));
-        DME_TRY(tp.get(&accw.t, nn));
-        DME_TRY(tp.get(&accw.wsd, oz_acc_ws_doubles(n, n, n)));
-        for (SliceBuf* b : {&accw.a, &accw.b}) {
-            b->rows = n;
-            b->k = n;
-            b->Kp = slice_kpad(n);
-            b->ns = OZ_SLICES_ACC;
-            b->scheme = OZ_DIG7;
-        }
-        accw.a.data = reinterpret_cast<__nv_bfloat16*>(ad);
-        accw.b.data = reinterpret_cast<__nv_bfloat16*>(bd);
-        accw.a.scale = reinterpret_cast<float*>(sc);
-        accw.b.scale = reinterpret_cast<float*>(sc) + n;
-        DME_TRY(make_slice_tmap(accw.a, &accw.a.tmap));
-        DME_TRY(make_slice_tmap(accw.b, &accw.b.tmap));
-        accw.status = p->status;
+        DME_TRY(acc_setup(tp, n, p->status, &accw));
         aw = &accw;
     }
 
@@ -625,8 +632,8 @@ dme_status norm2_sq(const double* M, int n, double* work, size_t work_len, cudaS
 // every fixed operand G the plan's steps use (E_t^T per step length, S), one
 // congruence G X G^T of the probe X = W_t (Q if W_t = 0, I if both are) under
 // P10, P13 and P14 (cheapest first, stopping at the first that meets the
-// target) against the FP64 congruence gives the worst relative error e of one
-// application.  An error made at some step reaches the end of the
+// target) against the FP64 congruence (from n = 512 the accurate tensor mode)
+// gives the worst relative error e of one application.  An error made at some step reaches the end of the
 // horizon through the later steps, which shrink it at most by
 // rho = prod ||E_t||_2^2 over the step's congruences (times 1 + t ||S||^2 +
 // t^2 ||S||^4 / 2 per S-flow; T2 and T3 counted as 1, and rho = 1 for the
@@ -698,22 +705,30 @@ dme_status choose_pairs(dme_plan_t p) {
     } else {
         launch_lincomb(X, n, n, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0, 1.0, st);
     }
-    // FP64 references of the probe congruence for every fixed operand: E_t^T X E_t, S X S^T
+    // references of the probe congruence for every fixed operand, E_t^T X E_t and S X S^T:
+    // FP64, or from n = kAccMinN on the accurate tensor mode (about 2^-39 of the row
+    // scales per product, two orders below the errors measured against it)
+    AccWork accw;
+    AccWork* aw = nullptr;
+    if (n >= kAccMinN) {
+        DME_TRY(acc_setup(tp, n, p->status, &accw));
+        aw = &accw;
+    }
     std::vector<double*> refs;
     std::vector<const SliceBuf*> gs;
     for (const EWEntry& e : p->ew) {
         double* r = nullptr;
         DME_TRY(tp.get(&r, nn));
-        DME_TRY(gemm1(gp(n, n, n, X, n, 0, e.E, n, 0, tmp, n, 1.0), st));
-        DME_TRY(gemm1(gp(n, n, n, e.E, n, 1, tmp, n, 0, r, n, 1.0, 1), st));
+        DME_TRY(prod(n, aw, X, 0, e.E, 0, tmp, 1.0, nullptr, 0.0, st));
+        DME_TRY(prod(n, aw, e.E, 1, tmp, 0, r, 1.0, nullptr, 0.0, st));
         refs.push_back(r);
         gs.push_back(&e.Gsl);
     }
     if (sflow && p->S) {
         double* r = nullptr;
         DME_TRY(tp.get(&r, nn));
-        DME_TRY(gemm1(gp(n, n, n, X, n, 0, p->S, n, 1, tmp, n, 1.0), st));
-        DME_TRY(gemm1(gp(n, n, n, p->S, n, 0, tmp, n, 0, r, n, 1.0, 1), st));
+        DME_TRY(prod(n, aw, X, 0, p->S, 1, tmp, 1.0, nullptr, 0.0, st));
+        DME_TRY(prod(n, aw, p->S, 0, tmp, 0, r, 1.0, nullptr, 0.0, st));
         refs.push_back(r);
         gs.push_back(&p->Ssl);
     }
