@@ -830,9 +830,10 @@ def run_lowrank_only(args):
 
 def run_cong_only(args):
     """Profile target: the split plan of the bench workload (n = 4096, its slice
-    products chosen for the 256-step horizon) applying the congruence
-    T12(h/2) (E^T P E + W: two tensor-kernel launches) --reps times to a PSD
-    state, inside the NVTX range "cong"."""
+    products chosen for the 256-step horizon, or --pairs) applying one sub-flow
+    --reps times to a PSD state, inside the NVTX range "cong": --flow F12 (the
+    congruence T12(h/2), E^T P E + W: two tensor-kernel launches) or F3 (the
+    Riccati flow: Z^T = Bt^T P and P - t Y Y^T on the tensor kernel)."""
     import torch
     import paper_1805_08990_gb300 as dme
     from paper_1805_08990_gb300 import build
@@ -844,16 +845,18 @@ def run_cong_only(args):
     plan = dme.Plan(t(pr.A), C=t(pr.C), h=h, flows=["F12", "F3"], comp="strang", B=t(pr.B), R=t(pr.R),
                     prec="split_bf16", horizon=FULL_STEPS, pairs=args.pairs)
     P = t(W.random_psd(pr.n, 3, rank=64))
-    plan.apply("F12", 0.5 * h, P)
+    tau = 0.5 * h if args.flow == "F12" else h
+    plan.apply(args.flow, tau, P)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("cong")
     t0 = time.perf_counter()
     for _ in range(args.reps):
-        plan.apply_async("F12", 0.5 * h, P)
+        plan.apply_async(args.flow, tau, P)
     plan.sync()
     dt = (time.perf_counter() - t0) / args.reps
     torch.cuda.nvtx.range_pop()
-    print(json.dumps({"cong_only": pr.n, "pairs": plan.split_choice[0], "ms_per_congruence": dt * 1e3}))
+    print(json.dumps({"cong_only": pr.n, "flow": args.flow, "pairs": plan.split_choice[0],
+                      "ms_per_application": dt * 1e3}))
     plan.close()
     return 0
 
@@ -898,6 +901,7 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--cong-only", action="store_true", help="profile target: the split congruence at n = 4096")
     ap.add_argument("--pairs", type=int, default=0, help="--cong-only: slice products (0: the plan's choice)")
+    ap.add_argument("--flow", default="F12", choices=["F12", "F3"], help="--cong-only: the sub-flow applied")
     ap.add_argument("--lowrank-only", default="", choices=["", "fp64", "split", "sparse"],
                     help="profile target: one low-rank configuration alone (--lowrank-steps timed steps)")
     ap.add_argument("--serving-requests", type=int, default=32, help="serving sample size (0: skip)")

@@ -56,10 +56,14 @@ constexpr uint32_t OZ_IDESC = idesc_bf16_f32(OZ_BM, OZ_BN);
 // stride 129 words), through which the epilogue writes row segments coalesced.
 constexpr int OZ_EPI_STAGE_BYTES = 32 * (OZ_BM + 1) * 8;
 
-template <int SA_, int SB_, int L_, int STAGES_, bool ACC_>
+template <int SA_, int SB_, int L_, int STAGES_, bool ACC_, int NACC_ = 4>
 struct OzCfg {
     static constexpr int SA = SA_, SB = SB_, L = L_, STAGES = STAGES_;
     static constexpr bool ACC = ACC_;                                // accurate mode (exact chunks)
+    // TMEM accumulators: levels 0, 1, 2, >= 3 (4), or level 0 and levels >= 1 (2: products
+    // of at most 64 K, where the shared accumulator rounds at most four times)
+    static constexpr int NACC = NACC_;
+    static constexpr int TMEM_COLS = NACC * OZ_BN;
     static constexpr int A_BYTES = SA * OZ_SLICE_BYTES;
     static constexpr int STAGE_BYTES = (SA + SB) * OZ_SLICE_BYTES;
     // the staged epilogue when the buffer fits beside the stage ring
@@ -69,9 +73,16 @@ struct OzCfg {
 };
 using CfgP10 = OzCfg<4, 4, 3, 3, false>;
 using CfgP13 = OzCfg<4, 4, 4, 3, false>;
+// short products (K <= 64: the Riccati update P - t Y Y^T): one stage, two accumulators,
+// 256 TMEM columns and about 100 KB of shared memory, so two CTAs share an SM and their
+// epilogues (which are the work here) overlap
+using CfgP10s = OzCfg<4, 4, 3, 1, false, 2>;
+using CfgP13s = OzCfg<4, 4, 4, 1, false, 2>;
+using CfgP14s = OzCfg<5, 4, 4, 1, false, 2>;
 using CfgP14 = OzCfg<5, 4, 4, 3, false>;
 using CfgA21 = OzCfg<6, 6, 5, 2, true>;
 static_assert(CfgP14::SMEM <= 232448 && CfgA21::SMEM <= 232448, "shared memory per CTA");
+static_assert(2 * CfgP14s::SMEM <= 232448 && 2 * CfgP10s::SMEM <= 232448, "two short CTAs per SM");
 
 int oz_cfg_pairs(int cfg) {
     switch (cfg) {
@@ -719,7 +730,7 @@ __device__ __forceinline__ void oz_persistent(int units, Resolve resolve) {
         fence_mbar_init();
     }
     if (warp == 1) {
-        tmem_alloc(smem_u32(tmem_slot), 512);
+        tmem_alloc(smem_u32(tmem_slot), Cfg::TMEM_COLS);
         tmem_relinquish();
     }
     fence_before_sync();
@@ -824,12 +835,12 @@ __device__ __forceinline__ void oz_persistent(int units, Resolve resolve) {
 #pragma unroll
                             for (int sb = 0; sb < Cfg::SB; ++sb) {
                                 if (sa + sb > Cfg::L) continue;
-                                const int lvl = (sa + sb < OZ_NACC - 1) ? sa + sb : OZ_NACC - 1;
+                                const int lvl = (sa + sb < Cfg::NACC - 1) ? sa + sb : Cfg::NACC - 1;
                                 const uint64_t ad = desc_kmajor_sw64(a0 + sa * OZ_SLICE_BYTES + kk * 32);
                                 const uint64_t bd = desc_kmajor_sw64(b0 + sb * OZ_SLICE_BYTES + kk * 32);
                                 // the pairs (0, t), t <= 3, come first and open accumulator t at the
                                 // unit's first k step; everything else accumulates
-                                const uint32_t acc = (it == 0 && kk == 0 && sa == 0 && sb < OZ_NACC) ? 0u : 1u;
+                                const uint32_t acc = (it == 0 && kk == 0 && sa == 0 && sb < Cfg::NACC) ? 0u : 1u;
                                 mma_bf16(tmem + (uint32_t)(lvl * OZ_BN), ad, bd, OZ_IDESC, acc);
                             }
                         }
@@ -888,8 +899,17 @@ __device__ __forceinline__ void oz_persistent(int units, Resolve resolve) {
                 continue;
             }
             uint32_t h0[32], l0[32], h1[32], l1[32];
-            oz_load_half(tmem, q, cq, h0, l0);
-            oz_load_half(tmem, q, cq + 32, h1, l1);
+            if (Cfg::NACC == 4) {
+                oz_load_half(tmem, q, cq, h0, l0);
+                oz_load_half(tmem, q, cq + 32, h1, l1);
+            } else {
+                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)cq;
+                tmem_ld_32x32b_x32(ta, h0);
+                tmem_ld_32x32b_x32(ta + OZ_BN, l0);
+                tmem_ld_32x32b_x32(ta + 32, h1);
+                tmem_ld_32x32b_x32(ta + OZ_BN + 32, l1);
+                tmem_ld_wait();
+            }
             // the accumulators are in registers: hand TMEM back to the MMA warp
             fence_before_sync();
             __syncwarp();
@@ -920,7 +940,7 @@ __device__ __forceinline__ void oz_persistent(int units, Resolve resolve) {
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    if (warp == 1) tmem_dealloc(tmem, 512);
+    if (warp == 1) tmem_dealloc(tmem, Cfg::TMEM_COLS);
 }
 
 template <class Cfg>
@@ -1132,11 +1152,18 @@ dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzPar
         }
         p.units = p.split_first + (tiles - p.split_first) * p.split_parts;
     }
-    const int grid = std::min(p.units, nsm);
+    const bool shortk = !acc && p.Kp <= 2 * OZ_BK;      // two CTAs per SM
+    const int grid = std::min(p.units, shortk ? 2 * nsm : nsm);
     switch (p.cfg) {
-        case OZ_P10: DME_TRY(oz_launch_single<CfgP10>(tA, tB, p, grid, st)); break;
-        case OZ_P13: DME_TRY(oz_launch_single<CfgP13>(tA, tB, p, grid, st)); break;
-        case OZ_P14: DME_TRY(oz_launch_single<CfgP14>(tA, tB, p, grid, st)); break;
+        case OZ_P10:
+            DME_TRY(shortk ? oz_launch_single<CfgP10s>(tA, tB, p, grid, st) : oz_launch_single<CfgP10>(tA, tB, p, grid, st));
+            break;
+        case OZ_P13:
+            DME_TRY(shortk ? oz_launch_single<CfgP13s>(tA, tB, p, grid, st) : oz_launch_single<CfgP13>(tA, tB, p, grid, st));
+            break;
+        case OZ_P14:
+            DME_TRY(shortk ? oz_launch_single<CfgP14s>(tA, tB, p, grid, st) : oz_launch_single<CfgP14>(tA, tB, p, grid, st));
+            break;
         case OZ_A21: DME_TRY(oz_launch_single<CfgA21>(tA, tB, p, grid, st)); break;
         default: return set_error("ozaki gemm: unknown configuration"), DME_EINVAL;
     }
