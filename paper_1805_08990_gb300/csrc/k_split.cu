@@ -64,6 +64,7 @@ struct OzCfg {
     // of at most 64 K, where the shared accumulator rounds at most four times)
     static constexpr int NACC = NACC_;
     static constexpr int TMEM_COLS = NACC * OZ_BN;
+    static constexpr int MIN_BLOCKS = NACC == 2 ? 2 : 1;            // CTAs per SM the registers allow
     static constexpr int A_BYTES = SA * OZ_SLICE_BYTES;
     static constexpr int STAGE_BYTES = (SA + SB) * OZ_SLICE_BYTES;
     // the staged epilogue when the buffer fits beside the stage ring
@@ -898,6 +899,26 @@ __device__ __forceinline__ void oz_persistent(int units, Resolve resolve) {
                 if (lane == 0) mbar_arrive(acc_empty);
                 continue;
             }
+            if (Cfg::NACC == 2) {
+                // short products (never split in K): 32 columns at a time, TMEM released at
+                // the end (the next unit's product is as short), so that the registers allow
+                // two CTAs per SM
+                const bool diag = p.tri && w.tm == w.tn;
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    uint32_t hs[32], ls[32];
+                    const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(cq + 32 * hh);
+                    tmem_ld_32x32b_x32(ta, hs);
+                    tmem_ld_32x32b_x32(ta + OZ_BN, ls);
+                    tmem_ld_wait();
+                    oz_store_staged(p, m0, n0, il, cq + 32 * hh, 0, diag, hs, ls, stage_T, ew, lane);
+                    oz_store_staged(p, m0, n0, il, cq + 32 * hh, 16, diag, hs, ls, stage_T, ew, lane);
+                }
+                fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acc_empty);
+                continue;
+            }
             uint32_t h0[32], l0[32], h1[32], l1[32];
             if (Cfg::NACC == 4) {
                 oz_load_half(tmem, q, cq, h0, l0);
@@ -944,7 +965,7 @@ __device__ __forceinline__ void oz_persistent(int units, Resolve resolve) {
 }
 
 template <class Cfg>
-__global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(OZ_THREADS, Cfg::MIN_BLOCKS) ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                    const __grid_constant__ CUtensorMap tmB,
                                                                    const __grid_constant__ OzParams p) {
     oz_persistent<Cfg>(p.units, [&](int u, OzUnit& o) { oz_single_unit(&p, &tmA, &tmB, Cfg::ACC, u, o); });
@@ -1152,7 +1173,7 @@ dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzPar
         }
         p.units = p.split_first + (tiles - p.split_first) * p.split_parts;
     }
-    const bool shortk = !acc && p.Kp <= 2 * OZ_BK;      // two CTAs per SM
+    const bool shortk = !acc && p.Kp <= 2 * OZ_BK;      // two CTAs per SM (never split: Kp / 32 < 16)
     const int grid = std::min(p.units, shortk ? 2 * nsm : nsm);
     switch (p.cfg) {
         case OZ_P10:
