@@ -1173,7 +1173,10 @@ dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzPar
         }
         p.units = p.split_first + (tiles - p.split_first) * p.split_parts;
     }
-    const bool shortk = !acc && p.Kp <= 2 * OZ_BK;      // two CTAs per SM (never split: Kp / 32 < 16)
+    // short and wide products (the Riccati update of large plans): two CTAs per SM (never
+    // split: Kp / 32 < 16).  Narrower ones keep the four accumulators, so that a plan's
+    // products round exactly as the grouped serving kernel's.
+    const bool shortk = !acc && p.Kp <= 2 * OZ_BK && tiles > nsm;
     const int grid = std::min(p.units, shortk ? 2 * nsm : nsm);
     switch (p.cfg) {
         case OZ_P10:
