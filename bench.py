@@ -41,10 +41,11 @@ NOMINAL_FP64_TFLOPS = 1.25    # GB300 FP64 (non-tensor and tensor), the profilin
 
 FP64_MAX_STEPS = 16
 
-# DRAM bytes (read + write) of one full 4096^3 launch of the tensor kernel as it is
-# now, from the ncu capture summarised in profiles/ozaki_gemm_n4096_ncu.md; None while
-# the kernel has changed since the last capture.
-OZAKI_FULL_LAUNCH_DRAM_BYTES = None
+# DRAM bytes (read + write) per launch of the tensor kernel in the congruence at n = 4096
+# (10 slice products), the mean of its two launches (U = G P: 871.8 + 157.5 MB; the
+# triangle G U^T: 656.3 + 122.5 MB), from the ncu capture summarised in
+# profiles/ozaki_gemm_n4096_ncu.md; None while the kernel has changed since that capture.
+OZAKI_LAUNCH_DRAM_BYTES = 0.5 * ((871.8 + 157.5) + (656.3 + 122.5)) * 1e6
 
 
 def load_peaks():
@@ -400,9 +401,10 @@ def roofline_split(n, avg_ms, pairs, peak, peak_src, traffic, cong_ms, slice_ms)
     pipe = pairs * 3.0 * n ** 3 / 2 / (avg_ms / 1e3) / 1e12
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic,
-            "traffic_of": "one full n = 4096 product of the tensor kernel (dram__bytes_read.sum + "
-                          "dram__bytes_write.sum, ncu, profiles/ozaki_gemm_n4096_ncu.md), or null when the kernel "
-                          "changed since that capture",
+            "traffic_of": "dram__bytes_read.sum + dram__bytes_write.sum per launch of the tensor kernel in the "
+                          "n = 4096 congruence (mean of U = G P and the triangle G U^T; ncu, "
+                          "profiles/ozaki_gemm_n4096_ncu.md); algorithmic bytes per launch: slices of A and B "
+                          "268 MB + output 134 MB",
             "kernel": "ozaki_gemm_kernel (tcgen05 kind::f16, 2 launches per congruence)",
             "work": "algorithmic: 6 bf16 products x (2n^3 + n^3) per congruence = 9 n^3 tensor flops per launch",
             "peak_source": f"bf16 dense burst, {peak_src} (MEASURED_PEAKS.json)",
@@ -550,7 +552,7 @@ def run_ours(args):
                 "peak_source": "nominal GB300 FP64 rate (profiling recipe table)"}
     else:
         avg_ms = r["kernel_ms"] / max(r["kernel_launches"], 1)
-        roof = roofline_split(n, avg_ms, r["pairs"], peaks["bf16_tflops"], peaks_src, OZAKI_FULL_LAUNCH_DRAM_BYTES,
+        roof = roofline_split(n, avg_ms, r["pairs"], peaks["bf16_tflops"], peaks_src, OZAKI_LAUNCH_DRAM_BYTES,
                               r["cong_ms"], r["slice_ms"] / max(r["R"], 1))
     med_step = statistics.median(r["per_step_ms"])
     line = {

@@ -77,6 +77,9 @@ using CfgP13 = OzCfg<4, 4, 4, 3, false>;
 // short products (K <= 64: the Riccati update P - t Y Y^T): one stage, two accumulators,
 // 256 TMEM columns and about 100 KB of shared memory, so two CTAs share an SM and their
 // epilogues (which are the work here) overlap
+// 14 products for at most one wave of tiles (latency-bound, nothing to overlap the epilogue
+// with): two stages, so that the staged epilogue fits beside them (same arithmetic as CfgP14)
+using CfgP14e = OzCfg<5, 4, 4, 2, false>;
 using CfgP10s = OzCfg<4, 4, 3, 1, false, 2>;
 using CfgP13s = OzCfg<4, 4, 4, 1, false, 2>;
 using CfgP14s = OzCfg<5, 4, 4, 1, false, 2>;
@@ -84,6 +87,7 @@ using CfgP14 = OzCfg<5, 4, 4, 3, false>;
 using CfgA21 = OzCfg<6, 6, 5, 2, true>;
 static_assert(CfgP14::SMEM <= 232448 && CfgA21::SMEM <= 232448, "shared memory per CTA");
 static_assert(2 * CfgP14s::SMEM <= 232448 && 2 * CfgP10s::SMEM <= 232448, "two short CTAs per SM");
+static_assert(CfgP14e::STAGED_EPI, "the one-wave 14-product variant stages its epilogue");
 
 int oz_cfg_pairs(int cfg) {
     switch (cfg) {
@@ -1186,7 +1190,9 @@ dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzPar
             DME_TRY(shortk ? oz_launch_single<CfgP13s>(tA, tB, p, grid, st) : oz_launch_single<CfgP13>(tA, tB, p, grid, st));
             break;
         case OZ_P14:
-            DME_TRY(shortk ? oz_launch_single<CfgP14s>(tA, tB, p, grid, st) : oz_launch_single<CfgP14>(tA, tB, p, grid, st));
+            if (shortk) DME_TRY(oz_launch_single<CfgP14s>(tA, tB, p, grid, st));
+            else if (p.units <= nsm) DME_TRY(oz_launch_single<CfgP14e>(tA, tB, p, grid, st));
+            else DME_TRY(oz_launch_single<CfgP14>(tA, tB, p, grid, st));
             break;
         case OZ_A21: DME_TRY(oz_launch_single<CfgA21>(tA, tB, p, grid, st)); break;
         default: return set_error("ozaki gemm: unknown configuration"), DME_EINVAL;
@@ -1215,7 +1221,7 @@ static dme_status oz_grouped_attr() {
 dme_status ozaki_grouped_prepare() {
     DME_TRY(oz_grouped_attr<CfgP10>());
     DME_TRY(oz_grouped_attr<CfgP13>());
-    DME_TRY(oz_grouped_attr<CfgP14>());
+    DME_TRY(oz_grouped_attr<CfgP14e>());
     return DME_OK;
 }
 
@@ -1260,8 +1266,8 @@ dme_status launch_ozaki_grouped(std::vector<OzGroupDesc>& items, OzGroupDesc* de
         case OZ_P13:
             ozaki_gemm_grouped_kernel<CfgP13><<<grid, OZ_THREADS, CfgP13::SMEM, st>>>(d, nd, total);
             break;
-        default:
-            ozaki_gemm_grouped_kernel<CfgP14><<<grid, OZ_THREADS, CfgP14::SMEM, st>>>(d, nd, total);
+        default:   // serving problems are small: the staged two-stage form of 14 products
+            ozaki_gemm_grouped_kernel<CfgP14e><<<grid, OZ_THREADS, CfgP14e::SMEM, st>>>(d, nd, total);
             break;
     }
     DME_CUDA_TRY(cudaGetLastError());
