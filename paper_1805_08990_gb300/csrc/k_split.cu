@@ -56,7 +56,7 @@ constexpr uint32_t OZ_IDESC = idesc_bf16_f32(OZ_BM, OZ_BN);
 // stride 129 words), through which the epilogue writes row segments coalesced.
 constexpr int OZ_EPI_STAGE_BYTES = 32 * (OZ_BM + 1) * 8;
 
-template <int SA_, int SB_, int L_, int STAGES_, bool ACC_, int NACC_ = 4>
+template <int SA_, int SB_, int L_, int STAGES_, bool ACC_, int NACC_ = 4, bool ONE_UNIT_ = false>
 struct OzCfg {
     static constexpr int SA = SA_, SB = SB_, L = L_, STAGES = STAGES_;
     static constexpr bool ACC = ACC_;                                // accurate mode (exact chunks)
@@ -67,9 +67,13 @@ struct OzCfg {
     static constexpr int MIN_BLOCKS = NACC == 2 ? 2 : 1;            // CTAs per SM the registers allow
     static constexpr int A_BYTES = SA * OZ_SLICE_BYTES;
     static constexpr int STAGE_BYTES = (SA + SB) * OZ_SLICE_BYTES;
-    // the staged epilogue when the buffer fits beside the stage ring
-    static constexpr bool STAGED_EPI = !ACC && STAGES * STAGE_BYTES + OZ_EPI_STAGE_BYTES + 1024 + 256 <= 232448;
-    static constexpr int EPI_BYTES = STAGED_EPI ? OZ_EPI_STAGE_BYTES : 0;
+    // launches where every CTA computes exactly one unit: the epilogue's staging buffer
+    // lives in the stage ring, idle once the unit's MMAs are done
+    static constexpr bool ONE_UNIT = ONE_UNIT_;
+    // the staged epilogue when the buffer fits beside the stage ring (or in it)
+    static constexpr bool STAGED_EPI =
+        !ACC && (ONE_UNIT || STAGES * STAGE_BYTES + OZ_EPI_STAGE_BYTES + 1024 + 256 <= 232448);
+    static constexpr int EPI_BYTES = (STAGED_EPI && !ONE_UNIT) ? OZ_EPI_STAGE_BYTES : 0;
     static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_BYTES + 1024 + 256;
 };
 using CfgP10 = OzCfg<4, 4, 3, 3, false>;
@@ -80,6 +84,9 @@ using CfgP13 = OzCfg<4, 4, 4, 3, false>;
 // 14 products for at most one wave of tiles (latency-bound, nothing to overlap the epilogue
 // with): two stages, so that the staged epilogue fits beside them (same arithmetic as CfgP14)
 using CfgP14e = OzCfg<5, 4, 4, 2, false>;
+// 14 products, one tile per CTA (single-problem launches of at most one wave): three stages,
+// the staging buffer in the ring
+using CfgP14w = OzCfg<5, 4, 4, 3, false, 4, true>;
 using CfgP10s = OzCfg<4, 4, 3, 1, false, 2>;
 using CfgP13s = OzCfg<4, 4, 4, 1, false, 2>;
 using CfgP14s = OzCfg<5, 4, 4, 1, false, 2>;
@@ -87,7 +94,8 @@ using CfgP14 = OzCfg<5, 4, 4, 3, false>;
 using CfgA21 = OzCfg<6, 6, 5, 2, true>;
 static_assert(CfgP14::SMEM <= 232448 && CfgA21::SMEM <= 232448, "shared memory per CTA");
 static_assert(2 * CfgP14s::SMEM <= 232448 && 2 * CfgP10s::SMEM <= 232448, "two short CTAs per SM");
-static_assert(CfgP14e::STAGED_EPI, "the one-wave 14-product variant stages its epilogue");
+static_assert(CfgP14e::STAGED_EPI && CfgP14w::STAGED_EPI && CfgP14w::SMEM <= 232448, "staged 14-product forms");
+static_assert(OZ_EPI_STAGE_BYTES <= 3 * 73728, "the staging buffer fits in the ring");
 
 int oz_cfg_pairs(int cfg) {
     switch (cfg) {
@@ -714,7 +722,7 @@ template <class Cfg, class Resolve>
 __device__ __forceinline__ void oz_persistent(int units, Resolve resolve) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* stage_T = reinterpret_cast<uint64_t*>(smem + Cfg::STAGES * Cfg::STAGE_BYTES);
+    uint64_t* stage_T = reinterpret_cast<uint64_t*>(Cfg::ONE_UNIT ? smem : smem + Cfg::STAGES * Cfg::STAGE_BYTES);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::STAGES * Cfg::STAGE_BYTES + Cfg::EPI_BYTES);
     // bars[0..S): full, [S..2S): empty, [2S]: accumulators full, [2S+1]: accumulators
     // empty, [2S+2]: drain (every MMA done before TMEM is freed)
@@ -1191,7 +1199,7 @@ dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzPar
             break;
         case OZ_P14:
             if (shortk) DME_TRY(oz_launch_single<CfgP14s>(tA, tB, p, grid, st));
-            else if (p.units <= nsm) DME_TRY(oz_launch_single<CfgP14e>(tA, tB, p, grid, st));
+            else if (p.units <= nsm) DME_TRY(oz_launch_single<CfgP14w>(tA, tB, p, grid, st));   // grid = units
             else DME_TRY(oz_launch_single<CfgP14>(tA, tB, p, grid, st));
             break;
         case OZ_A21: DME_TRY(oz_launch_single<CfgA21>(tA, tB, p, grid, st)); break;

@@ -561,16 +561,6 @@ __global__ void __launch_bounds__(256) gemv_rows_kernel(const double* __restrict
     }
 }
 
-// z = M^T y: a thread per column (coalesced over the columns of each row).
-__global__ void __launch_bounds__(256) gemv_cols_kernel(const double* __restrict__ M, const double* __restrict__ y,
-                                                        int n, double* __restrict__ z) {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-        double a = 0.0;
-        for (int r = 0; r < n; ++r) a += M[(size_t)r * n + c] * y[r];
-        z[c] = a;
-    }
-}
-
 // One block: rq[0] = x . z (the Rayleigh quotient of M^T M at the unit x), then
 // x = z / ||z|| (fixed-order reductions; x left unchanged if z = 0).
 __global__ void __launch_bounds__(1024) rayleigh_normalize_kernel(double* __restrict__ x,
@@ -601,23 +591,25 @@ __global__ void __launch_bounds__(1024) rayleigh_normalize_kernel(double* __rest
 }
 
 // Doubles of norm2_sq's work vector.
-size_t norm2_work_doubles(int n) { return 3 * (size_t)n + 2; }
+size_t norm2_work_doubles(int n) { return (size_t)n * n + 3 * (size_t)n + 2; }
 
 // The largest eigenvalue of M^T M (M n x n), i.e. ||M||_2^2, by 20 steps of the
 // power iteration from the unit vector of equal entries, returned as the last
 // Rayleigh quotient: an estimate from below that converges to the eigenvalue.
-// work: norm2_work_doubles(n) doubles (x, y, z and two scalars).
+// work: norm2_work_doubles(n) doubles (M^T, x, y, z and two scalars).
 dme_status norm2_sq(const double* M, int n, double* work, size_t work_len, cudaStream_t st, double* out) {
     if (work_len < norm2_work_doubles(n)) return set_error("norm2_sq: work vector too short"), DME_EINVAL;
-    double* x = work;
+    double* Mt = work;
+    double* x = Mt + (size_t)n * n;
     double* y = x + n;
     double* z = y + n;
     double* s = z + n;
-    const int gr = std::min((n + 7) / 8, 1024), gc = std::min((n + 255) / 256, 1024);
+    const int gr = std::min((n + 7) / 8, 1024);
+    launch_transpose(M, Mt, n, n, n, n, st);
     fill_kernel<<<(n + 255) / 256, 256, 0, st>>>(x, n, 1.0 / std::sqrt((double)n));
     for (int it = 0; it < 20; ++it) {
         gemv_rows_kernel<<<gr, 256, 0, st>>>(M, x, n, y);                     // y = M x
-        gemv_cols_kernel<<<gc, 256, 0, st>>>(M, y, n, z);                     // z = M^T y
+        gemv_rows_kernel<<<gr, 256, 0, st>>>(Mt, y, n, z);                    // z = M^T y
         rayleigh_normalize_kernel<<<1, 1024, 0, st>>>(x, z, n, s);            // rq = x.z; x = z/|z|
     }
     DME_CUDA_TRY(cudaGetLastError());
