@@ -56,7 +56,7 @@ constexpr uint32_t OZ_IDESC = idesc_bf16_f32(OZ_BM, OZ_BN);
 // stride 129 words), through which the epilogue writes row segments coalesced.
 constexpr int OZ_EPI_STAGE_BYTES = 32 * (OZ_BM + 1) * 8;
 
-template <int SA_, int SB_, int L_, int STAGES_, bool ACC_, int NACC_ = 4, bool ONE_UNIT_ = false>
+template <int SA_, int SB_, int L_, int STAGES_, bool ACC_, int NACC_ = 4>
 struct OzCfg {
     static constexpr int SA = SA_, SB = SB_, L = L_, STAGES = STAGES_;
     static constexpr bool ACC = ACC_;                                // accurate mode (exact chunks)
@@ -67,13 +67,9 @@ struct OzCfg {
     static constexpr int MIN_BLOCKS = NACC == 2 ? 2 : 1;            // CTAs per SM the registers allow
     static constexpr int A_BYTES = SA * OZ_SLICE_BYTES;
     static constexpr int STAGE_BYTES = (SA + SB) * OZ_SLICE_BYTES;
-    // launches where every CTA computes exactly one unit: the epilogue's staging buffer
-    // lives in the stage ring, idle once the unit's MMAs are done
-    static constexpr bool ONE_UNIT = ONE_UNIT_;
-    // the staged epilogue when the buffer fits beside the stage ring (or in it)
-    static constexpr bool STAGED_EPI =
-        !ACC && (ONE_UNIT || STAGES * STAGE_BYTES + OZ_EPI_STAGE_BYTES + 1024 + 256 <= 232448);
-    static constexpr int EPI_BYTES = (STAGED_EPI && !ONE_UNIT) ? OZ_EPI_STAGE_BYTES : 0;
+    // the staged epilogue when the buffer fits beside the stage ring
+    static constexpr bool STAGED_EPI = !ACC && STAGES * STAGE_BYTES + OZ_EPI_STAGE_BYTES + 1024 + 256 <= 232448;
+    static constexpr int EPI_BYTES = STAGED_EPI ? OZ_EPI_STAGE_BYTES : 0;
     static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_BYTES + 1024 + 256;
 };
 using CfgP10 = OzCfg<4, 4, 3, 3, false>;
@@ -84,9 +80,6 @@ using CfgP13 = OzCfg<4, 4, 4, 3, false>;
 // 14 products for at most one wave of tiles (latency-bound, nothing to overlap the epilogue
 // with): two stages, so that the staged epilogue fits beside them (same arithmetic as CfgP14)
 using CfgP14e = OzCfg<5, 4, 4, 2, false>;
-// 14 products, one tile per CTA (single-problem launches of at most one wave): three stages,
-// the staging buffer in the ring
-using CfgP14w = OzCfg<5, 4, 4, 3, false, 4, true>;
 using CfgP10s = OzCfg<4, 4, 3, 1, false, 2>;
 using CfgP13s = OzCfg<4, 4, 4, 1, false, 2>;
 using CfgP14s = OzCfg<5, 4, 4, 1, false, 2>;
@@ -94,8 +87,7 @@ using CfgP14 = OzCfg<5, 4, 4, 3, false>;
 using CfgA21 = OzCfg<6, 6, 5, 2, true>;
 static_assert(CfgP14::SMEM <= 232448 && CfgA21::SMEM <= 232448, "shared memory per CTA");
 static_assert(2 * CfgP14s::SMEM <= 232448 && 2 * CfgP10s::SMEM <= 232448, "two short CTAs per SM");
-static_assert(CfgP14e::STAGED_EPI && CfgP14w::STAGED_EPI && CfgP14w::SMEM <= 232448, "staged 14-product forms");
-static_assert(OZ_EPI_STAGE_BYTES <= 3 * 73728, "the staging buffer fits in the ring");
+static_assert(CfgP14e::STAGED_EPI, "the two-stage 14-product form stages its epilogue");
 
 int oz_cfg_pairs(int cfg) {
     switch (cfg) {
@@ -722,7 +714,7 @@ template <class Cfg, class Resolve>
 __device__ __forceinline__ void oz_persistent(int units, Resolve resolve) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* stage_T = reinterpret_cast<uint64_t*>(Cfg::ONE_UNIT ? smem : smem + Cfg::STAGES * Cfg::STAGE_BYTES);
+    uint64_t* stage_T = reinterpret_cast<uint64_t*>(smem + Cfg::STAGES * Cfg::STAGE_BYTES);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::STAGES * Cfg::STAGE_BYTES + Cfg::EPI_BYTES);
     // bars[0..S): full, [S..2S): empty, [2S]: accumulators full, [2S+1]: accumulators
     // empty, [2S+2]: drain (every MMA done before TMEM is freed)
@@ -781,12 +773,10 @@ __device__ __forceinline__ void oz_persistent(int units, Resolve resolve) {
                     uint8_t* st = smem + s * Cfg::STAGE_BYTES;
                     const int kc = (w.kb0 + it) * OZ_BK;
                     mbar_arrive_expect_tx(full, Cfg::STAGE_BYTES);
-#pragma unroll
-                    for (int sa = 0; sa < Cfg::SA; ++sa)
-                        tma_load_3d(smem_u32(st + sa * OZ_SLICE_BYTES), w.tA, full, kc, m0, sa);
-#pragma unroll
-                    for (int sb = 0; sb < Cfg::SB; ++sb)
-                        tma_load_3d(smem_u32(st + Cfg::A_BYTES + sb * OZ_SLICE_BYTES), w.tB, full, kc, n0, sb);
+                    // one box per operand: the 32 x 128 tile of each of its SA (SB) planes,
+                    // planes 8 KB apart in the stage
+                    tma_load_3d(smem_u32(st), w.tA, full, kc, m0, 0);
+                    tma_load_3d(smem_u32(st + Cfg::A_BYTES), w.tB, full, kc, n0, 0);
                     issued |= 1u << s;
                     last_ph = (last_ph & ~(1u << s)) | (ph << s);
                     // pull the epilogue's addend rows into L2: spread over the K loop, and all
@@ -1075,11 +1065,11 @@ static dme_status get_encoder() {
     return DME_OK;
 }
 
-dme_status make_slice_tmap(const SliceBuf& sb, CUtensorMap* out) {
+static dme_status make_slice_tmap(const SliceBuf& sb, int planes, CUtensorMap* out) {
     DME_TRY(get_encoder());
     cuuint64_t dims[3] = {(cuuint64_t)sb.Kp, (cuuint64_t)sb.rows, (cuuint64_t)sb.ns};
     cuuint64_t strides[2] = {(cuuint64_t)sb.Kp * 2, (cuuint64_t)sb.rows * sb.Kp * 2};
-    cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)OZ_BM, 1};
+    cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)OZ_BM, (cuuint32_t)planes};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = g_encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)sb.data, dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
@@ -1088,6 +1078,13 @@ dme_status make_slice_tmap(const SliceBuf& sb, CUtensorMap* out) {
         set_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
         return DME_ECUDA;
     }
+    return DME_OK;
+}
+
+dme_status make_slice_tmaps(SliceBuf& sb) {
+    if (sb.ns < 1 || sb.ns > 8) return set_error("slice buffer: 1 to 8 planes"), DME_EINVAL;
+    DME_TRY(make_slice_tmap(sb, sb.ns, &sb.tmap));
+    if (sb.ns > 4) DME_TRY(make_slice_tmap(sb, 4, &sb.tmap4));
     return DME_OK;
 }
 
@@ -1100,6 +1097,10 @@ dme_status oz_params(const SliceBuf& A, const SliceBuf& B, int cfg, OzParams* p)
     if (A.ns < oz_cfg_slices_a(cfg) || B.ns < oz_cfg_slices_b(cfg) || A.scheme != oz_cfg_scheme(cfg) ||
         B.scheme != oz_cfg_scheme(cfg) || A.Kp != B.Kp)
         return set_error("split gemm: the slice buffers do not hold what the configuration reads"), DME_EINVAL;
+    // a buffer with more planes than read is addressed through its four-plane map
+    if ((A.ns > oz_cfg_slices_a(cfg) && oz_cfg_slices_a(cfg) != 4) ||
+        (B.ns > oz_cfg_slices_b(cfg) && oz_cfg_slices_b(cfg) != 4))
+        return set_error("split gemm: no tensor map spans the planes the configuration reads"), DME_EINVAL;
     std::memset(p, 0, sizeof(*p));
     p->M = A.rows;
     p->N = B.rows;
@@ -1199,7 +1200,7 @@ dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzPar
             break;
         case OZ_P14:
             if (shortk) DME_TRY(oz_launch_single<CfgP14s>(tA, tB, p, grid, st));
-            else if (p.units <= nsm) DME_TRY(oz_launch_single<CfgP14w>(tA, tB, p, grid, st));   // grid = units
+            else if (p.units <= nsm) DME_TRY(oz_launch_single<CfgP14e>(tA, tB, p, grid, st));
             else DME_TRY(oz_launch_single<CfgP14>(tA, tB, p, grid, st));
             break;
         case OZ_A21: DME_TRY(oz_launch_single<CfgA21>(tA, tB, p, grid, st)); break;
@@ -1360,8 +1361,8 @@ extern "C" dme_status dme_gemm_split_noalloc(int M, int N, int K, const double* 
         sb.ns = OZ_SLICES_STEP;
         sb.scale = reinterpret_cast<float*>(base + off_sb);
         sb.data = reinterpret_cast<__nv_bfloat16*>(base + off_b);
-        DME_TRY(make_slice_tmap(sa, &sa.tmap));
-        DME_TRY(make_slice_tmap(sb, &sb.tmap));
+        DME_TRY(make_slice_tmaps(sa));
+        DME_TRY(make_slice_tmaps(sb));
         // the array keeps the previous call's contents: the status word must start at zero
         // (slices, padding and scales are rewritten in full below)
         DME_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
@@ -1373,7 +1374,7 @@ extern "C" dme_status dme_gemm_split_noalloc(int M, int N, int K, const double* 
         o.ldc = N;
         o.Cd = C;
         o.status = status;
-        DME_TRY(launch_ozaki_gemm(sa.tmap, sb.tmap, o, st));
+        DME_TRY(launch_ozaki_gemm(oz_tmap_a(sa, OZ_P14), oz_tmap_b(sb, OZ_P14), o, st));
         int hs = 0;
         DME_CUDA_TRY(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
         DME_CUDA_TRY(cudaStreamSynchronize(st));

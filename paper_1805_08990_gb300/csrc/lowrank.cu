@@ -477,7 +477,7 @@ dme_status apply_split(dme_lr_t lr, const SliceBuf& Msl, const double* X, int ld
     p.status = lr->status;
     p.ws = lr->P->kws;
     p.ws_cnt = lr->P->kcnt;
-    return launch_ozaki_gemm(Msl.tmap, lr->xsl.tmap, p, st);
+    return launch_ozaki_gemm(oz_tmap_a(Msl, OZ_P14), oz_tmap_b(lr->xsl, OZ_P14), p, st);
 }
 
 dme_status lr_T1(dme_lr_t lr, double tau) {
@@ -691,7 +691,7 @@ dme_status lr_setup(dme_lr_t lr, const dme_plan_desc* desc, const double* C, int
         lr->xsl.scale = reinterpret_cast<float*>(xs);
         DME_CUDA_TRY(cudaMemsetAsync(xd, 0, slice_buf_bytes((int)rc, (int)n, OZ_SLICES_STEP), st));
         DME_CUDA_TRY(cudaMemsetAsync(xs, 0, sizeof(float) * rc, st));
-        DME_TRY(make_slice_tmap(lr->xsl, &lr->xsl.tmap));
+        DME_TRY(make_slice_tmaps(lr->xsl));
     }
     double* kd = nullptr;
     DME_TRY(lr_alloc(lr, &kd, 1));

@@ -191,7 +191,7 @@ dme_status acc_prod(int n, AccWork& w, const double* L, int tL, const double* R,
     o.b1 = b1;
     o.wsd = w.wsd;
     o.status = w.status;
-    return launch_ozaki_gemm(w.a.tmap, w.b.tmap, o, st);
+    return launch_ozaki_gemm(oz_tmap_a(w.a, OZ_A21), oz_tmap_b(w.b, OZ_A21), o, st);
 }
 
 // Scratch of the accurate mode for n x n products, from a plan-time pool.
@@ -215,8 +215,8 @@ dme_status acc_setup(TmpPool& tp, int n, int* status, AccWork* w) {
     w->b.data = reinterpret_cast<__nv_bfloat16*>(bd);
     w->a.scale = reinterpret_cast<float*>(sc);
     w->b.scale = reinterpret_cast<float*>(sc) + n;
-    DME_TRY(make_slice_tmap(w->a, &w->a.tmap));
-    DME_TRY(make_slice_tmap(w->b, &w->b.tmap));
+    DME_TRY(make_slice_tmaps(w->a));
+    DME_TRY(make_slice_tmaps(w->b));
     w->status = status;
     return DME_OK;
 }
@@ -276,7 +276,7 @@ dme_status alloc_slices(dme_plan_t p, SliceBuf* sb, int rows, int k, int ns, int
     sb->scheme = scheme;
     DME_TRY(palloc(p, reinterpret_cast<void**>(&sb->data), slice_buf_bytes(rows, k, ns)));
     DME_TRY(palloc_t(p, &sb->scale, (size_t)rows));
-    return make_slice_tmap(*sb, &sb->tmap);
+    return make_slice_tmaps(*sb);
 }
 
 // out = alpha G P G^T + b1 D1 + b2 D2 + b3 D3 on the split-precision path (P
@@ -300,7 +300,7 @@ dme_status split_cong(dme_plan_t p, const double* P, const SliceBuf& G, double* 
     a.ws_cnt = p->kcnt;
     {
         ProfScope ps(p, DME_KIND_SPLIT_GEMM);
-        DME_TRY(launch_ozaki_gemm(G.tmap, p->psl.tmap, a, st));
+        DME_TRY(launch_ozaki_gemm(oz_tmap_a(G, cfg), oz_tmap_b(p->psl, cfg), a, st));
     }
     {
         ProfScope ps(p, DME_KIND_SLICE);
@@ -323,7 +323,7 @@ dme_status split_cong(dme_plan_t p, const double* P, const SliceBuf& G, double* 
     b.ws = p->kws;
     b.ws_cnt = p->kcnt;
     ProfScope ps(p, DME_KIND_SPLIT_GEMM);
-    return launch_ozaki_gemm(G.tmap, p->usl.tmap, b, st);
+    return launch_ozaki_gemm(oz_tmap_a(G, cfg), oz_tmap_b(p->usl, cfg), b, st);
 }
 
 // T3 on the split path for n > 1536: Z^T = Bt^T P (P symmetric) on the tensor
@@ -346,7 +346,7 @@ dme_status split_riccati(dme_plan_t p, double* P, double tau, double qcoef) {
     a.status = p->status;
     a.ws = p->kws;
     a.ws_cnt = p->kcnt;
-    DME_TRY(launch_ozaki_gemm(p->btsl.tmap, p->psl.tmap, a, st));
+    DME_TRY(launch_ozaki_gemm(oz_tmap_a(p->btsl, p->cfg), oz_tmap_b(p->psl, p->cfg), a, st));
     launch_transpose(p->Zt, Z, m, n, n, m, st);
     DME_TRY(launch_riccati_from_z(p->Bt, n, m, tau, p->rwork, p->status, st));
     launch_slice_rows_f64(Y, n, m, m, p->ysla, st);
@@ -365,7 +365,7 @@ dme_status split_riccati(dme_plan_t p, double* P, double tau, double qcoef) {
         b.b2 = qcoef;
     }
     b.status = p->status;
-    return launch_ozaki_gemm(p->ysla.tmap, p->yslb.tmap, b, st);
+    return launch_ozaki_gemm(oz_tmap_a(p->ysla, p->cfg), oz_tmap_b(p->yslb, p->cfg), b, st);
 }
 
 dme_status compute_ew(dme_plan_t p, double tau, int* idx) {
@@ -1539,7 +1539,7 @@ static dme_status gemm_split_impl(int M, int N, int K, const double* A, const do
             (s = get(sizeof(float) * M, reinterpret_cast<void**>(&sa.scale))) != DME_OK ||
             (s = get(sizeof(float) * N, reinterpret_cast<void**>(&sb.scale))) != DME_OK ||
             (s = get(sizeof(int), reinterpret_cast<void**>(&status))) != DME_OK ||
-            (s = make_slice_tmap(sa, &sa.tmap)) != DME_OK || (s = make_slice_tmap(sb, &sb.tmap)) != DME_OK) {
+            (s = make_slice_tmaps(sa)) != DME_OK || (s = make_slice_tmaps(sb)) != DME_OK) {
             cleanup();
             return s;
         }
@@ -1558,7 +1558,7 @@ static dme_status gemm_split_impl(int M, int N, int K, const double* A, const do
         o.Cd = C;
         o.status = status;
         o.wsd = wsd;
-        if (s == DME_OK) s = launch_ozaki_gemm(sa.tmap, sb.tmap, o, st);
+        if (s == DME_OK) s = launch_ozaki_gemm(oz_tmap_a(sa, o.cfg), oz_tmap_b(sb, o.cfg), o, st);
         int hs = 0;
         if (s == DME_OK) {
             cudaError_t e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);

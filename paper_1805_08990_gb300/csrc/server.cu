@@ -394,8 +394,8 @@ dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
                 const int n = p->n;
                 OzGroupDesc a;
                 std::memset(&a, 0, sizeof(a));
-                a.tmA = e.Gsl.tmap;
-                a.tmB = p->psl.tmap;
+                a.tmA = oz_tmap_a(e.Gsl, p->cfg);
+                a.tmB = oz_tmap_b(p->psl, p->cfg);
                 DME_TRY(oz_params(e.Gsl, p->psl, p->cfg, &a.p));
                 a.p.mode = OZ_OUT_PAIR;
                 a.p.ldc = n;
@@ -404,8 +404,8 @@ dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
                 o1c[p->cfg].push_back(a);
                 OzGroupDesc b;
                 std::memset(&b, 0, sizeof(b));
-                b.tmA = e.Gsl.tmap;
-                b.tmB = p->usl.tmap;
+                b.tmA = oz_tmap_a(e.Gsl, p->cfg);
+                b.tmB = oz_tmap_b(p->usl, p->cfg);
                 DME_TRY(oz_params(e.Gsl, p->usl, p->cfg, &b.p));
                 b.p.mode = OZ_OUT_F64;
                 b.p.tri = 1;

@@ -44,14 +44,16 @@ int oz_cfg_scheme(int cfg);         // OZ_DIG9 or OZ_DIG7
 enum { OZ_OUT_PAIR = 0, OZ_OUT_F64 = 1 };
 
 // Slices of a rows x k operand: planes [ns][rows][Kp] bf16 (Kp = k rounded
-// up to 32, zero padded) and one power-of-two scale per row.  The tensor map
-// addresses one plane per load (box 32 x 128 x 1).
+// up to 32, zero padded) and one power-of-two scale per row.  A tensor-map load
+// brings a 32 x 128 tile of every plane a configuration reads (box 32 x 128 x
+// planes): tmap spans all ns planes, tmap4 the first four (when ns > 4).
 struct SliceBuf {
     __nv_bfloat16* data = nullptr;
     float* scale = nullptr;
     int rows = 0, k = 0, Kp = 0, ns = 0;
     int scheme = OZ_DIG9;
     CUtensorMap tmap;
+    CUtensorMap tmap4;
 };
 
 struct OzParams {
@@ -111,7 +113,15 @@ struct SliceDesc {
 
 int slice_kpad(int k);
 size_t slice_buf_bytes(int rows, int k, int ns);
-dme_status make_slice_tmap(const SliceBuf& sb, CUtensorMap* out);
+// Encode sb.tmap and (ns > 4) sb.tmap4.
+dme_status make_slice_tmaps(SliceBuf& sb);
+// The tensor map of A's (or B's) slices whose box spans the planes configuration cfg reads.
+inline const CUtensorMap& oz_tmap_a(const SliceBuf& A, int cfg) {
+    return A.ns > oz_cfg_slices_a(cfg) ? A.tmap4 : A.tmap;
+}
+inline const CUtensorMap& oz_tmap_b(const SliceBuf& B, int cfg) {
+    return B.ns > oz_cfg_slices_b(cfg) ? B.tmap4 : B.tmap;
+}
 // Slice the rows of X (rows x cols, leading dimension ldx; rows <= sb.rows) into sb
 // (planes and digit scheme of sb: DIG9 with 4 or 5, DIG7 with 6; each plane holds
 // sb.rows rows, the ones past `rows` untouched).
