@@ -339,8 +339,11 @@ dme_status dme_gemm_split_acc(int M, int N, int K, const double* A, const double
 /* B <- M^{-1} B for a dense n x n M and an n x nrhs B (float64, row-major,
  * host or device memory; M is copied and left unchanged): Gauss-Jordan
  * elimination with partial pivoting (largest |entry| of the column, the
- * smallest row on ties) in one cooperative launch with one grid barrier per
- * column, the kernel of the plan's Pade step (the denominator systems
+ * smallest row on ties), blocked by panels of 16 columns whose trailing
+ * update is one pass over the remaining columns (n <= 4096: three launches
+ * per panel, the panel factored by a thread-block cluster; larger n: one
+ * cooperative launch with 18 grid barriers per panel), the kernels of the
+ * plan's Pade step (the denominator systems
  * q R = p of the [13/13] approximant, Eq. full) and of dme_plan_mass.
  * Synchronises `cuda_stream` (NULL: a stream of its own).  DME_EINVAL if
  * n < 1, nrhs < 0, a pointer is NULL, or a pivot column is zero or not finite

@@ -91,11 +91,13 @@ void launch_block_norm1(const double* A, const double* Q, int n, double* colsum_
 void launch_max_reduce(const double* x, int len, double* out, cudaStream_t st);
 
 // B (n x nrhs, ldb) <- M^{-1} B by Gauss-Jordan elimination with partial
-// pivoting in one cooperative launch (M, n x n with ldm, is overwritten).
-// work: gj_work_doubles() doubles.  A zero pivot column sets DEV_SINGULAR.
+// pivoting, blocked by panels of 16 columns (n <= 4096: stream-ordered
+// launches per panel; larger: one cooperative launch).  M (n x n with ldm) is
+// overwritten.  work: gj_work_doubles(n, nrhs) doubles.
+// A zero pivot column sets DEV_SINGULAR.
 dme_status launch_gj_solve(double* M, int n, int ldm, double* B, int nrhs, int ldb, double* work, int* status,
                            cudaStream_t st);
-size_t gj_work_doubles();
+size_t gj_work_doubles(int n, int nrhs);
 // Self-test of the bounded grid-barrier wait: one block waits for a release
 // that never comes; *timed_out = 1 once the wait gave up with DEV_TIMEOUT.
 dme_status wait_timeout_selftest(int* timed_out);

@@ -404,7 +404,7 @@ dme_status compute_ew(dme_plan_t p, double tau, int* idx) {
     DME_TRY(tp.get(&V22, nn));
     DME_TRY(tp.get(&V12, nn));
     double* gjw = nullptr;
-    DME_TRY(tp.get(&gjw, gj_work_doubles()));
+    DME_TRY(tp.get(&gjw, gj_work_doubles(n, n)));
     // split plans of n >= kAccMinN: the Pade products on the tensor cores (accurate mode)
     AccWork accw;
     AccWork* aw = nullptr;
@@ -1265,7 +1265,7 @@ dme_status dme_plan_mass(const dme_plan_desc* desc, const double* M, const doubl
         DME_TRY(tp.get(&X, nn));
         DME_TRY(tp.get(&Y, nn));
         DME_TRY(tp.get(&Mi, nn));
-        DME_TRY(tp.get(&gjw, gj_work_doubles()));
+        DME_TRY(tp.get(&gjw, gj_work_doubles(n, n)));
         DME_TRY(tp.get(&stat, 2));
         int* status = reinterpret_cast<int*>(stat);
         DME_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
@@ -1327,7 +1327,7 @@ dme_status dme_dense_solve(const double* M, int n, double* B, int nrhs, void* cu
         double *Md, *Bd, *gjw, *stat;
         DME_TRY(tp.get(&Md, nn));
         DME_TRY(tp.get(&Bd, nb));
-        DME_TRY(tp.get(&gjw, gj_work_doubles()));
+        DME_TRY(tp.get(&gjw, gj_work_doubles(n, nrhs)));
         DME_TRY(tp.get(&stat, 2));
         int* status = reinterpret_cast<int*>(stat);
         DME_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));

@@ -351,11 +351,12 @@ def test_extrapolation_rejections():
 
 
 # ---------------------------------------------------------------- the dense solve of the Pade step
-@pytest.mark.parametrize("n,nrhs", [(1, 3), (37, 5), (200, 300), (64, 26000)])
+@pytest.mark.parametrize("n,nrhs", [(1, 3), (37, 5), (200, 300), (64, 26000), (1100, 40), (4100, 3)])
 def test_dense_solve_matches_numpy(n, nrhs):
-    """Gauss-Jordan with partial pivoting (the plan's Pade solves) against numpy's
-    LU solve; (64, 26000) leaves the pivot row too long for shared memory, so
-    the unstaged path of the kernel runs."""
+    """Blocked Gauss-Jordan with partial pivoting (the plan's Pade solves) against
+    numpy's LU solve: one panel and a ragged one (37), several (200), a trailing
+    block far wider than M (64, 26000), a cluster of 8 CTAs per panel (1100), and
+    above 4096 the single cooperative launch (4100)."""
     rng = np.random.default_rng(n + nrhs)
     M = rng.standard_normal((n, n)) + n ** 0.5 * np.eye(n)
     B = rng.standard_normal((n, nrhs))
