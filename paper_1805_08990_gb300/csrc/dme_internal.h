@@ -80,6 +80,13 @@ dme_status gemm64_grouped(std::vector<GemmProb>& probs, GemmProb* dev_desc, cuda
                           DescArena* arena = nullptr, int tile = 64);
 // Query the persistent grid sizes ahead of any stream capture.
 void gemm64_prepare();
+// One product of fewer 32-wide tiles than half the SMs (the plan's products for
+// small n) with K split in up to 8 parts (each at least 16 deep), their partial
+// sums in ws, added in part order by a second kernel that applies the epilogue;
+// larger products, or ws shorter than the parts need, take gemm64_grouped.  The
+// result depends only on the problem's shape, not on the stream or the batch.
+dme_status gemm64_splitk(const GemmProb& g, double* ws, size_t ws_len, cudaStream_t st);
+size_t gemm64_splitk_ws_doubles(int M, int N);
 
 // ---------------------------------------------------------------- small kernels
 void launch_axpy_sym(double* P, const double* Q, double a, int n, int ld, cudaStream_t st);

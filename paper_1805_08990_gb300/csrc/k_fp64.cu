@@ -39,22 +39,19 @@ __device__ __forceinline__ void tile_coords(const GemmProb& pb, int lt, int& ti,
 
 // One BM x BM output tile (BM = 32 or 64) with 256 threads, each holding a
 // TM x TM register tile (TM = BM / 16).  Every output is accumulated over k in
-// increasing order with fma, whatever BM is.
+// increasing order with fma, whatever BM is; gemm64_accum covers [kbeg, kend).
 template <int BM>
-__device__ __forceinline__ void gemm64_tile(const GemmProb& pb, int lt, double (&As)[G64_BK][BM + 1],
-                                            double (&Bs)[G64_BK][BM + 1]) {
+__device__ __forceinline__ void gemm64_accum(const GemmProb& pb, int row0, int col0, int kbeg, int kend,
+                                             double (&As)[G64_BK][BM + 1], double (&Bs)[G64_BK][BM + 1],
+                                             double (&acc)[BM / 16][BM / 16]) {
     constexpr int TM = BM / 16;
-    int ti, tj;
-    tile_coords(pb, lt, ti, tj);
-    const int row0 = ti * BM, col0 = tj * BM;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    double acc[TM][TM];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TM; ++j) acc[i][j] = 0.0;
 
-    for (int k0 = 0; k0 < pb.K; k0 += G64_BK) {
+    for (int k0 = kbeg; k0 < kend; k0 += G64_BK) {
 #pragma unroll
         for (int q = 0; q < TM; ++q) {
             const int e = tid + 256 * q;     // BM x 16 elements of each operand tile
@@ -64,12 +61,12 @@ __device__ __forceinline__ void gemm64_tile(const GemmProb& pb, int lt, double (
                 r = e >> 4;
                 k = e & 15;
                 int gr = row0 + r, gk = k0 + k;
-                if (gr < pb.M && gk < pb.K) v = pb.A[(size_t)gr * pb.lda + gk];
+                if (gr < pb.M && gk < kend) v = pb.A[(size_t)gr * pb.lda + gk];
             } else {
                 r = e % BM;
                 k = e / BM;
                 int gr = row0 + r, gk = k0 + k;
-                if (gr < pb.M && gk < pb.K) v = pb.A[(size_t)gk * pb.lda + gr];
+                if (gr < pb.M && gk < kend) v = pb.A[(size_t)gk * pb.lda + gr];
             }
             As[k][r] = v;
             int c;
@@ -78,12 +75,12 @@ __device__ __forceinline__ void gemm64_tile(const GemmProb& pb, int lt, double (
                 c = e % BM;
                 k = e / BM;
                 int gc = col0 + c, gk = k0 + k;
-                if (gc < pb.N && gk < pb.K) w = pb.B[(size_t)gk * pb.ldb + gc];
+                if (gc < pb.N && gk < kend) w = pb.B[(size_t)gk * pb.ldb + gc];
             } else {
                 c = e >> 4;
                 k = e & 15;
                 int gc = col0 + c, gk = k0 + k;
-                if (gc < pb.N && gk < pb.K) w = pb.B[(size_t)gc * pb.ldb + gk];
+                if (gc < pb.N && gk < kend) w = pb.B[(size_t)gc * pb.ldb + gk];
             }
             Bs[k][c] = w;
         }
@@ -102,7 +99,30 @@ __device__ __forceinline__ void gemm64_tile(const GemmProb& pb, int lt, double (
         }
         __syncthreads();
     }
+}
 
+// C = alpha acc + b1 D1 + b2 D2 + b3 D3 (a triangle problem writes (r, c), r <= c,
+// and its mirror).
+__device__ __forceinline__ void gemm64_out(const GemmProb& pb, int r, int c, double sum) {
+    const size_t off = (size_t)r * pb.ldd + c;
+    double v = pb.alpha * sum;
+    if (pb.D1) v += pb.b1 * pb.D1[off];
+    if (pb.D2) v += pb.b2 * pb.D2[off];
+    if (pb.D3) v += pb.b3 * pb.D3[off];
+    pb.C[(size_t)r * pb.ldc + c] = v;
+    if (pb.tri && r != c) pb.C[(size_t)c * pb.ldc + r] = v;
+}
+
+template <int BM>
+__device__ __forceinline__ void gemm64_tile(const GemmProb& pb, int lt, double (&As)[G64_BK][BM + 1],
+                                            double (&Bs)[G64_BK][BM + 1]) {
+    constexpr int TM = BM / 16;
+    int ti, tj;
+    tile_coords(pb, lt, ti, tj);
+    const int row0 = ti * BM, col0 = tj * BM;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[TM][TM];
+    gemm64_accum<BM>(pb, row0, col0, 0, pb.K, As, Bs, acc);
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
         const int r = row0 + ty + 16 * i;
@@ -112,13 +132,7 @@ __device__ __forceinline__ void gemm64_tile(const GemmProb& pb, int lt, double (
             const int c = col0 + tx + 16 * j;
             if (c >= pb.N) continue;
             if (pb.tri && r > c) continue;
-            const size_t off = (size_t)r * pb.ldd + c;
-            double v = pb.alpha * acc[i][j];
-            if (pb.D1) v += pb.b1 * pb.D1[off];
-            if (pb.D2) v += pb.b2 * pb.D2[off];
-            if (pb.D3) v += pb.b3 * pb.D3[off];
-            pb.C[(size_t)r * pb.ldc + c] = v;
-            if (pb.tri && r != c) pb.C[(size_t)c * pb.ldc + r] = v;
+            gemm64_out(pb, r, c, acc[i][j]);
         }
     }
 }
@@ -153,6 +167,46 @@ __global__ void __launch_bounds__(256) gemm64_desc_kernel(const GemmProb* __rest
         GemmProb pb = probs[ip];
         gemm64_tile<BM>(pb, t - pb.tile_start, As, Bs);
     }
+}
+
+// Split K for products of fewer tiles than SMs (the plan's small products, whose
+// tiles would otherwise each run the whole K on one SM's narrow FP64 pipe): CTA
+// (tile, part) writes its partial sums over K range `part` to ws[part][M][N];
+// the reduction adds the parts in order and applies the epilogue.
+__global__ void __launch_bounds__(256) gemm64_splitk_kernel(const __grid_constant__ GemmProb pb, int ntiles,
+                                                            int kchunk, double* __restrict__ ws) {
+    __shared__ double As[G64_BK][33];
+    __shared__ double Bs[G64_BK][33];
+    const int lt = blockIdx.x % ntiles, part = blockIdx.x / ntiles;
+    int ti, tj;
+    tile_coords(pb, lt, ti, tj);
+    const int row0 = ti * 32, col0 = tj * 32;
+    const int kb = part * kchunk, ke = min(pb.K, kb + kchunk);
+    double acc[2][2];
+    gemm64_accum<32>(pb, row0, col0, kb, ke, As, Bs, acc);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double* w = ws + (size_t)part * pb.M * pb.N;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int r = row0 + ty + 16 * i;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int c = col0 + tx + 16 * j;
+            if (r < pb.M && c < pb.N) w[(size_t)r * pb.N + c] = acc[i][j];
+        }
+    }
+}
+
+__global__ void gemm64_splitk_reduce_kernel(const __grid_constant__ GemmProb pb, int parts,
+                                            const double* __restrict__ ws) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t mn = (size_t)pb.M * pb.N;
+    if (e >= mn) return;
+    const int r = (int)(e / pb.N), c = (int)(e % pb.N);
+    if (pb.tri && r > c) return;
+    double sum = 0.0;
+    for (int q = 0; q < parts; ++q) sum += ws[(size_t)q * mn + e];
+    gemm64_out(pb, r, c, sum);
 }
 
 static int prepare_tiles(std::vector<GemmProb>& probs, int bm) {
@@ -248,6 +302,35 @@ dme_status gemm64_grouped(std::vector<GemmProb>& probs, GemmProb* dev_desc, cuda
         if (p.M > 0 && p.N > 0) live.push_back(p);
     if (live.empty()) return DME_OK;
     return tile == 32 ? gemm64_launch<32>(live, dev_desc, st, arena) : gemm64_launch<64>(live, dev_desc, st, arena);
+}
+
+size_t gemm64_splitk_ws_doubles(int M, int N) { return (size_t)8 * M * N; }
+
+dme_status gemm64_splitk(const GemmProb& g, double* ws, size_t ws_len, cudaStream_t st) {
+    std::vector<GemmProb> v{g};
+    if (g.M <= 0 || g.N <= 0) return DME_OK;
+    if (g.tri && g.M != g.N) return set_error("gemm64: triangle mode needs M == N"), DME_EINVAL;
+    const int tm = (g.M + 31) / 32, tn = (g.N + 31) / 32;
+    const int tiles = g.tri ? tn * (tn + 1) / 2 : tm * tn;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // parts of at least one 16-deep K block, up to 8, for about two CTAs per SM
+    int parts = std::min(8, std::min(g.K / G64_BK, std::max(1, 2 * nsm / std::max(tiles, 1))));
+    if (tiles >= nsm / 2 || parts < 2 || !ws || ws_len < (size_t)parts * g.M * g.N) {
+        long tiles64 = (long)((g.M + 63) / 64) * ((g.N + 63) / 64);
+        if (g.tri) tiles64 = (tiles64 + (g.M + 63) / 64) / 2;
+        return gemm64_grouped(v, nullptr, st, nullptr, tiles64 < nsm ? 32 : 64);
+    }
+    const int kchunk = ((g.K + parts - 1) / parts + G64_BK - 1) / G64_BK * G64_BK;
+    parts = (g.K + kchunk - 1) / kchunk;
+    GemmProb pb = g;
+    pb.tiles_n = tn;
+    gemm64_splitk_kernel<<<tiles * parts, 256, 0, st>>>(pb, tiles, kchunk, ws);
+    const size_t mn = (size_t)g.M * g.N;
+    gemm64_splitk_reduce_kernel<<<(unsigned)((mn + 255) / 256), 256, 0, st>>>(pb, parts, ws);
+    DME_CUDA_TRY(cudaGetLastError());
+    return DME_OK;
 }
 
 // ============================================================== elementwise

@@ -223,17 +223,18 @@ dme_status acc_setup(TmpPool& tp, int n, int* status, AccWork* w) {
 
 // C = alpha op(L) op(R) + b1 D1 (n x n): the accurate tensor mode with aw, else FP64.
 dme_status prod(int n, AccWork* aw, const double* L, int tL, const double* R, int tR, double* C, double alpha,
-                const double* D1, double b1, cudaStream_t st) {
+                const double* D1, double b1, cudaStream_t st, double* skw = nullptr, size_t skl = 0) {
     if (aw) return acc_prod(n, *aw, L, tL, R, tR, C, alpha, D1, b1, st);
-    return gemm1(gp(n, n, n, L, n, tL, R, n, tR, C, n, alpha, 0, D1, b1), st);
+    return gemm64_splitk(gp(n, n, n, L, n, tL, R, n, tR, C, n, alpha, 0, D1, b1), skw, skl, st);
 }
 
 // (O22, O12) = (L, L11 = ls L22^T) * (R):  O22 = L22 R22, O12 = ls L22^T R12 + L12 R22.
 dme_status bprod(int n, AccWork* aw, const double* L22, const double* L12, double ls, const double* R22,
-                 const double* R12, double* O22, double* O12, cudaStream_t st) {
-    DME_TRY(prod(n, aw, L22, 0, R22, 0, O22, 1.0, nullptr, 0.0, st));
-    DME_TRY(prod(n, aw, L22, 1, R12, 0, O12, ls, nullptr, 0.0, st));
-    DME_TRY(prod(n, aw, L12, 0, R22, 0, O12, 1.0, O12, 1.0, st));
+                 const double* R12, double* O22, double* O12, cudaStream_t st, double* skw = nullptr,
+                 size_t skl = 0) {
+    DME_TRY(prod(n, aw, L22, 0, R22, 0, O22, 1.0, nullptr, 0.0, st, skw, skl));
+    DME_TRY(prod(n, aw, L22, 1, R12, 0, O12, ls, nullptr, 0.0, st, skw, skl));
+    DME_TRY(prod(n, aw, L12, 0, R22, 0, O12, 1.0, O12, 1.0, st, skw, skl));
     return DME_OK;
 }
 
@@ -405,6 +406,13 @@ dme_status compute_ew(dme_plan_t p, double tau, int* idx) {
     DME_TRY(tp.get(&V12, nn));
     double* gjw = nullptr;
     DME_TRY(tp.get(&gjw, gj_work_doubles(n, n)));
+    // split-K partial sums of the small FP64 products (n <= 288: fewer 32-wide tiles than half the SMs)
+    double* skw = nullptr;
+    size_t skl = 0;
+    if (n <= 288) {
+        skl = gemm64_splitk_ws_doubles(n, n);
+        DME_TRY(tp.get(&skw, skl));
+    }
     // split plans of n >= kAccMinN: the Pade products on the tensor cores (accurate mode)
     AccWork accw;
     AccWork* aw = nullptr;
@@ -417,22 +425,22 @@ dme_status compute_ew(dme_plan_t p, double tau, int* idx) {
     launch_lincomb(X22, n, n, p->A, sc, nullptr, 0, nullptr, 0, 0.0, st);
     launch_lincomb(X12, n, n, p->Q, sc, nullptr, 0, nullptr, 0, 0.0, st);
     // X2 = X X (odd * odd -> even), X4 = X2 X2, X6 = X4 X2
-    DME_TRY(bprod(n, aw, X22, X12, -1.0, X22, X12, A22, A12, st));
-    DME_TRY(bprod(n, aw, A22, A12, 1.0, A22, A12, B22, B12, st));
-    DME_TRY(bprod(n, aw, B22, B12, 1.0, A22, A12, C22, C12, st));
+    DME_TRY(bprod(n, aw, X22, X12, -1.0, X22, X12, A22, A12, st, skw, skl));
+    DME_TRY(bprod(n, aw, A22, A12, 1.0, A22, A12, B22, B12, st, skw, skl));
+    DME_TRY(bprod(n, aw, B22, B12, 1.0, A22, A12, C22, C12, st, skw, skl));
     // odd part: U = X (X6 (c13 X6 + c11 X4 + c9 X2) + c7 X6 + c5 X4 + c3 X2 + c1 I)
     launch_lincomb(Y22, n, n, C22, c[13], B22, c[11], A22, c[9], 0.0, st);
     launch_lincomb(Y12, n, n, C12, c[13], B12, c[11], A12, c[9], 0.0, st);
-    DME_TRY(bprod(n, aw, C22, C12, 1.0, Y22, Y12, T22, T12, st));
+    DME_TRY(bprod(n, aw, C22, C12, 1.0, Y22, Y12, T22, T12, st, skw, skl));
     launch_lincomb(U22, n, n, C22, c[7], B22, c[5], A22, c[3], c[1], st);
     launch_lincomb(U12, n, n, C12, c[7], B12, c[5], A12, c[3], 0.0, st);
     launch_lincomb(T22, n, n, T22, 1.0, U22, 1.0, nullptr, 0, 0.0, st);
     launch_lincomb(T12, n, n, T12, 1.0, U12, 1.0, nullptr, 0, 0.0, st);
-    DME_TRY(bprod(n, aw, X22, X12, -1.0, T22, T12, U22, U12, st));
+    DME_TRY(bprod(n, aw, X22, X12, -1.0, T22, T12, U22, U12, st, skw, skl));
     // even part: V = X6 (c12 X6 + c10 X4 + c8 X2) + c6 X6 + c4 X4 + c2 X2 + c0 I
     launch_lincomb(Y22, n, n, C22, c[12], B22, c[10], A22, c[8], 0.0, st);
     launch_lincomb(Y12, n, n, C12, c[12], B12, c[10], A12, c[8], 0.0, st);
-    DME_TRY(bprod(n, aw, C22, C12, 1.0, Y22, Y12, V22, V12, st));
+    DME_TRY(bprod(n, aw, C22, C12, 1.0, Y22, Y12, V22, V12, st, skw, skl));
     launch_lincomb(T22, n, n, C22, c[6], B22, c[4], A22, c[2], c[0], st);
     launch_lincomb(T12, n, n, C12, c[6], B12, c[4], A12, c[2], 0.0, st);
     launch_lincomb(V22, n, n, V22, 1.0, T22, 1.0, nullptr, 0, 0.0, st);
@@ -454,7 +462,7 @@ dme_status compute_ew(dme_plan_t p, double tau, int* idx) {
     DME_TRY(launch_gj_solve(LUq, n, n, R22, n, n, gjw, p->status, st));
     // R12 = p22^{-T} (p12 - q12 R22)
     R12 = C12;
-    DME_TRY(prod(n, aw, q12, 0, R22, 0, R12, -1.0, p12, 1.0, st));
+    DME_TRY(prod(n, aw, q12, 0, R22, 0, R12, -1.0, p12, 1.0, st, skw, skl));
     LUp = C22;
     launch_transpose(p22, LUp, n, n, n, n, st);
     DME_TRY(launch_gj_solve(LUp, n, n, R12, n, n, gjw, p->status, st));
@@ -464,12 +472,12 @@ dme_status compute_ew(dme_plan_t p, double tau, int* idx) {
     double* tmp = T22;
     double* E2 = T12;
     launch_lincomb(E, n, n, R22, 1.0, nullptr, 0, nullptr, 0, 0.0, st);
-    DME_TRY(prod(n, aw, R22, 1, R12, 0, Wm, 1.0, nullptr, 0.0, st));
+    DME_TRY(prod(n, aw, R22, 1, R12, 0, Wm, 1.0, nullptr, 0.0, st, skw, skl));
     launch_symmetrize(Wm, n, n, st);
     for (int i = 0; i < s; ++i) {
-        DME_TRY(gemm1(gp(n, n, n, Wm, n, 0, E, n, 0, tmp, n, 1.0), st));             // tmp = W E
-        DME_TRY(gemm1(gp(n, n, n, E, n, 1, tmp, n, 0, Wm, n, 1.0, 1, Wm, 1.0), st));   // W = E^T tmp + W
-        DME_TRY(gemm1(gp(n, n, n, E, n, 0, E, n, 0, E2, n, 1.0), st));               // E2 = E E
+        DME_TRY(gemm64_splitk(gp(n, n, n, Wm, n, 0, E, n, 0, tmp, n, 1.0), skw, skl, st));   // tmp = W E
+        DME_TRY(gemm64_splitk(gp(n, n, n, E, n, 1, tmp, n, 0, Wm, n, 1.0, 1, Wm, 1.0), skw, skl, st));   // W = E^T tmp + W
+        DME_TRY(gemm64_splitk(gp(n, n, n, E, n, 0, E, n, 0, E2, n, 1.0), skw, skl, st));     // E2 = E E
         std::swap(E, E2);
     }
     EWEntry ent;
