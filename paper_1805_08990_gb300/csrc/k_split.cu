@@ -819,6 +819,10 @@ __device__ __forceinline__ void oz_persistent(int units, Resolve resolve) {
                 }
                 fence_after_sync();
                 bool ok = true;
+                // the unit's own level cut: a grouped launch of the 4 x 4 slice kernel also
+                // runs 10-product problems (levels <= 3), with the same MMAs in the same order
+                // as their own kernel
+                const int Lu = min(Cfg::L, w.p->cfg == OZ_P10 ? 3 : Cfg::L);
                 for (int it = 0; it < w.nk; ++it, ++kit) {
                     const int s = kit % S;
                     const uint32_t ph = (kit / S) & 1;
@@ -837,7 +841,7 @@ __device__ __forceinline__ void oz_persistent(int units, Resolve resolve) {
                         for (int sa = 0; sa < Cfg::SA; ++sa) {
 #pragma unroll
                             for (int sb = 0; sb < Cfg::SB; ++sb) {
-                                if (sa + sb > Cfg::L) continue;
+                                if (sa + sb > Cfg::L || sa + sb > Lu) continue;
                                 const int lvl = (sa + sb < Cfg::NACC - 1) ? sa + sb : Cfg::NACC - 1;
                                 const uint64_t ad = desc_kmajor_sw64(a0 + sa * OZ_SLICE_BYTES + kk * 32);
                                 const uint64_t bd = desc_kmajor_sw64(b0 + sb * OZ_SLICE_BYTES + kk * 32);
@@ -1228,7 +1232,6 @@ static dme_status oz_grouped_attr() {
 }
 
 dme_status ozaki_grouped_prepare() {
-    DME_TRY(oz_grouped_attr<CfgP10>());
     DME_TRY(oz_grouped_attr<CfgP13>());
     DME_TRY(oz_grouped_attr<CfgP14e>());
     return DME_OK;
@@ -1236,17 +1239,22 @@ dme_status ozaki_grouped_prepare() {
 
 dme_status launch_ozaki_grouped(std::vector<OzGroupDesc>& items, OzGroupDesc* dev_desc, cudaStream_t st,
                                 DescArena* arena) {
+    // configurations of one launch: 10 and 13 products (4 x 4 slices, the 13-product
+    // kernel cutting the 10-product problems at level 3), or 14 alone
     int total = 0, cfg = -1;
     std::vector<OzGroupDesc> live;
+    std::stable_sort(items.begin(), items.end(),
+                     [](const OzGroupDesc& x, const OzGroupDesc& y) { return x.p.Kp > y.p.Kp; });
     for (auto& it : items) {
         OzParams& p = it.p;
         if (p.M <= 0 || p.N <= 0) continue;
+        const int cls = p.cfg == OZ_P10 ? OZ_P13 : p.cfg;
         if (p.Kp % OZ_BK != 0 || p.Kp > OZ_MAX_K || (p.tri && p.M != p.N) || p.cfg == OZ_A21 ||
-            (cfg >= 0 && p.cfg != cfg)) {
+            (cfg >= 0 && cls != cfg)) {
             set_error("ozaki grouped gemm: bad problem shape or mixed configurations");
             return DME_EINVAL;
         }
-        cfg = p.cfg;
+        cfg = cls;
         const int tmt = (p.M + OZ_BM - 1) / OZ_BM, tnt = (p.N + OZ_BN - 1) / OZ_BN;
         p.tiles_n = tnt;
         p.tiles = p.tri ? tnt * (tnt + 1) / 2 : tmt * tnt;
@@ -1269,9 +1277,6 @@ dme_status launch_ozaki_grouped(std::vector<OzGroupDesc>& items, OzGroupDesc* de
     const int grid = std::min(total, sm_count());
     const int nd = (int)live.size();
     switch (cfg) {
-        case OZ_P10:
-            ozaki_gemm_grouped_kernel<CfgP10><<<grid, OZ_THREADS, CfgP10::SMEM, st>>>(d, nd, total);
-            break;
         case OZ_P13:
             ozaki_gemm_grouped_kernel<CfgP13><<<grid, OZ_THREADS, CfgP13::SMEM, st>>>(d, nd, total);
             break;

@@ -385,8 +385,9 @@ dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
                 s2.push_back(b);
             }
             DME_TRY(launch_slice_grouped(s1, false, s->st, &s->arena));
-            // one grouped launch per slice-pair configuration present (each plan chose its own)
-            std::vector<OzGroupDesc> o1c[OZ_NCFG], o2c[OZ_NCFG];
+            // one grouped launch for the plans of 10 or 13 slice products (4 x 4 slices), one for
+            // those of 14 (each plan chose its own)
+            std::vector<OzGroupDesc> o1c[2], o2c[2];
             for (Req* r : L.sc) {
                 dme_plan_t p = r->plan;
                 const Op& o = p->ops[k];
@@ -401,7 +402,7 @@ dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
                 a.p.ldc = n;
                 a.p.Cp = p->U;
                 a.p.status = s->dstat + r->slot;
-                o1c[p->cfg].push_back(a);
+                o1c[p->cfg == OZ_P14].push_back(a);
                 OzGroupDesc b;
                 std::memset(&b, 0, sizeof(b));
                 b.tmA = oz_tmap_a(e.Gsl, p->cfg);
@@ -421,7 +422,7 @@ dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
                     b.p.b2 = o.qcoef;
                 }
                 b.p.status = s->dstat + r->slot;
-                o2c[p->cfg].push_back(b);
+                o2c[p->cfg == OZ_P14].push_back(b);
                 (void)n;
             }
             for (auto& g : o1c)

@@ -136,8 +136,10 @@ dme_status oz_params(const SliceBuf& A, const SliceBuf& B, int cfg, OzParams* p)
 // The accurate mode's chunk workspace in doubles for an M x N product over K.
 size_t oz_acc_ws_doubles(int M, int N, int K);
 dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzParams p, cudaStream_t st);
-// Grouped launch over independent problems (every item with the same cfg, not the
-// accurate mode); dev_desc holds items.size() descriptors.
+// Grouped launch over independent problems: items of 10 and 13 slice products
+// together, or of 14 alone (not the accurate mode), reordered by K, largest
+// first, so that the longest tiles start in the first wave; dev_desc holds
+// items.size() descriptors.
 // Set the grouped kernel's shared-memory attribute (before any stream capture).
 dme_status ozaki_grouped_prepare();
 // With `arena` the descriptors are staged there instead of copied to dev_desc.
