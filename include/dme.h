@@ -309,7 +309,9 @@ dme_status dme_submit_gain(dme_server_t server, const dme_plan_desc* desc, const
 dme_status dme_poll_gain(dme_server_t server, uint64_t ticket, double* P_out, double* K_out, int64_t timeout_us);
 
 /* Server statistics as a JSON object (completed, failed, resident, queued,
- * p50/p99 latency in ms, solves/s); the string stays valid until the next call. */
+ * p50/p99 latency in ms, solves/s, rounds, round-graph builds and their host
+ * time, the stepper's time blocked on its round batches, plans and their mean
+ * time); the string stays valid until the next call. */
 const char* dme_server_stats(dme_server_t srv);
 
 dme_status dme_server_destroy(dme_server_t srv);

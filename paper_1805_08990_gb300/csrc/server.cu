@@ -102,6 +102,7 @@ struct dme_server_s {
     int completed = 0, failed = 0, tuned = 0;
     std::atomic<int> rounds{0}, graph_builds{0};   // written by the stepper, read by dme_server_stats
     double build_s = 0.0;   // host time spent building round graphs (stepper thread; under mu)
+    double wait_s = 0.0;    // stepper time blocked on the round batches' completion (under mu)
     double plan_s = 0.0;    // wall time of the admission threads' plan builds, summed (under mu)
     int planned = 0;
     int pairs_hist[3] = {0, 0, 0};   // split plans by slice products chosen: 10, 13, 14 (under mu)
@@ -520,9 +521,14 @@ void step_loop(dme_server_t s) {
         }
         std::string err = get_error();
         if (st == DME_OK) {
+            const double tw = now_s();
             cudaError_t e = cudaMemcpyAsync(hstat.data(), s->dstat, sizeof(int) * s->max_slots,
                                             cudaMemcpyDeviceToHost, s->st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+            {
+                std::lock_guard<std::mutex> g(s->mu);
+                s->wait_s += now_s() - tw;
+            }
             if (e != cudaSuccess) {
                 st = DME_ECUDA;
                 err = std::string("serving: ") + cudaGetErrorString(e);
@@ -753,11 +759,12 @@ const char* dme_server_stats(dme_server_t s) {
     char buf[768];
     snprintf(buf, sizeof(buf),
              "{\"completed\": %d, \"failed\": %d, \"resident\": %d, \"queued\": %d, \"rounds\": %d, "
-             "\"graph_builds\": %d, \"graph_build_ms\": %.1f, \"tuned_groups\": %d, \"tiles32\": %d, "
+             "\"graph_builds\": %d, \"graph_build_ms\": %.1f, \"round_wait_ms\": %.1f, \"tuned_groups\": %d, "
+             "\"tiles32\": %d, "
              "\"p50_ms\": %.3f, \"p99_ms\": %.3f, \"solves_per_s\": %.4f, \"reserved_bytes\": %zu, "
              "\"plans\": %d, \"plan_ms_mean\": %.3f, \"split_pairs_10_13_14\": [%d, %d, %d]}",
              s->completed, s->failed, resident, queued, s->rounds.load(), s->graph_builds.load(), s->build_s * 1e3,
-             s->tuned, t32,
+             s->wait_s * 1e3, s->tuned, t32,
              pct(0.5), pct(0.99),
              span > 0 ? s->completed / span : 0.0, s->reserved, s->planned,
              s->planned ? 1e3 * s->plan_s / s->planned : 0.0, s->pairs_hist[0], s->pairs_hist[1], s->pairs_hist[2]);
