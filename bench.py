@@ -334,6 +334,7 @@ def run_serving_suite(args):
                          "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "completed": st["completed"],
                          "failed": st["failed"] + st["client_failures"], "wall_s": st["wall_s"],
                          "graph_builds": st.get("graph_builds"), "rounds": st.get("rounds"),
+                         "graph_build_ms": st.get("graph_build_ms"), "round_wait_ms": st.get("round_wait_ms"),
                          "busy_retries": st.get("busy_retries"), "plan_ms_mean": st.get("plan_ms_mean"),
                          "split_pairs_10_13_14": st.get("split_pairs_10_13_14"),
                          "roofline": serving_roofline(st, prec, peaks)})
