@@ -91,6 +91,8 @@ struct dme_server_s {
     std::vector<std::thread> admit_thrs;
     std::thread step_thr;
     cudaStream_t st = nullptr;
+    cudaStream_t st2 = nullptr;   // the 14-product group's GEMMs, beside the 10/13 group's (forked in the round)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int* dstat = nullptr;         // per-slot device status words
     DescArena arena;              // launch descriptors of the captured round
     GemmProb* tune_desc = nullptr;  // autotuner's descriptor buffer (max_slots)
@@ -338,6 +340,32 @@ dme_status tune_tiles(dme_server_t s, std::vector<Req*>& res) {
     return DME_OK;
 }
 
+void destroy_streams(dme_server_t s) {
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
+    if (s->st2) cudaStreamDestroy(s->st2);
+    if (s->st) cudaStreamDestroy(s->st);
+}
+
+// The split GEMMs of one stage: the group of 10/13-product plans on the serving stream and,
+// when both groups are present, the 14-product group on the second stream at the same time
+// (independent problems; the persistent kernels share the SMs neither fills), joined before
+// the next stage.
+dme_status launch_split_groups(dme_server_t s, std::vector<OzGroupDesc> (&g)[2]) {
+    if (g[0].empty() || g[1].empty()) {
+        for (auto& x : g)
+            if (!x.empty()) DME_TRY(launch_ozaki_grouped(x, nullptr, s->st, &s->arena));
+        return DME_OK;
+    }
+    DME_CUDA_TRY(cudaEventRecord(s->ev_fork, s->st));
+    DME_CUDA_TRY(cudaStreamWaitEvent(s->st2, s->ev_fork, 0));
+    DME_TRY(launch_ozaki_grouped(g[1], nullptr, s->st2, &s->arena));
+    DME_TRY(launch_ozaki_grouped(g[0], nullptr, s->st, &s->arena));
+    DME_CUDA_TRY(cudaEventRecord(s->ev_join, s->st2));
+    DME_CUDA_TRY(cudaStreamWaitEvent(s->st, s->ev_join, 0));
+    return DME_OK;
+}
+
 // Enqueue one scheduler round over the residents: stage by stage, grouped
 // launches, descriptors staged in the arena (no host synchronisation: the
 // sequence is captured into a graph).
@@ -426,11 +454,9 @@ dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
                 o2c[p->cfg == OZ_P14].push_back(b);
                 (void)n;
             }
-            for (auto& g : o1c)
-                if (!g.empty()) DME_TRY(launch_ozaki_grouped(g, nullptr, s->st, &s->arena));
+            DME_TRY(launch_split_groups(s, o1c));
             DME_TRY(launch_slice_grouped(s2, true, s->st, &s->arena));
-            for (auto& g : o2c)
-                if (!g.empty()) DME_TRY(launch_ozaki_grouped(g, nullptr, s->st, &s->arena));
+            DME_TRY(launch_split_groups(s, o2c));
         }
         if (!L.ric.empty()) DME_TRY(launch_riccati_grouped(L.ric, nullptr, s->st, &s->arena));
     }
@@ -589,6 +615,9 @@ dme_status dme_server_create(size_t hbm_budget_bytes, int max_slots, dme_server_
     s->queue_cap = (size_t)max_slots * 64;
     for (int i = max_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
     cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&s->dstat, sizeof(int) * max_slots);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->dstat, 0, sizeof(int) * max_slots, s->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
@@ -602,7 +631,7 @@ dme_status dme_server_create(size_t hbm_budget_bytes, int max_slots, dme_server_
     if (e != cudaSuccess) {
         set_error(std::string("dme_server_create: ") + cudaGetErrorString(e));
         cudaGetLastError();
-        if (s->st) cudaStreamDestroy(s->st);
+        destroy_streams(s);
         cudaFree(s->dstat);
         cudaFree(s->arena.dev);
         cudaFree(s->tune_desc);
@@ -611,7 +640,7 @@ dme_status dme_server_create(size_t hbm_budget_bytes, int max_slots, dme_server_
     }
     gemm64_prepare();
     if (ozaki_grouped_prepare() != DME_OK) {
-        cudaStreamDestroy(s->st);
+        destroy_streams(s);
         cudaFree(s->dstat);
         cudaFree(s->arena.dev);
         cudaFree(s->tune_desc);
@@ -792,7 +821,7 @@ dme_status dme_server_destroy(dme_server_t s) {
     cudaFree(s->dstat);
     cudaFree(s->arena.dev);
     cudaFree(s->tune_desc);
-    cudaStreamDestroy(s->st);
+    destroy_streams(s);
     delete s;
     return DME_OK;
 }
