@@ -91,8 +91,12 @@ struct dme_server_s {
     std::vector<std::thread> admit_thrs;
     std::thread step_thr;
     cudaStream_t st = nullptr;
-    cudaStream_t st2 = nullptr;   // the 14-product group's GEMMs, beside the 10/13 group's (forked in the round)
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // a round runs its residents in two lanes (two halves, each its own chain of stages, forked
+    // from and joined to st); in a lane the 14-product group's split GEMMs run on the lane's
+    // second stream beside the 10/13 group's
+    cudaStream_t lane_st[2] = {nullptr, nullptr}, lane_st2[2] = {nullptr, nullptr};
+    cudaEvent_t ev_split = nullptr, ev_done[2] = {nullptr, nullptr};
+    cudaEvent_t ev_fork[2] = {nullptr, nullptr}, ev_join[2] = {nullptr, nullptr};
     int* dstat = nullptr;         // per-slot device status words
     DescArena arena;              // launch descriptors of the captured round
     GemmProb* tune_desc = nullptr;  // autotuner's descriptor buffer (max_slots)
@@ -341,9 +345,13 @@ dme_status tune_tiles(dme_server_t s, std::vector<Req*>& res) {
 }
 
 void destroy_streams(dme_server_t s) {
-    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
-    if (s->ev_join) cudaEventDestroy(s->ev_join);
-    if (s->st2) cudaStreamDestroy(s->st2);
+    for (int l = 0; l < 2; ++l) {
+        for (cudaEvent_t ev : {s->ev_done[l], s->ev_fork[l], s->ev_join[l]})
+            if (ev) cudaEventDestroy(ev);
+        if (s->lane_st[l]) cudaStreamDestroy(s->lane_st[l]);
+        if (s->lane_st2[l]) cudaStreamDestroy(s->lane_st2[l]);
+    }
+    if (s->ev_split) cudaEventDestroy(s->ev_split);
     if (s->st) cudaStreamDestroy(s->st);
 }
 
@@ -351,38 +359,40 @@ void destroy_streams(dme_server_t s) {
 // when both groups are present, the 14-product group on the second stream at the same time
 // (independent problems; the persistent kernels share the SMs neither fills), joined before
 // the next stage.
-dme_status launch_split_groups(dme_server_t s, std::vector<OzGroupDesc> (&g)[2]) {
+dme_status launch_split_groups(dme_server_t s, int lane, std::vector<OzGroupDesc> (&g)[2]) {
+    cudaStream_t st = s->lane_st[lane], st2 = s->lane_st2[lane];
     if (g[0].empty() || g[1].empty()) {
         for (auto& x : g)
-            if (!x.empty()) DME_TRY(launch_ozaki_grouped(x, nullptr, s->st, &s->arena));
+            if (!x.empty()) DME_TRY(launch_ozaki_grouped(x, nullptr, st, &s->arena));
         return DME_OK;
     }
-    DME_CUDA_TRY(cudaEventRecord(s->ev_fork, s->st));
-    DME_CUDA_TRY(cudaStreamWaitEvent(s->st2, s->ev_fork, 0));
-    DME_TRY(launch_ozaki_grouped(g[1], nullptr, s->st2, &s->arena));
-    DME_TRY(launch_ozaki_grouped(g[0], nullptr, s->st, &s->arena));
-    DME_CUDA_TRY(cudaEventRecord(s->ev_join, s->st2));
-    DME_CUDA_TRY(cudaStreamWaitEvent(s->st, s->ev_join, 0));
+    DME_CUDA_TRY(cudaEventRecord(s->ev_fork[lane], st));
+    DME_CUDA_TRY(cudaStreamWaitEvent(st2, s->ev_fork[lane], 0));
+    DME_TRY(launch_ozaki_grouped(g[1], nullptr, st2, &s->arena));
+    DME_TRY(launch_ozaki_grouped(g[0], nullptr, st, &s->arena));
+    DME_CUDA_TRY(cudaEventRecord(s->ev_join[lane], st2));
+    DME_CUDA_TRY(cudaStreamWaitEvent(st, s->ev_join[lane], 0));
     return DME_OK;
 }
 
 // Enqueue one scheduler round over the residents: stage by stage, grouped
 // launches, descriptors staged in the arena (no host synchronisation: the
 // sequence is captured into a graph).
-dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
+dme_status run_lane(dme_server_t s, std::vector<Req*>& res, int lane) {
+    cudaStream_t st = s->lane_st[lane];
     const size_t stages = round_stages(res);
     for (size_t k = 0; k < stages; ++k) {
         StageLists L;
         DME_TRY(stage_lists(s, res, k, L));
         for (Req* r : L.axpy) {
             const Op& o = r->plan->ops[k];
-            launch_axpy_sym(r->P, r->plan->Q, o.qcoef, r->plan->n, r->plan->n, s->st);
+            launch_axpy_sym(r->P, r->plan->Q, o.qcoef, r->plan->n, r->plan->n, st);
         }
         if (!L.g1.empty()) {
             auto it = s->tile_choice.find(tile_key(L.g1));
             const int tile = it == s->tile_choice.end() ? 64 : it->second;
-            DME_TRY(gemm64_grouped(L.g1, nullptr, s->st, &s->arena, tile));
-            DME_TRY(gemm64_grouped(L.g2, nullptr, s->st, &s->arena, tile));
+            DME_TRY(gemm64_grouped(L.g1, nullptr, st, &s->arena, tile));
+            DME_TRY(gemm64_grouped(L.g2, nullptr, st, &s->arena, tile));
         }
         if (!L.sc.empty()) {
             // the split congruence G P G^T of every request: slice P, grouped U = G P,
@@ -413,7 +423,7 @@ dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
                 b.scale = p->usl.scale;
                 s2.push_back(b);
             }
-            DME_TRY(launch_slice_grouped(s1, false, s->st, &s->arena));
+            DME_TRY(launch_slice_grouped(s1, false, st, &s->arena));
             // one grouped launch for the plans of 10 or 13 slice products (4 x 4 slices), one for
             // those of 14 (each plan chose its own)
             std::vector<OzGroupDesc> o1c[2], o2c[2];
@@ -454,19 +464,44 @@ dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
                 o2c[p->cfg == OZ_P14].push_back(b);
                 (void)n;
             }
-            DME_TRY(launch_split_groups(s, o1c));
-            DME_TRY(launch_slice_grouped(s2, true, s->st, &s->arena));
-            DME_TRY(launch_split_groups(s, o2c));
+            DME_TRY(launch_split_groups(s, lane, o1c));
+            DME_TRY(launch_slice_grouped(s2, true, st, &s->arena));
+            DME_TRY(launch_split_groups(s, lane, o2c));
         }
-        if (!L.ric.empty()) DME_TRY(launch_riccati_grouped(L.ric, nullptr, s->st, &s->arena));
+        if (!L.ric.empty()) DME_TRY(launch_riccati_grouped(L.ric, nullptr, st, &s->arena));
     }
     // after the step: the gain of every request that records it (the launches read
     // the device step counter, so the captured round stays valid for every replay)
     for (Req* r : res)
         if (r->gain)
             DME_TRY(launch_lqr_gain_hist(r->P, r->plan->Bt, r->plan->LR, r->plan->n, r->plan->m, r->plan->rwork,
-                                         r->Kh, r->kctr, r->nsteps, s->st));
+                                         r->Kh, r->kctr, r->nsteps, st));
     DME_CUDA_TRY(cudaGetLastError());
+    return DME_OK;
+}
+
+// One round: the residents in two lanes of about equal work (largest first, each to the
+// lighter lane), each lane its own chain of stages on its own stream, forked from the
+// serving stream and joined back; so one lane's slicing and Riccati stages overlap the
+// other's GEMMs.  A request's arithmetic does not depend on its lane or group.
+dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
+    std::vector<Req*> order(res);
+    std::stable_sort(order.begin(), order.end(), [](const Req* x, const Req* y) { return x->plan->n > y->plan->n; });
+    std::vector<Req*> part[2];
+    double w[2] = {0.0, 0.0};
+    for (Req* r : order) {
+        const double n = r->plan->n;
+        const int l = w[1] < w[0] ? 1 : 0;
+        part[l].push_back(r);
+        w[l] += n * n * n;
+    }
+    DME_CUDA_TRY(cudaEventRecord(s->ev_split, s->st));
+    for (int l = 0; l < 2; ++l) {
+        DME_CUDA_TRY(cudaStreamWaitEvent(s->lane_st[l], s->ev_split, 0));
+        if (!part[l].empty()) DME_TRY(run_lane(s, part[l], l));
+        DME_CUDA_TRY(cudaEventRecord(s->ev_done[l], s->lane_st[l]));
+    }
+    for (int l = 0; l < 2; ++l) DME_CUDA_TRY(cudaStreamWaitEvent(s->st, s->ev_done[l], 0));
     return DME_OK;
 }
 
@@ -615,9 +650,14 @@ dme_status dme_server_create(size_t hbm_budget_bytes, int max_slots, dme_server_
     s->queue_cap = (size_t)max_slots * 64;
     for (int i = max_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
     cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st2, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_split, cudaEventDisableTiming);
+    for (int l = 0; l < 2; ++l) {
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->lane_st[l], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->lane_st2[l], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_done[l], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_fork[l], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_join[l], cudaEventDisableTiming);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&s->dstat, sizeof(int) * max_slots);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->dstat, 0, sizeof(int) * max_slots, s->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
