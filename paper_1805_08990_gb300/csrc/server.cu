@@ -75,6 +75,8 @@ struct Req {
 
 }  // namespace
 
+constexpr int kLanes = 2;   // concurrent lanes of a round
+
 struct dme_server_s {
     size_t budget = 0;
     int max_slots = 0;
@@ -91,12 +93,12 @@ struct dme_server_s {
     std::vector<std::thread> admit_thrs;
     std::thread step_thr;
     cudaStream_t st = nullptr;
-    // a round runs its residents in two lanes (two halves, each its own chain of stages, forked
+    // a round runs its residents in kLanes lanes (each its own chain of stages, forked
     // from and joined to st); in a lane the 14-product group's split GEMMs run on the lane's
     // second stream beside the 10/13 group's
-    cudaStream_t lane_st[2] = {nullptr, nullptr}, lane_st2[2] = {nullptr, nullptr};
-    cudaEvent_t ev_split = nullptr, ev_done[2] = {nullptr, nullptr};
-    cudaEvent_t ev_fork[2] = {nullptr, nullptr}, ev_join[2] = {nullptr, nullptr};
+    cudaStream_t lane_st[kLanes] = {}, lane_st2[kLanes] = {};
+    cudaEvent_t ev_split = nullptr, ev_done[kLanes] = {};
+    cudaEvent_t ev_fork[kLanes] = {}, ev_join[kLanes] = {};
     int* dstat = nullptr;         // per-slot device status words
     DescArena arena;              // launch descriptors of the captured round
     GemmProb* tune_desc = nullptr;  // autotuner's descriptor buffer (max_slots)
@@ -345,7 +347,7 @@ dme_status tune_tiles(dme_server_t s, std::vector<Req*>& res) {
 }
 
 void destroy_streams(dme_server_t s) {
-    for (int l = 0; l < 2; ++l) {
+    for (int l = 0; l < kLanes; ++l) {
         for (cudaEvent_t ev : {s->ev_done[l], s->ev_fork[l], s->ev_join[l]})
             if (ev) cudaEventDestroy(ev);
         if (s->lane_st[l]) cudaStreamDestroy(s->lane_st[l]);
@@ -480,28 +482,30 @@ dme_status run_lane(dme_server_t s, std::vector<Req*>& res, int lane) {
     return DME_OK;
 }
 
-// One round: the residents in two lanes of about equal work (largest first, each to the
-// lighter lane), each lane its own chain of stages on its own stream, forked from the
+// One round: the residents in kLanes lanes of about equal work (largest first, each to the
+// lightest lane), each lane its own chain of stages on its own stream, forked from the
 // serving stream and joined back; so one lane's slicing and Riccati stages overlap the
 // other's GEMMs.  A request's arithmetic does not depend on its lane or group.
 dme_status run_round(dme_server_t s, std::vector<Req*>& res) {
     std::vector<Req*> order(res);
     std::stable_sort(order.begin(), order.end(), [](const Req* x, const Req* y) { return x->plan->n > y->plan->n; });
-    std::vector<Req*> part[2];
-    double w[2] = {0.0, 0.0};
+    std::vector<Req*> part[kLanes];
+    double w[kLanes] = {};
     for (Req* r : order) {
         const double n = r->plan->n;
-        const int l = w[1] < w[0] ? 1 : 0;
+        int l = 0;
+        for (int q = 1; q < kLanes; ++q)
+            if (w[q] < w[l]) l = q;
         part[l].push_back(r);
         w[l] += n * n * n;
     }
     DME_CUDA_TRY(cudaEventRecord(s->ev_split, s->st));
-    for (int l = 0; l < 2; ++l) {
+    for (int l = 0; l < kLanes; ++l) {
         DME_CUDA_TRY(cudaStreamWaitEvent(s->lane_st[l], s->ev_split, 0));
         if (!part[l].empty()) DME_TRY(run_lane(s, part[l], l));
         DME_CUDA_TRY(cudaEventRecord(s->ev_done[l], s->lane_st[l]));
     }
-    for (int l = 0; l < 2; ++l) DME_CUDA_TRY(cudaStreamWaitEvent(s->st, s->ev_done[l], 0));
+    for (int l = 0; l < kLanes; ++l) DME_CUDA_TRY(cudaStreamWaitEvent(s->st, s->ev_done[l], 0));
     return DME_OK;
 }
 
@@ -651,7 +655,7 @@ dme_status dme_server_create(size_t hbm_budget_bytes, int max_slots, dme_server_
     for (int i = max_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
     cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_split, cudaEventDisableTiming);
-    for (int l = 0; l < 2; ++l) {
+    for (int l = 0; l < kLanes; ++l) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->lane_st[l], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->lane_st2[l], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_done[l], cudaEventDisableTiming);
