@@ -502,16 +502,7 @@ __device__ __forceinline__ void oz_group_unit(const OzGroupDesc* __restrict__ d,
         if (d[mid].start <= u) lo = mid;
         else hi = mid - 1;
     }
-    o.p = &d[lo].p;
-    o.tA = &d[lo].tmA;
-    o.tB = &d[lo].tmB;
-    oz_tile_coords(d[lo].p, u - d[lo].start, o.tm, o.tn);
-    o.kb0 = 0;
-    o.nk = d[lo].p.Kp / OZ_BK;
-    o.part = 0;
-    o.nparts = 1;
-    o.widx = 0;
-    o.chunk = 0;
+    oz_single_unit(&d[lo].p, &d[lo].tmA, &d[lo].tmB, false, u - d[lo].start, o);
 }
 
 // Load 32 columns of the four accumulators of TMEM lane quadrant q at column c0
@@ -995,9 +986,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_gemm_grouped_kernel(const
 // and the row-direction stores are coalesced; the element arithmetic is
 // oz_store_half's, so a split tile gives what an unsplit one would from the
 // same level sums.
-__global__ void __launch_bounds__(256) oz_tail_kernel(const __grid_constant__ OzParams p) {
+__device__ __forceinline__ void oz_tail_tile(const OzParams& p, int widx) {
     constexpr size_t tile_elems = (size_t)OZ_BM * OZ_BN;
-    const int widx = blockIdx.x;
     const int il = blockIdx.y * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     int tm, tn;
     oz_tile_coords(p, p.split_first + widx, tm, tn);
@@ -1032,6 +1022,24 @@ __global__ void __launch_bounds__(256) oz_tail_kernel(const __grid_constant__ Oz
         p.Cd[off] = v;
         if (p.tri && i != j) p.Cd[(size_t)j * p.ldc + i] = v;
     }
+}
+
+__global__ void __launch_bounds__(256) oz_tail_kernel(const __grid_constant__ OzParams p) {
+    oz_tail_tile(p, blockIdx.x);
+}
+
+// The tails of every split problem of a grouped launch: block x is split tile
+// x - tail_start of the last problem whose tail_start <= x (problems without a
+// split add no tiles, so that one is always a split problem).
+__global__ void __launch_bounds__(256) oz_tail_grouped_kernel(const OzGroupDesc* __restrict__ d, int nd) {
+    const int x = blockIdx.x;
+    int lo = 0, hi = nd - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d[mid].tail_start <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    oz_tail_tile(d[lo].p, x - d[lo].tail_start);
 }
 
 // Accurate mode, second pass: C = alpha sum_c ws[c] + b1 D1 + b2 D2 (chunk order).
@@ -1142,6 +1150,34 @@ static dme_status oz_launch_single(const CUtensorMap& tA, const CUtensorMap& tB,
     return DME_OK;
 }
 
+// The split of K of a problem (not the accurate mode), from the problem alone: with a
+// workspace (p.ws), the last partial wave in two K halves when it fills at most half
+// of the SMs (it then takes about half a tile time instead of a whole one), or a
+// single partial wave of skinny products in up to 4 K parts of at least 8 K blocks,
+// within the SM count and the workspace's 2 x OZ_SPLIT_MAX_TAIL tile slots.  The
+// single-problem and the grouped launches both apply it, so a problem gives the same
+// bits in either.
+static void oz_split_rule(OzParams& p, int nsm) {
+    const int tiles = p.tiles;
+    p.split_parts = 1;
+    p.split_first = tiles;
+    const int tail = tiles % nsm;
+    if (p.ws && tiles > nsm && tail > 0 && tail <= OZ_SPLIT_MAX_TAIL && tail <= nsm / 2 && p.Kp / OZ_BK >= 16) {
+        p.split_parts = 2;
+        p.split_first = tiles - tail;
+    } else if (p.ws && tiles <= nsm / 2 && tiles <= OZ_SPLIT_MAX_TAIL && p.Kp / OZ_BK >= 16) {
+        int parts = 1;
+        while (parts < 4 && tiles * (parts * 2) <= nsm && tiles * (parts * 2) <= 2 * OZ_SPLIT_MAX_TAIL &&
+               p.Kp / OZ_BK / (parts * 2) >= 8)
+            parts *= 2;
+        if (parts > 1) {
+            p.split_parts = parts;
+            p.split_first = 0;
+        }
+    }
+    p.units = p.split_first + (tiles - p.split_first) * p.split_parts;
+}
+
 dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzParams p, cudaStream_t st) {
     if (p.M <= 0 || p.N <= 0) return DME_OK;
     if (p.Kp % OZ_BK != 0 || p.Kp > OZ_MAX_K) {
@@ -1169,26 +1205,7 @@ dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzPar
         p.nchunks = (p.Kp / OZ_BK + OZ_ACC_CHUNK_KB - 1) / OZ_ACC_CHUNK_KB;
         p.units = tiles * p.nchunks;
     } else {
-        // split K of the last partial wave in two when it fills at most half of the SMs:
-        // the wave then takes about half a tile time instead of a whole one
-        const int tail = tiles % nsm;
-        if (p.ws && tiles > nsm && tail > 0 && tail <= OZ_SPLIT_MAX_TAIL && tail <= nsm / 2 &&
-            p.Kp / OZ_BK >= 16) {
-            p.split_parts = 2;
-            p.split_first = tiles - tail;
-        } else if (p.ws && tiles <= nsm / 2 && tiles <= OZ_SPLIT_MAX_TAIL && p.Kp / OZ_BK >= 16) {
-            // a single partial wave (skinny products): up to 4 K parts, at least 8 K blocks each,
-            // within the SM count and the workspace's 2 x OZ_SPLIT_MAX_TAIL tile slots
-            int parts = 1;
-            while (parts < 4 && tiles * (parts * 2) <= nsm && tiles * (parts * 2) <= 2 * OZ_SPLIT_MAX_TAIL &&
-                   p.Kp / OZ_BK / (parts * 2) >= 8)
-                parts *= 2;
-            if (parts > 1) {
-                p.split_parts = parts;
-                p.split_first = 0;
-            }
-        }
-        p.units = p.split_first + (tiles - p.split_first) * p.split_parts;
+        oz_split_rule(p, nsm);
     }
     // short and wide products (the Riccati update of large plans): two CTAs per SM (never
     // split: Kp / 32 < 16).  Narrower ones keep the four accumulators, so that a plan's
@@ -1243,8 +1260,6 @@ dme_status launch_ozaki_grouped(std::vector<OzGroupDesc>& items, OzGroupDesc* de
     // kernel cutting the 10-product problems at level 3), or 14 alone
     int total = 0, cfg = -1;
     std::vector<OzGroupDesc> live;
-    std::stable_sort(items.begin(), items.end(),
-                     [](const OzGroupDesc& x, const OzGroupDesc& y) { return x.p.Kp > y.p.Kp; });
     for (auto& it : items) {
         OzParams& p = it.p;
         if (p.M <= 0 || p.N <= 0) continue;
@@ -1258,12 +1273,19 @@ dme_status launch_ozaki_grouped(std::vector<OzGroupDesc>& items, OzGroupDesc* de
         const int tmt = (p.M + OZ_BM - 1) / OZ_BM, tnt = (p.N + OZ_BN - 1) / OZ_BN;
         p.tiles_n = tnt;
         p.tiles = p.tri ? tnt * (tnt + 1) / 2 : tmt * tnt;
-        p.split_parts = 1;
-        p.split_first = p.tiles;
-        p.units = p.tiles;
-        it.start = total;
-        total += p.tiles;
+        oz_split_rule(p, sm_count());
         live.push_back(it);
+    }
+    // the longest units (K per unit) first, so that they start in the first wave
+    std::stable_sort(live.begin(), live.end(), [](const OzGroupDesc& x, const OzGroupDesc& y) {
+        return x.p.Kp / x.p.split_parts > y.p.Kp / y.p.split_parts;
+    });
+    int tail_total = 0;
+    for (auto& it : live) {
+        it.start = total;
+        total += it.p.units;
+        it.tail_start = tail_total;
+        if (it.p.split_parts > 1) tail_total += it.p.tiles - it.p.split_first;
     }
     if (total == 0) return DME_OK;
     DME_TRY(ozaki_grouped_prepare());
@@ -1285,6 +1307,11 @@ dme_status launch_ozaki_grouped(std::vector<OzGroupDesc>& items, OzGroupDesc* de
             break;
     }
     DME_CUDA_TRY(cudaGetLastError());
+    // the parts of the split problems added and their epilogues run, in one launch
+    if (tail_total > 0) {
+        oz_tail_grouped_kernel<<<dim3(tail_total, OZ_BM / 8), 256, 0, st>>>(d, nd);
+        DME_CUDA_TRY(cudaGetLastError());
+    }
     return DME_OK;
 }
 

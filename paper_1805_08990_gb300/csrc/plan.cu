@@ -1040,7 +1040,10 @@ void dme::free_plan(dme_plan_t p) {
     delete p;
 }
 
-size_t dme::plan_estimate_bytes(const dme_plan_desc& d) {
+// Split plans from this size on hold a split-K workspace (their products have K >= 512).
+constexpr int kSplitKMinN = 512;
+
+size_t dme::plan_estimate_bytes(const dme_plan_desc& d, bool serving) {
     const size_t nn = (size_t)d.n * d.n * sizeof(double);
     int taus = 0;
     for (int i = 0; i < d.nflows; ++i) taus += (d.flows[i] == DME_F1 || d.flows[i] == DME_F12) ? 1 : 0;
@@ -1051,6 +1054,7 @@ size_t dme::plan_estimate_bytes(const dme_plan_desc& d) {
     if (d.prec == DME_SPLIT_BF16) {
         const size_t sl = (size_t)d.n * slice_kpad(d.n) * 2;           // one bf16 slice plane
         split = (5 * (size_t)taus + 5 + 8) * sl + nn;                   // E^T / S slices, P and U slices, U pairs
+        if (d.n >= kSplitKMinN && (!serving || d.n > 1536)) split += OZ_SPLIT_WS_FLOAT2 * sizeof(float2);
     }
     return persistent + transient + split + (size_t)d.n * 64 * sizeof(double) + (1u << 20);
 }
@@ -1060,7 +1064,7 @@ namespace {
 }  // namespace
 
 dme_status dme::plan_create(const dme_plan_desc* d, const double* A, const double* QorC, const double* B,
-                            const double* R, const double* S, void* stream, dme_plan_t* out) {
+                            const double* R, const double* S, void* stream, dme_plan_t* out, bool serving) {
     DME_TRY(validate(d, A, QorC, B, R, S));
     if (d->prec == DME_SPLIT_BF16 && d->n > OZ_MAX_K) {
         set_error("DME_SPLIT_BF16 supports n <= 4096 (exact slice accumulation over K <= 4096)");
@@ -1134,10 +1138,15 @@ dme_status dme::plan_create(const dme_plan_desc* d, const double* A, const doubl
         DME_TRY(alloc_slices(p, &p->psl, n, n, OZ_SLICES_STEP));
         DME_TRY(alloc_slices(p, &p->usl, n, n, OZ_SLICES_STEP));
         DME_TRY(palloc_t(p, &p->U, nn));
-        if (n > 1536) {    // only then does a GEMM have a full wave of tiles (split K of the tail)
+        if (n >= kSplitKMinN && (!serving || n > 1536)) {
+            // split K (K >= 512): the single partial wave of a product of at most 76 tiles
+            // (n <= 1024 here), or the last partial wave of one with more tiles than SMs
+            // (n > 1536; the plan's own tensor Riccati products need it in serving too)
             DME_TRY(palloc_t(p, &p->kws, OZ_SPLIT_WS_FLOAT2));
             DME_TRY(palloc_t(p, &p->kcnt, (size_t)OZ_SPLIT_MAX_TAIL));
             DME_CUDA_TRY(cudaMemsetAsync(p->kcnt, 0, sizeof(int) * OZ_SPLIT_MAX_TAIL, st));
+        }
+        if (n > 1536) {
             if (ric) {
                 // the Riccati products on the tensor cores (below 1537 the FP64 kernels are
                 // cheap, and serving, which uses them, stays bit-identical to single plans)

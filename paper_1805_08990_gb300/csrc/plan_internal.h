@@ -97,9 +97,11 @@ struct dme_plan_s {
 
 namespace dme {
 
-// Build a plan (validated descriptor; pointers host or device).
+// Build a plan (validated descriptor; pointers host or device).  A serving plan
+// (grouped launches, which never split K: at the server's loads splitting only adds
+// units and tail work to launches that are already full) holds no split-K workspace.
 dme_status plan_create(const dme_plan_desc* d, const double* A, const double* QorC, const double* B,
-                       const double* R, const double* S, void* stream, dme_plan_t* out);
+                       const double* R, const double* S, void* stream, dme_plan_t* out, bool serving = false);
 // Free a plan and everything it owns (synchronises its stream).
 void free_plan(dme_plan_t p);
 // Compile one step of size h into p->ops (computes missing E_t, W_t).
@@ -107,7 +109,7 @@ dme_status build_ops(dme_plan_t p, double h);
 // Enqueue one op on the plan's stream.
 dme_status run_op(dme_plan_t p, const Op& o, double* P);
 // Bytes reserved while a plan of this descriptor is built (persistent + transient).
-size_t plan_estimate_bytes(const dme_plan_desc& d);
+size_t plan_estimate_bytes(const dme_plan_desc& d, bool serving = false);
 // E_t, W_t of the plan for step t (computed and cached on first use): index into p->ew.
 dme_status plan_ew(dme_plan_t p, double t, int* idx);
 // Report (and clear) the plan's device status word after synchronising its stream.

@@ -163,7 +163,7 @@ void admit_loop(dme_server_t s) {
             s->cv.wait(lk, [&] {
                 if (s->stop) return true;
                 if (s->queue.empty() || s->free_slots.empty()) return false;
-                return s->reserved + plan_estimate_bytes(s->queue.front()->desc) <= s->budget;
+                return s->reserved + plan_estimate_bytes(s->queue.front()->desc, true) <= s->budget;
             });
             if (s->stop) return;
             r = s->queue.front();
@@ -171,7 +171,7 @@ void admit_loop(dme_server_t s) {
             r->state = Q_PLANNING;
             r->slot = s->free_slots.back();
             s->free_slots.pop_back();
-            r->reserved = plan_estimate_bytes(r->desc);
+            r->reserved = plan_estimate_bytes(r->desc, true);
             s->reserved += r->reserved;
         }
         set_error("");
@@ -180,7 +180,7 @@ void admit_loop(dme_server_t s) {
         const double* Rp = r->R.empty() ? nullptr : r->R.data();
         const double* Sp = r->S.empty() ? nullptr : r->S.data();
         const double tp0 = now_s();
-        dme_status st = plan_create(&r->desc, r->A.data(), r->QC.data(), Bp, Rp, Sp, nullptr, &p);
+        dme_status st = plan_create(&r->desc, r->A.data(), r->QC.data(), Bp, Rp, Sp, nullptr, &p, true);
         const double tp1 = now_s();
         const size_t nn = (size_t)r->desc.n * r->desc.n;
         if (st == DME_OK) {
@@ -443,6 +443,7 @@ dme_status run_lane(dme_server_t s, std::vector<Req*>& res, int lane) {
                 a.p.ldc = n;
                 a.p.Cp = p->U;
                 a.p.status = s->dstat + r->slot;
+
                 o1c[p->cfg == OZ_P14].push_back(a);
                 OzGroupDesc b;
                 std::memset(&b, 0, sizeof(b));
@@ -762,7 +763,7 @@ dme_status submit_impl(dme_server_t s, const dme_plan_desc* desc, const double* 
         r->nsteps = nsteps;
         r->gain = gain;
         std::lock_guard<std::mutex> g(s->mu);
-        if (plan_estimate_bytes(r->desc) > s->budget)
+        if (plan_estimate_bytes(r->desc, true) > s->budget)
             return set_error("request footprint exceeds the server's HBM budget"), DME_ENOMEM;
         if (s->queue.size() >= s->queue_cap) return set_error("queue full"), DME_EBUSY;
         r->id = s->next_id++;

@@ -97,7 +97,8 @@ struct OzGroupDesc {
     CUtensorMap tmA;
     CUtensorMap tmB;
     OzParams p;
-    int start;            // first unit (tile) index (set by the launcher)
+    int start;            // first unit index (set by the launcher)
+    int tail_start;       // first split tile in the launch's tail kernel (set by the launcher)
 };
 
 // One problem of a grouped slicing launch (rows of X or of pair matrix Xp).
@@ -137,9 +138,11 @@ dme_status oz_params(const SliceBuf& A, const SliceBuf& B, int cfg, OzParams* p)
 size_t oz_acc_ws_doubles(int M, int N, int K);
 dme_status launch_ozaki_gemm(const CUtensorMap& tA, const CUtensorMap& tB, OzParams p, cudaStream_t st);
 // Grouped launch over independent problems: items of 10 and 13 slice products
-// together, or of 14 alone (not the accurate mode), reordered by K, largest
-// first, so that the longest tiles start in the first wave; dev_desc holds
-// items.size() descriptors.
+// together, or of 14 alone (not the accurate mode), ordered by K per unit,
+// largest first, so that the longest units start in the first wave.  A problem
+// with a workspace (p.ws) splits K by the same rule as its single-problem
+// launch (and gives the same bits); one tail launch adds the parts of every
+// split problem.  dev_desc holds items.size() descriptors.
 // Set the grouped kernel's shared-memory attribute (before any stream capture).
 dme_status ozaki_grouped_prepare();
 // With `arena` the descriptors are staged there instead of copied to dev_desc.
