@@ -42,10 +42,10 @@ NOMINAL_FP64_TFLOPS = 1.25    # GB300 FP64 (non-tensor and tensor), the profilin
 FP64_MAX_STEPS = 16
 
 # DRAM bytes (read + write) per launch of the tensor kernel in the congruence at n = 4096
-# (10 slice products), the mean of its two launches (U = G P: 871.8 + 157.5 MB; the
-# triangle G U^T: 656.3 + 122.5 MB), from the ncu capture summarised in
+# (10 slice products), the mean of its two launches (U = G P: 872.1 + 157.5 MB; the
+# triangle G U^T: 657.0 + 121.7 MB), from the ncu capture summarised in
 # profiles/ozaki_gemm_n4096_ncu.md; None while the kernel has changed since that capture.
-OZAKI_LAUNCH_DRAM_BYTES = 0.5 * ((871.8 + 157.5) + (656.3 + 122.5)) * 1e6
+OZAKI_LAUNCH_DRAM_BYTES = 0.5 * ((872.1 + 157.5) + (657.0 + 121.7)) * 1e6
 
 
 def load_peaks():
