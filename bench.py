@@ -342,6 +342,8 @@ def run_serving_suite(args):
                      "burst_plan_ms_mean": burst.get("plan_ms_mean"),
                      "burst_split_pairs_10_13_14": burst.get("split_pairs_10_13_14"),
                      "saturation_roofline": serving_roofline(burst, prec, peaks), "loads": rows}
+    if args.serving_oracle > 0:
+        out["cpu_baseline"] = serving_oracle_run(args.serving_oracle)
     print(json.dumps({"serving_suite": out, "workload": "n log-uniform 32..1024 (Laplacian or stable random A), "
                       "m, p ~ U{1..8}, R = I_m, T ~ U[0.1, 10], 50-500 Strang F12F3 steps, P0 = 0, Poisson arrivals",
                       "max_slots": 32}))
@@ -384,6 +386,35 @@ def run_reference(args):
             "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def serving_oracle_run(count: int, seed: int = 3, n_max: int = 1024):
+    """CPU baseline of the serving configuration: the oracle (numpy/OpenBLAS, FP64,
+    all host threads) solving the first `count` requests of the same stream
+    (seed 3, as the serving suite's Poisson streams) one after another, each
+    with its own 2n x 2n exponential for E, W and its Strang F12F3 steps from
+    P0 = 0.  A bounded sample: the oracle is slow, the GPU server serves
+    10,000 such requests per load."""
+    import oracle as O
+    specs = W.serving_requests(count, seed=seed, n_max=n_max)
+    t_plan = 0.0
+    t0 = time.perf_counter()
+    for sp in specs:
+        pr = W.materialize(sp)
+        tp = time.perf_counter()
+        plan = O.Plan(pr.A, pr.Q, pr.B, pr.R)
+        plan.EW(0.5 * pr.T / sp["steps"])
+        t_plan += time.perf_counter() - tp
+        O.solve(pr.A, pr.Q, pr.P0, pr.T, sp["steps"], "strang", ["F12", "F3"], B=pr.B, R=pr.R, plan=plan)
+    wall = time.perf_counter() - t0
+    ns = [sp["n"] for sp in specs]
+    return {"value": count / wall, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "wall_s": wall, "plan_s": t_plan, "requests": count,
+            "steps_total": int(sum(sp["steps"] for sp in specs)),
+            "n_median": float(statistics.median(ns)), "n_max": int(max(ns)),
+            "sample": f"the first {count} requests of the serving stream (seed {seed}: n log-uniform "
+                      f"32..{n_max}, 50-500 Strang F12F3 steps), solved one after another by the oracle "
+                      "with all host threads, its 2n x 2n exponential included"}
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -913,6 +944,8 @@ def main():
                     help="run only the steps/s of the other workload configurations")
     ap.add_argument("--serving-suite", type=int, default=0,
                     help="run only the serving loads 0.5/0.9/1.2 x saturation with this many split requests")
+    ap.add_argument("--serving-oracle", type=int, default=0,
+                    help="--serving-suite: also time the CPU oracle on this many requests of the stream")
     ap.add_argument("--serving-suite-fp64", type=int, default=0,
                     help="FP64 requests per load of the serving suite (0: an eighth of the split count)")
     ap.add_argument("--lowrank-steps", type=int, default=32)
@@ -933,6 +966,10 @@ def main():
         return run_cong_only(args)
     if args.serving_suite:
         return run_serving_suite(args)
+    if args.serving_oracle:
+        # the serving configuration's CPU baseline alone (no GPU work)
+        print(json.dumps({"serving_cpu_baseline": serving_oracle_run(args.serving_oracle)}), flush=True)
+        return 0
     if args.config_suite:
         return run_config_suite(args)
     return run_ours(args)

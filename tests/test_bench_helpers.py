@@ -90,3 +90,16 @@ def test_are_residual_is_zero_at_the_care_solution():
     t = lambda x: torch.as_tensor(x, dtype=torch.float64)    # noqa: E731
     assert bench.are_residual(t(X), t(A), t(Q), t(Bt)) < 1e-12
     assert bench.are_residual(t(X * 1.01), t(A), t(Q), t(Bt)) > 1e-4
+
+
+def test_serving_oracle_baseline_solves_the_stream_prefix():
+    """The serving CPU baseline times the oracle on the first requests of the
+    stream; with small n it runs in well under a second here, reports its
+    sample and equals the count over its wall time."""
+    out = bench.serving_oracle_run(2, seed=3, n_max=40)
+    specs = W.serving_requests(2, seed=3, n_max=40)
+    assert out["kind"] == "oracle" and out["unit"] == "solves/s" and out["requests"] == 2
+    assert out["steps_total"] == sum(sp["steps"] for sp in specs)
+    assert out["n_max"] == max(sp["n"] for sp in specs) <= 40
+    assert math.isclose(out["value"], 2 / out["wall_s"], rel_tol=1e-12)
+    assert 0 <= out["plan_s"] <= out["wall_s"]
