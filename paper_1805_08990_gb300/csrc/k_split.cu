@@ -18,7 +18,8 @@
 // Kernel shape: persistent, one CTA per SM, 10 warps, 128 x 128 output tiles:
 //   warp 0  TMA producer (one thread): a ring of STAGES stages, each holding
 //           the SA slices of a 128 x 32 A tile and the SB slices of a 128 x 32
-//           B tile (64-byte swizzled rows, one TMA load per slice plane),
+//           B tile (64-byte swizzled rows; one 3-D box per operand and stage,
+//           {32 k, 128 rows, planes}, the planes 8 KB apart),
 //   warp 1  TMEM allocator + MMA issuer (one thread): 2 x pairs tcgen05.mma
 //           per stage into the four accumulators (512 TMEM columns),
 //   warps 2-9 epilogue, two warps per TMEM lane quadrant, each on 64 columns:
